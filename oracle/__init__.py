@@ -1,0 +1,206 @@
+"""CPU FP64 oracle for the standing-wave shooting Jacobian (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its Python binding) never touches it, and the two share no code.
+
+The arithmetic lives in ``ww_oracle.c`` (plain C99, IEEE double, optional
+OpenMP over independent rows/columns).  This module compiles it with gcc on
+first use and exposes thin numpy wrappers.  Each wrapper names the passage of
+the paper the C function follows:
+
+* ``fft``            -- textbook radix-2 DFT used for every spectral step
+* ``spectral``       -- Fourier multipliers: d/dx, Hilbert (-i sgn k),
+                        36th-order filter (Eq. filter), projection P
+* ``dtn_matrices``   -- A = 1/2 I + K and G of Eq. (K1K2) (image sign: reading R1)
+* ``dtn``            -- Dirichlet-to-Neumann operator, Eqs. (fred), (G)
+* ``rhs``            -- Eq. (ww) base RHS and Eqs. (l5a), (l6a) variational RHS
+* ``shoot``          -- r and f of Eq. (f:phi)
+* ``shoot_jacobian`` -- J of Eqs. (Jik), (q:qdot), T column by reading R2
+* ``energy``         -- the energy monitor of Sec. 4
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ww_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libww_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ww_oracle.c into oracle/_build/libww_oracle.so (gcc -O2 -fopenmp)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Problem(C.Structure):
+    _fields_ = [
+        ("N", C.c_int), ("n", C.c_int), ("g", C.c_double), ("tau", C.c_double),
+        ("h", C.c_double), ("steps", C.c_int), ("basis", C.POINTER(C.c_double)),
+    ]
+
+
+_D = C.POINTER(C.c_double)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            P = C.POINTER(Problem)
+            sig = {
+                "orc_fft": (None, [C.c_int, _D, C.c_int]),
+                "orc_spectral": (None, [C.c_int, C.c_int, _D, _D]),
+                "orc_assemble": (None, [C.c_int, C.c_double, _D, _D, _D, _D, _D]),
+                "orc_dtn_matrices": (None, [C.c_int, C.c_double, _D, _D, _D]),
+                "orc_dtn": (None, [C.c_int, C.c_double, _D, _D, C.c_int, _D]),
+                "orc_lu": (C.c_int, [C.c_int, _D, C.POINTER(C.c_int)]),
+                "orc_lu_solve": (None, [C.c_int, _D, C.POINTER(C.c_int), _D, _D]),
+                "orc_rhs": (None, [P, C.c_double, _D, C.c_int, C.c_int, _D]),
+                "orc_initial": (None, [P, _D, _D]),
+                "orc_evolve": (None, [P, C.c_double, _D, _D]),
+                "orc_evolve_columns": (None, [P, C.c_double, _D, _D, C.c_int, C.c_int, _D]),
+                "orc_shoot": (None, [P, _D, _D, _D]),
+                "orc_shoot_jacobian": (None, [P, _D, _D, _D, _D]),
+                "orc_energy": (C.c_double, [P, _D]),
+                "orc_threads": (C.c_int, []),
+                "orc_set_threads": (None, [C.c_int]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+MUL_DERIV, MUL_HILBERT, MUL_FILTER, MUL_PROJECT = 0, 1, 2, 3
+
+
+def threads() -> int:
+    return lib().orc_threads()
+
+
+def set_threads(t: int) -> None:
+    lib().orc_set_threads(int(t))
+
+
+def make_problem(N, n, g=1.0, tau=0.0, h=1.0, steps=64, basis=None):
+    """Return (Problem, keepalive) -- the basis array must outlive the struct."""
+    keep = None
+    bp = C.cast(None, _D)
+    if basis is not None:
+        keep = np.asfortranarray(np.asarray(basis, dtype=np.float64))
+        assert keep.shape == (2 * N, n)
+        keep = np.ascontiguousarray(keep.T)  # column k contiguous (2N each)
+        bp = _p(keep)
+    return Problem(int(N), int(n), float(g), float(tau), float(h), int(steps), bp), keep
+
+
+def fft(x, inverse=False) -> np.ndarray:
+    z = np.ascontiguousarray(np.asarray(x, dtype=np.complex128)).copy()
+    lib().orc_fft(len(z), z.ctypes.data_as(_D), 1 if inverse else 0)
+    return z
+
+
+def spectral(kind: int, f) -> np.ndarray:
+    f = _f64(f)
+    out = np.empty_like(f)
+    lib().orc_spectral(len(f), int(kind), _p(f), _p(out))
+    return out
+
+
+def dtn_matrices(eta, h):
+    """(A, G) row-major N x N: A = 1/2 I + K, Eq. (K1K2) / N."""
+    eta = _f64(eta)
+    N = len(eta)
+    A = np.empty((N, N)); G = np.empty((N, N))
+    lib().orc_dtn_matrices(N, float(h), _p(eta), _p(A), _p(G))
+    return A, G
+
+
+def dtn(eta, phi, h) -> np.ndarray:
+    """DtN of phi (shape (N,) or (nrhs, N)) on the surface eta, Eqs. (fred), (G)."""
+    eta = _f64(eta)
+    phi = _f64(phi)
+    one = phi.ndim == 1
+    phi2 = phi.reshape(1, -1) if one else phi
+    out = np.empty_like(phi2)
+    lib().orc_dtn(len(eta), float(h), _p(eta), _p(phi2), phi2.shape[0], _p(out))
+    return out[0] if one else out
+
+
+def rhs(prob: Problem, T: float, y, ncol: int, t_col: int = 0) -> np.ndarray:
+    """Filtered RHS; y has shape (ncol+1, 2N): row 0 = (eta, phi), rows 1.. = columns."""
+    y = _f64(y).reshape(ncol + 1, 2 * prob.N)
+    out = np.empty_like(y)
+    lib().orc_rhs(C.byref(prob), float(T), _p(y), int(ncol), int(t_col), _p(out))
+    return out
+
+
+def initial(prob: Problem, c) -> np.ndarray:
+    c = _f64(c)
+    q = np.empty(2 * prob.N)
+    lib().orc_initial(C.byref(prob), _p(c), _p(q))
+    return q
+
+
+def evolve(prob: Problem, T: float, q0) -> np.ndarray:
+    q0 = _f64(q0)
+    out = np.empty_like(q0)
+    lib().orc_evolve(C.byref(prob), float(T), _p(q0), _p(out))
+    return out
+
+
+def evolve_columns(prob: Problem, T: float, q0, cols, t_col: int = 0) -> np.ndarray:
+    q0 = _f64(q0)
+    cols = _f64(cols)
+    ncol = cols.shape[0]
+    out = np.empty((ncol + 1, 2 * prob.N))
+    lib().orc_evolve_columns(C.byref(prob), float(T), _p(q0), _p(cols), ncol, int(t_col), _p(out))
+    return out
+
+
+def shoot(prob: Problem, c):
+    c = _f64(c)
+    r = np.empty(prob.N); f = np.empty(1)
+    lib().orc_shoot(C.byref(prob), _p(c), _p(r), _p(f))
+    return r, float(f[0])
+
+
+def shoot_jacobian(prob: Problem, c):
+    """(r, J, f) with J of shape (N, n+1) (column 0 = d r / d T)."""
+    c = _f64(c)
+    N, n = prob.N, prob.n
+    r = np.empty(N); f = np.empty(1)
+    Jc = np.empty((n + 1, N))  # column-major storage = row-major of J^T
+    lib().orc_shoot_jacobian(C.byref(prob), _p(c), _p(r), _p(Jc), _p(f))
+    return r, np.ascontiguousarray(Jc.T), float(f[0])
+
+
+def energy(prob: Problem, q) -> float:
+    q = _f64(q)
+    return float(lib().orc_energy(C.byref(prob), _p(q)))

@@ -1,0 +1,529 @@
+/*
+ * ww_oracle.c -- plain, slow, obviously-correct CPU FP64 oracle for the
+ * Jacobian of the standing-water-wave shooting map (Wilkening & Yu,
+ * "Overdetermined shooting methods for computing standing water waves with
+ * spectral accuracy").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: only the tests, the smoke check and the CPU-baseline leg
+ * of the benchmark do.  It shares no code, header, table or helper with the
+ * CUDA path.
+ *
+ * Everything is IEEE double.  Complex arithmetic uses C99 <complex.h>, the
+ * cotangent is the textbook cos/sin quotient (not the branch formula of
+ * Sec. 2.2, which the GPU uses), the linear solve is LU with partial
+ * pivoting, and the FFT is a textbook iterative radix-2 transform whose
+ * twiddles are evaluated directly with cos/sin.  OpenMP (when compiled with
+ * -fopenmp) only distributes independent rows / columns over threads; it
+ * does not change any arithmetic.
+ *
+ * Paper references are by section / equation:
+ *   Eq. (ww)            free-surface Euler equations               Sec. 2.1
+ *   Eqs. (fred), (G)    DtN in three steps                          Sec. 2.1
+ *   Eq. (uv:from:G)     surface velocities from (phi', G phi)       Sec. 2.1
+ *   Eq. (K1K2)          regularised kernels, trapezoid collocation  Sec. 2.2
+ *   Eq. (filter)        36th-order filter                           Sec. 2.2
+ *   Eqs. (Phi), (plemelj:1), (plemelj:2)  image-kernel signs        App. A
+ *   Eqs. (l5a), (l6a)   linearised (variational) equations          App. B
+ *   Eqs. (f:phi), (Jik), (q:qdot)  objective and Jacobian           Sec. 3.1, 3.3
+ *
+ * Readings where the paper is garbled or silent (listed again in the design doc):
+ *  R1 image terms K2, G2 carry a MINUS sign (the integrals of App. A subtract
+ *     the mirror-image double layer; the printed "+" in Eq. (K1K2) gives the
+ *     symbol k coth(kh) on a flat surface instead of k tanh(kh)).
+ *  R2 the T column of J is the variational column w = dq/dT of the discrete
+ *     map, w' = DF(q) w + F(q)/T, w(0) = 0, integrated by the same RK4.
+ *  R3 derivatives and the Hilbert transform zero the Nyquist mode; second
+ *     derivatives are two first derivatives; P removes the k = 0 mode.
+ *  R4 the filter multiplies every RHS evaluation and the state after each
+ *     full RK4 step (not after stages), base and variational columns alike.
+ *  R5 residual weight w = sqrt(1/N) (uniform grid, E = 1 in Eq. (f:phi)).
+ *  R6 the linearisation is the continuum one of App. B with the shared
+ *     discrete DtN operator (K and G are not differentiated).
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+/* ------------------------------------------------------------------ */
+/* Problem description (oracle-side copy; the CUDA path has its own). */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int N;          /* grid points alpha_j = 2 pi j / N (uniform, xi = alpha)   */
+    int n;          /* number of mode unknowns c_1..c_n                         */
+    double g;       /* gravity                                                  */
+    double tau;     /* surface tension sigma/rho                                */
+    double h;       /* mean depth; isinf(h) => infinite depth, no image kernels */
+    int steps;      /* RK4 steps from 0 to T/4                                  */
+    const double *basis; /* 2N x n column-major (eta rows, then phi rows) or NULL
+                            for the default column k = (cos kx, 0)             */
+} orc_problem;
+
+static const double TWO_PI = 6.283185307179586476925286766559;
+
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
+/* ------------------------------------------------------------------ */
+/* FFT: textbook iterative radix-2 Cooley-Tukey, N a power of two.     */
+/* forward: X_k = sum_j x_j exp(-2 pi i jk/N); inverse divides by N.   */
+/* ------------------------------------------------------------------ */
+void orc_fft(int N, cplx *x, int inverse)
+{
+    /* bit-reversal permutation */
+    for (int i = 1, j = 0; i < N; ++i) {
+        int bit = N >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) { cplx t = x[i]; x[i] = x[j]; x[j] = t; }
+    }
+    double sgn = inverse ? 1.0 : -1.0;
+    for (int len = 2; len <= N; len <<= 1) {
+        int half = len >> 1;
+        for (int s = 0; s < N; s += len) {
+            for (int k = 0; k < half; ++k) {
+                double ang = sgn * TWO_PI * (double)k / (double)len;
+                cplx w = cos(ang) + I * sin(ang);
+                cplx u = x[s + k];
+                cplx v = x[s + k + half] * w;
+                x[s + k] = u + v;
+                x[s + k + half] = u - v;
+            }
+        }
+    }
+    if (inverse)
+        for (int i = 0; i < N; ++i) x[i] /= (double)N;
+}
+
+/* signed wavenumber of FFT slot j */
+static int wavenumber(int N, int j) { return j <= N / 2 ? j : j - N; }
+
+/* Fourier multipliers (Sec. 2.1, 2.2; readings R3, R4) */
+enum { MUL_DERIV = 0, MUL_HILBERT = 1, MUL_FILTER = 2, MUL_PROJECT = 3 };
+
+static cplx multiplier(int kind, int N, int k)
+{
+    int nyq = (k == N / 2 || k == -N / 2);
+    switch (kind) {
+    case MUL_DERIV:   return nyq ? 0.0 : I * (double)k;               /* d/dx     */
+    case MUL_HILBERT: return nyq ? 0.0 : -I * (double)((k > 0) - (k < 0)); /* H   */
+    case MUL_FILTER: {                                                 /* Eq. (filter) */
+        double r = fabs((double)k) / (double)(N / 2);
+        return exp(-36.0 * pow(r, 36.0));
+    }
+    case MUL_PROJECT: return k == 0 ? 0.0 : 1.0;                       /* P = id - P0 */
+    }
+    return 0.0;
+}
+
+/* out = Re IFFT( m(k) * FFT(in) ); in and out may alias */
+void orc_spectral(int N, int kind, const double *in, double *out)
+{
+    cplx *x = malloc(sizeof(cplx) * N);
+    for (int j = 0; j < N; ++j) x[j] = in[j];
+    orc_fft(N, x, 0);
+    for (int j = 0; j < N; ++j) x[j] *= multiplier(kind, N, wavenumber(N, j));
+    orc_fft(N, x, 1);
+    for (int j = 0; j < N; ++j) out[j] = creal(x[j]);
+    free(x);
+}
+
+/* ------------------------------------------------------------------ */
+/* Kernel assembly, Eq. (K1K2) with reading R1; trapezoid rule (Sec. 2.2) */
+/* ------------------------------------------------------------------ */
+static cplx ccot(cplx z) { return ccos(z) / csin(z); }
+
+/* A = 1/2 I + K and G, both row-major N x N: row i = collocation point
+ * alpha_i, column j = quadrature point beta = alpha_j; entries divided by N. */
+void orc_assemble(int N, double h, const double *eta, const double *eta_x,
+                  const double *eta_xx, double *A, double *G)
+{
+    int deep = isinf(h);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int i = 0; i < N; ++i) {
+        double ai = TWO_PI * i / N;
+        cplx zi = ai + I * eta[i];
+        cplx dzi = 1.0 + I * eta_x[i];
+        cplx ddzi = I * eta_xx[i];
+        for (int j = 0; j < N; ++j) {
+            double aj = TWO_PI * j / N;
+            cplx zj = aj + I * eta[j];
+            cplx dzj = 1.0 + I * eta_x[j];
+            double k1, g1, k2 = 0.0, g2 = 0.0;
+            if (i == j) {                       /* diagonal limits, Sec. 2.2 */
+                k1 = -cimag(ddzi / (2.0 * dzi));
+                g1 = creal(ddzi / (2.0 * dzi));
+            } else {
+                cplx c = ccot((zi - zj) / 2.0);
+                cplx c0 = ccot((cplx)((ai - aj) / 2.0));
+                k1 = cimag(dzj / 2.0 * c - 0.5 * c0);
+                g1 = creal(dzi / 2.0 * c - 0.5 * c0);
+            }
+            if (!deep) {                        /* mirror image, reading R1 */
+                cplx cb = ccot((zi - conj(zj)) / 2.0);
+                k2 = -cimag(conj(dzj) / 2.0 * cb);
+                g2 = -creal(dzi / 2.0 * cb);
+            }
+            A[(size_t)i * N + j] = (k1 + k2) / N + (i == j ? 0.5 : 0.0);
+            G[(size_t)i * N + j] = (g1 + g2) / N;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* LU with partial pivoting (row-major, in place) and solve.            */
+/* ------------------------------------------------------------------ */
+int orc_lu(int N, double *A, int *piv)
+{
+    for (int k = 0; k < N; ++k) {
+        int p = k;
+        double best = fabs(A[(size_t)k * N + k]);
+        for (int i = k + 1; i < N; ++i)
+            if (fabs(A[(size_t)i * N + k]) > best) { best = fabs(A[(size_t)i * N + k]); p = i; }
+        piv[k] = p;
+        if (best == 0.0) return -1;
+        if (p != k)
+            for (int j = 0; j < N; ++j) {
+                double t = A[(size_t)k * N + j];
+                A[(size_t)k * N + j] = A[(size_t)p * N + j];
+                A[(size_t)p * N + j] = t;
+            }
+        double d = A[(size_t)k * N + k];
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) if (N - k > 256)
+#endif
+        for (int i = k + 1; i < N; ++i) {
+            double l = A[(size_t)i * N + k] / d;
+            A[(size_t)i * N + k] = l;
+            double *ri = A + (size_t)i * N;
+            const double *rk = A + (size_t)k * N;
+            for (int j = k + 1; j < N; ++j) ri[j] -= l * rk[j];
+        }
+    }
+    return 0;
+}
+
+/* x = A^{-1} b using the factors of orc_lu; b and x may alias */
+void orc_lu_solve(int N, const double *LU, const int *piv, const double *b, double *x)
+{
+    if (x != b) memcpy(x, b, sizeof(double) * N);
+    for (int k = 0; k < N; ++k)
+        if (piv[k] != k) { double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
+    for (int i = 0; i < N; ++i) {            /* unit lower */
+        double s = x[i];
+        for (int j = 0; j < i; ++j) s -= LU[(size_t)i * N + j] * x[j];
+        x[i] = s;
+    }
+    for (int i = N - 1; i >= 0; --i) {       /* upper */
+        double s = x[i];
+        for (int j = i + 1; j < N; ++j) s -= LU[(size_t)i * N + j] * x[j];
+        x[i] = s / LU[(size_t)i * N + i];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* The per-stage DtN of the base surface (Sec. 2.1, Eqs. (fred), (G))  */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int N;
+    double *eta, *eta_x, *eta_xx;
+    double *LU, *G;
+    int *piv;
+} dtn_state;
+
+static void dtn_prepare(dtn_state *s, int N, double h, const double *eta)
+{
+    s->N = N;
+    s->eta = malloc(sizeof(double) * N);
+    s->eta_x = malloc(sizeof(double) * N);
+    s->eta_xx = malloc(sizeof(double) * N);
+    s->LU = malloc(sizeof(double) * (size_t)N * N);
+    s->G = malloc(sizeof(double) * (size_t)N * N);
+    s->piv = malloc(sizeof(int) * N);
+    memcpy(s->eta, eta, sizeof(double) * N);
+    orc_spectral(N, MUL_DERIV, eta, s->eta_x);
+    orc_spectral(N, MUL_DERIV, s->eta_x, s->eta_xx);
+    orc_assemble(N, h, s->eta, s->eta_x, s->eta_xx, s->LU, s->G);
+    orc_lu(N, s->LU, s->piv);
+}
+
+static void dtn_release(dtn_state *s)
+{
+    free(s->eta); free(s->eta_x); free(s->eta_xx);
+    free(s->LU); free(s->G); free(s->piv);
+}
+
+/* G phi on the surface: mu = A^{-1} phi; gamma = mu'; 1/2 H gamma + G gamma
+ * (|xi'| = 1 on the uniform grid). */
+static void dtn_apply_one(const dtn_state *s, const double *phi, double *out)
+{
+    int N = s->N;
+    double *mu = malloc(sizeof(double) * N);
+    double *gam = malloc(sizeof(double) * N);
+    double *hg = malloc(sizeof(double) * N);
+    orc_lu_solve(N, s->LU, s->piv, phi, mu);
+    orc_spectral(N, MUL_DERIV, mu, gam);
+    orc_spectral(N, MUL_HILBERT, gam, hg);
+    for (int i = 0; i < N; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < N; ++j) acc += s->G[(size_t)i * N + j] * gam[j];
+        out[i] = 0.5 * hg[i] + acc;
+    }
+    free(mu); free(gam); free(hg);
+}
+
+/* Public: DtN of phi (nrhs columns, each length N, contiguous) on surface eta. */
+void orc_dtn(int N, double h, const double *eta, const double *phi, int nrhs, double *out)
+{
+    dtn_state s;
+    dtn_prepare(&s, N, h, eta);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic)
+#endif
+    for (int c = 0; c < nrhs; ++c)
+        dtn_apply_one(&s, phi + (size_t)c * N, out + (size_t)c * N);
+    dtn_release(&s);
+}
+
+/* Public: the assembled matrices (for tests). */
+void orc_dtn_matrices(int N, double h, const double *eta, double *A, double *G)
+{
+    double *ex = malloc(sizeof(double) * N), *exx = malloc(sizeof(double) * N);
+    orc_spectral(N, MUL_DERIV, eta, ex);
+    orc_spectral(N, MUL_DERIV, ex, exx);
+    orc_assemble(N, h, eta, ex, exx, A, G);
+    free(ex); free(exx);
+}
+
+/* ------------------------------------------------------------------ */
+/* Right-hand sides: Eq. (ww) for the base state, Eqs. (l5a), (l6a) for  */
+/* every variational column; all outputs filtered (Eq. (filter)).        */
+/* ------------------------------------------------------------------ */
+
+/* state layout used by the oracle's time stepper: ncol+1 columns, each
+ * column = [eta (N) | phi (N)]; column 0 is the base state q, columns
+ * 1..ncol are the variational columns. */
+
+/* Evaluate the filtered RHS of the base state and of ncol variational
+ * columns.  t_col: index (1-based among the variational columns) of the
+ * column that additionally receives F(q)/T (reading R2), or 0 for none. */
+void orc_rhs(const orc_problem *p, double T, const double *y, int ncol, int t_col, double *out)
+{
+    int N = p->N;
+    const double *eta = y, *phi = y + N;
+    dtn_state s;
+    dtn_prepare(&s, N, p->h, eta);
+
+    double *phi_p = malloc(sizeof(double) * N);
+    double *Gphi = malloc(sizeof(double) * N);
+    double *ux = malloc(sizeof(double) * N);  /* phi_x on the surface */
+    double *vy = malloc(sizeof(double) * N);  /* phi_y on the surface */
+    double *w3 = malloc(sizeof(double) * N);  /* (1 + eta'^2)^{-3/2} */
+    double *tmp = malloc(sizeof(double) * N);
+
+    orc_spectral(N, MUL_DERIV, phi, phi_p);
+    dtn_apply_one(&s, phi, Gphi);
+    for (int i = 0; i < N; ++i) {              /* Eq. (uv:from:G) */
+        double ex = s.eta_x[i], d = 1.0 + ex * ex;
+        ux[i] = (phi_p[i] - ex * Gphi[i]) / d;
+        vy[i] = (ex * phi_p[i] + Gphi[i]) / d;
+        w3[i] = 1.0 / (d * sqrt(d));
+    }
+
+    /* base: eta_t = G phi ; phi_t = P[ v eta_t - u^2/2 - v^2/2 - g eta + tau d/dx(eta'/sqrt(1+eta'^2)) ] */
+    double *F = out;                 /* column 0 of out */
+    for (int i = 0; i < N; ++i) F[i] = Gphi[i];
+    for (int i = 0; i < N; ++i) {
+        double ex = s.eta_x[i];
+        tmp[i] = ex / sqrt(1.0 + ex * ex);
+    }
+    orc_spectral(N, MUL_DERIV, tmp, tmp);
+    for (int i = 0; i < N; ++i)
+        F[N + i] = vy[i] * Gphi[i] - 0.5 * ux[i] * ux[i] - 0.5 * vy[i] * vy[i]
+                   - p->g * eta[i] + p->tau * tmp[i];
+    orc_spectral(N, MUL_PROJECT, F + N, F + N);
+    orc_spectral(N, MUL_FILTER, F, F);
+    orc_spectral(N, MUL_FILTER, F + N, F + N);
+
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic)
+#endif
+    for (int c = 1; c <= ncol; ++c) {
+        const double *ed = y + (size_t)c * 2 * N, *pd = ed + N;
+        double *oe = out + (size_t)c * 2 * N, *op = oe + N;
+        double *psi = malloc(sizeof(double) * N), *Gpsi = malloc(sizeof(double) * N);
+        double *dpsi = malloc(sizeof(double) * N), *a = malloc(sizeof(double) * N);
+        double *b = malloc(sizeof(double) * N), *e1 = malloc(sizeof(double) * N);
+        /* psi = phidot - phi_y etadot : the perturbation potential on the surface */
+        for (int i = 0; i < N; ++i) psi[i] = pd[i] - vy[i] * ed[i];
+        dtn_apply_one(&s, psi, Gpsi);
+        orc_spectral(N, MUL_DERIV, psi, dpsi);
+        /* Eq. (l5a): etadot_t = G psi - (etadot u)' */
+        for (int i = 0; i < N; ++i) a[i] = ed[i] * ux[i];
+        orc_spectral(N, MUL_DERIV, a, a);
+        for (int i = 0; i < N; ++i) oe[i] = Gpsi[i] - a[i];
+        /* Eq. (l6a): phidot_t = P[ -(etadot u v)' - u psi' + v G psi - g etadot
+         *                        + tau d/dx( etadot' (1+eta'^2)^{-3/2} ) ] */
+        for (int i = 0; i < N; ++i) b[i] = ed[i] * ux[i] * vy[i];
+        orc_spectral(N, MUL_DERIV, b, b);
+        orc_spectral(N, MUL_DERIV, ed, e1);
+        for (int i = 0; i < N; ++i) e1[i] *= w3[i];
+        orc_spectral(N, MUL_DERIV, e1, e1);
+        for (int i = 0; i < N; ++i)
+            op[i] = -b[i] - ux[i] * dpsi[i] + vy[i] * Gpsi[i] - p->g * ed[i] + p->tau * e1[i];
+        orc_spectral(N, MUL_PROJECT, op, op);
+        orc_spectral(N, MUL_FILTER, oe, oe);
+        orc_spectral(N, MUL_FILTER, op, op);
+        if (c == t_col)
+            for (int i = 0; i < 2 * N; ++i) oe[i] += F[i] / T;
+        free(psi); free(Gpsi); free(dpsi); free(a); free(b); free(e1);
+    }
+    free(phi_p); free(Gphi); free(ux); free(vy); free(w3); free(tmp);
+    dtn_release(&s);
+}
+
+/* ------------------------------------------------------------------ */
+/* Initial data (Sec. 3.1, reading of the basis) and RK4 (classic)       */
+/* ------------------------------------------------------------------ */
+static double basis_entry(const orc_problem *p, int row, int k /* 1..n */)
+{
+    int N = p->N;
+    if (p->basis) return p->basis[(size_t)(k - 1) * 2 * N + row];
+    if (row >= N) return 0.0;
+    return cos((double)k * TWO_PI * row / N);
+}
+
+/* q0 = (mean + sum c_k B_eta[:,k], sum c_k B_phi[:,k]) */
+void orc_initial(const orc_problem *p, const double *c, double *q0)
+{
+    int N = p->N;
+    double mean = isinf(p->h) ? 0.0 : p->h;
+    for (int r = 0; r < 2 * N; ++r) {
+        double s = r < N ? mean : 0.0;
+        for (int k = 1; k <= p->n; ++k) s += c[k] * basis_entry(p, r, k);
+        q0[r] = s;
+    }
+}
+
+/* Integrate base + ncol variational columns from 0 to T/4 with p->steps RK4
+ * steps; y holds the initial data on entry and the final data on exit. */
+static void integrate(const orc_problem *p, double T, double *y, int ncol, int t_col)
+{
+    int N = p->N;
+    size_t len = (size_t)(ncol + 1) * 2 * N;
+    double dt = T / 4.0 / p->steps;
+    double *k = malloc(sizeof(double) * len), *acc = malloc(sizeof(double) * len);
+    double *ys = malloc(sizeof(double) * len);
+    static const double a[4] = {0.0, 0.5, 0.5, 1.0};
+    static const double b[4] = {1.0, 2.0, 2.0, 1.0};
+    for (int n = 0; n < p->steps; ++n) {
+        for (size_t i = 0; i < len; ++i) acc[i] = 0.0;
+        for (int st = 0; st < 4; ++st) {
+            if (st == 0) memcpy(ys, y, sizeof(double) * len);
+            else for (size_t i = 0; i < len; ++i) ys[i] = y[i] + a[st] * dt * k[i];
+            orc_rhs(p, T, ys, ncol, t_col, k);
+            for (size_t i = 0; i < len; ++i) acc[i] += b[st] * k[i];
+        }
+        for (size_t i = 0; i < len; ++i) y[i] += dt / 6.0 * acc[i];
+        for (int c = 0; c <= ncol; ++c) {             /* filter the solution (R4) */
+            orc_spectral(N, MUL_FILTER, y + (size_t)c * 2 * N, y + (size_t)c * 2 * N);
+            orc_spectral(N, MUL_FILTER, y + (size_t)c * 2 * N + N, y + (size_t)c * 2 * N + N);
+        }
+    }
+    free(k); free(acc); free(ys);
+}
+
+/* Evolve the base state only (no columns): q_end = q(T/4). */
+void orc_evolve(const orc_problem *p, double T, const double *q0, double *q_end)
+{
+    memcpy(q_end, q0, sizeof(double) * 2 * p->N);
+    integrate(p, T, q_end, 0, 0);
+}
+
+/* Evolve base + ncol given variational columns (each 2N, contiguous) with
+ * an optional T-forcing column (t_col as in orc_rhs). */
+void orc_evolve_columns(const orc_problem *p, double T, const double *q0, const double *cols,
+                        int ncol, int t_col, double *y_end /* (ncol+1)*2N */)
+{
+    int N = p->N;
+    memcpy(y_end, q0, sizeof(double) * 2 * N);
+    memcpy(y_end + 2 * N, cols, sizeof(double) * (size_t)ncol * 2 * N);
+    integrate(p, T, y_end, ncol, t_col);
+}
+
+/* Objective, Eq. (f:phi) with reading R5: r_i = phi(x_i, T/4)/sqrt(N). */
+void orc_shoot(const orc_problem *p, const double *c, double *r, double *f)
+{
+    int N = p->N;
+    double *y = malloc(sizeof(double) * 2 * N);
+    orc_initial(p, c, y);
+    integrate(p, c[0], y, 0, 0);
+    double w = 1.0 / sqrt((double)N), s = 0.0;
+    for (int i = 0; i < N; ++i) { r[i] = w * y[N + i]; s += r[i] * r[i]; }
+    *f = 0.5 * s;
+    free(y);
+}
+
+/* Jacobian, Eqs. (Jik), (q:qdot) with reading R2: J is N x (n+1) column-major,
+ * column 0 = d r / d T, column k = d r / d c_k. */
+void orc_shoot_jacobian(const orc_problem *p, const double *c, double *r, double *J, double *f)
+{
+    int N = p->N, n = p->n, ncol = n + 1;
+    size_t len = (size_t)(ncol + 1) * 2 * N;
+    double *y = calloc(len, sizeof(double));
+    orc_initial(p, c, y);
+    /* column 1 (J column 0) = T column, zero initial data; columns 2.. = basis */
+    for (int k = 1; k <= n; ++k)
+        for (int rr = 0; rr < 2 * N; ++rr)
+            y[(size_t)(k + 1) * 2 * N + rr] = basis_entry(p, rr, k);
+    integrate(p, c[0], y, ncol, 1);
+    double w = 1.0 / sqrt((double)N), s = 0.0;
+    for (int i = 0; i < N; ++i) { r[i] = w * y[N + i]; s += r[i] * r[i]; }
+    *f = 0.5 * s;
+    for (int k = 0; k <= n; ++k)
+        for (int i = 0; i < N; ++i)
+            J[(size_t)k * N + i] = w * y[(size_t)(k + 1) * 2 * N + N + i];
+    free(y);
+}
+
+/* Energy (Sec. 4, energy monitor): E = 1/2 int (phi G phi + g (eta - hbar)^2) dx
+ * + tau int (sqrt(1 + eta'^2) - 1) dx, trapezoid rule. */
+double orc_energy(const orc_problem *p, const double *q)
+{
+    int N = p->N;
+    const double *eta = q, *phi = q + N;
+    double *Gphi = malloc(sizeof(double) * N), *ex = malloc(sizeof(double) * N);
+    orc_dtn(N, p->h, eta, phi, 1, Gphi);
+    orc_spectral(N, MUL_DERIV, eta, ex);
+    double mean = isinf(p->h) ? 0.0 : p->h, e = 0.0;
+    for (int i = 0; i < N; ++i) {
+        double d = eta[i] - mean;
+        e += 0.5 * (phi[i] * Gphi[i] + p->g * d * d) + p->tau * (sqrt(1.0 + ex[i] * ex[i]) - 1.0);
+    }
+    free(Gphi); free(ex);
+    return e * TWO_PI / N;
+}
