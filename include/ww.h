@@ -1,0 +1,137 @@
+/*
+ * ww.h -- C ABI of the GB300 library for the Jacobian of the standing-water-
+ * wave shooting map (Wilkening & Yu, "Overdetermined shooting methods for
+ * computing standing water waves with spectral accuracy").
+ *
+ * The method: the 2 pi-periodic free-surface Euler equations (Sec. 2.1,
+ * Eq. ww) are advanced from t = 0 to T/4 by classic RK4 together with the
+ * variational equations of every Jacobian column (Sec. 3.3, Eq. q:qdot;
+ * App. B, Eqs. l5a, l6a).  In each RK stage the boundary-integral matrices of
+ * the base surface (Eq. K1K2, Sec. 2.2) are assembled once, A = 1/2 I + K is
+ * factored (or inverted) once, and every column's Dirichlet data is solved
+ * against it as one multi-right-hand-side solve (Sec. 3.3).
+ *
+ * Conventions for every entry point
+ *  - All arrays are IEEE double.  Matrices are column-major with leading
+ *    dimension N (the number of surface points).
+ *  - Unless a name ends in _host, array arguments are DEVICE pointers (memory
+ *    of the GPU the context was created on) owned by the caller; the library
+ *    only reads inputs and writes outputs, and keeps no reference after the
+ *    call returns.  Work is queued on the context's stream (ww_set_stream),
+ *    and each call synchronises that stream before returning its status.
+ *  - Every call returns WW_OK (0) or a negative WW_ERR_* code; the thread-local
+ *    ww_last_error() string says why.  No call aborts or exits the process.
+ *  - A context is not thread-safe; use one context per host thread/stream.
+ *
+ * Grid: alpha_j = 2 pi j / N, j = 0..N-1, N a power of two (16 <= N <= 4096).
+ * The mean depth is absorbed into eta (bottom at y = 0, Sec. 2.1), so a
+ * finite-depth surface must satisfy eta_j > 0; in deep water (h = INFINITY)
+ * the mirror-image kernels K2, G2 are omitted.
+ */
+#ifndef WW_H
+#define WW_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WW_OK                  0
+#define WW_ERR_ARG            -1  /* bad argument (size, NULL pointer, layout)        */
+#define WW_ERR_GEOMETRY       -2  /* surface at/below the bottom, or non-finite data   */
+#define WW_ERR_NO_CONVERGENCE -3  /* iterative refinement missed refine_tol            */
+#define WW_ERR_CUDA           -4  /* a CUDA runtime call failed                        */
+#define WW_ERR_TIMEOUT        -5  /* a bounded device-side wait gave up                */
+#define WW_ERR_ALLOC          -6  /* device or host allocation failed                  */
+
+/* Arithmetic of the dense DtN linear algebra. */
+#define WW_FP64  0  /* plain FP64: LU of A, triangular solves, G apply, all FP64 */
+#define WW_MIXED 1  /* FP32-accurate approximate inverse of A on the tensor cores,
+                       FP64-accurate residuals and G apply by exact bf16 splitting,
+                       iterative refinement to refine_tol (Sec. 3.3 refinement
+                       precedent: quad residuals + double solves, here FP64
+                       residuals + FP32 solves) */
+
+typedef struct {
+    int N;              /* surface points, power of two in [16, 4096]                 */
+    int n;              /* mode unknowns c_1..c_n (J has n+1 columns), 0 <= n <= 4096 */
+    double g;           /* gravity                                                    */
+    double tau;         /* surface tension sigma/rho (>= 0)                           */
+    double h;           /* mean depth, or INFINITY for deep water                     */
+    int steps;          /* RK4 steps from t = 0 to t = T/4 (>= 1)                     */
+    const double *basis;/* HOST pointer: 2N x n column-major initial-data basis
+                           (rows 0..N-1 eta, N..2N-1 phi), copied at ww_create;
+                           NULL selects column k = (cos k x, 0)                       */
+    int precision;      /* WW_FP64 or WW_MIXED                                        */
+    double refine_tol;  /* WW_MIXED: relative residual target, 0 => 1e-13             */
+    int max_refine;     /* WW_MIXED: refinement iterations allowed, 0 => 8            */
+} ww_problem;
+
+typedef struct {
+    int refine_iters_max;      /* most refinement iterations any stage needed       */
+    double refine_resid_max;   /* largest final relative residual of any stage      */
+    double ns_resid_max;       /* WW_MIXED: largest ||I - X A||_max seen            */
+    int stages;                /* RK stages run by the last call                     */
+} ww_stats;
+
+typedef struct ww_ctx ww_ctx;
+
+/* Create a context for problem *p on the current CUDA device: validates the
+ * sizes, allocates all device workspace (about 3 N^2 + 8 N (n+2) doubles in
+ * WW_FP64; WW_MIXED adds FP32/bf16 copies of the N x N operators), uploads
+ * the basis.  *ctx is NULL on failure. */
+int ww_create(ww_ctx **ctx, const ww_problem *p);
+
+/* Free everything ww_create allocated.  NULL is a no-op. */
+void ww_destroy(ww_ctx *ctx);
+
+/* Queue subsequent work on `stream` (a cudaStream_t; NULL = legacy default). */
+int ww_set_stream(ww_ctx *ctx, void *stream);
+
+/* Statistics of the last shoot / shoot_jacobian / dtn_apply call. */
+int ww_get_stats(const ww_ctx *ctx, ww_stats *out);
+
+/* Thread-local description of the last error (empty string if none). */
+const char *ww_last_error(void);
+
+/* dtn_setup -- Sec. 2.1 Eqs. (fred), (G); Sec. 2.2 Eq. (K1K2).
+ * Assemble A = 1/2 I + K and G for the surface eta (device, N doubles; mean
+ * depth included), and factor A (WW_FP64) or build its approximate inverse
+ * (WW_MIXED).  Returns WW_ERR_GEOMETRY if eta is non-finite or, with finite
+ * depth, min(eta) <= 0. */
+int dtn_setup(ww_ctx *ctx, const double *eta);
+
+/* dtn_apply -- the Dirichlet-to-Neumann operator of the surface given to the
+ * last dtn_setup (Sec. 2.1, three steps: solve Eq. (fred) for mu, gamma = mu',
+ * G phi = 1/2 H gamma + (1/2 pi) int G gamma, |xi'| = 1 on the uniform grid).
+ * phi: device, N x nrhs column-major; Gphi: device, N x nrhs (may not alias
+ * phi).  1 <= nrhs <= n + 2.  WW_ERR_ARG if dtn_setup was not called. */
+int dtn_apply(ww_ctx *ctx, const double *phi, int nrhs, double *Gphi);
+
+/* shoot -- Sec. 3.1 Eq. (f:phi).  c: device, n+1 doubles (c[0] = T, c[k] the
+ * coefficient of basis column k).  Evolves q0 = (hbar + B_eta c, B_phi c) to
+ * T/4 with `steps` RK4 steps (36th-order filter on every RHS and after every
+ * step, Eq. filter) and writes r_i = phi(x_i, T/4)/sqrt(N) (device, N) and
+ * f = r.r/2 (device, 1 double). */
+int shoot(ww_ctx *ctx, const double *c, double *r, double *f);
+
+/* shoot_jacobian -- Sec. 3.3 Eqs. (Jik), (q:qdot).  As shoot, and also
+ * J (device, N x (n+1) column-major): column 0 = dr/dT (the variational
+ * column forced by F(q)/T, exact for the discrete map), column k = dr/dc_k
+ * (variational column started from basis column k).  All n+1 columns share
+ * each stage's DtN setup. */
+int shoot_jacobian(ww_ctx *ctx, const double *c, double *r, double *J, double *f);
+
+/* shoot_jacobian_host -- shoot_jacobian with HOST arrays: copies c in, runs,
+ * copies r, J, f out (pinned or pageable host memory). */
+int shoot_jacobian_host(ww_ctx *ctx, const double *c, double *r, double *J, double *f);
+
+/* objective_and_grad -- Sec. 3.2 Eqs. (f:phi:again), (nabla:f): f and its
+ * gradient with respect to c (device, n+1 doubles), grad = J^T r computed from
+ * the forward variational columns of shoot_jacobian (same discrete map, so
+ * it equals the discrete adjoint's result up to roundoff). */
+int objective_and_grad(ww_ctx *ctx, const double *c, double *f, double *grad);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WW_H */

@@ -1,0 +1,255 @@
+"""GB300 (sm_103a) library for the Jacobian of the standing-water-wave shooting
+map (Wilkening & Yu, overdetermined shooting methods, Sec. 3.3).
+
+This module is a thin ctypes binding of the C ABI in ``include/ww.h``: it
+marshals torch CUDA tensors (device pointers) and numpy arrays (host pointers)
+into the library calls and turns negative status codes into exceptions.  No
+step of the method runs in Python; if the compiled library is missing the
+import of any entry point raises.
+
+Names follow the C ABI: ``dtn_setup``, ``dtn_apply``, ``shoot``,
+``shoot_jacobian``, ``shoot_jacobian_host``, ``objective_and_grad``, plus the
+``Context`` that owns the device workspace and ``ShootingObjective``, a
+``torch.autograd.Function`` around ``objective_and_grad``.
+
+Layouts: every array is float64; matrices are column-major with leading
+dimension N, so an N x m matrix is passed as a contiguous torch tensor of
+shape (m, N) (row j = column j of the matrix).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libww.so")
+
+WW_OK = 0
+ERRORS = {
+    -1: "WW_ERR_ARG", -2: "WW_ERR_GEOMETRY", -3: "WW_ERR_NO_CONVERGENCE",
+    -4: "WW_ERR_CUDA", -5: "WW_ERR_TIMEOUT", -6: "WW_ERR_ALLOC",
+}
+WW_FP64, WW_MIXED = 0, 1
+EXPORTS = ("ww_create", "ww_destroy", "ww_set_stream", "ww_get_stats", "ww_last_error", "dtn_setup",
+           "dtn_apply", "shoot", "shoot_jacobian", "shoot_jacobian_host", "objective_and_grad")
+
+
+class WWError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Problem(C.Structure):
+    _fields_ = [
+        ("N", C.c_int), ("n", C.c_int), ("g", C.c_double), ("tau", C.c_double), ("h", C.c_double),
+        ("steps", C.c_int), ("basis", C.POINTER(C.c_double)), ("precision", C.c_int),
+        ("refine_tol", C.c_double), ("max_refine", C.c_int),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("refine_iters_max", C.c_int), ("refine_resid_max", C.c_double), ("ns_resid_max", C.c_double),
+        ("stages", C.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load the compiled library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; "
+                               "g.build()')")
+        L = C.CDLL(LIB_PATH)
+        V, I, D = C.c_void_p, C.c_int, C.c_double
+        sig = {
+            "ww_create": (I, [C.POINTER(V), C.POINTER(_Problem)]),
+            "ww_destroy": (None, [V]),
+            "ww_set_stream": (I, [V, V]),
+            "ww_get_stats": (I, [V, C.POINTER(Stats)]),
+            "ww_last_error": (C.c_char_p, []),
+            "dtn_setup": (I, [V, V]),
+            "dtn_apply": (I, [V, V, I, V]),
+            "shoot": (I, [V, V, V, V]),
+            "shoot_jacobian": (I, [V, V, V, V, V]),
+            "shoot_jacobian_host": (I, [V, V, V, V, V]),
+            "objective_and_grad": (I, [V, V, V, V]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != WW_OK:
+        raise WWError(code, lib().ww_last_error().decode())
+
+
+def _dptr(t, numel: int, name: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name}: expected a contiguous float64 CUDA tensor")
+    if t.numel() < numel:
+        raise ValueError(f"{name}: needs at least {numel} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(a: np.ndarray, numel: int, name: str):
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise TypeError(f"{name}: expected a contiguous float64 numpy array")
+    if a.size < numel:
+        raise ValueError(f"{name}: needs at least {numel} elements, got {a.size}")
+    return C.c_void_p(a.ctypes.data)
+
+
+class Context:
+    """Owns a ww_ctx (device workspace for one problem size) on the current device."""
+
+    def __init__(self, N, n, g=1.0, tau=0.0, h=1.0, steps=64, basis=None, precision=WW_FP64,
+                 refine_tol=0.0, max_refine=0):
+        self.N, self.n, self.steps = int(N), int(n), int(steps)
+        self.g, self.tau, self.h = float(g), float(tau), float(h)
+        self.precision = int(precision)
+        self._basis = None
+        bp = C.cast(None, C.POINTER(C.c_double))
+        if basis is not None:
+            b = np.asarray(basis, dtype=np.float64)
+            if b.shape != (2 * self.N, self.n):
+                raise ValueError("basis must have shape (2N, n)")
+            self._basis = np.ascontiguousarray(b.T)   # column-major 2N x n
+            bp = self._basis.ctypes.data_as(C.POINTER(C.c_double))
+        p = _Problem(self.N, self.n, self.g, self.tau, self.h, self.steps, bp, self.precision,
+                     float(refine_tol), int(max_refine))
+        h_ = C.c_void_p()
+        _check(lib().ww_create(C.byref(h_), C.byref(p)))
+        self._h = h_
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("context is closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().ww_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream):
+        """Queue work on a torch.cuda.Stream (or raw cudaStream_t int)."""
+        raw = getattr(stream, "cuda_stream", stream)
+        _check(lib().ww_set_stream(self.handle, C.c_void_p(int(raw) if raw else None)))
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().ww_get_stats(self.handle, C.byref(s)))
+        return s.as_dict()
+
+    # convenience allocation of outputs on the current CUDA device
+    def empty_outputs(self):
+        import torch
+        r = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        J = torch.empty(self.n + 1, self.N, dtype=torch.float64, device="cuda")
+        f = torch.empty(1, dtype=torch.float64, device="cuda")
+        return r, J, f
+
+
+# ------------------------------------------------------------- entry points
+def dtn_setup(ctx: Context, eta):
+    """Assemble and factor the DtN operator of the surface eta (CUDA, N)."""
+    _check(lib().dtn_setup(ctx.handle, _dptr(eta, ctx.N, "eta")))
+
+
+def dtn_apply(ctx: Context, phi, Gphi=None):
+    """G phi for nrhs columns: phi is (nrhs, N) or (N,) CUDA float64."""
+    import torch
+    nrhs = 1 if phi.dim() == 1 else phi.shape[0]
+    if Gphi is None:
+        Gphi = torch.empty_like(phi)
+    _check(lib().dtn_apply(ctx.handle, _dptr(phi, nrhs * ctx.N, "phi"), int(nrhs),
+                           _dptr(Gphi, nrhs * ctx.N, "Gphi")))
+    return Gphi
+
+
+def shoot(ctx: Context, c, r, f):
+    _check(lib().shoot(ctx.handle, _dptr(c, ctx.n + 1, "c"), _dptr(r, ctx.N, "r"), _dptr(f, 1, "f")))
+
+
+def shoot_jacobian(ctx: Context, c, r, J, f):
+    """J: (n+1, N) CUDA float64 (= N x (n+1) column-major)."""
+    _check(lib().shoot_jacobian(ctx.handle, _dptr(c, ctx.n + 1, "c"), _dptr(r, ctx.N, "r"),
+                                _dptr(J, ctx.N * (ctx.n + 1), "J"), _dptr(f, 1, "f")))
+
+
+def shoot_jacobian_host(ctx: Context, c: np.ndarray, r: np.ndarray, J: np.ndarray, f: np.ndarray):
+    """Host-array variant; J is (n+1, N) float64 (= N x (n+1) column-major)."""
+    _check(lib().shoot_jacobian_host(ctx.handle, _hptr(c, ctx.n + 1, "c"), _hptr(r, ctx.N, "r"),
+                                     _hptr(J, ctx.N * (ctx.n + 1), "J"), _hptr(f, 1, "f")))
+
+
+def objective_and_grad(ctx: Context, c, f, grad):
+    _check(lib().objective_and_grad(ctx.handle, _dptr(c, ctx.n + 1, "c"), _dptr(f, 1, "f"),
+                                    _dptr(grad, ctx.n + 1, "grad")))
+
+
+def _autograd_fn():
+    import torch
+
+    class ShootingObjective(torch.autograd.Function):
+        """f(c) = |r(c)|^2 / 2 with d f / d c from objective_and_grad."""
+
+        @staticmethod
+        def forward(ctx_, c, wwctx):
+            cc = c.detach().contiguous()
+            f = torch.empty(1, dtype=torch.float64, device=c.device)
+            grad = torch.empty(wwctx.n + 1, dtype=torch.float64, device=c.device)
+            objective_and_grad(wwctx, cc, f, grad)
+            ctx_.save_for_backward(grad)
+            return f[0]
+
+        @staticmethod
+        def backward(ctx_, gout):
+            (grad,) = ctx_.saved_tensors
+            return gout * grad, None
+
+    return ShootingObjective
+
+
+def shooting_objective(c, wwctx: Context):
+    """Differentiable objective f(c) (torch autograd), gradient from the library."""
+    return _autograd_fn().apply(c, wwctx)
+
+
+def default_basis(N: int, n: int) -> np.ndarray:
+    """(2N, n) basis of the default initial data: column k = (cos(k x), 0)."""
+    x = 2.0 * math.pi * np.arange(N) / N
+    B = np.zeros((2 * N, n))
+    for k in range(1, n + 1):
+        B[:N, k - 1] = np.cos(k * x)
+    return B

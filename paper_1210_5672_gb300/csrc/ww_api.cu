@@ -1,0 +1,388 @@
+// ww_api.cu -- the C ABI declared in include/ww.h: context lifetime, the DtN
+// entry points, and the RK4 driver of shoot / shoot_jacobian.  One RK4 step
+// (four stages, each: base geometry -> assembly -> factor -> base solve and
+// DtN -> base RHS -> variational solves and DtN -> variational RHS) is
+// captured once per context into a CUDA graph and replayed `steps` times.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ww_internal.cuh"
+
+namespace ww {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+namespace {
+
+__global__ void k_jtr(const double *__restrict__ J, const double *__restrict__ r, int N, double *grad) {
+    __shared__ double red[32];
+    const double *col = J + (size_t)blockIdx.x * N;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) acc = fma(col[i], r[i], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) grad[blockIdx.x] = acc;
+    }
+}
+
+struct Graphs {
+    cudaGraphExec_t step[2] = {nullptr, nullptr};   // [with_columns]
+};
+
+struct Owned {
+    Ctx c;
+    double *cbuf = nullptr, *rbuf = nullptr, *Jbuf = nullptr, *fbuf = nullptr;
+    Graphs graphs;
+    cudaStream_t own_stream = nullptr;   // created by ww_create, used unless ww_set_stream overrides
+    std::vector<void *> allocs;
+};
+
+int dalloc(Owned *o, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return fail(WW_ERR_ALLOC, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    o->allocs.push_back(*p);
+    return WW_OK;
+}
+
+template <typename T>
+int dalloc_n(Owned *o, T **p, size_t n) {
+    return dalloc(o, reinterpret_cast<void **>(p), sizeof(T) * (n ? n : 1));
+}
+
+Owned *owner(ww_ctx *ctx) { return reinterpret_cast<Owned *>(ctx); }
+
+int factor(Ctx *c) {
+    if (c->precision == WW_MIXED) return mixed_setup(c);
+    return lu_factor_fp64(c);
+}
+
+int solve(Ctx *c, double *B, int ncols) {
+    if (c->precision == WW_MIXED) return mixed_solve(c, B, ncols);
+    return lu_solve_fp64(c, B, ncols);
+}
+
+// Gout[:, col0 : col0+ncols] += G Gam[:, col0 : ...]
+int apply_G(Ctx *c, int col0, int ncols) {
+    if (c->precision == WW_MIXED) return mixed_apply_G(c, col0, ncols);
+    return dgemm(c->stream, c->N, ncols, c->N, 1.0, c->G, c->N, c->Gam + (size_t)col0 * c->N, c->N, 1.0,
+                 c->Gout + (size_t)col0 * c->N, c->N);
+}
+
+// one RK4 stage; cvec is the context's device copy of c (T = cvec[0])
+int run_stage(Ctx *c, int st, const double *cvec, int with_cols) {
+    WW_TRY(launch_base_geometry(c, c->Ys, c->Ys + c->N, 1));
+    WW_TRY(launch_assemble(c));
+    WW_TRY(factor(c));
+    WW_TRY(launch_phi0(c));
+    WW_TRY(solve(c, c->M, 1));
+    WW_TRY(launch_gamma(c, 0, 1));
+    WW_TRY(apply_G(c, 0, 1));
+    WW_TRY(launch_base_rhs(c, st, cvec));
+    if (with_cols && c->nc > 0) {
+        WW_TRY(launch_psi(c));
+        WW_TRY(solve(c, c->M + c->N, c->nc));
+        WW_TRY(launch_gamma(c, 1, c->nc));
+        WW_TRY(apply_G(c, 1, c->nc));
+        WW_TRY(launch_col_rhs(c, st, cvec));
+    }
+    return WW_OK;
+}
+
+int build_step_graph(Owned *o, int with_cols) {
+    Ctx *c = &o->c;
+    if (o->graphs.step[with_cols]) return WW_OK;
+    cudaGraph_t g = nullptr;
+    WW_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int st = WW_OK;
+    for (int s = 0; s < 4 && st == WW_OK; ++s) st = run_stage(c, s, o->cbuf, with_cols);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (st != WW_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(WW_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&o->graphs.step[with_cols], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(WW_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return WW_OK;
+}
+
+int check_status(Ctx *c) {
+    int st = 0;
+    WW_CUDA_TRY(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    WW_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (st & ST_GEOMETRY)
+        return fail(WW_ERR_GEOMETRY, "surface touches the bottom (finite depth needs eta > 0) or is non-finite");
+    if (st & ST_NONFINITE) return fail(WW_ERR_GEOMETRY, "non-finite value in a right-hand side or factor");
+    if (st & ST_NO_CONV) return fail(WW_ERR_NO_CONVERGENCE, "iterative refinement missed its tolerance");
+    return WW_OK;
+}
+
+int run_shot(Owned *o, const double *cvec, bool c_on_host, double *r, double *J, double *f, int with_cols) {
+    Ctx *c = &o->c;
+    WW_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    WW_CUDA_TRY(cudaMemcpyAsync(o->cbuf, cvec, sizeof(double) * (c->n + 1),
+                                c_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+    WW_TRY(launch_initial(c, o->cbuf, with_cols));
+    if (c->stream == nullptr) {
+        // the legacy default stream cannot be captured: launch the stages directly
+        for (int s = 0; s < c->steps; ++s)
+            for (int k = 0; k < 4; ++k) WW_TRY(run_stage(c, k, o->cbuf, with_cols));
+    } else {
+        WW_TRY(build_step_graph(o, with_cols));
+        for (int s = 0; s < c->steps; ++s) WW_CUDA_TRY(cudaGraphLaunch(o->graphs.step[with_cols], c->stream));
+    }
+    WW_TRY(launch_outputs(c, r, J, f, with_cols));
+    c->stats.stages = 4 * c->steps;
+    c->dtn_ready = false;   // the operator now belongs to the last stage's surface
+    return check_status(c);
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+}  // namespace
+}  // namespace ww
+
+using namespace ww;
+
+extern "C" {
+
+const char *ww_last_error(void) { return g_err.c_str(); }
+
+int ww_create(ww_ctx **out, const ww_problem *p) {
+    if (!out || !p) return fail(WW_ERR_ARG, "ww_create: NULL argument");
+    *out = nullptr;
+    if (!is_pow2(p->N) || p->N < 16 || p->N > 4096)
+        return fail(WW_ERR_ARG, "ww_create: N must be a power of two in [16, 4096]");
+    if (p->n < 0 || p->n > 4096) return fail(WW_ERR_ARG, "ww_create: n must be in [0, 4096]");
+    if (p->steps < 1) return fail(WW_ERR_ARG, "ww_create: steps must be >= 1");
+    if (!std::isfinite(p->g) || !std::isfinite(p->tau) || p->tau < 0.0)
+        return fail(WW_ERR_ARG, "ww_create: g and tau must be finite, tau >= 0");
+    if (!(p->h > 0.0)) return fail(WW_ERR_ARG, "ww_create: h must be > 0 (INFINITY for deep water)");
+    if (p->precision != WW_FP64 && p->precision != WW_MIXED)
+        return fail(WW_ERR_ARG, "ww_create: precision must be WW_FP64 or WW_MIXED");
+
+    Owned *o = new Owned();
+    Ctx *c = &o->c;
+    std::memset(c, 0, sizeof(Ctx));
+    c->N = p->N;
+    c->logN = 0;
+    while ((1 << c->logN) < c->N) ++c->logN;
+    c->n = p->n;
+    c->nc = p->n + 1;
+    c->NC = c->nc + 1;
+    c->g = p->g;
+    c->tau = p->tau;
+    c->h = p->h;
+    c->deep = std::isinf(p->h);
+    c->steps = p->steps;
+    c->precision = p->precision;
+    c->refine_tol = p->refine_tol > 0.0 ? p->refine_tol : 1e-13;
+    c->max_refine = p->max_refine > 0 ? p->max_refine : 8;
+    c->nb = c->N < LU_NB ? c->N : LU_NB;
+    {
+        cudaError_t e0 = cudaStreamCreateWithFlags(&o->own_stream, cudaStreamNonBlocking);
+        if (e0 != cudaSuccess) {
+            delete o;
+            return fail(WW_ERR_CUDA, std::string("ww_create stream: ") + cudaGetErrorString(e0));
+        }
+    }
+    c->stream = o->own_stream;
+
+    const size_t N = c->N, NC = c->NC, nb = c->nb;
+    const size_t nblk = (N + nb - 1) / nb;
+    int st = WW_OK;
+#define ALLOC(ptr, cnt)                                     \
+    if (st == WW_OK) st = dalloc_n(o, &(ptr), (size_t)(cnt))
+    ALLOC(c->tw, N / 2);
+    ALLOC(c->cs, 3 * N);
+    ALLOC(c->eta, N);
+    ALLOC(c->eta_x, N);
+    ALLOC(c->eta_xx, N);
+    ALLOC(c->phi_s, N);
+    ALLOC(c->E, N);
+    ALLOC(c->Einv, N);
+    ALLOC(c->ux, N);
+    ALLOC(c->vy, N);
+    ALLOC(c->w3, N);
+    ALLOC(c->curv, N);
+    ALLOC(c->Fbase, 2 * N);
+    ALLOC(c->A, N * N);
+    ALLOC(c->G, N * N);
+    ALLOC(c->Dinv, nblk * 2 * nb * nb);
+    ALLOC(c->Y, NC * 2 * N);
+    ALLOC(c->Ys, NC * 2 * N);
+    ALLOC(c->Kacc, NC * 2 * N);
+    ALLOC(c->M, N * NC);
+    ALLOC(c->Gam, N * NC);
+    ALLOC(c->Gout, N * NC);
+    ALLOC(c->basis, 2 * N * (size_t)(p->n > 0 ? p->n : 1));
+    ALLOC(c->status, 1);
+    ALLOC(c->small, 64);
+    ALLOC(o->cbuf, c->n + 1);
+    ALLOC(o->rbuf, N);
+    ALLOC(o->Jbuf, N * c->nc);
+    ALLOC(o->fbuf, 1);
+#undef ALLOC
+    if (st != WW_OK) {
+        ww_destroy(reinterpret_cast<ww_ctx *>(o));
+        return st;
+    }
+    // tables (host double precision): twiddles, cos/sin of 2 pi m/N, cot(pi m/N)
+    std::vector<double> tw(N), cs(3 * N);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (size_t k = 0; k < N / 2; ++k) {
+        tw[2 * k] = std::cos(two_pi * (double)k / (double)N);
+        tw[2 * k + 1] = -std::sin(two_pi * (double)k / (double)N);
+    }
+    for (size_t m = 0; m < N; ++m) {
+        cs[m] = std::cos(two_pi * (double)m / (double)N);
+        cs[N + m] = std::sin(two_pi * (double)m / (double)N);
+        cs[2 * N + m] = m == 0 ? 0.0 : 1.0 / std::tan(0.5 * two_pi * (double)m / (double)N);
+    }
+    // exact values where the argument is a multiple of pi/2
+    for (size_t m = 0; m < N; m += N / 4) {
+        int q = (int)(m / (N / 4));
+        cs[m] = (q == 0) ? 1.0 : (q == 2 ? -1.0 : 0.0);
+        cs[N + m] = (q == 1) ? 1.0 : (q == 3 ? -1.0 : 0.0);
+        if (q == 2) cs[2 * N + m] = 0.0;
+    }
+    for (size_t k = 0; k < N / 2; k += N / 4) {
+        int q = (int)(k / (N / 4));
+        tw[2 * k] = q == 0 ? 1.0 : 0.0;
+        tw[2 * k + 1] = q == 0 ? 0.0 : -1.0;
+    }
+    std::vector<double> basis(2 * N * (size_t)(p->n > 0 ? p->n : 1), 0.0);
+    for (int k = 0; k < p->n; ++k)
+        for (size_t r = 0; r < 2 * N; ++r)
+            basis[(size_t)k * 2 * N + r] =
+                p->basis ? p->basis[(size_t)k * 2 * N + r]
+                         : (r < N ? std::cos((double)(k + 1) * two_pi * (double)r / (double)N) : 0.0);
+    cudaError_t e = cudaMemcpy(c->tw, tw.data(), sizeof(double) * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->cs, cs.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->basis, basis.data(), sizeof(double) * basis.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        ww_destroy(reinterpret_cast<ww_ctx *>(o));
+        return fail(WW_ERR_CUDA, std::string("ww_create upload: ") + cudaGetErrorString(e));
+    }
+    st = prepare_spectral(c);
+    if (st != WW_OK) {
+        ww_destroy(reinterpret_cast<ww_ctx *>(o));
+        return st;
+    }
+    if (c->precision == WW_MIXED) {
+        st = mixed_create(c);
+        if (st != WW_OK) {
+            ww_destroy(reinterpret_cast<ww_ctx *>(o));
+            return st;
+        }
+    }
+    *out = reinterpret_cast<ww_ctx *>(o);
+    g_err.clear();
+    return WW_OK;
+}
+
+void ww_destroy(ww_ctx *ctx) {
+    if (!ctx) return;
+    Owned *o = owner(ctx);
+    for (int w = 0; w < 2; ++w)
+        if (o->graphs.step[w]) cudaGraphExecDestroy(o->graphs.step[w]);
+    if (o->c.mx) mixed_destroy(&o->c);
+    if (o->c.stream) cudaStreamSynchronize(o->c.stream);
+    for (void *p : o->allocs) cudaFree(p);
+    if (o->own_stream) cudaStreamDestroy(o->own_stream);
+    delete o;
+}
+
+int ww_set_stream(ww_ctx *ctx, void *stream) {
+    if (!ctx) return fail(WW_ERR_ARG, "ww_set_stream: NULL context");
+    Owned *o = owner(ctx);
+    // graphs are replayed on whatever stream is current, so nothing is rebuilt;
+    // the legacy default stream (NULL) selects direct launches instead of graphs
+    o->c.stream = (cudaStream_t)stream;
+    return WW_OK;
+}
+
+int ww_get_stats(const ww_ctx *ctx, ww_stats *out) {
+    if (!ctx || !out) return fail(WW_ERR_ARG, "ww_get_stats: NULL argument");
+    *out = reinterpret_cast<const Owned *>(ctx)->c.stats;
+    return WW_OK;
+}
+
+int dtn_setup(ww_ctx *ctx, const double *eta) {
+    if (!ctx || !eta) return fail(WW_ERR_ARG, "dtn_setup: NULL argument");
+    Ctx *c = &owner(ctx)->c;
+    c->dtn_ready = false;
+    WW_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    WW_TRY(launch_base_geometry(c, eta, nullptr, 0));
+    WW_TRY(launch_assemble(c));
+    WW_TRY(factor(c));
+    WW_TRY(check_status(c));
+    c->dtn_ready = true;
+    return WW_OK;
+}
+
+int dtn_apply(ww_ctx *ctx, const double *phi, int nrhs, double *Gphi) {
+    if (!ctx || !phi || !Gphi) return fail(WW_ERR_ARG, "dtn_apply: NULL argument");
+    Ctx *c = &owner(ctx)->c;
+    if (!c->dtn_ready) return fail(WW_ERR_ARG, "dtn_apply: call dtn_setup first");
+    if (nrhs < 1 || nrhs > c->NC) return fail(WW_ERR_ARG, "dtn_apply: nrhs must be in [1, n + 2]");
+    WW_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    WW_TRY(launch_copy_cols(c, phi, nrhs, c->M));
+    WW_TRY(solve(c, c->M, nrhs));
+    WW_TRY(launch_gamma(c, 0, nrhs));
+    WW_TRY(apply_G(c, 0, nrhs));
+    WW_TRY(launch_copy_cols(c, c->Gout, nrhs, Gphi));
+    return check_status(c);
+}
+
+int shoot(ww_ctx *ctx, const double *cvec, double *r, double *f) {
+    if (!ctx || !cvec || !r || !f) return fail(WW_ERR_ARG, "shoot: NULL argument");
+    return run_shot(owner(ctx), cvec, false, r, nullptr, f, 0);
+}
+
+int shoot_jacobian(ww_ctx *ctx, const double *cvec, double *r, double *J, double *f) {
+    if (!ctx || !cvec || !r || !J || !f) return fail(WW_ERR_ARG, "shoot_jacobian: NULL argument");
+    return run_shot(owner(ctx), cvec, false, r, J, f, 1);
+}
+
+int shoot_jacobian_host(ww_ctx *ctx, const double *cvec, double *r, double *J, double *f) {
+    if (!ctx || !cvec || !r || !J || !f) return fail(WW_ERR_ARG, "shoot_jacobian_host: NULL argument");
+    Owned *o = owner(ctx);
+    Ctx *c = &o->c;
+    WW_TRY(run_shot(o, cvec, true, o->rbuf, o->Jbuf, o->fbuf, 1));
+    WW_CUDA_TRY(cudaMemcpyAsync(r, o->rbuf, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream));
+    WW_CUDA_TRY(cudaMemcpyAsync(J, o->Jbuf, sizeof(double) * c->N * c->nc, cudaMemcpyDeviceToHost, c->stream));
+    WW_CUDA_TRY(cudaMemcpyAsync(f, o->fbuf, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    WW_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return WW_OK;
+}
+
+int objective_and_grad(ww_ctx *ctx, const double *cvec, double *f, double *grad) {
+    if (!ctx || !cvec || !f || !grad) return fail(WW_ERR_ARG, "objective_and_grad: NULL argument");
+    Owned *o = owner(ctx);
+    Ctx *c = &o->c;
+    WW_TRY(run_shot(o, cvec, false, o->rbuf, o->Jbuf, f, 1));
+    k_jtr<<<c->nc, 256, 0, c->stream>>>(o->Jbuf, o->rbuf, c->N, grad);
+    WW_CUDA_TRY(cudaGetLastError());
+    WW_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return WW_OK;
+}
+
+}  // extern "C"

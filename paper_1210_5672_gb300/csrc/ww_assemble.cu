@@ -1,0 +1,118 @@
+// ww_assemble.cu -- boundary-integral kernel matrices of Sec. 2.2, Eq. (K1K2),
+// trapezoid collocation K_ij = K(alpha_i, alpha_j)/N, G_ij = G(alpha_i, alpha_j)/N,
+// A = 1/2 I + K.  Image kernels K2, G2 (finite depth) enter with a minus sign:
+// App. A, Eqs. (Phi), (plemelj:1), (plemelj:2) subtract the mirror-image layer,
+// which gives the flat-surface symbol k tanh(kh).
+//
+// Uniform grid: x = alpha_i - alpha_j = 2 pi (i - j)/N, so cos x, sin x and
+// cot(x/2) come from length-N tables.  exp(+-(eta_i -+ eta_j)) are products of
+// E = exp(eta) and 1/E, so no entry evaluates a transcendental function.  The
+// complex cotangent uses the branch-stable quotient of Sec. 2.2,
+//   cot((x+iy)/2) = (cos x + cosh y)/(sin x + i sinh y),   cos x >= 0,
+//                 = (sin x - i sinh y)/(cosh y - cos x),   cos x <  0,
+// neither of which cancels.  sinh of the small differences eta_i - eta_j is
+// taken from its Taylor series so that it keeps full relative accuracy.
+#include "ww_internal.cuh"
+
+namespace ww {
+
+namespace {
+
+constexpr int ASM_TI = 128;   // rows (i) per block, one per thread
+constexpr int ASM_TJ = 16;    // columns (j) per block, looped by each thread
+
+// sinh(y) for a difference y = eta_i - eta_j: series when small (no cancellation)
+__device__ __forceinline__ double sinh_diff(double y, double ey, double eyi) {
+    if (fabs(y) < 0.25) {
+        double y2 = y * y;
+        // y (1 + y^2/3! + y^4/5! + ... + y^12/13!), truncation < 1e-17 relative for |y| < 1/4
+        double p = 1.0 / 6227020800.0;
+        p = fma(p, y2, 1.0 / 39916800.0);
+        p = fma(p, y2, 1.0 / 362880.0);
+        p = fma(p, y2, 1.0 / 5040.0);
+        p = fma(p, y2, 1.0 / 120.0);
+        p = fma(p, y2, 1.0 / 6.0);
+        p = fma(p, y2, 1.0);
+        return y * p;
+    }
+    return 0.5 * (ey - eyi);
+}
+
+// cot((x + i y)/2) with cx = cos x, sx = sin x, ch = cosh y, sh = sinh y
+__device__ __forceinline__ double2 cot_half(double cx, double sx, double ch, double sh) {
+    if (cx >= 0.0) {
+        double num = cx + ch;
+        double inv = num / fma(sx, sx, sh * sh);
+        return make_double2(sx * inv, -sh * inv);
+    } else {
+        double inv = 1.0 / (ch - cx);
+        return make_double2(sx * inv, -sh * inv);
+    }
+}
+
+__global__ void __launch_bounds__(ASM_TI) k_assemble(const double *__restrict__ eta, const double *__restrict__ eta_x,
+                                                     const double *__restrict__ eta_xx, const double *__restrict__ E,
+                                                     const double *__restrict__ Einv, const double *__restrict__ cs,
+                                                     const double *__restrict__ cot0, int N, int deep, double *A,
+                                                     double *G) {
+    const int i = blockIdx.x * ASM_TI + threadIdx.x;
+    const int j0 = blockIdx.y * ASM_TJ;
+    if (i >= N) return;
+    const double invN = 1.0 / N;
+    const double ei = eta[i], exi = eta_x[i], Ei = E[i], Eii = Einv[i];
+    for (int jj = 0; jj < ASM_TJ; ++jj) {
+        const int j = j0 + jj;
+        if (j >= N) break;
+        const double ej = eta[j], exj = eta_x[j], Ej = E[j], Eij = Einv[j];
+        double k1, g1;
+        if (i == j) {
+            // diagonal limits: zeta''/(2 zeta') = (eta' eta'' + i eta'') / (2 (1 + eta'^2))
+            double d = 0.5 / fma(exi, exi, 1.0);
+            k1 = -eta_xx[i] * d;
+            g1 = exi * eta_xx[i] * d;
+        } else {
+            int m = i - j;
+            if (m < 0) m += N;
+            const double cx = cs[m], sx = cs[N + m];
+            // y = eta_i - eta_j: e^y = E_i / E_j
+            const double y = ei - ej;
+            const double ey = Ei * Eij, eyi = Eii * Ej;
+            const double ch = 0.5 * (ey + eyi);
+            const double sh = sinh_diff(y, ey, eyi);
+            double2 ct = cot_half(cx, sx, ch, sh);
+            // K1 = Im{ zeta'(beta)/2 cot }, zeta'(beta) = 1 + i eta'_j
+            k1 = 0.5 * fma(exj, ct.x, ct.y);
+            // G1 = Re{ zeta'(alpha)/2 cot - 1/2 cot((alpha - beta)/2) }, zeta'(alpha) = 1 + i eta'_i
+            g1 = 0.5 * (fma(-exi, ct.y, ct.x) - cot0[m]);
+        }
+        double k2 = 0.0, g2 = 0.0;
+        if (!deep) {
+            int m = i - j;
+            if (m < 0) m += N;
+            const double cx = cs[m], sx = cs[N + m];
+            // image: zeta(alpha) - conj(zeta(beta)) = x + i (eta_i + eta_j)
+            const double ep = Ei * Ej, epi = Eii * Eij;
+            const double ch = 0.5 * (ep + epi), sh = 0.5 * (ep - epi);
+            double2 ct = cot_half(cx, sx, ch, sh);
+            // K2 = -Im{ conj(zeta'(beta))/2 cot },  conj(zeta'(beta)) = 1 - i eta'_j
+            k2 = -0.5 * fma(-exj, ct.x, ct.y);
+            // G2 = -Re{ zeta'(alpha)/2 cot }
+            g2 = -0.5 * fma(-exi, ct.y, ct.x);
+        }
+        const size_t idx = (size_t)j * N + i;
+        A[idx] = (k1 + k2) * invN + (i == j ? 0.5 : 0.0);
+        G[idx] = (g1 + g2) * invN;
+    }
+}
+
+}  // namespace
+
+int launch_assemble(Ctx *c) {
+    dim3 grid((c->N + ASM_TI - 1) / ASM_TI, (c->N + ASM_TJ - 1) / ASM_TJ);
+    k_assemble<<<grid, ASM_TI, 0, c->stream>>>(c->eta, c->eta_x, c->eta_xx, c->E, c->Einv, c->cs, c->cs + 2 * c->N,
+                                               c->N, c->deep ? 1 : 0, c->A, c->G);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+}  // namespace ww

@@ -1,0 +1,181 @@
+// ww_internal.cuh -- context layout, launch helpers and shared-memory FFT of
+// the GB300 standing-wave Jacobian library.  Everything here is FP64 unless a
+// name says otherwise.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/ww.h"
+
+namespace ww {
+
+// --------------------------------------------------------------------------
+// error plumbing (thread-local message, status codes of ww.h)
+// --------------------------------------------------------------------------
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+
+#define WW_CUDA_TRY(expr)                                                        \
+    do {                                                                         \
+        cudaError_t e_ = (expr);                                                 \
+        if (e_ != cudaSuccess)                                                   \
+            return ::ww::fail(WW_ERR_CUDA, std::string(#expr " : ") +            \
+                                               cudaGetErrorString(e_));          \
+    } while (0)
+
+#define WW_TRY(expr)                                                             \
+    do {                                                                         \
+        int s_ = (expr);                                                         \
+        if (s_ != WW_OK) return s_;                                              \
+    } while (0)
+
+// device status bits (context status word)
+enum : int {
+    ST_GEOMETRY = 1,     // surface at/below the bottom or non-finite data
+    ST_NONFINITE = 2,    // NaN/Inf appeared in a right-hand side
+    ST_NO_CONV = 4,      // refinement did not reach its tolerance
+};
+
+constexpr int LU_NB = 64;   // block size of the blocked LU / triangular solves
+
+// --------------------------------------------------------------------------
+// the per-problem context: all device buffers are allocated in ww_create
+// --------------------------------------------------------------------------
+struct Mixed;   // mixed-precision workspace (ww_mixed.cu)
+
+struct Ctx {
+    // problem
+    int N, logN, n, nc, NC;   // nc = n + 1 Jacobian columns, NC = nc + 1 incl. base
+    double g, tau, h;
+    bool deep;
+    int steps, precision;
+    double refine_tol;
+    int max_refine;
+    int nb;                   // LU block size actually used (min(LU_NB, N))
+    cudaStream_t stream;
+
+    // tables
+    double2 *tw;              // tw[k] = exp(-2 pi i k / N), k < N/2
+    double *cs;               // cs[m] = cos(2 pi m / N), cs[N + m] = sin(2 pi m / N)
+
+    // base-surface geometry of the current stage (N each)
+    double *eta, *eta_x, *eta_xx, *phi_s;   // eta, eta', eta'', phi'
+    double *E, *Einv;                        // exp(eta), exp(-eta)
+    double *ux, *vy, *w3;                    // phi_x, phi_y, (1+eta'^2)^{-3/2}
+    double *curv;                            // d/dx (eta'/sqrt(1+eta'^2))
+    double *Fbase;                           // filtered base RHS (2N)
+
+    // dense operators
+    double *A;                // N x N: 1/2 I + K, overwritten by its LU factors
+    double *G;                // N x N
+    double *Dinv;             // inverted diagonal LU blocks: [nblk][2][nb x nb] (L^-1, U^-1)
+
+    // time-stepping state: [NC][2][N]  (column c: eta at c*2N, phi at c*2N + N)
+    double *Y, *Ys, *Kacc;
+
+    // multi-RHS workspaces (N x NC each, column-major)
+    double *M;                // right-hand sides -> solutions mu
+    double *Gam;              // gamma = mu'
+    double *Gout;             // 1/2 H gamma + G gamma
+
+    double *basis;            // N x 2 x n : column k = (eta part, phi part)
+    int *status;              // device status word
+    double *small;            // scratch doubles (reductions)
+
+    bool dtn_ready;
+    ww_stats stats;
+    Mixed *mx;
+};
+
+// --------------------------------------------------------------------------
+// complex helpers
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+// --------------------------------------------------------------------------
+// In-place complex FFT of length N = 2^logN held in shared memory, computed by
+// the whole thread block (radix-2, decimation in time after a bit-reversal
+// permutation).  Forward sign exp(-2 pi i jk/N); the inverse is unscaled.
+// Callers synchronise before and after.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void block_fft(double2 *s, int N, int logN, const double2 *__restrict__ tw,
+                                          bool inverse) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        int j = (int)(__brev((unsigned)i) >> (32 - logN));
+        if (i < j) {
+            double2 t = s[i];
+            s[i] = s[j];
+            s[j] = t;
+        }
+    }
+    __syncthreads();
+    const int halfN = N >> 1;
+    for (int lh = 0; lh < logN; ++lh) {         // half = 2^lh
+        const int half = 1 << lh;
+        const int tshift = logN - 1 - lh;      // twiddle stride N / (2 half)
+        for (int b = threadIdx.x; b < halfN; b += blockDim.x) {
+            int k = b & (half - 1);
+            int i0 = ((b >> lh) << (lh + 1)) + k;
+            int i1 = i0 + half;
+            double2 w = __ldg(&tw[k << tshift]);
+            if (inverse) w.y = -w.y;
+            double2 v = cmul(s[i1], w);
+            double2 u = s[i0];
+            s[i0] = cadd(u, v);
+            s[i1] = csub(u, v);
+        }
+        __syncthreads();
+    }
+}
+
+// signed wavenumber of FFT slot j
+__device__ __forceinline__ int wavenum(int j, int N) { return j <= (N >> 1) ? j : j - N; }
+
+// 36th-order filter of Eq. (filter): exp(-36 (|k| / (N/2))^36)
+__device__ __forceinline__ double filt36(int k, int N) {
+    double r = fabs((double)k) / (double)(N >> 1);
+    double r2 = r * r, r4 = r2 * r2, r8 = r4 * r4, r16 = r8 * r8, r32 = r16 * r16;
+    return exp(-36.0 * r32 * r4);
+}
+
+// --------------------------------------------------------------------------
+// kernels / host launchers implemented in the .cu files
+// --------------------------------------------------------------------------
+// spectral (ww_spectral.cu)
+int prepare_spectral(Ctx *c);                        // shared-memory limits of the FFT kernels
+int launch_base_geometry(Ctx *c, const double *eta, const double *phi, int with_phi);
+int launch_gamma(Ctx *c, int col0, int ncols);       // Gam = D M, Gout = 1/2 H D M (columns col0..)
+int launch_psi(Ctx *c);                              // M[:,1..nc] = phidot - phi_y etadot
+int launch_phi0(Ctx *c);                             // M[:,0] = phi of the base stage state
+int launch_base_rhs(Ctx *c, int stage, const double *cvec);
+int launch_col_rhs(Ctx *c, int stage, const double *cvec);
+int launch_initial(Ctx *c, const double *cvec, int with_columns);
+int launch_outputs(Ctx *c, double *r, double *J, double *f, int with_J);
+int launch_copy_cols(Ctx *c, const double *src, int ncols, double *dst);
+
+// assembly (ww_assemble.cu)
+int launch_assemble(Ctx *c);
+
+// dense FP64 (ww_dense.cu)
+int dgemm(cudaStream_t s, int m, int n, int k, double alpha, const double *A, int lda, const double *B,
+          int ldb, double beta, double *C, int ldc);
+int lu_factor_fp64(Ctx *c);
+int lu_solve_fp64(Ctx *c, double *B, int ncols);     // B <- A^{-1} B using the factors in c->A
+
+// mixed precision (ww_mixed.cu)
+int mixed_create(Ctx *c);
+void mixed_destroy(Ctx *c);
+int mixed_setup(Ctx *c);                             // after assembly: update the inverse
+int mixed_solve(Ctx *c, double *B, int ncols);       // B <- A^{-1} B (refined)
+int mixed_apply_G(Ctx *c, int col0, int ncols);      // Gout += G Gam (FP64-accurate)
+
+}  // namespace ww

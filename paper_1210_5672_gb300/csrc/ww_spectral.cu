@@ -1,0 +1,450 @@
+// ww_spectral.cu -- FFT-based kernels of one RK4 stage: base-surface
+// geometry, gamma = mu' and H gamma, the variational Dirichlet data psi, the
+// filtered right-hand sides of Eq. (ww) and Eqs. (l5a)/(l6a), the RK4 stage
+// combination and the end-of-step filter, initial data and outputs.
+//
+// Spectral conventions (Sec. 2.1, 2.2): d/dx multiplies mode k by ik and the
+// Hilbert transform by -i sgn k, both zero at the Nyquist mode; P removes
+// mode 0; the filter multiplies mode k by exp(-36 (|k|/(N/2))^36).  Because
+// d/dx, H d/dx = |k| and the filter are real operators, two real signals a, b
+// are transformed together as one complex signal a + i b and come back as
+// (L a) + i (L b) -- no even/odd separation is needed anywhere.
+#include "ww_internal.cuh"
+
+namespace ww {
+
+namespace {
+
+constexpr int FFT_THREADS = 256;
+
+__device__ __forceinline__ double2 times_ik(double2 z, int k) {   // (ik) z
+    return make_double2(-(double)k * z.y, (double)k * z.x);
+}
+
+// s <- s * m(k) / N for the derivative multiplier (ik, Nyquist zero)
+__device__ __forceinline__ void mul_deriv(double2 *s, int N) {
+    const double invN = 1.0 / N;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        int k = wavenum(j, N);
+        s[j] = (j == (N >> 1)) ? make_double2(0.0, 0.0) : cscale(times_ik(s[j], k), invN);
+    }
+}
+
+// ------------------------------------------------------------------------
+// base geometry: eta', phi', eta'' (= d/dx of eta'), curvature term
+// d/dx (eta'/sqrt(1+eta'^2)), exp(+-eta); geometry check.   (Sec. 2.1)
+// ------------------------------------------------------------------------
+__global__ void k_base_geometry(const double *__restrict__ eta_in, const double *__restrict__ phi_in,
+                                int with_phi, int N, int logN, int deep, const double2 *__restrict__ tw,
+                                double *eta, double *eta_x, double *eta_xx, double *phi_s, double *curv,
+                                double *E, double *Einv, int *status) {
+    extern __shared__ double2 sm[];
+    double2 *s = sm;
+    int bad = 0;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double e = eta_in[j];
+        double p = with_phi ? phi_in[j] : 0.0;
+        if (!isfinite(e) || !isfinite(p) || (!deep && e <= 0.0)) bad = 1;
+        eta[j] = e;
+        E[j] = exp(e);
+        Einv[j] = exp(-e);
+        s[j] = make_double2(e, p);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_GEOMETRY);
+    block_fft(s, N, logN, tw, false);
+    mul_deriv(s, N);
+    __syncthreads();
+    block_fft(s, N, logN, tw, true);
+    // s = eta' + i phi'
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double ex = s[j].x;
+        eta_x[j] = ex;
+        phi_s[j] = s[j].y;
+        s[j] = make_double2(ex / sqrt(1.0 + ex * ex), ex);   // (eta'/sqrt(1+eta'^2)) + i eta'
+    }
+    __syncthreads();
+    block_fft(s, N, logN, tw, false);
+    mul_deriv(s, N);
+    __syncthreads();
+    block_fft(s, N, logN, tw, true);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        curv[j] = s[j].x;
+        eta_xx[j] = s[j].y;
+    }
+}
+
+// ------------------------------------------------------------------------
+// gamma = mu' and 1/2 H gamma for pairs of columns of M (Eq. G)
+// ------------------------------------------------------------------------
+__global__ void k_gamma(const double *__restrict__ M, int ncols, int N, int logN,
+                        const double2 *__restrict__ tw, double *Gam, double *Gout) {
+    extern __shared__ double2 sm[];
+    double2 *s = sm, *z = sm + N;
+    const int ca = 2 * blockIdx.x, cb = ca + 1;
+    const bool hasb = cb < ncols;
+    const double *ma = M + (size_t)ca * N, *mb = M + (size_t)cb * N;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) s[j] = make_double2(ma[j], hasb ? mb[j] : 0.0);
+    __syncthreads();
+    block_fft(s, N, logN, tw, false);
+    const double invN = 1.0 / N;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        int k = wavenum(j, N);
+        double2 v = s[j];
+        bool nyq = (j == (N >> 1));
+        z[j] = nyq ? make_double2(0.0, 0.0) : cscale(v, 0.5 * fabs((double)k) * invN);  // 1/2 H d/dx = |k|/2
+        s[j] = nyq ? make_double2(0.0, 0.0) : cscale(times_ik(v, k), invN);
+    }
+    __syncthreads();
+    block_fft(s, N, logN, tw, true);
+    block_fft(z, N, logN, tw, true);
+    double *ga = Gam + (size_t)ca * N, *gb = Gam + (size_t)cb * N;
+    double *oa = Gout + (size_t)ca * N, *ob = Gout + (size_t)cb * N;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        ga[j] = s[j].x;
+        oa[j] = z[j].x;
+        if (hasb) {
+            gb[j] = s[j].y;
+            ob[j] = z[j].y;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// psi_c = phidot_c - phi_y etadot_c for the variational columns (App. B)
+// ------------------------------------------------------------------------
+__global__ void k_psi(const double *__restrict__ Ys, const double *__restrict__ vy, int N, int nc,
+                      double *M) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y + 1;   // variational columns 1..nc
+    if (i >= N || c > nc) return;
+    const double *col = Ys + (size_t)c * 2 * N;
+    M[(size_t)c * N + i] = col[N + i] - vy[i] * col[i];
+}
+
+// ------------------------------------------------------------------------
+// RK4 stage combination for one column held in registers/shared memory.
+// Classic RK4: stages at a = (0, 1/2, 1/2, 1), weights b = (1, 2, 2, 1)/6.
+// For stage < 3: acc (+)= b k, Ys = Y + a_next dt k.  For the last stage the
+// caller filters Y + dt/6 (acc + k) and stores it in Y and Ys.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ double rk_b(int st) { return (st == 1 || st == 2) ? 2.0 : 1.0; }
+__device__ __forceinline__ double rk_a_next(int st) { return st == 2 ? 1.0 : 0.5; }
+
+// end-of-step update of one column: s holds k (eta part .x, phi part .y) in
+// physical space; writes the filtered new state into Y and Ys.
+__device__ void finish_step(double2 *s, int N, int logN, const double2 *__restrict__ tw, double dt,
+                            double *Yc, double *Ysc, const double *Accc) {
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double2 k = s[j];
+        s[j] = make_double2(Yc[j] + dt / 6.0 * (Accc[j] + k.x), Yc[N + j] + dt / 6.0 * (Accc[N + j] + k.y));
+    }
+    __syncthreads();
+    block_fft(s, N, logN, tw, false);
+    const double invN = 1.0 / N;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) s[j] = cscale(s[j], filt36(wavenum(j, N), N) * invN);
+    __syncthreads();
+    block_fft(s, N, logN, tw, true);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        Yc[j] = Ysc[j] = s[j].x;
+        Yc[N + j] = Ysc[N + j] = s[j].y;
+    }
+}
+
+__device__ void stage_update(double2 *s, int N, int logN, const double2 *__restrict__ tw, int st, double dt,
+                             double *Yc, double *Ysc, double *Accc) {
+    if (st < 3) {
+        const double b = rk_b(st), a = rk_a_next(st);
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            double2 k = s[j];
+            if (st == 0) {
+                Accc[j] = b * k.x;
+                Accc[N + j] = b * k.y;
+            } else {
+                Accc[j] += b * k.x;
+                Accc[N + j] += b * k.y;
+            }
+            Ysc[j] = Yc[j] + a * dt * k.x;
+            Ysc[N + j] = Yc[N + j] + a * dt * k.y;
+        }
+    } else {
+        __syncthreads();
+        finish_step(s, N, logN, tw, dt, Yc, Ysc, Accc);
+    }
+}
+
+// ------------------------------------------------------------------------
+// base right-hand side, Eq. (ww) with Eq. (uv:from:G); filtered; RK update
+// ------------------------------------------------------------------------
+__global__ void k_base_rhs(const double *__restrict__ Gphi, const double *__restrict__ eta,
+                           const double *__restrict__ eta_x, const double *__restrict__ phi_s,
+                           const double *__restrict__ curv, double g, double tau, int N, int logN,
+                           const double2 *__restrict__ tw, double *ux, double *vy, double *w3, double *Fbase,
+                           double *Y, double *Ys, double *Acc, int st, const double *__restrict__ cvec,
+                           int steps, int update, int *status) {
+    extern __shared__ double2 sm[];
+    double2 *s = sm;
+    int bad = 0;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double ex = eta_x[j], d = 1.0 + ex * ex, gp = Gphi[j], pp = phi_s[j];
+        double u = (pp - ex * gp) / d;
+        double v = (ex * pp + gp) / d;
+        ux[j] = u;
+        vy[j] = v;
+        w3[j] = 1.0 / (d * sqrt(d));
+        double pt = v * gp - 0.5 * u * u - 0.5 * v * v - g * eta[j] + tau * curv[j];
+        if (!isfinite(pt) || !isfinite(gp)) bad = 1;
+        s[j] = make_double2(gp, pt);   // eta_t = G phi ; phi_t before P and the filter
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
+    block_fft(s, N, logN, tw, false);
+    const double invN = 1.0 / N;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double f = filt36(wavenum(j, N), N) * invN;
+        // P acts on the phi part only: at k = 0 keep Re (eta mean), drop Im (phi mean)
+        s[j] = (j == 0) ? make_double2(s[0].x * f, 0.0) : cscale(s[j], f);
+    }
+    __syncthreads();
+    block_fft(s, N, logN, tw, true);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        Fbase[j] = s[j].x;
+        Fbase[N + j] = s[j].y;
+    }
+    if (!update) return;
+    const double dt = cvec[0] / (4.0 * steps);
+    __syncthreads();
+    stage_update(s, N, logN, tw, st, dt, Y, Ys, Acc);
+}
+
+// ------------------------------------------------------------------------
+// variational right-hand sides, Eqs. (l5a) and (l6a), one column per block:
+//   etadot_t = G psi - (etadot u)'
+//   phidot_t = P[ -(etadot u v)' - u psi' + v G psi - g etadot
+//                 + tau (etadot' (1+eta'^2)^{-3/2})' ]
+// filtered; the T column (column 1) adds F(q)/T; then the RK update.
+// ------------------------------------------------------------------------
+__global__ void k_col_rhs(const double *__restrict__ Gout, const double *__restrict__ ux,
+                          const double *__restrict__ vy, const double *__restrict__ w3,
+                          const double *__restrict__ Fbase, double g, double tau, int N, int logN,
+                          const double2 *__restrict__ tw, double *Y, double *Ys, double *Acc, int st,
+                          const double *__restrict__ cvec, int steps, int *status) {
+    extern __shared__ double2 sm[];
+    double2 *s = sm, *z = sm + N;
+    const int c = blockIdx.x + 1;
+    double *Yc = Y + (size_t)c * 2 * N, *Ysc = Ys + (size_t)c * 2 * N, *Accc = Acc + (size_t)c * 2 * N;
+    const double *Gpsi = Gout + (size_t)c * N;
+    // psi + i etadot  ->  psi' + i etadot'
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double ed = Ysc[j];
+        s[j] = make_double2(Ysc[N + j] - vy[j] * ed, ed);
+    }
+    __syncthreads();
+    block_fft(s, N, logN, tw, false);
+    mul_deriv(s, N);
+    __syncthreads();
+    block_fft(s, N, logN, tw, true);
+    int bad = 0;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double ed = Ysc[j], u = ux[j], v = vy[j], gp = Gpsi[j];
+        double dpsi = s[j].x, ded = s[j].y;
+        // undifferentiated terms: (G psi, -u psi' + v G psi - g etadot)
+        z[j] = make_double2(gp, -u * dpsi + v * gp - g * ed);
+        // terms under one d/dx: (-etadot u, tau etadot' w3 - etadot u v)
+        s[j] = make_double2(-ed * u, tau * ded * w3[j] - ed * u * v);
+        if (!isfinite(gp)) bad = 1;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
+    block_fft(z, N, logN, tw, false);
+    block_fft(s, N, logN, tw, false);
+    const double invN = 1.0 / N;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        int k = wavenum(j, N);
+        double f = filt36(k, N) * invN;
+        double2 w;
+        if (j == 0)
+            w = make_double2(z[0].x * f, 0.0);       // P on the phi part; d/dx kills k = 0
+        else if (j == (N >> 1))
+            w = cscale(z[j], f);                      // d/dx is zero at Nyquist
+        else
+            w = cscale(cadd(z[j], times_ik(s[j], k)), f);
+        s[j] = w;
+    }
+    __syncthreads();
+    block_fft(s, N, logN, tw, true);
+    if (c == 1) {   // d/dT column: + F(q) / T  (dt = T / (4 steps) is a function of T)
+        const double invT = 1.0 / cvec[0];
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            s[j].x += Fbase[j] * invT;
+            s[j].y += Fbase[N + j] * invT;
+        }
+    }
+    const double dt = cvec[0] / (4.0 * steps);
+    __syncthreads();
+    stage_update(s, N, logN, tw, st, dt, Yc, Ysc, Accc);
+}
+
+// ------------------------------------------------------------------------
+// initial data (Sec. 3.1): q0 = (hbar + B_eta c, B_phi c); T column 0;
+// mode columns = basis
+// ------------------------------------------------------------------------
+__global__ void k_initial(const double *__restrict__ basis, const double *__restrict__ cvec, int N, int n,
+                          double hbar, int with_columns, double *Y, double *Ys, double *Acc) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double se = hbar, sp = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double ck = cvec[k + 1];
+        se = fma(ck, basis[(size_t)k * 2 * N + i], se);
+        sp = fma(ck, basis[(size_t)k * 2 * N + N + i], sp);
+    }
+    Y[i] = Ys[i] = se;
+    Y[N + i] = Ys[N + i] = sp;
+    Acc[i] = Acc[N + i] = 0.0;
+    if (!with_columns) return;
+    // T column
+    double *t = Y + 2 * N, *ts = Ys + 2 * N;
+    t[i] = t[N + i] = ts[i] = ts[N + i] = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double *y = Y + (size_t)(k + 2) * 2 * N, *ys = Ys + (size_t)(k + 2) * 2 * N;
+        double be = basis[(size_t)k * 2 * N + i], bp = basis[(size_t)k * 2 * N + N + i];
+        y[i] = ys[i] = be;
+        y[N + i] = ys[N + i] = bp;
+    }
+}
+
+// ------------------------------------------------------------------------
+// outputs, Eqs. (f:phi), (Jik): r = phi/sqrt(N), J_k = phidot_k/sqrt(N)
+// ------------------------------------------------------------------------
+__global__ void k_outputs_J(const double *__restrict__ Y, int N, int nc, double *J) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    if (i >= N || c >= nc) return;
+    J[(size_t)c * N + i] = Y[(size_t)(c + 1) * 2 * N + N + i] * rsqrt((double)N);
+}
+
+__global__ void k_outputs_r(const double *__restrict__ Y, int N, double *r, double *f) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    const double w = rsqrt((double)N);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double v = Y[N + i] * w;
+        r[i] = v;
+        acc = fma(v, v, acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int nw = blockDim.x >> 5;
+        acc = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) *f = 0.5 * acc;
+    }
+}
+
+__global__ void k_copy_cols(const double *__restrict__ src, int N, int ncols, double *dst) {
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < (size_t)N * ncols) dst[i] = src[i];
+}
+
+__global__ void k_copy_phi0(const double *__restrict__ Ys, int N, double *M) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) M[i] = Ys[N + i];
+}
+
+template <typename K>
+int set_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) WW_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return WW_OK;
+}
+
+}  // namespace
+
+// ==========================================================================
+// host launchers
+// ==========================================================================
+int prepare_spectral(Ctx *c) {
+    const size_t one = sizeof(double2) * c->N, two = 2 * one;
+    WW_TRY(set_smem(k_base_geometry, one));
+    WW_TRY(set_smem(k_base_rhs, one));
+    WW_TRY(set_smem(k_gamma, two));
+    WW_TRY(set_smem(k_col_rhs, two));
+    return WW_OK;
+}
+
+int launch_base_geometry(Ctx *c, const double *eta, const double *phi, int with_phi) {
+    size_t sm = sizeof(double2) * c->N;
+    k_base_geometry<<<1, FFT_THREADS, sm, c->stream>>>(eta, phi, with_phi, c->N, c->logN, c->deep ? 1 : 0, c->tw,
+                                                      c->eta, c->eta_x, c->eta_xx, c->phi_s, c->curv, c->E,
+                                                      c->Einv, c->status);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+int launch_gamma(Ctx *c, int col0, int ncols) {
+    size_t sm = 2 * sizeof(double2) * c->N;
+    size_t off = (size_t)col0 * c->N;
+    k_gamma<<<(ncols + 1) / 2, FFT_THREADS, sm, c->stream>>>(c->M + off, ncols, c->N, c->logN, c->tw, c->Gam + off,
+                                                            c->Gout + off);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+int launch_psi(Ctx *c) {
+    dim3 grid((c->N + 255) / 256, c->nc);
+    k_psi<<<grid, 256, 0, c->stream>>>(c->Ys, c->vy, c->N, c->nc, c->M);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+int launch_phi0(Ctx *c) {
+    k_copy_phi0<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->Ys, c->N, c->M);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+// stage < 0: evaluate the base RHS only (no RK update)
+int launch_base_rhs(Ctx *c, int stage, const double *cvec) {
+    size_t sm = sizeof(double2) * c->N;
+    k_base_rhs<<<1, FFT_THREADS, sm, c->stream>>>(c->Gout, c->eta, c->eta_x, c->phi_s, c->curv, c->g, c->tau, c->N,
+                                                 c->logN, c->tw, c->ux, c->vy, c->w3, c->Fbase, c->Y, c->Ys,
+                                                 c->Kacc, stage < 0 ? 0 : stage, cvec, c->steps, stage >= 0 ? 1 : 0,
+                                                 c->status);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+int launch_col_rhs(Ctx *c, int stage, const double *cvec) {
+    if (c->nc <= 0) return WW_OK;
+    size_t sm = 2 * sizeof(double2) * c->N;
+    k_col_rhs<<<c->nc, FFT_THREADS, sm, c->stream>>>(c->Gout, c->ux, c->vy, c->w3, c->Fbase, c->g, c->tau, c->N,
+                                                    c->logN, c->tw, c->Y, c->Ys, c->Kacc, stage, cvec, c->steps,
+                                                    c->status);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+int launch_initial(Ctx *c, const double *cvec, int with_columns) {
+    k_initial<<<(c->N + 127) / 128, 128, 0, c->stream>>>(c->basis, cvec, c->N, c->n, c->deep ? 0.0 : c->h,
+                                                        with_columns, c->Y, c->Ys, c->Kacc);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+int launch_outputs(Ctx *c, double *r, double *J, double *f, int with_J) {
+    k_outputs_r<<<1, 1024, 0, c->stream>>>(c->Y, c->N, r, f);
+    if (with_J) {
+        dim3 grid((c->N + 255) / 256, c->nc);
+        k_outputs_J<<<grid, 256, 0, c->stream>>>(c->Y, c->N, c->nc, J);
+    }
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+int launch_copy_cols(Ctx *c, const double *src, int ncols, double *dst) {
+    size_t tot = (size_t)c->N * ncols;
+    k_copy_cols<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(src, c->N, ncols, dst);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+}  // namespace ww

@@ -1,0 +1,217 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Tolerance: 1e-11 relative in the FP64 form, measured as ||d r||/||r||,
+|d f|/|f| and, per Jacobian column, ||d J_k||/||J_k|| (max over k).  The two
+sides use different summation orders, FFTs, cotangent formulas and solvers
+(no pivoting on the GPU, partial pivoting in the oracle), so agreement is at
+the roundoff floor of the method, not bitwise.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1210_5672_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def ww():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1210_5672_gb300 import build as B
+    B.build()
+    import paper_1210_5672_gb300 as m
+    m.lib()
+    return m
+
+
+def dev(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def x_grid(N):
+    return 2 * np.pi * np.arange(N) / N
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def col_rel(J, J0):
+    return max(rel(J[:, k], J0[:, k]) for k in range(J0.shape[1]))
+
+
+def gpu_jacobian(ww, w, c, precision=0, basis=None, **kw):
+    with ww.Context(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps, basis=basis, precision=precision,
+                    **kw) as ctx:
+        r, J, f = ctx.empty_outputs()
+        ww.shoot_jacobian(ctx, dev(c), r, J, f)
+        st = ctx.stats()
+        return r.cpu().numpy(), J.cpu().numpy().T.copy(), float(f.item()), st
+
+
+# ------------------------------------------------------------------ DtN
+@pytest.mark.parametrize("N,h", [(64, 1.0), (256, 0.3), (64, math.inf), (1024, 0.05)])
+def test_dtn_flat_symbol(ww, N, h):
+    x = x_grid(N)
+    eta = np.full(N, 0.0 if math.isinf(h) else h)
+    ks = [1, 2, 5, N // 4 - 1]
+    phi = np.stack([np.cos(k * x) for k in ks])
+    with ww.Context(N, len(ks) + 2, h=h) as ctx:
+        ww.dtn_setup(ctx, dev(eta))
+        out = ww.dtn_apply(ctx, dev(phi)).cpu().numpy()
+    for row, k in zip(out, ks):
+        sym = k if math.isinf(h) else k * math.tanh(k * h)
+        assert np.max(np.abs(row - sym * np.cos(k * x))) < 2e-12 * max(1, sym), k
+
+
+@pytest.mark.parametrize("N,h,nrhs", [(64, 1.0, 7), (512, 1.0, 37), (128, math.inf, 5), (512, 0.4, 1)])
+def test_dtn_apply_matches_oracle(ww, N, h, nrhs):
+    """Random smooth surface and data; nrhs spans several 64-column tiles with a ragged tail."""
+    rng = np.random.default_rng(N + nrhs)
+    x = x_grid(N)
+    eta = (0.0 if math.isinf(h) else h) + sum(0.1 / k**2 * rng.uniform(-1, 1) * np.cos(k * x) for k in range(1, 9))
+    phi = np.stack([sum(rng.uniform(-1, 1) / k**2 * np.cos(k * x + rng.uniform(0, 6)) for k in range(1, 12))
+                    for _ in range(nrhs)])
+    with ww.Context(N, nrhs, h=h) as ctx:
+        ww.dtn_setup(ctx, dev(eta))
+        got = ww.dtn_apply(ctx, dev(phi)).cpu().numpy()
+    ref = O.dtn(eta, phi, h)
+    for a, b in zip(got, ref):
+        assert rel(a, b) < 1e-12
+
+
+def test_dtn_geometry_error(ww):
+    N = 64
+    x = x_grid(N)
+    with ww.Context(N, 2, h=1.0) as ctx:
+        with pytest.raises(ww.WWError) as ei:
+            ww.dtn_setup(ctx, dev(0.5 * np.cos(x)))   # touches the bottom (eta <= 0)
+        assert ei.value.code == -2
+        eta = np.full(N, 1.0)
+        eta[3] = np.nan
+        with pytest.raises(ww.WWError):
+            ww.dtn_setup(ctx, dev(eta))
+        with pytest.raises(ww.WWError) as ei:
+            ww.dtn_apply(ctx, dev(np.zeros((1, N))))   # no valid setup
+        assert ei.value.code == -1
+
+
+def test_bad_sizes_rejected(ww):
+    for kw in ({"N": 100, "n": 4}, {"N": 8, "n": 4}, {"N": 64, "n": -1}, {"N": 64, "n": 4, "steps": 0},
+               {"N": 64, "n": 4, "h": -1.0}, {"N": 64, "n": 4, "precision": 7}):
+        with pytest.raises(ww.WWError) as ei:
+            ww.Context(**kw)
+        assert ei.value.code == -1
+
+
+# ------------------------------------------------------------------ Jacobian
+def test_small_workload_jacobian(ww):
+    """N = 64, 12 modes + T, 64 RK4 steps, h = 1 (the small benchmark shape)."""
+    w = W.SMALL
+    c, _ = W.coefficients(w)
+    r, J, f, _ = gpu_jacobian(ww, w, c)
+    prob, _ = O.make_problem(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps)
+    r0, J0, f0 = O.shoot_jacobian(prob, c)
+    assert rel(r, r0) < TOL and abs(f - f0) / f0 < TOL
+    assert col_rel(J, J0) < TOL
+
+
+@pytest.mark.parametrize("N,n,steps,h,tau,amp", [
+    (256, 70, 8, 1.0, 0.0, 0.2),       # several 64-wide tiles, ragged tail (71 columns)
+    (128, 20, 16, math.inf, 0.1, 0.1),  # deep water with surface tension
+    (512, 33, 4, 0.3, 0.05, 0.05),      # shallower, tension, odd column count
+])
+def test_jacobian_matches_oracle(ww, N, n, steps, h, tau, amp):
+    w = W.Workload("t", N=N, n=n, steps=steps, h=h, tau=tau, amp=amp)
+    c, _ = W.coefficients(w)
+    r, J, f, _ = gpu_jacobian(ww, w, c)
+    prob, _ = O.make_problem(N, n, g=w.g, tau=tau, h=h, steps=steps)
+    r0, J0, f0 = O.shoot_jacobian(prob, c)
+    assert rel(r, r0) < TOL and abs(f - f0) / f0 < TOL
+    assert col_rel(J, J0) < TOL
+
+
+def test_custom_basis_and_phi_initial_data(ww):
+    """Paper's own parameterisation (Eq. init:stand): even modes on eta, odd on phi."""
+    N, n, steps = 64, 6, 12
+    x = x_grid(N)
+    B = np.zeros((2 * N, n))
+    for k in range(1, n + 1):
+        if k % 2 == 0:
+            B[:N, k - 1] = 2 * np.cos(k * x)
+        else:
+            B[N:, k - 1] = 2 * np.cos(k * x)
+    c = np.array([7.2, 0.01, 0.02, -0.003, 0.001, 0.0004, -0.0001])
+    w = W.Workload("t", N=N, n=n, steps=steps)
+    r, J, f, _ = gpu_jacobian(ww, w, c, basis=B)
+    prob, keep = O.make_problem(N, n, steps=steps, basis=B)
+    r0, J0, f0 = O.shoot_jacobian(prob, c)
+    assert rel(r, r0) < TOL and abs(f - f0) / f0 < TOL and col_rel(J, J0) < TOL
+
+
+def test_shoot_and_gradient_consistent(ww):
+    import torch
+    w = W.shrink(W.MEDIUM, N=128, n=16, steps=8)
+    c, _ = W.coefficients(w)
+    with ww.Context(w.N, w.n, h=w.h, steps=w.steps) as ctx:
+        ct = dev(c)
+        r, J, f = ctx.empty_outputs()
+        ww.shoot_jacobian(ctx, ct, r, J, f)
+        r2 = torch.empty_like(r)
+        f2 = torch.empty_like(f)
+        ww.shoot(ctx, ct, r2, f2)
+        grad = torch.empty(w.n + 1, dtype=torch.float64, device="cuda")
+        f3 = torch.empty_like(f)
+        ww.objective_and_grad(ctx, ct, f3, grad)
+        cg = ct.clone().requires_grad_(True)
+        fa = ww.shooting_objective(cg, ctx)
+        fa.backward()
+    r, J, r2 = r.cpu().numpy(), J.cpu().numpy().T, r2.cpu().numpy()
+    assert np.array_equal(r, r2) and f.item() == f2.item() == f3.item()
+    jtr = J.T @ r
+    assert rel(grad.cpu().numpy(), jtr) < 1e-13
+    assert rel(cg.grad.cpu().numpy(), jtr) < 1e-13 and fa.item() == f.item()
+
+
+def test_host_entry_point_matches_device(ww):
+    w = W.shrink(W.MEDIUM, N=128, n=10, steps=4)
+    c, _ = W.coefficients(w)
+    with ww.Context(w.N, w.n, h=w.h, steps=w.steps) as ctx:
+        r, J, f = ctx.empty_outputs()
+        ww.shoot_jacobian(ctx, dev(c), r, J, f)
+        rh, Jh, fh = np.empty(w.N), np.empty((w.n + 1, w.N)), np.empty(1)
+        ww.shoot_jacobian_host(ctx, np.ascontiguousarray(c), rh, Jh, fh)
+    assert np.array_equal(rh, r.cpu().numpy()) and np.array_equal(Jh, J.cpu().numpy()) and fh[0] == f.item()
+
+
+def test_geometry_failure_in_shot_reports_status(ww):
+    """Initial surface below the bottom: the shot returns WW_ERR_GEOMETRY (read
+    from the device status word) instead of producing garbage."""
+    N, n = 64, 2
+    c = np.array([8.0, 1.2, 0.0])
+    with ww.Context(N, n, h=1.0, steps=4) as ctx:
+        r, J, f = ctx.empty_outputs()
+        with pytest.raises(ww.WWError) as ei:
+            ww.shoot_jacobian(ctx, dev(c), r, J, f)
+        assert ei.value.code == -2
+
+
+@pytest.mark.slow
+def test_large_workload_one_step_sampled(ww):
+    """Full-size shape (N = 2048, 512 modes + T) in the benchmark's launch
+    configuration for ONE RK4 step (the oracle cannot run 1024 steps); every
+    column compared, plus r and f."""
+    w = W.shrink(W.LARGE, steps=1)
+    c, _ = W.coefficients(w)
+    r, J, f, _ = gpu_jacobian(ww, w, c)
+    prob, _ = O.make_problem(w.N, w.n, h=w.h, steps=1)
+    r0, J0, f0 = O.shoot_jacobian(prob, c)
+    assert rel(r, r0) < TOL and abs(f - f0) / f0 < TOL
+    assert col_rel(J, J0) < TOL
