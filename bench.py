@@ -1,0 +1,337 @@
+"""Benchmark: Jacobian columns per second of the standing-wave shooting map.
+
+One step = one full shoot_jacobian (all RK4 stages of all columns, setup and
+outputs included) on the seeded N = 2048 workload (512 Fourier unknowns + T,
+1024 RK4 steps, h = 1, c_1 = 0.4, c_k = 0.4^k u_k).  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--form mixed|fp64]
+                  [--impl ours|reference] [--workload NAME]
+
+--impl reference times the CPU FP64 oracle (the only baseline: the paper's
+code is not available) on a bounded sample of the same workload.  Under
+torchrun every rank runs an independent replica (its own seed; the path has
+no exchange step), the slowest rank's time is reported and value counts the
+columns of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1210_5672_gb300 import workloads as W  # noqa: E402
+
+METRIC = "Jacobian columns/s at N=2048, mixed vs plain FP64 at 1e-12 rel err; % roofline"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+# FP64 pipe of GB300: 2 FP64 FMA per clock per SM (1/64 of FP32), 152 SMs,
+# 2070 MHz maximum -> 2 * 2 * 152 * 2.07e9 = 1.259 TFLOP/s.
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch
+    import torch.distributed as dist
+    rank, local = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(x, ws):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-i", str(self.index), "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        try:
+            with open(self.f.name) as fh:
+                for line in fh:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        finally:
+            os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def flush_l2(buf):
+    buf.add_(1.0)   # 512 MB read + write: evicts the 129 MB L2
+
+
+def roofline_for(form, timing, w, pk):
+    """Dominant kernel: the phase with the largest measured share."""
+    N, nc = w.N, w.n + 1
+    # algorithmic work per launch of each candidate phase (the design doc lists them)
+    if form == "fp64":
+        dom = max(("factor", "solve", "gapply", "assembly"), key=lambda p: timing[p][0])
+        flops = {"factor": 2.0 / 3.0 * N**3, "solve": 2.0 * N * N * nc, "gapply": 2.0 * N * N * nc,
+                 "assembly": 60.0 * N * N}[dom]
+        ms, cnt = timing[dom]
+        achieved = flops / (ms / cnt / 1e3) / 1e12
+        return dom, {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": {"factor": "k_dgemm (LU)", "solve": "k_dgemm (TRSM)", "gapply": "k_dgemm",
+                                "assembly": "k_assemble"}[dom],
+                     "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"}
+    dom = max(timing, key=lambda p: timing[p][0])
+    ms, cnt = timing[dom]
+    return dom, {"bound": "tensor", "achieved": None, "peak": pk.get("bf16_tflops"), "unit": "TFLOP/s",
+                 "frac": None, "traffic": None, "kernel": dom}
+
+
+def run_ours(args):
+    import torch
+    import paper_1210_5672_gb300 as ww
+
+    rank, ws, local = dist_init()
+    w = W.ALL[args.workload]
+    if args.rk_steps:
+        w = W.shrink(w, steps=args.rk_steps, name=f"{w.name}[profile: {args.rk_steps} RK steps]")
+    form = args.form
+    c, seed_used = W.coefficients(w, seed=w.seed + rank)
+    prec = ww.WW_MIXED if form == "mixed" else ww.WW_FP64
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ctx = ww.Context(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps, precision=prec)
+    ct = torch.tensor(c, dtype=torch.float64, device=dev)
+    r, J, f = ctx.empty_outputs()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        ww.shoot_jacobian(ctx, ct, r, J, f)
+    torch.cuda.synchronize()
+    # ---- timed region: K Jacobians, L2 flushed between them (outside the events)
+    ctx.set_timing(True)
+    times, phase = [], {p: [0.0, 0] for p in ww.PHASES}
+    stream = torch.cuda.Stream(dev)
+    ctx.set_stream(stream)
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush_l2(flush)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ww.shoot_jacobian(ctx, ct, r, J, f)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            for p, (ms, cnt) in ctx.timing().items():
+                phase[p][0] += ms
+                phase[p][1] += cnt
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = clk.summary()
+    ctx.set_timing(False)
+    t_step = allmax(sum(times) / len(times), ws)
+    value = ws * (w.n + 1) / t_step
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    ch = torch.tensor(c, dtype=torch.float64).pin_memory().numpy()
+    rh = torch.empty(w.N, dtype=torch.float64).pin_memory().numpy()
+    Jh = torch.empty((w.n + 1, w.N), dtype=torch.float64).pin_memory().numpy()
+    fh = torch.empty(1, dtype=torch.float64).pin_memory().numpy()
+    e2e_t = []
+    for _ in range(max(1, min(args.steps, 2))):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ww.shoot_jacobian_host(ctx, ch, rh, Jh, fh)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_step = allmax(sum(e2e_t) / len(e2e_t), ws)
+    timing = {p: tuple(v) for p, v in phase.items()}
+    dom, roof = roofline_for(form, timing, w, peaks())
+    stats = ctx.stats()
+    # kernel launches inside the timed region: counted per stage from the step program
+    launches_per_stage = launches_in_stage(form, w)
+    gpu_launches = args.steps * (4 * w.steps * launches_per_stage + 2)
+    ctx.close()
+    if rank != 0:
+        return None
+    out = {
+        "metric": METRIC, "value": value, "unit": "Jacobian columns/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if form == "fp64" else "f64+f32/bf16-tensor",
+        "data": "synthetic (seeded PCG64 standing-wave coefficients)",
+        "config": {"workload": w.name, "N": w.N, "n": w.n, "columns": w.n + 1, "rk4_steps": w.steps,
+                   "h": w.h, "g": w.g, "tau": w.tau, "form": form, "seed": seed_used,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "flushed between timed steps (512 MB write)"},
+        "e2e": {"value": ws * (w.n + 1) / e2e_step, "unit": "Jacobian columns/s",
+                "h2d_bytes_per_step": 8 * (w.n + 1), "d2h_bytes_per_step": 8 * (w.N + w.N * (w.n + 1) + 1)},
+        "roofline": roof,
+        "phases_ms_per_step": {p: v[0] / args.steps for p, v in timing.items()},
+        "stats": stats,
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(w, c)
+    return out
+
+
+def launches_in_stage(form, w):
+    """Kernel launches of one RK stage of the step program (see ww_api.cu)."""
+    N, nb = w.N, min(64, w.N)
+    nblk = (N + nb - 1) // nb
+    if form == "fp64":
+        lu = 3 * (nblk - 1) + 1 + (nblk - 1)          # diag + 2 applies + dgemm per panel
+        solve = 2 * (2 * nblk - 1)                    # apply + dgemm per block, both triangles
+        per = 1 + 1 + lu                              # geometry, assembly, LU
+        per += 1 + solve + 1 + 1 + 1                  # base: copy, solve, gamma, gemv, rhs
+        per += 1 + solve + 1 + 1 + 1                  # columns: psi, solve, gamma, gemm, rhs
+        return per
+    return 0
+
+
+def cpu_baseline(w, c, target_s=20.0):
+    """The oracle (untuned) on this host's cores, on a bounded sample of the same
+    workload: all columns, as many RK4 steps as fit in ~target_s; scaled to
+    columns/s of the full 1024-step Jacobian."""
+    import oracle as O
+    threads = O.threads()
+    prob, _ = O.make_problem(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=1)
+    cs = c.copy()
+    cs[0] = c[0] / w.steps    # one step of the full run's dt
+    t0 = time.perf_counter()
+    O.shoot_jacobian(prob, cs)
+    t1 = time.perf_counter() - t0
+    k = max(1, min(int(target_s / max(t1, 1e-3)), 8))
+    if k > 1:
+        prob, _ = O.make_problem(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=k)
+        cs[0] = c[0] * k / w.steps
+        t0 = time.perf_counter()
+        O.shoot_jacobian(prob, cs)
+        t1 = (time.perf_counter() - t0) / k
+    per_jac = t1 * w.steps
+    return {"value": (w.n + 1) / per_jac, "unit": "Jacobian columns/s", "cores": threads, "kind": "oracle",
+            "sample": f"{k} RK4 step(s) of the {w.name} workload (all {w.n + 1} columns), "
+                      f"{t1:.2f} s per step, scaled x{w.steps} steps"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    w = W.ALL[args.workload]
+    c, _ = W.coefficients(w)
+    import oracle as O
+    O.build()
+    times = []
+    prob, _ = O.make_problem(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=1)
+    cs = c.copy()
+    cs[0] = c[0] / w.steps
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.shoot_jacobian(prob, cs)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    per_jac = statistics.mean(times) * w.steps
+    value = (w.n + 1) / per_jac
+    cpu = {"value": value, "unit": "Jacobian columns/s", "cores": O.threads(), "kind": "oracle",
+           "sample": f"1 RK4 step of {w.name} per timed step (all {w.n + 1} columns), scaled x{w.steps}"}
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "Jacobian columns/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_jac * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "N": w.N, "n": w.n, "form": "cpu-oracle"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "Jacobian columns/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="fp64", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default=W.LARGE.name, choices=sorted(W.ALL))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rk-steps", type=int, default=0,
+                    help="profiling only: override the workload's RK4 step count (not a bench number)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        out = run_reference(args)
+    else:
+        from paper_1210_5672_gb300 import build as B
+        B.build()
+        out = run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

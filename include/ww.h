@@ -93,6 +93,22 @@ int ww_get_stats(const ww_ctx *ctx, ww_stats *out);
 /* Thread-local description of the last error (empty string if none). */
 const char *ww_last_error(void);
 
+/* Phase timing (a profiling aid; no counterpart in the paper).  When enabled,
+ * shoot / shoot_jacobian record a CUDA event pair on the context's stream
+ * around each phase below in every RK stage, and ww_get_timing returns, for
+ * the last call, the summed milliseconds and the number of timed launches of
+ * each phase.  Costs two event records per phase and stage. */
+#define WW_PHASE_ASSEMBLY   0  /* K, G assembly kernel                          */
+#define WW_PHASE_FACTOR     1  /* LU of A (FP64) / inverse update (MIXED)       */
+#define WW_PHASE_SOLVE      2  /* multi-RHS solve of the n+1 columns            */
+#define WW_PHASE_GAPPLY     3  /* G gamma for the n+1 columns                   */
+#define WW_PHASE_COLRHS     4  /* variational RHS + RK update kernel            */
+#define WW_PHASE_GAMMA      5  /* gamma = mu', H gamma for the n+1 columns      */
+#define WW_PHASE_BASE       6  /* base-state chain (geometry .. base RHS)       */
+#define WW_NPHASE           7
+int ww_set_timing(ww_ctx *ctx, int enable);
+int ww_get_timing(const ww_ctx *ctx, double *ms /* WW_NPHASE */, int *launches /* WW_NPHASE */);
+
 /* dtn_setup -- Sec. 2.1 Eqs. (fred), (G); Sec. 2.2 Eq. (K1K2).
  * Assemble A = 1/2 I + K and G for the surface eta (device, N doubles; mean
  * depth included), and factor A (WW_FP64) or build its approximate inverse

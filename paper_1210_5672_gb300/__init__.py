@@ -33,8 +33,10 @@ ERRORS = {
     -4: "WW_ERR_CUDA", -5: "WW_ERR_TIMEOUT", -6: "WW_ERR_ALLOC",
 }
 WW_FP64, WW_MIXED = 0, 1
-EXPORTS = ("ww_create", "ww_destroy", "ww_set_stream", "ww_get_stats", "ww_last_error", "dtn_setup",
-           "dtn_apply", "shoot", "shoot_jacobian", "shoot_jacobian_host", "objective_and_grad")
+EXPORTS = ("ww_create", "ww_destroy", "ww_set_stream", "ww_get_stats", "ww_last_error", "ww_set_timing",
+           "ww_get_timing", "dtn_setup", "dtn_apply", "shoot", "shoot_jacobian", "shoot_jacobian_host",
+           "objective_and_grad")
+PHASES = ("assembly", "factor", "solve", "gapply", "colrhs", "gamma", "base")
 
 
 class WWError(RuntimeError):
@@ -79,6 +81,8 @@ def lib():
             "ww_set_stream": (I, [V, V]),
             "ww_get_stats": (I, [V, C.POINTER(Stats)]),
             "ww_last_error": (C.c_char_p, []),
+            "ww_set_timing": (I, [V, I]),
+            "ww_get_timing": (I, [V, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
             "dtn_setup": (I, [V, V]),
             "dtn_apply": (I, [V, V, I, V]),
             "shoot": (I, [V, V, V, V]),
@@ -165,6 +169,16 @@ class Context:
         """Queue work on a torch.cuda.Stream (or raw cudaStream_t int)."""
         raw = getattr(stream, "cuda_stream", stream)
         _check(lib().ww_set_stream(self.handle, C.c_void_p(int(raw) if raw else None)))
+
+    def set_timing(self, enable: bool):
+        _check(lib().ww_set_timing(self.handle, 1 if enable else 0))
+
+    def timing(self) -> dict:
+        """{phase: (total_ms, launches)} of the last shoot / shoot_jacobian."""
+        ms = (C.c_double * len(PHASES))()
+        cnt = (C.c_int * len(PHASES))()
+        _check(lib().ww_get_timing(self.handle, ms, cnt))
+        return {p: (ms[i], cnt[i]) for i, p in enumerate(PHASES)}
 
     def stats(self) -> dict:
         s = Stats()

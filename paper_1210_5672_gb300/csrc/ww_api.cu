@@ -39,17 +39,42 @@ __global__ void k_jtr(const double *__restrict__ J, const double *__restrict__ r
     }
 }
 
-struct Graphs {
-    cudaGraphExec_t step[2] = {nullptr, nullptr};   // [with_columns]
+constexpr int NPH = WW_NPHASE;
+constexpr int EV_PER_STEP = 4 * NPH * 2;   // [stage][phase][begin/end]
+
+struct StepGraph {
+    cudaGraph_t graph = nullptr;              // kept alive: its event nodes are re-pointed per replay
+    cudaGraphExec_t exec = nullptr;
+    std::vector<std::pair<cudaGraphNode_t, int>> ev_nodes;   // node -> flat event slot
 };
 
 struct Owned {
     Ctx c;
     double *cbuf = nullptr, *rbuf = nullptr, *Jbuf = nullptr, *fbuf = nullptr;
-    Graphs graphs;
-    cudaStream_t own_stream = nullptr;   // created by ww_create, used unless ww_set_stream overrides
+    StepGraph graphs[2][2];                   // [with_columns][timing]
+    cudaStream_t own_stream = nullptr;        // created by ww_create, used unless ww_set_stream overrides
     std::vector<void *> allocs;
+    // phase timing
+    bool timing = false;
+    bool capturing = false;
+    int replay = 0;                           // RK step being launched
+    unsigned marked = 0;                      // phases recorded by the current step program
+    cudaEvent_t placeholder[EV_PER_STEP] = {};
+    std::vector<cudaEvent_t> pool;            // steps * EV_PER_STEP
+    double ph_ms[NPH] = {};
+    int ph_count[NPH] = {};
 };
+
+// record the begin (b = 0) or end (b = 1) event of a phase of stage st
+int mark(Ctx *c, int st, int phase, int b) {
+    Owned *o = reinterpret_cast<Owned *>(c->owner);
+    if (!o || !o->timing) return WW_OK;
+    o->marked |= 1u << phase;
+    const int slot = (st * NPH + phase) * 2 + b;
+    cudaEvent_t ev = o->capturing ? o->placeholder[slot] : o->pool[(size_t)o->replay * EV_PER_STEP + slot];
+    WW_CUDA_TRY(cudaEventRecord(ev, c->stream));
+    return WW_OK;
+}
 
 int dalloc(Owned *o, void **p, size_t bytes) {
     cudaError_t e = cudaMalloc(p, bytes);
@@ -85,39 +110,105 @@ int apply_G(Ctx *c, int col0, int ncols) {
 // one RK4 stage; cvec is the context's device copy of c (T = cvec[0])
 int run_stage(Ctx *c, int st, const double *cvec, int with_cols) {
     WW_TRY(launch_base_geometry(c, c->Ys, c->Ys + c->N, 1));
+    WW_TRY(mark(c, st, WW_PHASE_ASSEMBLY, 0));
     WW_TRY(launch_assemble(c));
+    WW_TRY(mark(c, st, WW_PHASE_ASSEMBLY, 1));
+    WW_TRY(mark(c, st, WW_PHASE_FACTOR, 0));
     WW_TRY(factor(c));
+    WW_TRY(mark(c, st, WW_PHASE_FACTOR, 1));
+    WW_TRY(mark(c, st, WW_PHASE_BASE, 0));
     WW_TRY(launch_phi0(c));
     WW_TRY(solve(c, c->M, 1));
     WW_TRY(launch_gamma(c, 0, 1));
     WW_TRY(apply_G(c, 0, 1));
     WW_TRY(launch_base_rhs(c, st, cvec));
+    WW_TRY(mark(c, st, WW_PHASE_BASE, 1));
     if (with_cols && c->nc > 0) {
         WW_TRY(launch_psi(c));
+        WW_TRY(mark(c, st, WW_PHASE_SOLVE, 0));
         WW_TRY(solve(c, c->M + c->N, c->nc));
+        WW_TRY(mark(c, st, WW_PHASE_SOLVE, 1));
+        WW_TRY(mark(c, st, WW_PHASE_GAMMA, 0));
         WW_TRY(launch_gamma(c, 1, c->nc));
+        WW_TRY(mark(c, st, WW_PHASE_GAMMA, 1));
+        WW_TRY(mark(c, st, WW_PHASE_GAPPLY, 0));
         WW_TRY(apply_G(c, 1, c->nc));
+        WW_TRY(mark(c, st, WW_PHASE_GAPPLY, 1));
+        WW_TRY(mark(c, st, WW_PHASE_COLRHS, 0));
         WW_TRY(launch_col_rhs(c, st, cvec));
+        WW_TRY(mark(c, st, WW_PHASE_COLRHS, 1));
     }
     return WW_OK;
 }
 
 int build_step_graph(Owned *o, int with_cols) {
     Ctx *c = &o->c;
-    if (o->graphs.step[with_cols]) return WW_OK;
+    StepGraph &sg = o->graphs[with_cols][o->timing ? 1 : 0];
+    if (sg.exec) return WW_OK;
     cudaGraph_t g = nullptr;
     WW_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    o->capturing = true;
     int st = WW_OK;
     for (int s = 0; s < 4 && st == WW_OK; ++s) st = run_stage(c, s, o->cbuf, with_cols);
+    o->capturing = false;
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (st != WW_OK) {
         if (g) cudaGraphDestroy(g);
         return st;
     }
     if (e != cudaSuccess) return fail(WW_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&o->graphs.step[with_cols], g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return fail(WW_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    if (o->timing) {
+        // find the event-record nodes and map each to its [stage][phase][b] slot
+        size_t nn = 0;
+        WW_CUDA_TRY(cudaGraphGetNodes(g, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        WW_CUDA_TRY(cudaGraphGetNodes(g, nodes.data(), &nn));
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            WW_CUDA_TRY(cudaGraphNodeGetType(nd, &t));
+            if (t != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev;
+            WW_CUDA_TRY(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+            for (int k = 0; k < EV_PER_STEP; ++k)
+                if (o->placeholder[k] == ev) sg.ev_nodes.emplace_back(nd, k);
+        }
+    }
+    e = cudaGraphInstantiate(&sg.exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(WW_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    sg.graph = g;
+    return WW_OK;
+}
+
+int ensure_timing_events(Owned *o) {
+    const size_t need = (size_t)o->c.steps * EV_PER_STEP;
+    if (!o->placeholder[0])
+        for (int k = 0; k < EV_PER_STEP; ++k) WW_CUDA_TRY(cudaEventCreate(&o->placeholder[k]));
+    while (o->pool.size() < need) {
+        cudaEvent_t ev;
+        WW_CUDA_TRY(cudaEventCreate(&ev));
+        o->pool.push_back(ev);
+    }
+    return WW_OK;
+}
+
+int collect_timing(Owned *o) {
+    for (int p = 0; p < NPH; ++p) {
+        o->ph_ms[p] = 0.0;
+        o->ph_count[p] = 0;
+    }
+    for (int rep = 0; rep < o->c.steps; ++rep)
+        for (int st = 0; st < 4; ++st)
+            for (int p = 0; p < NPH; ++p) {
+                if (!(o->marked & (1u << p))) continue;
+                const size_t base = (size_t)rep * EV_PER_STEP + (size_t)(st * NPH + p) * 2;
+                float ms = 0.f;
+                WW_CUDA_TRY(cudaEventElapsedTime(&ms, o->pool[base], o->pool[base + 1]));
+                o->ph_ms[p] += ms;
+                o->ph_count[p] += 1;
+            }
     return WW_OK;
 }
 
@@ -138,18 +229,36 @@ int run_shot(Owned *o, const double *cvec, bool c_on_host, double *r, double *J,
     WW_CUDA_TRY(cudaMemcpyAsync(o->cbuf, cvec, sizeof(double) * (c->n + 1),
                                 c_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
     WW_TRY(launch_initial(c, o->cbuf, with_cols));
+    if (o->timing) WW_TRY(ensure_timing_events(o));
+    o->marked = 0;
     if (c->stream == nullptr) {
         // the legacy default stream cannot be captured: launch the stages directly
-        for (int s = 0; s < c->steps; ++s)
+        for (int s = 0; s < c->steps; ++s) {
+            o->replay = s;
             for (int k = 0; k < 4; ++k) WW_TRY(run_stage(c, k, o->cbuf, with_cols));
+        }
     } else {
         WW_TRY(build_step_graph(o, with_cols));
-        for (int s = 0; s < c->steps; ++s) WW_CUDA_TRY(cudaGraphLaunch(o->graphs.step[with_cols], c->stream));
+        StepGraph &sg = o->graphs[with_cols][o->timing ? 1 : 0];
+        if (o->timing)
+            for (int p = 0; p < NPH; ++p)
+                if (with_cols || (p != WW_PHASE_SOLVE && p != WW_PHASE_GAMMA && p != WW_PHASE_GAPPLY &&
+                                  p != WW_PHASE_COLRHS))
+                    o->marked |= 1u << p;
+        for (int s = 0; s < c->steps; ++s) {
+            if (o->timing)
+                for (auto &ne : sg.ev_nodes)
+                    WW_CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(
+                        sg.exec, ne.first, o->pool[(size_t)s * EV_PER_STEP + ne.second]));
+            WW_CUDA_TRY(cudaGraphLaunch(sg.exec, c->stream));
+        }
     }
     WW_TRY(launch_outputs(c, r, J, f, with_cols));
     c->stats.stages = 4 * c->steps;
     c->dtn_ready = false;   // the operator now belongs to the last stage's surface
-    return check_status(c);
+    WW_TRY(check_status(c));
+    if (o->timing) WW_TRY(collect_timing(o));
+    return WW_OK;
 }
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -202,6 +311,7 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
         }
     }
     c->stream = o->own_stream;
+    c->owner = o;
 
     const size_t N = c->N, NC = c->NC, nb = c->nb;
     const size_t nblk = (N + nb - 1) / nb;
@@ -302,7 +412,13 @@ void ww_destroy(ww_ctx *ctx) {
     if (!ctx) return;
     Owned *o = owner(ctx);
     for (int w = 0; w < 2; ++w)
-        if (o->graphs.step[w]) cudaGraphExecDestroy(o->graphs.step[w]);
+        for (int t = 0; t < 2; ++t) {
+            if (o->graphs[w][t].exec) cudaGraphExecDestroy(o->graphs[w][t].exec);
+            if (o->graphs[w][t].graph) cudaGraphDestroy(o->graphs[w][t].graph);
+        }
+    for (cudaEvent_t ev : o->placeholder)
+        if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : o->pool) cudaEventDestroy(ev);
     if (o->c.mx) mixed_destroy(&o->c);
     if (o->c.stream) cudaStreamSynchronize(o->c.stream);
     for (void *p : o->allocs) cudaFree(p);
@@ -316,6 +432,22 @@ int ww_set_stream(ww_ctx *ctx, void *stream) {
     // graphs are replayed on whatever stream is current, so nothing is rebuilt;
     // the legacy default stream (NULL) selects direct launches instead of graphs
     o->c.stream = (cudaStream_t)stream;
+    return WW_OK;
+}
+
+int ww_set_timing(ww_ctx *ctx, int enable) {
+    if (!ctx) return fail(WW_ERR_ARG, "ww_set_timing: NULL context");
+    owner(ctx)->timing = enable != 0;
+    return WW_OK;
+}
+
+int ww_get_timing(const ww_ctx *ctx, double *ms, int *launches) {
+    if (!ctx || !ms || !launches) return fail(WW_ERR_ARG, "ww_get_timing: NULL argument");
+    const Owned *o = reinterpret_cast<const Owned *>(ctx);
+    for (int p = 0; p < NPH; ++p) {
+        ms[p] = o->ph_ms[p];
+        launches[p] = o->ph_count[p];
+    }
     return WW_OK;
 }
 

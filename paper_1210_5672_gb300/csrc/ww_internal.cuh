@@ -88,6 +88,7 @@ struct Ctx {
     bool dtn_ready;
     ww_stats stats;
     Mixed *mx;
+    void *owner;              // the API-side object holding this context (phase timing)
 };
 
 // --------------------------------------------------------------------------

@@ -1,10 +1,14 @@
 """Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
 
 Tolerance: 1e-11 relative in the FP64 form, measured as ||d r||/||r||,
-|d f|/|f| and, per Jacobian column, ||d J_k||/||J_k|| (max over k).  The two
-sides use different summation orders, FFTs, cotangent formulas and solvers
-(no pivoting on the GPU, partial pivoting in the oracle), so agreement is at
-the roundoff floor of the method, not bitwise.
+|d f|/|f| and, per Jacobian column, ||d J_k|| / max(||J_k||, 1e-4 max_j ||J_j||)
+(max over k).  The two sides use different summation orders, FFTs, cotangent
+formulas and solvers (no pivoting on the GPU, partial pivoting in the
+oracle), so agreement is at the roundoff floor of the method, not bitwise.
+The column floor 1e-4 max_j ||J_j|| covers columns that are small through
+cancellation (the d/dT column of a near-linear wave is 1e-5 of the others);
+their roundoff is set by the size of the terms that cancel: perturbing c by
+one ulp moves that column of the ORACLE itself by 2e-11 of its norm.
 """
 import math
 
@@ -44,7 +48,18 @@ def rel(a, b):
 
 
 def col_rel(J, J0):
-    return max(rel(J[:, k], J0[:, k]) for k in range(J0.shape[1]))
+    norms = np.linalg.norm(J0, axis=0)
+    floor = 1e-4 * norms.max()
+    return max(np.linalg.norm(J[:, k] - J0[:, k]) / max(norms[k], floor) for k in range(J0.shape[1]))
+
+
+def stable_T(N, steps, g=1.0, tau=0.0, h=1.0, cfl=1.2):
+    """A period T whose RK4 step dt = T / (4 steps) keeps omega_max dt = cfl, with
+    omega_max^2 = (g k + tau k^3) tanh(k h) at k = N/2 (RK4 is stable to 2.83):
+    parity is compared on the same discrete map, so T is just a parameter."""
+    k = N / 2
+    wmax = math.sqrt((g * k + tau * k**3) * (1.0 if math.isinf(h) else math.tanh(k * h)))
+    return 4 * steps * cfl / wmax
 
 
 def gpu_jacobian(ww, w, c, precision=0, basis=None, **kw):
@@ -131,6 +146,7 @@ def test_small_workload_jacobian(ww):
 def test_jacobian_matches_oracle(ww, N, n, steps, h, tau, amp):
     w = W.Workload("t", N=N, n=n, steps=steps, h=h, tau=tau, amp=amp)
     c, _ = W.coefficients(w)
+    c[0] = min(c[0], stable_T(N, steps, tau=tau, h=h))
     r, J, f, _ = gpu_jacobian(ww, w, c)
     prob, _ = O.make_problem(N, n, g=w.g, tau=tau, h=h, steps=steps)
     r0, J0, f0 = O.shoot_jacobian(prob, c)
@@ -206,10 +222,11 @@ def test_geometry_failure_in_shot_reports_status(ww):
 @pytest.mark.slow
 def test_large_workload_one_step_sampled(ww):
     """Full-size shape (N = 2048, 512 modes + T) in the benchmark's launch
-    configuration for ONE RK4 step (the oracle cannot run 1024 steps); every
-    column compared, plus r and f."""
+    configuration for ONE RK4 step of the full run's dt (T scaled by 1/1024;
+    the oracle cannot run 1024 steps); every column compared, plus r and f."""
     w = W.shrink(W.LARGE, steps=1)
-    c, _ = W.coefficients(w)
+    c, _ = W.coefficients(W.LARGE)
+    c[0] /= W.LARGE.steps
     r, J, f, _ = gpu_jacobian(ww, w, c)
     prob, _ = O.make_problem(w.N, w.n, h=w.h, steps=1)
     r0, J0, f0 = O.shoot_jacobian(prob, c)
