@@ -71,8 +71,12 @@ int mark(Ctx *c, int st, int phase, int b) {
     if (!o || !o->timing) return WW_OK;
     o->marked |= 1u << phase;
     const int slot = (st * NPH + phase) * 2 + b;
-    cudaEvent_t ev = o->capturing ? o->placeholder[slot] : o->pool[(size_t)o->replay * EV_PER_STEP + slot];
-    WW_CUDA_TRY(cudaEventRecord(ev, c->stream));
+    if (o->capturing) {
+        // an "external" record becomes an event-record node of the captured graph
+        WW_CUDA_TRY(cudaEventRecordWithFlags(o->placeholder[slot], c->stream, cudaEventRecordExternal));
+    } else {
+        WW_CUDA_TRY(cudaEventRecord(o->pool[(size_t)o->replay * EV_PER_STEP + slot], c->stream));
+    }
     return WW_OK;
 }
 
@@ -171,6 +175,10 @@ int build_step_graph(Owned *o, int with_cols) {
             WW_CUDA_TRY(cudaGraphEventRecordNodeGetEvent(nd, &ev));
             for (int k = 0; k < EV_PER_STEP; ++k)
                 if (o->placeholder[k] == ev) sg.ev_nodes.emplace_back(nd, k);
+        }
+        if (sg.ev_nodes.empty()) {
+            cudaGraphDestroy(g);
+            return fail(WW_ERR_CUDA, "phase timing: no event-record nodes in the captured step");
         }
     }
     e = cudaGraphInstantiate(&sg.exec, g, 0);
