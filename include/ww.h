@@ -147,6 +147,17 @@ int shoot_jacobian_host(ww_ctx *ctx, const double *c, double *r, double *J, doub
  * it equals the discrete adjoint's result up to roundoff). */
 int objective_and_grad(ww_ctx *ctx, const double *c, double *f, double *grad);
 
+/* Self-tests of the tensor-core products of WW_MIXED (diagnostics; no
+ * counterpart in the paper).  C = A B for column-major FP64 device arrays A
+ * (M x K, ld M) and B (K x Nn, ld K), K a multiple of 64, through
+ *   ww_selftest_f32gemm: the FP32-accurate product of 3 + 3 bf16 slices,
+ *   ww_selftest_ozaki:   the FP64-accurate product of 7 + 7 exact bf16 digits;
+ * *max_rel = max|C - C_ref| / max|C_ref| with C_ref the library's FP64 DGEMM.
+ * They allocate their own scratch, use the legacy default stream and
+ * synchronise the device; WW_ERR_TIMEOUT if a bounded device wait expired. */
+int ww_selftest_f32gemm(const double *A, const double *B, int M, int Nn, int K, double *max_rel);
+int ww_selftest_ozaki(const double *A, const double *B, int M, int Nn, int K, double *max_rel);
+
 #ifdef __cplusplus
 }
 #endif

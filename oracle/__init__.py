@@ -36,15 +36,18 @@ _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile ww_oracle.c into oracle/_build/libww_oracle.so (gcc -O2 -fopenmp)."""
+def build(force: bool = False, plant: int = 0) -> str:
+    """Compile ww_oracle.c into oracle/_build/libww_oracle.so (gcc -O2 -fopenmp).
+    plant > 0 builds a deliberately wrong variant (tests of the pins only)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+    lib_path = _LIB if plant == 0 else os.path.join(_BUILD, f"libww_oracle_plant{plant}.so")
+    if force or not os.path.exists(lib_path) or os.path.getmtime(lib_path) < os.path.getmtime(_SRC):
+        tmp = lib_path + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", f"-DORC_PLANT={int(plant)}", _SRC,
+               "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 class Problem(C.Structure):
@@ -57,36 +60,45 @@ class Problem(C.Structure):
 _D = C.POINTER(C.c_double)
 
 
+def load(path: str):
+    """ctypes handle of a compiled oracle with the signatures set."""
+    L = C.CDLL(path)
+    _set_signatures(L)
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
-            P = C.POINTER(Problem)
-            sig = {
-                "orc_fft": (None, [C.c_int, _D, C.c_int]),
-                "orc_spectral": (None, [C.c_int, C.c_int, _D, _D]),
-                "orc_assemble": (None, [C.c_int, C.c_double, _D, _D, _D, _D, _D]),
-                "orc_dtn_matrices": (None, [C.c_int, C.c_double, _D, _D, _D]),
-                "orc_dtn": (None, [C.c_int, C.c_double, _D, _D, C.c_int, _D]),
-                "orc_lu": (C.c_int, [C.c_int, _D, C.POINTER(C.c_int)]),
-                "orc_lu_solve": (None, [C.c_int, _D, C.POINTER(C.c_int), _D, _D]),
-                "orc_rhs": (None, [P, C.c_double, _D, C.c_int, C.c_int, _D]),
-                "orc_initial": (None, [P, _D, _D]),
-                "orc_evolve": (None, [P, C.c_double, _D, _D]),
-                "orc_evolve_columns": (None, [P, C.c_double, _D, _D, C.c_int, C.c_int, _D]),
-                "orc_shoot": (None, [P, _D, _D, _D]),
-                "orc_shoot_jacobian": (None, [P, _D, _D, _D, _D]),
-                "orc_energy": (C.c_double, [P, _D]),
-                "orc_threads": (C.c_int, []),
-                "orc_set_threads": (None, [C.c_int]),
-            }
-            for name, (res, args) in sig.items():
-                f = getattr(L, name)
-                f.restype = res
-                f.argtypes = args
-            _lib = L
+            _lib = load(build())
     return _lib
+
+
+def _set_signatures(L):
+    P = C.POINTER(Problem)
+    sig = {
+        "orc_fft": (None, [C.c_int, _D, C.c_int]),
+        "orc_spectral": (None, [C.c_int, C.c_int, _D, _D]),
+        "orc_assemble": (None, [C.c_int, C.c_double, _D, _D, _D, _D, _D]),
+        "orc_dtn_matrices": (None, [C.c_int, C.c_double, _D, _D, _D]),
+        "orc_dtn": (None, [C.c_int, C.c_double, _D, _D, C.c_int, _D]),
+        "orc_lu": (C.c_int, [C.c_int, _D, C.POINTER(C.c_int)]),
+        "orc_lu_solve": (None, [C.c_int, _D, C.POINTER(C.c_int), _D, _D]),
+        "orc_rhs": (None, [P, C.c_double, _D, C.c_int, C.c_int, _D]),
+        "orc_initial": (None, [P, _D, _D]),
+        "orc_evolve": (None, [P, C.c_double, _D, _D]),
+        "orc_evolve_columns": (None, [P, C.c_double, _D, _D, C.c_int, C.c_int, _D]),
+        "orc_shoot": (None, [P, _D, _D, _D]),
+        "orc_shoot_jacobian": (None, [P, _D, _D, _D, _D]),
+        "orc_energy": (C.c_double, [P, _D]),
+        "orc_threads": (C.c_int, []),
+        "orc_set_threads": (None, [C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
 
 
 def _p(a: np.ndarray):

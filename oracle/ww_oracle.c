@@ -41,6 +41,14 @@
  *  R6 the linearisation is the continuum one of App. B with the shared
  *     discrete DtN operator (K and G are not differentiated).
  */
+/* ORC_PLANT (tests only, default 0) compiles a deliberately wrong variant so
+ * that the pin tests can show they catch it: 1 = image kernels with the
+ * printed "+" sign, 2 = zeta'(alpha) in K1 instead of zeta'(beta), 3 = gravity
+ * term dropped from phi_t, 4 = u psi' term dropped from the variational RHS. */
+#ifndef ORC_PLANT
+#define ORC_PLANT 0
+#endif
+
 #include <complex.h>
 #include <math.h>
 #include <stdlib.h>
@@ -180,13 +188,14 @@ void orc_assemble(int N, double h, const double *eta, const double *eta_x,
             } else {
                 cplx c = ccot((zi - zj) / 2.0);
                 cplx c0 = ccot((cplx)((ai - aj) / 2.0));
-                k1 = cimag(dzj / 2.0 * c - 0.5 * c0);
+                k1 = cimag((ORC_PLANT == 2 ? dzi : dzj) / 2.0 * c - 0.5 * c0);
                 g1 = creal(dzi / 2.0 * c - 0.5 * c0);
             }
             if (!deep) {                        /* mirror image, reading R1 */
                 cplx cb = ccot((zi - conj(zj)) / 2.0);
-                k2 = -cimag(conj(dzj) / 2.0 * cb);
-                g2 = -creal(dzi / 2.0 * cb);
+                double sgn = ORC_PLANT == 1 ? -1.0 : 1.0;
+                k2 = -sgn * cimag(conj(dzj) / 2.0 * cb);
+                g2 = -sgn * creal(dzi / 2.0 * cb);
             }
             A[(size_t)i * N + j] = (k1 + k2) / N + (i == j ? 0.5 : 0.0);
             G[(size_t)i * N + j] = (g1 + g2) / N;
@@ -364,7 +373,7 @@ void orc_rhs(const orc_problem *p, double T, const double *y, int ncol, int t_co
     orc_spectral(N, MUL_DERIV, tmp, tmp);
     for (int i = 0; i < N; ++i)
         F[N + i] = vy[i] * Gphi[i] - 0.5 * ux[i] * ux[i] - 0.5 * vy[i] * vy[i]
-                   - p->g * eta[i] + p->tau * tmp[i];
+                   - (ORC_PLANT == 3 ? 0.0 : p->g) * eta[i] + p->tau * tmp[i];
     orc_spectral(N, MUL_PROJECT, F + N, F + N);
     orc_spectral(N, MUL_FILTER, F, F);
     orc_spectral(N, MUL_FILTER, F + N, F + N);
@@ -394,7 +403,8 @@ void orc_rhs(const orc_problem *p, double T, const double *y, int ncol, int t_co
         for (int i = 0; i < N; ++i) e1[i] *= w3[i];
         orc_spectral(N, MUL_DERIV, e1, e1);
         for (int i = 0; i < N; ++i)
-            op[i] = -b[i] - ux[i] * dpsi[i] + vy[i] * Gpsi[i] - p->g * ed[i] + p->tau * e1[i];
+            op[i] = -b[i] - (ORC_PLANT == 4 ? 0.0 : ux[i]) * dpsi[i] + vy[i] * Gpsi[i] - p->g * ed[i]
+                    + p->tau * e1[i];
         orc_spectral(N, MUL_PROJECT, op, op);
         orc_spectral(N, MUL_FILTER, oe, oe);
         orc_spectral(N, MUL_FILTER, op, op);

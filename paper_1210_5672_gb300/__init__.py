@@ -35,7 +35,7 @@ ERRORS = {
 WW_FP64, WW_MIXED = 0, 1
 EXPORTS = ("ww_create", "ww_destroy", "ww_set_stream", "ww_get_stats", "ww_last_error", "ww_set_timing",
            "ww_get_timing", "dtn_setup", "dtn_apply", "shoot", "shoot_jacobian", "shoot_jacobian_host",
-           "objective_and_grad")
+           "objective_and_grad", "ww_selftest_f32gemm", "ww_selftest_ozaki")
 PHASES = ("assembly", "factor", "solve", "gapply", "colrhs", "gamma", "base")
 
 
@@ -89,6 +89,8 @@ def lib():
             "shoot_jacobian": (I, [V, V, V, V, V]),
             "shoot_jacobian_host": (I, [V, V, V, V, V]),
             "objective_and_grad": (I, [V, V, V, V]),
+            "ww_selftest_f32gemm": (I, [V, V, I, I, I, C.POINTER(D)]),
+            "ww_selftest_ozaki": (I, [V, V, I, I, I, C.POINTER(D)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -230,6 +232,20 @@ def shoot_jacobian_host(ctx: Context, c: np.ndarray, r: np.ndarray, J: np.ndarra
 def objective_and_grad(ctx: Context, c, f, grad):
     _check(lib().objective_and_grad(ctx.handle, _dptr(c, ctx.n + 1, "c"), _dptr(f, 1, "f"),
                                     _dptr(grad, ctx.n + 1, "grad")))
+
+
+def selftest(kind: str, A, B) -> float:
+    """max relative error of the tensor-core product A @ B (A: M x K, B: K x Nn CUDA
+    float64 tensors) against the library's FP64 DGEMM; kind 'f32gemm' or 'ozaki'."""
+    M, K = A.shape
+    K2, Nn = B.shape
+    assert K == K2
+    At = A.t().contiguous()   # column-major storage
+    Bt = B.t().contiguous()
+    out = C.c_double(-1.0)
+    fn = lib().ww_selftest_f32gemm if kind == "f32gemm" else lib().ww_selftest_ozaki
+    _check(fn(_dptr(At, M * K, "A"), _dptr(Bt, K * Nn, "B"), M, Nn, K, C.byref(out)))
+    return out.value
 
 
 def _autograd_fn():

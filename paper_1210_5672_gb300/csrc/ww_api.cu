@@ -22,6 +22,32 @@ int fail(int code, const std::string &msg) {
     return code;
 }
 
+// twiddles tw[2k], tw[2k+1] = cos, -sin(2 pi k/N) (k < N/2); cs = cos(2 pi m/N),
+// sin(2 pi m/N), cot(pi m/N) (m < N; cot slot 0 unused), exact at multiples of pi/2
+void fill_tables(int N, double *tw, double *cs) {
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int k = 0; k < N / 2; ++k) {
+        tw[2 * k] = std::cos(two_pi * (double)k / (double)N);
+        tw[2 * k + 1] = -std::sin(two_pi * (double)k / (double)N);
+    }
+    for (int m = 0; m < N; ++m) {
+        cs[m] = std::cos(two_pi * (double)m / (double)N);
+        cs[N + m] = std::sin(two_pi * (double)m / (double)N);
+        cs[2 * N + m] = m == 0 ? 0.0 : 1.0 / std::tan(0.5 * two_pi * (double)m / (double)N);
+    }
+    for (int m = 0; m < N; m += N / 4) {
+        int q = m / (N / 4);
+        cs[m] = (q == 0) ? 1.0 : (q == 2 ? -1.0 : 0.0);
+        cs[N + m] = (q == 1) ? 1.0 : (q == 3 ? -1.0 : 0.0);
+        if (q == 2) cs[2 * N + m] = 0.0;
+    }
+    for (int k = 0; k < N / 2; k += N / 4) {
+        int q = k / (N / 4);
+        tw[2 * k] = q == 0 ? 1.0 : 0.0;
+        tw[2 * k + 1] = q == 0 ? 0.0 : -1.0;
+    }
+}
+
 namespace {
 
 __global__ void k_jtr(const double *__restrict__ J, const double *__restrict__ r, int N, double *grad) {
@@ -94,8 +120,8 @@ int dalloc_n(Owned *o, T **p, size_t n) {
 
 Owned *owner(ww_ctx *ctx) { return reinterpret_cast<Owned *>(ctx); }
 
-int factor(Ctx *c) {
-    if (c->precision == WW_MIXED) return mixed_setup(c);
+int factor(Ctx *c, int fresh = 0) {
+    if (c->precision == WW_MIXED) return mixed_setup(c, fresh);
     return lu_factor_fp64(c);
 }
 
@@ -224,6 +250,14 @@ int check_status(Ctx *c) {
     int st = 0;
     WW_CUDA_TRY(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     WW_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (c->precision == WW_MIXED) {
+        double ratio = 0;
+        int err = 0;
+        WW_TRY(mixed_read_stats(c, &ratio, &err));
+        c->stats.refine_resid_max = ratio;
+        c->stats.refine_iters_max = c->max_refine;
+        if (err) return fail(WW_ERR_TIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)");
+    }
     if (st & ST_GEOMETRY)
         return fail(WW_ERR_GEOMETRY, "surface touches the bottom (finite depth needs eta > 0) or is non-finite");
     if (st & ST_NONFINITE) return fail(WW_ERR_GEOMETRY, "non-finite value in a right-hand side or factor");
@@ -237,6 +271,12 @@ int run_shot(Owned *o, const double *cvec, bool c_on_host, double *r, double *J,
     WW_CUDA_TRY(cudaMemcpyAsync(o->cbuf, cvec, sizeof(double) * (c->n + 1),
                                 c_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
     WW_TRY(launch_initial(c, o->cbuf, with_cols));
+    if (c->precision == WW_MIXED) {
+        // approximate inverse for the initial surface, before the step program
+        WW_TRY(launch_base_geometry(c, c->Ys, c->Ys + c->N, 1));
+        WW_TRY(launch_assemble(c));
+        WW_TRY(factor(c, 1));
+    }
     if (o->timing) WW_TRY(ensure_timing_events(o));
     o->marked = 0;
     if (c->stream == nullptr) {
@@ -292,6 +332,8 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
     if (!(p->h > 0.0)) return fail(WW_ERR_ARG, "ww_create: h must be > 0 (INFINITY for deep water)");
     if (p->precision != WW_FP64 && p->precision != WW_MIXED)
         return fail(WW_ERR_ARG, "ww_create: precision must be WW_FP64 or WW_MIXED");
+    if (p->precision == WW_MIXED && p->N < 64)
+        return fail(WW_ERR_ARG, "ww_create: WW_MIXED needs N >= 64 (64-wide tensor-core K tiles)");
 
     Owned *o = new Owned();
     Ctx *c = &o->c;
@@ -360,30 +402,9 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
         ww_destroy(reinterpret_cast<ww_ctx *>(o));
         return st;
     }
-    // tables (host double precision): twiddles, cos/sin of 2 pi m/N, cot(pi m/N)
     std::vector<double> tw(N), cs(3 * N);
+    fill_tables(c->N, tw.data(), cs.data());
     const double two_pi = 6.283185307179586476925286766559;
-    for (size_t k = 0; k < N / 2; ++k) {
-        tw[2 * k] = std::cos(two_pi * (double)k / (double)N);
-        tw[2 * k + 1] = -std::sin(two_pi * (double)k / (double)N);
-    }
-    for (size_t m = 0; m < N; ++m) {
-        cs[m] = std::cos(two_pi * (double)m / (double)N);
-        cs[N + m] = std::sin(two_pi * (double)m / (double)N);
-        cs[2 * N + m] = m == 0 ? 0.0 : 1.0 / std::tan(0.5 * two_pi * (double)m / (double)N);
-    }
-    // exact values where the argument is a multiple of pi/2
-    for (size_t m = 0; m < N; m += N / 4) {
-        int q = (int)(m / (N / 4));
-        cs[m] = (q == 0) ? 1.0 : (q == 2 ? -1.0 : 0.0);
-        cs[N + m] = (q == 1) ? 1.0 : (q == 3 ? -1.0 : 0.0);
-        if (q == 2) cs[2 * N + m] = 0.0;
-    }
-    for (size_t k = 0; k < N / 2; k += N / 4) {
-        int q = (int)(k / (N / 4));
-        tw[2 * k] = q == 0 ? 1.0 : 0.0;
-        tw[2 * k + 1] = q == 0 ? 0.0 : -1.0;
-    }
     std::vector<double> basis(2 * N * (size_t)(p->n > 0 ? p->n : 1), 0.0);
     for (int k = 0; k < p->n; ++k)
         for (size_t r = 0; r < 2 * N; ++r)
@@ -472,7 +493,7 @@ int dtn_setup(ww_ctx *ctx, const double *eta) {
     WW_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     WW_TRY(launch_base_geometry(c, eta, nullptr, 0));
     WW_TRY(launch_assemble(c));
-    WW_TRY(factor(c));
+    WW_TRY(factor(c, 1));
     WW_TRY(check_status(c));
     c->dtn_ready = true;
     return WW_OK;

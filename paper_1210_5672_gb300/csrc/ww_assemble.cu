@@ -105,9 +105,92 @@ __global__ void __launch_bounds__(ASM_TI) k_assemble(const double *__restrict__ 
     }
 }
 
+// Symmetric form: cot is odd, so the (j, i) entry follows from the (i, j) one:
+//   cot((-x - iy)/2) = -cot((x + iy)/2),  cot((-x + iy')/2) = -conj(cot((x + iy')/2)),
+// and cot((alpha_j - alpha_i)/2) = -cot((alpha_i - alpha_j)/2).  Each block
+// takes a pair of 32 x 32 tiles (I, J), I < J, evaluates the two cotangents
+// of every unordered pair once and writes both tiles (the transposed one
+// through shared memory, so both stores are coalesced); diagonal tiles are
+// evaluated entry by entry.
+constexpr int ST = 32;
+
+__global__ void __launch_bounds__(256) k_assemble_sym(const double *__restrict__ eta, const double *__restrict__ eta_x,
+                                                      const double *__restrict__ eta_xx, const double *__restrict__ E,
+                                                      const double *__restrict__ Einv,
+                                                      const double *__restrict__ cs, const double *__restrict__ cot0,
+                                                      int N, int deep, double *A, double *G) {
+    __shared__ double tA[ST][ST + 1], tG[ST][ST + 1];
+    // triangular tile index -> (I, J), I <= J
+    const int T = N / ST;
+    int b = blockIdx.x, I = 0;
+    while (b >= T - I) {
+        b -= T - I;
+        ++I;
+    }
+    const int J = I + b;
+    const double invN = 1.0 / N;
+    const int il = threadIdx.x & 31;
+    const int i = I * ST + il;
+    const double ei = eta[i], exi = eta_x[i], Ei = E[i], Eii = Einv[i];
+    for (int jl = threadIdx.x >> 5; jl < ST; jl += 8) {
+        const int j = J * ST + jl;
+        const double ej = eta[j], exj = eta_x[j], Ej = E[j], Eij = Einv[j];
+        double kij, gij, kji, gji;
+        if (i == j) {
+            const double d = 0.5 / fma(exi, exi, 1.0);
+            kij = kji = -eta_xx[i] * d;
+            gij = gji = exi * eta_xx[i] * d;
+        } else {
+            int m = i - j;
+            if (m < 0) m += N;
+            const double cx = cs[m], sx = cs[N + m];
+            const double y = ei - ej;
+            const double ey = Ei * Eij, eyi = Eii * Ej;
+            const double2 ct = cot_half(cx, sx, 0.5 * (ey + eyi), sinh_diff(y, ey, eyi));
+            const double c0 = cot0[m];
+            kij = 0.5 * fma(exj, ct.x, ct.y);
+            gij = 0.5 * (fma(-exi, ct.y, ct.x) - c0);
+            kji = -0.5 * fma(exi, ct.x, ct.y);
+            gji = -0.5 * (fma(-exj, ct.y, ct.x) - c0);
+        }
+        if (!deep) {
+            int m = i - j;
+            if (m < 0) m += N;
+            const double cx = cs[m], sx = cs[N + m];
+            const double ep = Ei * Ej, epi = Eii * Eij;
+            const double2 ct = cot_half(cx, sx, 0.5 * (ep + epi), 0.5 * (ep - epi));
+            kij += -0.5 * fma(-exj, ct.x, ct.y);
+            gij += -0.5 * fma(-exi, ct.y, ct.x);
+            kji += -0.5 * fma(exi, ct.x, ct.y);
+            gji += 0.5 * fma(exj, ct.y, ct.x);
+        }
+        const size_t idx = (size_t)j * N + i;
+        A[idx] = kij * invN + (i == j ? 0.5 : 0.0);
+        G[idx] = gij * invN;
+        tA[jl][il] = kji * invN + (i == j ? 0.5 : 0.0);
+        tG[jl][il] = gji * invN;
+    }
+    if (I == J) return;   // the diagonal tile is complete (uniform branch: no barrier skipped unevenly)
+    __syncthreads();
+    // transposed tile: entry (j, i) at A[i * N + j]; consecutive threads walk j
+    for (int il2 = threadIdx.x >> 5; il2 < ST; il2 += 8) {
+        const int jl2 = threadIdx.x & 31;
+        const size_t idx = (size_t)(I * ST + il2) * N + J * ST + jl2;
+        A[idx] = tA[jl2][il2];
+        G[idx] = tG[jl2][il2];
+    }
+}
+
 }  // namespace
 
 int launch_assemble(Ctx *c) {
+    if (c->N % ST == 0) {
+        const int T = c->N / ST;
+        k_assemble_sym<<<T * (T + 1) / 2, 256, 0, c->stream>>>(c->eta, c->eta_x, c->eta_xx, c->E, c->Einv, c->cs,
+                                                              c->cs + 2 * c->N, c->N, c->deep ? 1 : 0, c->A, c->G);
+        WW_CUDA_TRY(cudaGetLastError());
+        return WW_OK;
+    }
     dim3 grid((c->N + ASM_TI - 1) / ASM_TI, (c->N + ASM_TJ - 1) / ASM_TJ);
     k_assemble<<<grid, ASM_TI, 0, c->stream>>>(c->eta, c->eta_x, c->eta_xx, c->E, c->Einv, c->cs, c->cs + 2 * c->N,
                                                c->N, c->deep ? 1 : 0, c->A, c->G);

@@ -17,6 +17,7 @@ namespace ww {
 // --------------------------------------------------------------------------
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
+void fill_tables(int N, double *tw /* N */, double *cs /* 3N */);
 
 #define WW_CUDA_TRY(expr)                                                        \
     do {                                                                         \
@@ -175,7 +176,8 @@ int lu_solve_fp64(Ctx *c, double *B, int ncols);     // B <- A^{-1} B using the 
 // mixed precision (ww_mixed.cu)
 int mixed_create(Ctx *c);
 void mixed_destroy(Ctx *c);
-int mixed_setup(Ctx *c);                             // after assembly: update the inverse
+int mixed_setup(Ctx *c, int fresh);                  // after assembly: update the inverse
+int mixed_read_stats(Ctx *c, double *ratio, int *err);
 int mixed_solve(Ctx *c, double *B, int ncols);       // B <- A^{-1} B (refined)
 int mixed_apply_G(Ctx *c, int col0, int ncols);      // Gout += G Gam (FP64-accurate)
 

@@ -1,0 +1,391 @@
+// ww_ozaki.cu -- FP64-accurate products on the bf16 tensor cores by exact
+// splitting (the Ozaki scheme: Ozaki, Ogita, Oishi & Rump, Numer. Algorithms
+// 2012; its tensor-core form: Ootomo, Ozaki & Yokota, IJHPCA 2024), used for
+// the refinement residuals R = Psi - A M and for the G apply of the DtN
+// (Sec. 3.3 computes its refinement residuals in quad precision for the same
+// reason: the correction solves may be inexact, the residual may not).
+//
+// Splitting.  Row i of the left operand gets a power-of-two scale 2^ea_i >
+// max_k |a_ik|, column j of the right operand 2^fb_j.  Each entry is written as
+//   a_ik = 2^ea_i sum_{p=1..7} a_p 2^{-6-7(p-1)},   a_p integers in [-64, 64]
+// (round-to-nearest digits computed exactly in 64-bit fixed point; 48 bits
+// kept, remainder < 2^-49 of the row maximum).  The digits are exact in bf16.
+//
+// Products.  a_p b_q has weight 2^{E - 7g}, g = p + q - 2, E = ea_i + fb_j - 12.
+// All pairs with g <= 6 (28 of 49) are accumulated per group g in TMEM (fp32);
+// |digit products| <= 2^12, so a group over a 1024-long K block stays below
+// 2^24 for g <= 2 and the tensor cores sum it exactly; groups g >= 3 carry
+// weights <= 2^-21 and their fp32 rounding (if any) is below 2^-45 of the
+// result.  After each K block the 7 groups are converted to integers and
+// folded exactly into two int64 accumulators per entry,
+//   hi = V0 2^14 + V1 2^7 + V2,  lo = V3 2^21 + V4 2^14 + V5 2^7 + V6,
+// and the result is 2^ea_i 2^fb_j (2^-26 hi + 2^-54 lo).
+//
+// Kernel.  One CTA per 128 x 64 output tile.  Warp 0: TMA producer (ring of 4
+// A-digit tiles of 128 x 64 and ring of 2 B stages holding all 7 B-digit
+// tiles of 64 x 64); warp 1: TMEM owner and tcgen05.mma issuer (M = 128,
+// N = 64, K = 16); warps 2..9: fold and epilogue, each thread one row and 32
+// columns.  All waits are bounded.
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <string>
+#include <vector>
+
+#include "ww_internal.cuh"
+#include "ww_tc.cuh"
+
+namespace ww {
+
+int tc_make_map(CUtensorMap *map, const void *ptr, int K, long rows, int box_rows);   // ww_tcgemm.cu
+
+namespace {
+
+constexpr int OZ_S = 7;             // digits per operand
+constexpr int OZ_G = 7;             // groups g = 0..6
+constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 64;
+constexpr int OZ_KBLOCK = 16;       // K chunks (of 64) per exact block = 1024
+constexpr int OZ_ASLOTS = 4, OZ_BSLOTS = 2;
+constexpr int OZ_EPI_WARPS = 8;
+constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
+constexpr int OZ_A_TILE = OZ_BM * OZ_BK * 2;           // 16 KB
+constexpr int OZ_B_TILE = OZ_BN * OZ_BK * 2;           // 8 KB
+constexpr int OZ_B_STAGE = OZ_S * OZ_B_TILE;           // 56 KB
+constexpr int OZ_SMEM = OZ_ASLOTS * OZ_A_TILE + OZ_BSLOTS * OZ_B_STAGE + 1024 + 256;
+
+struct OzOut {
+    int mode;                 // 0: C += value; 1: C = Psi - 0.5 Mh - value (residual)
+    double *C;
+    int ldc;
+    const double *Psi;
+    int ldpsi;
+    const double *Mh;
+    int ldm;
+    unsigned long long *colmax;   // mode 1: per-column max |R| (bits of a positive double), or NULL
+};
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int Nn, int K,
+            const double *__restrict__ sa, const double *__restrict__ sb, OzOut out, int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t base = tc::smem_u32(smem_raw);
+    uint8_t *smem = smem_raw + ((1024 - (base & 1023)) & 1023);
+    uint8_t *aring = smem;
+    uint8_t *bring = smem + OZ_ASLOTS * OZ_A_TILE;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(bring + OZ_BSLOTS * OZ_B_STAGE);
+    uint64_t *a_full = bar, *a_empty = bar + OZ_ASLOTS;
+    uint64_t *b_full = a_empty + OZ_ASLOTS, *b_empty = b_full + OZ_BSLOTS;
+    uint64_t *acc_full = b_empty + OZ_BSLOTS, *acc_empty = acc_full + 1;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(acc_empty + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * OZ_BM, n0 = blockIdx.y * OZ_BN;
+    const int nk = K / OZ_BK;
+    const int nblk = (nk + OZ_KBLOCK - 1) / OZ_KBLOCK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < OZ_ASLOTS; ++s) {
+            tc::mbar_init(&a_full[s], 1);
+            tc::mbar_init(&a_empty[s], 1);
+        }
+        for (int s = 0; s < OZ_BSLOTS; ++s) {
+            tc::mbar_init(&b_full[s], 1);
+            tc::mbar_init(&b_empty[s], 1);
+        }
+        tc::mbar_init(acc_full, 1);
+        tc::mbar_init(acc_empty, OZ_EPI_WARPS);
+        tc::mbar_fence_init();
+        tc::prefetch_tmap(&tmA);
+        tc::prefetch_tmap(&tmB);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tslot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------ TMA producer
+        for (int kc = 0; kc < nk; ++kc) {
+            const int bs = kc % OZ_BSLOTS;
+            tc::mbar_wait(&b_empty[bs], ((kc / OZ_BSLOTS) & 1) ^ 1, err);
+            tc::mbar_arrive_expect_tx(&b_full[bs], OZ_B_STAGE);
+            for (int q = 0; q < OZ_S; ++q)
+                tc::tma_load_2d(&tmB, &b_full[bs], bring + bs * OZ_B_STAGE + q * OZ_B_TILE, kc * OZ_BK, q * Nn + n0);
+            for (int p = 0; p < OZ_S; ++p) {
+                const int ai = kc * OZ_S + p, as = ai % OZ_ASLOTS;
+                tc::mbar_wait(&a_empty[as], ((ai / OZ_ASLOTS) & 1) ^ 1, err);
+                tc::mbar_arrive_expect_tx(&a_full[as], OZ_A_TILE);
+                tc::tma_load_2d(&tmA, &a_full[as], aring + as * OZ_A_TILE, kc * OZ_BK, p * M + m0);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------ MMA issuer
+        constexpr uint32_t idesc = tc::idesc_bf16(OZ_BM, OZ_BN);
+        for (int kc = 0; kc < nk; ++kc) {
+            const int kb = kc / OZ_KBLOCK;
+            const bool first = (kc % OZ_KBLOCK) == 0;
+            if (first && kb > 0) {
+                tc::mbar_wait(acc_empty, (kb - 1) & 1, err);   // epilogue drained the last block
+                tc::fence_after();
+            }
+            const int bs = kc % OZ_BSLOTS;
+            tc::mbar_wait(&b_full[bs], (kc / OZ_BSLOTS) & 1, err);
+            tc::fence_after();
+            const uint32_t bst = tc::smem_u32(bring + bs * OZ_B_STAGE);
+            for (int p = 0; p < OZ_S; ++p) {
+                const int ai = kc * OZ_S + p, as = ai % OZ_ASLOTS;
+                tc::mbar_wait(&a_full[as], (ai / OZ_ASLOTS) & 1, err);
+                tc::fence_after();
+                const uint32_t ast = tc::smem_u32(aring + as * OZ_A_TILE);
+                for (int q = 0; q + p < OZ_G; ++q) {
+                    const uint32_t d = tmem + (uint32_t)((p + q) * OZ_BN);
+#pragma unroll
+                    for (int kk = 0; kk < OZ_BK / 16; ++kk)
+                        tc::mma_bf16(d, tc::desc_k128(ast + kk * 32), tc::desc_k128(bst + q * OZ_B_TILE + kk * 32),
+                                     idesc, !(first && p == 0 && kk == 0));
+                }
+                tc::mma_commit(&a_empty[as]);
+            }
+            tc::mma_commit(&b_empty[bs]);
+            if ((kc % OZ_KBLOCK) == OZ_KBLOCK - 1 || kc == nk - 1) tc::mma_commit(acc_full);
+        }
+    } else if (warp >= 2) {
+        // ------------------------------------------------ fold + epilogue
+        const int ew = warp - 2;
+        const int quarter = warp & 3;            // TMEM lane quarter this warp may access
+        const int chalf = ew >> 2;               // columns 32*chalf .. +31
+        const int row = m0 + quarter * 32 + lane;
+        long long hi[32], lo[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0;
+        for (int kb = 0; kb < nblk; ++kb) {
+            tc::mbar_wait(acc_full, kb & 1, err);
+            tc::fence_after();
+#pragma unroll 1
+            for (int g = 0; g < OZ_G; ++g) {
+                float v[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(g * OZ_BN + chalf * 32), v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const long long iv = (long long)__float2int_rn(v[j]);
+                    if (g < 3)
+                        hi[j] += iv * (1LL << (7 * (2 - g)));
+                    else
+                        lo[j] += iv * (1LL << (7 * (6 - g)));
+                }
+            }
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(acc_empty);
+        }
+        if (row < M) {
+            const double si = sa[row];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int col = n0 + chalf * 32 + j;
+                if (col < Nn) {
+                    const double val = si * sb[col] * fma((double)hi[j], 0x1p-26, (double)lo[j] * 0x1p-54);
+                    const size_t ic = (size_t)col * out.ldc + row;
+                    if (out.mode == 0) {
+                        out.C[ic] += val;
+                    } else {
+                        const double r = (out.Psi[(size_t)col * out.ldpsi + row] -
+                                          0.5 * out.Mh[(size_t)col * out.ldm + row]) - val;
+                        out.C[ic] = r;
+                        if (out.colmax)
+                            atomicMax(&out.colmax[col], (unsigned long long)__double_as_longlong(fabs(r)));
+                    }
+                }
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tmem, 512);
+}
+
+// ---------------------------------------------------------------- digits
+__device__ __forceinline__ int bexp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+
+// biased-exponent maxima of the rows of a column-major matrix (one thread per
+// row and 64-column strip; emax zeroed by the caller)
+__global__ void k_expmax_rows(const double *__restrict__ X, int ld, int rows, int cols, float diag_shift,
+                              int *emax) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c0 = blockIdx.y * 64;
+    if (r >= rows) return;
+    int m = 0;
+    for (int c = c0; c < min(cols, c0 + 64); ++c) {
+        double x = X[(size_t)c * ld + r];
+        if (diag_shift != 0.f && r == c) x -= (double)diag_shift;
+        m = max(m, bexp(x));
+    }
+    atomicMax(&emax[r], m);
+}
+
+// biased-exponent maxima of the columns (one block per column)
+__global__ void k_expmax_cols(const double *__restrict__ X, int ld, int rows, int *emax) {
+    __shared__ int red[32];
+    const double *col = X + (size_t)blockIdx.x * ld;
+    int m = 0;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) m = max(m, bexp(col[r]));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) emax[blockIdx.x] = m;
+    }
+}
+
+// scale 2^ea from the biased exponent maximum: 2^(emax - 1022) > max |x|
+__global__ void k_scales(const int *__restrict__ emax, int n, double *scale) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int e = emax[i];
+    scale[i] = e == 0 ? 1.0 : ldexp(1.0, e - 1022);
+}
+
+// 7 digits of every entry.  side 0 (left operand, rows of a column-major
+// M x K matrix): dst[p][i][k]; side 1 (right operand, columns of a K x Nn
+// column-major matrix): dst[q][j][k].  Digits are computed in 64-bit fixed
+// point: F = x 2^-ea 2^60, a_p = round(F / 2^{54 - 7(p-1)}).
+__global__ void k_digits(const double *__restrict__ X, int ld, int rows, int K, int side, float diag_shift,
+                         const int *__restrict__ emax, __nv_bfloat16 *dst) {
+    __shared__ long long tile[32][33];
+    const int t0 = blockIdx.y * 32, k0 = blockIdx.x * 32;   // t: row (side 0) or column (side 1)
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int yy = ty; yy < 32; yy += 8) {
+        int t, k;
+        double x;
+        if (side == 0) {   // read coalesced along the rows of the column-major source
+            t = t0 + tx;
+            k = k0 + yy;
+            x = (t < rows && k < K) ? X[(size_t)k * ld + t] : 0.0;
+        } else {
+            t = t0 + yy;
+            k = k0 + tx;
+            x = (t < rows && k < K) ? X[(size_t)t * ld + k] : 0.0;
+        }
+        if (diag_shift != 0.f && t == k) x -= (double)diag_shift;
+        long long F = 0;
+        if (t < rows && k < K) {
+            const long long bits = __double_as_longlong(x);
+            const int e = (int)((bits >> 52) & 0x7FF);
+            if (e != 0) {
+                const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+                const int sh = e - emax[t] + 7;
+                F = sh >= 0 ? (mant << sh) : (sh > -63 ? (mant >> -sh) : 0);
+                if (bits < 0) F = -F;
+            }
+        }
+        if (side == 0)
+            tile[yy][tx] = F;   // tile[k][t]
+        else
+            tile[tx][yy] = F;
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int t = t0 + yy, k = k0 + tx;
+        if (t >= rows || k >= K) continue;
+        long long F = tile[tx][yy];
+#pragma unroll
+        for (int p = 0; p < OZ_S; ++p) {
+            const int sh = 54 - 7 * p;
+            const long long a = (F + (1LL << (sh - 1))) >> sh;   // arithmetic shift: round to nearest
+            F -= a * (1LL << sh);
+            dst[((size_t)p * rows + t) * K + k] = __int2bfloat16_rn((int)a);
+        }
+    }
+}
+
+}  // namespace
+
+// Digits and scales of an operand.  side 0: left operand = the rows of the
+// column-major rows x K matrix X (minus diag_shift on its diagonal);
+// side 1: right operand = the columns of the column-major K x rows matrix X.
+// emax: int[rows] work (zeroed here); scale: double[rows]; dst: 7 x rows x K bf16.
+int ozaki_digits(cudaStream_t s, const double *X, int ld, int rows, int K, int side, float diag_shift, int *emax,
+                 double *scale, __nv_bfloat16 *dst) {
+    if (side == 0) {
+        WW_CUDA_TRY(cudaMemsetAsync(emax, 0, sizeof(int) * rows, s));
+        dim3 g((rows + 127) / 128, (K + 63) / 64);
+        k_expmax_rows<<<g, 128, 0, s>>>(X, ld, rows, K, diag_shift, emax);
+    } else {
+        k_expmax_cols<<<rows, 256, 0, s>>>(X, ld, K, emax);
+    }
+    k_scales<<<(rows + 255) / 256, 256, 0, s>>>(emax, rows, scale);
+    dim3 gd((K + 31) / 32, (rows + 31) / 32);
+    k_digits<<<gd, 256, 0, s>>>(X, ld, rows, K, side, diag_shift, emax, dst);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+// mode 0: C += A B ; mode 1: C = Psi - 0.5 Mh - A B  (A = left digits, B = right digits)
+int ozaki_gemm(cudaStream_t s, const __nv_bfloat16 *Ad, const double *sa, const __nv_bfloat16 *Bd, const double *sb,
+               int M, int Nn, int K, int mode, double *C, int ldc, const double *Psi, int ldpsi, const double *Mh,
+               int ldm, unsigned long long *colmax, int *err) {
+    if (K % OZ_BK != 0) return fail(WW_ERR_ARG, "ozaki_gemm: K must be a multiple of 64");
+    CUtensorMap ta, tb;
+    WW_TRY(tc_make_map(&ta, Ad, K, (long)OZ_S * M, OZ_BM));
+    WW_TRY(tc_make_map(&tb, Bd, K, (long)OZ_S * Nn, OZ_BN));
+    WW_CUDA_TRY(cudaFuncSetAttribute(k_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+    OzOut o{mode, C, ldc, Psi, ldpsi, Mh, ldm, colmax};
+    dim3 grid((M + OZ_BM - 1) / OZ_BM, (Nn + OZ_BN - 1) / OZ_BN);
+    k_ozaki<<<grid, OZ_THREADS, OZ_SMEM, s>>>(ta, tb, M, Nn, K, sa, sb, o, err);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+}  // namespace ww
+
+// -------------------------------------------------------------------------
+// self-test (declared in ww.h): C = A B (A: M x K, B: K x Nn, column-major
+// FP64 device arrays) through the digit path; *max_rel = max |C - C_fp64| /
+// max |C_fp64| against the library's FP64 DGEMM.
+// -------------------------------------------------------------------------
+extern "C" int ww_selftest_ozaki(const double *A, const double *B, int M, int Nn, int K, double *max_rel) {
+    using namespace ww;
+    cudaStream_t s = nullptr;
+    __nv_bfloat16 *Ad = nullptr, *Bd = nullptr;
+    double *C = nullptr, *C0 = nullptr, *sa = nullptr, *sb = nullptr;
+    int *ea = nullptr, *eb = nullptr, *err = nullptr;
+    int st = WW_OK;
+    if (cudaMalloc(&Ad, 2 * (7 * (size_t)M + 256) * K) != cudaSuccess ||
+        cudaMalloc(&Bd, 2 * (7 * (size_t)Nn + 256) * K) != cudaSuccess ||
+        cudaMalloc(&C, 8 * (size_t)M * Nn) != cudaSuccess || cudaMalloc(&C0, 8 * (size_t)M * Nn) != cudaSuccess ||
+        cudaMalloc(&sa, 8 * (size_t)M) != cudaSuccess || cudaMalloc(&sb, 8 * (size_t)Nn) != cudaSuccess ||
+        cudaMalloc(&ea, 4 * (size_t)M) != cudaSuccess || cudaMalloc(&eb, 4 * (size_t)Nn) != cudaSuccess ||
+        cudaMalloc(&err, 4) != cudaSuccess)
+        st = fail(WW_ERR_ALLOC, "selftest alloc");
+    if (st == WW_OK && (cudaMemset(err, 0, 4) != cudaSuccess || cudaMemset(C, 0, 8 * (size_t)M * Nn) != cudaSuccess))
+        st = WW_ERR_CUDA;
+    if (st == WW_OK) st = ozaki_digits(s, A, M, M, K, 0, 0.f, ea, sa, Ad);
+    if (st == WW_OK) st = ozaki_digits(s, B, K, Nn, K, 1, 0.f, eb, sb, Bd);
+    if (st == WW_OK)
+        st = ozaki_gemm(s, Ad, sa, Bd, sb, M, Nn, K, 0, C, M, nullptr, 0, nullptr, 0, nullptr, err);
+    if (st == WW_OK) st = dgemm(s, M, Nn, K, 1.0, A, M, B, K, 0.0, C0, M);
+    if (st == WW_OK && cudaDeviceSynchronize() != cudaSuccess) st = fail(WW_ERR_CUDA, "selftest sync");
+    if (st == WW_OK) {
+        std::vector<double> h((size_t)M * Nn), h0((size_t)M * Nn);
+        cudaMemcpy(h.data(), C, 8 * h.size(), cudaMemcpyDeviceToHost);
+        cudaMemcpy(h0.data(), C0, 8 * h.size(), cudaMemcpyDeviceToHost);
+        int e = 0;
+        cudaMemcpy(&e, err, 4, cudaMemcpyDeviceToHost);
+        double mx = 0, md = 0;
+        for (size_t i = 0; i < h.size(); ++i) {
+            mx = fmax(mx, fabs(h0[i]));
+            md = fmax(md, fabs(h[i] - h0[i]));
+        }
+        *max_rel = md / (mx > 0 ? mx : 1);
+        if (e) st = fail(WW_ERR_TIMEOUT, "ozaki GEMM wait timed out");
+    }
+    cudaFree(Ad); cudaFree(Bd); cudaFree(C); cudaFree(C0); cudaFree(sa); cudaFree(sb);
+    cudaFree(ea); cudaFree(eb); cudaFree(err);
+    return st;
+}

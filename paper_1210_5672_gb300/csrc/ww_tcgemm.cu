@@ -1,0 +1,324 @@
+// ww_tcgemm.cu -- tensor-core GEMM on sliced operands (tcgen05 + TMA + TMEM).
+//
+//   C (+)= alpha * sum_{(p,q) in pairs} A_p * B_q^T
+//
+// A_p (M x K) and B_q (Nn x K) are bf16 "slices" stored K-contiguous, stacked
+// slice after slice ([S][rows][K]).  Writing an FP32 (or FP64) operand as a
+// sum of bf16 slices and keeping the products whose combined significance is
+// large gives an FP32-accurate (or better) product on the bf16 tensor cores,
+// whose rate on GB300 is ~1.9 PFLOP/s against 70 TFLOP/s for FP32 FMA and
+// 1 TFLOP/s for FP64.
+//
+// One CTA computes a 128 x BN tile.  Warp 0 issues TMA loads of all slices of
+// a 64-wide K chunk into a 2-stage ring; warp 1 owns the TMEM accumulator and
+// issues tcgen05.mma (M = 128, N = BN, K = 16) for every pair; warps 2..5 read
+// the accumulator with tcgen05.ld and write C.  Every mbarrier wait is
+// bounded (~1 s); a timeout sets *err and the block still exits.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "ww_internal.cuh"
+#include "ww_tc.cuh"
+
+namespace ww {
+
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;
+constexpr int TC_STAGES = 2;
+constexpr int TC_THREADS = 192;
+
+struct Pairs {
+    int n;
+    unsigned char p[16], q[16];
+};
+
+template <int BN, int SA, int SB>
+struct TcSmem {
+    static constexpr int A_TILE = TC_BM * TC_BK * 2;   // bytes
+    static constexpr int B_TILE = BN * TC_BK * 2;
+    static constexpr int STAGE = SA * A_TILE + SB * B_TILE;
+    static constexpr int BYTES = TC_STAGES * STAGE + 1024 /* align */ + 256 /* barriers */;
+};
+
+template <int BN, int SA, int SB>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int Nn, int K,
+              Pairs pairs, int out_mode, float *Cf, double *Cd, int ldc, double alpha, int *err) {
+    using L = TcSmem<BN, SA, SB>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t base = tc::smem_u32(smem_raw);
+    uint8_t *smem = smem_raw + ((1024 - (base & 1023)) & 1023);
+    uint8_t *tiles = smem;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + TC_STAGES * L::STAGE);
+    uint64_t *empty = full + TC_STAGES;
+    uint64_t *done = empty + TC_STAGES;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
+    const int nk = K / TC_BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(done, 1);
+        tc::mbar_fence_init();
+        tc::prefetch_tmap(&tmA);
+        tc::prefetch_tmap(&tmB);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tslot, BN);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc % TC_STAGES;
+            const uint32_t ph = (kc / TC_STAGES) & 1;
+            tc::mbar_wait(&empty[s], ph ^ 1, err);
+            tc::mbar_arrive_expect_tx(&full[s], L::STAGE);
+            uint8_t *st = tiles + s * L::STAGE;
+#pragma unroll
+            for (int a = 0; a < SA; ++a) tc::tma_load_2d(&tmA, &full[s], st + a * L::A_TILE, kc * TC_BK, a * M + m0);
+#pragma unroll
+            for (int b = 0; b < SB; ++b)
+                tc::tma_load_2d(&tmB, &full[s], st + SA * L::A_TILE + b * L::B_TILE, kc * TC_BK, b * Nn + n0);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        constexpr uint32_t idesc = tc::idesc_bf16(TC_BM, BN);
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc % TC_STAGES;
+            const uint32_t ph = (kc / TC_STAGES) & 1;
+            tc::mbar_wait(&full[s], ph, err);
+            tc::fence_after();
+            const uint32_t st = tc::smem_u32(tiles + s * L::STAGE);
+            for (int pi = 0; pi < pairs.n; ++pi) {
+                const uint32_t a0 = st + pairs.p[pi] * L::A_TILE;
+                const uint32_t b0 = st + SA * L::A_TILE + pairs.q[pi] * L::B_TILE;
+#pragma unroll
+                for (int kk = 0; kk < TC_BK / 16; ++kk)
+                    tc::mma_bf16(tmem, tc::desc_k128(a0 + kk * 32), tc::desc_k128(b0 + kk * 32), idesc,
+                                 (kc | pi | kk) != 0);
+            }
+            tc::mma_commit(&empty[s]);   // frees this stage once its MMAs have read it
+        }
+        tc::mma_commit(done);
+    } else if (warp >= 2) {
+        // ---------------- epilogue: TMEM -> registers -> C (column-major)
+        const int quarter = warp & 3;   // TMEM lanes 32*quarter .. +31
+        const int row = m0 + quarter * 32 + lane;
+        tc::mbar_wait(done, 0, err);
+        tc::fence_after();
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            float v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + c0, v);
+            if (row < M) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = n0 + c0 + j;
+                    if (col < Nn) {
+                        const size_t idx = (size_t)col * ldc + row;
+                        if (out_mode == 0)
+                            Cf[idx] = (float)(alpha * (double)v[j]);
+                        else if (out_mode == 1)
+                            Cd[idx] = alpha * (double)v[j];
+                        else
+                            Cd[idx] += alpha * (double)v[j];
+                    }
+                }
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tmem, BN);
+}
+
+// ---------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+int get_encoder() {
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!g_encode) return fail(WW_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    return WW_OK;
+}
+
+}  // namespace
+
+// 2-D bf16 tensor [rows][K] (K contiguous), tile box {64, box_rows}, 128-byte swizzle
+int tc_make_map(CUtensorMap *map, const void *ptr, int K, long rows, int box_rows) {
+    WW_TRY(get_encoder());
+    // the caller's buffer holds at least box_rows rows; rows past the logical
+    // end only feed output rows / columns that the epilogue discards
+    if (rows < box_rows) rows = box_rows;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(WW_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return WW_OK;
+}
+
+namespace {
+
+template <int BN, int SA, int SB>
+int launch_tc(cudaStream_t s, const void *A, const void *B, int M, int Nn, int K, const Pairs &pairs, int out_mode,
+              float *Cf, double *Cd, int ldc, double alpha, int *err) {
+    using L = TcSmem<BN, SA, SB>;
+    static_assert(L::BYTES <= 227 * 1024, "shared memory");
+    CUtensorMap ta, tb;
+    WW_TRY(tc_make_map(&ta, A, K, (long)SA * M, TC_BM));
+    WW_TRY(tc_make_map(&tb, B, K, (long)SB * Nn, BN));
+    auto kern = k_tc_gemm<BN, SA, SB>;
+    WW_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES));
+    dim3 grid((M + TC_BM - 1) / TC_BM, (Nn + BN - 1) / BN);
+    kern<<<grid, TC_THREADS, L::BYTES, s>>>(ta, tb, M, Nn, K, pairs, out_mode, Cf, Cd, ldc, alpha, err);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+// ---------------------------------------------------------------- slicing
+// dst[s][r][k] (bf16, K contiguous) from a column-major source:
+//   trans = 1: value(r, k) = src[r + k*ld]   (A side: rows of the source)
+//   trans = 0: value(r, k) = src[k + r*ld]   (B side: columns of the source)
+// optionally v -> shift*delta(r,k) - v.  S bf16 slices, v = sum_s slice_s + O(2^-8S |v|).
+template <typename T>
+__global__ void k_slice(const T *__restrict__ src, int ld, int rows, int K, int trans, float shift, int S,
+                        __nv_bfloat16 *dst) {
+    __shared__ float tile[32][33];
+    const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+    for (int yy = ty; yy < 32; yy += 8) {
+        float v;
+        if (trans) {
+            // read coalesced along r (column-major source), tile[k][r]
+            const int r = r0 + tx, k = k0 + yy;
+            v = (r < rows && k < K) ? (float)src[(size_t)k * ld + r] : 0.f;
+            if (shift != 0.f) v = (r == k ? shift : 0.f) - v;
+            tile[yy][tx] = v;
+        } else {
+            const int k = k0 + tx, r = r0 + yy;
+            v = (r < rows && k < K) ? (float)src[(size_t)r * ld + k] : 0.f;
+            if (shift != 0.f) v = (r == k ? shift : 0.f) - v;
+            tile[tx][yy] = v;
+        }
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int r = r0 + yy, k = k0 + tx;
+        if (r >= rows || k >= K) continue;
+        float v = tile[tx][yy];
+        for (int s = 0; s < S; ++s) {
+            __nv_bfloat16 b = __float2bfloat16_rn(v);
+            dst[((size_t)s * rows + r) * K + k] = b;
+            v -= __bfloat162float(b);
+        }
+    }
+}
+
+}  // namespace
+
+int tc_slice_f32(cudaStream_t s, const float *src, int ld, int rows, int K, int trans, float shift, int S,
+                 __nv_bfloat16 *dst) {
+    dim3 grid((K + 31) / 32, (rows + 31) / 32);
+    k_slice<float><<<grid, 256, 0, s>>>(src, ld, rows, K, trans, shift, S, dst);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+int tc_slice_f64(cudaStream_t s, const double *src, int ld, int rows, int K, int trans, float shift, int S,
+                 __nv_bfloat16 *dst) {
+    dim3 grid((K + 31) / 32, (rows + 31) / 32);
+    k_slice<double><<<grid, 256, 0, s>>>(src, ld, rows, K, trans, shift, S, dst);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+// FP32-accurate product from 3 + 3 slices (pairs with p + q <= 2, 0-based):
+// out_mode 0: Cf = alpha A B^T (fp32); 1: Cd = alpha A B^T; 2: Cd += alpha A B^T
+int tc_gemm_f32acc(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 *B3, int M, int Nn, int K,
+                   int out_mode, float *Cf, double *Cd, int ldc, double alpha, int *err) {
+    if (K % TC_BK != 0) return fail(WW_ERR_ARG, "tc_gemm: K must be a multiple of 64");
+    Pairs P{};
+    const int pp[6] = {2, 1, 0, 1, 0, 0}, qq[6] = {0, 1, 2, 0, 1, 0};   // smallest terms first
+    P.n = 6;
+    for (int i = 0; i < 6; ++i) {
+        P.p[i] = (unsigned char)pp[i];
+        P.q[i] = (unsigned char)qq[i];
+    }
+    return launch_tc<128, 3, 3>(s, A3, B3, M, Nn, K, P, out_mode, Cf, Cd, ldc, alpha, err);
+}
+
+}  // namespace ww
+
+// -------------------------------------------------------------------------
+// self-test (declared in ww.h): C = A B with A (M x K), B (K x Nn) column-major
+// FP64 device arrays through the 3x3-slice tensor-core path; returns the
+// max |C - C_fp64| / max |C_fp64| against the FP64 DGEMM of the library.
+// -------------------------------------------------------------------------
+extern "C" int ww_selftest_f32gemm(const double *A, const double *B, int M, int Nn, int K, double *max_rel) {
+    using namespace ww;
+    cudaStream_t s = nullptr;
+    __nv_bfloat16 *As = nullptr, *Bs = nullptr;
+    double *C = nullptr, *C0 = nullptr;
+    int *err = nullptr;
+    int st = WW_OK;
+    if (cudaMalloc(&As, sizeof(__nv_bfloat16) * (3 * (size_t)M + 256) * K) != cudaSuccess ||
+        cudaMalloc(&Bs, sizeof(__nv_bfloat16) * (3 * (size_t)Nn + 256) * K) != cudaSuccess ||
+        cudaMalloc(&C, sizeof(double) * (size_t)M * Nn) != cudaSuccess ||
+        cudaMalloc(&C0, sizeof(double) * (size_t)M * Nn) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess)
+        st = fail(WW_ERR_ALLOC, "selftest alloc");
+    if (st == WW_OK) st = (cudaMemset(err, 0, sizeof(int)) == cudaSuccess) ? WW_OK : WW_ERR_CUDA;
+    if (st == WW_OK) st = tc_slice_f64(s, A, M, M, K, 1, 0.f, 3, As);
+    if (st == WW_OK) st = tc_slice_f64(s, B, K, Nn, K, 0, 0.f, 3, Bs);
+    if (st == WW_OK) st = tc_gemm_f32acc(s, As, Bs, M, Nn, K, 1, nullptr, C, M, 1.0, err);
+    if (st == WW_OK) st = dgemm(s, M, Nn, K, 1.0, A, M, B, K, 0.0, C0, M);
+    if (st == WW_OK && cudaDeviceSynchronize() != cudaSuccess) st = fail(WW_ERR_CUDA, "selftest sync");
+    if (st == WW_OK) {
+        std::vector<double> h(M * (size_t)Nn), h0(M * (size_t)Nn);
+        cudaMemcpy(h.data(), C, sizeof(double) * h.size(), cudaMemcpyDeviceToHost);
+        cudaMemcpy(h0.data(), C0, sizeof(double) * h.size(), cudaMemcpyDeviceToHost);
+        int e = 0;
+        cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost);
+        double mx = 0, md = 0;
+        for (size_t i = 0; i < h.size(); ++i) {
+            mx = fmax(mx, fabs(h0[i]));
+            md = fmax(md, fabs(h[i] - h0[i]));
+        }
+        *max_rel = md / (mx > 0 ? mx : 1);
+        if (e) st = fail(WW_ERR_TIMEOUT, "tensor-core GEMM wait timed out");
+    }
+    cudaFree(As);
+    cudaFree(Bs);
+    cudaFree(C);
+    cudaFree(C0);
+    cudaFree(err);
+    return st;
+}

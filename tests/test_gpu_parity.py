@@ -232,3 +232,38 @@ def test_large_workload_one_step_sampled(ww):
     r0, J0, f0 = O.shoot_jacobian(prob, c)
     assert rel(r, r0) < TOL and abs(f - f0) / f0 < TOL
     assert col_rel(J, J0) < TOL
+
+
+# ------------------------------------------------------------------ mixed precision
+@pytest.mark.parametrize("N,n,steps,h,tau,amp", [
+    (64, 12, 64, 1.0, 0.0, 0.01),       # the small workload shape
+    (256, 70, 8, 1.0, 0.0, 0.2),        # several tiles, ragged tail
+    (128, 20, 16, math.inf, 0.1, 0.1),  # deep water with surface tension
+])
+def test_mixed_jacobian_matches_oracle(ww, N, n, steps, h, tau, amp):
+    """WW_MIXED: FP32-accurate tensor-core inverse + FP64-accurate digit
+    residuals and G products, refined to 1e-13; same 1e-11 bar as FP64."""
+    w = W.Workload("t", N=N, n=n, steps=steps, h=h, tau=tau, amp=amp)
+    c, _ = W.coefficients(w)
+    c[0] = min(c[0], stable_T(N, steps, tau=tau, h=h))
+    r, J, f, st = gpu_jacobian(ww, w, c, precision=1)
+    prob, _ = O.make_problem(N, n, g=w.g, tau=tau, h=h, steps=steps)
+    r0, J0, f0 = O.shoot_jacobian(prob, c)
+    assert st["refine_resid_max"] <= 1e-13
+    assert rel(r, r0) < TOL and abs(f - f0) / f0 < TOL
+    assert col_rel(J, J0) < TOL
+
+
+def test_mixed_dtn_apply_matches_oracle(ww):
+    N, nrhs, h = 512, 37, 1.0
+    rng = np.random.default_rng(5)
+    x = x_grid(N)
+    eta = h + sum(0.1 / k**2 * rng.uniform(-1, 1) * np.cos(k * x) for k in range(1, 9))
+    phi = np.stack([sum(rng.uniform(-1, 1) / k**2 * np.cos(k * x + rng.uniform(0, 6)) for k in range(1, 12))
+                    for _ in range(nrhs)])
+    with ww.Context(N, nrhs, h=h, precision=1) as ctx:
+        ww.dtn_setup(ctx, dev(eta))
+        got = ww.dtn_apply(ctx, dev(phi)).cpu().numpy()
+    ref = O.dtn(eta, phi, h)
+    for a, b in zip(got, ref):
+        assert rel(a, b) < 1e-12

@@ -1,0 +1,81 @@
+"""The oracle pins catch planted mistakes.  Each variant of ww_oracle.c is
+compiled with one deliberate error (ORC_PLANT, on the CPU only) and the pin
+that targets it must fail, while the unmodified oracle passes it."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def x_grid(N):
+    return 2 * np.pi * np.arange(N) / N
+
+
+def flat_symbol_error(L, h=1.0, k=3, N=64):
+    x = x_grid(N)
+    eta = np.full(N, h)
+    phi = np.cos(k * x)
+    out = np.empty(N)
+    L.orc_dtn(N, h, O._p(eta), O._p(phi), 1, O._p(out))
+    return np.max(np.abs(out - k * math.tanh(k * h) * phi))
+
+
+def analytic_error(L, N=64, k=2):
+    x = x_grid(N)
+    eta = 1.0 + 0.15 * np.cos(x) + 0.03 * np.cos(2 * x) - 0.02 * np.cos(3 * x)
+    z = x + 1j * eta
+    phi = np.ascontiguousarray(np.cos(k * z).real)
+    d = -k * np.sin(k * z)
+    u, v = d.real, -d.imag
+    ex = np.empty(N)
+    L.orc_spectral(N, O.MUL_DERIV, O._p(eta), O._p(ex))
+    out = np.empty(N)
+    L.orc_dtn(N, 1.0, O._p(eta), O._p(phi), 1, O._p(out))
+    return np.max(np.abs(out - (v - ex * u)))
+
+
+def dispersion_rest(L, eps=1e-3, N=32, steps=128):
+    h = 1.0
+    T = 2 * math.pi / math.sqrt(math.tanh(h))
+    prob, _ = O.make_problem(N, 0, h=h, steps=steps)
+    q0 = np.concatenate([np.full(N, h), eps * np.cos(x_grid(N))])
+    q1 = np.empty(2 * N)
+    import ctypes as C
+    L.orc_evolve(C.byref(prob), T, O._p(q0), O._p(q1))
+    return np.max(np.abs(q1[N:])) / eps
+
+
+def linearisation_gap(L, N=64):
+    import ctypes as C
+    x = x_grid(N)
+    prob, _ = O.make_problem(N, 0, h=1.0)
+    q = np.concatenate([1.0 + 0.08 * np.cos(x) + 0.02 * np.cos(2 * x), 0.05 * np.cos(x) - 0.01 * np.cos(3 * x)])
+    qd = np.concatenate([0.3 * np.cos(2 * x + 0.4), 0.2 * np.cos(x + 1.0) + 0.1 * np.cos(3 * x)])
+    y = np.stack([q, qd])
+    out = np.empty_like(y)
+    L.orc_rhs(C.byref(prob), 7.0, O._p(y), 1, 0, O._p(out))
+    eps = 1e-5
+    fp, fm = np.empty(2 * N), np.empty(2 * N)
+    a, b = q + eps * qd, q - eps * qd
+    L.orc_rhs(C.byref(prob), 7.0, O._p(a), 0, 0, O._p(fp))
+    L.orc_rhs(C.byref(prob), 7.0, O._p(b), 0, 0, O._p(fm))
+    return np.max(np.abs(out[1] - (fp - fm) / (2 * eps)))
+
+
+@pytest.fixture(scope="module")
+def good():
+    return O.load(O.build())
+
+
+@pytest.mark.parametrize("plant,probe,bound", [
+    (1, flat_symbol_error, 1e-12),      # image sign as printed
+    (2, analytic_error, 1e-11),         # zeta'(alpha) for zeta'(beta) in K1
+    (3, dispersion_rest, 5e-3),         # gravity dropped
+    (4, linearisation_gap, 1e-8),       # u psi' dropped from Eq. (l6a)
+])
+def test_pin_catches_planted_mistake(good, plant, probe, bound):
+    assert probe(good) < bound
+    bad = O.load(O.build(plant=plant))
+    assert probe(bad) > 10 * bound
