@@ -147,6 +147,26 @@ int shoot_jacobian_host(ww_ctx *ctx, const double *c, double *r, double *J, doub
  * it equals the discrete adjoint's result up to roundoff). */
 int objective_and_grad(ww_ctx *ctx, const double *c, double *f, double *grad);
 
+/* dtn_apply_static -- the same operator as dtn_setup followed by dtn_apply,
+ * for callers that cannot allocate device memory: code that runs while a
+ * stream is being captured or under an allocator that forbids cudaMalloc,
+ * and host applications that own every allocation themselves.  (The paper
+ * has no counterpart; it is an interface convenience.)  The caller passes
+ * only inputs and outputs -- eta (device, N), phi (device, N x nrhs,
+ * column-major), Gphi (device, N x nrhs, must not alias phi), h (mean depth
+ * or INFINITY) and a cudaStream_t (NULL = legacy default stream) -- and the
+ * call allocates nothing: its workspace is one fixed array inside the
+ * library, sized for N <= WW_STATIC_MAX_N and nrhs <= WW_STATIC_MAX_RHS
+ * (1.7 MB, held by every GPU that loads the library until the process
+ * exits).  Larger sizes return WW_ERR_ARG.  The first call on a device looks
+ * up the array's device address, so make that first call before any stream
+ * capture.  All calls share the array and the call synchronises its stream
+ * before returning; calls that overlap on the GPU (other threads, other
+ * streams) race on the array and must be serialised by the caller. */
+#define WW_STATIC_MAX_N   256
+#define WW_STATIC_MAX_RHS 64
+int dtn_apply_static(const double *eta, const double *phi, int N, int nrhs, double h, double *Gphi, void *stream);
+
 /* Self-tests of the tensor-core products of WW_MIXED (diagnostics; no
  * counterpart in the paper).  C = A B for column-major FP64 device arrays A
  * (M x K, ld M) and B (K x Nn, ld K), K a multiple of 64, through

@@ -35,7 +35,8 @@ ERRORS = {
 WW_FP64, WW_MIXED = 0, 1
 EXPORTS = ("ww_create", "ww_destroy", "ww_set_stream", "ww_get_stats", "ww_last_error", "ww_set_timing",
            "ww_get_timing", "dtn_setup", "dtn_apply", "shoot", "shoot_jacobian", "shoot_jacobian_host",
-           "objective_and_grad", "ww_selftest_f32gemm", "ww_selftest_ozaki")
+           "objective_and_grad", "dtn_apply_static", "ww_selftest_f32gemm", "ww_selftest_ozaki")
+STATIC_MAX_N, STATIC_MAX_RHS = 256, 64
 PHASES = ("assembly", "factor", "solve", "gapply", "colrhs", "gamma", "base")
 
 
@@ -89,6 +90,7 @@ def lib():
             "shoot_jacobian": (I, [V, V, V, V, V]),
             "shoot_jacobian_host": (I, [V, V, V, V, V]),
             "objective_and_grad": (I, [V, V, V, V]),
+            "dtn_apply_static": (I, [V, V, I, I, D, V, V]),
             "ww_selftest_f32gemm": (I, [V, V, I, I, I, C.POINTER(D)]),
             "ww_selftest_ozaki": (I, [V, V, I, I, I, C.POINTER(D)]),
         }
@@ -232,6 +234,18 @@ def shoot_jacobian_host(ctx: Context, c: np.ndarray, r: np.ndarray, J: np.ndarra
 def objective_and_grad(ctx: Context, c, f, grad):
     _check(lib().objective_and_grad(ctx.handle, _dptr(c, ctx.n + 1, "c"), _dptr(f, 1, "f"),
                                     _dptr(grad, ctx.n + 1, "grad")))
+
+
+def dtn_apply_static(eta, phi, h, Gphi, stream=None):
+    """G phi without any allocation (fixed workspace inside the library):
+    eta (N,), phi and Gphi (nrhs, N) CUDA float64; N <= STATIC_MAX_N,
+    nrhs <= STATIC_MAX_RHS."""
+    N = eta.numel()
+    nrhs = 1 if phi.dim() == 1 else phi.shape[0]
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(lib().dtn_apply_static(_dptr(eta, N, "eta"), _dptr(phi, N * nrhs, "phi"), int(N), int(nrhs),
+                                  float(h), _dptr(Gphi, N * nrhs, "Gphi"), C.c_void_p(int(raw) if raw else None)))
+    return Gphi
 
 
 def selftest(kind: str, A, B) -> float:
