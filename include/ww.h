@@ -63,7 +63,7 @@ typedef struct {
                            NULL selects column k = (cos k x, 0)                       */
     int precision;      /* WW_FP64 or WW_MIXED                                        */
     double refine_tol;  /* WW_MIXED: relative residual target, 0 => 1e-13             */
-    int max_refine;     /* WW_MIXED: refinement iterations allowed, 0 => 8            */
+    int max_refine;     /* WW_MIXED: refinement corrections per solve, 0 => 2         */
 } ww_problem;
 
 typedef struct {

@@ -251,17 +251,21 @@ int check_status(Ctx *c) {
     WW_CUDA_TRY(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     WW_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (c->precision == WW_MIXED) {
-        double ratio = 0;
+        double ratio = 0, nsres = 0;
         int err = 0;
-        WW_TRY(mixed_read_stats(c, &ratio, &err));
+        WW_TRY(mixed_read_stats(c, &ratio, &nsres, &err));
         c->stats.refine_resid_max = ratio;
+        c->stats.ns_resid_max = nsres;
         c->stats.refine_iters_max = c->max_refine;
         if (err) return fail(WW_ERR_TIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)");
     }
+    if (st & ST_NO_CONV)
+        return fail(WW_ERR_NO_CONVERGENCE, "iterative refinement missed its tolerance (or the approximate inverse "
+                                           "lost contact: the surface moved too far in one RK stage)");
     if (st & ST_GEOMETRY)
         return fail(WW_ERR_GEOMETRY, "surface touches the bottom (finite depth needs eta > 0) or is non-finite");
-    if (st & ST_NONFINITE) return fail(WW_ERR_GEOMETRY, "non-finite value in a right-hand side or factor");
-    if (st & ST_NO_CONV) return fail(WW_ERR_NO_CONVERGENCE, "iterative refinement missed its tolerance");
+    if (st & ST_NONFINITE)
+        return fail(WW_ERR_GEOMETRY, "non-finite value in a right-hand side or factor (is dt within RK4 stability?)");
     return WW_OK;
 }
 
@@ -351,7 +355,7 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
     c->steps = p->steps;
     c->precision = p->precision;
     c->refine_tol = p->refine_tol > 0.0 ? p->refine_tol : 1e-13;
-    c->max_refine = p->max_refine > 0 ? p->max_refine : 8;
+    c->max_refine = p->max_refine > 0 ? p->max_refine : 2;
     c->nb = c->N < LU_NB ? c->N : LU_NB;
     {
         cudaError_t e0 = cudaStreamCreateWithFlags(&o->own_stream, cudaStreamNonBlocking);
@@ -421,6 +425,7 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
         return fail(WW_ERR_CUDA, std::string("ww_create upload: ") + cudaGetErrorString(e));
     }
     st = prepare_spectral(c);
+    if (st == WW_OK) st = prepare_dense();
     if (st != WW_OK) {
         ww_destroy(reinterpret_cast<ww_ctx *>(o));
         return st;

@@ -75,10 +75,19 @@ __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha
 
 // ---------------------------------------------------------------- LU pieces
 // Factor the kb x kb diagonal block at A(k0, k0) in place (no pivoting) and
-// write its inverse triangles: Linv (unit lower) and Uinv (upper), kb x kb.
+// write its inverse triangles Linv (unit lower) and Uinv (upper), kb x kb,
+// column-major.  Everything happens in shared memory (3 x 64 x 65 doubles,
+// dynamic): threads 0..127 build Linv row by row from the top while threads
+// 128..255 build Uinv row by row from the bottom.
+constexpr int LD = LU_NB + 1;
+constexpr size_t LU_DIAG_SMEM = 3 * sizeof(double) * LU_NB * LD;
+
 __global__ void __launch_bounds__(256) k_lu_diag(double *A, int lda, int k0, int kb, double *Linv, double *Uinv,
                                                  int *status) {
-    __shared__ double a[LU_NB][LU_NB + 1];   // a[col][row]
+    extern __shared__ double dsm[];
+    double(*a)[LD] = reinterpret_cast<double(*)[LD]>(dsm);                    // a[col][row]
+    double(*li)[LD] = reinterpret_cast<double(*)[LD]>(dsm + LU_NB * LD);      // li[row][col]
+    double(*ui)[LD] = reinterpret_cast<double(*)[LD]>(dsm + 2 * LU_NB * LD);  // ui[row][col]
     const int tid = threadIdx.x;
     for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
         int r = idx % kb, c = idx / kb;
@@ -104,26 +113,85 @@ __global__ void __launch_bounds__(256) k_lu_diag(double *A, int lda, int k0, int
         A[(size_t)(k0 + c) * lda + k0 + r] = v;
     }
     if (__syncthreads_or(bad) && tid == 0) atomicOr(status, ST_NONFINITE);
-    // inverse triangles, one column per thread
-    if (tid < kb) {
-        const int c = tid;
-        // Linv(:, c): solve L x = e_c (unit lower)
-        for (int r = 0; r < kb; ++r) {
-            double s = (r == c) ? 1.0 : 0.0;
-            for (int q = c; q < r; ++q) s = fma(-a[q][r], Linv[(size_t)c * kb + q], s);
-            Linv[(size_t)c * kb + r] = (r < c) ? 0.0 : s;
-        }
-    } else if (tid >= 128 && tid < 128 + kb) {
-        const int c = tid - 128;
-        // Uinv(:, c): solve U x = e_c (upper), rows c down to 0
-        for (int r = kb - 1; r >= 0; --r) {
-            if (r > c) {
-                Uinv[(size_t)c * kb + r] = 0.0;
-                continue;
+    // inverse triangles: step s builds row s of Linv and row kb-1-s of Uinv
+    for (int st = 0; st < kb; ++st) {
+        if (tid < 128) {
+            const int r = st;
+            for (int c = tid; c < kb; c += 128) {
+                double v;
+                if (c > r) {
+                    v = 0.0;
+                } else if (c == r) {
+                    v = 1.0;
+                } else {
+                    v = 0.0;   // Linv(r,c) = -sum_{q=c}^{r-1} L(r,q) Linv(q,c)
+                    for (int q = c; q < r; ++q) v = fma(-a[q][r], li[q][c], v);
+                }
+                li[r][c] = v;
             }
-            double s = (r == c) ? 1.0 : 0.0;
-            for (int q = r + 1; q <= c; ++q) s = fma(-a[q][r], Uinv[(size_t)c * kb + q], s);
-            Uinv[(size_t)c * kb + r] = s / a[r][r];
+        } else {
+            const int r = kb - 1 - st, t = tid - 128;
+            for (int c = t; c < kb; c += 128) {
+                double v;
+                if (c < r) {
+                    v = 0.0;
+                } else if (c == r) {
+                    v = 1.0 / a[r][r];
+                } else {
+                    v = 0.0;   // Uinv(r,c) = -sum_{q=r+1}^{c} U(r,q) Uinv(q,c) / U(r,r)
+                    for (int q = r + 1; q <= c; ++q) v = fma(-a[q][r], ui[q][c], v);
+                    v /= a[r][r];
+                }
+                ui[r][c] = v;
+            }
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
+        int r = idx % kb, c = idx / kb;
+        Linv[(size_t)c * kb + r] = li[r][c];
+        Uinv[(size_t)c * kb + r] = ui[r][c];
+    }
+}
+
+// Deterministic FP64 GEMV-like product for narrow right-hand sides (n <= 8):
+// C = alpha A B + beta C.  A block owns 16 rows; its 16 warps split K into 32
+// chunks (two per warp, half-warps over the rows, coalesced down the columns
+// of A); the partial sums are added in a fixed order in shared memory.
+constexpr int NV_ROWS = 16, NV_WARPS = 16, NV_MAXN = 8;
+
+__global__ void __launch_bounds__(512) k_dgemv_narrow(int m, int n, int k, double alpha, const double *__restrict__ A,
+                                                      int lda, const double *__restrict__ B, int ldb, double beta,
+                                                      double *C, int ldc) {
+    __shared__ double part[2 * NV_WARPS][NV_ROWS][NV_MAXN];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rl = lane & 15, sub = lane >> 4;
+    const int row = blockIdx.x * NV_ROWS + rl;
+    const int chunk = warp * 2 + sub, nchunk = 2 * NV_WARPS;
+    const int kc = (k + nchunk - 1) / nchunk;
+    const int kb = chunk * kc, ke = min(k, kb + kc);
+    double acc[NV_MAXN];
+#pragma unroll
+    for (int j = 0; j < NV_MAXN; ++j) acc[j] = 0.0;
+    if (row < m) {
+        for (int kk = kb; kk < ke; ++kk) {
+            const double a = A[(size_t)kk * lda + row];
+#pragma unroll
+            for (int j = 0; j < NV_MAXN; ++j)
+                if (j < n) acc[j] = fma(a, B[(size_t)j * ldb + kk], acc[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NV_MAXN; ++j) part[chunk][rl][j] = acc[j];
+    __syncthreads();
+    if (threadIdx.x < NV_ROWS * NV_MAXN) {
+        const int r = threadIdx.x / NV_MAXN, j = threadIdx.x % NV_MAXN;
+        const int gr = blockIdx.x * NV_ROWS + r;
+        if (gr < m && j < n) {
+            double s = 0.0;
+            for (int c = 0; c < nchunk; ++c) s += part[c][r][j];
+            double *p = C + (size_t)j * ldc + gr;
+            *p = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *p);
         }
     }
 }
@@ -179,9 +247,19 @@ __global__ void __launch_bounds__(256) k_apply_right(const double *__restrict__ 
 
 }  // namespace
 
+int prepare_dense() {
+    WW_CUDA_TRY(cudaFuncSetAttribute(k_lu_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LU_DIAG_SMEM));
+    return WW_OK;
+}
+
 int dgemm(cudaStream_t s, int m, int n, int k, double alpha, const double *A, int lda, const double *B, int ldb,
           double beta, double *C, int ldc) {
     if (m <= 0 || n <= 0) return WW_OK;
+    if (n <= NV_MAXN) {
+        k_dgemv_narrow<<<(m + NV_ROWS - 1) / NV_ROWS, 512, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+        WW_CUDA_TRY(cudaGetLastError());
+        return WW_OK;
+    }
     dim3 grid((m + GB_M - 1) / GB_M, (n + GB_N - 1) / GB_N);
     k_dgemm<<<grid, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     WW_CUDA_TRY(cudaGetLastError());
@@ -193,7 +271,7 @@ int lu_factor_fp64(Ctx *c) {
     for (int k0 = 0, blk = 0; k0 < N; k0 += nb, ++blk) {
         const int kb = min(nb, N - k0);
         double *Linv = c->Dinv + (size_t)blk * 2 * nb * nb, *Uinv = Linv + (size_t)nb * nb;
-        k_lu_diag<<<1, 256, 0, c->stream>>>(c->A, N, k0, kb, Linv, Uinv, c->status);
+        k_lu_diag<<<1, 256, LU_DIAG_SMEM, c->stream>>>(c->A, N, k0, kb, Linv, Uinv, c->status);
         WW_CUDA_TRY(cudaGetLastError());
         const int r = N - k0 - kb;
         if (r <= 0) continue;

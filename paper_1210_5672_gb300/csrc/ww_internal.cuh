@@ -168,6 +168,7 @@ int launch_copy_cols(Ctx *c, const double *src, int ncols, double *dst);
 int launch_assemble(Ctx *c);
 
 // dense FP64 (ww_dense.cu)
+int prepare_dense();                                 // shared-memory limit of the LU block kernel
 int dgemm(cudaStream_t s, int m, int n, int k, double alpha, const double *A, int lda, const double *B,
           int ldb, double beta, double *C, int ldc);
 int lu_factor_fp64(Ctx *c);
@@ -177,7 +178,7 @@ int lu_solve_fp64(Ctx *c, double *B, int ncols);     // B <- A^{-1} B using the 
 int mixed_create(Ctx *c);
 void mixed_destroy(Ctx *c);
 int mixed_setup(Ctx *c, int fresh);                  // after assembly: update the inverse
-int mixed_read_stats(Ctx *c, double *ratio, int *err);
+int mixed_read_stats(Ctx *c, double *ratio, double *nsres, int *err);
 int mixed_solve(Ctx *c, double *B, int ncols);       // B <- A^{-1} B (refined)
 int mixed_apply_G(Ctx *c, int col0, int ncols);      // Gout += G Gam (FP64-accurate)
 

@@ -26,7 +26,7 @@ namespace ww {
 
 // ww_tcgemm.cu
 int tc_slice_f32(cudaStream_t s, const float *src, int ld, int rows, int K, int trans, float shift, int S,
-                 __nv_bfloat16 *dst);
+                 __nv_bfloat16 *dst, unsigned *dev_max = nullptr);
 int tc_slice_f64(cudaStream_t s, const double *src, int ld, int rows, int K, int trans, float shift, int S,
                  __nv_bfloat16 *dst);
 int tc_gemm_f32acc(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 *B3, int M, int Nn, int K,
@@ -56,6 +56,7 @@ struct Mixed {
     int *psie;
     unsigned long long *colmax;            // NC
     double *ratio;                         // worst final residual ratio (device, bits as u64)
+    unsigned *nsres;                       // worst max|I - A X| before an update (fp32 bits)
     int *err;
 };
 
@@ -107,14 +108,16 @@ int alloc(Ctx *c, T **p, size_t n) {
     return WW_OK;
 }
 
-// one Newton-Schulz step X <- X (2I - A X), all products FP32-accurate
-int ns_step(Ctx *c) {
+// one Newton-Schulz step X <- X (2I - A X), all products FP32-accurate;
+// record: fold max|I - A X| (the contraction of this stage's refinement
+// before the update) into the diagnostics
+int ns_step(Ctx *c, bool record) {
     Mixed *m = c->mx;
     const int N = c->N;
     cudaStream_t s = c->stream;
     WW_TRY(tc_slice_f32(s, m->X, N, N, N, 0, 0.f, 3, m->XslcB));                 // columns of X
     WW_TRY(tc_gemm_f32acc(s, m->Aslc, m->XslcB, N, N, N, 0, m->P, nullptr, N, 1.0, m->err));   // P = A X
-    WW_TRY(tc_slice_f32(s, m->P, N, N, N, 0, 2.f, 3, m->Wslc));                  // columns of 2I - P
+    WW_TRY(tc_slice_f32(s, m->P, N, N, N, 0, 2.f, 3, m->Wslc, record ? m->nsres : nullptr));   // columns of 2I - P
     WW_TRY(tc_slice_f32(s, m->X, N, N, N, 1, 0.f, 3, m->XslcA));                 // rows of X
     WW_TRY(tc_gemm_f32acc(s, m->XslcA, m->Wslc, N, N, N, 0, m->X, nullptr, N, 1.0, m->err));   // X = X W
     return WW_OK;
@@ -173,11 +176,13 @@ int mixed_create(Ctx *c) {
     MA(m->psie, NC);
     MA(m->colmax, NC);
     MA(m->ratio, 1);
+    MA(m->nsres, 1);
     MA(m->err, 1);
 #undef MA
     if (st != WW_OK) return st;
     WW_CUDA_TRY(cudaMemset(m->err, 0, sizeof(int)));
     WW_CUDA_TRY(cudaMemset(m->ratio, 0, sizeof(double)));
+    WW_CUDA_TRY(cudaMemset(m->nsres, 0, sizeof(unsigned)));
     return WW_OK;
 }
 
@@ -186,7 +191,7 @@ void mixed_destroy(Ctx *c) {
     if (!m) return;
     void *ptrs[] = {m->X,  m->P,  m->Aslc, m->XslcB, m->XslcA, m->Wslc, m->Kd,  m->Gd,   m->Ks,     m->Gs,    m->Ke,
                     m->Ge, m->Rd, m->Rs,   m->Re,    m->Bslc,  m->R,    m->Psi, m->psis, m->psie, m->colmax, m->ratio,
-                    m->err};
+                    m->nsres, m->err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -203,9 +208,9 @@ int mixed_setup(Ctx *c, int fresh) {
         const size_t NN = (size_t)N * N;
         k_scaled_identity<<<(unsigned)((NN + 255) / 256), 256, 0, s>>>(m->X, N, 4.f / 3.f);
         WW_CUDA_TRY(cudaGetLastError());
-        for (int i = 0; i < NS_INIT; ++i) WW_TRY(ns_step(c));
+        for (int i = 0; i < NS_INIT; ++i) WW_TRY(ns_step(c, false));
     } else {
-        WW_TRY(ns_step(c));
+        WW_TRY(ns_step(c, true));
     }
     WW_TRY(tc_slice_f32(s, m->X, N, N, N, 1, 0.f, 3, m->XslcA));   // rows of the new X
     WW_TRY(ozaki_digits(s, c->A, N, N, N, 0, 0.5f, m->Ke, m->Ks, m->Kd));   // K = A - I/2
@@ -259,13 +264,19 @@ int mixed_apply_G(Ctx *c, int col0, int ncols) {
                       m->err);
 }
 
-// device diagnostics of the mixed path, read after a call
-int mixed_read_stats(Ctx *c, double *ratio, int *err) {
+// device diagnostics of the mixed path, read (and reset) after a call
+int mixed_read_stats(Ctx *c, double *ratio, double *nsres, int *err) {
     Mixed *m = c->mx;
+    unsigned nb = 0;
     WW_CUDA_TRY(cudaMemcpyAsync(ratio, m->ratio, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    WW_CUDA_TRY(cudaMemcpyAsync(&nb, m->nsres, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     WW_CUDA_TRY(cudaMemcpyAsync(err, m->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     WW_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    float nf;
+    memcpy(&nf, &nb, sizeof(nf));
+    *nsres = nf;
     WW_CUDA_TRY(cudaMemsetAsync(m->ratio, 0, sizeof(double), c->stream));
+    WW_CUDA_TRY(cudaMemsetAsync(m->nsres, 0, sizeof(unsigned), c->stream));
     WW_CUDA_TRY(cudaMemsetAsync(m->err, 0, sizeof(int), c->stream));
     return WW_OK;
 }

@@ -58,6 +58,7 @@ int workspace(double **out) {
         if (e != cudaSuccess)
             return fail(WW_ERR_CUDA, std::string("dtn_apply_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         g_ws_ptr[dev] = static_cast<double *>(p);
+        WW_TRY(prepare_dense());   // shared-memory limit of the LU block kernel on this device
     }
     *out = g_ws_ptr[dev];
     return WW_OK;

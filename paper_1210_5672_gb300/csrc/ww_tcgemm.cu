@@ -211,8 +211,9 @@ int launch_tc(cudaStream_t s, const void *A, const void *B, int M, int Nn, int K
 // optionally v -> shift*delta(r,k) - v.  S bf16 slices, v = sum_s slice_s + O(2^-8S |v|).
 template <typename T>
 __global__ void k_slice(const T *__restrict__ src, int ld, int rows, int K, int trans, float shift, int S,
-                        __nv_bfloat16 *dst) {
+                        __nv_bfloat16 *dst, unsigned *dev_max) {
     __shared__ float tile[32][33];
+    float dmax = 0.f;   // with shift = 2: max |(2 delta - v) - delta| = max |delta - v|
     const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
     for (int yy = ty; yy < 32; yy += 8) {
@@ -226,9 +227,16 @@ __global__ void k_slice(const T *__restrict__ src, int ld, int rows, int K, int 
         } else {
             const int k = k0 + tx, r = r0 + yy;
             v = (r < rows && k < K) ? (float)src[(size_t)r * ld + k] : 0.f;
-            if (shift != 0.f) v = (r == k ? shift : 0.f) - v;
+            if (shift != 0.f) {
+                v = (r == k ? shift : 0.f) - v;
+                if (r < rows && k < K) dmax = fmaxf(dmax, fabsf(v - (r == k ? 0.5f * shift : 0.f)));
+            }
             tile[tx][yy] = v;
         }
+    }
+    if (dev_max) {
+        for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(dev_max, __float_as_uint(dmax));
     }
     __syncthreads();
     for (int yy = ty; yy < 32; yy += 8) {
@@ -246,9 +254,9 @@ __global__ void k_slice(const T *__restrict__ src, int ld, int rows, int K, int 
 }  // namespace
 
 int tc_slice_f32(cudaStream_t s, const float *src, int ld, int rows, int K, int trans, float shift, int S,
-                 __nv_bfloat16 *dst) {
+                 __nv_bfloat16 *dst, unsigned *dev_max) {
     dim3 grid((K + 31) / 32, (rows + 31) / 32);
-    k_slice<float><<<grid, 256, 0, s>>>(src, ld, rows, K, trans, shift, S, dst);
+    k_slice<float><<<grid, 256, 0, s>>>(src, ld, rows, K, trans, shift, S, dst, dev_max);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
@@ -256,7 +264,7 @@ int tc_slice_f32(cudaStream_t s, const float *src, int ld, int rows, int K, int 
 int tc_slice_f64(cudaStream_t s, const double *src, int ld, int rows, int K, int trans, float shift, int S,
                  __nv_bfloat16 *dst) {
     dim3 grid((K + 31) / 32, (rows + 31) / 32);
-    k_slice<double><<<grid, 256, 0, s>>>(src, ld, rows, K, trans, shift, S, dst);
+    k_slice<double><<<grid, 256, 0, s>>>(src, ld, rows, K, trans, shift, S, dst, nullptr);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
