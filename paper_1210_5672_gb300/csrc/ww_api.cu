@@ -373,6 +373,7 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
 #define ALLOC(ptr, cnt)                                     \
     if (st == WW_OK) st = dalloc_n(o, &(ptr), (size_t)(cnt))
     ALLOC(c->tw, N / 2);
+    if (p->precision == WW_MIXED) ALLOC(c->twd, N / 2);
     ALLOC(c->cs, 3 * N);
     ALLOC(c->eta, N);
     ALLOC(c->eta_x, N);
@@ -420,6 +421,16 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
     if (e == cudaSuccess)
         e = cudaMemcpy(c->basis, basis.data(), sizeof(double) * basis.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
+    if (e == cudaSuccess && c->twd) {
+        // double-float twiddles: hi = float(w), lo = float(w - hi)
+        std::vector<float> twd(2 * N);
+        for (size_t k = 0; k < N; ++k) {
+            const float hi = (float)tw[k];
+            twd[2 * k] = hi;
+            twd[2 * k + 1] = (float)(tw[k] - (double)hi);
+        }
+        e = cudaMemcpy(c->twd, twd.data(), sizeof(float) * 2 * N, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         ww_destroy(reinterpret_cast<ww_ctx *>(o));
         return fail(WW_ERR_CUDA, std::string("ww_create upload: ") + cudaGetErrorString(e));

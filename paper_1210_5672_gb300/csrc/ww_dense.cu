@@ -174,7 +174,19 @@ __global__ void __launch_bounds__(512) k_dgemv_narrow(int m, int n, int k, doubl
 #pragma unroll
     for (int j = 0; j < NV_MAXN; ++j) acc[j] = 0.0;
     if (row < m) {
-        for (int kk = kb; kk < ke; ++kk) {
+        int kk = kb;
+        // eight independent loads in flight per thread (the loop is latency bound)
+        for (; kk + 8 <= ke; kk += 8) {
+            double a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] = A[(size_t)(kk + u) * lda + row];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int j = 0; j < NV_MAXN; ++j)
+                    if (j < n) acc[j] = fma(a[u], B[(size_t)j * ldb + kk + u], acc[j]);
+        }
+        for (; kk < ke; ++kk) {
             const double a = A[(size_t)kk * lda + row];
 #pragma unroll
             for (int j = 0; j < NV_MAXN; ++j)

@@ -60,6 +60,7 @@ struct Ctx {
 
     // tables
     double2 *tw;              // tw[k] = exp(-2 pi i k / N), k < N/2
+    float4 *twd;              // the same twiddles in double-float (WW_MIXED), or NULL
     double *cs;               // cs[m] = cos(2 pi m / N), cs[N + m] = sin(2 pi m / N)
 
     // base-surface geometry of the current stage (N each)

@@ -9,6 +9,7 @@
 // d/dx, H d/dx = |k| and the filter are real operators, two real signals a, b
 // are transformed together as one complex signal a + i b and come back as
 // (L a) + i (L b) -- no even/odd separation is needed anywhere.
+#include "ww_df.cuh"
 #include "ww_internal.cuh"
 
 namespace ww {
@@ -21,25 +22,59 @@ __device__ __forceinline__ double2 times_ik(double2 z, int k) {   // (ik) z
     return make_double2(-(double)k * z.y, (double)k * z.x);
 }
 
-// s <- s * m(k) / N for the derivative multiplier (ik, Nyquist zero)
-__device__ __forceinline__ void mul_deriv(double2 *s, int N) {
-    const double invN = 1.0 / N;
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        int k = wavenum(j, N);
-        s[j] = (j == (N >> 1)) ? make_double2(0.0, 0.0) : cscale(times_ik(s[j], k), invN);
+// Arithmetic of the in-shared-memory transforms.  ArF64: IEEE double (the
+// WW_FP64 form).  ArDF: double-float (ww_df.cuh) for the WW_MIXED form, where
+// the FP64 pipe is the bottleneck; inputs, outputs and all pointwise algebra
+// stay FP64 in both.
+struct ArF64 {
+    using C = double2;
+    static __device__ __forceinline__ C mk(double re, double im) { return make_double2(re, im); }
+    static __device__ __forceinline__ double2 get(C z) { return z; }
+    static __device__ __forceinline__ void fft(C *s, int N, int logN, const void *tw, bool inv) {
+        block_fft(s, N, logN, static_cast<const double2 *>(tw), inv);
     }
+    static __device__ __forceinline__ C scale(C z, double f) { return cscale(z, f); }
+    static __device__ __forceinline__ C ikscale(C z, int k, float p2) { return cscale(times_ik(z, k), (double)p2); }
+    static __device__ __forceinline__ C add(C a, C b) { return cadd(a, b); }
+    static __device__ __forceinline__ C zero() { return make_double2(0.0, 0.0); }
+    static __device__ __forceinline__ C re_only(C z, double f) { return make_double2(z.x * f, 0.0); }
+};
+
+struct ArDF {
+    using C = dfl::cdf;
+    static __device__ __forceinline__ C mk(double re, double im) { return dfl::from_d2(make_double2(re, im)); }
+    static __device__ __forceinline__ double2 get(C z) { return dfl::to_d2(z); }
+    static __device__ __forceinline__ void fft(C *s, int N, int logN, const void *tw, bool inv) {
+        dfl::block_fft(s, N, logN, static_cast<const dfl::cdf *>(tw), inv);
+    }
+    static __device__ __forceinline__ C scale(C z, double f) { return dfl::cscale(z, dfl::from_double(f)); }
+    static __device__ __forceinline__ C ikscale(C z, int k, float p2) { return dfl::cscalef(dfl::times_ik(z, k), p2); }
+    static __device__ __forceinline__ C add(C a, C b) { return dfl::cadd(a, b); }
+    static __device__ __forceinline__ C zero() { return C{0.f, 0.f, 0.f, 0.f}; }
+    static __device__ __forceinline__ C re_only(C z, double f) {
+        return dfl::make(dfl::mul(dfl::re(z), dfl::from_double(f)), dfl::df{0.f, 0.f});
+    }
+};
+
+// s <- s * (ik) / N (Nyquist zero)
+template <class AR>
+__device__ __forceinline__ void mul_deriv(typename AR::C *s, int N) {
+    const float invN = 1.0f / (float)N;   // exact: N is a power of two
+    for (int j = threadIdx.x; j < N; j += blockDim.x)
+        s[j] = (j == (N >> 1)) ? AR::zero() : AR::ikscale(s[j], wavenum(j, N), invN);
 }
 
 // ------------------------------------------------------------------------
 // base geometry: eta', phi', eta'' (= d/dx of eta'), curvature term
 // d/dx (eta'/sqrt(1+eta'^2)), exp(+-eta); geometry check.   (Sec. 2.1)
 // ------------------------------------------------------------------------
+template <class AR>
 __global__ void k_base_geometry(const double *__restrict__ eta_in, const double *__restrict__ phi_in,
-                                int with_phi, int N, int logN, int deep, const double2 *__restrict__ tw,
+                                int with_phi, int N, int logN, int deep, const void *__restrict__ tw,
                                 double *eta, double *eta_x, double *eta_xx, double *phi_s, double *curv,
                                 double *E, double *Einv, int *status) {
-    extern __shared__ double2 sm[];
-    double2 *s = sm;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw);
     int bad = 0;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         double e = eta_in[j];
@@ -48,63 +83,67 @@ __global__ void k_base_geometry(const double *__restrict__ eta_in, const double 
         eta[j] = e;
         E[j] = exp(e);
         Einv[j] = exp(-e);
-        s[j] = make_double2(e, p);
+        s[j] = AR::mk(e, p);
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_GEOMETRY);
-    block_fft(s, N, logN, tw, false);
-    mul_deriv(s, N);
+    AR::fft(s, N, logN, tw, false);
+    mul_deriv<AR>(s, N);
     __syncthreads();
-    block_fft(s, N, logN, tw, true);
+    AR::fft(s, N, logN, tw, true);
     // s = eta' + i phi'
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        double ex = s[j].x;
+        const double2 v = AR::get(s[j]);
+        const double ex = v.x;
         eta_x[j] = ex;
-        phi_s[j] = s[j].y;
-        s[j] = make_double2(ex / sqrt(1.0 + ex * ex), ex);   // (eta'/sqrt(1+eta'^2)) + i eta'
+        phi_s[j] = v.y;
+        s[j] = AR::mk(ex / sqrt(1.0 + ex * ex), ex);   // (eta'/sqrt(1+eta'^2)) + i eta'
     }
     __syncthreads();
-    block_fft(s, N, logN, tw, false);
-    mul_deriv(s, N);
+    AR::fft(s, N, logN, tw, false);
+    mul_deriv<AR>(s, N);
     __syncthreads();
-    block_fft(s, N, logN, tw, true);
+    AR::fft(s, N, logN, tw, true);
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        curv[j] = s[j].x;
-        eta_xx[j] = s[j].y;
+        const double2 v = AR::get(s[j]);
+        curv[j] = v.x;
+        eta_xx[j] = v.y;
     }
 }
 
 // ------------------------------------------------------------------------
 // gamma = mu' and 1/2 H gamma for pairs of columns of M (Eq. G)
 // ------------------------------------------------------------------------
-__global__ void k_gamma(const double *__restrict__ M, int ncols, int N, int logN,
-                        const double2 *__restrict__ tw, double *Gam, double *Gout) {
-    extern __shared__ double2 sm[];
-    double2 *s = sm, *z = sm + N;
+template <class AR>
+__global__ void k_gamma(const double *__restrict__ M, int ncols, int N, int logN, const void *__restrict__ tw,
+                        double *Gam, double *Gout) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw), *z = s + N;
     const int ca = 2 * blockIdx.x, cb = ca + 1;
     const bool hasb = cb < ncols;
     const double *ma = M + (size_t)ca * N, *mb = M + (size_t)cb * N;
-    for (int j = threadIdx.x; j < N; j += blockDim.x) s[j] = make_double2(ma[j], hasb ? mb[j] : 0.0);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) s[j] = AR::mk(ma[j], hasb ? mb[j] : 0.0);
     __syncthreads();
-    block_fft(s, N, logN, tw, false);
-    const double invN = 1.0 / N;
+    AR::fft(s, N, logN, tw, false);
+    const float invN = 1.0f / (float)N;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        int k = wavenum(j, N);
-        double2 v = s[j];
-        bool nyq = (j == (N >> 1));
-        z[j] = nyq ? make_double2(0.0, 0.0) : cscale(v, 0.5 * fabs((double)k) * invN);  // 1/2 H d/dx = |k|/2
-        s[j] = nyq ? make_double2(0.0, 0.0) : cscale(times_ik(v, k), invN);
+        const int k = wavenum(j, N);
+        const bool nyq = (j == (N >> 1));
+        const typename AR::C v = s[j];
+        z[j] = nyq ? AR::zero() : AR::scale(v, 0.5 * fabs((double)k) * (double)invN);   // 1/2 H d/dx = |k|/2
+        s[j] = nyq ? AR::zero() : AR::ikscale(v, k, invN);
     }
     __syncthreads();
-    block_fft(s, N, logN, tw, true);
-    block_fft(z, N, logN, tw, true);
+    AR::fft(s, N, logN, tw, true);
+    AR::fft(z, N, logN, tw, true);
     double *ga = Gam + (size_t)ca * N, *gb = Gam + (size_t)cb * N;
     double *oa = Gout + (size_t)ca * N, *ob = Gout + (size_t)cb * N;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        ga[j] = s[j].x;
-        oa[j] = z[j].x;
+        const double2 g = AR::get(s[j]), h = AR::get(z[j]);
+        ga[j] = g.x;
+        oa[j] = h.x;
         if (hasb) {
-            gb[j] = s[j].y;
-            ob[j] = z[j].y;
+            gb[j] = g.y;
+            ob[j] = h.y;
         }
     }
 }
@@ -122,7 +161,7 @@ __global__ void k_psi(const double *__restrict__ Ys, const double *__restrict__ 
 }
 
 // ------------------------------------------------------------------------
-// RK4 stage combination for one column held in registers/shared memory.
+// RK4 stage combination for one column held in shared memory.
 // Classic RK4: stages at a = (0, 1/2, 1/2, 1), weights b = (1, 2, 2, 1)/6.
 // For stage < 3: acc (+)= b k, Ys = Y + a_next dt k.  For the last stage the
 // caller filters Y + dt/6 (acc + k) and stores it in Y and Ys.
@@ -132,30 +171,33 @@ __device__ __forceinline__ double rk_a_next(int st) { return st == 2 ? 1.0 : 0.5
 
 // end-of-step update of one column: s holds k (eta part .x, phi part .y) in
 // physical space; writes the filtered new state into Y and Ys.
-__device__ void finish_step(double2 *s, int N, int logN, const double2 *__restrict__ tw, double dt,
-                            double *Yc, double *Ysc, const double *Accc) {
+template <class AR>
+__device__ void finish_step(typename AR::C *s, int N, int logN, const void *__restrict__ tw, double dt, double *Yc,
+                            double *Ysc, const double *Accc) {
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        double2 k = s[j];
-        s[j] = make_double2(Yc[j] + dt / 6.0 * (Accc[j] + k.x), Yc[N + j] + dt / 6.0 * (Accc[N + j] + k.y));
+        const double2 k = AR::get(s[j]);
+        s[j] = AR::mk(Yc[j] + dt / 6.0 * (Accc[j] + k.x), Yc[N + j] + dt / 6.0 * (Accc[N + j] + k.y));
     }
     __syncthreads();
-    block_fft(s, N, logN, tw, false);
+    AR::fft(s, N, logN, tw, false);
     const double invN = 1.0 / N;
-    for (int j = threadIdx.x; j < N; j += blockDim.x) s[j] = cscale(s[j], filt36(wavenum(j, N), N) * invN);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) s[j] = AR::scale(s[j], filt36(wavenum(j, N), N) * invN);
     __syncthreads();
-    block_fft(s, N, logN, tw, true);
+    AR::fft(s, N, logN, tw, true);
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        Yc[j] = Ysc[j] = s[j].x;
-        Yc[N + j] = Ysc[N + j] = s[j].y;
+        const double2 v = AR::get(s[j]);
+        Yc[j] = Ysc[j] = v.x;
+        Yc[N + j] = Ysc[N + j] = v.y;
     }
 }
 
-__device__ void stage_update(double2 *s, int N, int logN, const double2 *__restrict__ tw, int st, double dt,
+template <class AR>
+__device__ void stage_update(typename AR::C *s, int N, int logN, const void *__restrict__ tw, int st, double dt,
                              double *Yc, double *Ysc, double *Accc) {
     if (st < 3) {
         const double b = rk_b(st), a = rk_a_next(st);
         for (int j = threadIdx.x; j < N; j += blockDim.x) {
-            double2 k = s[j];
+            const double2 k = AR::get(s[j]);
             if (st == 0) {
                 Accc[j] = b * k.x;
                 Accc[N + j] = b * k.y;
@@ -168,21 +210,22 @@ __device__ void stage_update(double2 *s, int N, int logN, const double2 *__restr
         }
     } else {
         __syncthreads();
-        finish_step(s, N, logN, tw, dt, Yc, Ysc, Accc);
+        finish_step<AR>(s, N, logN, tw, dt, Yc, Ysc, Accc);
     }
 }
 
 // ------------------------------------------------------------------------
 // base right-hand side, Eq. (ww) with Eq. (uv:from:G); filtered; RK update
 // ------------------------------------------------------------------------
+template <class AR>
 __global__ void k_base_rhs(const double *__restrict__ Gphi, const double *__restrict__ eta,
                            const double *__restrict__ eta_x, const double *__restrict__ phi_s,
                            const double *__restrict__ curv, double g, double tau, int N, int logN,
-                           const double2 *__restrict__ tw, double *ux, double *vy, double *w3, double *Fbase,
+                           const void *__restrict__ tw, double *ux, double *vy, double *w3, double *Fbase,
                            double *Y, double *Ys, double *Acc, int st, const double *__restrict__ cvec,
                            int steps, int update, int *status) {
-    extern __shared__ double2 sm[];
-    double2 *s = sm;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw);
     int bad = 0;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         double ex = eta_x[j], d = 1.0 + ex * ex, gp = Gphi[j], pp = phi_s[j];
@@ -193,26 +236,27 @@ __global__ void k_base_rhs(const double *__restrict__ Gphi, const double *__rest
         w3[j] = 1.0 / (d * sqrt(d));
         double pt = v * gp - 0.5 * u * u - 0.5 * v * v - g * eta[j] + tau * curv[j];
         if (!isfinite(pt) || !isfinite(gp)) bad = 1;
-        s[j] = make_double2(gp, pt);   // eta_t = G phi ; phi_t before P and the filter
+        s[j] = AR::mk(gp, pt);   // eta_t = G phi ; phi_t before P and the filter
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
-    block_fft(s, N, logN, tw, false);
+    AR::fft(s, N, logN, tw, false);
     const double invN = 1.0 / N;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        double f = filt36(wavenum(j, N), N) * invN;
+        const double f = filt36(wavenum(j, N), N) * invN;
         // P acts on the phi part only: at k = 0 keep Re (eta mean), drop Im (phi mean)
-        s[j] = (j == 0) ? make_double2(s[0].x * f, 0.0) : cscale(s[j], f);
+        s[j] = (j == 0) ? AR::re_only(s[0], f) : AR::scale(s[j], f);
     }
     __syncthreads();
-    block_fft(s, N, logN, tw, true);
+    AR::fft(s, N, logN, tw, true);
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        Fbase[j] = s[j].x;
-        Fbase[N + j] = s[j].y;
+        const double2 v = AR::get(s[j]);
+        Fbase[j] = v.x;
+        Fbase[N + j] = v.y;
     }
     if (!update) return;
     const double dt = cvec[0] / (4.0 * steps);
     __syncthreads();
-    stage_update(s, N, logN, tw, st, dt, Y, Ys, Acc);
+    stage_update<AR>(s, N, logN, tw, st, dt, Y, Ys, Acc);
 }
 
 // ------------------------------------------------------------------------
@@ -222,64 +266,66 @@ __global__ void k_base_rhs(const double *__restrict__ Gphi, const double *__rest
 //                 + tau (etadot' (1+eta'^2)^{-3/2})' ]
 // filtered; the T column (column 1) adds F(q)/T; then the RK update.
 // ------------------------------------------------------------------------
+template <class AR>
 __global__ void k_col_rhs(const double *__restrict__ Gout, const double *__restrict__ ux,
                           const double *__restrict__ vy, const double *__restrict__ w3,
                           const double *__restrict__ Fbase, double g, double tau, int N, int logN,
-                          const double2 *__restrict__ tw, double *Y, double *Ys, double *Acc, int st,
+                          const void *__restrict__ tw, double *Y, double *Ys, double *Acc, int st,
                           const double *__restrict__ cvec, int steps, int *status) {
-    extern __shared__ double2 sm[];
-    double2 *s = sm, *z = sm + N;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw), *z = s + N;
     const int c = blockIdx.x + 1;
     double *Yc = Y + (size_t)c * 2 * N, *Ysc = Ys + (size_t)c * 2 * N, *Accc = Acc + (size_t)c * 2 * N;
     const double *Gpsi = Gout + (size_t)c * N;
     // psi + i etadot  ->  psi' + i etadot'
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         double ed = Ysc[j];
-        s[j] = make_double2(Ysc[N + j] - vy[j] * ed, ed);
+        s[j] = AR::mk(Ysc[N + j] - vy[j] * ed, ed);
     }
     __syncthreads();
-    block_fft(s, N, logN, tw, false);
-    mul_deriv(s, N);
+    AR::fft(s, N, logN, tw, false);
+    mul_deriv<AR>(s, N);
     __syncthreads();
-    block_fft(s, N, logN, tw, true);
+    AR::fft(s, N, logN, tw, true);
     int bad = 0;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         double ed = Ysc[j], u = ux[j], v = vy[j], gp = Gpsi[j];
-        double dpsi = s[j].x, ded = s[j].y;
+        const double2 dd = AR::get(s[j]);
+        const double dpsi = dd.x, ded = dd.y;
         // undifferentiated terms: (G psi, -u psi' + v G psi - g etadot)
-        z[j] = make_double2(gp, -u * dpsi + v * gp - g * ed);
+        z[j] = AR::mk(gp, -u * dpsi + v * gp - g * ed);
         // terms under one d/dx: (-etadot u, tau etadot' w3 - etadot u v)
-        s[j] = make_double2(-ed * u, tau * ded * w3[j] - ed * u * v);
+        s[j] = AR::mk(-ed * u, tau * ded * w3[j] - ed * u * v);
         if (!isfinite(gp)) bad = 1;
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
-    block_fft(z, N, logN, tw, false);
-    block_fft(s, N, logN, tw, false);
+    AR::fft(z, N, logN, tw, false);
+    AR::fft(s, N, logN, tw, false);
     const double invN = 1.0 / N;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        int k = wavenum(j, N);
-        double f = filt36(k, N) * invN;
-        double2 w;
+        const int k = wavenum(j, N);
+        const double f = filt36(k, N) * invN;
+        typename AR::C w;
         if (j == 0)
-            w = make_double2(z[0].x * f, 0.0);       // P on the phi part; d/dx kills k = 0
+            w = AR::re_only(z[0], f);                 // P on the phi part; d/dx kills k = 0
         else if (j == (N >> 1))
-            w = cscale(z[j], f);                      // d/dx is zero at Nyquist
+            w = AR::scale(z[j], f);                   // d/dx is zero at Nyquist
         else
-            w = cscale(cadd(z[j], times_ik(s[j], k)), f);
+            w = AR::scale(AR::add(z[j], AR::ikscale(s[j], k, 1.0f)), f);
         s[j] = w;
     }
     __syncthreads();
-    block_fft(s, N, logN, tw, true);
+    AR::fft(s, N, logN, tw, true);
     if (c == 1) {   // d/dT column: + F(q) / T  (dt = T / (4 steps) is a function of T)
         const double invT = 1.0 / cvec[0];
         for (int j = threadIdx.x; j < N; j += blockDim.x) {
-            s[j].x += Fbase[j] * invT;
-            s[j].y += Fbase[N + j] * invT;
+            const double2 v = AR::get(s[j]);
+            s[j] = AR::mk(v.x + Fbase[j] * invT, v.y + Fbase[N + j] * invT);
         }
     }
     const double dt = cvec[0] / (4.0 * steps);
     __syncthreads();
-    stage_update(s, N, logN, tw, st, dt, Yc, Ysc, Accc);
+    stage_update<AR>(s, N, logN, tw, st, dt, Yc, Ysc, Accc);
 }
 
 // ------------------------------------------------------------------------
@@ -364,18 +410,28 @@ int set_smem(K kernel, size_t bytes) {
 // ==========================================================================
 int prepare_spectral(Ctx *c) {
     const size_t one = sizeof(double2) * c->N, two = 2 * one;
-    WW_TRY(set_smem(k_base_geometry, one));
-    WW_TRY(set_smem(k_base_rhs, one));
-    WW_TRY(set_smem(k_gamma, two));
-    WW_TRY(set_smem(k_col_rhs, two));
+    WW_TRY(set_smem(k_base_geometry<ArF64>, one));
+    WW_TRY(set_smem(k_base_rhs<ArF64>, one));
+    WW_TRY(set_smem(k_gamma<ArF64>, two));
+    WW_TRY(set_smem(k_col_rhs<ArF64>, two));
+    WW_TRY(set_smem(k_gamma<ArDF>, two));
+    WW_TRY(set_smem(k_col_rhs<ArDF>, two));
     return WW_OK;
 }
 
+// The mixed form runs the transforms of the VARIATIONAL columns in
+// double-float (c->twd); the base state (whose eta'' enters every matrix
+// entry and whose errors reach r directly) and the FP64 form stay in FP64.
+// Measured: double-float base transforms cost ~1e-9 relative in the DtN at
+// N = 2048 (derivatives amplify the 2^-48 FFT roundoff by |k|), column
+// transforms keep J within ~1e-13 of the FP64 form.
+static bool use_df(const Ctx *c) { return c->precision == WW_MIXED && c->twd != nullptr; }
+
 int launch_base_geometry(Ctx *c, const double *eta, const double *phi, int with_phi) {
     size_t sm = sizeof(double2) * c->N;
-    k_base_geometry<<<1, FFT_THREADS, sm, c->stream>>>(eta, phi, with_phi, c->N, c->logN, c->deep ? 1 : 0, c->tw,
-                                                      c->eta, c->eta_x, c->eta_xx, c->phi_s, c->curv, c->E,
-                                                      c->Einv, c->status);
+    k_base_geometry<ArF64><<<1, FFT_THREADS, sm, c->stream>>>(eta, phi, with_phi, c->N, c->logN, c->deep ? 1 : 0,
+                                                                 c->tw, c->eta, c->eta_x, c->eta_xx, c->phi_s,
+                                                                 c->curv, c->E, c->Einv, c->status);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
@@ -383,8 +439,12 @@ int launch_base_geometry(Ctx *c, const double *eta, const double *phi, int with_
 int launch_gamma(Ctx *c, int col0, int ncols) {
     size_t sm = 2 * sizeof(double2) * c->N;
     size_t off = (size_t)col0 * c->N;
-    k_gamma<<<(ncols + 1) / 2, FFT_THREADS, sm, c->stream>>>(c->M + off, ncols, c->N, c->logN, c->tw, c->Gam + off,
-                                                            c->Gout + off);
+    if (use_df(c) && col0 >= 1)
+        k_gamma<ArDF><<<(ncols + 1) / 2, FFT_THREADS, sm, c->stream>>>(c->M + off, ncols, c->N, c->logN, c->twd,
+                                                                      c->Gam + off, c->Gout + off);
+    else
+        k_gamma<ArF64><<<(ncols + 1) / 2, FFT_THREADS, sm, c->stream>>>(c->M + off, ncols, c->N, c->logN, c->tw,
+                                                                       c->Gam + off, c->Gout + off);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
@@ -405,10 +465,10 @@ int launch_phi0(Ctx *c) {
 // stage < 0: evaluate the base RHS only (no RK update)
 int launch_base_rhs(Ctx *c, int stage, const double *cvec) {
     size_t sm = sizeof(double2) * c->N;
-    k_base_rhs<<<1, FFT_THREADS, sm, c->stream>>>(c->Gout, c->eta, c->eta_x, c->phi_s, c->curv, c->g, c->tau, c->N,
-                                                 c->logN, c->tw, c->ux, c->vy, c->w3, c->Fbase, c->Y, c->Ys,
-                                                 c->Kacc, stage < 0 ? 0 : stage, cvec, c->steps, stage >= 0 ? 1 : 0,
-                                                 c->status);
+    k_base_rhs<ArF64><<<1, FFT_THREADS, sm, c->stream>>>(c->Gout, c->eta, c->eta_x, c->phi_s, c->curv, c->g, c->tau,
+                                            c->N, c->logN, (const void *)c->tw, c->ux,
+                                            c->vy, c->w3, c->Fbase, c->Y, c->Ys, c->Kacc, stage < 0 ? 0 : stage,
+                                            cvec, c->steps, stage >= 0 ? 1 : 0, c->status);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
@@ -416,9 +476,10 @@ int launch_base_rhs(Ctx *c, int stage, const double *cvec) {
 int launch_col_rhs(Ctx *c, int stage, const double *cvec) {
     if (c->nc <= 0) return WW_OK;
     size_t sm = 2 * sizeof(double2) * c->N;
-    k_col_rhs<<<c->nc, FFT_THREADS, sm, c->stream>>>(c->Gout, c->ux, c->vy, c->w3, c->Fbase, c->g, c->tau, c->N,
-                                                    c->logN, c->tw, c->Y, c->Ys, c->Kacc, stage, cvec, c->steps,
-                                                    c->status);
+    auto kern = use_df(c) ? k_col_rhs<ArDF> : k_col_rhs<ArF64>;
+    kern<<<c->nc, FFT_THREADS, sm, c->stream>>>(c->Gout, c->ux, c->vy, c->w3, c->Fbase, c->g, c->tau, c->N, c->logN,
+                                                use_df(c) ? (const void *)c->twd : (const void *)c->tw, c->Y, c->Ys,
+                                                c->Kacc, stage, cvec, c->steps, c->status);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     if (col < Nn) {
                         const size_t idx = (size_t)col * ldc + row;
                         if (out_mode == 0)
-                            Cf[idx] = (float)(alpha * (double)v[j]);
+                            Cf[idx] = v[j] * (float)alpha;   // fp32 result: no FP64 work
                         else if (out_mode == 1)
                             Cd[idx] = alpha * (double)v[j];
                         else
