@@ -12,9 +12,10 @@
 //     first call); both products run on the bf16 tensor cores with 3 + 3
 //     slices (FP32-accurate);
 //   * M = X Psi; repeat { R = Psi - 1/2 M - K M (FP64-accurate, ww_ozaki.cu);
-//     M += X R } max_refine times; the last residual is checked against
-//     refine_tol (relative to max|Psi| + max|M| per column) and a miss raises
-//     WW_ERR_NO_CONVERGENCE;
+//     M += X R } max_refine times; the residual after the last correction
+//     (estimated from the observed contraction, see mixed_solve) is checked
+//     against refine_tol (relative to max|Psi| + max|M| per column) and a
+//     miss raises WW_ERR_NO_CONVERGENCE;
 //   * G gamma is FP64-accurate (ww_ozaki.cu).
 // Single-column solves (the base state) use FP64 residuals and G products on
 // the FP64 pipe instead, where a tensor-core tile would be 99% padding.
@@ -54,7 +55,7 @@ struct Mixed {
     double *R, *Psi;                       // N x NC
     double *psis;                          // N... column scales of Psi
     int *psie;
-    unsigned long long *colmax;            // NC
+    unsigned long long *colmax, *colmax0;  // NC: max|R_j| of the last and the previous residual
     double *ratio;                         // worst final residual ratio (device, bits as u64)
     unsigned *nsres;                       // worst max|I - A X| before an update (fp32 bits)
     int *err;
@@ -67,13 +68,19 @@ __global__ void k_scaled_identity(float *X, int N, float v) {
     if (i < (size_t)N * N) X[i] = ((i % N) == (i / N)) ? v : 0.f;
 }
 
-// per-column residual check: ratio = max|R_j| / (max|Psi_j| + max|M_j|), with the
-// power-of-two column scales of Psi and M as the (within 2x) maxima
-__global__ void k_check(const unsigned long long *colmax, const double *psis, const double *ms, int ncols, double tol,
-                        unsigned long long *ratio, int *status) {
+// per-column residual check: ratio = r_j / (max|Psi_j| + max|M_j|), where
+// r_j = max|R_j| of the last residual, or, given the previous one, the
+// contraction estimate max|R_j|^2 / max|R_prev,j| of the residual after the
+// last correction
+__global__ void k_check(const unsigned long long *colmax, const unsigned long long *colmax_prev, const double *psis,
+                        const double *ms, int ncols, double tol, unsigned long long *ratio, int *status) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= ncols) return;
-    const double r = __longlong_as_double((long long)colmax[j]);
+    double r = __longlong_as_double((long long)colmax[j]);
+    if (colmax_prev) {
+        const double rp = __longlong_as_double((long long)colmax_prev[j]);
+        r = rp > 0 ? r * (r / rp) : r;
+    }
     const double den = psis[j] + ms[j];
     const double q = den > 0 ? r / den : (r > 0 ? 1.0 : 0.0);
     atomicMax(ratio, (unsigned long long)__double_as_longlong(q));
@@ -123,23 +130,24 @@ int ns_step(Ctx *c, bool record) {
     return WW_OK;
 }
 
-// R = Psi - A M on the FP64 pipe (narrow blocks)
-int resid_fp64(Ctx *c, const double *M, int ncols) {
+// R = Psi - A M on the FP64 pipe (narrow blocks); colmax <- max|R_j|
+int resid_fp64(Ctx *c, const double *M, int ncols, unsigned long long *colmax) {
     Mixed *m = c->mx;
     const int N = c->N;
     WW_CUDA_TRY(cudaMemcpyAsync(m->R, m->Psi, sizeof(double) * N * ncols, cudaMemcpyDeviceToDevice, c->stream));
     WW_TRY(dgemm(c->stream, N, ncols, N, -1.0, c->A, N, M, N, 1.0, m->R, N));
-    k_colmax<<<ncols, 256, 0, c->stream>>>(m->R, N, m->colmax);
+    k_colmax<<<ncols, 256, 0, c->stream>>>(m->R, N, colmax);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
 
-// R = Psi - A M FP64-accurately on the tensor cores (wide blocks)
-int resid_ozaki(Ctx *c, const double *M, int ncols) {
+// R = Psi - A M FP64-accurately on the tensor cores (wide blocks); colmax
+// (zeroed by the caller) <- max|R_j|
+int resid_ozaki(Ctx *c, const double *M, int ncols, unsigned long long *colmax) {
     Mixed *m = c->mx;
     const int N = c->N;
     WW_TRY(ozaki_digits(c->stream, M, N, ncols, N, 1, 0.f, m->Re, m->Rs, m->Rd));
-    WW_TRY(ozaki_gemm(c->stream, m->Kd, m->Ks, m->Rd, m->Rs, N, ncols, N, 1, m->R, N, m->Psi, N, M, N, m->colmax,
+    WW_TRY(ozaki_gemm(c->stream, m->Kd, m->Ks, m->Rd, m->Rs, N, ncols, N, 1, m->R, N, m->Psi, N, M, N, colmax,
                       m->err));
     return WW_OK;
 }
@@ -175,6 +183,7 @@ int mixed_create(Ctx *c) {
     MA(m->psis, NC);
     MA(m->psie, NC);
     MA(m->colmax, NC);
+    MA(m->colmax0, NC);
     MA(m->ratio, 1);
     MA(m->nsres, 1);
     MA(m->err, 1);
@@ -190,8 +199,8 @@ void mixed_destroy(Ctx *c) {
     Mixed *m = c->mx;
     if (!m) return;
     void *ptrs[] = {m->X,  m->P,  m->Aslc, m->XslcB, m->XslcA, m->Wslc, m->Kd,  m->Gd,   m->Ks,     m->Gs,    m->Ke,
-                    m->Ge, m->Rd, m->Rs,   m->Re,    m->Bslc,  m->R,    m->Psi, m->psis, m->psie, m->colmax, m->ratio,
-                    m->nsres, m->err};
+                    m->Ge, m->Rd, m->Rs,   m->Re,    m->Bslc,  m->R,    m->Psi, m->psis, m->psie, m->colmax, m->colmax0,
+                    m->ratio, m->nsres, m->err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -232,22 +241,36 @@ int mixed_solve(Ctx *c, double *B, int ncols) {
     // M = X Psi
     WW_TRY(tc_slice_f64(s, m->Psi, N, ncols, N, 0, 0.f, 3, m->Bslc));
     WW_TRY(tc_gemm_f32acc(s, m->XslcA, m->Bslc, N, ncols, N, 1, nullptr, B, N, 1.0, m->err));
-    for (int it = 0; it <= c->max_refine; ++it) {
-        if (!narrow) WW_CUDA_TRY(cudaMemsetAsync(m->colmax, 0, sizeof(unsigned long long) * ncols, s));
-        if (narrow)
-            WW_TRY(resid_fp64(c, B, ncols));
-        else
-            WW_TRY(resid_ozaki(c, B, ncols));
-        if (it == c->max_refine) break;
+    // R_k = Psi - A M_k (FP64-accurate), M_{k+1} = M_k + X R_k.  With two or
+    // more corrections the final residual is not recomputed: per column it is
+    // estimated as |R_last| rho with the observed contraction rho = |R_last| /
+    // |R_prev| (the iteration is linear with a fixed X), which saves one
+    // FP64-accurate product per solve.  With one correction it is recomputed.
+    unsigned long long *cm_prev = m->colmax0, *cm = m->colmax;
+    const int nres = c->max_refine >= 2 ? c->max_refine : c->max_refine + 1;
+    for (int it = 0; it < nres; ++it) {
+        if (it > 0) {
+            unsigned long long *t = cm_prev;
+            cm_prev = cm;
+            cm = t;
+        }
+        if (narrow) {
+            WW_TRY(resid_fp64(c, B, ncols, cm));
+        } else {
+            WW_CUDA_TRY(cudaMemsetAsync(cm, 0, sizeof(unsigned long long) * ncols, s));
+            WW_TRY(resid_ozaki(c, B, ncols, cm));
+        }
+        if (it == c->max_refine) break;   // one correction: the last residual is the check
         WW_TRY(tc_slice_f64(s, m->R, N, ncols, N, 0, 0.f, 3, m->Bslc));
         WW_TRY(tc_gemm_f32acc(s, m->XslcA, m->Bslc, N, ncols, N, 2, nullptr, B, N, 1.0, m->err));   // M += X R
     }
-    // convergence of the last residual (scales of M: column max of the solution)
+    // convergence test (scales of M: column max of the solution)
     k_colmax<<<ncols, 256, 0, s>>>(B, N, reinterpret_cast<unsigned long long *>(m->Rs));
     k_colscale_from_max<<<(ncols + 255) / 256, 256, 0, s>>>(reinterpret_cast<unsigned long long *>(m->Rs), ncols,
                                                             m->Rs);
-    k_check<<<(ncols + 127) / 128, 128, 0, s>>>(m->colmax, m->psis, m->Rs, ncols, c->refine_tol,
-                                                reinterpret_cast<unsigned long long *>(m->ratio), c->status);
+    k_check<<<(ncols + 127) / 128, 128, 0, s>>>(cm, c->max_refine >= 2 ? cm_prev : nullptr, m->psis, m->Rs, ncols,
+                                                c->refine_tol, reinterpret_cast<unsigned long long *>(m->ratio),
+                                                c->status);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }

@@ -70,44 +70,54 @@ __device__ __forceinline__ void mul_deriv(typename AR::C *s, int N) {
 // ------------------------------------------------------------------------
 template <class AR>
 __global__ void k_base_geometry(const double *__restrict__ eta_in, const double *__restrict__ phi_in,
-                                int with_phi, int N, int logN, int deep, const void *__restrict__ tw,
+                                int with_phi, int N, int logN, int deep, int with_curv, const void *__restrict__ tw,
                                 double *eta, double *eta_x, double *eta_xx, double *phi_s, double *curv,
                                 double *E, double *Einv, int *status) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw);
+    typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw), *z = s + N;
     int bad = 0;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         double e = eta_in[j];
         double p = with_phi ? phi_in[j] : 0.0;
         if (!isfinite(e) || !isfinite(p) || (!deep && e <= 0.0)) bad = 1;
         eta[j] = e;
-        E[j] = exp(e);
-        Einv[j] = exp(-e);
+        const double ee = exp(e);
+        E[j] = ee;
+        Einv[j] = 1.0 / ee;
         s[j] = AR::mk(e, p);
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_GEOMETRY);
     AR::fft(s, N, logN, tw, false);
-    mul_deriv<AR>(s, N);
+    // d/dx and d2/dx2 (= d/dx applied twice, Nyquist zero) of eta + i phi
+    const float invN = 1.0f / (float)N;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const int k = wavenum(j, N);
+        const bool nyq = (j == (N >> 1));
+        const typename AR::C v = AR::ikscale(s[j], k, invN);
+        s[j] = nyq ? AR::zero() : v;
+        z[j] = nyq ? AR::zero() : AR::ikscale(v, k, 1.0f);
+    }
     __syncthreads();
     AR::fft(s, N, logN, tw, true);
-    // s = eta' + i phi'
+    AR::fft(z, N, logN, tw, true);
+    // s = eta' + i phi',  z = eta'' + i phi''
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         const double2 v = AR::get(s[j]);
-        const double ex = v.x;
-        eta_x[j] = ex;
+        eta_x[j] = v.x;
         phi_s[j] = v.y;
-        s[j] = AR::mk(ex / sqrt(1.0 + ex * ex), ex);   // (eta'/sqrt(1+eta'^2)) + i eta'
+        eta_xx[j] = AR::get(z[j]).x;
+        if (with_curv)
+            s[j] = AR::mk(v.x / sqrt(1.0 + v.x * v.x), 0.0);   // eta'/sqrt(1+eta'^2)
+        else
+            curv[j] = 0.0;   // the curvature term is multiplied by tau = 0
     }
+    if (!with_curv) return;
     __syncthreads();
     AR::fft(s, N, logN, tw, false);
     mul_deriv<AR>(s, N);
     __syncthreads();
     AR::fft(s, N, logN, tw, true);
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        const double2 v = AR::get(s[j]);
-        curv[j] = v.x;
-        eta_xx[j] = v.y;
-    }
+    for (int j = threadIdx.x; j < N; j += blockDim.x) curv[j] = AR::get(s[j]).x;
 }
 
 // ------------------------------------------------------------------------
@@ -125,6 +135,25 @@ __global__ void k_gamma(const double *__restrict__ M, int ncols, int N, int logN
     __syncthreads();
     AR::fft(s, N, logN, tw, false);
     const float invN = 1.0f / (float)N;
+    if (!hasb) {
+        // one real column: gamma and 1/2 H gamma come back as the real and
+        // imaginary parts of one inverse transform of (ik + i |k|/2) mu^
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            const int k = wavenum(j, N);
+            const bool nyq = (j == (N >> 1));
+            const typename AR::C v = s[j];
+            s[j] = nyq ? AR::zero()
+                       : AR::add(AR::ikscale(v, k, invN), AR::ikscale(AR::scale(v, 0.5 * fabs((double)k)), 1, invN));
+        }
+        __syncthreads();
+        AR::fft(s, N, logN, tw, true);
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            const double2 g = AR::get(s[j]);
+            Gam[(size_t)ca * N + j] = g.x;
+            Gout[(size_t)ca * N + j] = g.y;
+        }
+        return;
+    }
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         const int k = wavenum(j, N);
         const bool nyq = (j == (N >> 1));
@@ -410,7 +439,7 @@ int set_smem(K kernel, size_t bytes) {
 // ==========================================================================
 int prepare_spectral(Ctx *c) {
     const size_t one = sizeof(double2) * c->N, two = 2 * one;
-    WW_TRY(set_smem(k_base_geometry<ArF64>, one));
+    WW_TRY(set_smem(k_base_geometry<ArF64>, two));
     WW_TRY(set_smem(k_base_rhs<ArF64>, one));
     WW_TRY(set_smem(k_gamma<ArF64>, two));
     WW_TRY(set_smem(k_col_rhs<ArF64>, two));
@@ -428,9 +457,9 @@ int prepare_spectral(Ctx *c) {
 static bool use_df(const Ctx *c) { return c->precision == WW_MIXED && c->twd != nullptr; }
 
 int launch_base_geometry(Ctx *c, const double *eta, const double *phi, int with_phi) {
-    size_t sm = sizeof(double2) * c->N;
+    size_t sm = 2 * sizeof(double2) * c->N;
     k_base_geometry<ArF64><<<1, FFT_THREADS, sm, c->stream>>>(eta, phi, with_phi, c->N, c->logN, c->deep ? 1 : 0,
-                                                                 c->tw, c->eta, c->eta_x, c->eta_xx, c->phi_s,
+                                                                 c->tau != 0.0 ? 1 : 0, c->tw, c->eta, c->eta_x, c->eta_xx, c->phi_s,
                                                                  c->curv, c->E, c->Einv, c->status);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
