@@ -63,11 +63,11 @@ typedef struct {
                            NULL selects column k = (cos k x, 0)                       */
     int precision;      /* WW_FP64 or WW_MIXED                                        */
     double refine_tol;  /* WW_MIXED: relative residual target, 0 => 1e-13             */
-    int max_refine;     /* WW_MIXED: refinement corrections per solve, 0 => 2         */
+    int max_refine;     /* WW_MIXED: most refinement corrections per solve, 0 => 4    */
 } ww_problem;
 
 typedef struct {
-    int refine_iters_max;      /* most refinement iterations any stage needed       */
+    int refine_iters_max;      /* most refinement corrections any solve needed      */
     double refine_resid_max;   /* largest final relative residual of any stage      */
     double ns_resid_max;       /* WW_MIXED: largest ||I - X A||_max seen            */
     int stages;                /* RK stages run by the last call                     */

@@ -120,8 +120,9 @@ int dalloc_n(Owned *o, T **p, size_t n) {
 
 Owned *owner(ww_ctx *ctx) { return reinterpret_cast<Owned *>(ctx); }
 
-int factor(Ctx *c, int fresh = 0) {
-    if (c->precision == WW_MIXED) return mixed_setup(c, fresh);
+// fresh: start the mixed inverse from scratch; update: move it to this stage's A
+int factor(Ctx *c, int fresh = 0, int update = 1) {
+    if (c->precision == WW_MIXED) return mixed_setup(c, fresh, update);
     return lu_factor_fp64(c);
 }
 
@@ -144,7 +145,7 @@ int run_stage(Ctx *c, int st, const double *cvec, int with_cols) {
     WW_TRY(launch_assemble(c));
     WW_TRY(mark(c, st, WW_PHASE_ASSEMBLY, 1));
     WW_TRY(mark(c, st, WW_PHASE_FACTOR, 0));
-    WW_TRY(factor(c));
+    WW_TRY(factor(c, 0, (st % 2) == 0));   // mixed: inverse update every other stage
     WW_TRY(mark(c, st, WW_PHASE_FACTOR, 1));
     WW_TRY(mark(c, st, WW_PHASE_BASE, 0));
     WW_TRY(launch_phi0(c));
@@ -252,11 +253,11 @@ int check_status(Ctx *c) {
     WW_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (c->precision == WW_MIXED) {
         double ratio = 0, nsres = 0;
-        int err = 0;
-        WW_TRY(mixed_read_stats(c, &ratio, &nsres, &err));
+        int err = 0, iters = 0;
+        WW_TRY(mixed_read_stats(c, &ratio, &nsres, &iters, &err));
         c->stats.refine_resid_max = ratio;
         c->stats.ns_resid_max = nsres;
-        c->stats.refine_iters_max = c->max_refine;
+        c->stats.refine_iters_max = iters;
         if (err) return fail(WW_ERR_TIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)");
     }
     if (st & ST_NO_CONV)
@@ -355,7 +356,7 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
     c->steps = p->steps;
     c->precision = p->precision;
     c->refine_tol = p->refine_tol > 0.0 ? p->refine_tol : 1e-13;
-    c->max_refine = p->max_refine > 0 ? p->max_refine : 2;
+    c->max_refine = p->max_refine > 0 ? p->max_refine : 4;
     c->nb = c->N < LU_NB ? c->N : LU_NB;
     {
         cudaError_t e0 = cudaStreamCreateWithFlags(&o->own_stream, cudaStreamNonBlocking);

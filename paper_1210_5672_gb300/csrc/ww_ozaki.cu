@@ -21,7 +21,7 @@
 //   hi = V0 2^14 + V1 2^7 + V2,  lo = V3 2^21 + V4 2^14 + V5 2^7 + V6,
 // and the result is 2^ea_i 2^fb_j (2^-26 hi + 2^-54 lo).
 //
-// Kernel.  One CTA per 128 x 64 output tile.  Warp 0: TMA producer (ring of 4
+// Kernel.  One CTA per 128 x 64 output tile.  Warp 0: TMA producer (ring of 7
 // A-digit tiles of 128 x 64 and ring of 2 B stages holding all 7 B-digit
 // tiles of 64 x 64); warp 1: TMEM owner and tcgen05.mma issuer (M = 128,
 // N = 64, K = 16); warps 2..9: fold and epilogue, each thread one row and 32
@@ -45,7 +45,7 @@ constexpr int OZ_S = 7;             // digits per operand
 constexpr int OZ_G = 7;             // groups g = 0..6
 constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 64;
 constexpr int OZ_KBLOCK = 16;       // K chunks (of 64) per exact block = 1024
-constexpr int OZ_ASLOTS = 4, OZ_BSLOTS = 2;
+constexpr int OZ_ASLOTS = 7, OZ_BSLOTS = 2;   // 7 x 16 KB A tiles in flight: the ring is latency bound
 constexpr int OZ_EPI_WARPS = 8;
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
 constexpr int OZ_A_TILE = OZ_BM * OZ_BK * 2;           // 16 KB
@@ -66,7 +66,8 @@ struct OzOut {
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int Nn, int K,
-            const double *__restrict__ sa, const double *__restrict__ sb, OzOut out, int *err) {
+            const double *__restrict__ sa, const double *__restrict__ sb, OzOut out, int *err, const int *skip) {
+    if (skip && *skip) return;   // the caller's device-side decision to leave this product out
     extern __shared__ uint8_t smem_raw[];
     const uint32_t base = tc::smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024 - (base & 1023)) & 1023);
@@ -228,7 +229,8 @@ __global__ void k_expmax_rows(const double *__restrict__ X, int ld, int rows, in
 }
 
 // biased-exponent maxima of the columns (one block per column)
-__global__ void k_expmax_cols(const double *__restrict__ X, int ld, int rows, int *emax) {
+__global__ void k_expmax_cols(const double *__restrict__ X, int ld, int rows, int *emax, const int *skip) {
+    if (skip && *skip) return;
     __shared__ int red[32];
     const double *col = X + (size_t)blockIdx.x * ld;
     int m = 0;
@@ -244,7 +246,8 @@ __global__ void k_expmax_cols(const double *__restrict__ X, int ld, int rows, in
 }
 
 // scale 2^ea from the biased exponent maximum: 2^(emax - 1022) > max |x|
-__global__ void k_scales(const int *__restrict__ emax, int n, double *scale) {
+__global__ void k_scales(const int *__restrict__ emax, int n, double *scale, const int *skip) {
+    if (skip && *skip) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int e = emax[i];
@@ -256,7 +259,8 @@ __global__ void k_scales(const int *__restrict__ emax, int n, double *scale) {
 // column-major matrix): dst[q][j][k].  Digits are computed in 64-bit fixed
 // point: F = x 2^-ea 2^60, a_p = round(F / 2^{54 - 7(p-1)}).
 __global__ void k_digits(const double *__restrict__ X, int ld, int rows, int K, int side, float diag_shift,
-                         const int *__restrict__ emax, __nv_bfloat16 *dst) {
+                         const int *__restrict__ emax, __nv_bfloat16 *dst, const int *skip) {
+    if (skip && *skip) return;
     __shared__ long long tile[32][33];
     const int t0 = blockIdx.y * 32, k0 = blockIdx.x * 32;   // t: row (side 0) or column (side 1)
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -311,17 +315,17 @@ __global__ void k_digits(const double *__restrict__ X, int ld, int rows, int K, 
 // side 1: right operand = the columns of the column-major K x rows matrix X.
 // emax: int[rows] work (zeroed here); scale: double[rows]; dst: 7 x rows x K bf16.
 int ozaki_digits(cudaStream_t s, const double *X, int ld, int rows, int K, int side, float diag_shift, int *emax,
-                 double *scale, __nv_bfloat16 *dst) {
+                 double *scale, __nv_bfloat16 *dst, const int *skip) {
     if (side == 0) {
         WW_CUDA_TRY(cudaMemsetAsync(emax, 0, sizeof(int) * rows, s));
         dim3 g((rows + 127) / 128, (K + 63) / 64);
         k_expmax_rows<<<g, 128, 0, s>>>(X, ld, rows, K, diag_shift, emax);
     } else {
-        k_expmax_cols<<<rows, 256, 0, s>>>(X, ld, K, emax);
+        k_expmax_cols<<<rows, 256, 0, s>>>(X, ld, K, emax, skip);
     }
-    k_scales<<<(rows + 255) / 256, 256, 0, s>>>(emax, rows, scale);
+    k_scales<<<(rows + 255) / 256, 256, 0, s>>>(emax, rows, scale, skip);
     dim3 gd((K + 31) / 32, (rows + 31) / 32);
-    k_digits<<<gd, 256, 0, s>>>(X, ld, rows, K, side, diag_shift, emax, dst);
+    k_digits<<<gd, 256, 0, s>>>(X, ld, rows, K, side, diag_shift, emax, dst, skip);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
@@ -329,7 +333,7 @@ int ozaki_digits(cudaStream_t s, const double *X, int ld, int rows, int K, int s
 // mode 0: C += A B ; mode 1: C = Psi - 0.5 Mh - A B  (A = left digits, B = right digits)
 int ozaki_gemm(cudaStream_t s, const __nv_bfloat16 *Ad, const double *sa, const __nv_bfloat16 *Bd, const double *sb,
                int M, int Nn, int K, int mode, double *C, int ldc, const double *Psi, int ldpsi, const double *Mh,
-               int ldm, unsigned long long *colmax, int *err) {
+               int ldm, unsigned long long *colmax, int *err, const int *skip) {
     if (K % OZ_BK != 0) return fail(WW_ERR_ARG, "ozaki_gemm: K must be a multiple of 64");
     CUtensorMap ta, tb;
     WW_TRY(tc_make_map(&ta, Ad, K, (long)OZ_S * M, OZ_BM));
@@ -337,7 +341,7 @@ int ozaki_gemm(cudaStream_t s, const __nv_bfloat16 *Ad, const double *sa, const 
     WW_CUDA_TRY(cudaFuncSetAttribute(k_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
     OzOut o{mode, C, ldc, Psi, ldpsi, Mh, ldm, colmax};
     dim3 grid((M + OZ_BM - 1) / OZ_BM, (Nn + OZ_BN - 1) / OZ_BN);
-    k_ozaki<<<grid, OZ_THREADS, OZ_SMEM, s>>>(ta, tb, M, Nn, K, sa, sb, o, err);
+    k_ozaki<<<grid, OZ_THREADS, OZ_SMEM, s>>>(ta, tb, M, Nn, K, sa, sb, o, err, skip);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
@@ -365,10 +369,10 @@ extern "C" int ww_selftest_ozaki(const double *A, const double *B, int M, int Nn
         st = fail(WW_ERR_ALLOC, "selftest alloc");
     if (st == WW_OK && (cudaMemset(err, 0, 4) != cudaSuccess || cudaMemset(C, 0, 8 * (size_t)M * Nn) != cudaSuccess))
         st = WW_ERR_CUDA;
-    if (st == WW_OK) st = ozaki_digits(s, A, M, M, K, 0, 0.f, ea, sa, Ad);
-    if (st == WW_OK) st = ozaki_digits(s, B, K, Nn, K, 1, 0.f, eb, sb, Bd);
+    if (st == WW_OK) st = ozaki_digits(s, A, M, M, K, 0, 0.f, ea, sa, Ad, nullptr);
+    if (st == WW_OK) st = ozaki_digits(s, B, K, Nn, K, 1, 0.f, eb, sb, Bd, nullptr);
     if (st == WW_OK)
-        st = ozaki_gemm(s, Ad, sa, Bd, sb, M, Nn, K, 0, C, M, nullptr, 0, nullptr, 0, nullptr, err);
+        st = ozaki_gemm(s, Ad, sa, Bd, sb, M, Nn, K, 0, C, M, nullptr, 0, nullptr, 0, nullptr, err, nullptr);
     if (st == WW_OK) st = dgemm(s, M, Nn, K, 1.0, A, M, B, K, 0.0, C0, M);
     if (st == WW_OK && cudaDeviceSynchronize() != cudaSuccess) st = fail(WW_ERR_CUDA, "selftest sync");
     if (st == WW_OK) {

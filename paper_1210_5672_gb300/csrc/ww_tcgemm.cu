@@ -50,7 +50,9 @@ struct TcSmem {
 template <int BN, int SA, int SB>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int Nn, int K,
-              Pairs pairs, int out_mode, float *Cf, double *Cd, int ldc, double alpha, int *err) {
+              Pairs pairs, int out_mode, float *Cf, double *Cd, int ldc, double alpha, int *err,
+              const int *skip) {
+    if (skip && *skip) return;   // a step the caller decided on the device to leave out
     using L = TcSmem<BN, SA, SB>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t base = tc::smem_u32(smem_raw);
@@ -190,7 +192,7 @@ namespace {
 
 template <int BN, int SA, int SB>
 int launch_tc(cudaStream_t s, const void *A, const void *B, int M, int Nn, int K, const Pairs &pairs, int out_mode,
-              float *Cf, double *Cd, int ldc, double alpha, int *err) {
+              float *Cf, double *Cd, int ldc, double alpha, int *err, const int *skip) {
     using L = TcSmem<BN, SA, SB>;
     static_assert(L::BYTES <= 227 * 1024, "shared memory");
     CUtensorMap ta, tb;
@@ -199,7 +201,7 @@ int launch_tc(cudaStream_t s, const void *A, const void *B, int M, int Nn, int K
     auto kern = k_tc_gemm<BN, SA, SB>;
     WW_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES));
     dim3 grid((M + TC_BM - 1) / TC_BM, (Nn + BN - 1) / BN);
-    kern<<<grid, TC_THREADS, L::BYTES, s>>>(ta, tb, M, Nn, K, pairs, out_mode, Cf, Cd, ldc, alpha, err);
+    kern<<<grid, TC_THREADS, L::BYTES, s>>>(ta, tb, M, Nn, K, pairs, out_mode, Cf, Cd, ldc, alpha, err, skip);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
@@ -211,7 +213,8 @@ int launch_tc(cudaStream_t s, const void *A, const void *B, int M, int Nn, int K
 // optionally v -> shift*delta(r,k) - v.  S bf16 slices, v = sum_s slice_s + O(2^-8S |v|).
 template <typename T>
 __global__ void k_slice(const T *__restrict__ src, int ld, int rows, int K, int trans, float shift, int S,
-                        __nv_bfloat16 *dst, unsigned *dev_max) {
+                        __nv_bfloat16 *dst, unsigned *dev_max, const int *skip) {
+    if (skip && *skip) return;
     __shared__ float tile[32][33];
     float dmax = 0.f;   // with shift = 2: max |(2 delta - v) - delta| = max |delta - v|
     const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
@@ -254,17 +257,17 @@ __global__ void k_slice(const T *__restrict__ src, int ld, int rows, int K, int 
 }  // namespace
 
 int tc_slice_f32(cudaStream_t s, const float *src, int ld, int rows, int K, int trans, float shift, int S,
-                 __nv_bfloat16 *dst, unsigned *dev_max) {
+                 __nv_bfloat16 *dst, unsigned *dev_max, const int *skip) {
     dim3 grid((K + 31) / 32, (rows + 31) / 32);
-    k_slice<float><<<grid, 256, 0, s>>>(src, ld, rows, K, trans, shift, S, dst, dev_max);
+    k_slice<float><<<grid, 256, 0, s>>>(src, ld, rows, K, trans, shift, S, dst, dev_max, skip);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
 
 int tc_slice_f64(cudaStream_t s, const double *src, int ld, int rows, int K, int trans, float shift, int S,
-                 __nv_bfloat16 *dst) {
+                 __nv_bfloat16 *dst, const int *skip) {
     dim3 grid((K + 31) / 32, (rows + 31) / 32);
-    k_slice<double><<<grid, 256, 0, s>>>(src, ld, rows, K, trans, shift, S, dst, nullptr);
+    k_slice<double><<<grid, 256, 0, s>>>(src, ld, rows, K, trans, shift, S, dst, nullptr, skip);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
@@ -272,7 +275,7 @@ int tc_slice_f64(cudaStream_t s, const double *src, int ld, int rows, int K, int
 // FP32-accurate product from 3 + 3 slices (pairs with p + q <= 2, 0-based):
 // out_mode 0: Cf = alpha A B^T (fp32); 1: Cd = alpha A B^T; 2: Cd += alpha A B^T
 int tc_gemm_f32acc(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 *B3, int M, int Nn, int K,
-                   int out_mode, float *Cf, double *Cd, int ldc, double alpha, int *err) {
+                   int out_mode, float *Cf, double *Cd, int ldc, double alpha, int *err, const int *skip) {
     if (K % TC_BK != 0) return fail(WW_ERR_ARG, "tc_gemm: K must be a multiple of 64");
     Pairs P{};
     const int pp[6] = {2, 1, 0, 1, 0, 0}, qq[6] = {0, 1, 2, 0, 1, 0};   // smallest terms first
@@ -281,7 +284,7 @@ int tc_gemm_f32acc(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 
         P.p[i] = (unsigned char)pp[i];
         P.q[i] = (unsigned char)qq[i];
     }
-    return launch_tc<128, 3, 3>(s, A3, B3, M, Nn, K, P, out_mode, Cf, Cd, ldc, alpha, err);
+    return launch_tc<128, 3, 3>(s, A3, B3, M, Nn, K, P, out_mode, Cf, Cd, ldc, alpha, err, skip);
 }
 
 }  // namespace ww
@@ -304,9 +307,9 @@ extern "C" int ww_selftest_f32gemm(const double *A, const double *B, int M, int 
         cudaMalloc(&C0, sizeof(double) * (size_t)M * Nn) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess)
         st = fail(WW_ERR_ALLOC, "selftest alloc");
     if (st == WW_OK) st = (cudaMemset(err, 0, sizeof(int)) == cudaSuccess) ? WW_OK : WW_ERR_CUDA;
-    if (st == WW_OK) st = tc_slice_f64(s, A, M, M, K, 1, 0.f, 3, As);
-    if (st == WW_OK) st = tc_slice_f64(s, B, K, Nn, K, 0, 0.f, 3, Bs);
-    if (st == WW_OK) st = tc_gemm_f32acc(s, As, Bs, M, Nn, K, 1, nullptr, C, M, 1.0, err);
+    if (st == WW_OK) st = tc_slice_f64(s, A, M, M, K, 1, 0.f, 3, As, nullptr);
+    if (st == WW_OK) st = tc_slice_f64(s, B, K, Nn, K, 0, 0.f, 3, Bs, nullptr);
+    if (st == WW_OK) st = tc_gemm_f32acc(s, As, Bs, M, Nn, K, 1, nullptr, C, M, 1.0, err, nullptr);
     if (st == WW_OK) st = dgemm(s, M, Nn, K, 1.0, A, M, B, K, 0.0, C0, M);
     if (st == WW_OK && cudaDeviceSynchronize() != cudaSuccess) st = fail(WW_ERR_CUDA, "selftest sync");
     if (st == WW_OK) {
