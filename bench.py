@@ -7,6 +7,11 @@ outputs included) on the seeded N = 2048 workload (512 Fourier unknowns + T,
   python bench.py [--gpus N] [--steps K] [--warmup W] [--form mixed|fp64]
                   [--impl ours|reference] [--workload NAME]
 
+--form mixed (default) is the tensor-core form (FP32-accurate inverse, FP64-
+accurate Ozaki products, iterative refinement to a 1e-13 residual); --form
+fp64 is the plain FP64 form it is compared with (~2 minutes per Jacobian at
+N = 2048: run it with --warmup 3 --steps 1).
+
 --impl reference times the CPU FP64 oracle (the only baseline: the paper's
 code is not available) on a bounded sample of the same workload.  Under
 torchrun every rank runs an independent replica (its own seed; the path has
@@ -65,6 +70,13 @@ def barrier(ws):
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def replica_rate(local_step_s, ws, columns):
+    """Whole-job rate of ws independent replicas: each rank ran `columns` columns
+    per step in local_step_s seconds; the slowest rank's step time sets the job's."""
+    t = allmax(local_step_s, ws)
+    return t, ws * columns / t
 
 
 def allmax(x, ws):
@@ -131,25 +143,40 @@ def flush_l2(buf):
     buf.add_(1.0)   # 512 MB read + write: evicts the 129 MB L2
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the timed product
+# kernel, from the ncu captures summarised under profiles/ (None: not captured
+# since the kernel last changed).
+TRAFFIC_BYTES = {"mixed": None, "fp64": None}
+
+# slice pairs (p, q) with p + q <= 6 of the 7 x 7 integer digits: 28 bf16 GEMMs
+OZAKI_PAIRS = 28
+
+
 def roofline_for(form, timing, w, pk):
-    """Dominant kernel: the phase with the largest measured share."""
+    """Roofline of the dominant kernel, from the GKERNEL phase: the events around
+    the one product kernel of each stage's column G-apply (k_ozaki in the mixed
+    form, k_dgemm in the FP64 form; the same kernels carry the solves and the
+    FP64 factorisation), so duration = GKERNEL ms / launches."""
     N, nc = w.N, w.n + 1
-    # algorithmic work per launch of each candidate phase (DESIGN.md lists them)
+    ms, cnt = timing["gkernel"]
+    if cnt == 0:
+        return None
+    dur = ms / cnt / 1e3
+    fp64_flops = 2.0 * N * N * nc          # the FP64 product G Gamma it delivers
     if form == "fp64":
-        dom = max(("factor", "solve", "gapply", "assembly"), key=lambda p: timing[p][0])
-        flops = {"factor": 2.0 / 3.0 * N**3, "solve": 2.0 * N * N * nc, "gapply": 2.0 * N * N * nc,
-                 "assembly": 60.0 * N * N}[dom]
-        ms, cnt = timing[dom]
-        achieved = flops / (ms / cnt / 1e3) / 1e12
-        return dom, {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                     "kernel": {"factor": "k_dgemm (LU)", "solve": "k_dgemm (TRSM)", "gapply": "k_dgemm",
-                                "assembly": "k_assemble"}[dom],
-                     "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"}
-    dom = max(timing, key=lambda p: timing[p][0])
-    ms, cnt = timing[dom]
-    return dom, {"bound": "tensor", "achieved": None, "peak": pk.get("bf16_tflops"), "unit": "TFLOP/s",
-                 "frac": None, "traffic": None, "kernel": dom}
+        achieved = fp64_flops / dur / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES["fp64"], "kernel": "k_dgemm",
+                "launch_ms": dur * 1e3,
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"}
+    peak = pk.get("bf16_tflops_sustained") or 1700.0
+    src = "of measured (bf16_tflops_sustained)" if pk.get("bf16_tflops_sustained") else "of fallback (sustained)"
+    achieved = OZAKI_PAIRS * fp64_flops / dur / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": TRAFFIC_BYTES["mixed"], "kernel": "k_ozaki",
+            "launch_ms": dur * 1e3, "fp64_equivalent_tflops": fp64_flops / dur / 1e12,
+            "work": f"{OZAKI_PAIRS} bf16 digit-pair GEMMs of {N} x {nc} x {N}",
+            "peak_source": src}
 
 
 def run_ours(args):
@@ -178,7 +205,7 @@ def run_ours(args):
         ww.shoot_jacobian(ctx, ct, r, J, f)
     torch.cuda.synchronize()
     # ---- timed region: K Jacobians, L2 flushed between them (outside the events)
-    times, phase = [], {p: [0.0, 0] for p in ww.PHASES}
+    times, phase, gpu_launches = [], {p: [0.0, 0] for p in ww.PHASES}, 0
     barrier(ws)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
@@ -191,6 +218,8 @@ def run_ours(args):
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
+            # our kernels in this call: the library counts the kernel nodes it replays
+            gpu_launches += ctx.stats()["launches"]
             for p, (ms, cnt) in ctx.timing().items():
                 phase[p][0] += ms
                 phase[p][1] += cnt
@@ -198,8 +227,7 @@ def run_ours(args):
     barrier(ws)
     clocks = clk.summary()
     ctx.set_timing(False)
-    t_step = allmax(sum(times) / len(times), ws)
-    value = ws * (w.n + 1) / t_step
+    t_step, value = replica_rate(sum(times) / len(times), ws, w.n + 1)
     # ---- end to end through the host-buffer entry point (pinned host memory)
     ch = torch.tensor(c, dtype=torch.float64).pin_memory().numpy()
     rh = torch.empty(w.N, dtype=torch.float64).pin_memory().numpy()
@@ -212,13 +240,10 @@ def run_ours(args):
         t0 = time.perf_counter()
         ww.shoot_jacobian_host(ctx, ch, rh, Jh, fh)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_step = allmax(sum(e2e_t) / len(e2e_t), ws)
+    _, e2e_value = replica_rate(sum(e2e_t) / len(e2e_t), ws, w.n + 1)
     timing = {p: tuple(v) for p, v in phase.items()}
-    dom, roof = roofline_for(form, timing, w, peaks())
+    roof = roofline_for(form, timing, w, peaks())
     stats = ctx.stats()
-    # kernel launches inside the timed region: counted per stage from the step program
-    launches_per_stage = launches_in_stage(form, w)
-    gpu_launches = args.steps * (4 * w.steps * launches_per_stage + 2)
     ctx.close()
     if rank != 0:
         return None
@@ -231,7 +256,7 @@ def run_ours(args):
                    "h": w.h, "g": w.g, "tau": w.tau, "form": form, "seed": seed_used,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "flushed between timed steps (512 MB write)"},
-        "e2e": {"value": ws * (w.n + 1) / e2e_step, "unit": "Jacobian columns/s",
+        "e2e": {"value": e2e_value, "unit": "Jacobian columns/s",
                 "h2d_bytes_per_step": 8 * (w.n + 1), "d2h_bytes_per_step": 8 * (w.N + w.N * (w.n + 1) + 1)},
         "roofline": roof,
         "phases_ms_per_step": {p: v[0] / args.steps for p, v in timing.items()},
@@ -242,20 +267,6 @@ def run_ours(args):
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(w, c)
     return out
-
-
-def launches_in_stage(form, w):
-    """Kernel launches of one RK stage of the step program (see ww_api.cu)."""
-    N, nb = w.N, min(64, w.N)
-    nblk = (N + nb - 1) // nb
-    if form == "fp64":
-        lu = 3 * (nblk - 1) + 1 + (nblk - 1)          # diag + 2 applies + dgemm per panel
-        solve = 2 * (2 * nblk - 1)                    # apply + dgemm per block, both triangles
-        per = 1 + 1 + lu                              # geometry, assembly, LU
-        per += 1 + solve + 1 + 1 + 1                  # base: copy, solve, gamma, gemv, rhs
-        per += 1 + solve + 1 + 1 + 1                  # columns: psi, solve, gamma, gemm, rhs
-        return per
-    return 0
 
 
 def cpu_baseline(w, c, target_s=20.0):
@@ -316,10 +327,10 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="fp64", choices=["mixed", "fp64"])
+    ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--workload", default=W.LARGE.name, choices=sorted(W.ALL))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rk-steps", type=int, default=0,

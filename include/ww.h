@@ -71,6 +71,9 @@ typedef struct {
     double refine_resid_max;   /* largest final relative residual of any stage      */
     double ns_resid_max;       /* WW_MIXED: largest ||I - X A||_max seen            */
     int stages;                /* RK stages run by the last call                     */
+    long long launches;        /* kernels launched by the last shoot / shoot_jacobian
+                                  (graph kernel nodes x replays + outputs; -1 when
+                                  the legacy stream forced direct launches)        */
 } ww_stats;
 
 typedef struct ww_ctx ww_ctx;
@@ -105,7 +108,10 @@ const char *ww_last_error(void);
 #define WW_PHASE_COLRHS     4  /* variational RHS + RK update kernel            */
 #define WW_PHASE_GAMMA      5  /* gamma = mu', H gamma for the n+1 columns      */
 #define WW_PHASE_BASE       6  /* base-state chain (geometry .. base RHS)       */
-#define WW_NPHASE           7
+#define WW_PHASE_GKERNEL    7  /* the single product kernel inside GAPPLY (the
+                                  FP64 GEMM, or the MIXED Ozaki tensor-core GEMM
+                                  without its operand split)                    */
+#define WW_NPHASE           8
 int ww_set_timing(ww_ctx *ctx, int enable);
 int ww_get_timing(const ww_ctx *ctx, double *ms /* WW_NPHASE */, int *launches /* WW_NPHASE */);
 

@@ -37,7 +37,7 @@ EXPORTS = ("ww_create", "ww_destroy", "ww_set_stream", "ww_get_stats", "ww_last_
            "ww_get_timing", "dtn_setup", "dtn_apply", "shoot", "shoot_jacobian", "shoot_jacobian_host",
            "objective_and_grad", "dtn_apply_static", "ww_selftest_f32gemm", "ww_selftest_ozaki")
 STATIC_MAX_N, STATIC_MAX_RHS = 256, 64
-PHASES = ("assembly", "factor", "solve", "gapply", "colrhs", "gamma", "base")
+PHASES = ("assembly", "factor", "solve", "gapply", "colrhs", "gamma", "base", "gkernel")
 
 
 class WWError(RuntimeError):
@@ -57,7 +57,7 @@ class _Problem(C.Structure):
 class Stats(C.Structure):
     _fields_ = [
         ("refine_iters_max", C.c_int), ("refine_resid_max", C.c_double), ("ns_resid_max", C.c_double),
-        ("stages", C.c_int),
+        ("stages", C.c_int), ("launches", C.c_longlong),
     ]
 
     def as_dict(self):

@@ -72,12 +72,29 @@ struct StepGraph {
     cudaGraph_t graph = nullptr;              // kept alive: its event nodes are re-pointed per replay
     cudaGraphExec_t exec = nullptr;
     std::vector<std::pair<cudaGraphNode_t, int>> ev_nodes;   // node -> flat event slot
+    int nkern = 0;                            // kernel nodes (launches per replay)
 };
+
+int count_kernel_nodes(cudaGraph_t g, int *out) {
+    size_t nn = 0;
+    WW_CUDA_TRY(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    WW_CUDA_TRY(cudaGraphGetNodes(g, nodes.data(), &nn));
+    int k = 0;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        WW_CUDA_TRY(cudaGraphNodeGetType(nd, &t));
+        if (t == cudaGraphNodeTypeKernel) ++k;
+    }
+    *out = k;
+    return WW_OK;
+}
 
 struct Owned {
     Ctx c;
     double *cbuf = nullptr, *rbuf = nullptr, *Jbuf = nullptr, *fbuf = nullptr;
     StepGraph graphs[2][2];                   // [with_columns][timing]
+    StepGraph prologue[2];                    // [with_columns]: initial data (+ the mixed inverse)
     cudaStream_t own_stream = nullptr;        // created by ww_create, used unless ww_set_stream overrides
     std::vector<void *> allocs;
     // phase timing
@@ -131,11 +148,20 @@ int solve(Ctx *c, double *B, int ncols) {
     return lu_solve_fp64(c, B, ncols);
 }
 
-// Gout[:, col0 : col0+ncols] += G Gam[:, col0 : ...]
-int apply_G(Ctx *c, int col0, int ncols) {
-    if (c->precision == WW_MIXED) return mixed_apply_G(c, col0, ncols);
-    return dgemm(c->stream, c->N, ncols, c->N, 1.0, c->G, c->N, c->Gam + (size_t)col0 * c->N, c->N, 1.0,
-                 c->Gout + (size_t)col0 * c->N, c->N);
+// Gout[:, col0 : col0+ncols] += G Gam[:, col0 : ...]; st >= 0 times the product kernel
+int apply_G(Ctx *c, int col0, int ncols, int st = -1) {
+    if (c->precision == WW_MIXED) {
+        WW_TRY(mixed_apply_G(c, col0, ncols, 0));                 // operand split (none when narrow)
+        if (st >= 0) WW_TRY(mark(c, st, WW_PHASE_GKERNEL, 0));
+        WW_TRY(mixed_apply_G(c, col0, ncols, 1));                 // the product
+        if (st >= 0) WW_TRY(mark(c, st, WW_PHASE_GKERNEL, 1));
+        return WW_OK;
+    }
+    if (st >= 0) WW_TRY(mark(c, st, WW_PHASE_GKERNEL, 0));
+    WW_TRY(dgemm(c->stream, c->N, ncols, c->N, 1.0, c->G, c->N, c->Gam + (size_t)col0 * c->N, c->N, 1.0,
+                 c->Gout + (size_t)col0 * c->N, c->N));
+    if (st >= 0) WW_TRY(mark(c, st, WW_PHASE_GKERNEL, 1));
+    return WW_OK;
 }
 
 // one RK4 stage; cvec is the context's device copy of c (T = cvec[0])
@@ -163,7 +189,7 @@ int run_stage(Ctx *c, int st, const double *cvec, int with_cols) {
         WW_TRY(launch_gamma(c, 1, c->nc));
         WW_TRY(mark(c, st, WW_PHASE_GAMMA, 1));
         WW_TRY(mark(c, st, WW_PHASE_GAPPLY, 0));
-        WW_TRY(apply_G(c, 1, c->nc));
+        WW_TRY(apply_G(c, 1, c->nc, st));
         WW_TRY(mark(c, st, WW_PHASE_GAPPLY, 1));
         WW_TRY(mark(c, st, WW_PHASE_COLRHS, 0));
         WW_TRY(launch_col_rhs(c, st, cvec));
@@ -208,12 +234,48 @@ int build_step_graph(Owned *o, int with_cols) {
             return fail(WW_ERR_CUDA, "phase timing: no event-record nodes in the captured step");
         }
     }
+    WW_TRY(count_kernel_nodes(g, &sg.nkern));
     e = cudaGraphInstantiate(&sg.exec, g, 0);
     if (e != cudaSuccess) {
         cudaGraphDestroy(g);
         return fail(WW_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
     sg.graph = g;
+    return WW_OK;
+}
+
+// initial data (and, in WW_MIXED, the approximate inverse of the initial
+// surface): one graph per context, replayed at the start of every shot
+int prologue(Ctx *c, const double *cvec, int with_cols) {
+    WW_TRY(launch_initial(c, cvec, with_cols));
+    if (c->precision == WW_MIXED) {
+        WW_TRY(launch_base_geometry(c, c->Ys, c->Ys + c->N, 1));
+        WW_TRY(launch_assemble(c));
+        WW_TRY(factor(c, 1));
+    }
+    return WW_OK;
+}
+
+int run_prologue(Owned *o, int with_cols) {
+    Ctx *c = &o->c;
+    if (c->stream == nullptr) return prologue(c, o->cbuf, with_cols);
+    StepGraph &pg = o->prologue[with_cols];
+    if (!pg.exec) {
+        cudaGraph_t g = nullptr;
+        WW_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        int st = prologue(c, o->cbuf, with_cols);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (st != WW_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return fail(WW_ERR_CUDA, std::string("prologue capture: ") + cudaGetErrorString(e));
+        WW_TRY(count_kernel_nodes(g, &pg.nkern));
+        e = cudaGraphInstantiate(&pg.exec, g, 0);
+        pg.graph = g;
+        if (e != cudaSuccess) return fail(WW_ERR_CUDA, std::string("prologue instantiate: ") + cudaGetErrorString(e));
+    }
+    WW_CUDA_TRY(cudaGraphLaunch(pg.exec, c->stream));
     return WW_OK;
 }
 
@@ -275,13 +337,7 @@ int run_shot(Owned *o, const double *cvec, bool c_on_host, double *r, double *J,
     WW_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     WW_CUDA_TRY(cudaMemcpyAsync(o->cbuf, cvec, sizeof(double) * (c->n + 1),
                                 c_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
-    WW_TRY(launch_initial(c, o->cbuf, with_cols));
-    if (c->precision == WW_MIXED) {
-        // approximate inverse for the initial surface, before the step program
-        WW_TRY(launch_base_geometry(c, c->Ys, c->Ys + c->N, 1));
-        WW_TRY(launch_assemble(c));
-        WW_TRY(factor(c, 1));
-    }
+    WW_TRY(run_prologue(o, with_cols));
     if (o->timing) WW_TRY(ensure_timing_events(o));
     o->marked = 0;
     if (c->stream == nullptr) {
@@ -296,7 +352,7 @@ int run_shot(Owned *o, const double *cvec, bool c_on_host, double *r, double *J,
         if (o->timing)
             for (int p = 0; p < NPH; ++p)
                 if (with_cols || (p != WW_PHASE_SOLVE && p != WW_PHASE_GAMMA && p != WW_PHASE_GAPPLY &&
-                                  p != WW_PHASE_COLRHS))
+                                  p != WW_PHASE_COLRHS && p != WW_PHASE_GKERNEL))
                     o->marked |= 1u << p;
         for (int s = 0; s < c->steps; ++s) {
             if (o->timing)
@@ -308,6 +364,11 @@ int run_shot(Owned *o, const double *cvec, bool c_on_host, double *r, double *J,
     }
     WW_TRY(launch_outputs(c, r, J, f, with_cols));
     c->stats.stages = 4 * c->steps;
+    if (c->stream == nullptr)
+        c->stats.launches = -1;   // direct launches are not counted
+    else
+        c->stats.launches = (long long)o->prologue[with_cols].nkern +
+                            (long long)c->steps * o->graphs[with_cols][o->timing ? 1 : 0].nkern + (with_cols ? 2 : 1);
     c->dtn_ready = false;   // the operator now belongs to the last stage's surface
     WW_TRY(check_status(c));
     if (o->timing) WW_TRY(collect_timing(o));
@@ -457,11 +518,14 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
 void ww_destroy(ww_ctx *ctx) {
     if (!ctx) return;
     Owned *o = owner(ctx);
-    for (int w = 0; w < 2; ++w)
+    for (int w = 0; w < 2; ++w) {
         for (int t = 0; t < 2; ++t) {
             if (o->graphs[w][t].exec) cudaGraphExecDestroy(o->graphs[w][t].exec);
             if (o->graphs[w][t].graph) cudaGraphDestroy(o->graphs[w][t].graph);
         }
+        if (o->prologue[w].exec) cudaGraphExecDestroy(o->prologue[w].exec);
+        if (o->prologue[w].graph) cudaGraphDestroy(o->prologue[w].graph);
+    }
     for (cudaEvent_t ev : o->placeholder)
         if (ev) cudaEventDestroy(ev);
     for (cudaEvent_t ev : o->pool) cudaEventDestroy(ev);

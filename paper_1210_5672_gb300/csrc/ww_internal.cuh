@@ -177,10 +177,11 @@ int lu_solve_fp64(Ctx *c, double *B, int ncols);     // B <- A^{-1} B using the 
 
 // mixed precision (ww_mixed.cu)
 int mixed_create(Ctx *c);
+int tc_init();   // resolves the tensor-map encoder (called before any capture)
 void mixed_destroy(Ctx *c);
 int mixed_setup(Ctx *c, int fresh, int update);      // after assembly: operands, inverse update
 int mixed_read_stats(Ctx *c, double *ratio, double *nsres, int *iters, int *err);
 int mixed_solve(Ctx *c, double *B, int ncols);       // B <- A^{-1} B (refined)
-int mixed_apply_G(Ctx *c, int col0, int ncols);      // Gout += G Gam (FP64-accurate)
+int mixed_apply_G(Ctx *c, int col0, int ncols, int part);   // Gout += G Gam (part 0 split, 1 product; FP64-accurate)
 
 }  // namespace ww

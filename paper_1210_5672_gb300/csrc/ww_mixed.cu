@@ -266,6 +266,7 @@ int ns_step(Ctx *c, bool record, const int *skip) {
 }  // namespace
 
 int mixed_create(Ctx *c) {
+    WW_TRY(tc_init());
     Mixed *m = new Mixed();
     memset(m, 0, sizeof(Mixed));
     c->mx = m;
@@ -417,13 +418,14 @@ int mixed_solve(Ctx *c, double *B, int ncols) {
 }
 
 // Gout[:, col0 .. col0+ncols) += G Gam[:, col0 ..]
-int mixed_apply_G(Ctx *c, int col0, int ncols) {
+// part 0: split Gam into digits; part 1: the product (the two run back to back)
+int mixed_apply_G(Ctx *c, int col0, int ncols, int part) {
     Mixed *m = c->mx;
     const int N = c->N;
     const double *Gam = c->Gam + (size_t)col0 * N;
     double *Out = c->Gout + (size_t)col0 * N;
-    if (ncols <= SMALL_COLS) return dgemm(c->stream, N, ncols, N, 1.0, c->G, N, Gam, N, 1.0, Out, N);
-    WW_TRY(ozaki_digits(c->stream, Gam, N, ncols, N, 1, 0.f, m->Re, m->Rs, m->Rd, nullptr));
+    if (ncols <= SMALL_COLS) return part == 0 ? WW_OK : dgemm(c->stream, N, ncols, N, 1.0, c->G, N, Gam, N, 1.0, Out, N);
+    if (part == 0) return ozaki_digits(c->stream, Gam, N, ncols, N, 1, 0.f, m->Re, m->Rs, m->Rd, nullptr);
     return ozaki_gemm(c->stream, m->Gd, m->Gs, m->Rd, m->Rs, N, ncols, N, 0, Out, N, nullptr, 0, nullptr, 0, nullptr,
                       m->err, nullptr);
 }

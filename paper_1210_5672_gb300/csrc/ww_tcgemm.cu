@@ -171,6 +171,9 @@ int get_encoder() {
 
 }  // namespace
 
+// resolve the driver's tensor-map encoder outside any stream capture
+int tc_init() { return get_encoder(); }
+
 // 2-D bf16 tensor [rows][K] (K contiguous), tile box {64, box_rows}, 128-byte swizzle
 int tc_make_map(CUtensorMap *map, const void *ptr, int K, long rows, int box_rows) {
     WW_TRY(get_encoder());

@@ -267,3 +267,29 @@ def test_mixed_dtn_apply_matches_oracle(ww):
     ref = O.dtn(eta, phi, h)
     for a, b in zip(got, ref):
         assert rel(a, b) < 1e-12
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_phase_timing_and_launch_count(ww, mixed):
+    """Every phase is timed once per RK stage; the product-kernel phase sits inside
+    the G-apply phase; the library's launch count covers all stages."""
+    w = W.shrink(W.SMALL, N=128, n=12, steps=4)
+    c, _ = W.coefficients(w)
+    c[0] = stable_T(w.N, w.steps)
+    prec = ww.WW_MIXED if mixed else ww.WW_FP64
+    with ww.Context(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps, precision=prec) as ctx:
+        ctx.set_timing(True)
+        r, J, f = ctx.empty_outputs()
+        ww.shoot_jacobian(ctx, dev(c), r, J, f)
+        t, st = ctx.timing(), ctx.stats()
+        ww.shoot(ctx, dev(c), r, f)
+        st_shoot = ctx.stats()
+    stages = 4 * w.steps
+    for p in ww.PHASES:
+        assert t[p][1] == stages, p
+        assert t[p][0] > 0, p
+    assert t["gkernel"][0] <= t["gapply"][0]
+    assert st["stages"] == stages
+    # at least geometry, assembly, the factor/inverse, base chain and column work per stage
+    assert st["launches"] >= 8 * stages
+    assert 0 < st_shoot["launches"] < st["launches"]
