@@ -154,60 +154,6 @@ __global__ void __launch_bounds__(256) k_lu_diag(double *A, int lda, int k0, int
     }
 }
 
-// Deterministic FP64 GEMV-like product for narrow right-hand sides (n <= 8):
-// C = alpha A B + beta C.  A block owns 16 rows; its 16 warps split K into 32
-// chunks (two per warp, half-warps over the rows, coalesced down the columns
-// of A); the partial sums are added in a fixed order in shared memory.
-constexpr int NV_ROWS = 16, NV_WARPS = 16, NV_MAXN = 8;
-
-__global__ void __launch_bounds__(512) k_dgemv_narrow(int m, int n, int k, double alpha, const double *__restrict__ A,
-                                                      int lda, const double *__restrict__ B, int ldb, double beta,
-                                                      double *C, int ldc) {
-    __shared__ double part[2 * NV_WARPS][NV_ROWS][NV_MAXN];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rl = lane & 15, sub = lane >> 4;
-    const int row = blockIdx.x * NV_ROWS + rl;
-    const int chunk = warp * 2 + sub, nchunk = 2 * NV_WARPS;
-    const int kc = (k + nchunk - 1) / nchunk;
-    const int kb = chunk * kc, ke = min(k, kb + kc);
-    double acc[NV_MAXN];
-#pragma unroll
-    for (int j = 0; j < NV_MAXN; ++j) acc[j] = 0.0;
-    if (row < m) {
-        int kk = kb;
-        // eight independent loads in flight per thread (the loop is latency bound)
-        for (; kk + 8 <= ke; kk += 8) {
-            double a[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) a[u] = A[(size_t)(kk + u) * lda + row];
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-#pragma unroll
-                for (int j = 0; j < NV_MAXN; ++j)
-                    if (j < n) acc[j] = fma(a[u], B[(size_t)j * ldb + kk + u], acc[j]);
-        }
-        for (; kk < ke; ++kk) {
-            const double a = A[(size_t)kk * lda + row];
-#pragma unroll
-            for (int j = 0; j < NV_MAXN; ++j)
-                if (j < n) acc[j] = fma(a, B[(size_t)j * ldb + kk], acc[j]);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < NV_MAXN; ++j) part[chunk][rl][j] = acc[j];
-    __syncthreads();
-    if (threadIdx.x < NV_ROWS * NV_MAXN) {
-        const int r = threadIdx.x / NV_MAXN, j = threadIdx.x % NV_MAXN;
-        const int gr = blockIdx.x * NV_ROWS + r;
-        if (gr < m && j < n) {
-            double s = 0.0;
-            for (int c = 0; c < nchunk; ++c) s += part[c][r][j];
-            double *p = C + (size_t)j * ldc + gr;
-            *p = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *p);
-        }
-    }
-}
-
 constexpr int AP_T = 16;   // columns (apply_left) / rows (apply_right) per block
 
 // B(kb x ncols, leading dim ldb) <- T * B, T kb x kb (in place).
@@ -267,11 +213,7 @@ int prepare_dense() {
 int dgemm(cudaStream_t s, int m, int n, int k, double alpha, const double *A, int lda, const double *B, int ldb,
           double beta, double *C, int ldc) {
     if (m <= 0 || n <= 0) return WW_OK;
-    if (n <= NV_MAXN) {
-        k_dgemv_narrow<<<(m + NV_ROWS - 1) / NV_ROWS, 512, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
-        WW_CUDA_TRY(cudaGetLastError());
-        return WW_OK;
-    }
+    if (n <= 8) return gemv_narrow(s, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     dim3 grid((m + GB_M - 1) / GB_M, (n + GB_N - 1) / GB_N);
     k_dgemm<<<grid, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     WW_CUDA_TRY(cudaGetLastError());

@@ -172,6 +172,15 @@ int launch_assemble(Ctx *c);
 int prepare_dense();                                 // shared-memory limit of the LU block kernel
 int dgemm(cudaStream_t s, int m, int n, int k, double alpha, const double *A, int lda, const double *B,
           int ldb, double beta, double *C, int ldc);
+// narrow products (n <= 8 columns) on the CUDA cores, deterministic (ww_gemv.cu):
+// C = alpha A B + beta C (FP64); C = A B + beta C with the FP32 matrix A;
+// R = Psi - A B (FP64).  A non-null skip that reads nonzero leaves the call out.
+int gemv_narrow(cudaStream_t s, int m, int n, int k, double alpha, const double *A, int lda, const double *B, int ldb,
+                double beta, double *C, int ldc, const int *skip = nullptr);
+int gemv_narrow_f32(cudaStream_t s, int m, int n, int k, const float *A, int lda, const double *B, int ldb,
+                    double beta, double *C, int ldc, const int *skip = nullptr);
+int resid_narrow(cudaStream_t s, int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                 const double *Psi, int ldp, double *R, int ldr, const int *skip = nullptr);
 int lu_factor_fp64(Ctx *c);
 int lu_solve_fp64(Ctx *c, double *B, int ncols);     // B <- A^{-1} B using the factors in c->A
 

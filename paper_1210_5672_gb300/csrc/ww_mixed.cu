@@ -155,87 +155,6 @@ __global__ void k_converged(const unsigned long long *cm, const unsigned long lo
     }
 }
 
-// Narrow blocks (ncols <= 8): deterministic GEMV-like kernels, one block per
-// 16 rows, 16 warps splitting K into 32 chunks, partial sums added in a fixed
-// order.  k_sgemv_narrow: Y (=, or += when add) X R with the FP32 inverse X
-// (FP32 products and sums).  k_resid_narrow: R = Psi - A M in FP64.
-constexpr int SV_ROWS = 16, SV_WARPS = 16, SV_MAXN = 8;
-
-template <typename TA, typename TACC>
-__device__ __forceinline__ void narrow_partial(int N, int ncols, const TA *__restrict__ A,
-                                               const double *__restrict__ Bm, int row, int kb, int ke,
-                                               TACC (&acc)[SV_MAXN]) {
-#pragma unroll
-    for (int j = 0; j < SV_MAXN; ++j) acc[j] = 0;
-    if (row >= N) return;
-    int kk = kb;
-    for (; kk + 8 <= ke; kk += 8) {   // eight loads in flight per thread
-        TA a[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) a[u] = A[(size_t)(kk + u) * N + row];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-#pragma unroll
-            for (int j = 0; j < SV_MAXN; ++j)
-                if (j < ncols) acc[j] = fma((TACC)a[u], (TACC)Bm[(size_t)j * N + kk + u], acc[j]);
-    }
-    for (; kk < ke; ++kk) {
-        const TA a = A[(size_t)kk * N + row];
-#pragma unroll
-        for (int j = 0; j < SV_MAXN; ++j)
-            if (j < ncols) acc[j] = fma((TACC)a, (TACC)Bm[(size_t)j * N + kk], acc[j]);
-    }
-}
-
-__global__ void __launch_bounds__(512) k_sgemv_narrow(int N, int ncols, const float *__restrict__ X,
-                                                      const double *__restrict__ R, double *Y, int add,
-                                                      const int *skip) {
-    if (skip && *skip) return;
-    __shared__ float part[2 * SV_WARPS][SV_ROWS][SV_MAXN];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rl = lane & 15, chunk = warp * 2 + (lane >> 4), nchunk = 2 * SV_WARPS;
-    const int kc = (N + nchunk - 1) / nchunk, kb = chunk * kc, ke = min(N, kb + kc);
-    float acc[SV_MAXN];
-    narrow_partial<float, float>(N, ncols, X, R, blockIdx.x * SV_ROWS + rl, kb, ke, acc);
-#pragma unroll
-    for (int j = 0; j < SV_MAXN; ++j) part[chunk][rl][j] = acc[j];
-    __syncthreads();
-    if (threadIdx.x < SV_ROWS * SV_MAXN) {
-        const int r = threadIdx.x / SV_MAXN, j = threadIdx.x % SV_MAXN;
-        const int gr = blockIdx.x * SV_ROWS + r;
-        if (gr < N && j < ncols) {
-            float sum = 0.f;
-            for (int c = 0; c < nchunk; ++c) sum += part[c][r][j];
-            double *p = Y + (size_t)j * N + gr;
-            *p = add ? *p + (double)sum : (double)sum;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(512) k_resid_narrow(int N, int ncols, const double *__restrict__ A,
-                                                      const double *__restrict__ M, const double *__restrict__ Psi,
-                                                      double *R, const int *skip) {
-    if (skip && *skip) return;
-    __shared__ double part[2 * SV_WARPS][SV_ROWS][SV_MAXN];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rl = lane & 15, chunk = warp * 2 + (lane >> 4), nchunk = 2 * SV_WARPS;
-    const int kc = (N + nchunk - 1) / nchunk, kb = chunk * kc, ke = min(N, kb + kc);
-    double acc[SV_MAXN];
-    narrow_partial<double, double>(N, ncols, A, M, blockIdx.x * SV_ROWS + rl, kb, ke, acc);
-#pragma unroll
-    for (int j = 0; j < SV_MAXN; ++j) part[chunk][rl][j] = acc[j];
-    __syncthreads();
-    if (threadIdx.x < SV_ROWS * SV_MAXN) {
-        const int r = threadIdx.x / SV_MAXN, j = threadIdx.x % SV_MAXN;
-        const int gr = blockIdx.x * SV_ROWS + r;
-        if (gr < N && j < ncols) {
-            double sum = 0.0;
-            for (int c = 0; c < nchunk; ++c) sum += part[c][r][j];
-            R[(size_t)j * N + gr] = Psi[(size_t)j * N + gr] - sum;
-        }
-    }
-}
-
 template <typename T>
 int alloc(T **p, size_t n) {
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (n ? n : 1));
@@ -373,8 +292,7 @@ int mixed_solve(Ctx *c, double *B, int ncols) {
     WW_CUDA_TRY(cudaGetLastError());
     // M = X Psi
     if (narrow) {
-        k_sgemv_narrow<<<(N + SV_ROWS - 1) / SV_ROWS, 512, 0, s>>>(N, ncols, m->X, m->Psi, B, 0, nullptr);
-        WW_CUDA_TRY(cudaGetLastError());
+        WW_TRY(gemv_narrow_f32(s, N, ncols, N, m->X, N, m->Psi, N, 0.0, B, N));
     } else {
         WW_TRY(tc_slice_f64(s, m->Psi, N, ncols, N, 0, 0.f, 3, m->Bslc));
         WW_TRY(tc_gemm_f32acc(s, m->XslcA, m->Bslc, N, ncols, N, 1, nullptr, B, N, 1.0, m->err));
@@ -385,7 +303,7 @@ int mixed_solve(Ctx *c, double *B, int ncols) {
     for (int it = 0; it < nit; ++it) {
         // R = Psi - A M_it (FP64-accurate) and max|R_j|
         if (narrow) {
-            k_resid_narrow<<<(N + SV_ROWS - 1) / SV_ROWS, 512, 0, s>>>(N, ncols, c->A, B, m->Psi, m->R, done);
+            WW_TRY(resid_narrow(s, N, ncols, N, c->A, N, B, N, m->Psi, N, m->R, N, done));
             k_colmax<<<ncols, 256, 0, s>>>(m->R, N, cm, done);
             k_colmax<<<ncols, 256, 0, s>>>(B, N, reinterpret_cast<unsigned long long *>(m->mscale), done);
             k_colscale_from_max<<<cg, 256, 0, s>>>(reinterpret_cast<unsigned long long *>(m->mscale), ncols,
@@ -399,8 +317,7 @@ int mixed_solve(Ctx *c, double *B, int ncols) {
         }
         // M += X R
         if (narrow) {
-            k_sgemv_narrow<<<(N + SV_ROWS - 1) / SV_ROWS, 512, 0, s>>>(N, ncols, m->X, m->R, B, 1, done);
-            WW_CUDA_TRY(cudaGetLastError());
+            WW_TRY(gemv_narrow_f32(s, N, ncols, N, m->X, N, m->R, N, 1.0, B, N, done));
         } else {
             WW_TRY(tc_slice_f64(s, m->R, N, ncols, N, 0, 0.f, 3, m->Bslc, done));
             WW_TRY(tc_gemm_f32acc(s, m->XslcA, m->Bslc, N, ncols, N, 2, nullptr, B, N, 1.0, m->err, done));

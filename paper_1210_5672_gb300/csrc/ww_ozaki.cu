@@ -24,8 +24,9 @@
 // Kernel.  One CTA per 128 x 64 output tile.  Warp 0: TMA producer (ring of 7
 // A-digit tiles of 128 x 64 and ring of 2 B stages holding all 7 B-digit
 // tiles of 64 x 64); warp 1: TMEM owner and tcgen05.mma issuer (M = 128,
-// N = 64, K = 16); warps 2..9: fold and epilogue, each thread one row and 32
-// columns.  All waits are bounded.
+// K = 16, N = 64..256: the B digits of one A digit are issued together, 10
+// MMAs per K step instead of 28); warps 2..9: fold and epilogue, each thread
+// one row and 32 columns.  All waits are bounded.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -125,7 +126,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         }
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------ MMA issuer
-        constexpr uint32_t idesc = tc::idesc_bf16(OZ_BM, OZ_BN);
         for (int kc = 0; kc < nk; ++kc) {
             const int kb = kc / OZ_KBLOCK;
             const bool first = (kc % OZ_KBLOCK) == 0;
@@ -142,12 +142,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 tc::mbar_wait(&a_full[as], (ai / OZ_ASLOTS) & 1, err);
                 tc::fence_after();
                 const uint32_t ast = tc::smem_u32(aring + as * OZ_A_TILE);
-                for (int q = 0; q + p < OZ_G; ++q) {
-                    const uint32_t d = tmem + (uint32_t)((p + q) * OZ_BN);
+                // pairs (p, q), q = 0 .. 6-p, land in groups p .. 6: consecutive TMEM
+                // column blocks, and the B digits q are consecutive 64-row tiles of
+                // the stage, so up to four of them form one N = 256 operand.  One
+                // wide MMA reads the A digit once instead of once per q.
+                for (int q0 = 0; q0 + p < OZ_G; q0 += 4) {
+                    const int nq = min(4, OZ_G - p - q0);
+                    const uint32_t id = tc::idesc_bf16(OZ_BM, OZ_BN * nq);
+                    const uint32_t d = tmem + (uint32_t)((p + q0) * OZ_BN);
 #pragma unroll
                     for (int kk = 0; kk < OZ_BK / 16; ++kk)
-                        tc::mma_bf16(d, tc::desc_k128(ast + kk * 32), tc::desc_k128(bst + q * OZ_B_TILE + kk * 32),
-                                     idesc, !(first && p == 0 && kk == 0));
+                        tc::mma_bf16(d, tc::desc_k128(ast + kk * 32), tc::desc_k128(bst + q0 * OZ_B_TILE + kk * 32),
+                                     id, !(first && p == 0 && kk == 0));
                 }
                 tc::mma_commit(&a_empty[as]);
             }
