@@ -74,6 +74,7 @@ typedef struct {
     long long launches;        /* kernels launched by the last shoot / shoot_jacobian
                                   (graph kernel nodes x replays + outputs; -1 when
                                   the legacy stream forced direct launches)        */
+    double refine_iters_mean;  /* WW_MIXED: mean refinement corrections per solve   */
 } ww_stats;
 
 typedef struct ww_ctx ww_ctx;

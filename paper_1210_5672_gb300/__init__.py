@@ -57,7 +57,7 @@ class _Problem(C.Structure):
 class Stats(C.Structure):
     _fields_ = [
         ("refine_iters_max", C.c_int), ("refine_resid_max", C.c_double), ("ns_resid_max", C.c_double),
-        ("stages", C.c_int), ("launches", C.c_longlong),
+        ("stages", C.c_int), ("launches", C.c_longlong), ("refine_iters_mean", C.c_double),
     ]
 
     def as_dict(self):

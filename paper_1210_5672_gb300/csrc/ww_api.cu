@@ -2,7 +2,9 @@
 // entry points, and the RK4 driver of shoot / shoot_jacobian.  One RK4 step
 // (four stages, each: base geometry -> assembly -> factor -> base solve and
 // DtN -> base RHS -> variational solves and DtN -> variational RHS) is
-// captured once per context into a CUDA graph and replayed `steps` times.
+// captured once per context into a CUDA graph and replayed `steps` times; in
+// the mixed form the base chain runs one stage ahead of the columns on a
+// second branch of that graph (capture_overlapped).
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -96,6 +98,8 @@ struct Owned {
     StepGraph graphs[2][2];                   // [with_columns][timing]
     StepGraph prologue[2];                    // [with_columns]: initial data (+ the mixed inverse)
     cudaStream_t own_stream = nullptr;        // created by ww_create, used unless ww_set_stream overrides
+    cudaStream_t side_stream = nullptr;       // the base chain's branch inside captured step graphs
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_base[4] = {}, ev_cols[4] = {};   // capture fork/join
     std::vector<void *> allocs;
     // phase timing
     bool timing = false;
@@ -164,14 +168,20 @@ int apply_G(Ctx *c, int col0, int ncols, int st = -1) {
     return WW_OK;
 }
 
-// one RK4 stage; cvec is the context's device copy of c (T = cvec[0])
-int run_stage(Ctx *c, int st, const double *cvec, int with_cols) {
+// The base chain of RK stage st: geometry, DtN setup (assembly, factor / inverse
+// update and the per-stage operands) and the base state's own DtN and right-hand
+// side with its RK update.  It reads and writes only the base column of the
+// state, so it does not depend on the variational columns.
+// ns_every: move the mixed inverse to every stage's A (when the base chain is
+// hidden behind the columns: a fresher inverse saves column refinement
+// iterations), else on even stages and on odd ones only when it drifted.
+int run_base(Ctx *c, int st, const double *cvec, bool ns_every = false) {
     WW_TRY(launch_base_geometry(c, c->Ys, c->Ys + c->N, 1));
     WW_TRY(mark(c, st, WW_PHASE_ASSEMBLY, 0));
     WW_TRY(launch_assemble(c));
     WW_TRY(mark(c, st, WW_PHASE_ASSEMBLY, 1));
     WW_TRY(mark(c, st, WW_PHASE_FACTOR, 0));
-    WW_TRY(factor(c, 0, (st % 2) == 0));   // mixed: inverse update every other stage
+    WW_TRY(factor(c, 0, ns_every || (st % 2) == 0));
     WW_TRY(mark(c, st, WW_PHASE_FACTOR, 1));
     WW_TRY(mark(c, st, WW_PHASE_BASE, 0));
     WW_TRY(launch_phi0(c));
@@ -180,21 +190,82 @@ int run_stage(Ctx *c, int st, const double *cvec, int with_cols) {
     WW_TRY(apply_G(c, 0, 1));
     WW_TRY(launch_base_rhs(c, st, cvec));
     WW_TRY(mark(c, st, WW_PHASE_BASE, 1));
-    if (with_cols && c->nc > 0) {
-        WW_TRY(launch_psi(c));
-        WW_TRY(mark(c, st, WW_PHASE_SOLVE, 0));
-        WW_TRY(solve(c, c->M + c->N, c->nc));
-        WW_TRY(mark(c, st, WW_PHASE_SOLVE, 1));
-        WW_TRY(mark(c, st, WW_PHASE_GAMMA, 0));
-        WW_TRY(launch_gamma(c, 1, c->nc));
-        WW_TRY(mark(c, st, WW_PHASE_GAMMA, 1));
-        WW_TRY(mark(c, st, WW_PHASE_GAPPLY, 0));
-        WW_TRY(apply_G(c, 1, c->nc, st));
-        WW_TRY(mark(c, st, WW_PHASE_GAPPLY, 1));
-        WW_TRY(mark(c, st, WW_PHASE_COLRHS, 0));
-        WW_TRY(launch_col_rhs(c, st, cvec));
-        WW_TRY(mark(c, st, WW_PHASE_COLRHS, 1));
+    return WW_OK;
+}
+
+// The variational columns of RK stage st (App. B): they read the base results
+// of the same stage (its DtN operands, u, v, w3 and F).
+int run_cols(Ctx *c, int st, const double *cvec) {
+    if (c->nc <= 0) return WW_OK;
+    WW_TRY(launch_psi(c));
+    WW_TRY(mark(c, st, WW_PHASE_SOLVE, 0));
+    WW_TRY(solve(c, c->M + c->N, c->nc));
+    WW_TRY(mark(c, st, WW_PHASE_SOLVE, 1));
+    WW_TRY(mark(c, st, WW_PHASE_GAMMA, 0));
+    WW_TRY(launch_gamma(c, 1, c->nc));
+    WW_TRY(mark(c, st, WW_PHASE_GAMMA, 1));
+    WW_TRY(mark(c, st, WW_PHASE_GAPPLY, 0));
+    WW_TRY(apply_G(c, 1, c->nc, st));
+    WW_TRY(mark(c, st, WW_PHASE_GAPPLY, 1));
+    WW_TRY(mark(c, st, WW_PHASE_COLRHS, 0));
+    WW_TRY(launch_col_rhs(c, st, cvec));
+    WW_TRY(mark(c, st, WW_PHASE_COLRHS, 1));
+    return WW_OK;
+}
+
+// one RK4 stage in order; cvec is the context's device copy of c (T = cvec[0])
+int run_stage(Ctx *c, int st, const double *cvec, int with_cols) {
+    select_parity(c, st & 1);
+    WW_TRY(run_base(c, st, cvec));
+    if (with_cols) WW_TRY(run_cols(c, st, cvec));
+    return WW_OK;
+}
+
+// In the mixed form a Jacobian step runs as two chains: the base chain one
+// stage ahead on a second stream, the column chain of the stage before on the
+// caller's stream (the column work is tensor-core bound, the base chain is
+// mostly latency bound, so they share the GPU well).  Per-stage buffers
+// alternate by stage parity.  One replay covers
+//   columns of stages 0..3 of this step  ||  base of stages 1..3 and of stage 0 of the next step,
+// with  columns(s) after base(s)  and  base(s+1) after columns(s-1)  (the
+// latter frees the parity buffers base(s+1) overwrites).  Before the first
+// replay the prologue runs base(0); the last replay's base(0) is for a step
+// that is not taken and changes nothing that is read afterwards.
+bool overlapped(const Owned *o, int with_cols) {
+    const Ctx *c = &o->c;
+    return c->precision == WW_MIXED && with_cols && c->nc > 0 && c->stream != nullptr && o->side_stream != nullptr;
+}
+
+int capture_overlapped(Owned *o, const double *cvec) {
+    Ctx *c = &o->c;
+    cudaStream_t main_s = c->stream, side = o->side_stream;
+    int st = WW_OK;
+    WW_CUDA_TRY(cudaEventRecord(o->ev_fork, main_s));
+    WW_CUDA_TRY(cudaStreamWaitEvent(side, o->ev_fork, 0));
+    for (int s = 0; s < 4 && st == WW_OK; ++s) {
+        c->stream = main_s;
+        if (s > 0) WW_CUDA_TRY(cudaStreamWaitEvent(main_s, o->ev_base[s], 0));
+        select_parity(c, s & 1);
+        st = run_cols(c, s, cvec);
+        if (st != WW_OK) break;
+        WW_CUDA_TRY(cudaEventRecord(o->ev_cols[s], main_s));
+        c->stream = side;
+        if (s > 0) {
+            cudaError_t e = cudaStreamWaitEvent(side, o->ev_cols[s - 1], 0);
+            if (e != cudaSuccess) st = fail(WW_ERR_CUDA, std::string("capture join: ") + cudaGetErrorString(e));
+        }
+        select_parity(c, (s + 1) & 1);
+        if (st == WW_OK) st = run_base(c, (s + 1) & 3, cvec, true);
+        if (st == WW_OK && s < 3) {
+            cudaError_t e = cudaEventRecord(o->ev_base[s + 1], side);
+            if (e != cudaSuccess) st = fail(WW_ERR_CUDA, std::string("capture fork: ") + cudaGetErrorString(e));
+        }
     }
+    c->stream = main_s;
+    select_parity(c, 0);
+    if (st != WW_OK) return st;
+    WW_CUDA_TRY(cudaEventRecord(o->ev_join, side));
+    WW_CUDA_TRY(cudaStreamWaitEvent(main_s, o->ev_join, 0));
     return WW_OK;
 }
 
@@ -206,7 +277,10 @@ int build_step_graph(Owned *o, int with_cols) {
     WW_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     o->capturing = true;
     int st = WW_OK;
-    for (int s = 0; s < 4 && st == WW_OK; ++s) st = run_stage(c, s, o->cbuf, with_cols);
+    if (overlapped(o, with_cols))
+        st = capture_overlapped(o, o->cbuf);
+    else
+        for (int s = 0; s < 4 && st == WW_OK; ++s) st = run_stage(c, s, o->cbuf, with_cols);
     o->capturing = false;
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (st != WW_OK) {
@@ -246,25 +320,40 @@ int build_step_graph(Owned *o, int with_cols) {
 
 // initial data (and, in WW_MIXED, the approximate inverse of the initial
 // surface): one graph per context, replayed at the start of every shot
-int prologue(Ctx *c, const double *cvec, int with_cols) {
+int prologue(Owned *o, const double *cvec, int with_cols) {
+    Ctx *c = &o->c;
+    select_parity(c, 0);
     WW_TRY(launch_initial(c, cvec, with_cols));
     if (c->precision == WW_MIXED) {
         WW_TRY(launch_base_geometry(c, c->Ys, c->Ys + c->N, 1));
         WW_TRY(launch_assemble(c));
         WW_TRY(factor(c, 1));
+        if (overlapped(o, with_cols)) WW_TRY(run_base(c, 0, cvec, true));   // the base chain runs one stage ahead
     }
     return WW_OK;
 }
 
 int run_prologue(Owned *o, int with_cols) {
     Ctx *c = &o->c;
-    if (c->stream == nullptr) return prologue(c, o->cbuf, with_cols);
+    const bool timing = o->timing;
+    o->timing = false;   // the prologue is not part of the timed phases
+    int st = WW_OK;
+    if (c->stream == nullptr) {
+        st = prologue(o, o->cbuf, with_cols);
+        o->timing = timing;
+        return st;
+    }
     StepGraph &pg = o->prologue[with_cols];
     if (!pg.exec) {
         cudaGraph_t g = nullptr;
-        WW_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        int st = prologue(c, o->cbuf, with_cols);
-        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            o->timing = timing;
+            return fail(WW_ERR_CUDA, std::string("prologue capture: ") + cudaGetErrorString(e));
+        }
+        st = prologue(o, o->cbuf, with_cols);
+        e = cudaStreamEndCapture(c->stream, &g);
+        o->timing = timing;
         if (st != WW_OK) {
             if (g) cudaGraphDestroy(g);
             return st;
@@ -275,6 +364,7 @@ int run_prologue(Owned *o, int with_cols) {
         pg.graph = g;
         if (e != cudaSuccess) return fail(WW_ERR_CUDA, std::string("prologue instantiate: ") + cudaGetErrorString(e));
     }
+    o->timing = timing;
     WW_CUDA_TRY(cudaGraphLaunch(pg.exec, c->stream));
     return WW_OK;
 }
@@ -315,11 +405,12 @@ int check_status(Ctx *c) {
     WW_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (c->precision == WW_MIXED) {
         double ratio = 0, nsres = 0;
-        int err = 0, iters = 0;
-        WW_TRY(mixed_read_stats(c, &ratio, &nsres, &iters, &err));
+        int err = 0, iters[3] = {0, 0, 0};
+        WW_TRY(mixed_read_stats(c, &ratio, &nsres, iters, &err));
         c->stats.refine_resid_max = ratio;
         c->stats.ns_resid_max = nsres;
-        c->stats.refine_iters_max = iters;
+        c->stats.refine_iters_max = iters[0];
+        c->stats.refine_iters_mean = iters[2] > 0 ? (double)iters[1] / iters[2] : 0.0;
         if (err) return fail(WW_ERR_TIMEOUT, "a tensor-core kernel gave up waiting (bounded wait expired)");
     }
     if (st & ST_NO_CONV)
@@ -428,6 +519,22 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
     }
     c->stream = o->own_stream;
     c->owner = o;
+    {
+        // the base chain is latency bound: its blocks go first when SMs free up
+        int lo = 0, hi = 0;
+        cudaError_t e0 = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e0 == cudaSuccess) e0 = cudaStreamCreateWithPriority(&o->side_stream, cudaStreamNonBlocking, hi);
+        if (e0 == cudaSuccess) e0 = cudaEventCreateWithFlags(&o->ev_fork, cudaEventDisableTiming);
+        if (e0 == cudaSuccess) e0 = cudaEventCreateWithFlags(&o->ev_join, cudaEventDisableTiming);
+        for (int k = 0; k < 4 && e0 == cudaSuccess; ++k) {
+            e0 = cudaEventCreateWithFlags(&o->ev_base[k], cudaEventDisableTiming);
+            if (e0 == cudaSuccess) e0 = cudaEventCreateWithFlags(&o->ev_cols[k], cudaEventDisableTiming);
+        }
+        if (e0 != cudaSuccess) {
+            ww_destroy(reinterpret_cast<ww_ctx *>(o));
+            return fail(WW_ERR_CUDA, std::string("ww_create streams/events: ") + cudaGetErrorString(e0));
+        }
+    }
 
     const size_t N = c->N, NC = c->NC, nb = c->nb;
     const size_t nblk = (N + nb - 1) / nb;
@@ -443,11 +550,20 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
     ALLOC(c->phi_s, N);
     ALLOC(c->E, N);
     ALLOC(c->Einv, N);
-    ALLOC(c->ux, N);
-    ALLOC(c->vy, N);
-    ALLOC(c->w3, N);
+    for (int q = 0; q < 2; ++q) {
+        ALLOC(c->ux_p[q], N);
+        ALLOC(c->vy_p[q], N);
+        ALLOC(c->w3_p[q], N);
+        ALLOC(c->Fbase_p[q], 2 * N);
+        if (p->precision == WW_MIXED) {
+            ALLOC(c->uxd_p[q], N);
+            ALLOC(c->vyd_p[q], N);
+            ALLOC(c->w3d_p[q], N);
+        }
+    }
+    ALLOC(c->filt_d, N);
+    if (p->precision == WW_MIXED) ALLOC(c->filt_df, N);
     ALLOC(c->curv, N);
-    ALLOC(c->Fbase, 2 * N);
     ALLOC(c->A, N * N);
     ALLOC(c->G, N * N);
     ALLOC(c->Dinv, nblk * 2 * nb * nb);
@@ -469,6 +585,7 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
         ww_destroy(reinterpret_cast<ww_ctx *>(o));
         return st;
     }
+    select_parity(c, 0);
     std::vector<double> tw(N), cs(3 * N);
     fill_tables(c->N, tw.data(), cs.data());
     const double two_pi = 6.283185307179586476925286766559;
@@ -498,6 +615,8 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
         return fail(WW_ERR_CUDA, std::string("ww_create upload: ") + cudaGetErrorString(e));
     }
     st = prepare_spectral(c);
+    if (st == WW_OK) st = launch_fill_filter(c);
+    if (st == WW_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = fail(WW_ERR_CUDA, "ww_create: filter tables");
     if (st == WW_OK) st = prepare_dense();
     if (st != WW_OK) {
         ww_destroy(reinterpret_cast<ww_ctx *>(o));
@@ -531,8 +650,14 @@ void ww_destroy(ww_ctx *ctx) {
     for (cudaEvent_t ev : o->pool) cudaEventDestroy(ev);
     if (o->c.mx) mixed_destroy(&o->c);
     if (o->c.stream) cudaStreamSynchronize(o->c.stream);
+    if (o->side_stream) cudaStreamSynchronize(o->side_stream);
     for (void *p : o->allocs) cudaFree(p);
     if (o->own_stream) cudaStreamDestroy(o->own_stream);
+    if (o->side_stream) cudaStreamDestroy(o->side_stream);
+    cudaEvent_t evs[] = {o->ev_fork, o->ev_join, o->ev_base[0], o->ev_base[1], o->ev_base[2], o->ev_base[3],
+                         o->ev_cols[0], o->ev_cols[1], o->ev_cols[2], o->ev_cols[3]};
+    for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
     delete o;
 }
 
@@ -571,6 +696,7 @@ int dtn_setup(ww_ctx *ctx, const double *eta) {
     if (!ctx || !eta) return fail(WW_ERR_ARG, "dtn_setup: NULL argument");
     Ctx *c = &owner(ctx)->c;
     c->dtn_ready = false;
+    select_parity(c, 0);
     WW_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     WW_TRY(launch_base_geometry(c, eta, nullptr, 0));
     WW_TRY(launch_assemble(c));

@@ -121,5 +121,150 @@ __device__ __forceinline__ void block_fft(cdf *s, int N, int logN, const cdf *__
     }
 }
 
+// ---------------------------------------------------------------------------
+// Stockham FFT in double-float: radix-8 passes (one radix-4 or radix-2 pass
+// last when log2 N is not a multiple of 3), each thread taking R points into
+// registers, applying the inter-pass twiddles and an R-point DFT, and writing
+// them back; natural order in and out, no bit reversal.  Every pass reads all
+// its points before a barrier and writes after it, so it runs in place.  The
+// intermediate passes use a padded layout (one 16-byte slot every 8 points:
+// the first pass writes each thread's 8 outputs contiguously, which the
+// padding spreads over all banks), so s needs room for N + N/8 points.
+// Stockham's formulation (Stockham 1966; the GPU form of Govindaraju et al.,
+// SC 2008):  pass with sub-transform length L (1, R, R^2, ..): thread j reads
+// x[j + r N/R], multiplies by W_{L R}^{(j mod L) r}, takes the R-point DFT and
+// writes y[(j / L) L R + (j mod L) + r L].
+// ---------------------------------------------------------------------------
+constexpr double kRsqrt2 = 0.70710678118654752440084436210484903928;
+
+__device__ __forceinline__ df neg(df a) { return df{-a.hi, -a.lo}; }
+__device__ __forceinline__ cdf cneg(cdf a) { return cdf{-a.rh, -a.rl, -a.ih, -a.il}; }
+// (-i) z for the forward transform, (+i) z for the inverse
+template <bool INV>
+__device__ __forceinline__ cdf mul_mi(cdf z) {
+    return INV ? cdf{-z.ih, -z.il, z.rh, z.rl} : cdf{z.ih, z.il, -z.rh, -z.rl};
+}
+// z * (1 -+ i)/sqrt2  (forward: W8^1 = (1 - i)/sqrt2; inverse: its conjugate)
+template <bool INV>
+__device__ __forceinline__ cdf mul_w8(cdf z) {
+    const df c{(float)kRsqrt2, (float)(kRsqrt2 - (double)(float)kRsqrt2)};
+    const df a = re(z), b = im(z);
+    // forward: ((a + b) + i (b - a)) / sqrt2 ; inverse: ((a - b) + i (a + b)) / sqrt2
+    return INV ? make(mul(sub(a, b), c), mul(add(a, b), c)) : make(mul(add(a, b), c), mul(sub(b, a), c));
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(cdf &x0, cdf &x1, cdf &x2, cdf &x3) {
+    const cdf t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), t3 = mul_mi<INV>(csub(x1, x3));
+    x0 = cadd(t0, t2);
+    x2 = csub(t0, t2);
+    x1 = cadd(t1, t3);
+    x3 = csub(t1, t3);
+}
+
+// v[k] <- sum_r v[r] W8^{rk}
+template <bool INV>
+__device__ __forceinline__ void dft8(cdf *v) {
+    cdf e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    cdf o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<INV>(e0, e1, e2, e3);
+    dft4<INV>(o0, o1, o2, o3);
+    o1 = mul_w8<INV>(o1);
+    o2 = mul_mi<INV>(o2);
+    o3 = mul_mi<INV>(mul_w8<INV>(o3));   // W8^3 = W8^1 W8^2
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1);
+    v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2);
+    v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3);
+    v[7] = csub(e3, o3);
+}
+
+__device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
+
+// W_N^m for 0 <= m < N from the half table twd[k] = exp(-2 pi i k/N), k < N/2
+template <bool INV>
+__device__ __forceinline__ cdf twiddle(const cdf *__restrict__ twd, int m, int halfN) {
+    cdf w = m < halfN ? twd[m] : cneg(twd[m - halfN]);
+    if (INV) {
+        w.ih = -w.ih;
+        w.il = -w.il;
+    }
+    return w;
+}
+
+template <bool INV, int R>
+__device__ __forceinline__ void stockham_pass(cdf *s, int N, int L, bool pad_in, bool pad_out,
+                                              const cdf *__restrict__ twd) {
+    // each thread holds up to MAXC groups of R points (N <= 2048 with 256 threads)
+    constexpr int MAXC = (R == 8) ? 1 : 2;
+    const int NR = N / R, halfN = N >> 1;
+    const int tstride = N / (L * R);   // W_{L R}^{k r} = W_N^{k r N / (L R)}
+    cdf v[MAXC][R];
+#pragma unroll
+    for (int c = 0; c < MAXC; ++c) {
+        const int j = c * blockDim.x + threadIdx.x;
+        if (j < NR) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int i = j + r * NR;
+                v[c][r] = s[pad_in ? pad8(i) : i];
+            }
+            const int k = j % L;
+            if (k != 0) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[c][r] = cmul(v[c][r], twiddle<INV>(twd, k * r * tstride, halfN));
+            }
+            if (R == 8)
+                dft8<INV>(v[c]);
+            else
+                dft4<INV>(v[c][0], v[c][1], v[c][2], v[c][3]);
+        }
+    }
+    __syncthreads();   // every point of this pass read before any is overwritten
+#pragma unroll
+    for (int c = 0; c < MAXC; ++c) {
+        const int j = c * blockDim.x + threadIdx.x;
+        if (j < NR) {
+            const int base = (j / L) * L * R + (j % L);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int o = base + r * L;
+                s[pad_out ? pad8(o) : o] = v[c][r];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// In-place FFT of s[0..N) (natural order in and out), 16 <= N = 2^logN <= 2048
+// and blockDim.x == 256 (FFT_STOCKHAM_MAXN), s with room for N + N/8 points;
+// unscaled inverse.  Radix-8 passes, and one or two radix-4 passes when
+// log2 N is not a multiple of 3.  Callers synchronise before (the data is
+// complete); the routine ends with a barrier.
+constexpr int FFT_STOCKHAM_MAXN = 2048;
+
+__device__ __forceinline__ void block_fft_stockham(cdf *s, int N, int logN, const cdf *__restrict__ twd,
+                                                   bool inverse) {
+    const int n4 = (logN % 3 == 0) ? 0 : (logN % 3 == 2 ? 1 : 2);   // radix-4 passes
+    const int n8 = (logN - 2 * n4) / 3;                              // radix-8 passes
+    const int npass = n4 + n8;
+    int L = 1;
+    for (int pi = 0; pi < npass; ++pi) {
+        const bool r8 = pi < n8;
+        const bool pin = pi > 0, pout = pi < npass - 1;
+        if (inverse) {
+            if (r8) stockham_pass<true, 8>(s, N, L, pin, pout, twd);
+            else stockham_pass<true, 4>(s, N, L, pin, pout, twd);
+        } else {
+            if (r8) stockham_pass<false, 8>(s, N, L, pin, pout, twd);
+            else stockham_pass<false, 4>(s, N, L, pin, pout, twd);
+        }
+        L *= r8 ? 8 : 4;
+    }
+}
+
 }  // namespace dfl
 }  // namespace ww

@@ -8,7 +8,8 @@
 // Layout of the work.  A CTA owns 64 rows and a 1/KS slice of k; its 8 warps
 // split that slice again, each lane holding two adjacent rows (one 8- or
 // 16-byte vector load per column of A, a warp reads 64 contiguous rows), with
-// eight column loads in flight per lane.  The KS CTAs of a row tile form a
+// eight column loads in flight per lane, and the CTA's slice of B converted
+// once into shared memory.  The KS CTAs of a row tile form a
 // thread-block cluster: each sums its warps in shared memory, then CTA r adds
 // the KS partials of its share of the rows through distributed shared memory,
 // in rank order.  Every sum is taken in a fixed order, so results do not
@@ -38,16 +39,22 @@ struct Vec2<double> {
 
 // MODE 0: C = alpha S + beta C (beta == 0: C = alpha S);  MODE 1: C = Psi - S.
 // S = A B with products and per-lane sums in TA (FP32 for the FP32 inverse,
-// FP64 otherwise); warp, CTA and cluster partials are added in FP64.
-template <typename TA, bool VEC, int MODE>
+// FP64 otherwise); warp, CTA and cluster partials are added in FP64.  NB >= n
+// is the compile-time column count (1, 2, 4 or 8): the loops over the columns
+// are unrolled to NB, so no predicated-off FMA of an absent column is issued
+// (on GB300 the FP64 pipe retires 2 lanes per clock per SM).  The CTA's slice
+// of B is converted to TA once and held in shared memory.
+template <typename TA, bool VEC, int MODE, int NB>
 __global__ void __launch_bounds__(NR_WARPS * 32) k_gemv_nr(int m, int n, int k, double alpha,
                                                            const TA *__restrict__ A, int lda,
                                                            const double *__restrict__ B, int ldb, double beta,
                                                            double *C, int ldc, const double *__restrict__ Psi,
                                                            int ldp, const int *skip) {
     if (skip && *skip) return;   // the same flag for every CTA of the cluster: all leave together
-    __shared__ double part[NR_WARPS][NR_MAXN][NR_ROWS];
-    __shared__ double cta[NR_MAXN][NR_ROWS];
+    __shared__ double part[NR_WARPS][NB][NR_ROWS];
+    __shared__ double cta[NB][NR_ROWS];
+    extern __shared__ __align__(16) unsigned char bsh_raw[];
+    TA *bsh = reinterpret_cast<TA *>(bsh_raw);   // [NB][kcl]
     cg::cluster_group cluster = cg::this_cluster();
     const int KS = gridDim.y, rank = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -58,11 +65,17 @@ __global__ void __launch_bounds__(NR_WARPS * 32) k_gemv_nr(int m, int n, int k, 
     const bool oka = ra < m, okb = rb < m;
     // k slice of this CTA, then of this warp
     const int kc = (k + KS - 1) / KS, kb0 = rank * kc, ke0 = min(k, kb0 + kc);
-    const int wc = (max(0, ke0 - kb0) + NR_WARPS - 1) / NR_WARPS;
+    const int kcl = max(0, ke0 - kb0);
+    for (int t = threadIdx.x; t < NB * kcl; t += blockDim.x) {
+        const int j = t / kcl, kk = t - j * kcl;
+        bsh[t] = j < n ? (TA)B[(size_t)j * ldb + kb0 + kk] : (TA)0;
+    }
+    __syncthreads();
+    const int wc = (kcl + NR_WARPS - 1) / NR_WARPS;
     const int kb = kb0 + warp * wc, ke = min(ke0, kb + wc);
-    TA acc0[NR_MAXN], acc1[NR_MAXN];
+    TA acc0[NB], acc1[NB];
 #pragma unroll
-    for (int j = 0; j < NR_MAXN; ++j) acc0[j] = acc1[j] = (TA)0;
+    for (int j = 0; j < NB; ++j) acc0[j] = acc1[j] = (TA)0;
     int kk = kb;
     for (; kk + 8 <= ke; kk += 8) {
         TA a0[8], a1[8];
@@ -83,34 +96,32 @@ __global__ void __launch_bounds__(NR_WARPS * 32) k_gemv_nr(int m, int n, int k, 
                 a1[u] = okb ? col[rb] : (TA)0;
             }
         }
+        const TA *bk = bsh + (kk - kb0);
 #pragma unroll
         for (int u = 0; u < 8; ++u)
 #pragma unroll
-            for (int j = 0; j < NR_MAXN; ++j)
-                if (j < n) {
-                    const TA b = (TA)__ldg(B + (size_t)j * ldb + kk + u);
-                    acc0[j] = fma(a0[u], b, acc0[j]);
-                    acc1[j] = fma(a1[u], b, acc1[j]);
-                }
+            for (int j = 0; j < NB; ++j) {
+                const TA b = bk[j * kcl + u];
+                acc0[j] = fma(a0[u], b, acc0[j]);
+                acc1[j] = fma(a1[u], b, acc1[j]);
+            }
     }
     for (; kk < ke; ++kk) {
         const TA *col = A + (size_t)kk * lda;
         const TA x0 = oka ? col[ra] : (TA)0, x1 = okb ? col[rb] : (TA)0;
 #pragma unroll
-        for (int j = 0; j < NR_MAXN; ++j)
-            if (j < n) {
-                const TA b = (TA)__ldg(B + (size_t)j * ldb + kk);
-                acc0[j] = fma(x0, b, acc0[j]);
-                acc1[j] = fma(x1, b, acc1[j]);
-            }
+        for (int j = 0; j < NB; ++j) {
+            const TA b = bsh[j * kcl + (kk - kb0)];
+            acc0[j] = fma(x0, b, acc0[j]);
+            acc1[j] = fma(x1, b, acc1[j]);
+        }
     }
     const int la = VEC ? 2 * lane : lane, lb = VEC ? la + 1 : la + 32;   // local rows
 #pragma unroll
-    for (int j = 0; j < NR_MAXN; ++j)
-        if (j < n) {
-            part[warp][j][la] = (double)acc0[j];
-            part[warp][j][lb] = (double)acc1[j];
-        }
+    for (int j = 0; j < NB; ++j) {
+        part[warp][j][la] = (double)acc0[j];
+        part[warp][j][lb] = (double)acc1[j];
+    }
     __syncthreads();
     for (int t = threadIdx.x; t < n * NR_ROWS; t += blockDim.x) {
         const int j = t / NR_ROWS, r = t % NR_ROWS;
@@ -138,16 +149,20 @@ __global__ void __launch_bounds__(NR_WARPS * 32) k_gemv_nr(int m, int n, int k, 
     cluster.sync();   // no CTA leaves while another still reads its shared memory
 }
 
-template <typename TA, bool VEC, int MODE>
+template <typename TA, bool VEC, int MODE, int NB>
 int launch_nr(cudaStream_t s, int m, int n, int k, double alpha, const TA *A, int lda, const double *B, int ldb,
               double beta, double *C, int ldc, const double *Psi, int ldp, const int *skip) {
     // split k over up to 8 CTAs, at least 128 columns each
     int ks = k / 128;
     ks = ks < 1 ? 1 : (ks > NR_MAXKS ? NR_MAXKS : ks);
+    const int kcl = (k + ks - 1) / ks;
+    const size_t dyn = sizeof(TA) * (size_t)NB * (size_t)(kcl > 0 ? kcl : 1);
+    auto kern = k_gemv_nr<TA, VEC, MODE, NB>;
+    WW_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)((m + NR_ROWS - 1) / NR_ROWS), (unsigned)ks, 1);
     cfg.blockDim = dim3(NR_WARPS * 32, 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = dyn;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -156,9 +171,17 @@ int launch_nr(cudaStream_t s, int m, int n, int k, double alpha, const TA *A, in
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    WW_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_gemv_nr<TA, VEC, MODE>, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
-                                   Psi, ldp, skip));
+    WW_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, Psi, ldp, skip));
     return WW_OK;
+}
+
+template <typename TA, bool VEC, int MODE>
+int launch_nb(cudaStream_t s, int m, int n, int k, double alpha, const TA *A, int lda, const double *B, int ldb,
+              double beta, double *C, int ldc, const double *Psi, int ldp, const int *skip) {
+    if (n == 1) return launch_nr<TA, VEC, MODE, 1>(s, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, Psi, ldp, skip);
+    if (n == 2) return launch_nr<TA, VEC, MODE, 2>(s, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, Psi, ldp, skip);
+    if (n <= 4) return launch_nr<TA, VEC, MODE, 4>(s, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, Psi, ldp, skip);
+    return launch_nr<TA, VEC, MODE, 8>(s, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, Psi, ldp, skip);
 }
 
 template <typename TA, int MODE>
@@ -168,8 +191,8 @@ int dispatch_nr(cudaStream_t s, int m, int n, int k, double alpha, const TA *A, 
     if (n > NR_MAXN) return fail(WW_ERR_ARG, "gemv_narrow: at most 8 columns");
     // two-row vector loads need an aligned base, an even leading dimension and an even m
     const bool vec = (reinterpret_cast<uintptr_t>(A) % (2 * sizeof(TA)) == 0) && (lda % 2 == 0) && (m % 2 == 0);
-    if (vec) return launch_nr<TA, true, MODE>(s, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, Psi, ldp, skip);
-    return launch_nr<TA, false, MODE>(s, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, Psi, ldp, skip);
+    if (vec) return launch_nb<TA, true, MODE>(s, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, Psi, ldp, skip);
+    return launch_nb<TA, false, MODE>(s, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, Psi, ldp, skip);
 }
 
 }  // namespace

@@ -69,6 +69,19 @@ struct Ctx {
     double *ux, *vy, *w3;                    // phi_x, phi_y, (1+eta'^2)^{-3/2}
     double *curv;                            // d/dx (eta'/sqrt(1+eta'^2))
     double *Fbase;                           // filtered base RHS (2N)
+    // The base-state results that the variational columns of a stage read
+    // (ux, vy, w3, Fbase above) are double-buffered by stage parity, so the
+    // base chain of stage s+1 can run while the columns of stage s still read
+    // stage s's; `par` selects the copy the pointers above refer to.
+    int par;
+    double *ux_p[2], *vy_p[2], *w3_p[2], *Fbase_p[2];
+    // double-float copies of ux, vy, w3 for the columns' double-float kernels
+    // (WW_MIXED; NULL otherwise), also per parity
+    float2 *uxd, *vyd, *w3d;
+    float2 *uxd_p[2], *vyd_p[2], *w3d_p[2];
+    // filter multipliers exp(-36 (|k|/(N/2))^36) / N per FFT slot: FP64 and double-float
+    double *filt_d;
+    float2 *filt_df;
 
     // dense operators
     double *A;                // N x N: 1/2 I + K, overwritten by its LU factors
@@ -92,6 +105,27 @@ struct Ctx {
     Mixed *mx;
     void *owner;              // the API-side object holding this context (phase timing)
 };
+
+// point the per-stage buffers (base results here, mixed operands in ww_mixed.cu)
+// at copy p
+inline void select_parity(Ctx *c, int p) {
+    c->par = p;
+    if (c->ux_p[p]) {
+        c->ux = c->ux_p[p];
+        c->vy = c->vy_p[p];
+        c->w3 = c->w3_p[p];
+        c->Fbase = c->Fbase_p[p];
+        c->uxd = c->uxd_p[p];
+        c->vyd = c->vyd_p[p];
+        c->w3d = c->w3d_p[p];
+    }
+}
+
+// a double as a double-float pair (hi, lo): hi = x rounded to float, lo = the rest
+__host__ __device__ inline float2 df_split(double x) {
+    const float hi = (float)x;
+    return make_float2(hi, (float)(x - (double)hi));
+}
 
 // --------------------------------------------------------------------------
 // complex helpers
@@ -162,6 +196,7 @@ int launch_phi0(Ctx *c);                             // M[:,0] = phi of the base
 int launch_base_rhs(Ctx *c, int stage, const double *cvec);
 int launch_col_rhs(Ctx *c, int stage, const double *cvec);
 int launch_initial(Ctx *c, const double *cvec, int with_columns);
+int launch_fill_filter(Ctx *c);                      // filter tables (once, at ww_create)
 int launch_outputs(Ctx *c, double *r, double *J, double *f, int with_J);
 int launch_copy_cols(Ctx *c, const double *src, int ncols, double *dst);
 
@@ -189,7 +224,7 @@ int mixed_create(Ctx *c);
 int tc_init();   // resolves the tensor-map encoder (called before any capture)
 void mixed_destroy(Ctx *c);
 int mixed_setup(Ctx *c, int fresh, int update);      // after assembly: operands, inverse update
-int mixed_read_stats(Ctx *c, double *ratio, double *nsres, int *iters, int *err);
+int mixed_read_stats(Ctx *c, double *ratio, double *nsres, int *iters /* [3]: max, sum, solves */, int *err);
 int mixed_solve(Ctx *c, double *B, int ncols);       // B <- A^{-1} B (refined)
 int mixed_apply_G(Ctx *c, int col0, int ncols, int part);   // Gout += G Gam (part 0 split, 1 product; FP64-accurate)
 

@@ -20,7 +20,9 @@
 //     max|M|).  The test runs on the device; the remaining iterations of a
 //     converged solve are launched but return at once, so the step program
 //     stays one CUDA graph.  A solve that does not converge raises
-//     WW_ERR_NO_CONVERGENCE;
+//     WW_ERR_NO_CONVERGENCE.  The products with X in this loop use 2 + 2
+//     slices (~2^-16 relative): their error only adds to the contraction
+//     factor of the iteration, the residuals stay FP64-accurate;
 //   * G gamma is FP64-accurate (ww_ozaki.cu).
 // Single-column solves (the base state) use FP64 residuals and FP32 products
 // with X on the CUDA cores instead, where a tensor-core tile would be 99%
@@ -38,6 +40,8 @@ int tc_slice_f64(cudaStream_t s, const double *src, int ld, int rows, int K, int
                  __nv_bfloat16 *dst, const int *skip = nullptr);
 int tc_gemm_f32acc(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 *B3, int M, int Nn, int K,
                    int out_mode, float *Cf, double *Cd, int ldc, double alpha, int *err, const int *skip = nullptr);
+int tc_gemm_2x2(cudaStream_t s, const __nv_bfloat16 *A2, const __nv_bfloat16 *B2, int M, int Nn, int K, int out_mode,
+                float *Cf, double *Cd, int ldc, double alpha, int *err, const int *skip = nullptr);
 // ww_ozaki.cu
 int ozaki_digits(cudaStream_t s, const double *X, int ld, int rows, int K, int side, float diag_shift, int *emax,
                  double *scale, __nv_bfloat16 *dst, const int *skip);
@@ -49,24 +53,34 @@ constexpr int NS_INIT = 6;          // Newton-Schulz steps from X = 4/3 I
 constexpr int SMALL_COLS = 8;       // solves / G products this narrow use the CUDA cores
 constexpr float NS_SKIP = 1e-5f;    // max|I - A X| at the last update that lets the next stage reuse X
 
+// scratch of one refinement loop (the base column's narrow solve and the
+// columns' wide solve run on different streams, so each has its own)
+struct SolveWs {
+    double *R, *Psi;                       // N x width
+    double *psis, *mscale;                 // width: column maxima of Psi and of the solution
+    unsigned long long *colmax, *colmax0;  // width: max|R_j| of the last and the previous residual
+    int *done;                             // device decision: the current solve has converged
+};
+
 struct Mixed {
     float *X, *P;                          // approximate inverse, N x N work (column-major)
-    __nv_bfloat16 *Aslc, *XslcB, *XslcA, *Wslc;   // 3-slice operands (3 x N x N)
-    __nv_bfloat16 *Kd, *Gd;                // 7-digit left operands (7 x N x N)
-    double *Ks, *Gs;                       // their row scales
+    __nv_bfloat16 *Aslc, *XslcB, *XslcA, *Wslc;   // 3-slice operands of the inverse update (3 x N x N)
+    // per-stage operands of the column solves and G-apply, double-buffered by
+    // stage parity: the base chain builds stage s+1's while the columns of
+    // stage s still read stage s's
+    __nv_bfloat16 *Xrow[2];                // 3 slices of the rows of X
+    __nv_bfloat16 *Kd[2], *Gd[2];          // 7-digit left operands (7 x N x N) of K = A - I/2 and G
+    double *Ks[2], *Gs[2];                 // their row scales
     int *Ke, *Ge;                          // row exponent work
     __nv_bfloat16 *Rd;                     // 7-digit right operand ((7 NC + 256) x N)
     double *Rs;                            // its column scales
     int *Re;
     __nv_bfloat16 *Bslc;                   // 3-slice right operand ((3 NC + 256) x N)
-    double *R, *Psi;                       // N x NC
-    double *psis, *mscale;                 // NC: column maxima of Psi and of the solution
-    unsigned long long *colmax, *colmax0;  // NC: max|R_j| of the last and the previous residual
+    SolveWs wide, nar;
     double *ratio;                         // worst final residual ratio (bits of a double)
     unsigned *nsres, *nsres_last;          // max|I - A X| before an update: worst, and the latest (fp32 bits)
     int *ns_skip;                          // device decision: this stage reuses the previous X
-    int *done;                             // device decision: the current solve has converged
-    int *iters;                            // most residuals any solve needed
+    int *iters;                            // [0] most residuals any solve needed, [1] their sum, [2] solves
     int *err;
 };
 
@@ -146,10 +160,14 @@ __global__ void k_converged(const unsigned long long *cm, const unsigned long lo
         if (worst <= tol) {
             *done = 1;
             atomicMax(iters, it + 1);
+            atomicAdd(iters + 1, it + 1);
+            atomicAdd(iters + 2, 1);
             atomicMax(ratio, (unsigned long long)__double_as_longlong(worst));
         } else if (last) {
             atomicOr(status, ST_NO_CONV);
             atomicMax(iters, it + 1);
+            atomicAdd(iters + 1, it + 1);
+            atomicAdd(iters + 2, 1);
             if (isfinite(worst)) atomicMax(ratio, (unsigned long long)__double_as_longlong(worst));
         }
     }
@@ -199,28 +217,35 @@ int mixed_create(Ctx *c) {
     MA(m->XslcB, 3 * NN);
     MA(m->XslcA, 3 * NN);
     MA(m->Wslc, 3 * NN);
-    MA(m->Kd, 7 * NN);
-    MA(m->Gd, 7 * NN);
-    MA(m->Ks, N);
-    MA(m->Gs, N);
+    for (int q = 0; q < 2; ++q) {
+        MA(m->Xrow[q], 3 * NN);
+        MA(m->Kd[q], 7 * NN);
+        MA(m->Gd[q], 7 * NN);
+        MA(m->Ks[q], N);
+        MA(m->Gs[q], N);
+    }
     MA(m->Ke, N);
     MA(m->Ge, N);
     MA(m->Rd, (7 * NC + 256) * N);   // + rows so that a TMA box never leaves the buffer
     MA(m->Rs, NC);
     MA(m->Re, NC);
     MA(m->Bslc, (3 * NC + 256) * N);
-    MA(m->R, N * NC);
-    MA(m->Psi, N * NC);
-    MA(m->psis, NC);
-    MA(m->mscale, NC);
-    MA(m->colmax, NC);
-    MA(m->colmax0, NC);
+    SolveWs *ws[2] = {&m->wide, &m->nar};
+    const size_t width[2] = {NC, (size_t)SMALL_COLS};
+    for (int q = 0; q < 2; ++q) {
+        MA(ws[q]->R, N * width[q]);
+        MA(ws[q]->Psi, N * width[q]);
+        MA(ws[q]->psis, width[q]);
+        MA(ws[q]->mscale, width[q]);
+        MA(ws[q]->colmax, width[q]);
+        MA(ws[q]->colmax0, width[q]);
+        MA(ws[q]->done, 1);
+    }
     MA(m->ratio, 1);
     MA(m->nsres, 1);
     MA(m->nsres_last, 1);
     MA(m->ns_skip, 1);
-    MA(m->done, 1);
-    MA(m->iters, 1);
+    MA(m->iters, 3);
     MA(m->err, 1);
 #undef MA
     if (st != WW_OK) return st;
@@ -229,17 +254,20 @@ int mixed_create(Ctx *c) {
     WW_CUDA_TRY(cudaMemset(m->nsres, 0, sizeof(unsigned)));
     WW_CUDA_TRY(cudaMemset(m->nsres_last, 0xFF, sizeof(unsigned)));   // NaN bits: never skip before an update
     WW_CUDA_TRY(cudaMemset(m->ns_skip, 0, sizeof(int)));
-    WW_CUDA_TRY(cudaMemset(m->iters, 0, sizeof(int)));
+    WW_CUDA_TRY(cudaMemset(m->iters, 0, 3 * sizeof(int)));
     return WW_OK;
 }
 
 void mixed_destroy(Ctx *c) {
     Mixed *m = c->mx;
     if (!m) return;
-    void *ptrs[] = {m->X,    m->P,      m->Aslc,   m->XslcB,  m->XslcA,      m->Wslc,    m->Kd,   m->Gd,
-                    m->Ks,   m->Gs,     m->Ke,     m->Ge,     m->Rd,         m->Rs,      m->Re,   m->Bslc,
-                    m->R,    m->Psi,    m->psis,   m->mscale, m->colmax,     m->colmax0, m->ratio, m->nsres,
-                    m->nsres_last, m->ns_skip, m->done, m->iters, m->err};
+    void *ptrs[] = {m->X,          m->P,           m->Aslc,       m->XslcB,        m->XslcA,       m->Wslc,
+                    m->Xrow[0],     m->Xrow[1],     m->Kd[0],      m->Kd[1],        m->Gd[0],       m->Gd[1],
+                    m->Ks[0],       m->Ks[1],       m->Gs[0],      m->Gs[1],        m->Ke,          m->Ge,
+                    m->Rd,          m->Rs,          m->Re,         m->Bslc,         m->wide.R,      m->wide.Psi,
+                    m->wide.psis,   m->wide.mscale, m->wide.colmax, m->wide.colmax0, m->wide.done,  m->nar.R,
+                    m->nar.Psi,     m->nar.psis,    m->nar.mscale, m->nar.colmax,   m->nar.colmax0, m->nar.done,
+                    m->ratio,       m->nsres,       m->nsres_last, m->ns_skip,      m->iters,       m->err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -271,60 +299,62 @@ int mixed_setup(Ctx *c, int fresh, int update) {
     } else {
         WW_TRY(ns_step(c, skip == nullptr, skip));
     }
-    WW_TRY(tc_slice_f32(s, m->X, N, N, N, 1, 0.f, 3, m->XslcA, nullptr, skip));   // rows of the new X
-    WW_TRY(ozaki_digits(s, c->A, N, N, N, 0, 0.5f, m->Ke, m->Ks, m->Kd, nullptr));   // K = A - I/2
-    WW_TRY(ozaki_digits(s, c->G, N, N, N, 0, 0.f, m->Ge, m->Gs, m->Gd, nullptr));
+    const int q = c->par;
+    WW_TRY(tc_slice_f32(s, m->X, N, N, N, 1, 0.f, 2, m->Xrow[q]));   // rows of the (new) X, for this stage
+    WW_TRY(ozaki_digits(s, c->A, N, N, N, 0, 0.5f, m->Ke, m->Ks[q], m->Kd[q], nullptr));   // K = A - I/2
+    WW_TRY(ozaki_digits(s, c->G, N, N, N, 0, 0.f, m->Ge, m->Gs[q], m->Gd[q], nullptr));
     return WW_OK;
 }
 
 // B (N x ncols) <- A^{-1} B
 int mixed_solve(Ctx *c, double *B, int ncols) {
     Mixed *m = c->mx;
-    const int N = c->N;
+    const int N = c->N, q = c->par;
     cudaStream_t s = c->stream;
     const bool narrow = ncols <= SMALL_COLS;
+    SolveWs &w = narrow ? m->nar : m->wide;
     const unsigned cg = (unsigned)((ncols + 255) / 256);
-    WW_CUDA_TRY(cudaMemcpyAsync(m->Psi, B, sizeof(double) * N * ncols, cudaMemcpyDeviceToDevice, s));
-    WW_CUDA_TRY(cudaMemsetAsync(m->done, 0, sizeof(int), s));
+    WW_CUDA_TRY(cudaMemcpyAsync(w.Psi, B, sizeof(double) * N * ncols, cudaMemcpyDeviceToDevice, s));
+    WW_CUDA_TRY(cudaMemsetAsync(w.done, 0, sizeof(int), s));
     // column maxima of Psi (scale of the convergence test)
-    k_colmax<<<ncols, 256, 0, s>>>(m->Psi, N, m->colmax, nullptr);
-    k_colscale_from_max<<<cg, 256, 0, s>>>(m->colmax, ncols, m->psis, nullptr);
+    k_colmax<<<ncols, 256, 0, s>>>(w.Psi, N, w.colmax, nullptr);
+    k_colscale_from_max<<<cg, 256, 0, s>>>(w.colmax, ncols, w.psis, nullptr);
     WW_CUDA_TRY(cudaGetLastError());
     // M = X Psi
     if (narrow) {
-        WW_TRY(gemv_narrow_f32(s, N, ncols, N, m->X, N, m->Psi, N, 0.0, B, N));
+        WW_TRY(gemv_narrow_f32(s, N, ncols, N, m->X, N, w.Psi, N, 0.0, B, N));
     } else {
-        WW_TRY(tc_slice_f64(s, m->Psi, N, ncols, N, 0, 0.f, 3, m->Bslc));
-        WW_TRY(tc_gemm_f32acc(s, m->XslcA, m->Bslc, N, ncols, N, 1, nullptr, B, N, 1.0, m->err));
+        WW_TRY(tc_slice_f64(s, w.Psi, N, ncols, N, 0, 0.f, 2, m->Bslc));
+        WW_TRY(tc_gemm_2x2(s, m->Xrow[q], m->Bslc, N, ncols, N, 1, nullptr, B, N, 1.0, m->err));
     }
-    unsigned long long *cm_prev = m->colmax0, *cm = m->colmax;
-    const int *done = m->done;
+    unsigned long long *cm_prev = w.colmax0, *cm = w.colmax;
+    const int *done = w.done;
     const int nit = c->max_refine < 1 ? 1 : c->max_refine;
     for (int it = 0; it < nit; ++it) {
         // R = Psi - A M_it (FP64-accurate) and max|R_j|
         if (narrow) {
-            WW_TRY(resid_narrow(s, N, ncols, N, c->A, N, B, N, m->Psi, N, m->R, N, done));
-            k_colmax<<<ncols, 256, 0, s>>>(m->R, N, cm, done);
-            k_colmax<<<ncols, 256, 0, s>>>(B, N, reinterpret_cast<unsigned long long *>(m->mscale), done);
-            k_colscale_from_max<<<cg, 256, 0, s>>>(reinterpret_cast<unsigned long long *>(m->mscale), ncols,
-                                                   m->mscale, done);
+            WW_TRY(resid_narrow(s, N, ncols, N, c->A, N, B, N, w.Psi, N, w.R, N, done));
+            k_colmax<<<ncols, 256, 0, s>>>(w.R, N, cm, done);
+            k_colmax<<<ncols, 256, 0, s>>>(B, N, reinterpret_cast<unsigned long long *>(w.mscale), done);
+            k_colscale_from_max<<<cg, 256, 0, s>>>(reinterpret_cast<unsigned long long *>(w.mscale), ncols,
+                                                   w.mscale, done);
             WW_CUDA_TRY(cudaGetLastError());
         } else {
             k_zero_u64<<<cg, 256, 0, s>>>(cm, ncols, done);
             WW_TRY(ozaki_digits(s, B, N, ncols, N, 1, 0.f, m->Re, m->Rs, m->Rd, done));   // scales of M -> Rs
-            WW_TRY(ozaki_gemm(s, m->Kd, m->Ks, m->Rd, m->Rs, N, ncols, N, 1, m->R, N, m->Psi, N, B, N, cm, m->err,
-                              done));
+            WW_TRY(ozaki_gemm(s, m->Kd[q], m->Ks[q], m->Rd, m->Rs, N, ncols, N, 1, w.R, N, w.Psi, N, B, N, cm,
+                              m->err, done));
         }
         // M += X R
         if (narrow) {
-            WW_TRY(gemv_narrow_f32(s, N, ncols, N, m->X, N, m->R, N, 1.0, B, N, done));
+            WW_TRY(gemv_narrow_f32(s, N, ncols, N, m->X, N, w.R, N, 1.0, B, N, done));
         } else {
-            WW_TRY(tc_slice_f64(s, m->R, N, ncols, N, 0, 0.f, 3, m->Bslc, done));
-            WW_TRY(tc_gemm_f32acc(s, m->XslcA, m->Bslc, N, ncols, N, 2, nullptr, B, N, 1.0, m->err, done));
+            WW_TRY(tc_slice_f64(s, w.R, N, ncols, N, 0, 0.f, 2, m->Bslc, done));
+            WW_TRY(tc_gemm_2x2(s, m->Xrow[q], m->Bslc, N, ncols, N, 2, nullptr, B, N, 1.0, m->err, done));
         }
         // converged after this correction?
-        k_converged<<<1, 512, 0, s>>>(cm, it > 0 ? cm_prev : nullptr, m->psis, narrow ? m->mscale : m->Rs, ncols,
-                                      c->refine_tol, it, it == nit - 1, m->done, m->iters,
+        k_converged<<<1, 512, 0, s>>>(cm, it > 0 ? cm_prev : nullptr, w.psis, narrow ? w.mscale : m->Rs, ncols,
+                                      c->refine_tol, it, it == nit - 1, w.done, m->iters,
                                       reinterpret_cast<unsigned long long *>(m->ratio), c->status);
         WW_CUDA_TRY(cudaGetLastError());
         unsigned long long *t = cm_prev;
@@ -343,7 +373,7 @@ int mixed_apply_G(Ctx *c, int col0, int ncols, int part) {
     double *Out = c->Gout + (size_t)col0 * N;
     if (ncols <= SMALL_COLS) return part == 0 ? WW_OK : dgemm(c->stream, N, ncols, N, 1.0, c->G, N, Gam, N, 1.0, Out, N);
     if (part == 0) return ozaki_digits(c->stream, Gam, N, ncols, N, 1, 0.f, m->Re, m->Rs, m->Rd, nullptr);
-    return ozaki_gemm(c->stream, m->Gd, m->Gs, m->Rd, m->Rs, N, ncols, N, 0, Out, N, nullptr, 0, nullptr, 0, nullptr,
+    return ozaki_gemm(c->stream, m->Gd[c->par], m->Gs[c->par], m->Rd, m->Rs, N, ncols, N, 0, Out, N, nullptr, 0, nullptr, 0, nullptr,
                       m->err, nullptr);
 }
 
@@ -353,7 +383,7 @@ int mixed_read_stats(Ctx *c, double *ratio, double *nsres, int *iters, int *err)
     unsigned nb = 0;
     WW_CUDA_TRY(cudaMemcpyAsync(ratio, m->ratio, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     WW_CUDA_TRY(cudaMemcpyAsync(&nb, m->nsres, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
-    WW_CUDA_TRY(cudaMemcpyAsync(iters, m->iters, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    WW_CUDA_TRY(cudaMemcpyAsync(iters, m->iters, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     WW_CUDA_TRY(cudaMemcpyAsync(err, m->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     WW_CUDA_TRY(cudaStreamSynchronize(c->stream));
     float nf;
@@ -361,7 +391,7 @@ int mixed_read_stats(Ctx *c, double *ratio, double *nsres, int *iters, int *err)
     *nsres = nf;
     WW_CUDA_TRY(cudaMemsetAsync(m->ratio, 0, sizeof(double), c->stream));
     WW_CUDA_TRY(cudaMemsetAsync(m->nsres, 0, sizeof(unsigned), c->stream));
-    WW_CUDA_TRY(cudaMemsetAsync(m->iters, 0, sizeof(int), c->stream));
+    WW_CUDA_TRY(cudaMemsetAsync(m->iters, 0, 3 * sizeof(int), c->stream));
     WW_CUDA_TRY(cudaMemsetAsync(m->err, 0, sizeof(int), c->stream));
     return WW_OK;
 }

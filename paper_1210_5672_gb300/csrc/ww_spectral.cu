@@ -28,32 +28,71 @@ __device__ __forceinline__ double2 times_ik(double2 z, int k) {   // (ik) z
 // stay FP64 in both.
 struct ArF64 {
     using C = double2;
+    using R = double;   // real values of the pointwise algebra
+    using T = double;   // entries of the per-slot / per-point tables
     static __device__ __forceinline__ C mk(double re, double im) { return make_double2(re, im); }
     static __device__ __forceinline__ double2 get(C z) { return z; }
     static __device__ __forceinline__ void fft(C *s, int N, int logN, const void *tw, bool inv) {
         block_fft(s, N, logN, static_cast<const double2 *>(tw), inv);
     }
-    static __device__ __forceinline__ C scale(C z, double f) { return cscale(z, f); }
+    // points of shared memory one transform needs
+    static __host__ __device__ __forceinline__ int cap(int N) { return N; }
+    static __device__ __forceinline__ C scalef(C z, float f) { return cscale(z, (double)f); }
     static __device__ __forceinline__ C ikscale(C z, int k, float p2) { return cscale(times_ik(z, k), (double)p2); }
     static __device__ __forceinline__ C add(C a, C b) { return cadd(a, b); }
     static __device__ __forceinline__ C zero() { return make_double2(0.0, 0.0); }
-    static __device__ __forceinline__ C re_only(C z, double f) { return make_double2(z.x * f, 0.0); }
+    // tables and real arithmetic
+    static __device__ __forceinline__ R tab(const void *t, int j) { return static_cast<const T *>(t)[j]; }
+    static __device__ __forceinline__ C scale_tab(C z, const void *t, int j) { return cscale(z, tab(t, j)); }
+    static __device__ __forceinline__ C re_only_tab(C z, const void *t, int j) { return make_double2(z.x * tab(t, j), 0.0); }
+    static __device__ __forceinline__ R from(double x) { return x; }
+    static __device__ __forceinline__ R rmul(R a, R b) { return a * b; }
+    static __device__ __forceinline__ R radd(R a, R b) { return a + b; }
+    static __device__ __forceinline__ R rsub(R a, R b) { return a - b; }
+    static __device__ __forceinline__ R rneg(R a) { return -a; }
+    static __device__ __forceinline__ C mkr(R re, R im) { return make_double2(re, im); }
+    static __device__ __forceinline__ R re(C z) { return z.x; }
+    static __device__ __forceinline__ R im(C z) { return z.y; }
+    static __device__ __forceinline__ C addr(C z, R a, R b) { return make_double2(z.x + a, z.y + b); }
 };
 
 struct ArDF {
     using C = dfl::cdf;
+    using R = dfl::df;
+    using T = float2;   // double-float table entry (hi, lo)
     static __device__ __forceinline__ C mk(double re, double im) { return dfl::from_d2(make_double2(re, im)); }
     static __device__ __forceinline__ double2 get(C z) { return dfl::to_d2(z); }
     static __device__ __forceinline__ void fft(C *s, int N, int logN, const void *tw, bool inv) {
-        dfl::block_fft(s, N, logN, static_cast<const dfl::cdf *>(tw), inv);
+        if (N >= 16 && N <= dfl::FFT_STOCKHAM_MAXN)
+            dfl::block_fft_stockham(s, N, logN, static_cast<const dfl::cdf *>(tw), inv);
+        else
+            dfl::block_fft(s, N, logN, static_cast<const dfl::cdf *>(tw), inv);
     }
-    static __device__ __forceinline__ C scale(C z, double f) { return dfl::cscale(z, dfl::from_double(f)); }
+    // points of shared memory one transform needs (the Stockham passes pad)
+    static __host__ __device__ __forceinline__ int cap(int N) {
+        return (N >= 16 && N <= dfl::FFT_STOCKHAM_MAXN) ? N + N / 8 : N;
+    }
+    static __device__ __forceinline__ C scalef(C z, float f) { return dfl::cscalef(z, f); }
     static __device__ __forceinline__ C ikscale(C z, int k, float p2) { return dfl::cscalef(dfl::times_ik(z, k), p2); }
     static __device__ __forceinline__ C add(C a, C b) { return dfl::cadd(a, b); }
     static __device__ __forceinline__ C zero() { return C{0.f, 0.f, 0.f, 0.f}; }
-    static __device__ __forceinline__ C re_only(C z, double f) {
-        return dfl::make(dfl::mul(dfl::re(z), dfl::from_double(f)), dfl::df{0.f, 0.f});
+    static __device__ __forceinline__ R tab(const void *t, int j) {
+        const float2 v = static_cast<const T *>(t)[j];
+        return R{v.x, v.y};
     }
+    static __device__ __forceinline__ C scale_tab(C z, const void *t, int j) { return dfl::cscale(z, tab(t, j)); }
+    static __device__ __forceinline__ C re_only_tab(C z, const void *t, int j) {
+        return dfl::make(dfl::mul(dfl::re(z), tab(t, j)), dfl::df{0.f, 0.f});
+    }
+    static __device__ __forceinline__ R from(double x) { return dfl::from_double(x); }
+    static __device__ __forceinline__ R rmul(R a, R b) { return dfl::mul(a, b); }
+    static __device__ __forceinline__ R radd(R a, R b) { return dfl::add(a, b); }
+    static __device__ __forceinline__ R rsub(R a, R b) { return dfl::sub(a, b); }
+    static __device__ __forceinline__ R rneg(R a) { return R{-a.hi, -a.lo}; }
+    static __device__ __forceinline__ C mkr(R re, R im) { return dfl::make(re, im); }
+    static __device__ __forceinline__ R re(C z) { return dfl::re(z); }
+    static __device__ __forceinline__ R im(C z) { return dfl::im(z); }
+    static __device__ __forceinline__ C addr(C z, R a, R b) { return dfl::make(dfl::add(dfl::re(z), a), dfl::add(dfl::im(z), b)); }
 };
 
 // s <- s * (ik) / N (Nyquist zero)
@@ -74,7 +113,7 @@ __global__ void k_base_geometry(const double *__restrict__ eta_in, const double 
                                 double *eta, double *eta_x, double *eta_xx, double *phi_s, double *curv,
                                 double *E, double *Einv, int *status) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw), *z = s + N;
+    typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw), *z = s + AR::cap(N);
     int bad = 0;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         double e = eta_in[j];
@@ -124,10 +163,10 @@ __global__ void k_base_geometry(const double *__restrict__ eta_in, const double 
 // gamma = mu' and 1/2 H gamma for pairs of columns of M (Eq. G)
 // ------------------------------------------------------------------------
 template <class AR>
-__global__ void k_gamma(const double *__restrict__ M, int ncols, int N, int logN, const void *__restrict__ tw,
+__global__ void __launch_bounds__(FFT_THREADS, 2) k_gamma(const double *__restrict__ M, int ncols, int N, int logN, const void *__restrict__ tw,
                         double *Gam, double *Gout) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw), *z = s + N;
+    typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw), *z = s + AR::cap(N);
     const int ca = 2 * blockIdx.x, cb = ca + 1;
     const bool hasb = cb < ncols;
     const double *ma = M + (size_t)ca * N, *mb = M + (size_t)cb * N;
@@ -143,7 +182,7 @@ __global__ void k_gamma(const double *__restrict__ M, int ncols, int N, int logN
             const bool nyq = (j == (N >> 1));
             const typename AR::C v = s[j];
             s[j] = nyq ? AR::zero()
-                       : AR::add(AR::ikscale(v, k, invN), AR::ikscale(AR::scale(v, 0.5 * fabs((double)k)), 1, invN));
+                       : AR::add(AR::ikscale(v, k, invN), AR::ikscale(AR::scalef(v, 0.5f * (float)abs(k)), 1, invN));
         }
         __syncthreads();
         AR::fft(s, N, logN, tw, true);
@@ -158,7 +197,7 @@ __global__ void k_gamma(const double *__restrict__ M, int ncols, int N, int logN
         const int k = wavenum(j, N);
         const bool nyq = (j == (N >> 1));
         const typename AR::C v = s[j];
-        z[j] = nyq ? AR::zero() : AR::scale(v, 0.5 * fabs((double)k) * (double)invN);   // 1/2 H d/dx = |k|/2
+        z[j] = nyq ? AR::zero() : AR::scalef(v, 0.5f * (float)abs(k) * invN);   // 1/2 H d/dx = |k|/2 (exact in float)
         s[j] = nyq ? AR::zero() : AR::ikscale(v, k, invN);
     }
     __syncthreads();
@@ -199,18 +238,18 @@ __device__ __forceinline__ double rk_b(int st) { return (st == 1 || st == 2) ? 2
 __device__ __forceinline__ double rk_a_next(int st) { return st == 2 ? 1.0 : 0.5; }
 
 // end-of-step update of one column: s holds k (eta part .x, phi part .y) in
-// physical space; writes the filtered new state into Y and Ys.
+// physical space; writes the filtered new state into Y and Ys.  filt: the
+// filter multipliers exp(-36 (|k|/(N/2))^36) / N per FFT slot (AR table).
 template <class AR>
 __device__ void finish_step(typename AR::C *s, int N, int logN, const void *__restrict__ tw, double dt, double *Yc,
-                            double *Ysc, const double *Accc) {
+                            double *Ysc, const double *Accc, const void *__restrict__ filt) {
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         const double2 k = AR::get(s[j]);
         s[j] = AR::mk(Yc[j] + dt / 6.0 * (Accc[j] + k.x), Yc[N + j] + dt / 6.0 * (Accc[N + j] + k.y));
     }
     __syncthreads();
     AR::fft(s, N, logN, tw, false);
-    const double invN = 1.0 / N;
-    for (int j = threadIdx.x; j < N; j += blockDim.x) s[j] = AR::scale(s[j], filt36(wavenum(j, N), N) * invN);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) s[j] = AR::scale_tab(s[j], filt, j);
     __syncthreads();
     AR::fft(s, N, logN, tw, true);
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
@@ -222,7 +261,7 @@ __device__ void finish_step(typename AR::C *s, int N, int logN, const void *__re
 
 template <class AR>
 __device__ void stage_update(typename AR::C *s, int N, int logN, const void *__restrict__ tw, int st, double dt,
-                             double *Yc, double *Ysc, double *Accc) {
+                             double *Yc, double *Ysc, double *Accc, const void *__restrict__ filt) {
     if (st < 3) {
         const double b = rk_b(st), a = rk_a_next(st);
         for (int j = threadIdx.x; j < N; j += blockDim.x) {
@@ -239,7 +278,7 @@ __device__ void stage_update(typename AR::C *s, int N, int logN, const void *__r
         }
     } else {
         __syncthreads();
-        finish_step<AR>(s, N, logN, tw, dt, Yc, Ysc, Accc);
+        finish_step<AR>(s, N, logN, tw, dt, Yc, Ysc, Accc, filt);
     }
 }
 
@@ -250,9 +289,9 @@ template <class AR>
 __global__ void k_base_rhs(const double *__restrict__ Gphi, const double *__restrict__ eta,
                            const double *__restrict__ eta_x, const double *__restrict__ phi_s,
                            const double *__restrict__ curv, double g, double tau, int N, int logN,
-                           const void *__restrict__ tw, double *ux, double *vy, double *w3, double *Fbase,
-                           double *Y, double *Ys, double *Acc, int st, const double *__restrict__ cvec,
-                           int steps, int update, int *status) {
+                           const void *__restrict__ tw, const void *__restrict__ filt, double *ux, double *vy,
+                           double *w3, float2 *uxd, float2 *vyd, float2 *w3d, double *Fbase, double *Y, double *Ys,
+                           double *Acc, int st, const double *__restrict__ cvec, int steps, int update, int *status) {
     extern __shared__ __align__(16) unsigned char smraw[];
     typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw);
     int bad = 0;
@@ -260,21 +299,24 @@ __global__ void k_base_rhs(const double *__restrict__ Gphi, const double *__rest
         double ex = eta_x[j], d = 1.0 + ex * ex, gp = Gphi[j], pp = phi_s[j];
         double u = (pp - ex * gp) / d;
         double v = (ex * pp + gp) / d;
+        const double w = 1.0 / (d * sqrt(d));
         ux[j] = u;
         vy[j] = v;
-        w3[j] = 1.0 / (d * sqrt(d));
+        w3[j] = w;
+        if (uxd) {   // double-float copies for the columns' double-float kernels
+            uxd[j] = df_split(u);
+            vyd[j] = df_split(v);
+            w3d[j] = df_split(w);
+        }
         double pt = v * gp - 0.5 * u * u - 0.5 * v * v - g * eta[j] + tau * curv[j];
         if (!isfinite(pt) || !isfinite(gp)) bad = 1;
         s[j] = AR::mk(gp, pt);   // eta_t = G phi ; phi_t before P and the filter
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
     AR::fft(s, N, logN, tw, false);
-    const double invN = 1.0 / N;
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        const double f = filt36(wavenum(j, N), N) * invN;
+    for (int j = threadIdx.x; j < N; j += blockDim.x)
         // P acts on the phi part only: at k = 0 keep Re (eta mean), drop Im (phi mean)
-        s[j] = (j == 0) ? AR::re_only(s[0], f) : AR::scale(s[j], f);
-    }
+        s[j] = (j == 0) ? AR::re_only_tab(s[0], filt, 0) : AR::scale_tab(s[j], filt, j);
     __syncthreads();
     AR::fft(s, N, logN, tw, true);
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
@@ -285,7 +327,7 @@ __global__ void k_base_rhs(const double *__restrict__ Gphi, const double *__rest
     if (!update) return;
     const double dt = cvec[0] / (4.0 * steps);
     __syncthreads();
-    stage_update<AR>(s, N, logN, tw, st, dt, Y, Ys, Acc);
+    stage_update<AR>(s, N, logN, tw, st, dt, Y, Ys, Acc, filt);
 }
 
 // ------------------------------------------------------------------------
@@ -296,13 +338,14 @@ __global__ void k_base_rhs(const double *__restrict__ Gphi, const double *__rest
 // filtered; the T column (column 1) adds F(q)/T; then the RK update.
 // ------------------------------------------------------------------------
 template <class AR>
-__global__ void k_col_rhs(const double *__restrict__ Gout, const double *__restrict__ ux,
-                          const double *__restrict__ vy, const double *__restrict__ w3,
+__global__ void __launch_bounds__(FFT_THREADS, 2) k_col_rhs(const double *__restrict__ Gout, const void *__restrict__ uT, const void *__restrict__ vT,
+                          const void *__restrict__ wT, const double *__restrict__ vy,
                           const double *__restrict__ Fbase, double g, double tau, int N, int logN,
-                          const void *__restrict__ tw, double *Y, double *Ys, double *Acc, int st,
-                          const double *__restrict__ cvec, int steps, int *status) {
+                          const void *__restrict__ tw, const void *__restrict__ filt, double *Y, double *Ys,
+                          double *Acc, int st, const double *__restrict__ cvec, int steps, int *status) {
+    using R = typename AR::R;
     extern __shared__ __align__(16) unsigned char smraw[];
-    typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw), *z = s + N;
+    typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw), *z = s + AR::cap(N);
     const int c = blockIdx.x + 1;
     double *Yc = Y + (size_t)c * 2 * N, *Ysc = Ys + (size_t)c * 2 * N, *Accc = Acc + (size_t)c * 2 * N;
     const double *Gpsi = Gout + (size_t)c * N;
@@ -317,44 +360,55 @@ __global__ void k_col_rhs(const double *__restrict__ Gout, const double *__restr
     __syncthreads();
     AR::fft(s, N, logN, tw, true);
     int bad = 0;
+    // pointwise algebra in the transforms' arithmetic (double-float in the
+    // mixed form: no FP64 pipe work besides converting the two FP64 inputs)
+    const R gR = AR::from(g), tauR = AR::from(tau);
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        double ed = Ysc[j], u = ux[j], v = vy[j], gp = Gpsi[j];
-        const double2 dd = AR::get(s[j]);
-        const double dpsi = dd.x, ded = dd.y;
-        // undifferentiated terms: (G psi, -u psi' + v G psi - g etadot)
-        z[j] = AR::mk(gp, -u * dpsi + v * gp - g * ed);
+        const double gpd = Gpsi[j];
+        const R ed = AR::from(Ysc[j]), gp = AR::from(gpd);
+        const R u = AR::tab(uT, j), v = AR::tab(vT, j);
+        const R dpsi = AR::re(s[j]), ded = AR::im(s[j]);
+        // undifferentiated terms: (G psi, v G psi - u psi' - g etadot)
+        z[j] = AR::mkr(gp, AR::rsub(AR::rsub(AR::rmul(v, gp), AR::rmul(u, dpsi)), AR::rmul(gR, ed)));
         // terms under one d/dx: (-etadot u, tau etadot' w3 - etadot u v)
-        s[j] = AR::mk(-ed * u, tau * ded * w3[j] - ed * u * v);
-        if (!isfinite(gp)) bad = 1;
+        const R eu = AR::rmul(ed, u);
+        R im = AR::rneg(AR::rmul(eu, v));
+        if (tau != 0.0) im = AR::radd(im, AR::rmul(tauR, AR::rmul(ded, AR::tab(wT, j))));
+        s[j] = AR::mkr(AR::rneg(eu), im);
+        if (!isfinite(gpd)) bad = 1;
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
     AR::fft(z, N, logN, tw, false);
     AR::fft(s, N, logN, tw, false);
-    const double invN = 1.0 / N;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        const int k = wavenum(j, N);
-        const double f = filt36(k, N) * invN;
         typename AR::C w;
         if (j == 0)
-            w = AR::re_only(z[0], f);                 // P on the phi part; d/dx kills k = 0
+            w = AR::re_only_tab(z[0], filt, 0);       // P on the phi part; d/dx kills k = 0
         else if (j == (N >> 1))
-            w = AR::scale(z[j], f);                   // d/dx is zero at Nyquist
+            w = AR::scale_tab(z[j], filt, j);          // d/dx is zero at Nyquist
         else
-            w = AR::scale(AR::add(z[j], AR::ikscale(s[j], k, 1.0f)), f);
+            w = AR::scale_tab(AR::add(z[j], AR::ikscale(s[j], wavenum(j, N), 1.0f)), filt, j);
         s[j] = w;
     }
     __syncthreads();
     AR::fft(s, N, logN, tw, true);
     if (c == 1) {   // d/dT column: + F(q) / T  (dt = T / (4 steps) is a function of T)
         const double invT = 1.0 / cvec[0];
-        for (int j = threadIdx.x; j < N; j += blockDim.x) {
-            const double2 v = AR::get(s[j]);
-            s[j] = AR::mk(v.x + Fbase[j] * invT, v.y + Fbase[N + j] * invT);
-        }
+        for (int j = threadIdx.x; j < N; j += blockDim.x)
+            s[j] = AR::addr(s[j], AR::from(Fbase[j] * invT), AR::from(Fbase[N + j] * invT));
     }
     const double dt = cvec[0] / (4.0 * steps);
     __syncthreads();
-    stage_update<AR>(s, N, logN, tw, st, dt, Yc, Ysc, Accc);
+    stage_update<AR>(s, N, logN, tw, st, dt, Yc, Ysc, Accc, filt);
+}
+
+// filter multipliers per FFT slot, FP64 and double-float (Eq. filter; / N)
+__global__ void k_fill_filter(int N, double *fd, float2 *fdf) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const double f = filt36(wavenum(j, N), N) / (double)N;
+    fd[j] = f;
+    if (fdf) fdf[j] = df_split(f);
 }
 
 // ------------------------------------------------------------------------
@@ -439,12 +493,13 @@ int set_smem(K kernel, size_t bytes) {
 // ==========================================================================
 int prepare_spectral(Ctx *c) {
     const size_t one = sizeof(double2) * c->N, two = 2 * one;
+    const size_t two_df = 2 * sizeof(double2) * (size_t)ArDF::cap(c->N);
     WW_TRY(set_smem(k_base_geometry<ArF64>, two));
     WW_TRY(set_smem(k_base_rhs<ArF64>, one));
     WW_TRY(set_smem(k_gamma<ArF64>, two));
     WW_TRY(set_smem(k_col_rhs<ArF64>, two));
-    WW_TRY(set_smem(k_gamma<ArDF>, two));
-    WW_TRY(set_smem(k_col_rhs<ArDF>, two));
+    WW_TRY(set_smem(k_gamma<ArDF>, two_df));
+    WW_TRY(set_smem(k_col_rhs<ArDF>, two_df));
     return WW_OK;
 }
 
@@ -454,7 +509,7 @@ int prepare_spectral(Ctx *c) {
 // Measured: double-float base transforms cost ~1e-9 relative in the DtN at
 // N = 2048 (derivatives amplify the 2^-48 FFT roundoff by |k|), column
 // transforms keep J within ~1e-13 of the FP64 form.
-static bool use_df(const Ctx *c) { return c->precision == WW_MIXED && c->twd != nullptr; }
+static bool use_df(const Ctx *c) { return c->precision == WW_MIXED && c->twd != nullptr && c->uxd != nullptr; }
 
 int launch_base_geometry(Ctx *c, const double *eta, const double *phi, int with_phi) {
     size_t sm = 2 * sizeof(double2) * c->N;
@@ -469,7 +524,7 @@ int launch_gamma(Ctx *c, int col0, int ncols) {
     size_t sm = 2 * sizeof(double2) * c->N;
     size_t off = (size_t)col0 * c->N;
     if (use_df(c) && col0 >= 1)
-        k_gamma<ArDF><<<(ncols + 1) / 2, FFT_THREADS, sm, c->stream>>>(c->M + off, ncols, c->N, c->logN, c->twd,
+        k_gamma<ArDF><<<(ncols + 1) / 2, FFT_THREADS, 2 * sizeof(double2) * (size_t)ArDF::cap(c->N), c->stream>>>(c->M + off, ncols, c->N, c->logN, c->twd,
                                                                       c->Gam + off, c->Gout + off);
     else
         k_gamma<ArF64><<<(ncols + 1) / 2, FFT_THREADS, sm, c->stream>>>(c->M + off, ncols, c->N, c->logN, c->tw,
@@ -495,20 +550,29 @@ int launch_phi0(Ctx *c) {
 int launch_base_rhs(Ctx *c, int stage, const double *cvec) {
     size_t sm = sizeof(double2) * c->N;
     k_base_rhs<ArF64><<<1, FFT_THREADS, sm, c->stream>>>(c->Gout, c->eta, c->eta_x, c->phi_s, c->curv, c->g, c->tau,
-                                            c->N, c->logN, (const void *)c->tw, c->ux,
-                                            c->vy, c->w3, c->Fbase, c->Y, c->Ys, c->Kacc, stage < 0 ? 0 : stage,
-                                            cvec, c->steps, stage >= 0 ? 1 : 0, c->status);
+                                            c->N, c->logN, (const void *)c->tw, (const void *)c->filt_d, c->ux,
+                                            c->vy, c->w3, c->uxd, c->vyd, c->w3d, c->Fbase, c->Y, c->Ys, c->Kacc,
+                                            stage < 0 ? 0 : stage, cvec, c->steps, stage >= 0 ? 1 : 0, c->status);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
 
 int launch_col_rhs(Ctx *c, int stage, const double *cvec) {
     if (c->nc <= 0) return WW_OK;
-    size_t sm = 2 * sizeof(double2) * c->N;
-    auto kern = use_df(c) ? k_col_rhs<ArDF> : k_col_rhs<ArF64>;
-    kern<<<c->nc, FFT_THREADS, sm, c->stream>>>(c->Gout, c->ux, c->vy, c->w3, c->Fbase, c->g, c->tau, c->N, c->logN,
-                                                use_df(c) ? (const void *)c->twd : (const void *)c->tw, c->Y, c->Ys,
-                                                c->Kacc, stage, cvec, c->steps, c->status);
+    const bool df = use_df(c);
+    const size_t sm = 2 * sizeof(double2) * (size_t)(df ? ArDF::cap(c->N) : c->N);
+    auto kern = df ? k_col_rhs<ArDF> : k_col_rhs<ArF64>;
+    kern<<<c->nc, FFT_THREADS, sm, c->stream>>>(
+        c->Gout, df ? (const void *)c->uxd : (const void *)c->ux, df ? (const void *)c->vyd : (const void *)c->vy,
+        df ? (const void *)c->w3d : (const void *)c->w3, c->vy, c->Fbase, c->g, c->tau, c->N, c->logN,
+        df ? (const void *)c->twd : (const void *)c->tw, df ? (const void *)c->filt_df : (const void *)c->filt_d, c->Y,
+        c->Ys, c->Kacc, stage, cvec, c->steps, c->status);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+int launch_fill_filter(Ctx *c) {
+    k_fill_filter<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->N, c->filt_d, c->filt_df);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }

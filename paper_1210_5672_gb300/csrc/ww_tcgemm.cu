@@ -290,6 +290,23 @@ int tc_gemm_f32acc(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 
     return launch_tc<128, 3, 3>(s, A3, B3, M, Nn, K, P, out_mode, Cf, Cd, ldc, alpha, err, skip);
 }
 
+// Product from 2 + 2 slices (pairs with p + q <= 1): relative accuracy ~2^-16,
+// for the refinement corrections X R, whose error only adds to the contraction
+// of the iteration (the residuals themselves are FP64-accurate).  Reads slices
+// 0 and 1 of 2- or 3-slice operands.
+int tc_gemm_2x2(cudaStream_t s, const __nv_bfloat16 *A2, const __nv_bfloat16 *B2, int M, int Nn, int K, int out_mode,
+                float *Cf, double *Cd, int ldc, double alpha, int *err, const int *skip) {
+    if (K % TC_BK != 0) return fail(WW_ERR_ARG, "tc_gemm: K must be a multiple of 64");
+    Pairs P{};
+    const int pp[3] = {1, 0, 0}, qq[3] = {0, 1, 0};   // smallest terms first
+    P.n = 3;
+    for (int i = 0; i < 3; ++i) {
+        P.p[i] = (unsigned char)pp[i];
+        P.q[i] = (unsigned char)qq[i];
+    }
+    return launch_tc<128, 2, 2>(s, A2, B2, M, Nn, K, P, out_mode, Cf, Cd, ldc, alpha, err, skip);
+}
+
 }  // namespace ww
 
 // -------------------------------------------------------------------------
