@@ -30,24 +30,29 @@
 #include <cuda_bf16.h>
 
 #include "ww_internal.cuh"
+#include "ww_tc.cuh"
 
 namespace ww {
 
 // ww_tcgemm.cu
 int tc_slice_f32(cudaStream_t s, const float *src, int ld, int rows, int K, int trans, float shift, int S,
-                 __nv_bfloat16 *dst, unsigned *dev_max = nullptr, const int *skip = nullptr);
+                 __nv_bfloat16 *dst, unsigned *dev_max = nullptr, const int *skip = nullptr, int run_if_skipped = 0);
 int tc_slice_f64(cudaStream_t s, const double *src, int ld, int rows, int K, int trans, float shift, int S,
                  __nv_bfloat16 *dst, const int *skip = nullptr);
 int tc_gemm_f32acc(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 *B3, int M, int Nn, int K,
                    int out_mode, float *Cf, double *Cd, int ldc, double alpha, int *err, const int *skip = nullptr);
 int tc_gemm_2x2(cudaStream_t s, const __nv_bfloat16 *A2, const __nv_bfloat16 *B2, int M, int Nn, int K, int out_mode,
                 float *Cf, double *Cd, int ldc, double alpha, int *err, const int *skip = nullptr);
+int tc_gemm_f32acc_sliced(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 *B3, int M, int Nn, int K,
+                          const TcOut &o, int *err, const int *skip);
 // ww_ozaki.cu
 int ozaki_digits(cudaStream_t s, const double *X, int ld, int rows, int K, int side, float diag_shift, int *emax,
                  double *scale, __nv_bfloat16 *dst, const int *skip);
 int ozaki_gemm(cudaStream_t s, const __nv_bfloat16 *Ad, const double *sa, const __nv_bfloat16 *Bd, const double *sb,
                int M, int Nn, int K, int mode, double *C, int ldc, const double *Psi, int ldpsi, const double *Mh,
-               int ldm, unsigned long long *colmax, int *err, const int *skip);
+               int ldm, unsigned long long *colmax, int *err, const int *skip, __nv_bfloat16 *rslc = nullptr);
+int ozaki_digits_cols(cudaStream_t s, const double *X, int ld, int ncols, int K, double *scale, __nv_bfloat16 *dst,
+                      unsigned long long *zero_cm, const int *skip);
 
 constexpr int NS_INIT = 6;          // Newton-Schulz steps from X = 4/3 I
 constexpr int SMALL_COLS = 8;       // solves / G products this narrow use the CUDA cores
@@ -63,8 +68,9 @@ struct SolveWs {
 };
 
 struct Mixed {
-    float *X, *P;                          // approximate inverse, N x N work (column-major)
+    float *X;                              // approximate inverse (column-major)
     __nv_bfloat16 *Aslc, *XslcB, *XslcA, *Wslc;   // 3-slice operands of the inverse update (3 x N x N)
+    __nv_bfloat16 *XnA, *XnB;              // the new X's slices, written by the update's second product
     // per-stage operands of the column solves and G-apply, double-buffered by
     // stage parity: the base chain builds stage s+1's while the columns of
     // stage s still read stage s's
@@ -120,12 +126,6 @@ __global__ void k_colscale_from_max(const unsigned long long *colmax, int n, dou
     if (j < n) scale[j] = __longlong_as_double((long long)colmax[j]);
 }
 
-__global__ void k_zero_u64(unsigned long long *p, int n, const int *skip) {
-    if (skip && *skip) return;
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n) p[j] = 0ull;
-}
-
 // Convergence test after residual `it` (0-based) and its correction: per
 // column the residual left after the correction is estimated as
 // |R_it| (|R_it| / |R_it-1|) (the refinement is a linear iteration with a
@@ -173,6 +173,34 @@ __global__ void k_converged(const unsigned long long *cm, const unsigned long lo
     }
 }
 
+// Start of a wide solve, one block per column: Psi <- B, max|Psi_j| -> psis,
+// and the 2 bf16 slices of Psi as the right operand of X Psi.
+__global__ void k_prep_psi(const double *__restrict__ B, int N, int ncols, double *Psi, double *psis,
+                           __nv_bfloat16 *slc) {
+    __shared__ double red[32];
+    const int col = blockIdx.x;
+    const double *b = B + (size_t)col * N;
+    double m = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double x = b[i];
+        Psi[(size_t)col * N + i] = x;
+        m = fmax(m, fabs(x));
+        float v = (float)x;
+        const __nv_bfloat16 b0 = __float2bfloat16_rn(v);
+        v -= __bfloat162float(b0);
+        slc[(size_t)col * N + i] = b0;
+        slc[((size_t)ncols + col) * N + i] = __float2bfloat16_rn(v);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) psis[col] = m;
+    }
+}
+
 template <typename T>
 int alloc(T **p, size_t n) {
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (n ? n : 1));
@@ -188,11 +216,27 @@ int ns_step(Ctx *c, bool record, const int *skip) {
     const int N = c->N;
     cudaStream_t s = c->stream;
     if (record) WW_CUDA_TRY(cudaMemsetAsync(m->nsres_last, 0, sizeof(unsigned), s));
-    WW_TRY(tc_slice_f32(s, m->X, N, N, N, 0, 0.f, 3, m->XslcB, nullptr, skip));                      // columns of X
-    WW_TRY(tc_gemm_f32acc(s, m->Aslc, m->XslcB, N, N, N, 0, m->P, nullptr, N, 1.0, m->err, skip));   // P = A X
-    WW_TRY(tc_slice_f32(s, m->P, N, N, N, 0, 2.f, 3, m->Wslc, record ? m->nsres_last : nullptr, skip));   // 2I - P
-    WW_TRY(tc_slice_f32(s, m->X, N, N, N, 1, 0.f, 3, m->XslcA, nullptr, skip));                      // rows of X
-    WW_TRY(tc_gemm_f32acc(s, m->XslcA, m->Wslc, N, N, N, 0, m->X, nullptr, N, 1.0, m->err, skip));   // X = X W
+    // W = 2I - A X, written straight as the slices of the next product's right operand
+    TcOut o3{};
+    o3.mode = 3;
+    o3.shift = 2.f;
+    o3.s_col = m->Wslc;
+    o3.dev_max = record ? m->nsres_last : nullptr;
+    WW_TRY(tc_gemm_f32acc_sliced(s, m->Aslc, m->XslcB, N, N, N, o3, m->err, skip));
+    // X <- X W: the FP32 X, its slices for the next update, and this stage's rows of X
+    TcOut o4{};
+    o4.mode = 4;
+    o4.Cf = m->X;
+    o4.ldc = N;
+    o4.s_col = m->XnB;
+    o4.s_row = m->XnA;
+    o4.s_row2 = m->Xrow[c->par];
+    WW_TRY(tc_gemm_f32acc_sliced(s, m->XslcA, m->Wslc, N, N, N, o4, m->err, skip));
+    // the product above still reads XslcA while it writes: its slices land in XnA / XnB
+    // and move over afterwards (after a skipped update both already hold the same data)
+    const size_t bytes = sizeof(__nv_bfloat16) * 3 * (size_t)N * N;
+    WW_CUDA_TRY(cudaMemcpyAsync(m->XslcA, m->XnA, bytes, cudaMemcpyDeviceToDevice, s));
+    WW_CUDA_TRY(cudaMemcpyAsync(m->XslcB, m->XnB, bytes, cudaMemcpyDeviceToDevice, s));
     if (record) {
         k_fold_nsres<<<1, 1, 0, s>>>(m->nsres_last, m->nsres);
         WW_CUDA_TRY(cudaGetLastError());
@@ -212,7 +256,8 @@ int mixed_create(Ctx *c) {
 #define MA(p, n) \
     if (st == WW_OK) st = alloc(&(p), (n))
     MA(m->X, NN);
-    MA(m->P, NN);
+    MA(m->XnA, 3 * NN);
+    MA(m->XnB, 3 * NN);
     MA(m->Aslc, 3 * NN);
     MA(m->XslcB, 3 * NN);
     MA(m->XslcA, 3 * NN);
@@ -261,7 +306,7 @@ int mixed_create(Ctx *c) {
 void mixed_destroy(Ctx *c) {
     Mixed *m = c->mx;
     if (!m) return;
-    void *ptrs[] = {m->X,          m->P,           m->Aslc,       m->XslcB,        m->XslcA,       m->Wslc,
+    void *ptrs[] = {m->X,          m->XnA,         m->XnB,        m->Aslc,       m->XslcB,        m->XslcA,       m->Wslc,
                     m->Xrow[0],     m->Xrow[1],     m->Kd[0],      m->Kd[1],        m->Gd[0],       m->Gd[1],
                     m->Ks[0],       m->Ks[1],       m->Gs[0],      m->Gs[1],        m->Ke,          m->Ge,
                     m->Rd,          m->Rs,          m->Re,         m->Bslc,         m->wide.R,      m->wide.Psi,
@@ -290,17 +335,20 @@ int mixed_setup(Ctx *c, int fresh, int update) {
         skip = m->ns_skip;
     }
     WW_TRY(tc_slice_f64(s, c->A, N, N, N, 1, 0.f, 3, m->Aslc, skip));   // rows of A
+    const int q = c->par;
     if (fresh) {
         const size_t NN = (size_t)N * N;
         k_scaled_identity<<<(unsigned)((NN + 255) / 256), 256, 0, s>>>(m->X, N, 4.f / 3.f);
         WW_CUDA_TRY(cudaGetLastError());
+        WW_TRY(tc_slice_f32(s, m->X, N, N, N, 0, 0.f, 3, m->XslcB));   // columns of X
+        WW_TRY(tc_slice_f32(s, m->X, N, N, N, 1, 0.f, 3, m->XslcA));   // rows of X
         for (int i = 0; i < NS_INIT; ++i) WW_TRY(ns_step(c, false, nullptr));
         WW_CUDA_TRY(cudaMemsetAsync(m->nsres_last, 0xFF, sizeof(unsigned), s));
     } else {
         WW_TRY(ns_step(c, skip == nullptr, skip));
     }
-    const int q = c->par;
-    WW_TRY(tc_slice_f32(s, m->X, N, N, N, 1, 0.f, 2, m->Xrow[q]));   // rows of the (new) X, for this stage
+    // an update left out on the device leaves this stage's rows of X to a slice of X
+    if (skip) WW_TRY(tc_slice_f32(s, m->X, N, N, N, 1, 0.f, 2, m->Xrow[q], nullptr, skip, 1));
     WW_TRY(ozaki_digits(s, c->A, N, N, N, 0, 0.5f, m->Ke, m->Ks[q], m->Kd[q], nullptr));   // K = A - I/2
     WW_TRY(ozaki_digits(s, c->G, N, N, N, 0, 0.f, m->Ge, m->Gs[q], m->Gd[q], nullptr));
     return WW_OK;
@@ -314,24 +362,24 @@ int mixed_solve(Ctx *c, double *B, int ncols) {
     const bool narrow = ncols <= SMALL_COLS;
     SolveWs &w = narrow ? m->nar : m->wide;
     const unsigned cg = (unsigned)((ncols + 255) / 256);
-    WW_CUDA_TRY(cudaMemcpyAsync(w.Psi, B, sizeof(double) * N * ncols, cudaMemcpyDeviceToDevice, s));
     WW_CUDA_TRY(cudaMemsetAsync(w.done, 0, sizeof(int), s));
-    // column maxima of Psi (scale of the convergence test)
-    k_colmax<<<ncols, 256, 0, s>>>(w.Psi, N, w.colmax, nullptr);
-    k_colscale_from_max<<<cg, 256, 0, s>>>(w.colmax, ncols, w.psis, nullptr);
-    WW_CUDA_TRY(cudaGetLastError());
-    // M = X Psi
+    // Psi = B, the column maxima of Psi (scale of the convergence test), M = X Psi
     if (narrow) {
+        WW_CUDA_TRY(cudaMemcpyAsync(w.Psi, B, sizeof(double) * N * ncols, cudaMemcpyDeviceToDevice, s));
+        k_colmax<<<ncols, 256, 0, s>>>(w.Psi, N, w.colmax, nullptr);
+        k_colscale_from_max<<<cg, 256, 0, s>>>(w.colmax, ncols, w.psis, nullptr);
+        WW_CUDA_TRY(cudaGetLastError());
         WW_TRY(gemv_narrow_f32(s, N, ncols, N, m->X, N, w.Psi, N, 0.0, B, N));
     } else {
-        WW_TRY(tc_slice_f64(s, w.Psi, N, ncols, N, 0, 0.f, 2, m->Bslc));
+        k_prep_psi<<<ncols, 256, 0, s>>>(B, N, ncols, w.Psi, w.psis, m->Bslc);
+        WW_CUDA_TRY(cudaGetLastError());
         WW_TRY(tc_gemm_2x2(s, m->Xrow[q], m->Bslc, N, ncols, N, 1, nullptr, B, N, 1.0, m->err));
     }
     unsigned long long *cm_prev = w.colmax0, *cm = w.colmax;
     const int *done = w.done;
     const int nit = c->max_refine < 1 ? 1 : c->max_refine;
     for (int it = 0; it < nit; ++it) {
-        // R = Psi - A M_it (FP64-accurate) and max|R_j|
+        // R = Psi - A M_it (FP64-accurate) and max|R_j|, then M += X R
         if (narrow) {
             WW_TRY(resid_narrow(s, N, ncols, N, c->A, N, B, N, w.Psi, N, w.R, N, done));
             k_colmax<<<ncols, 256, 0, s>>>(w.R, N, cm, done);
@@ -339,17 +387,13 @@ int mixed_solve(Ctx *c, double *B, int ncols) {
             k_colscale_from_max<<<cg, 256, 0, s>>>(reinterpret_cast<unsigned long long *>(w.mscale), ncols,
                                                    w.mscale, done);
             WW_CUDA_TRY(cudaGetLastError());
-        } else {
-            k_zero_u64<<<cg, 256, 0, s>>>(cm, ncols, done);
-            WW_TRY(ozaki_digits(s, B, N, ncols, N, 1, 0.f, m->Re, m->Rs, m->Rd, done));   // scales of M -> Rs
-            WW_TRY(ozaki_gemm(s, m->Kd[q], m->Ks[q], m->Rd, m->Rs, N, ncols, N, 1, w.R, N, w.Psi, N, B, N, cm,
-                              m->err, done));
-        }
-        // M += X R
-        if (narrow) {
             WW_TRY(gemv_narrow_f32(s, N, ncols, N, m->X, N, w.R, N, 1.0, B, N, done));
         } else {
-            WW_TRY(tc_slice_f64(s, w.R, N, ncols, N, 0, 0.f, 2, m->Bslc, done));
+            // digits and scales of M (scales -> Rs), max|R| reset; the residual
+            // kernel writes R straight into the slices of the correction's operand
+            WW_TRY(ozaki_digits_cols(s, B, N, ncols, N, m->Rs, m->Rd, cm, done));
+            WW_TRY(ozaki_gemm(s, m->Kd[q], m->Ks[q], m->Rd, m->Rs, N, ncols, N, 1, nullptr, N, w.Psi, N, B, N, cm,
+                              m->err, done, m->Bslc));
             WW_TRY(tc_gemm_2x2(s, m->Xrow[q], m->Bslc, N, ncols, N, 2, nullptr, B, N, 1.0, m->err, done));
         }
         // converged after this correction?

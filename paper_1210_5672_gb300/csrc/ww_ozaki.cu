@@ -63,6 +63,7 @@ struct OzOut {
     const double *Mh;
     int ldm;
     unsigned long long *colmax;   // mode 1: per-column max |R| (bits of a positive double), or NULL
+    __nv_bfloat16 *rslc;          // mode 1: 2 bf16 slices of R ([2][Nn][M], as the next product's B), or NULL
 };
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
@@ -202,7 +203,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                     } else {
                         const double r = (out.Psi[(size_t)col * out.ldpsi + row] -
                                           0.5 * out.Mh[(size_t)col * out.ldm + row]) - val;
-                        out.C[ic] = r;
+                        if (out.C) out.C[ic] = r;
+                        if (out.rslc) {   // the residual as the right operand of the correction X R
+                            float v = (float)r;
+                            const __nv_bfloat16 b0 = __float2bfloat16_rn(v);
+                            v -= __bfloat162float(b0);
+                            out.rslc[(size_t)col * M + row] = b0;
+                            out.rslc[((size_t)Nn + col) * M + row] = __float2bfloat16_rn(v);
+                        }
                         if (out.colmax)
                             atomicMax(&out.colmax[col], (unsigned long long)__double_as_longlong(fabs(r)));
                     }
@@ -234,23 +242,6 @@ __global__ void k_expmax_rows(const double *__restrict__ X, int ld, int rows, in
     atomicMax(&emax[r], m);
 }
 
-// biased-exponent maxima of the columns (one block per column)
-__global__ void k_expmax_cols(const double *__restrict__ X, int ld, int rows, int *emax, const int *skip) {
-    if (skip && *skip) return;
-    __shared__ int red[32];
-    const double *col = X + (size_t)blockIdx.x * ld;
-    int m = 0;
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) m = max(m, bexp(col[r]));
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
-        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (threadIdx.x == 0) emax[blockIdx.x] = m;
-    }
-}
-
 // scale 2^ea from the biased exponent maximum: 2^(emax - 1022) > max |x|
 __global__ void k_scales(const int *__restrict__ emax, int n, double *scale, const int *skip) {
     if (skip && *skip) return;
@@ -260,28 +251,19 @@ __global__ void k_scales(const int *__restrict__ emax, int n, double *scale, con
     scale[i] = e == 0 ? 1.0 : ldexp(1.0, e - 1022);
 }
 
-// 7 digits of every entry.  side 0 (left operand, rows of a column-major
-// M x K matrix): dst[p][i][k]; side 1 (right operand, columns of a K x Nn
-// column-major matrix): dst[q][j][k].  Digits are computed in 64-bit fixed
-// point: F = x 2^-ea 2^60, a_p = round(F / 2^{54 - 7(p-1)}).
-__global__ void k_digits(const double *__restrict__ X, int ld, int rows, int K, int side, float diag_shift,
+// 7 digits of every entry of the left operand (the rows of a column-major
+// M x K matrix, minus diag_shift on its diagonal): dst[p][i][k].  Digits are
+// computed in 64-bit fixed point: F = x 2^-ea 2^60, a_p = round(F / 2^{54 - 7(p-1)}).
+__global__ void k_digits(const double *__restrict__ X, int ld, int rows, int K, float diag_shift,
                          const int *__restrict__ emax, __nv_bfloat16 *dst, const int *skip) {
     if (skip && *skip) return;
     __shared__ long long tile[32][33];
-    const int t0 = blockIdx.y * 32, k0 = blockIdx.x * 32;   // t: row (side 0) or column (side 1)
+    const int t0 = blockIdx.y * 32, k0 = blockIdx.x * 32;   // t: row of the operand
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     for (int yy = ty; yy < 32; yy += 8) {
-        int t, k;
-        double x;
-        if (side == 0) {   // read coalesced along the rows of the column-major source
-            t = t0 + tx;
-            k = k0 + yy;
-            x = (t < rows && k < K) ? X[(size_t)k * ld + t] : 0.0;
-        } else {
-            t = t0 + yy;
-            k = k0 + tx;
-            x = (t < rows && k < K) ? X[(size_t)t * ld + k] : 0.0;
-        }
+        // read coalesced along the rows of the column-major source
+        const int t = t0 + tx, k = k0 + yy;
+        double x = (t < rows && k < K) ? X[(size_t)k * ld + t] : 0.0;
         if (diag_shift != 0.f && t == k) x -= (double)diag_shift;
         long long F = 0;
         if (t < rows && k < K) {
@@ -294,10 +276,7 @@ __global__ void k_digits(const double *__restrict__ X, int ld, int rows, int K, 
                 if (bits < 0) F = -F;
             }
         }
-        if (side == 0)
-            tile[yy][tx] = F;   // tile[k][t]
-        else
-            tile[tx][yy] = F;
+        tile[yy][tx] = F;   // tile[k][t]
     }
     __syncthreads();
     for (int yy = ty; yy < 32; yy += 8) {
@@ -314,7 +293,60 @@ __global__ void k_digits(const double *__restrict__ X, int ld, int rows, int K, 
     }
 }
 
+// Right operand (side 1) in one pass per column: max exponent, scale, the 7
+// digits, and (optionally) a zeroed column maximum for the product's residual.
+__global__ void k_col_digits(const double *__restrict__ X, int ld, int ncols, int K, double *scale,
+                             __nv_bfloat16 *dst, unsigned long long *zero_cm, const int *skip) {
+    if (skip && *skip) return;
+    __shared__ int red[32];
+    const int col = blockIdx.x;
+    const double *x = X + (size_t)col * ld;
+    int m = 0;
+    for (int r = threadIdx.x; r < K; r += blockDim.x) m = max(m, bexp(x[r]));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) {
+            red[0] = m;
+            scale[col] = m == 0 ? 1.0 : ldexp(1.0, m - 1022);
+            if (zero_cm) zero_cm[col] = 0ull;
+        }
+    }
+    __syncthreads();
+    const int em = red[0];
+    for (int r = threadIdx.x; r < K; r += blockDim.x) {
+        const long long bits = __double_as_longlong(x[r]);
+        const int e = (int)((bits >> 52) & 0x7FF);
+        long long F = 0;
+        if (e != 0) {
+            const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+            const int sh = e - em + 7;
+            F = sh >= 0 ? (mant << sh) : (sh > -63 ? (mant >> -sh) : 0);
+            if (bits < 0) F = -F;
+        }
+#pragma unroll
+        for (int p = 0; p < OZ_S; ++p) {
+            const int sh = 54 - 7 * p;
+            const long long a = (F + (1LL << (sh - 1))) >> sh;   // arithmetic shift: round to nearest
+            F -= a * (1LL << sh);
+            dst[((size_t)p * ncols + col) * K + r] = __int2bfloat16_rn((int)a);
+        }
+    }
+}
+
 }  // namespace
+
+// Digits and scales of the columns of the K x ncols column-major X (the right
+// operand) in one kernel; zero_cm (optional) is set to 0 for each column.
+int ozaki_digits_cols(cudaStream_t s, const double *X, int ld, int ncols, int K, double *scale, __nv_bfloat16 *dst,
+                      unsigned long long *zero_cm, const int *skip) {
+    k_col_digits<<<ncols, 256, 0, s>>>(X, ld, ncols, K, scale, dst, zero_cm, skip);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
 
 // Digits and scales of an operand.  side 0: left operand = the rows of the
 // column-major rows x K matrix X (minus diag_shift on its diagonal);
@@ -322,16 +354,16 @@ __global__ void k_digits(const double *__restrict__ X, int ld, int rows, int K, 
 // emax: int[rows] work (zeroed here); scale: double[rows]; dst: 7 x rows x K bf16.
 int ozaki_digits(cudaStream_t s, const double *X, int ld, int rows, int K, int side, float diag_shift, int *emax,
                  double *scale, __nv_bfloat16 *dst, const int *skip) {
-    if (side == 0) {
-        WW_CUDA_TRY(cudaMemsetAsync(emax, 0, sizeof(int) * rows, s));
-        dim3 g((rows + 127) / 128, (K + 63) / 64);
-        k_expmax_rows<<<g, 128, 0, s>>>(X, ld, rows, K, diag_shift, emax);
-    } else {
-        k_expmax_cols<<<rows, 256, 0, s>>>(X, ld, K, emax, skip);
+    if (side == 1) {
+        if (diag_shift != 0.f) return fail(WW_ERR_ARG, "ozaki_digits: no diagonal shift on a right operand");
+        return ozaki_digits_cols(s, X, ld, rows, K, scale, dst, nullptr, skip);
     }
+    WW_CUDA_TRY(cudaMemsetAsync(emax, 0, sizeof(int) * rows, s));
+    dim3 g((rows + 127) / 128, (K + 63) / 64);
+    k_expmax_rows<<<g, 128, 0, s>>>(X, ld, rows, K, diag_shift, emax);
     k_scales<<<(rows + 255) / 256, 256, 0, s>>>(emax, rows, scale, skip);
     dim3 gd((K + 31) / 32, (rows + 31) / 32);
-    k_digits<<<gd, 256, 0, s>>>(X, ld, rows, K, side, diag_shift, emax, dst, skip);
+    k_digits<<<gd, 256, 0, s>>>(X, ld, rows, K, diag_shift, emax, dst, skip);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
@@ -339,13 +371,13 @@ int ozaki_digits(cudaStream_t s, const double *X, int ld, int rows, int K, int s
 // mode 0: C += A B ; mode 1: C = Psi - 0.5 Mh - A B  (A = left digits, B = right digits)
 int ozaki_gemm(cudaStream_t s, const __nv_bfloat16 *Ad, const double *sa, const __nv_bfloat16 *Bd, const double *sb,
                int M, int Nn, int K, int mode, double *C, int ldc, const double *Psi, int ldpsi, const double *Mh,
-               int ldm, unsigned long long *colmax, int *err, const int *skip) {
+               int ldm, unsigned long long *colmax, int *err, const int *skip, __nv_bfloat16 *rslc) {
     if (K % OZ_BK != 0) return fail(WW_ERR_ARG, "ozaki_gemm: K must be a multiple of 64");
     CUtensorMap ta, tb;
     WW_TRY(tc_make_map(&ta, Ad, K, (long)OZ_S * M, OZ_BM));
     WW_TRY(tc_make_map(&tb, Bd, K, (long)OZ_S * Nn, OZ_BN));
     WW_CUDA_TRY(cudaFuncSetAttribute(k_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
-    OzOut o{mode, C, ldc, Psi, ldpsi, Mh, ldm, colmax};
+    OzOut o{mode, C, ldc, Psi, ldpsi, Mh, ldm, colmax, rslc};
     dim3 grid((M + OZ_BM - 1) / OZ_BM, (Nn + OZ_BN - 1) / OZ_BN);
     k_ozaki<<<grid, OZ_THREADS, OZ_SMEM, s>>>(ta, tb, M, Nn, K, sa, sb, o, err, skip);
     WW_CUDA_TRY(cudaGetLastError());
@@ -378,7 +410,7 @@ extern "C" int ww_selftest_ozaki(const double *A, const double *B, int M, int Nn
     if (st == WW_OK) st = ozaki_digits(s, A, M, M, K, 0, 0.f, ea, sa, Ad, nullptr);
     if (st == WW_OK) st = ozaki_digits(s, B, K, Nn, K, 1, 0.f, eb, sb, Bd, nullptr);
     if (st == WW_OK)
-        st = ozaki_gemm(s, Ad, sa, Bd, sb, M, Nn, K, 0, C, M, nullptr, 0, nullptr, 0, nullptr, err, nullptr);
+        st = ozaki_gemm(s, Ad, sa, Bd, sb, M, Nn, K, 0, C, M, nullptr, 0, nullptr, 0, nullptr, err, nullptr, nullptr);
     if (st == WW_OK) st = dgemm(s, M, Nn, K, 1.0, A, M, B, K, 0.0, C0, M);
     if (st == WW_OK && cudaDeviceSynchronize() != cudaSuccess) st = fail(WW_ERR_CUDA, "selftest sync");
     if (st == WW_OK) {

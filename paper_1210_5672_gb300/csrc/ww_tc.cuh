@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -53,20 +54,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 
 // Wait for phase `parity` of *bar, giving up after ~1 s: then set *err and
 // return false (the caller carries on so that the block still exits).  Once
-// *err is set, by this block or any other, every later wait returns at once,
-// so a failed launch drains in microseconds instead of 1 s per wait.
+// *err is set, by this block or any other, every later wait gives up within
+// 256 polls, so a failed launch drains quickly instead of taking 1 s per wait.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
     if (mbar_try_wait(bar, parity)) return true;
+    // The barrier is polled back to back; the error flag (a global load) and the
+    // clock are only read every 256 polls, so a phase that completes is seen at
+    // once rather than after an L2 round trip.
     const uint64_t t0 = globaltimer();
     volatile int *verr = err;
-    while (!mbar_try_wait(bar, parity)) {
-        if (*verr) return false;
-        if (globaltimer() - t0 > 1000000000ull) {
-            atomicOr(err, 1);
-            return false;
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 0) {
+            if (*verr) return false;
+            if (globaltimer() - t0 > 1000000000ull) {
+                atomicOr(err, 1);
+                return false;
+            }
         }
     }
-    return true;
 }
 
 // ---------------------------------------------------------------- TMA
@@ -158,4 +164,19 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 }
 
 }  // namespace tc
+
+// output of a sliced tensor-core product (ww_tcgemm.cu: modes 0..4)
+struct TcOut {
+    int mode;
+    float *Cf;
+    double *Cd;
+    int ldc;
+    double alpha;
+    float shift;              // mode 3: W = shift I - C
+    __nv_bfloat16 *s_col;     // modes 3, 4: 3 slices as a right operand
+    __nv_bfloat16 *s_row;     // mode 4: 3 slices as a left operand
+    __nv_bfloat16 *s_row2;    // mode 4: 2 slices as a left operand
+    unsigned *dev_max;        // mode 3: max |W - shift/2 I| (fp32 bits), or NULL
+};
+
 }  // namespace ww

@@ -10,7 +10,7 @@
 // 1 TFLOP/s for FP64.
 //
 // One CTA computes a 128 x BN tile.  Warp 0 issues TMA loads of all slices of
-// a 64-wide K chunk into a 2-stage ring; warp 1 owns the TMEM accumulator and
+// a 64-wide K chunk into a ring of 2-4 stages; warp 1 owns the TMEM accumulator and
 // issues tcgen05.mma (M = 128, N = BN, K = 16) for every pair; warps 2..5 read
 // the accumulator with tcgen05.ld and write C.  Every mbarrier wait is
 // bounded (~1 s); a timeout sets *err and the block still exits.
@@ -31,7 +31,6 @@ namespace {
 
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;
-constexpr int TC_STAGES = 2;
 constexpr int TC_THREADS = 192;
 
 struct Pairs {
@@ -39,28 +38,39 @@ struct Pairs {
     unsigned char p[16], q[16];
 };
 
+}  // namespace
+
+// Where a product goes (ww_tc.cuh declares the struct; modes:
+//   0: Cf = alpha C (FP32)      1: Cd = alpha C      2: Cd += alpha C
+//   3: the 3 bf16 slices of W = shift I - C, column-major as a right operand
+//      (s_col[k][j][i] = slice k of W(i, j)), and max|W - shift/2 I| into dev_max
+//   4: Cf = C, plus the 3 slices of C as a right operand (s_col) and as a left
+//      operand (s_row[k][i][j]), and 2 more left-operand slices (s_row2)).
+namespace {
+
+// ring depth: as many K-chunk stages as fit in ~200 KB, at most 4
 template <int BN, int SA, int SB>
 struct TcSmem {
     static constexpr int A_TILE = TC_BM * TC_BK * 2;   // bytes
     static constexpr int B_TILE = BN * TC_BK * 2;
     static constexpr int STAGE = SA * A_TILE + SB * B_TILE;
-    static constexpr int BYTES = TC_STAGES * STAGE + 1024 /* align */ + 256 /* barriers */;
+    static constexpr int STAGES = (200 * 1024 / STAGE) < 4 ? (200 * 1024 / STAGE) : 4;
+    static constexpr int BYTES = STAGES * STAGE + 1024 /* align */ + 256 /* barriers */;
 };
 
 template <int BN, int SA, int SB>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int Nn, int K,
-              Pairs pairs, int out_mode, float *Cf, double *Cd, int ldc, double alpha, int *err,
-              const int *skip) {
+              Pairs pairs, TcOut o, int *err, const int *skip) {
     if (skip && *skip) return;   // a step the caller decided on the device to leave out
     using L = TcSmem<BN, SA, SB>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t base = tc::smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024 - (base & 1023)) & 1023);
     uint8_t *tiles = smem;
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + TC_STAGES * L::STAGE);
-    uint64_t *empty = full + TC_STAGES;
-    uint64_t *done = empty + TC_STAGES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::STAGES * L::STAGE);
+    uint64_t *empty = full + L::STAGES;
+    uint64_t *done = empty + L::STAGES;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -68,7 +78,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int nk = K / TC_BK;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < L::STAGES; ++s) {
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
@@ -89,8 +99,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
         for (int kc = 0; kc < nk; ++kc) {
-            const int s = kc % TC_STAGES;
-            const uint32_t ph = (kc / TC_STAGES) & 1;
+            const int s = kc % L::STAGES;
+            const uint32_t ph = (kc / L::STAGES) & 1;
             tc::mbar_wait(&empty[s], ph ^ 1, err);
             tc::mbar_arrive_expect_tx(&full[s], L::STAGE);
             uint8_t *st = tiles + s * L::STAGE;
@@ -104,8 +114,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ---------------- MMA issuer
         constexpr uint32_t idesc = tc::idesc_bf16(TC_BM, BN);
         for (int kc = 0; kc < nk; ++kc) {
-            const int s = kc % TC_STAGES;
-            const uint32_t ph = (kc / TC_STAGES) & 1;
+            const int s = kc % L::STAGES;
+            const uint32_t ph = (kc / L::STAGES) & 1;
             tc::mbar_wait(&full[s], ph, err);
             tc::fence_after();
             const uint32_t st = tc::smem_u32(tiles + s * L::STAGE);
@@ -126,25 +136,79 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int row = m0 + quarter * 32 + lane;
         tc::mbar_wait(done, 0, err);
         tc::fence_after();
+        float dmax = 0.f;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 32) {
             float v[32];
             tc::tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + c0, v);
             if (row < M) {
+                if (o.mode <= 2) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = n0 + c0 + j;
-                    if (col < Nn) {
-                        const size_t idx = (size_t)col * ldc + row;
-                        if (out_mode == 0)
-                            Cf[idx] = v[j] * (float)alpha;   // fp32 result: no FP64 work
-                        else if (out_mode == 1)
-                            Cd[idx] = alpha * (double)v[j];
-                        else
-                            Cd[idx] += alpha * (double)v[j];
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = n0 + c0 + j;
+                        if (col < Nn) {
+                            const size_t idx = (size_t)col * o.ldc + row;
+                            if (o.mode == 0)
+                                o.Cf[idx] = v[j] * (float)o.alpha;   // fp32 result: no FP64 work
+                            else if (o.mode == 1)
+                                o.Cd[idx] = o.alpha * (double)v[j];
+                            else
+                                o.Cd[idx] += o.alpha * (double)v[j];
+                        }
+                    }
+                } else if (o.mode == 3) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = n0 + c0 + j;
+                        if (col < Nn) {
+                            const bool dg = col == row;
+                            float w = (dg ? o.shift : 0.f) - v[j];
+                            dmax = fmaxf(dmax, fabsf(w - (dg ? 0.5f * o.shift : 0.f)));
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) {
+                                const __nv_bfloat16 b = __float2bfloat16_rn(w);
+                                o.s_col[((size_t)k * Nn + col) * M + row] = b;
+                                w -= __bfloat162float(b);
+                            }
+                        }
+                    }
+                } else if (n0 + c0 < Nn) {   // mode 4 (square products, whole 32-column groups)
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {   // 8 columns at a time: one 16-byte store per slice
+                        uint32_t pk[3][4];
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) {
+                            const int j = 8 * g + jj, col = n0 + c0 + j;
+                            o.Cf[(size_t)col * o.ldc + row] = v[j];
+                            float w = v[j];
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) {
+                                const __nv_bfloat16 b = __float2bfloat16_rn(w);
+                                o.s_col[((size_t)k * Nn + col) * M + row] = b;
+                                const uint32_t u = (uint32_t)__bfloat16_as_ushort(b);
+                                if (jj & 1)
+                                    pk[k][jj >> 1] |= u << 16;
+                                else
+                                    pk[k][jj >> 1] = u;
+                                w -= __bfloat162float(b);
+                            }
+                        }
+                        const size_t off = (size_t)row * Nn + n0 + c0 + 8 * g;
+#pragma unroll
+                        for (int k = 0; k < 3; ++k)
+                            *reinterpret_cast<uint4 *>(o.s_row + (size_t)k * M * Nn + off) =
+                                make_uint4(pk[k][0], pk[k][1], pk[k][2], pk[k][3]);
+#pragma unroll
+                        for (int k = 0; k < 2; ++k)
+                            *reinterpret_cast<uint4 *>(o.s_row2 + (size_t)k * M * Nn + off) =
+                                make_uint4(pk[k][0], pk[k][1], pk[k][2], pk[k][3]);
                     }
                 }
             }
+        }
+        if (o.mode == 3 && o.dev_max) {
+            for (int off = 16; off > 0; off >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+            if (lane == 0) atomicMax(o.dev_max, __float_as_uint(dmax));
         }
     }
     tc::fence_before();
@@ -194,8 +258,10 @@ int tc_make_map(CUtensorMap *map, const void *ptr, int K, long rows, int box_row
 namespace {
 
 template <int BN, int SA, int SB>
-int launch_tc(cudaStream_t s, const void *A, const void *B, int M, int Nn, int K, const Pairs &pairs, int out_mode,
-              float *Cf, double *Cd, int ldc, double alpha, int *err, const int *skip) {
+int launch_tc(cudaStream_t s, const void *A, const void *B, int M, int Nn, int K, const Pairs &pairs, const TcOut &o,
+              int *err, const int *skip) {
+    if (o.mode == 4 && (M != Nn || Nn % 32 != 0))
+        return fail(WW_ERR_ARG, "tc_gemm: slice output needs a square product with N a multiple of 32");
     using L = TcSmem<BN, SA, SB>;
     static_assert(L::BYTES <= 227 * 1024, "shared memory");
     CUtensorMap ta, tb;
@@ -204,7 +270,7 @@ int launch_tc(cudaStream_t s, const void *A, const void *B, int M, int Nn, int K
     auto kern = k_tc_gemm<BN, SA, SB>;
     WW_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES));
     dim3 grid((M + TC_BM - 1) / TC_BM, (Nn + BN - 1) / BN);
-    kern<<<grid, TC_THREADS, L::BYTES, s>>>(ta, tb, M, Nn, K, pairs, out_mode, Cf, Cd, ldc, alpha, err, skip);
+    kern<<<grid, TC_THREADS, L::BYTES, s>>>(ta, tb, M, Nn, K, pairs, o, err, skip);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
@@ -216,8 +282,9 @@ int launch_tc(cudaStream_t s, const void *A, const void *B, int M, int Nn, int K
 // optionally v -> shift*delta(r,k) - v.  S bf16 slices, v = sum_s slice_s + O(2^-8S |v|).
 template <typename T>
 __global__ void k_slice(const T *__restrict__ src, int ld, int rows, int K, int trans, float shift, int S,
-                        __nv_bfloat16 *dst, unsigned *dev_max, const int *skip) {
-    if (skip && *skip) return;
+                        __nv_bfloat16 *dst, unsigned *dev_max, const int *skip, int run_if_skipped) {
+    // skip: a device decision; run_if_skipped inverts it (this slice replaces a skipped step's output)
+    if (skip && ((*skip != 0) != (run_if_skipped != 0))) return;
     __shared__ float tile[32][33];
     float dmax = 0.f;   // with shift = 2: max |(2 delta - v) - delta| = max |delta - v|
     const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
@@ -260,9 +327,9 @@ __global__ void k_slice(const T *__restrict__ src, int ld, int rows, int K, int 
 }  // namespace
 
 int tc_slice_f32(cudaStream_t s, const float *src, int ld, int rows, int K, int trans, float shift, int S,
-                 __nv_bfloat16 *dst, unsigned *dev_max, const int *skip) {
+                 __nv_bfloat16 *dst, unsigned *dev_max, const int *skip, int run_if_skipped) {
     dim3 grid((K + 31) / 32, (rows + 31) / 32);
-    k_slice<float><<<grid, 256, 0, s>>>(src, ld, rows, K, trans, shift, S, dst, dev_max, skip);
+    k_slice<float><<<grid, 256, 0, s>>>(src, ld, rows, K, trans, shift, S, dst, dev_max, skip, run_if_skipped);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
@@ -270,7 +337,7 @@ int tc_slice_f32(cudaStream_t s, const float *src, int ld, int rows, int K, int 
 int tc_slice_f64(cudaStream_t s, const double *src, int ld, int rows, int K, int trans, float shift, int S,
                  __nv_bfloat16 *dst, const int *skip) {
     dim3 grid((K + 31) / 32, (rows + 31) / 32);
-    k_slice<double><<<grid, 256, 0, s>>>(src, ld, rows, K, trans, shift, S, dst, nullptr, skip);
+    k_slice<double><<<grid, 256, 0, s>>>(src, ld, rows, K, trans, shift, S, dst, nullptr, skip, 0);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
@@ -287,7 +354,13 @@ int tc_gemm_f32acc(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 
         P.p[i] = (unsigned char)pp[i];
         P.q[i] = (unsigned char)qq[i];
     }
-    return launch_tc<128, 3, 3>(s, A3, B3, M, Nn, K, P, out_mode, Cf, Cd, ldc, alpha, err, skip);
+    TcOut o{};
+    o.mode = out_mode;
+    o.Cf = Cf;
+    o.Cd = Cd;
+    o.ldc = ldc;
+    o.alpha = alpha;
+    return launch_tc<128, 3, 3>(s, A3, B3, M, Nn, K, P, o, err, skip);
 }
 
 // Product from 2 + 2 slices (pairs with p + q <= 1): relative accuracy ~2^-16,
@@ -304,7 +377,28 @@ int tc_gemm_2x2(cudaStream_t s, const __nv_bfloat16 *A2, const __nv_bfloat16 *B2
         P.p[i] = (unsigned char)pp[i];
         P.q[i] = (unsigned char)qq[i];
     }
-    return launch_tc<128, 2, 2>(s, A2, B2, M, Nn, K, P, out_mode, Cf, Cd, ldc, alpha, err, skip);
+    TcOut o{};
+    o.mode = out_mode;
+    o.Cf = Cf;
+    o.Cd = Cd;
+    o.ldc = ldc;
+    o.alpha = alpha;
+    // 64-wide column tiles: 2x the CTAs of 128-wide ones for the narrow (513-column) products
+    return launch_tc<64, 2, 2>(s, A2, B2, M, Nn, K, P, o, err, skip);
+}
+
+// FP32-accurate product with a sliced output (modes 3 and 4 of TcOut), 3 + 3 slices
+int tc_gemm_f32acc_sliced(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 *B3, int M, int Nn, int K,
+                          const TcOut &o, int *err, const int *skip) {
+    if (K % TC_BK != 0) return fail(WW_ERR_ARG, "tc_gemm: K must be a multiple of 64");
+    Pairs P{};
+    const int pp[6] = {2, 1, 0, 1, 0, 0}, qq[6] = {0, 1, 2, 0, 1, 0};   // smallest terms first
+    P.n = 6;
+    for (int i = 0; i < 6; ++i) {
+        P.p[i] = (unsigned char)pp[i];
+        P.q[i] = (unsigned char)qq[i];
+    }
+    return launch_tc<128, 3, 3>(s, A3, B3, M, Nn, K, P, o, err, skip);
 }
 
 }  // namespace ww

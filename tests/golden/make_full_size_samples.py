@@ -1,0 +1,69 @@
+"""Write full_n2048_samples.json: the oracle's shooting map and sampled Jacobian
+columns on the N = 2048 workload (512 modes + T, 1024 RK4 steps, h = 1,
+c_1 = 0.4, c_k = 0.4^k u_k, seed 0), for the full-size parity test.
+
+Only the oracle computes here.  A Jacobian column d r / d c_k depends on the
+other coefficients only through the base trajectory, so the oracle runs a
+problem whose basis is [sum_k c_k cos kx, cos k1 x, cos k2 x, ...] with
+coefficients [1, 0, 0, ...]: the same initial surface and the same base
+trajectory, and variational columns only for the sampled modes (plus T).
+That keeps the run to ~9 columns; it is still the full 4096-stage trajectory
+with one N = 2048 LU per stage (about 40 minutes on 8 cores).
+
+    python tests/golden/make_full_size_samples.py
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle as O  # noqa: E402
+from paper_1210_5672_gb300 import workloads as W  # noqa: E402
+
+MODES = [1, 2, 3, 64, 255, 511, 512]   # sampled Jacobian columns (mode numbers); column 0 is T
+ROW_STRIDE = 16                        # sampled rows of r and J
+
+
+def main():
+    O.build()
+    w = W.LARGE
+    c, seed = W.coefficients(w)
+    x = 2 * np.pi * np.arange(w.N) / w.N
+    basis = np.zeros((2 * w.N, 1 + len(MODES)))
+    basis[: w.N, 0] = np.cos(np.outer(x, np.arange(1, w.n + 1))) @ c[1:]
+    for i, k in enumerate(MODES):
+        basis[: w.N, 1 + i] = np.cos(k * x)
+    cr = np.zeros(2 + len(MODES))
+    cr[0] = c[0]
+    cr[1] = 1.0
+    prob, keep = O.make_problem(w.N, 1 + len(MODES), g=w.g, tau=w.tau, h=w.h, steps=w.steps, basis=basis)
+    t0 = time.time()
+    r, J, f = O.shoot_jacobian(prob, cr)
+    elapsed = time.time() - t0
+    rows = list(range(0, w.N, ROW_STRIDE))
+    cols = {"T": J[:, 0]}
+    for i, k in enumerate(MODES):
+        cols[str(k)] = J[:, 2 + i]
+    out = {
+        "what": "oracle shoot_jacobian on the N2048_n512_steps1024_h1 workload, sampled",
+        "workload": w.name, "seed": seed, "N": w.N, "n": w.n, "steps": w.steps,
+        "T": c[0], "f": f, "r_norm": float(np.linalg.norm(r)),
+        "rows": rows, "r": [float(r[i]) for i in rows],
+        "columns": {k: {"norm": float(np.linalg.norm(v)), "values": [float(v[i]) for i in rows]}
+                    for k, v in cols.items()},
+        "oracle_threads": O.threads(), "oracle_seconds": round(elapsed, 1),
+    }
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "full_n2048_samples.json")
+    with open(path, "w") as fh:
+        json.dump(out, fh, indent=1)
+        fh.write("\n")
+    print(f"wrote {path} ({elapsed:.0f} s, {O.threads()} threads)")
+
+
+if __name__ == "__main__":
+    main()
