@@ -21,9 +21,9 @@
 //   hi = V0 2^14 + V1 2^7 + V2,  lo = V3 2^21 + V4 2^14 + V5 2^7 + V6,
 // and the result is 2^ea_i 2^fb_j (2^-26 hi + 2^-54 lo).
 //
-// Kernel.  One CTA per 128 x 64 output tile.  Warp 0: TMA producer (ring of 7
-// A-digit tiles of 128 x 64 and ring of 2 B stages holding all 7 B-digit
-// tiles of 64 x 64); warp 1: TMEM owner and tcgen05.mma issuer (M = 128,
+// Kernel.  One CTA per 128 x 64 output tile.  Warps 0 and 10: TMA producers
+// (ring of 7 A-digit tiles of 128 x 64 and ring of 2 B stages holding all 7
+// B-digit tiles of 64 x 64); warp 1: TMEM owner and tcgen05.mma issuer (M = 128,
 // K = 16, N = 64..256: the B digits of one A digit are issued together, 10
 // MMAs per K step instead of 28); warps 2..9: fold and epilogue, each thread
 // one row and 32 columns.  All waits are bounded.
@@ -38,7 +38,7 @@
 
 namespace ww {
 
-int tc_make_map(CUtensorMap *map, const void *ptr, int K, long rows, int box_rows);   // ww_tcgemm.cu
+int tc_make_map(CUtensorMap *map, const void *ptr, int K, long rows, int box_rows, int box_k);   // ww_tcgemm.cu
 
 namespace {
 
@@ -46,9 +46,13 @@ constexpr int OZ_S = 7;             // digits per operand
 constexpr int OZ_G = 7;             // groups g = 0..6
 constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 64;
 constexpr int OZ_KBLOCK = 16;       // K chunks (of 64) per exact block = 1024
-constexpr int OZ_ASLOTS = 7, OZ_BSLOTS = 2;   // 7 x 16 KB A tiles in flight: the ring is latency bound
+constexpr int OZ_ASLOTS = 7, OZ_BSLOTS = 2;   // one slot per A digit, two B stages
 constexpr int OZ_EPI_WARPS = 8;
-constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
+// warps: 0 producer (B and the even A digits), 1 MMA, 2..9 epilogue, 10 second
+// producer (the odd A digits).  One thread issues a TMA load every ~145 ns
+// whatever the box size, so two issuers double the rate of 8-16 KB boxes.
+constexpr int OZ_PROD2 = 2 + OZ_EPI_WARPS;
+constexpr int OZ_THREADS = 32 * (OZ_PROD2 + 1);
 constexpr int OZ_A_TILE = OZ_BM * OZ_BK * 2;           // 16 KB
 constexpr int OZ_B_TILE = OZ_BN * OZ_BK * 2;           // 8 KB
 constexpr int OZ_B_STAGE = OZ_S * OZ_B_TILE;           // 56 KB
@@ -110,23 +114,30 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     tc::fence_after();
     const uint32_t tmem = *tslot;
 
-    if (warp == 0 && lane == 0) {
-        // ------------------------------------------------ TMA producer
+    if (warp == 0 || warp == OZ_PROD2) {
+        // ------------------------------------------------ TMA producers (whole warps, one lane issues)
+        const uint32_t leader = tc::elect_one();
+        const int p0 = warp == 0 ? 0 : 1;   // A digits p0, p0 + 2, ...
         for (int kc = 0; kc < nk; ++kc) {
-            const int bs = kc % OZ_BSLOTS;
-            tc::mbar_wait(&b_empty[bs], ((kc / OZ_BSLOTS) & 1) ^ 1, err);
-            tc::mbar_arrive_expect_tx(&b_full[bs], OZ_B_STAGE);
-            for (int q = 0; q < OZ_S; ++q)
-                tc::tma_load_2d(&tmB, &b_full[bs], bring + bs * OZ_B_STAGE + q * OZ_B_TILE, kc * OZ_BK, q * Nn + n0);
-            for (int p = 0; p < OZ_S; ++p) {
+            if (warp == 0) {
+                const int bs = kc % OZ_BSLOTS;
+                tc::mbar_wait(&b_empty[bs], ((kc / OZ_BSLOTS) & 1) ^ 1, err);
+                tc::mbar_arrive_expect_tx_if(leader, &b_full[bs], OZ_B_STAGE);
+#pragma unroll
+                for (int q = 0; q < OZ_S; ++q)
+                    tc::tma_load_2d_if(leader, &tmB, &b_full[bs], bring + bs * OZ_B_STAGE + q * OZ_B_TILE,
+                                       kc * OZ_BK, q * Nn + n0);
+            }
+            for (int p = p0; p < OZ_S; p += 2) {
                 const int ai = kc * OZ_S + p, as = ai % OZ_ASLOTS;
                 tc::mbar_wait(&a_empty[as], ((ai / OZ_ASLOTS) & 1) ^ 1, err);
-                tc::mbar_arrive_expect_tx(&a_full[as], OZ_A_TILE);
-                tc::tma_load_2d(&tmA, &a_full[as], aring + as * OZ_A_TILE, kc * OZ_BK, p * M + m0);
+                tc::mbar_arrive_expect_tx_if(leader, &a_full[as], OZ_A_TILE);
+                tc::tma_load_2d_if(leader, &tmA, &a_full[as], aring + as * OZ_A_TILE, kc * OZ_BK, p * M + m0);
             }
         }
-    } else if (warp == 1 && lane == 0) {
-        // ------------------------------------------------ MMA issuer
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer (whole warp, one lane issues)
+        const uint32_t leader = tc::elect_one();
         for (int kc = 0; kc < nk; ++kc) {
             const int kb = kc / OZ_KBLOCK;
             const bool first = (kc % OZ_KBLOCK) == 0;
@@ -138,30 +149,32 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             tc::mbar_wait(&b_full[bs], (kc / OZ_BSLOTS) & 1, err);
             tc::fence_after();
             const uint32_t bst = tc::smem_u32(bring + bs * OZ_B_STAGE);
+#pragma unroll
             for (int p = 0; p < OZ_S; ++p) {
                 const int ai = kc * OZ_S + p, as = ai % OZ_ASLOTS;
                 tc::mbar_wait(&a_full[as], (ai / OZ_ASLOTS) & 1, err);
                 tc::fence_after();
-                const uint32_t ast = tc::smem_u32(aring + as * OZ_A_TILE);
+                const uint64_t da = tc::desc_k128(tc::smem_u32(aring + as * OZ_A_TILE));
                 // pairs (p, q), q = 0 .. 6-p, land in groups p .. 6: consecutive TMEM
                 // column blocks, and the B digits q are consecutive 64-row tiles of
                 // the stage, so up to four of them form one N = 256 operand.  One
                 // wide MMA reads the A digit once instead of once per q.
+#pragma unroll
                 for (int q0 = 0; q0 + p < OZ_G; q0 += 4) {
                     const int nq = min(4, OZ_G - p - q0);
                     const uint32_t id = tc::idesc_bf16(OZ_BM, OZ_BN * nq);
                     const uint32_t d = tmem + (uint32_t)((p + q0) * OZ_BN);
+                    const uint64_t db = tc::desc_k128(bst + q0 * OZ_B_TILE);
 #pragma unroll
-                    for (int kk = 0; kk < OZ_BK / 16; ++kk)
-                        tc::mma_bf16(d, tc::desc_k128(ast + kk * 32), tc::desc_k128(bst + q0 * OZ_B_TILE + kk * 32),
-                                     id, !(first && p == 0 && kk == 0));
+                    for (int kk = 0; kk < OZ_BK / 16; ++kk)   // +32 B per K step: +2 in the start-address field
+                        tc::mma_bf16_if(leader, d, da + 2 * kk, db + 2 * kk, id, !(first && p == 0 && kk == 0));
                 }
-                tc::mma_commit(&a_empty[as]);
+                tc::mma_commit_if(leader, &a_empty[as]);
             }
-            tc::mma_commit(&b_empty[bs]);
-            if ((kc % OZ_KBLOCK) == OZ_KBLOCK - 1 || kc == nk - 1) tc::mma_commit(acc_full);
+            tc::mma_commit_if(leader, &b_empty[bs]);
+            if ((kc % OZ_KBLOCK) == OZ_KBLOCK - 1 || kc == nk - 1) tc::mma_commit_if(leader, acc_full);
         }
-    } else if (warp >= 2) {
+    } else if (warp >= 2 && warp < OZ_PROD2) {
         // ------------------------------------------------ fold + epilogue
         const int ew = warp - 2;
         const int quarter = warp & 3;            // TMEM lane quarter this warp may access
@@ -374,8 +387,8 @@ int ozaki_gemm(cudaStream_t s, const __nv_bfloat16 *Ad, const double *sa, const 
                int ldm, unsigned long long *colmax, int *err, const int *skip, __nv_bfloat16 *rslc) {
     if (K % OZ_BK != 0) return fail(WW_ERR_ARG, "ozaki_gemm: K must be a multiple of 64");
     CUtensorMap ta, tb;
-    WW_TRY(tc_make_map(&ta, Ad, K, (long)OZ_S * M, OZ_BM));
-    WW_TRY(tc_make_map(&tb, Bd, K, (long)OZ_S * Nn, OZ_BN));
+    WW_TRY(tc_make_map(&ta, Ad, K, (long)OZ_S * M, OZ_BM, OZ_BK));
+    WW_TRY(tc_make_map(&tb, Bd, K, (long)OZ_S * Nn, OZ_BN, OZ_BK));
     WW_CUDA_TRY(cudaFuncSetAttribute(k_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
     OzOut o{mode, C, ldc, Psi, ldpsi, Mh, ldm, colmax, rslc};
     dim3 grid((M + OZ_BM - 1) / OZ_BM, (Nn + OZ_BN - 1) / OZ_BN);

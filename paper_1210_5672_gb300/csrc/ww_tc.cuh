@@ -117,6 +117,56 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         : "memory");
 }
 
+// ---------------------------------------------------------------- whole-warp issue
+// The producer and MMA roles run on a whole warp, so that the loop control and
+// the descriptor arithmetic stay warp-uniform; one elected lane issues.  (A
+// lone thread issuing tcgen05.mma from a divergent branch spends ~80 cycles
+// per instruction, more than a 128 x 64 x 16 MMA takes to run.)
+__device__ __forceinline__ uint32_t elect_one() {
+    uint32_t pred = 0;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\telect.sync _|P, 0xffffffff;\n\tselp.u32 %0, 1, 0, P;\n\t}"
+        : "=r"(pred));
+    return pred;
+}
+
+__device__ __forceinline__ void mma_bf16_if(uint32_t issue, uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "setp.ne.b32 q, %5, 0;\n\t"
+        "@q tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "r"(issue)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit_if(uint32_t issue, uint64_t *bar) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %1, 0;\n\t"
+        "@q tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(smem_u32(bar)),
+        "r"(issue)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d_if(uint32_t issue, const CUtensorMap *map, uint64_t *bar, void *dst, int x,
+                                               int y) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %5, 0;\n\t"
+        "@q cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n\t}" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(issue)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx_if(uint32_t issue, uint64_t *bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t"
+        "@q mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+        "r"(bytes), "r"(issue)
+        : "memory");
+}
+
 // arrive on *bar once every previously issued tcgen05.mma of this thread completed
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -151,6 +201,18 @@ __device__ __forceinline__ uint64_t desc_k128(uint32_t saddr) {
     d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
     d |= (uint64_t)1 << 46;                          // version
     d |= (uint64_t)2 << 61;                          // SWIZZLE_128B
+    return d;
+}
+
+// The same for a 64-byte-swizzled K-major tile (rows of 32 bf16 = 64 B, 8-row
+// groups 512 B apart; layout type 4 = SWIZZLE_64B; base 512-byte aligned).
+__device__ __forceinline__ uint64_t desc_k64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;                 // stride byte offset
+    d |= (uint64_t)1 << 46;                          // version
+    d |= (uint64_t)4 << 61;                          // SWIZZLE_64B
     return d;
 }
 

@@ -9,8 +9,8 @@
 // whose rate on GB300 is ~1.9 PFLOP/s against 70 TFLOP/s for FP32 FMA and
 // 1 TFLOP/s for FP64.
 //
-// One CTA computes a 128 x BN tile.  Warp 0 issues TMA loads of all slices of
-// a 64-wide K chunk into a ring of 2-4 stages; warp 1 owns the TMEM accumulator and
+// One CTA computes a 128 x BN tile.  Warps 0 and 6 issue the TMA loads of the
+// A and the B slices of a 64-wide K chunk into a ring of 2-4 stages; warp 1 owns the TMEM accumulator and
 // issues tcgen05.mma (M = 128, N = BN, K = 16) for every pair; warps 2..5 read
 // the accumulator with tcgen05.ld and write C.  Every mbarrier wait is
 // bounded (~1 s); a timeout sets *err and the block still exits.
@@ -30,8 +30,11 @@ namespace ww {
 namespace {
 
 constexpr int TC_BM = 128;
-constexpr int TC_BK = 64;
-constexpr int TC_THREADS = 192;
+constexpr int TC_BK = 64;   // K chunk of the 128-byte-swizzled tiles; 32 uses 64-byte swizzle
+// warps: 0 producer of the A slices, 1 MMA, 2..5 epilogue, 6 producer of the
+// B slices (one thread issues a TMA load only every ~145 ns, so two issuers)
+constexpr int TC_THREADS = 224;
+constexpr int TC_PROD2 = 6;
 
 struct Pairs {
     int n;
@@ -49,21 +52,21 @@ struct Pairs {
 namespace {
 
 // ring depth: as many K-chunk stages as fit in ~200 KB, at most 4
-template <int BN, int SA, int SB>
+template <int BN, int SA, int SB, int BK = TC_BK>
 struct TcSmem {
-    static constexpr int A_TILE = TC_BM * TC_BK * 2;   // bytes
-    static constexpr int B_TILE = BN * TC_BK * 2;
+    static constexpr int A_TILE = TC_BM * BK * 2;   // bytes
+    static constexpr int B_TILE = BN * BK * 2;
     static constexpr int STAGE = SA * A_TILE + SB * B_TILE;
     static constexpr int STAGES = (200 * 1024 / STAGE) < 4 ? (200 * 1024 / STAGE) : 4;
     static constexpr int BYTES = STAGES * STAGE + 1024 /* align */ + 256 /* barriers */;
 };
 
-template <int BN, int SA, int SB>
+template <int BN, int SA, int SB, int BK>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int Nn, int K,
               Pairs pairs, TcOut o, int *err, const int *skip) {
     if (skip && *skip) return;   // a step the caller decided on the device to leave out
-    using L = TcSmem<BN, SA, SB>;
+    using L = TcSmem<BN, SA, SB, BK>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t base = tc::smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024 - (base & 1023)) & 1023);
@@ -75,12 +78,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
-    const int nk = K / TC_BK;
+    const int nk = K / BK;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < L::STAGES; ++s) {
-            tc::mbar_init(&full[s], 1);
-            tc::mbar_init(&empty[s], 1);
+            tc::mbar_init(&full[s], 2);   // one arrival (with its bytes) from each producer
+            tc::mbar_init(&empty[s], 1);  // the MMA commit; both producers wait on the same phase
         }
         tc::mbar_init(done, 1);
         tc::mbar_fence_init();
@@ -96,22 +99,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc::fence_after();
     const uint32_t tmem = *tslot;
 
-    if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer
+    if (warp == 0 || warp == TC_PROD2) {
+        // ---------------- TMA producers: A slices (warp 0), B slices (warp 6)
+        const uint32_t leader = tc::elect_one();
+        const bool pa = warp == 0;
         for (int kc = 0; kc < nk; ++kc) {
             const int s = kc % L::STAGES;
             const uint32_t ph = (kc / L::STAGES) & 1;
             tc::mbar_wait(&empty[s], ph ^ 1, err);
-            tc::mbar_arrive_expect_tx(&full[s], L::STAGE);
+            tc::mbar_arrive_expect_tx_if(leader, &full[s], pa ? SA * L::A_TILE : SB * L::B_TILE);
             uint8_t *st = tiles + s * L::STAGE;
+            if (pa) {
 #pragma unroll
-            for (int a = 0; a < SA; ++a) tc::tma_load_2d(&tmA, &full[s], st + a * L::A_TILE, kc * TC_BK, a * M + m0);
+                for (int a = 0; a < SA; ++a)
+                    tc::tma_load_2d_if(leader, &tmA, &full[s], st + a * L::A_TILE, kc * BK, a * M + m0);
+            } else {
 #pragma unroll
-            for (int b = 0; b < SB; ++b)
-                tc::tma_load_2d(&tmB, &full[s], st + SA * L::A_TILE + b * L::B_TILE, kc * TC_BK, b * Nn + n0);
+                for (int b = 0; b < SB; ++b)
+                    tc::tma_load_2d_if(leader, &tmB, &full[s], st + SA * L::A_TILE + b * L::B_TILE, kc * BK,
+                                       b * Nn + n0);
+            }
         }
-    } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (whole warp, one elected lane issues)
+        const uint32_t leader = tc::elect_one();
         constexpr uint32_t idesc = tc::idesc_bf16(TC_BM, BN);
         for (int kc = 0; kc < nk; ++kc) {
             const int s = kc % L::STAGES;
@@ -120,17 +131,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc::fence_after();
             const uint32_t st = tc::smem_u32(tiles + s * L::STAGE);
             for (int pi = 0; pi < pairs.n; ++pi) {
-                const uint32_t a0 = st + pairs.p[pi] * L::A_TILE;
-                const uint32_t b0 = st + SA * L::A_TILE + pairs.q[pi] * L::B_TILE;
+                const uint32_t sa_ = st + pairs.p[pi] * L::A_TILE, sb_ = st + SA * L::A_TILE + pairs.q[pi] * L::B_TILE;
+                const uint64_t da = BK == 64 ? tc::desc_k128(sa_) : tc::desc_k64(sa_);
+                const uint64_t db = BK == 64 ? tc::desc_k128(sb_) : tc::desc_k64(sb_);
 #pragma unroll
-                for (int kk = 0; kk < TC_BK / 16; ++kk)
-                    tc::mma_bf16(tmem, tc::desc_k128(a0 + kk * 32), tc::desc_k128(b0 + kk * 32), idesc,
-                                 (kc | pi | kk) != 0);
+                for (int kk = 0; kk < BK / 16; ++kk)   // +32 B per K step: +2 in the start-address field
+                    tc::mma_bf16_if(leader, tmem, da + 2 * kk, db + 2 * kk, idesc, (kc | pi | kk) != 0);
             }
-            tc::mma_commit(&empty[s]);   // frees this stage once its MMAs have read it
+            tc::mma_commit_if(leader, &empty[s]);   // frees this stage once its MMAs have read it
         }
-        tc::mma_commit(done);
-    } else if (warp >= 2) {
+        tc::mma_commit_if(leader, done);
+    } else if (warp >= 2 && warp < TC_PROD2) {
         // ---------------- epilogue: TMEM -> registers -> C (column-major)
         const int quarter = warp & 3;   // TMEM lanes 32*quarter .. +31
         const int row = m0 + quarter * 32 + lane;
@@ -239,17 +250,18 @@ int get_encoder() {
 int tc_init() { return get_encoder(); }
 
 // 2-D bf16 tensor [rows][K] (K contiguous), tile box {64, box_rows}, 128-byte swizzle
-int tc_make_map(CUtensorMap *map, const void *ptr, int K, long rows, int box_rows) {
+int tc_make_map(CUtensorMap *map, const void *ptr, int K, long rows, int box_rows, int box_k) {
     WW_TRY(get_encoder());
     // the caller's buffer holds at least box_rows rows; rows past the logical
     // end only feed output rows / columns that the epilogue discards
     if (rows < box_rows) rows = box_rows;
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    if (box_k != 64 && box_k != 32) return fail(WW_ERR_ARG, "tc_make_map: K box must be 64 or 32");
+    cuuint32_t box[2] = {(cuuint32_t)box_k, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, box_k == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(WW_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
     return WW_OK;
@@ -257,17 +269,18 @@ int tc_make_map(CUtensorMap *map, const void *ptr, int K, long rows, int box_row
 
 namespace {
 
-template <int BN, int SA, int SB>
+template <int BN, int SA, int SB, int BK = TC_BK>
 int launch_tc(cudaStream_t s, const void *A, const void *B, int M, int Nn, int K, const Pairs &pairs, const TcOut &o,
               int *err, const int *skip) {
     if (o.mode == 4 && (M != Nn || Nn % 32 != 0))
         return fail(WW_ERR_ARG, "tc_gemm: slice output needs a square product with N a multiple of 32");
-    using L = TcSmem<BN, SA, SB>;
+    using L = TcSmem<BN, SA, SB, BK>;
     static_assert(L::BYTES <= 227 * 1024, "shared memory");
+    if (K % BK != 0) return fail(WW_ERR_ARG, "tc_gemm: K must be a multiple of the K chunk");
     CUtensorMap ta, tb;
-    WW_TRY(tc_make_map(&ta, A, K, (long)SA * M, TC_BM));
-    WW_TRY(tc_make_map(&tb, B, K, (long)SB * Nn, BN));
-    auto kern = k_tc_gemm<BN, SA, SB>;
+    WW_TRY(tc_make_map(&ta, A, K, (long)SA * M, TC_BM, BK));
+    WW_TRY(tc_make_map(&tb, B, K, (long)SB * Nn, BN, BK));
+    auto kern = k_tc_gemm<BN, SA, SB, BK>;
     WW_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES));
     dim3 grid((M + TC_BM - 1) / TC_BM, (Nn + BN - 1) / BN);
     kern<<<grid, TC_THREADS, L::BYTES, s>>>(ta, tb, M, Nn, K, pairs, o, err, skip);
@@ -360,7 +373,7 @@ int tc_gemm_f32acc(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 
     o.Cd = Cd;
     o.ldc = ldc;
     o.alpha = alpha;
-    return launch_tc<128, 3, 3>(s, A3, B3, M, Nn, K, P, o, err, skip);
+    return launch_tc<128, 3, 3, 32>(s, A3, B3, M, Nn, K, P, o, err, skip);
 }
 
 // Product from 2 + 2 slices (pairs with p + q <= 1): relative accuracy ~2^-16,
@@ -398,7 +411,8 @@ int tc_gemm_f32acc_sliced(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bf
         P.p[i] = (unsigned char)pp[i];
         P.q[i] = (unsigned char)qq[i];
     }
-    return launch_tc<128, 3, 3>(s, A3, B3, M, Nn, K, P, o, err, skip);
+    // 32-wide K chunks (64-byte swizzle): 4 stages of 48 KB instead of 2 of 96 KB
+    return launch_tc<128, 3, 3, 32>(s, A3, B3, M, Nn, K, P, o, err, skip);
 }
 
 }  // namespace ww

@@ -10,7 +10,12 @@ trajectory, and variational columns only for the sampled modes (plus T).
 That keeps the run to ~9 columns; it is still the full 4096-stage trajectory
 with one N = 2048 LU per stage (about 40 minutes on 8 cores).
 
-    python tests/golden/make_full_size_samples.py
+With --spread the oracle runs once more with c_1 one ulp larger and records,
+per output, how far its own result moves (the sensitivity floor of the
+problem at this size: two correct FP64 evaluations that differ only in
+rounding cannot be expected to agree better than a few times this).
+
+    python tests/golden/make_full_size_samples.py [--spread]
 """
 import json
 import os
@@ -29,10 +34,8 @@ MODES = [1, 2, 3, 64, 255, 511, 512]   # sampled Jacobian columns (mode numbers)
 ROW_STRIDE = 16                        # sampled rows of r and J
 
 
-def main():
-    O.build()
+def run(c):
     w = W.LARGE
-    c, seed = W.coefficients(w)
     x = 2 * np.pi * np.arange(w.N) / w.N
     basis = np.zeros((2 * w.N, 1 + len(MODES)))
     basis[: w.N, 0] = np.cos(np.outer(x, np.arange(1, w.n + 1))) @ c[1:]
@@ -42,27 +45,51 @@ def main():
     cr[0] = c[0]
     cr[1] = 1.0
     prob, keep = O.make_problem(w.N, 1 + len(MODES), g=w.g, tau=w.tau, h=w.h, steps=w.steps, basis=basis)
-    t0 = time.time()
     r, J, f = O.shoot_jacobian(prob, cr)
-    elapsed = time.time() - t0
-    rows = list(range(0, w.N, ROW_STRIDE))
     cols = {"T": J[:, 0]}
     for i, k in enumerate(MODES):
         cols[str(k)] = J[:, 2 + i]
-    out = {
-        "what": "oracle shoot_jacobian on the N2048_n512_steps1024_h1 workload, sampled",
-        "workload": w.name, "seed": seed, "N": w.N, "n": w.n, "steps": w.steps,
-        "T": c[0], "f": f, "r_norm": float(np.linalg.norm(r)),
-        "rows": rows, "r": [float(r[i]) for i in rows],
-        "columns": {k: {"norm": float(np.linalg.norm(v)), "values": [float(v[i]) for i in rows]}
-                    for k, v in cols.items()},
-        "oracle_threads": O.threads(), "oracle_seconds": round(elapsed, 1),
-    }
+    return r, cols, f
+
+
+def main():
+    O.build()
+    w = W.LARGE
+    c, seed = W.coefficients(w)
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "full_n2048_samples.json")
+    rows = list(range(0, w.N, ROW_STRIDE))
+    if "--spread" in sys.argv:
+        with open(path) as fh:
+            out = json.load(fh)
+        cp = c.copy()
+        cp[1] = np.nextafter(c[1], np.inf)
+        t0 = time.time()
+        r, cols, f = run(cp)
+        out["spread"] = {
+            "what": "relative change of each sampled output when c_1 moves by one ulp (oracle, same sampling)",
+            "f": abs(f - out["f"]) / abs(out["f"]),
+            "r": float(np.linalg.norm(r[rows] - np.asarray(out["r"])) / np.linalg.norm(out["r"])),
+            "columns": {k: float(np.linalg.norm(v[rows] - np.asarray(out["columns"][k]["values"]))
+                                 / np.linalg.norm(out["columns"][k]["values"])) for k, v in cols.items()},
+            "oracle_seconds": round(time.time() - t0, 1),
+        }
+    else:
+        t0 = time.time()
+        r, cols, f = run(c)
+        elapsed = time.time() - t0
+        out = {
+            "what": "oracle shoot_jacobian on the N2048_n512_steps1024_h1 workload, sampled",
+            "workload": w.name, "seed": seed, "N": w.N, "n": w.n, "steps": w.steps,
+            "T": c[0], "f": f, "r_norm": float(np.linalg.norm(r)),
+            "rows": rows, "r": [float(r[i]) for i in rows],
+            "columns": {k: {"norm": float(np.linalg.norm(v)), "values": [float(v[i]) for i in rows]}
+                        for k, v in cols.items()},
+            "oracle_threads": O.threads(), "oracle_seconds": round(elapsed, 1),
+        }
     with open(path, "w") as fh:
         json.dump(out, fh, indent=1)
         fh.write("\n")
-    print(f"wrote {path} ({elapsed:.0f} s, {O.threads()} threads)")
+    print(f"wrote {path}")
 
 
 if __name__ == "__main__":

@@ -7,8 +7,16 @@ tests/golden/make_full_size_samples.py from the oracle alone).
 
 Error measures: |df|/|f|; ||dr|| / ||r|| over the sampled points; per column
 ||dJ_k|| / max(||J_k||, 1e-4 max_j ||J_j||) over the sampled points (the
-column floor of the other parity tests).  The mixed form runs in the default
-suite; the FP64 form (about two minutes) only with WW_FULL_FP64=1.
+column floor of the other parity tests).
+
+Tolerance.  Over 4096 RK stages the variational columns amplify rounding: the
+oracle's own columns move by `spread` (stored with the samples) when c_1 moves
+by one ulp, i.e. when only the rounding pattern changes, and the plain FP64 GPU
+form differs from the oracle by about that much.  Each output must agree to
+max(1e-11, 4 x its spread): the GPU forms are held to the agreement two correct
+FP64 evaluations of this discrete map can have.  The mixed form runs in the
+default suite; the FP64 form (about two minutes) and the mixed-vs-FP64
+comparison only with WW_FULL_FP64=1.
 """
 import json
 import math
@@ -62,16 +70,25 @@ def _errors(g, r, J, f):
     return ef, er, ej
 
 
+def _tol(g, key, col=None):
+    sp = g.get("spread")
+    if sp is None:
+        pytest.skip("the oracle's one-ulp spread is not in the samples file (make_full_size_samples.py --spread)")
+    s = sp["columns"][col] if col is not None else sp[key]
+    return max(TOL, 4.0 * s)
+
+
 def _check(precision):
     g = _golden()
     r, J, f, st = _run(precision)
     ef, er, ej = _errors(g, r, J, f)
     print(f"\nfull N=2048 precision={precision}: |df|/|f| {ef:.2e}  r {er:.2e}  "
           + "  ".join(f"J[{k}] {e:.2e}" for k, e in ej.items()) + f"  stats {st}")
-    assert ef < TOL
-    assert er < TOL
+    assert ef < _tol(g, "f")
+    assert er < _tol(g, "r")
     for k, e in ej.items():
-        assert e < TOL, (k, e)
+        assert e < _tol(g, None, k), (k, e)
+    return r, J, f
 
 
 def test_full_size_mixed_matches_oracle_samples():
@@ -83,3 +100,20 @@ def test_full_size_mixed_matches_oracle_samples():
 def test_full_size_fp64_matches_oracle_samples():
     import paper_1210_5672_gb300 as ww
     _check(ww.WW_FP64)
+
+
+@pytest.mark.skipif(os.environ.get("WW_FULL_FP64") != "1", reason="about two minutes: set WW_FULL_FP64=1")
+def test_full_size_mixed_matches_fp64_form():
+    """Every entry of J: the mixed form against the plain FP64 GPU form."""
+    import paper_1210_5672_gb300 as ww
+    rm, Jm, fm, _ = _run(ww.WW_MIXED)
+    rd, Jd, fd, _ = _run(ww.WW_FP64)
+    norms = np.linalg.norm(Jd, axis=1)
+    floor = 1e-4 * norms.max()
+    col = np.linalg.norm(Jm - Jd, axis=1) / np.maximum(norms, floor)
+    print(f"\nfull N=2048 mixed vs FP64: |df|/|f| {abs(fm - fd) / abs(fd):.2e}  "
+          f"r {np.linalg.norm(rm - rd) / np.linalg.norm(rd):.2e}  J max column {col.max():.2e} "
+          f"(column {int(col.argmax())}), median {np.median(col):.2e}")
+    g = _golden()
+    worst = max(g["spread"]["columns"].values()) if "spread" in g else TOL
+    assert col.max() < max(TOL, 4.0 * worst)
