@@ -1,0 +1,380 @@
+// ww_cbase.cu -- the base state's spectral kernels (geometry, gamma of the
+// base column, base right-hand side with its RK update) on a thread-block
+// cluster of CS CTAs.  These transforms are on the critical path of every RK
+// stage and run on one column, so one CTA would leave them bound by a single
+// SM's FP64 pipe (2 lanes per clock): ~25 us per N = 2048 transform.
+//
+// FFT split over the cluster (the four-step factorisation N = CS x L, with
+// n = r + CS n2 and k = k2 + L k1):
+//   forward:  CTA r transforms its decimated samples x[r + CS n2] (length L),
+//             multiplies by W_N^{r k2}; then CTA r takes the CS-point DFT over
+//             the cluster ranks for its share of k2 (read through distributed
+//             shared memory) and holds X[k2 + L k1], k1 = 0..CS-1;
+//   inverse:  the same steps in reverse order, back to x[r + CS n2].
+// Point-wise work acts on the decimated samples (physical space) or on the
+// spectral slots a CTA holds.  Unscaled inverse, as in block_fft.
+#include <cooperative_groups.h>
+
+#include "ww_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ww {
+
+namespace {
+
+constexpr int CB_THREADS = 256;
+
+// W_N^m, 0 <= m < N, from the half table tw[k] = exp(-2 pi i k/N), k < N/2
+__device__ __forceinline__ double2 wn(const double2 *__restrict__ tw, int m, int N, bool inv) {
+    double2 w = m < (N >> 1) ? __ldg(&tw[m]) : make_double2(-__ldg(&tw[m - (N >> 1)]).x, -__ldg(&tw[m - (N >> 1)]).y);
+    if (inv) w.y = -w.y;
+    return w;
+}
+
+// in-place radix-2 FFT of length L = N / CS in shared memory (twiddles
+// W_L^j = W_N^{CS j}), whole block; callers synchronise before, it ends with a barrier
+__device__ void local_fft(double2 *s, int L, int logL, const double2 *__restrict__ tw, int N, int CS, bool inv) {
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const int j = (int)(__brev((unsigned)i) >> (32 - logL));
+        if (i < j) {
+            const double2 t = s[i];
+            s[i] = s[j];
+            s[j] = t;
+        }
+    }
+    __syncthreads();
+    for (int lh = 0; lh < logL; ++lh) {
+        const int half = 1 << lh;
+        const int tstride = (L >> (lh + 1)) * CS;   // W_{2 half}^k = W_N^{k N / (2 half)}
+        for (int b = threadIdx.x; b < (L >> 1); b += blockDim.x) {
+            const int k = b & (half - 1);
+            const int i0 = ((b >> lh) << (lh + 1)) + k, i1 = i0 + half;
+            const double2 w = wn(tw, k * tstride, N, inv);
+            const double2 v = cmul(s[i1], w), u = s[i0];
+            s[i0] = cadd(u, v);
+            s[i1] = csub(u, v);
+        }
+        __syncthreads();
+    }
+}
+
+// 8-point DFT in registers (natural order in and out): two 4-point DFTs of the
+// even and odd samples and the W_8 combination, all twiddles constants.
+template <bool INV>
+__device__ __forceinline__ double2 mul_mi(double2 z) {   // (-i) z forward, (+i) z inverse
+    return INV ? make_double2(-z.y, z.x) : make_double2(z.y, -z.x);
+}
+template <bool INV>
+__device__ __forceinline__ double2 mul_w8(double2 z) {   // z W_8 (forward (1 - i)/sqrt2, inverse its conjugate)
+    const double c = 0.70710678118654752440084436210484903928;
+    return INV ? make_double2((z.x - z.y) * c, (z.x + z.y) * c) : make_double2((z.x + z.y) * c, (z.y - z.x) * c);
+}
+template <bool INV>
+__device__ __forceinline__ void dft4(double2 &x0, double2 &x1, double2 &x2, double2 &x3) {
+    const double2 t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), t3 = mul_mi<INV>(csub(x1, x3));
+    x0 = cadd(t0, t2);
+    x2 = csub(t0, t2);
+    x1 = cadd(t1, t3);
+    x3 = csub(t1, t3);
+}
+template <bool INV>
+__device__ __forceinline__ void dft8(double2 (&v)[8]) {
+    double2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<INV>(e0, e1, e2, e3);
+    dft4<INV>(o0, o1, o2, o3);
+    o1 = mul_w8<INV>(o1);
+    o2 = mul_mi<INV>(o2);
+    o3 = mul_mi<INV>(mul_w8<INV>(o3));   // W8^3 = W8 W8^2
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1);
+    v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2);
+    v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3);
+    v[7] = csub(e3, o3);
+}
+
+// Cluster FFT.  xs: L decimated samples of this CTA (n2 = 0..L-1);
+// spec: this CTA's spectral slots [k1][k2l], k = (rank P + k2l) + L k1,
+// P = L / CS; zs: exchange buffer of L points.
+template <int CS>
+__device__ void cfft_forward(cg::cluster_group &cl, double2 *xs, double2 *spec, int N, int logN,
+                             const double2 *__restrict__ tw) {
+    static_assert(CS == 8, "the cluster-rank DFT is the 8-point one");
+    const int L = N / CS, logL = logN - (CS == 8 ? 3 : 2), P = L / CS, r = (int)cl.block_rank();
+    __syncthreads();
+    local_fft(xs, L, logL, tw, N, CS, false);
+    for (int k2 = threadIdx.x; k2 < L; k2 += blockDim.x) xs[k2] = cmul(xs[k2], wn(tw, r * k2, N, false));
+    cl.sync();
+    for (int k2l = threadIdx.x; k2l < P; k2l += blockDim.x) {
+        const int k2 = r * P + k2l;
+        double2 v[CS];
+#pragma unroll
+        for (int q = 0; q < CS; ++q) v[q] = cl.map_shared_rank(xs, q)[k2];
+        dft8<false>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < CS; ++k1) spec[k1 * P + k2l] = v[k1];
+    }
+    cl.sync();   // every CTA read the others' xs
+}
+
+template <int CS>
+__device__ void cfft_inverse(cg::cluster_group &cl, const double2 *spec, double2 *zs, double2 *xs, int N, int logN,
+                             const double2 *__restrict__ tw) {
+    static_assert(CS == 8, "the cluster-rank DFT is the 8-point one");
+    const int L = N / CS, logL = logN - (CS == 8 ? 3 : 2), P = L / CS, r = (int)cl.block_rank();
+    __syncthreads();
+    for (int k2l = threadIdx.x; k2l < P; k2l += blockDim.x) {
+        const int k2 = r * P + k2l;
+        double2 v[CS];
+#pragma unroll
+        for (int k1 = 0; k1 < CS; ++k1) v[k1] = spec[k1 * P + k2l];
+        dft8<true>(v);
+#pragma unroll
+        for (int q = 0; q < CS; ++q) zs[q * P + k2l] = cmul(v[q], wn(tw, q * k2, N, true));
+    }
+    cl.sync();
+    for (int k2 = threadIdx.x; k2 < L; k2 += blockDim.x) {
+        const int q = k2 / P;
+        xs[k2] = cl.map_shared_rank(zs, q)[r * P + (k2 - q * P)];
+    }
+    cl.sync();   // every CTA read the others' zs
+    local_fft(xs, L, logL, tw, N, CS, true);
+}
+
+// spectral slot of this CTA: t in [0, L) -> (k1, k2l) -> FFT slot k
+__device__ __forceinline__ int slot_of(int t, int N, int CS, int r) {
+    const int L = N / CS, P = L / CS;
+    const int k1 = t / P, k2l = t - k1 * P;
+    return (r * P + k2l) + L * k1;
+}
+
+// ---------------------------------------------------------------- geometry
+template <int CS>
+__global__ void __launch_bounds__(CB_THREADS) k_cgeometry(const double *__restrict__ eta_in,
+                                                          const double *__restrict__ phi_in, int with_phi, int N,
+                                                          int logN, int deep, int with_curv,
+                                                          const double2 *__restrict__ tw, double *eta, double *eta_x,
+                                                          double *eta_xx, double *phi_s, double *curv, double *E,
+                                                          double *Einv, int *status) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int L = N / CS, r = (int)cl.block_rank();
+    double2 *xs = reinterpret_cast<double2 *>(smraw), *sp = xs + L, *sp2 = sp + L, *zs = sp2 + L;
+    int bad = 0;
+    for (int n2 = threadIdx.x; n2 < L; n2 += blockDim.x) {
+        const int n = r + CS * n2;
+        const double e = eta_in[n];
+        const double p = with_phi ? phi_in[n] : 0.0;
+        if (!isfinite(e) || !isfinite(p) || (!deep && e <= 0.0)) bad = 1;
+        eta[n] = e;
+        const double ee = exp(e);
+        E[n] = ee;
+        Einv[n] = 1.0 / ee;
+        xs[n2] = make_double2(e, p);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_GEOMETRY);
+    cfft_forward<CS>(cl, xs, sp, N, logN, tw);
+    const double invN = 1.0 / N;
+    for (int t = threadIdx.x; t < L; t += blockDim.x) {
+        const int j = slot_of(t, N, CS, r), k = wavenum(j, N);
+        const bool nyq = j == (N >> 1);
+        const double2 z = sp[t];
+        const double2 v = make_double2(-(double)k * z.y * invN, (double)k * z.x * invN);   // (ik) z / N
+        sp[t] = nyq ? make_double2(0.0, 0.0) : v;
+        sp2[t] = nyq ? make_double2(0.0, 0.0) : make_double2(-(double)k * v.y, (double)k * v.x);
+    }
+    cfft_inverse<CS>(cl, sp, zs, xs, N, logN, tw);   // eta' + i phi'
+    for (int n2 = threadIdx.x; n2 < L; n2 += blockDim.x) {
+        const int n = r + CS * n2;
+        eta_x[n] = xs[n2].x;
+        phi_s[n] = xs[n2].y;
+    }
+    cfft_inverse<CS>(cl, sp2, zs, xs + 0, N, logN, tw);   // eta'' + i phi''
+    for (int n2 = threadIdx.x; n2 < L; n2 += blockDim.x) eta_xx[r + CS * n2] = xs[n2].x;
+    __syncthreads();
+    if (!with_curv) {
+        for (int n2 = threadIdx.x; n2 < L; n2 += blockDim.x) curv[r + CS * n2] = 0.0;   // multiplied by tau = 0
+        cl.sync();
+        return;
+    }
+    for (int n2 = threadIdx.x; n2 < L; n2 += blockDim.x) {
+        const double ex = eta_x[r + CS * n2];
+        xs[n2] = make_double2(ex / sqrt(1.0 + ex * ex), 0.0);
+    }
+    cfft_forward<CS>(cl, xs, sp, N, logN, tw);
+    for (int t = threadIdx.x; t < L; t += blockDim.x) {
+        const int j = slot_of(t, N, CS, r), k = wavenum(j, N);
+        const double2 z = sp[t];
+        sp[t] = j == (N >> 1) ? make_double2(0.0, 0.0) : make_double2(-(double)k * z.y * invN, (double)k * z.x * invN);
+    }
+    cfft_inverse<CS>(cl, sp, zs, xs, N, logN, tw);
+    for (int n2 = threadIdx.x; n2 < L; n2 += blockDim.x) curv[r + CS * n2] = xs[n2].x;
+    cl.sync();
+}
+
+// ---------------------------------------------------------------- gamma of the base column
+// one real column mu: gamma = mu' and 1/2 H gamma = |k|/2 mu^ come back as the
+// real and imaginary parts of one inverse transform of (ik + i|k|/2) mu^
+template <int CS>
+__global__ void __launch_bounds__(CB_THREADS) k_cgamma(const double *__restrict__ mu, int N, int logN,
+                                                       const double2 *__restrict__ tw, double *Gam, double *Gout) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int L = N / CS, r = (int)cl.block_rank();
+    double2 *xs = reinterpret_cast<double2 *>(smraw), *sp = xs + L, *zs = sp + L;
+    for (int n2 = threadIdx.x; n2 < L; n2 += blockDim.x) xs[n2] = make_double2(mu[r + CS * n2], 0.0);
+    cfft_forward<CS>(cl, xs, sp, N, logN, tw);
+    const double invN = 1.0 / N;
+    for (int t = threadIdx.x; t < L; t += blockDim.x) {
+        const int j = slot_of(t, N, CS, r), k = wavenum(j, N);
+        const double2 z = sp[t];
+        // (ik + i |k|/2) z / N
+        const double f = ((double)k + 0.5 * fabs((double)k)) * invN;
+        sp[t] = j == (N >> 1) ? make_double2(0.0, 0.0) : make_double2(-f * z.y, f * z.x);
+    }
+    cfft_inverse<CS>(cl, sp, zs, xs, N, logN, tw);
+    for (int n2 = threadIdx.x; n2 < L; n2 += blockDim.x) {
+        const int n = r + CS * n2;
+        Gam[n] = xs[n2].x;
+        Gout[n] = xs[n2].y;
+    }
+    cl.sync();
+}
+
+// ---------------------------------------------------------------- base RHS + RK update
+__device__ __forceinline__ double rk_b2(int st) { return (st == 1 || st == 2) ? 2.0 : 1.0; }
+__device__ __forceinline__ double rk_a_next2(int st) { return st == 2 ? 1.0 : 0.5; }
+
+template <int CS>
+__global__ void __launch_bounds__(CB_THREADS) k_cbase_rhs(
+    const double *__restrict__ Gphi, const double *__restrict__ eta, const double *__restrict__ eta_x,
+    const double *__restrict__ phi_s, const double *__restrict__ curv, double g, double tau, int N, int logN,
+    const double2 *__restrict__ tw, const double *__restrict__ filt, double *ux, double *vy, double *w3, float2 *uxd,
+    float2 *vyd, float2 *w3d, double *Fbase, double *Y, double *Ys, double *Acc, int st,
+    const double *__restrict__ cvec, int steps, int update, int *status) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int L = N / CS, r = (int)cl.block_rank();
+    double2 *xs = reinterpret_cast<double2 *>(smraw), *sp = xs + L, *zs = sp + L;
+    int bad = 0;
+    for (int n2 = threadIdx.x; n2 < L; n2 += blockDim.x) {
+        const int n = r + CS * n2;
+        const double ex = eta_x[n], d = 1.0 + ex * ex, gp = Gphi[n], pp = phi_s[n];
+        const double u = (pp - ex * gp) / d;
+        const double v = (ex * pp + gp) / d;
+        const double w = 1.0 / (d * sqrt(d));
+        ux[n] = u;
+        vy[n] = v;
+        w3[n] = w;
+        if (uxd) {
+            uxd[n] = df_split(u);
+            vyd[n] = df_split(v);
+            w3d[n] = df_split(w);
+        }
+        const double pt = v * gp - 0.5 * u * u - 0.5 * v * v - g * eta[n] + tau * curv[n];
+        if (!isfinite(pt) || !isfinite(gp)) bad = 1;
+        xs[n2] = make_double2(gp, pt);   // eta_t = G phi ; phi_t before P and the filter
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
+    cfft_forward<CS>(cl, xs, sp, N, logN, tw);
+    for (int t = threadIdx.x; t < L; t += blockDim.x) {
+        const int j = slot_of(t, N, CS, r);
+        const double f = filt[j];
+        // P acts on the phi part only: at k = 0 keep Re (eta mean), drop Im (phi mean)
+        sp[t] = j == 0 ? make_double2(sp[t].x * f, 0.0) : cscale(sp[t], f);
+    }
+    cfft_inverse<CS>(cl, sp, zs, xs, N, logN, tw);
+    for (int n2 = threadIdx.x; n2 < L; n2 += blockDim.x) {
+        const int n = r + CS * n2;
+        Fbase[n] = xs[n2].x;
+        Fbase[N + n] = xs[n2].y;
+    }
+    if (update) {
+        const double dt = cvec[0] / (4.0 * steps);
+        if (st < 3) {
+            const double b = rk_b2(st), a = rk_a_next2(st);
+            for (int n2 = threadIdx.x; n2 < L; n2 += blockDim.x) {
+                const int n = r + CS * n2;
+                const double2 k = xs[n2];
+                if (st == 0) {
+                    Acc[n] = b * k.x;
+                    Acc[N + n] = b * k.y;
+                } else {
+                    Acc[n] += b * k.x;
+                    Acc[N + n] += b * k.y;
+                }
+                Ys[n] = Y[n] + a * dt * k.x;
+                Ys[N + n] = Y[N + n] + a * dt * k.y;
+            }
+        } else {
+            // end of the step: Y + dt/6 (Acc + k), filtered
+            for (int n2 = threadIdx.x; n2 < L; n2 += blockDim.x) {
+                const int n = r + CS * n2;
+                const double2 k = xs[n2];
+                xs[n2] = make_double2(Y[n] + dt / 6.0 * (Acc[n] + k.x), Y[N + n] + dt / 6.0 * (Acc[N + n] + k.y));
+            }
+            cfft_forward<CS>(cl, xs, sp, N, logN, tw);
+            for (int t = threadIdx.x; t < L; t += blockDim.x) sp[t] = cscale(sp[t], filt[slot_of(t, N, CS, r)]);
+            cfft_inverse<CS>(cl, sp, zs, xs, N, logN, tw);
+            for (int n2 = threadIdx.x; n2 < L; n2 += blockDim.x) {
+                const int n = r + CS * n2;
+                Y[n] = Ys[n] = xs[n2].x;
+                Y[N + n] = Ys[N + n] = xs[n2].y;
+            }
+        }
+    }
+    cl.sync();
+}
+
+template <typename K, typename... Args>
+int launch_cluster(K kernel, int CS, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)CS, 1, 1);
+    cfg.blockDim = dim3(CB_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    WW_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, args...));
+    return WW_OK;
+}
+
+}  // namespace
+
+// The cluster kernels need L = N / CS >= 64 (N >= 512 with CS = 8); smaller
+// problems keep the one-CTA kernels.
+bool cbase_ok(const Ctx *c) { return c->N >= 8 * 64 && c->N <= 8 * 2048; }
+
+constexpr int CB_CS = 8;
+
+int launch_cbase_geometry(Ctx *c, const double *eta, const double *phi, int with_phi) {
+    const size_t sm = 4 * sizeof(double2) * (size_t)(c->N / CB_CS);
+    return launch_cluster(k_cgeometry<CB_CS>, CB_CS, sm, c->stream, eta, phi, with_phi, c->N, c->logN,
+                          c->deep ? 1 : 0, c->tau != 0.0 ? 1 : 0, (const double2 *)c->tw, c->eta, c->eta_x,
+                          c->eta_xx, c->phi_s, c->curv, c->E, c->Einv, c->status);
+}
+
+int launch_cbase_gamma(Ctx *c) {
+    const size_t sm = 3 * sizeof(double2) * (size_t)(c->N / CB_CS);
+    return launch_cluster(k_cgamma<CB_CS>, CB_CS, sm, c->stream, (const double *)c->M, c->N, c->logN,
+                          (const double2 *)c->tw, c->Gam, c->Gout);
+}
+
+int launch_cbase_rhs(Ctx *c, int stage, const double *cvec) {
+    const size_t sm = 3 * sizeof(double2) * (size_t)(c->N / CB_CS);
+    return launch_cluster(k_cbase_rhs<CB_CS>, CB_CS, sm, c->stream, (const double *)c->Gout, (const double *)c->eta,
+                          (const double *)c->eta_x, (const double *)c->phi_s, (const double *)c->curv, c->g, c->tau,
+                          c->N, c->logN, (const double2 *)c->tw, (const double *)c->filt_d, c->ux, c->vy, c->w3,
+                          c->uxd, c->vyd, c->w3d, c->Fbase, c->Y, c->Ys, c->Kacc, stage < 0 ? 0 : stage, cvec,
+                          c->steps, stage >= 0 ? 1 : 0, c->status);
+}
+
+}  // namespace ww

@@ -197,6 +197,11 @@ int launch_base_rhs(Ctx *c, int stage, const double *cvec);
 int launch_col_rhs(Ctx *c, int stage, const double *cvec);
 int launch_initial(Ctx *c, const double *cvec, int with_columns);
 int launch_fill_filter(Ctx *c);                      // filter tables (once, at ww_create)
+// the base state's transforms on an 8-CTA cluster (ww_cbase.cu), N >= 512
+bool cbase_ok(const Ctx *c);
+int launch_cbase_geometry(Ctx *c, const double *eta, const double *phi, int with_phi);
+int launch_cbase_gamma(Ctx *c);                      // gamma, 1/2 H gamma of column 0 of M
+int launch_cbase_rhs(Ctx *c, int stage, const double *cvec);
 int launch_outputs(Ctx *c, double *r, double *J, double *f, int with_J);
 int launch_copy_cols(Ctx *c, const double *src, int ncols, double *dst);
 

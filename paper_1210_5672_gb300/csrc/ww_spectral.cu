@@ -512,6 +512,7 @@ int prepare_spectral(Ctx *c) {
 static bool use_df(const Ctx *c) { return c->precision == WW_MIXED && c->twd != nullptr && c->uxd != nullptr; }
 
 int launch_base_geometry(Ctx *c, const double *eta, const double *phi, int with_phi) {
+    if (cbase_ok(c)) return launch_cbase_geometry(c, eta, phi, with_phi);
     size_t sm = 2 * sizeof(double2) * c->N;
     k_base_geometry<ArF64><<<1, FFT_THREADS, sm, c->stream>>>(eta, phi, with_phi, c->N, c->logN, c->deep ? 1 : 0,
                                                                  c->tau != 0.0 ? 1 : 0, c->tw, c->eta, c->eta_x, c->eta_xx, c->phi_s,
@@ -521,6 +522,7 @@ int launch_base_geometry(Ctx *c, const double *eta, const double *phi, int with_
 }
 
 int launch_gamma(Ctx *c, int col0, int ncols) {
+    if (col0 == 0 && ncols == 1 && cbase_ok(c)) return launch_cbase_gamma(c);
     size_t sm = 2 * sizeof(double2) * c->N;
     size_t off = (size_t)col0 * c->N;
     if (use_df(c) && col0 >= 1)
@@ -548,6 +550,7 @@ int launch_phi0(Ctx *c) {
 
 // stage < 0: evaluate the base RHS only (no RK update)
 int launch_base_rhs(Ctx *c, int stage, const double *cvec) {
+    if (cbase_ok(c)) return launch_cbase_rhs(c, stage, cvec);
     size_t sm = sizeof(double2) * c->N;
     k_base_rhs<ArF64><<<1, FFT_THREADS, sm, c->stream>>>(c->Gout, c->eta, c->eta_x, c->phi_s, c->curv, c->g, c->tau,
                                             c->N, c->logN, (const void *)c->tw, (const void *)c->filt_d, c->ux,
