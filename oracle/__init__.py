@@ -17,6 +17,10 @@ the paper the C function follows:
 * ``rhs``            -- Eq. (ww) base RHS and Eqs. (l5a), (l6a) variational RHS
 * ``shoot``          -- r and f of Eq. (f:phi)
 * ``shoot_jacobian`` -- J of Eqs. (Jik), (q:qdot), T column by reading R2
+* ``objective_and_grad`` -- f and its gradient by the discrete adjoint of the
+                        RK4 scheme (Sec. 3.2 Eqs. adj, nabla:f; App. C Eq. adj2;
+                        reading R7: exact transpose of the discrete map)
+* ``dtn_T``          -- the transpose of the discrete DtN operator
 * ``energy``         -- the energy monitor of Sec. 4
 """
 from __future__ import annotations
@@ -92,6 +96,9 @@ def _set_signatures(L):
         "orc_shoot": (None, [P, _D, _D, _D]),
         "orc_shoot_jacobian": (None, [P, _D, _D, _D, _D]),
         "orc_energy": (C.c_double, [P, _D]),
+        "orc_objective_and_grad": (None, [P, _D, _D, _D]),
+        "orc_dtn_T": (None, [C.c_int, C.c_double, _D, _D, _D]),
+        "orc_lu_solve_T": (None, [C.c_int, _D, C.POINTER(C.c_int), _D, _D]),
         "orc_threads": (C.c_int, []),
         "orc_set_threads": (None, [C.c_int]),
     }
@@ -211,6 +218,25 @@ def shoot_jacobian(prob: Problem, c):
     Jc = np.empty((n + 1, N))  # column-major storage = row-major of J^T
     lib().orc_shoot_jacobian(C.byref(prob), _p(c), _p(r), _p(Jc), _p(f))
     return r, np.ascontiguousarray(Jc.T), float(f[0])
+
+
+def objective_and_grad(prob: Problem, c):
+    """(f, grad) with grad[0] = d f / d T and grad[k] = d f / d c_k, by the
+    discrete adjoint (reading R7)."""
+    c = _f64(c)
+    f = np.empty(1)
+    g = np.empty(prob.n + 1)
+    lib().orc_objective_and_grad(C.byref(prob), _p(c), _p(f), _p(g))
+    return float(f[0]), g
+
+
+def dtn_T(eta, x, h) -> np.ndarray:
+    """The transpose of the discrete DtN operator applied to x."""
+    eta = _f64(eta)
+    x = _f64(x)
+    out = np.empty_like(x)
+    lib().orc_dtn_T(len(eta), float(h), _p(eta), _p(x), _p(out))
+    return out
 
 
 def energy(prob: Problem, q) -> float:

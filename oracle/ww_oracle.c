@@ -40,11 +40,19 @@
  *  R5 residual weight w = sqrt(1/N) (uniform grid, E = 1 in Eq. (f:phi)).
  *  R6 the linearisation is the continuum one of App. B with the shared
  *     discrete DtN operator (K and G are not differentiated).
+ *  R7 the gradient of f (Sec. 3.2, App. C) is the DISCRETE adjoint: the
+ *     transpose of the RK4 scheme above, so grad f = J^T r of the discrete
+ *     map up to roundoff.  App. C derives the continuous adjoint from the
+ *     self-adjointness of the continuous DtN map; its discretisation is only
+ *     nearly symmetric, and the discrete adjoint uses its exact transpose
+ *     A^{-T} D (1/2 H - G^T).
  */
 /* ORC_PLANT (tests only, default 0) compiles a deliberately wrong variant so
  * that the pin tests can show they catch it: 1 = image kernels with the
  * printed "+" sign, 2 = zeta'(alpha) in K1 instead of zeta'(beta), 3 = gravity
- * term dropped from phi_t, 4 = u psi' term dropped from the variational RHS. */
+ * term dropped from phi_t, 4 = u psi' term dropped from the variational RHS,
+ * 5 = the adjoint takes the forward DtN for its transpose (the continuous
+ * self-adjointness of App. C applied to the discrete operator). */
 #ifndef ORC_PLANT
 #define ORC_PLANT 0
 #endif
@@ -254,6 +262,26 @@ void orc_lu_solve(int N, const double *LU, const int *piv, const double *b, doub
     }
 }
 
+/* x = A^{-T} b using the factors of orc_lu: P A = L U, so A^T = U^T L^T P
+ * (solve with U^T, then the unit L^T, then undo the interchanges in reverse
+ * order); b and x may alias */
+void orc_lu_solve_T(int N, const double *LU, const int *piv, const double *b, double *x)
+{
+    if (x != b) memcpy(x, b, sizeof(double) * N);
+    for (int i = 0; i < N; ++i) {            /* U^T: lower, diagonal U_ii */
+        double s = x[i];
+        for (int j = 0; j < i; ++j) s -= LU[(size_t)j * N + i] * x[j];
+        x[i] = s / LU[(size_t)i * N + i];
+    }
+    for (int i = N - 1; i >= 0; --i) {       /* L^T: unit upper */
+        double s = x[i];
+        for (int j = i + 1; j < N; ++j) s -= LU[(size_t)j * N + i] * x[j];
+        x[i] = s;
+    }
+    for (int k = N - 1; k >= 0; --k)
+        if (piv[k] != k) { double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
+}
+
 /* ------------------------------------------------------------------ */
 /* The per-stage DtN of the base surface (Sec. 2.1, Eqs. (fred), (G))  */
 /* ------------------------------------------------------------------ */
@@ -303,6 +331,36 @@ static void dtn_apply_one(const dtn_state *s, const double *phi, double *out)
         out[i] = 0.5 * hg[i] + acc;
     }
     free(mu); free(gam); free(hg);
+}
+
+/* The transpose of the operator of dtn_apply_one (reading R7).  Forward:
+ * G phi = (1/2 H + G) D A^{-1} phi.  The Fourier multipliers ik and -i sgn k
+ * (Nyquist zeroed) are antisymmetric, D^T = -D and H^T = -H, so
+ * G^T x = A^{-T} D (1/2 H x - G^T x). */
+static void dtn_apply_T(const dtn_state *s, const double *x, double *out)
+{
+    int N = s->N;
+    if (ORC_PLANT == 5) { dtn_apply_one(s, x, out); return; }
+    double *hx = malloc(sizeof(double) * N);
+    double *t = malloc(sizeof(double) * N);
+    orc_spectral(N, MUL_HILBERT, x, hx);
+    for (int i = 0; i < N; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < N; ++j) acc += s->G[(size_t)j * N + i] * x[j];
+        t[i] = 0.5 * hx[i] - acc;
+    }
+    orc_spectral(N, MUL_DERIV, t, t);
+    orc_lu_solve_T(N, s->LU, s->piv, t, out);
+    free(hx); free(t);
+}
+
+/* Public: the transposed DtN of x on surface eta (tests). */
+void orc_dtn_T(int N, double h, const double *eta, const double *x, double *out)
+{
+    dtn_state s;
+    dtn_prepare(&s, N, h, eta);
+    dtn_apply_T(&s, x, out);
+    dtn_release(&s);
 }
 
 /* Public: DtN of phi (nrhs columns, each length N, contiguous) on surface eta. */
@@ -518,6 +576,132 @@ void orc_shoot_jacobian(const orc_problem *p, const double *c, double *r, double
         for (int i = 0; i < N; ++i)
             J[(size_t)k * N + i] = w * y[(size_t)(k + 1) * 2 * N + N + i];
     free(y);
+}
+
+/* ------------------------------------------------------------------ */
+/* Gradient by the discrete adjoint (Sec. 3.2 Eqs. (adj), (nabla:f);   */
+/* App. C Eq. (adj2); reading R7)                                       */
+/* ------------------------------------------------------------------ */
+
+/* Transpose of the filtered variational RHS of orc_rhs at the base state q,
+ * applied to kb = (adjoint of etadot_t, adjoint of phidot_t) (each N); out =
+ * (adjoint of etadot, adjoint of phidot).  *Fdot = kb . F(q) with F the
+ * filtered base RHS (the T column's forcing is F/T).  Term by term this is
+ * Eq. (adj2): with et = Filt(kb_eta), pt = P Filt(kb_phi) and the auxiliary
+ * chi = et + phi_y pt,
+ *   adjoint of phidot = G^T chi + (phi_x pt)'
+ *   adjoint of etadot = -phi_y (G^T chi + (phi_x pt)') + phi_x et'
+ *                       + phi_x phi_y pt' - g pt + tau (pt' (1+eta'^2)^{-3/2})'
+ * (the two phi_y terms combine to App. C's -phi_y phi_x' P phit). */
+static void rhs_T(const orc_problem *p, const double *q, const double *kb, double *out, double *Fdot)
+{
+    int N = p->N;
+    const double *eta = q, *phi = q + N;
+    double *F = malloc(sizeof(double) * 2 * N);
+    orc_rhs(p, 1.0, q, 0, 0, F);                 /* base RHS (no T forcing in column 0) */
+    double fd = 0.0;
+    for (int i = 0; i < 2 * N; ++i) fd += kb[i] * F[i];
+    *Fdot = fd;
+
+    dtn_state s;
+    dtn_prepare(&s, N, p->h, eta);
+    double *phi_p = malloc(sizeof(double) * N), *Gphi = malloc(sizeof(double) * N);
+    double *ux = malloc(sizeof(double) * N), *vy = malloc(sizeof(double) * N);
+    double *w3 = malloc(sizeof(double) * N);
+    orc_spectral(N, MUL_DERIV, phi, phi_p);
+    dtn_apply_one(&s, phi, Gphi);
+    for (int i = 0; i < N; ++i) {              /* Eq. (uv:from:G), as in orc_rhs */
+        double ex = s.eta_x[i], d = 1.0 + ex * ex;
+        ux[i] = (phi_p[i] - ex * Gphi[i]) / d;
+        vy[i] = (ex * phi_p[i] + Gphi[i]) / d;
+        w3[i] = 1.0 / (d * sqrt(d));
+    }
+    double *et = malloc(sizeof(double) * N), *pt = malloc(sizeof(double) * N);
+    double *chi = malloc(sizeof(double) * N), *Gchi = malloc(sizeof(double) * N);
+    double *d_et = malloc(sizeof(double) * N), *d_pt = malloc(sizeof(double) * N);
+    double *t1 = malloc(sizeof(double) * N), *t2 = malloc(sizeof(double) * N);
+    orc_spectral(N, MUL_FILTER, kb, et);
+    orc_spectral(N, MUL_FILTER, kb + N, pt);
+    orc_spectral(N, MUL_PROJECT, pt, pt);
+    for (int i = 0; i < N; ++i) chi[i] = et[i] + vy[i] * pt[i];
+    dtn_apply_T(&s, chi, Gchi);
+    orc_spectral(N, MUL_DERIV, et, d_et);
+    orc_spectral(N, MUL_DERIV, pt, d_pt);
+    for (int i = 0; i < N; ++i) t1[i] = ux[i] * pt[i];
+    orc_spectral(N, MUL_DERIV, t1, t1);        /* (phi_x pt)' */
+    for (int i = 0; i < N; ++i) t2[i] = w3[i] * d_pt[i];
+    orc_spectral(N, MUL_DERIV, t2, t2);        /* (pt' (1+eta'^2)^{-3/2})' */
+    for (int i = 0; i < N; ++i) {
+        double pb = Gchi[i] + t1[i];
+        out[N + i] = pb;
+        out[i] = -vy[i] * pb + ux[i] * d_et[i] + ux[i] * vy[i] * d_pt[i] - p->g * pt[i] + p->tau * t2[i];
+    }
+    free(F); free(phi_p); free(Gphi); free(ux); free(vy); free(w3);
+    free(et); free(pt); free(chi); free(Gchi); free(d_et); free(d_pt); free(t1); free(t2);
+    dtn_release(&s);
+}
+
+/* f and grad f (n+1 entries, grad[0] = d f / d T) by the discrete adjoint of
+ * the RK4 scheme of integrate().  The base trajectory runs forward once with
+ * every stage state kept; the adjoint starts from lambda = (0, phi(T/4)/N)
+ * (the gradient of f = r.r/2, r = phi/sqrt(N), with respect to the final
+ * state) and runs the transposed steps backward: per step the filter, then
+ * the stages in reverse order, stage st contributing its transposed RHS to
+ * lambda and, scaled by a_st dt, to the adjoint of the previous stage's RHS.
+ * grad_k = basis_k . lambda(0); grad_0 = sum over stages of kbar . F / T. */
+void orc_objective_and_grad(const orc_problem *p, const double *c, double *f, double *grad)
+{
+    int N = p->N, S = 4 * p->steps;
+    size_t n2 = (size_t)2 * N;
+    double T = c[0], dt = T / 4.0 / p->steps;
+    static const double a[4] = {0.0, 0.5, 0.5, 1.0};
+    static const double b[4] = {1.0, 2.0, 2.0, 1.0};
+    double *traj = malloc(sizeof(double) * n2 * (size_t)S);
+    double *y = malloc(sizeof(double) * n2), *k = malloc(sizeof(double) * n2);
+    double *acc = malloc(sizeof(double) * n2);
+    orc_initial(p, c, y);
+    for (int n = 0; n < p->steps; ++n) {         /* forward: as integrate() with no columns */
+        for (size_t i = 0; i < n2; ++i) acc[i] = 0.0;
+        for (int st = 0; st < 4; ++st) {
+            double *ys = traj + (size_t)(4 * n + st) * n2;
+            if (st == 0) memcpy(ys, y, sizeof(double) * n2);
+            else for (size_t i = 0; i < n2; ++i) ys[i] = y[i] + a[st] * dt * k[i];
+            orc_rhs(p, T, ys, 0, 0, k);
+            for (size_t i = 0; i < n2; ++i) acc[i] += b[st] * k[i];
+        }
+        for (size_t i = 0; i < n2; ++i) y[i] += dt / 6.0 * acc[i];
+        orc_spectral(N, MUL_FILTER, y, y);
+        orc_spectral(N, MUL_FILTER, y + N, y + N);
+    }
+    double s = 0.0;
+    for (int i = 0; i < N; ++i) s += y[N + i] * y[N + i] / N;
+    *f = 0.5 * s;
+
+    double *lam = malloc(sizeof(double) * n2), *kb = malloc(sizeof(double) * n2 * 4);
+    double *wb = malloc(sizeof(double) * n2);
+    for (int i = 0; i < N; ++i) { lam[i] = 0.0; lam[N + i] = y[N + i] / N; }
+    double gT = 0.0;
+    for (int n = p->steps - 1; n >= 0; --n) {
+        orc_spectral(N, MUL_FILTER, lam, lam);   /* the end-of-step filter, transposed */
+        orc_spectral(N, MUL_FILTER, lam + N, lam + N);
+        for (int st = 0; st < 4; ++st)
+            for (size_t i = 0; i < n2; ++i) kb[st * n2 + i] = b[st] * dt / 6.0 * lam[i];
+        for (int st = 3; st >= 0; --st) {
+            double Fd;
+            rhs_T(p, traj + (size_t)(4 * n + st) * n2, kb + st * n2, wb, &Fd);
+            gT += Fd / T;
+            for (size_t i = 0; i < n2; ++i) lam[i] += wb[i];
+            if (st > 0)
+                for (size_t i = 0; i < n2; ++i) kb[(st - 1) * n2 + i] += a[st] * dt * wb[i];
+        }
+    }
+    grad[0] = gT;
+    for (int kk = 1; kk <= p->n; ++kk) {
+        double g = 0.0;
+        for (size_t r = 0; r < n2; ++r) g += basis_entry(p, (int)r, kk) * lam[r];
+        grad[kk] = g;
+    }
+    free(traj); free(y); free(k); free(acc); free(lam); free(kb); free(wb);
 }
 
 /* Energy (Sec. 4, energy monitor): E = 1/2 int (phi G phi + g (eta - hbar)^2) dx

@@ -19,6 +19,13 @@ coefficient in the oracle fails at least one of them:
                          difference of the discrete RHS.
 * Jacobian            -- Eq. (Jik) columns against central differences of the
                          objective, T column included (reading R2).
+* adjoint gradient    -- Sec. 3.2 / App. C by the discrete adjoint (reading R7):
+                         equals J^T r of the forward variational columns (an
+                         independent algorithm) to roundoff, and central
+                         differences of f to the linearisation's accuracy;
+                         the transposed DtN is the explicit matrix transpose,
+                         and the discrete DtN is nearly self-adjoint (App. C,
+                         Green's identity), more so as N grows.
 """
 import math
 
@@ -318,3 +325,80 @@ def test_T_column_agrees_with_phi_t_to_order_dt4():
         gaps.append(np.max(np.abs(J[:, 0] - phit)))
     assert gaps[1] < 1e-7
     assert gaps[0] / gaps[1] > 8
+
+
+# ----------------------------------------------------------------- adjoint gradient
+def _adjoint_case(N, n, steps, h, tau, amp, phi_basis=False):
+    w = W.Workload("adj", N=N, n=n, steps=steps, h=h, tau=tau, amp=amp)
+    c, _ = W.coefficients(w)
+    basis = None
+    if phi_basis:
+        # the paper's convention (Eq. init:stand): even k on eta, odd k on phi
+        x = x_grid(N)
+        basis = np.zeros((2 * N, n))
+        for k in range(1, n + 1):
+            basis[(0 if k % 2 == 0 else N):(N if k % 2 == 0 else 2 * N), k - 1] = 2 * np.cos(k * x)
+    prob, keep = O.make_problem(N, n, g=w.g, tau=tau, h=h, steps=steps, basis=basis)
+    return prob, keep, c
+
+
+@pytest.mark.parametrize("h,tau,phi_basis", [(0.3, 0.05, False), (math.inf, 0.1, False), (1.0, 0.0, True)])
+def test_adjoint_gradient_equals_JT_r(h, tau, phi_basis):
+    """Reading R7: the discrete adjoint's gradient is J^T r of the discrete map,
+    where J comes from the forward variational columns (Eq. Jik)."""
+    prob, keep, c = _adjoint_case(32, 10, 24, h, tau, 0.05, phi_basis)
+    r, J, f = O.shoot_jacobian(prob, c)
+    f2, g = O.objective_and_grad(prob, c)
+    jtr = J.T @ r
+    assert abs(f2 - f) <= 1e-15 * f
+    assert np.linalg.norm(g - jtr) < 1e-13 * np.linalg.norm(jtr)
+    # every component carries information (the T entry included)
+    assert np.min(np.abs(jtr[:4])) > 1e-8 * np.linalg.norm(jtr)
+
+
+def test_adjoint_gradient_matches_central_differences():
+    """Sec. 3.2: df/dc_k and df/dT against central differences of f, eps =
+    1e-6 max(1, |c_k|); agreement to the linearisation's accuracy (reading R6)."""
+    prob, keep, c = _adjoint_case(32, 6, 16, 0.5, 0.05, 0.08)
+    f, g = O.objective_and_grad(prob, c)
+    fd = np.empty_like(g)
+    for k in range(len(c)):
+        e = 1e-6 * max(1.0, abs(c[k]))
+        cp, cm = c.copy(), c.copy()
+        cp[k] += e
+        cm[k] -= e
+        fd[k] = (O.shoot(prob, cp)[1] - O.shoot(prob, cm)[1]) / (2 * e)
+    assert np.max(np.abs(g - fd)) < 1e-6 * np.max(np.abs(fd))
+
+
+def test_transposed_dtn_and_self_adjointness():
+    """The transposed DtN equals the transpose of the assembled operator; the
+    discrete DtN is nearly symmetric (App. C: Green's identity makes the
+    continuous map self-adjoint), with the asymmetry falling as N grows."""
+    gaps = []
+    for N in (32, 64):
+        x = x_grid(N)
+        eta = 1.0 + 0.12 * np.cos(x) + 0.03 * np.sin(2 * x)
+        Gm = np.array([O.dtn(eta, e, 1.0) for e in np.eye(N)]).T   # column j = G e_j
+        v = np.random.default_rng(N).standard_normal(N)
+        gt = O.dtn_T(eta, v, 1.0)
+        assert np.max(np.abs(gt - Gm.T @ v)) < 1e-13 * np.max(np.abs(Gm.T @ v))
+        gaps.append(np.linalg.norm(Gm - Gm.T) / np.linalg.norm(Gm))
+    assert gaps[1] < 1e-8 and gaps[1] < 0.1 * gaps[0]
+
+
+def test_lu_transposed_solve():
+    """A^{-T} b from the pivoted LU factors against a library solve with A^T."""
+    import ctypes as C
+    rng = np.random.default_rng(3)
+    N = 40
+    A = rng.standard_normal((N, N)) + 0.1 * np.eye(N)
+    b = rng.standard_normal(N)
+    LU = np.ascontiguousarray(A.copy())
+    piv = np.zeros(N, dtype=np.int32)
+    assert O.lib().orc_lu(N, O._p(LU), piv.ctypes.data_as(C.POINTER(C.c_int))) == 0
+    assert np.any(piv != np.arange(N))   # interchanges happened
+    x = np.empty(N)
+    O.lib().orc_lu_solve_T(N, O._p(LU), piv.ctypes.data_as(C.POINTER(C.c_int)), O._p(b), O._p(x))
+    ref = np.linalg.solve(A.T, b)
+    assert np.max(np.abs(x - ref)) < 1e-12 * np.max(np.abs(ref))

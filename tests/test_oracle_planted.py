@@ -64,6 +64,22 @@ def linearisation_gap(L, N=64):
     return np.max(np.abs(out[1] - (fp - fm) / (2 * eps)))
 
 
+def adjoint_gap(L, N=32, n=6, steps=12):
+    """|grad (discrete adjoint) - J^T r| / |J^T r| (reading R7)."""
+    import ctypes as C
+    prob, _ = O.make_problem(N, n, h=0.5, tau=0.05, steps=steps)
+    c = np.zeros(n + 1)
+    c[0] = 2 * math.pi / math.sqrt(1.05 * math.tanh(0.5))
+    c[1:] = 0.08 * 0.5 ** np.arange(n)
+    r, f = np.empty(N), np.empty(1)
+    Jc = np.empty((n + 1, N))
+    L.orc_shoot_jacobian(C.byref(prob), O._p(c), O._p(r), O._p(Jc), O._p(f))
+    g = np.empty(n + 1)
+    L.orc_objective_and_grad(C.byref(prob), O._p(c), O._p(f), O._p(g))
+    jtr = Jc @ r
+    return np.linalg.norm(g - jtr) / np.linalg.norm(jtr)
+
+
 @pytest.fixture(scope="module")
 def good():
     return O.load(O.build())
@@ -74,6 +90,7 @@ def good():
     (2, analytic_error, 1e-11),         # zeta'(alpha) for zeta'(beta) in K1
     (3, dispersion_rest, 5e-3),         # gravity dropped
     (4, linearisation_gap, 1e-8),       # u psi' dropped from Eq. (l6a)
+    (5, adjoint_gap, 1e-13),            # forward DtN used as its own transpose
 ])
 def test_pin_catches_planted_mistake(good, plant, probe, bound):
     assert probe(good) < bound
