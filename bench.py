@@ -269,6 +269,128 @@ def run_ours(args):
     return out
 
 
+GRAD_METRIC = "gradients/s of f(c) by the discrete adjoint at N=1024 (256 modes + T, 2048 RK4 steps)"
+
+
+def run_gradient(args):
+    """--mode gradient: one step = one objective_and_grad (forward shot that
+    records every stage, then the transposed RK4 sweep) on a gradient workload
+    (default: N = 1024, 256 modes + T, 2048 steps, h = 0.05).  The forward
+    Jacobian route (shoot_jacobian, then J^T r) on the same problem is timed
+    once beside it."""
+    import torch
+    import paper_1210_5672_gb300 as ww
+
+    rank, ws, local = dist_init()
+    w = W.ALL[args.workload]
+    c, seed_used = W.coefficients(w, seed=w.seed + rank)
+    if args.rk_steps:
+        # profiling: fewer RK4 steps at the full run's dt (T scaled), not a bench number
+        c[0] *= args.rk_steps / w.steps
+        w = W.shrink(w, steps=args.rk_steps, name=f"{w.name}[profile: {args.rk_steps} RK steps at full dt]")
+    prec = ww.WW_MIXED if args.form == "mixed" else ww.WW_FP64
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ctx = ww.Context(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps, precision=prec)
+    ct = torch.tensor(c, dtype=torch.float64, device=dev)
+    f = torch.empty(1, dtype=torch.float64, device=dev)
+    grad = torch.empty(w.n + 1, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(dev)
+    ctx.set_stream(stream)
+    for _ in range(args.warmup):
+        ww.objective_and_grad(ctx, ct, f, grad)
+    torch.cuda.synchronize()
+    times, gpu_launches = [], 0
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush_l2(flush)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ww.objective_and_grad(ctx, ct, f, grad)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            gpu_launches += ctx.stats()["launches"]
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = clk.summary()
+    t_step, value = replica_rate(sum(times) / len(times), ws, 1)
+    stats = ctx.stats()
+    # end to end: c from pinned host memory in, f and grad back to pinned host memory
+    ch = torch.tensor(c, dtype=torch.float64).pin_memory()
+    fh = torch.empty(1, dtype=torch.float64).pin_memory()
+    gh = torch.empty(w.n + 1, dtype=torch.float64).pin_memory()
+    e2e_t = []
+    for _ in range(max(1, min(args.steps, 2))):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            ct.copy_(ch, non_blocking=True)
+            ww.objective_and_grad(ctx, ct, f, grad)
+            fh.copy_(f, non_blocking=True)
+            gh.copy_(grad, non_blocking=True)
+        stream.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    _, e2e_value = replica_rate(sum(e2e_t) / len(e2e_t), ws, 1)
+    # the forward route for comparison: n + 1 variational columns, then J^T r
+    r, J, fj = ctx.empty_outputs()
+    ww.shoot_jacobian(ctx, ct, r, J, fj)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ww.shoot_jacobian(ctx, ct, r, J, fj)
+    e1.record(stream)
+    e1.synchronize()
+    t_jac = e0.elapsed_time(e1) / 1e3
+    jtr = (J @ r).cpu().numpy()
+    g_adj = grad.cpu().numpy()
+    agree = float(np.linalg.norm(g_adj - jtr) / np.linalg.norm(jtr))
+    ctx.close()
+    if rank != 0:
+        return None
+    out = {
+        "metric": GRAD_METRIC, "value": value, "unit": "gradients/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.form == "fp64" else "f64+f32/bf16-tensor",
+        "data": "synthetic (seeded PCG64 standing-wave coefficients)",
+        "config": {"workload": w.name, "N": w.N, "n": w.n, "rk4_steps": w.steps, "h": w.h, "g": w.g,
+                   "tau": w.tau, "form": args.form, "seed": seed_used, "mode": "gradient",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "flushed between timed steps (512 MB write)"},
+        "e2e": {"value": e2e_value, "unit": "gradients/s", "h2d_bytes_per_step": 8 * (w.n + 1),
+                "d2h_bytes_per_step": 8 * (w.n + 2)},
+        "roofline": None,
+        "forward_route": {"shoot_jacobian_s": t_jac, "adjoint_s": t_step,
+                          "speedup": t_jac / t_step, "rel_diff_grad_vs_JTr": agree},
+        "stats": stats,
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline_gradient(w, c)
+    return out
+
+
+def cpu_baseline_gradient(w, c):
+    """The oracle's discrete adjoint on one RK4 step of the workload (the full
+    run's dt), scaled to the full step count."""
+    import oracle as O
+    prob, _ = O.make_problem(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=1)
+    cs = c.copy()
+    cs[0] = c[0] / w.steps
+    t0 = time.perf_counter()
+    O.objective_and_grad(prob, cs)
+    t1 = time.perf_counter() - t0
+    return {"value": 1.0 / (t1 * w.steps), "unit": "gradients/s", "cores": O.threads(), "kind": "oracle",
+            "sample": f"1 RK4 step (forward + adjoint) of the {w.name} workload, {t1:.2f} s, "
+                      f"scaled x{w.steps} steps"}
+
+
 def cpu_baseline(w, c, target_s=20.0):
     """The oracle (untuned) on this host's cores, on a bounded sample of the same
     workload: all columns, as many RK4 steps as fit in ~target_s; scaled to
@@ -331,17 +453,23 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default=W.LARGE.name, choices=sorted(W.ALL))
+    ap.add_argument("--workload", default=None, choices=sorted(W.ALL),
+                    help=f"default {W.LARGE.name} (jacobian mode), {W.SHALLOW.name} (gradient mode)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="jacobian", choices=["jacobian", "gradient"],
+                    help="gradient: objective_and_grad by the discrete adjoint (default workload "
+                         "N1024_n256_steps2048_h0.05)")
     ap.add_argument("--rk-steps", type=int, default=0,
                     help="profiling only: override the workload's RK4 step count (not a bench number)")
     args = ap.parse_args()
+    if args.workload is None:
+        args.workload = W.SHALLOW.name if args.mode == "gradient" else W.LARGE.name
     if args.impl == "reference":
         out = run_reference(args)
     else:
         from paper_1210_5672_gb300 import build as B
         B.build()
-        out = run_ours(args)
+        out = run_gradient(args) if args.mode == "gradient" else run_ours(args)
     if out is not None:
         print(json.dumps(out), flush=True)
 

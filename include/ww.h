@@ -148,10 +148,15 @@ int shoot_jacobian(ww_ctx *ctx, const double *c, double *r, double *J, double *f
  * copies r, J, f out (pinned or pageable host memory). */
 int shoot_jacobian_host(ww_ctx *ctx, const double *c, double *r, double *J, double *f);
 
-/* objective_and_grad -- Sec. 3.2 Eqs. (f:phi:again), (nabla:f): f and its
- * gradient with respect to c (device, n+1 doubles), grad = J^T r computed from
- * the forward variational columns of shoot_jacobian (same discrete map, so
- * it equals the discrete adjoint's result up to roundoff). */
+/* objective_and_grad -- Sec. 3.2 Eqs. (adj), (nabla:f), App. C Eq. (adj2):
+ * f (device, 1 double) and its gradient with respect to c (device, n+1
+ * doubles; grad[0] = d f / d T) by the DISCRETE adjoint: one forward pass of
+ * the base state that records every RK stage (6N doubles a stage, allocated
+ * on the first call and kept with the context), then the transposed RK4
+ * steps backward, each stage with its DtN assembled transposed (A^T, G^T) and
+ * factored as in the forward form.  grad equals J^T r of shoot_jacobian up to
+ * roundoff, at the cost of about two shots instead of n + 1 columns.
+ * Errors as shoot; WW_ERR_ALLOC if the trajectory record does not fit. */
 int objective_and_grad(ww_ctx *ctx, const double *c, double *f, double *grad);
 
 /* dtn_apply_static -- the same operator as dtn_setup followed by dtn_apply,

@@ -19,7 +19,7 @@ the paper the C function follows:
 * ``shoot_jacobian`` -- J of Eqs. (Jik), (q:qdot), T column by reading R2
 * ``objective_and_grad`` -- f and its gradient by the discrete adjoint of the
                         RK4 scheme (Sec. 3.2 Eqs. adj, nabla:f; App. C Eq. adj2;
-                        reading R7: exact transpose of the discrete map)
+                        reading R18: exact transpose of the discrete map)
 * ``dtn_T``          -- the transpose of the discrete DtN operator
 * ``energy``         -- the energy monitor of Sec. 4
 """
@@ -222,7 +222,7 @@ def shoot_jacobian(prob: Problem, c):
 
 def objective_and_grad(prob: Problem, c):
     """(f, grad) with grad[0] = d f / d T and grad[k] = d f / d c_k, by the
-    discrete adjoint (reading R7)."""
+    discrete adjoint (reading R18)."""
     c = _f64(c)
     f = np.empty(1)
     g = np.empty(prob.n + 1)

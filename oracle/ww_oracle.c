@@ -40,7 +40,7 @@
  *  R5 residual weight w = sqrt(1/N) (uniform grid, E = 1 in Eq. (f:phi)).
  *  R6 the linearisation is the continuum one of App. B with the shared
  *     discrete DtN operator (K and G are not differentiated).
- *  R7 the gradient of f (Sec. 3.2, App. C) is the DISCRETE adjoint: the
+ *  R18 the gradient of f (Sec. 3.2, App. C) is the DISCRETE adjoint: the
  *     transpose of the RK4 scheme above, so grad f = J^T r of the discrete
  *     map up to roundoff.  App. C derives the continuous adjoint from the
  *     self-adjointness of the continuous DtN map; its discretisation is only
@@ -333,7 +333,7 @@ static void dtn_apply_one(const dtn_state *s, const double *phi, double *out)
     free(mu); free(gam); free(hg);
 }
 
-/* The transpose of the operator of dtn_apply_one (reading R7).  Forward:
+/* The transpose of the operator of dtn_apply_one (reading R18).  Forward:
  * G phi = (1/2 H + G) D A^{-1} phi.  The Fourier multipliers ik and -i sgn k
  * (Nyquist zeroed) are antisymmetric, D^T = -D and H^T = -H, so
  * G^T x = A^{-T} D (1/2 H x - G^T x). */
@@ -580,7 +580,7 @@ void orc_shoot_jacobian(const orc_problem *p, const double *c, double *r, double
 
 /* ------------------------------------------------------------------ */
 /* Gradient by the discrete adjoint (Sec. 3.2 Eqs. (adj), (nabla:f);   */
-/* App. C Eq. (adj2); reading R7)                                       */
+/* App. C Eq. (adj2); reading R18)                                       */
 /* ------------------------------------------------------------------ */
 
 /* Transpose of the filtered variational RHS of orc_rhs at the base state q,

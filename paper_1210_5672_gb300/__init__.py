@@ -232,6 +232,7 @@ def shoot_jacobian_host(ctx: Context, c: np.ndarray, r: np.ndarray, J: np.ndarra
 
 
 def objective_and_grad(ctx: Context, c, f, grad):
+    """f (1,) and grad (n+1,) CUDA float64 by the discrete adjoint (grad[0] = d f / d T)."""
     _check(lib().objective_and_grad(ctx.handle, _dptr(c, ctx.n + 1, "c"), _dptr(f, 1, "f"),
                                     _dptr(grad, ctx.n + 1, "grad")))
 

@@ -52,21 +52,6 @@ void fill_tables(int N, double *tw, double *cs) {
 
 namespace {
 
-__global__ void k_jtr(const double *__restrict__ J, const double *__restrict__ r, int N, double *grad) {
-    __shared__ double red[32];
-    const double *col = J + (size_t)blockIdx.x * N;
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) acc = fma(col[i], r[i], acc);
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (threadIdx.x == 0) grad[blockIdx.x] = acc;
-    }
-}
-
 constexpr int NPH = WW_NPHASE;
 constexpr int EV_PER_STEP = 4 * NPH * 2;   // [stage][phase][begin/end]
 
@@ -110,6 +95,10 @@ struct Owned {
     std::vector<cudaEvent_t> pool;            // steps * EV_PER_STEP
     double ph_ms[NPH] = {};
     int ph_count[NPH] = {};
+    // the adjoint sweep (allocated by its first call): trajectory records and
+    // the forward step, the turn-around and the backward step as graphs
+    AdjWs adj = {};
+    StepGraph adj_fwd, adj_mid, adj_bwd;
 };
 
 // record the begin (b = 0) or end (b = 1) event of a phase of stage st
@@ -425,6 +414,7 @@ int check_status(Ctx *c) {
 
 int run_shot(Owned *o, const double *cvec, bool c_on_host, double *r, double *J, double *f, int with_cols) {
     Ctx *c = &o->c;
+    c->one_col = !with_cols;   // (graphs are captured per with_cols, each with its own setting)
     WW_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     WW_CUDA_TRY(cudaMemcpyAsync(o->cbuf, cvec, sizeof(double) * (c->n + 1),
                                 c_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
@@ -464,6 +454,135 @@ int run_shot(Owned *o, const double *cvec, bool c_on_host, double *r, double *J,
     WW_TRY(check_status(c));
     if (o->timing) WW_TRY(collect_timing(o));
     return WW_OK;
+}
+
+// ---------------------------------------------------------------- discrete adjoint
+int ensure_adjoint(Owned *o) {
+    AdjWs &a = o->adj;
+    if (a.rec) return WW_OK;
+    const Ctx *c = &o->c;
+    const size_t N = (size_t)c->N;
+    WW_TRY(dalloc_n(o, &a.rec, (size_t)4 * c->steps * ADJ_REC * N));
+    WW_TRY(dalloc_n(o, &a.lam, 2 * N));
+    WW_TRY(dalloc_n(o, &a.kb, 8 * N));
+    WW_TRY(dalloc_n(o, &a.eta, N));
+    WW_TRY(dalloc_n(o, &a.chi, N));
+    WW_TRY(dalloc_n(o, &a.y, N));
+    WW_TRY(dalloc_n(o, &a.etal, N));
+    WW_TRY(dalloc_n(o, &a.psil, N));
+    WW_TRY(dalloc_n(o, &a.gT, 1));
+    WW_TRY(dalloc_n(o, &a.step, 1));
+    return prepare_adjoint(c->N);
+}
+
+// forward: one RK step of the base state, each stage recorded (its surface
+// before the stage, its phi_x, phi_y, w3 and F after)
+int adj_forward_step(Owned *o) {
+    Ctx *c = &o->c;
+    for (int k = 0; k < 4; ++k) {
+        select_parity(c, k & 1);
+        WW_TRY(launch_adj_record_eta(c, &o->adj, k));
+        WW_TRY(run_base(c, k, o->cbuf));
+        WW_TRY(launch_adj_record_fields(c, &o->adj, k));
+    }
+    return WW_OK;
+}
+
+// turn-around: lambda = (0, phi(T/4)/N), and (mixed form) a fresh inverse of
+// the transposed operator at the final surface for the first backward stage
+int adj_turnaround(Owned *o) {
+    Ctx *c = &o->c;
+    select_parity(c, 0);
+    WW_TRY(launch_adj_init(c, &o->adj));
+    if (c->precision == WW_MIXED) {
+        WW_TRY(launch_base_geometry(c, c->Ys, c->Ys, 0));
+        WW_TRY(launch_assemble(c));
+        WW_TRY(factor(c, 1));
+    }
+    return WW_OK;
+}
+
+// backward: the transposed RK step (filter, then stages 3..0)
+int adj_backward_step(Owned *o) {
+    Ctx *c = &o->c;
+    AdjWs *a = &o->adj;
+    select_parity(c, 0);
+    WW_TRY(launch_adj_begin_step(c, a, o->cbuf));
+    for (int k = 3; k >= 0; --k) {
+        WW_TRY(launch_adj_fetch(c, a, k));
+        WW_TRY(launch_base_geometry(c, a->eta, a->eta, 0));
+        WW_TRY(launch_assemble(c));                  // A^T, G^T
+        WW_TRY(factor(c, 0, 1));
+        WW_TRY(launch_adj_local(c, a, k, o->cbuf));
+        WW_TRY(gemv_narrow(c->stream, c->N, 1, c->N, 1.0, c->G, c->N, a->chi, c->N, 0.0, a->y, c->N));   // G^T chi
+        WW_TRY(launch_adj_dtn(c, a));
+        WW_TRY(solve(c, c->M, 1));                   // A^{-T} D (1/2 H chi - G^T chi)
+        WW_TRY(launch_adj_update(c, a, k, o->cbuf));
+    }
+    return WW_OK;
+}
+
+// run `body` once on the stream, through a graph captured on first use
+template <class F>
+int replay(Owned *o, StepGraph &sg, F body) {
+    Ctx *c = &o->c;
+    if (c->stream == nullptr) return body();
+    if (!sg.exec) {
+        cudaGraph_t g = nullptr;
+        WW_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        o->capturing = true;
+        const int st = body();
+        o->capturing = false;
+        const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (st != WW_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return fail(WW_ERR_CUDA, std::string("adjoint capture: ") + cudaGetErrorString(e));
+        WW_TRY(count_kernel_nodes(g, &sg.nkern));
+        const cudaError_t ei = cudaGraphInstantiate(&sg.exec, g, 0);
+        sg.graph = g;
+        if (ei != cudaSuccess) return fail(WW_ERR_CUDA, std::string("adjoint instantiate: ") + cudaGetErrorString(ei));
+    }
+    WW_CUDA_TRY(cudaGraphLaunch(sg.exec, c->stream));
+    return WW_OK;
+}
+
+int run_adjoint(Owned *o, const double *cvec, bool c_on_host, double *f, double *grad) {
+    Ctx *c = &o->c;
+    WW_TRY(ensure_adjoint(o));
+    const bool timing = o->timing;
+    o->timing = false;   // the phase timers cover the forward Jacobian only
+    struct Restore {
+        Owned *o;
+        bool t;
+        ~Restore() {
+            o->timing = t;
+            o->c.trans = 0;
+        }
+    } restore{o, timing};
+    c->one_col = true;
+    WW_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    WW_CUDA_TRY(cudaMemsetAsync(o->adj.step, 0, sizeof(int), c->stream));
+    WW_CUDA_TRY(cudaMemcpyAsync(o->cbuf, cvec, sizeof(double) * (c->n + 1),
+                                c_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+    c->trans = 0;
+    WW_TRY(run_prologue(o, 0));
+    for (int s = 0; s < c->steps; ++s) WW_TRY(replay(o, o->adj_fwd, [&] { return adj_forward_step(o); }));
+    WW_TRY(launch_outputs(c, o->rbuf, nullptr, f, 0));
+    c->trans = 1;
+    WW_TRY(replay(o, o->adj_mid, [&] { return adj_turnaround(o); }));
+    for (int s = 0; s < c->steps; ++s) WW_TRY(replay(o, o->adj_bwd, [&] { return adj_backward_step(o); }));
+    c->trans = 0;
+    WW_TRY(launch_adj_grad(c, &o->adj, grad));
+    c->stats.stages = 8 * c->steps;
+    if (c->stream == nullptr)
+        c->stats.launches = -1;
+    else
+        c->stats.launches = (long long)o->prologue[0].nkern + (long long)c->steps * o->adj_fwd.nkern + 1 +
+                            o->adj_mid.nkern + (long long)c->steps * o->adj_bwd.nkern + 1;
+    c->dtn_ready = false;
+    return check_status(c);
 }
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -645,6 +764,10 @@ void ww_destroy(ww_ctx *ctx) {
         if (o->prologue[w].exec) cudaGraphExecDestroy(o->prologue[w].exec);
         if (o->prologue[w].graph) cudaGraphDestroy(o->prologue[w].graph);
     }
+    for (StepGraph *sg : {&o->adj_fwd, &o->adj_mid, &o->adj_bwd}) {
+        if (sg->exec) cudaGraphExecDestroy(sg->exec);
+        if (sg->graph) cudaGraphDestroy(sg->graph);
+    }
     for (cudaEvent_t ev : o->placeholder)
         if (ev) cudaEventDestroy(ev);
     for (cudaEvent_t ev : o->pool) cudaEventDestroy(ev);
@@ -696,6 +819,7 @@ int dtn_setup(ww_ctx *ctx, const double *eta) {
     if (!ctx || !eta) return fail(WW_ERR_ARG, "dtn_setup: NULL argument");
     Ctx *c = &owner(ctx)->c;
     c->dtn_ready = false;
+    c->one_col = false;   // dtn_apply may take many columns
     select_parity(c, 0);
     WW_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     WW_TRY(launch_base_geometry(c, eta, nullptr, 0));
@@ -745,11 +869,8 @@ int shoot_jacobian_host(ww_ctx *ctx, const double *cvec, double *r, double *J, d
 int objective_and_grad(ww_ctx *ctx, const double *cvec, double *f, double *grad) {
     if (!ctx || !cvec || !f || !grad) return fail(WW_ERR_ARG, "objective_and_grad: NULL argument");
     Owned *o = owner(ctx);
-    Ctx *c = &o->c;
-    WW_TRY(run_shot(o, cvec, false, o->rbuf, o->Jbuf, f, 1));
-    k_jtr<<<c->nc, 256, 0, c->stream>>>(o->Jbuf, o->rbuf, c->N, grad);
-    WW_CUDA_TRY(cudaGetLastError());
-    WW_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    WW_TRY(run_adjoint(o, cvec, false, f, grad));
+    WW_CUDA_TRY(cudaStreamSynchronize(o->c.stream));
     return WW_OK;
 }
 

@@ -53,8 +53,8 @@ __device__ __forceinline__ double2 cot_half(double cx, double sx, double ch, dou
 __global__ void __launch_bounds__(ASM_TI) k_assemble(const double *__restrict__ eta, const double *__restrict__ eta_x,
                                                      const double *__restrict__ eta_xx, const double *__restrict__ E,
                                                      const double *__restrict__ Einv, const double *__restrict__ cs,
-                                                     const double *__restrict__ cot0, int N, int deep, double *A,
-                                                     double *G) {
+                                                     const double *__restrict__ cot0, int N, int deep, int trans,
+                                                     double *A, double *G) {
     const int i = blockIdx.x * ASM_TI + threadIdx.x;
     const int j0 = blockIdx.y * ASM_TJ;
     if (i >= N) return;
@@ -99,12 +99,15 @@ __global__ void __launch_bounds__(ASM_TI) k_assemble(const double *__restrict__ 
             // G2 = -Re{ zeta'(alpha)/2 cot }
             g2 = -0.5 * fma(-exi, ct.y, ct.x);
         }
-        const size_t idx = (size_t)j * N + i;
+        const size_t idx = trans ? (size_t)i * N + j : (size_t)j * N + i;
         A[idx] = (k1 + k2) * invN + (i == j ? 0.5 : 0.0);
         G[idx] = (g1 + g2) * invN;
     }
 }
 
+// trans != 0 writes A^T and G^T instead (the operands of the transposed DtN
+// of the adjoint sweep).
+//
 // Symmetric form: cot is odd, so the (j, i) entry follows from the (i, j) one:
 //   cot((-x - iy)/2) = -cot((x + iy)/2),  cot((-x + iy')/2) = -conj(cot((x + iy')/2)),
 // and cot((alpha_j - alpha_i)/2) = -cot((alpha_i - alpha_j)/2).  Each block
@@ -118,7 +121,7 @@ __global__ void __launch_bounds__(256) k_assemble_sym(const double *__restrict__
                                                       const double *__restrict__ eta_xx, const double *__restrict__ E,
                                                       const double *__restrict__ Einv,
                                                       const double *__restrict__ cs, const double *__restrict__ cot0,
-                                                      int N, int deep, double *A, double *G) {
+                                                      int N, int deep, int trans, double *A, double *G) {
     __shared__ double tA[ST][ST + 1], tG[ST][ST + 1];
     // triangular tile index -> (I, J), I <= J
     const int T = N / ST;
@@ -164,6 +167,13 @@ __global__ void __launch_bounds__(256) k_assemble_sym(const double *__restrict__
             kji += -0.5 * fma(exi, ct.x, ct.y);
             gji += 0.5 * fma(exj, ct.y, ct.x);
         }
+        if (trans) {   // entry (i, j) of A^T is entry (j, i) of A
+            const double tk = kij, tg = gij;
+            kij = kji;
+            gij = gji;
+            kji = tk;
+            gji = tg;
+        }
         const size_t idx = (size_t)j * N + i;
         A[idx] = kij * invN + (i == j ? 0.5 : 0.0);
         G[idx] = gij * invN;
@@ -187,13 +197,14 @@ int launch_assemble(Ctx *c) {
     if (c->N % ST == 0) {
         const int T = c->N / ST;
         k_assemble_sym<<<T * (T + 1) / 2, 256, 0, c->stream>>>(c->eta, c->eta_x, c->eta_xx, c->E, c->Einv, c->cs,
-                                                              c->cs + 2 * c->N, c->N, c->deep ? 1 : 0, c->A, c->G);
+                                                              c->cs + 2 * c->N, c->N, c->deep ? 1 : 0, c->trans, c->A,
+                                                              c->G);
         WW_CUDA_TRY(cudaGetLastError());
         return WW_OK;
     }
     dim3 grid((c->N + ASM_TI - 1) / ASM_TI, (c->N + ASM_TJ - 1) / ASM_TJ);
     k_assemble<<<grid, ASM_TI, 0, c->stream>>>(c->eta, c->eta_x, c->eta_xx, c->E, c->Einv, c->cs, c->cs + 2 * c->N,
-                                               c->N, c->deep ? 1 : 0, c->A, c->G);
+                                               c->N, c->deep ? 1 : 0, c->trans, c->A, c->G);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }

@@ -101,6 +101,9 @@ struct Ctx {
     double *small;            // scratch doubles (reductions)
 
     bool dtn_ready;
+    int trans;                // 1 while the adjoint sweep assembles A^T and G^T in place of A and G
+    bool one_col;             // only one-column solves and products follow (base-only shots, the adjoint):
+                              // the mixed form skips the digit splits of K and G that wide products read
     ww_stats stats;
     Mixed *mx;
     void *owner;              // the API-side object holding this context (phase timing)
@@ -205,8 +208,31 @@ int launch_cbase_rhs(Ctx *c, int stage, const double *cvec);
 int launch_outputs(Ctx *c, double *r, double *J, double *f, int with_J);
 int launch_copy_cols(Ctx *c, const double *src, int ncols, double *dst);
 
-// assembly (ww_assemble.cu)
+// assembly (ww_assemble.cu); c->trans selects A^T, G^T
 int launch_assemble(Ctx *c);
+
+// the discrete adjoint (ww_adjoint.cu).  Trajectory record per RK stage:
+// [eta | phi_x | phi_y | (1+eta'^2)^{-3/2} | F (2N)], ADJ_REC doubles per point
+constexpr int ADJ_REC = 6;
+struct AdjWs {
+    double *rec;              // 4 steps records of ADJ_REC * N
+    double *lam;              // 2N: the adjoint state
+    double *kb;               // 4 x 2N: adjoints of the stage right-hand sides
+    double *eta;              // N: the stage surface fetched for its geometry
+    double *chi, *y, *etal, *psil;   // N each
+    double *gT;               // 1: d f / d T
+    int *step;                // 1: the RK step the record kernels address
+};
+int prepare_adjoint(int Nmax);                            // shared-memory limits of the sweep's FFT kernels
+int launch_adj_record_eta(Ctx *c, AdjWs *a, int st);      // forward: the stage surface (before its RK update)
+int launch_adj_record_fields(Ctx *c, AdjWs *a, int st);   // forward: phi_x, phi_y, w3, F; st == 3 advances the step
+int launch_adj_init(Ctx *c, AdjWs *a);                    // lambda = (0, phi(T/4)/N), dT = 0, step = steps
+int launch_adj_begin_step(Ctx *c, AdjWs *a, const double *cvec);   // step -= 1; filter lambda; kb = b dt/6 lambda
+int launch_adj_fetch(Ctx *c, AdjWs *a, int st);           // the stage surface into a->eta
+int launch_adj_local(Ctx *c, AdjWs *a, int st, const double *cvec);   // chi, local terms, dT += kb.F/T
+int launch_adj_dtn(Ctx *c, AdjWs *a);                     // M[:,0] = D (1/2 H chi - G^T chi)
+int launch_adj_update(Ctx *c, AdjWs *a, int st, const double *cvec);  // lambda, kb of the previous stage
+int launch_adj_grad(Ctx *c, AdjWs *a, double *grad);      // grad = (dT, basis^T lambda)
 
 // dense FP64 (ww_dense.cu)
 int prepare_dense();                                 // shared-memory limit of the LU block kernel

@@ -349,6 +349,7 @@ int mixed_setup(Ctx *c, int fresh, int update) {
     }
     // an update left out on the device leaves this stage's rows of X to a slice of X
     if (skip) WW_TRY(tc_slice_f32(s, m->X, N, N, N, 1, 0.f, 2, m->Xrow[q], nullptr, skip, 1));
+    if (c->one_col) return WW_OK;   // the narrow solves and products read A and G directly
     WW_TRY(ozaki_digits(s, c->A, N, N, N, 0, 0.5f, m->Ke, m->Ks[q], m->Kd[q], nullptr));   // K = A - I/2
     WW_TRY(ozaki_digits(s, c->G, N, N, N, 0, 0.f, m->Ge, m->Gs[q], m->Gd[q], nullptr));
     return WW_OK;

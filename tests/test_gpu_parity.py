@@ -196,6 +196,71 @@ def test_shoot_and_gradient_consistent(ww):
     assert rel(cg.grad.cpu().numpy(), jtr) < 1e-13 and fa.item() == f.item()
 
 
+def gpu_gradient(ww, w, c, precision=0, basis=None):
+    import torch
+    with ww.Context(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps, basis=basis, precision=precision) as ctx:
+        f = torch.empty(1, dtype=torch.float64, device="cuda")
+        grad = torch.empty(w.n + 1, dtype=torch.float64, device="cuda")
+        ww.objective_and_grad(ctx, dev(c), f, grad)
+        return float(f.item()), grad.cpu().numpy(), ctx.stats()
+
+
+def paper_basis(N, n):
+    # Eq. (init:stand): even k on eta, odd k on phi
+    x = x_grid(N)
+    B = np.zeros((2 * N, n))
+    for k in range(1, n + 1):
+        B[(0 if k % 2 == 0 else N):(N if k % 2 == 0 else 2 * N), k - 1] = 2 * np.cos(k * x)
+    return B
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("h,tau,amp,phi_basis", [
+    (0.3, 0.05, 0.05, False),          # shallow with surface tension
+    (math.inf, 0.1, 0.05, False),      # deep water with surface tension
+    (1.0, 0.0, 0.05, True),            # phi components in the basis
+])
+def test_adjoint_gradient_matches_oracle(ww, precision, h, tau, amp, phi_basis):
+    """objective_and_grad (the discrete adjoint, reading R18) against the oracle's
+    discrete adjoint, f and every gradient entry (the T entry included)."""
+    N, n, steps = 64, 12, 24
+    w = W.Workload("adj", N=N, n=n, steps=steps, h=h, tau=tau, amp=amp)
+    c, _ = W.coefficients(w)
+    c[0] = stable_T(N, steps, w.g, tau, h)   # RK4 inside its stability region at this N
+    B = paper_basis(N, n) if phi_basis else None
+    f, g, st = gpu_gradient(ww, w, c, precision, B)
+    prob, keep = O.make_problem(N, n, g=w.g, tau=tau, h=h, steps=steps, basis=B)
+    f0, g0 = O.objective_and_grad(prob, c)
+    assert abs(f - f0) / f0 < TOL
+    assert rel(g, g0) < TOL
+    assert np.max(np.abs(g - g0)) < TOL * np.max(np.abs(g0))
+    assert st["stages"] == 8 * steps and st["launches"] > 0
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("wl", ["N1024_n256_steps2048_h0.05", "N1024_n256_steps2048_deep_tau0.1"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_adjoint_full_size_two_steps(ww, wl, precision):
+    """The gradient workloads at full size (N = 1024, 256 modes + T) in the
+    launch configuration the benchmark times, for TWO RK4 steps of the full
+    run's dt (T scaled by 2/2048; the oracle cannot run 2048 steps at N = 1024),
+    against the oracle's discrete adjoint."""
+    full = W.ALL[wl]
+    w = W.shrink(full, steps=2)
+    c, _ = W.coefficients(full)
+    c[0] *= 2 / full.steps
+    f, g, _ = gpu_gradient(ww, w, c, precision)
+    if wl not in _ADJ_ORACLE:
+        prob, _ = O.make_problem(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps)
+        _ADJ_ORACLE[wl] = O.objective_and_grad(prob, c)
+    f0, g0 = _ADJ_ORACLE[wl]
+    assert abs(f - f0) / f0 < TOL
+    assert rel(g, g0) < TOL
+
+
+_ADJ_ORACLE = {}
+
+
 def test_host_entry_point_matches_device(ww):
     w = W.shrink(W.MEDIUM, N=128, n=10, steps=4)
     c, _ = W.coefficients(w)

@@ -19,7 +19,7 @@ coefficient in the oracle fails at least one of them:
                          difference of the discrete RHS.
 * Jacobian            -- Eq. (Jik) columns against central differences of the
                          objective, T column included (reading R2).
-* adjoint gradient    -- Sec. 3.2 / App. C by the discrete adjoint (reading R7):
+* adjoint gradient    -- Sec. 3.2 / App. C by the discrete adjoint (reading R18):
                          equals J^T r of the forward variational columns (an
                          independent algorithm) to roundoff, and central
                          differences of f to the linearisation's accuracy;
@@ -344,7 +344,7 @@ def _adjoint_case(N, n, steps, h, tau, amp, phi_basis=False):
 
 @pytest.mark.parametrize("h,tau,phi_basis", [(0.3, 0.05, False), (math.inf, 0.1, False), (1.0, 0.0, True)])
 def test_adjoint_gradient_equals_JT_r(h, tau, phi_basis):
-    """Reading R7: the discrete adjoint's gradient is J^T r of the discrete map,
+    """Reading R18: the discrete adjoint's gradient is J^T r of the discrete map,
     where J comes from the forward variational columns (Eq. Jik)."""
     prob, keep, c = _adjoint_case(32, 10, 24, h, tau, 0.05, phi_basis)
     r, J, f = O.shoot_jacobian(prob, c)

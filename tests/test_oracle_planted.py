@@ -65,7 +65,7 @@ def linearisation_gap(L, N=64):
 
 
 def adjoint_gap(L, N=32, n=6, steps=12):
-    """|grad (discrete adjoint) - J^T r| / |J^T r| (reading R7)."""
+    """|grad (discrete adjoint) - J^T r| / |J^T r| (reading R18)."""
     import ctypes as C
     prob, _ = O.make_problem(N, n, h=0.5, tau=0.05, steps=steps)
     c = np.zeros(n + 1)
