@@ -50,7 +50,8 @@ int ozaki_digits(cudaStream_t s, const double *X, int ld, int rows, int K, int s
                  double *scale, __nv_bfloat16 *dst, const int *skip);
 int ozaki_gemm(cudaStream_t s, const __nv_bfloat16 *Ad, const double *sa, const __nv_bfloat16 *Bd, const double *sb,
                int M, int Nn, int K, int mode, double *C, int ldc, const double *Psi, int ldpsi, const double *Mh,
-               int ldm, unsigned long long *colmax, int *err, const int *skip, __nv_bfloat16 *rslc = nullptr);
+               int ldm, unsigned long long *colmax, int *err, const int *skip, __nv_bfloat16 *rslc = nullptr,
+               int nd = 7);
 int ozaki_digits_cols(cudaStream_t s, const double *X, int ld, int ncols, int K, double *scale, __nv_bfloat16 *dst,
                       unsigned long long *zero_cm, const int *skip);
 
@@ -393,8 +394,10 @@ int mixed_solve(Ctx *c, double *B, int ncols) {
             // digits and scales of M (scales -> Rs), max|R| reset; the residual
             // kernel writes R straight into the slices of the correction's operand
             WW_TRY(ozaki_digits_cols(s, B, N, ncols, N, m->Rs, m->Rd, cm, done));
+            // the first residual's error is contracted by the next correction: 5 digits
+            // (2^-35 of the operands' maxima) leave the result within the 7-digit floor
             WW_TRY(ozaki_gemm(s, m->Kd[q], m->Ks[q], m->Rd, m->Rs, N, ncols, N, 1, nullptr, N, w.Psi, N, B, N, cm,
-                              m->err, done, m->Bslc));
+                              m->err, done, m->Bslc, it == 0 ? 5 : 7));
             WW_TRY(tc_gemm_2x2(s, m->Xrow[q], m->Bslc, N, ncols, N, 2, nullptr, B, N, 1.0, m->err, done));
         }
         // converged after this correction?

@@ -70,6 +70,10 @@ struct OzOut {
     __nv_bfloat16 *rslc;          // mode 1: 2 bf16 slices of R ([2][Nn][M], as the next product's B), or NULL
 };
 
+// ND <= OZ_S digits of each operand take part (ND = 7: all pairs with g <= 6;
+// ND = 5: g <= 4, 15 pairs, the operands to 2^-35 of their row / column maxima,
+// for residuals whose error is contracted by a later correction).
+template <int ND>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_ozaki(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int Nn, int K,
             const double *__restrict__ sa, const double *__restrict__ sb, OzOut out, int *err, const int *skip) {
@@ -122,14 +126,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             if (warp == 0) {
                 const int bs = kc % OZ_BSLOTS;
                 tc::mbar_wait(&b_empty[bs], ((kc / OZ_BSLOTS) & 1) ^ 1, err);
-                tc::mbar_arrive_expect_tx_if(leader, &b_full[bs], OZ_B_STAGE);
+                tc::mbar_arrive_expect_tx_if(leader, &b_full[bs], ND * OZ_B_TILE);
 #pragma unroll
-                for (int q = 0; q < OZ_S; ++q)
+                for (int q = 0; q < ND; ++q)
                     tc::tma_load_2d_if(leader, &tmB, &b_full[bs], bring + bs * OZ_B_STAGE + q * OZ_B_TILE,
                                        kc * OZ_BK, q * Nn + n0);
             }
-            for (int p = p0; p < OZ_S; p += 2) {
-                const int ai = kc * OZ_S + p, as = ai % OZ_ASLOTS;
+            for (int p = p0; p < ND; p += 2) {
+                const int ai = kc * ND + p, as = ai % OZ_ASLOTS;
                 tc::mbar_wait(&a_empty[as], ((ai / OZ_ASLOTS) & 1) ^ 1, err);
                 tc::mbar_arrive_expect_tx_if(leader, &a_full[as], OZ_A_TILE);
                 tc::tma_load_2d_if(leader, &tmA, &a_full[as], aring + as * OZ_A_TILE, kc * OZ_BK, p * M + m0);
@@ -150,8 +154,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             tc::fence_after();
             const uint32_t bst = tc::smem_u32(bring + bs * OZ_B_STAGE);
 #pragma unroll
-            for (int p = 0; p < OZ_S; ++p) {
-                const int ai = kc * OZ_S + p, as = ai % OZ_ASLOTS;
+            for (int p = 0; p < ND; ++p) {
+                const int ai = kc * ND + p, as = ai % OZ_ASLOTS;
                 tc::mbar_wait(&a_full[as], (ai / OZ_ASLOTS) & 1, err);
                 tc::fence_after();
                 const uint64_t da = tc::desc_k128(tc::smem_u32(aring + as * OZ_A_TILE));
@@ -160,8 +164,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 // the stage, so up to four of them form one N = 256 operand.  One
                 // wide MMA reads the A digit once instead of once per q.
 #pragma unroll
-                for (int q0 = 0; q0 + p < OZ_G; q0 += 4) {
-                    const int nq = min(4, OZ_G - p - q0);
+                for (int q0 = 0; q0 + p < ND; q0 += 4) {
+                    const int nq = min(4, ND - p - q0);
                     const uint32_t id = tc::idesc_bf16(OZ_BM, OZ_BN * nq);
                     const uint32_t d = tmem + (uint32_t)((p + q0) * OZ_BN);
                     const uint64_t db = tc::desc_k128(bst + q0 * OZ_B_TILE);
@@ -187,7 +191,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             tc::mbar_wait(acc_full, kb & 1, err);
             tc::fence_after();
 #pragma unroll 1
-            for (int g = 0; g < OZ_G; ++g) {
+            for (int g = 0; g < ND; ++g) {
                 float v[32];
                 tc::tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(g * OZ_BN + chalf * 32), v);
 #pragma unroll
@@ -384,15 +388,17 @@ int ozaki_digits(cudaStream_t s, const double *X, int ld, int rows, int K, int s
 // mode 0: C += A B ; mode 1: C = Psi - 0.5 Mh - A B  (A = left digits, B = right digits)
 int ozaki_gemm(cudaStream_t s, const __nv_bfloat16 *Ad, const double *sa, const __nv_bfloat16 *Bd, const double *sb,
                int M, int Nn, int K, int mode, double *C, int ldc, const double *Psi, int ldpsi, const double *Mh,
-               int ldm, unsigned long long *colmax, int *err, const int *skip, __nv_bfloat16 *rslc) {
+               int ldm, unsigned long long *colmax, int *err, const int *skip, __nv_bfloat16 *rslc, int nd) {
     if (K % OZ_BK != 0) return fail(WW_ERR_ARG, "ozaki_gemm: K must be a multiple of 64");
+    if (nd != 5 && nd != OZ_S) return fail(WW_ERR_ARG, "ozaki_gemm: 5 or 7 digits");
     CUtensorMap ta, tb;
     WW_TRY(tc_make_map(&ta, Ad, K, (long)OZ_S * M, OZ_BM, OZ_BK));
     WW_TRY(tc_make_map(&tb, Bd, K, (long)OZ_S * Nn, OZ_BN, OZ_BK));
-    WW_CUDA_TRY(cudaFuncSetAttribute(k_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+    auto kern = nd == 5 ? k_ozaki<5> : k_ozaki<OZ_S>;
+    WW_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
     OzOut o{mode, C, ldc, Psi, ldpsi, Mh, ldm, colmax, rslc};
     dim3 grid((M + OZ_BM - 1) / OZ_BM, (Nn + OZ_BN - 1) / OZ_BN);
-    k_ozaki<<<grid, OZ_THREADS, OZ_SMEM, s>>>(ta, tb, M, Nn, K, sa, sb, o, err, skip);
+    kern<<<grid, OZ_THREADS, OZ_SMEM, s>>>(ta, tb, M, Nn, K, sa, sb, o, err, skip);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
@@ -423,7 +429,7 @@ extern "C" int ww_selftest_ozaki(const double *A, const double *B, int M, int Nn
     if (st == WW_OK) st = ozaki_digits(s, A, M, M, K, 0, 0.f, ea, sa, Ad, nullptr);
     if (st == WW_OK) st = ozaki_digits(s, B, K, Nn, K, 1, 0.f, eb, sb, Bd, nullptr);
     if (st == WW_OK)
-        st = ozaki_gemm(s, Ad, sa, Bd, sb, M, Nn, K, 0, C, M, nullptr, 0, nullptr, 0, nullptr, err, nullptr, nullptr);
+        st = ozaki_gemm(s, Ad, sa, Bd, sb, M, Nn, K, 0, C, M, nullptr, 0, nullptr, 0, nullptr, err, nullptr, nullptr, 7);
     if (st == WW_OK) st = dgemm(s, M, Nn, K, 1.0, A, M, B, K, 0.0, C0, M);
     if (st == WW_OK && cudaDeviceSynchronize() != cudaSuccess) st = fail(WW_ERR_CUDA, "selftest sync");
     if (st == WW_OK) {
