@@ -376,6 +376,79 @@ def run_gradient(args):
     return out
 
 
+BATCH_METRIC = "Jacobian columns/s over a batch of 32 uneven shots (N 256..4096, 8..64 columns each)"
+
+
+def run_batch(args):
+    """--mode batch: one step = shoot_jacobian_batch over the 32 seeded shots of
+    the uneven batch (each shot's step count capped at --batch-step-cap at its
+    own dt); the per-shot loop (shoot_jacobian on each context in turn) on the
+    same shots is timed beside it, and the two must agree bitwise."""
+    import torch
+    import paper_1210_5672_gb300 as ww
+
+    rank, ws, local = dist_init()
+    shots = W.uneven_shots(n_shots=32, seed=rank, step_cap=args.batch_step_cap)
+    prec = ww.WW_MIXED if args.form == "mixed" else ww.WW_FP64
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ctxs = [ww.Context(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps, precision=prec) for w, _ in shots]
+    cs = [torch.tensor(c, dtype=torch.float64, device=dev) for _, c in shots]
+    outs = [ctx.empty_outputs() for ctx in ctxs]
+    cols = sum(w.n + 1 for w, _ in shots)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)
+
+    def batch():
+        ww.shoot_jacobian_batch(ctxs, cs, [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
+
+    for _ in range(args.warmup):
+        batch()
+    torch.cuda.synchronize()
+    times = []
+    barrier(ws)
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush_l2(flush)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            batch()                      # returns when every shot is done (device synchronised)
+            times.append(time.perf_counter() - t0)
+    barrier(ws)
+    clocks = clk.summary()
+    t_step, value = replica_rate(sum(times) / len(times), ws, cols)
+    got = [(o[0].cpu(), o[1].cpu(), o[2].cpu()) for o in outs]
+    # the per-shot loop on the same contexts
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for ctx, c, o in zip(ctxs, cs, outs):
+        ww.shoot_jacobian(ctx, c, o[0], o[1], o[2])
+    torch.cuda.synchronize()
+    t_loop = time.perf_counter() - t0
+    same = all(torch.equal(a[0], o[0].cpu()) and torch.equal(a[1], o[1].cpu()) and torch.equal(a[2], o[2].cpu())
+               for a, o in zip(got, outs))
+    launches = sum(ctx.stats()["launches"] for ctx in ctxs) * args.steps
+    for ctx in ctxs:
+        ctx.close()
+    if rank != 0:
+        return None
+    return {
+        "metric": BATCH_METRIC, "value": value, "unit": "Jacobian columns/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.form == "fp64" else "f64+f32/bf16-tensor",
+        "data": "synthetic (seeded uneven-batch recipe)",
+        "config": {"workload": f"uneven batch of 32 shots, steps capped at {args.batch_step_cap} (each shot's own dt)",
+                   "shots": [w.name + f"_steps{w.steps}" for w, _ in shots], "columns": cols, "form": args.form,
+                   "mode": "batch", "timing": "host wall clock around the batch call (it synchronises)",
+                   "l2": "flushed between timed steps (512 MB write)"},
+        "e2e": None,
+        "roofline": None,
+        "per_shot_loop": {"seconds": t_loop, "columns_per_s": cols / t_loop, "batch_speedup": t_loop / t_step,
+                          "bitwise_equal_to_batch": same},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+
+
 def cpu_baseline_gradient(w, c):
     """The oracle's discrete adjoint on one RK4 step of the workload (the full
     run's dt), scaled to the full step count."""
@@ -456,7 +529,9 @@ def main():
     ap.add_argument("--workload", default=None, choices=sorted(W.ALL),
                     help=f"default {W.LARGE.name} (jacobian mode), {W.SHALLOW.name} (gradient mode)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="jacobian", choices=["jacobian", "gradient"],
+    ap.add_argument("--batch-step-cap", type=int, default=64,
+                    help="batch mode: RK4 steps per shot at most (T scaled, each shot's dt kept)")
+    ap.add_argument("--mode", default="jacobian", choices=["jacobian", "gradient", "batch"],
                     help="gradient: objective_and_grad by the discrete adjoint (default workload "
                          "N1024_n256_steps2048_h0.05)")
     ap.add_argument("--rk-steps", type=int, default=0,
@@ -469,7 +544,7 @@ def main():
     else:
         from paper_1210_5672_gb300 import build as B
         B.build()
-        out = run_gradient(args) if args.mode == "gradient" else run_ours(args)
+        out = {"gradient": run_gradient, "batch": run_batch}.get(args.mode, run_ours)(args)
     if out is not None:
         print(json.dumps(out), flush=True)
 

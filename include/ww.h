@@ -148,6 +148,20 @@ int shoot_jacobian(ww_ctx *ctx, const double *c, double *r, double *J, double *f
  * copies r, J, f out (pinned or pageable host memory). */
 int shoot_jacobian_host(ww_ctx *ctx, const double *c, double *r, double *J, double *f);
 
+/* shoot_jacobian_batch -- nshots independent shots (each its own context,
+ * problem size and step count) in one call, run concurrently on one GPU:
+ * every shot replays its own captured step graph on its own stream, and the
+ * replays of all shots are issued in turn, so small shots fill the SMs that a
+ * large one leaves idle (the paper runs 2-3 jobs per GPU for the same reason,
+ * Sec. 4.6).  ctx[i], cvec[i], r[i], J[i], f[i] as for shoot_jacobian (device
+ * arrays of shot i's sizes).  The contexts must be distinct and each on a
+ * stream of its own (ww_create gives one; the legacy default stream is
+ * rejected with WW_ERR_ARG).  Returns when every shot is done; the first
+ * failing shot's status is returned, its message naming the shot.  Results
+ * are bitwise those of shoot_jacobian on each context. */
+int shoot_jacobian_batch(ww_ctx *const *ctx, int nshots, const double *const *cvec, double *const *r,
+                         double *const *J, double *const *f);
+
 /* objective_and_grad -- Sec. 3.2 Eqs. (adj), (nabla:f), App. C Eq. (adj2):
  * f (device, 1 double) and its gradient with respect to c (device, n+1
  * doubles; grad[0] = d f / d T) by the DISCRETE adjoint: one forward pass of

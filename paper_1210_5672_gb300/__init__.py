@@ -8,7 +8,8 @@ step of the method runs in Python; if the compiled library is missing the
 import of any entry point raises.
 
 Names follow the C ABI: ``dtn_setup``, ``dtn_apply``, ``shoot``,
-``shoot_jacobian``, ``shoot_jacobian_host``, ``objective_and_grad``, plus the
+``shoot_jacobian``, ``shoot_jacobian_host``, ``shoot_jacobian_batch``,
+``objective_and_grad``, plus the
 ``Context`` that owns the device workspace and ``ShootingObjective``, a
 ``torch.autograd.Function`` around ``objective_and_grad``.
 
@@ -35,7 +36,7 @@ ERRORS = {
 WW_FP64, WW_MIXED = 0, 1
 EXPORTS = ("ww_create", "ww_destroy", "ww_set_stream", "ww_get_stats", "ww_last_error", "ww_set_timing",
            "ww_get_timing", "dtn_setup", "dtn_apply", "shoot", "shoot_jacobian", "shoot_jacobian_host",
-           "objective_and_grad", "dtn_apply_static", "ww_selftest_f32gemm", "ww_selftest_ozaki")
+           "shoot_jacobian_batch", "objective_and_grad", "dtn_apply_static", "ww_selftest_f32gemm", "ww_selftest_ozaki")
 STATIC_MAX_N, STATIC_MAX_RHS = 256, 64
 PHASES = ("assembly", "factor", "solve", "gapply", "colrhs", "gamma", "base", "gkernel")
 
@@ -89,6 +90,8 @@ def lib():
             "shoot": (I, [V, V, V, V]),
             "shoot_jacobian": (I, [V, V, V, V, V]),
             "shoot_jacobian_host": (I, [V, V, V, V, V]),
+            "shoot_jacobian_batch": (I, [C.POINTER(V), I, C.POINTER(V), C.POINTER(V), C.POINTER(V),
+                                         C.POINTER(V)]),
             "objective_and_grad": (I, [V, V, V, V]),
             "dtn_apply_static": (I, [V, V, I, I, D, V, V]),
             "ww_selftest_f32gemm": (I, [V, V, I, I, I, C.POINTER(D)]),
@@ -229,6 +232,21 @@ def shoot_jacobian_host(ctx: Context, c: np.ndarray, r: np.ndarray, J: np.ndarra
     """Host-array variant; J is (n+1, N) float64 (= N x (n+1) column-major)."""
     _check(lib().shoot_jacobian_host(ctx.handle, _hptr(c, ctx.n + 1, "c"), _hptr(r, ctx.N, "r"),
                                      _hptr(J, ctx.N * (ctx.n + 1), "J"), _hptr(f, 1, "f")))
+
+
+def shoot_jacobian_batch(ctxs, cs, rs, Js, fs):
+    """Independent shots run concurrently (one stream each): lists of contexts
+    and of each shot's c, r, J (n+1, N) and f CUDA float64 tensors."""
+    n = len(ctxs)
+    if not (len(cs) == len(rs) == len(Js) == len(fs) == n):
+        raise ValueError("shoot_jacobian_batch: one c, r, J, f per context")
+    arr = C.c_void_p * max(n, 1)
+    hs = arr(*[x.handle for x in ctxs])
+    cp = arr(*[_dptr(c, x.n + 1, "c") for x, c in zip(ctxs, cs)])
+    rp = arr(*[_dptr(r, x.N, "r") for x, r in zip(ctxs, rs)])
+    Jp = arr(*[_dptr(J, x.N * (x.n + 1), "J") for x, J in zip(ctxs, Js)])
+    fp = arr(*[_dptr(f, 1, "f") for x, f in zip(ctxs, fs)])
+    _check(lib().shoot_jacobian_batch(hs, n, cp, rp, Jp, fp))
 
 
 def objective_and_grad(ctx: Context, c, f, grad):

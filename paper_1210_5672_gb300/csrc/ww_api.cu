@@ -866,6 +866,69 @@ int shoot_jacobian_host(ww_ctx *ctx, const double *cvec, double *r, double *J, d
     return WW_OK;
 }
 
+int shoot_jacobian_batch(ww_ctx *const *ctx, int nshots, const double *const *cvec, double *const *r,
+                         double *const *J, double *const *f) {
+    if (nshots < 0 || (nshots > 0 && (!ctx || !cvec || !r || !J || !f)))
+        return fail(WW_ERR_ARG, "shoot_jacobian_batch: NULL argument");
+    for (int i = 0; i < nshots; ++i) {
+        if (!ctx[i] || !cvec[i] || !r[i] || !J[i] || !f[i])
+            return fail(WW_ERR_ARG, "shoot_jacobian_batch: NULL entry for shot " + std::to_string(i));
+        if (owner(ctx[i])->c.stream == nullptr)
+            return fail(WW_ERR_ARG, "shoot_jacobian_batch: shot " + std::to_string(i) +
+                                        " runs on the legacy default stream (the shots need streams of their own)");
+        for (int k = 0; k < i; ++k)
+            if (ctx[k] == ctx[i] || owner(ctx[k])->c.stream == owner(ctx[i])->c.stream)
+                return fail(WW_ERR_ARG, "shoot_jacobian_batch: shots " + std::to_string(k) + " and " +
+                                            std::to_string(i) + " share a context or a stream");
+    }
+    // the batch replays each shot's untimed step program; timing flags come back on return
+    struct TimingGuard {
+        std::vector<std::pair<Owned *, bool>> saved;
+        ~TimingGuard() {
+            for (auto &p : saved) p.first->timing = p.second;
+        }
+    } guard;
+    for (int i = 0; i < nshots; ++i) {
+        Owned *o = owner(ctx[i]);
+        guard.saved.emplace_back(o, o->timing);
+        o->timing = false;
+    }
+    // 1. per shot: inputs, initial data, its step graph (captured on first use)
+    int max_steps = 0;
+    for (int i = 0; i < nshots; ++i) {
+        Owned *o = owner(ctx[i]);
+        Ctx *c = &o->c;
+        c->one_col = false;
+        WW_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+        WW_CUDA_TRY(cudaMemcpyAsync(o->cbuf, cvec[i], sizeof(double) * (c->n + 1), cudaMemcpyDeviceToDevice,
+                                    c->stream));
+        WW_TRY(run_prologue(o, 1));
+        WW_TRY(build_step_graph(o, 1));
+        max_steps = c->steps > max_steps ? c->steps : max_steps;
+    }
+    // 2. the RK steps of all shots interleaved, one graph launch per shot in turn:
+    //    every stream always has work queued, so the shots share the GPU
+    for (int s = 0; s < max_steps; ++s)
+        for (int i = 0; i < nshots; ++i) {
+            Owned *o = owner(ctx[i]);
+            if (s < o->c.steps) WW_CUDA_TRY(cudaGraphLaunch(o->graphs[1][0].exec, o->c.stream));
+        }
+    // 3. outputs and each shot's status
+    for (int i = 0; i < nshots; ++i) {
+        Owned *o = owner(ctx[i]);
+        Ctx *c = &o->c;
+        WW_TRY(launch_outputs(c, r[i], J[i], f[i], 1));
+        c->stats.stages = 4 * c->steps;
+        c->stats.launches = (long long)o->prologue[1].nkern + (long long)c->steps * o->graphs[1][0].nkern + 2;
+        c->dtn_ready = false;
+    }
+    for (int i = 0; i < nshots; ++i) {
+        const int st = check_status(&owner(ctx[i])->c);
+        if (st != WW_OK) return fail(st, "shot " + std::to_string(i) + ": " + ww_last_error());
+    }
+    return WW_OK;
+}
+
 int objective_and_grad(ww_ctx *ctx, const double *cvec, double *f, double *grad) {
     if (!ctx || !cvec || !f || !grad) return fail(WW_ERR_ARG, "objective_and_grad: NULL argument");
     Owned *o = owner(ctx);

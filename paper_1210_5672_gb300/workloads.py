@@ -18,7 +18,10 @@ shapes stand in for the paper's standing-wave runs):
 * if the depth is finite and min eta_0 < hbar / 2 the draw is repeated with
   seed + 1, seed + 2, ... (the seed actually used is returned);
 * T from the linear dispersion relation at k = 1, omega^2 = (g + tau) tanh(h)
-  (Eq. lin:soln), or omega^2 = g + tau in deep water.
+  (Eq. lin:soln), or omega^2 = g + tau in deep water;
+* the uneven batch (`uneven_shots`): 32 independent shots with N in
+  {256, ..., 4096}, 8 to 64 columns, h ~ U(0.1, 2), tau in {0, 0.05},
+  c_1 ~ U(0.01, 0.5), steps = max(N/2, (T/4) omega(0.9 N/2) / 2.5).
 """
 from __future__ import annotations
 
@@ -94,6 +97,46 @@ def coefficients(w: Workload, seed: int | None = None, max_redraw: int = 1000):
         c[1:] = ck
         return c, s
     raise RuntimeError(f"no admissible draw for {w.name} within {max_redraw} seeds")
+
+
+def stable_steps(N: int, g: float, tau: float, h: float, T: float) -> int:
+    """Step count of a shot of the uneven batch: max(N/2, ceil((T/4) omega(k_eff) / 2.5)),
+    k_eff = 0.9 N/2, omega^2 = (g k + tau k^3) tanh(k h) (RK4's imaginary-axis
+    stability limit is ~2.83)."""
+    k = 0.9 * N / 2
+    om = math.sqrt((g * k + tau * k**3) * (1.0 if math.isinf(h) else math.tanh(k * h)))
+    return max(N // 2, math.ceil(0.25 * T * om / 2.5))
+
+
+def uneven_shots(n_shots: int = 32, seed: int = 0, step_cap: int | None = None,
+                 sizes=(256, 512, 1024, 2048, 4096)):
+    """The batch of independent shots of uneven size: N drawn from `sizes`,
+    n + 1 columns in [8, 64], h ~ U(0.1, 2), tau in {0, 0.05}, c_1 ~ U(0.01, 0.5)
+    (c_k = c_1^k u_k), steps by `stable_steps`.  A shot whose c_1 would put the
+    surface near the bottom (c_1 >= 0.45 h) draws its depth and c_1 again; the
+    coefficient draw then follows `coefficients` (its own redraw rule).
+    step_cap bounds the step count (T scaled so dt stays that of the full shot),
+    for measurements that must end in minutes.  Returns [(Workload, c)]."""
+    rng = np.random.default_rng(seed)
+    shots = []
+    for i in range(n_shots):
+        N = int(rng.choice(sizes))
+        n = int(rng.integers(7, 64))          # n + 1 columns in [8, 64]
+        tau = float(rng.choice([0.0, 0.05]))
+        while True:
+            h = float(rng.uniform(0.1, 2.0))
+            amp = float(rng.uniform(0.01, 0.5))
+            if amp < 0.45 * h:
+                break
+        w = Workload(f"shot{i}_N{N}_n{n}_h{h:.3f}_tau{tau}", N=N, n=n, steps=1, tau=tau, h=h, amp=amp,
+                     seed=1000 * (seed + 1) + i)
+        c, _ = coefficients(w)
+        steps = stable_steps(N, w.g, tau, h, c[0])
+        if step_cap is not None and steps > step_cap:
+            c[0] *= step_cap / steps
+            steps = step_cap
+        shots.append((shrink(w, steps=steps, name=w.name), c))
+    return shots
 
 
 def shrink(w: Workload, N: int | None = None, n: int | None = None, steps: int | None = None,

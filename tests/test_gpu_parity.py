@@ -261,6 +261,43 @@ def test_adjoint_full_size_two_steps(ww, wl, precision):
 _ADJ_ORACLE = {}
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_of_uneven_shots_matches_single_shots(ww, precision):
+    """shoot_jacobian_batch: independent shots of uneven size (the uneven-batch
+    recipe at N = 128..512, 8 steps of each shot's own dt) run concurrently give
+    bitwise the results of shoot_jacobian on each context; one shot is also
+    checked against the oracle."""
+    shots = W.uneven_shots(n_shots=6, seed=5, step_cap=8, sizes=(128, 256, 512))
+    assert len({w.N for w, _ in shots}) > 1 and len({w.n for w, _ in shots}) > 1
+    ctxs = [ww.Context(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps, precision=precision) for w, _ in shots]
+    try:
+        cs = [dev(c) for _, c in shots]
+        single = []
+        for ctx, c in zip(ctxs, cs):
+            r, J, f = ctx.empty_outputs()
+            ww.shoot_jacobian(ctx, c, r, J, f)
+            single.append((r.cpu().numpy(), J.cpu().numpy(), f.item()))
+        outs = [ctx.empty_outputs() for ctx in ctxs]
+        ww.shoot_jacobian_batch(ctxs, cs, [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
+        for (r0, J0, f0), (r, J, f) in zip(single, outs):
+            assert np.array_equal(r.cpu().numpy(), r0) and np.array_equal(J.cpu().numpy(), J0) and f.item() == f0
+        with pytest.raises(ww.WWError) as ei:   # a context may appear once
+            dup = [outs[0], outs[1], outs[0]]
+            ww.shoot_jacobian_batch(ctxs[:2] + ctxs[:1], cs[:2] + cs[:1], [o[0] for o in dup],
+                                    [o[1] for o in dup], [o[2] for o in dup])
+        assert ei.value.code == -1
+    finally:
+        for ctx in ctxs:
+            ctx.close()
+    i = min(range(len(shots)), key=lambda k: shots[k][0].N)
+    w, c = shots[i]
+    prob, _ = O.make_problem(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps)
+    r0, J0, f0 = O.shoot_jacobian(prob, c)
+    r, J, f = outs[i]
+    assert rel(r.cpu().numpy(), r0) < TOL and abs(f.item() - f0) / f0 < TOL
+    assert col_rel(J.cpu().numpy().T, J0) < TOL
+
+
 def test_host_entry_point_matches_device(ww):
     w = W.shrink(W.MEDIUM, N=128, n=10, steps=4)
     c, _ = W.coefficients(w)
