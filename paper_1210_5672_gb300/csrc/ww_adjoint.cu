@@ -135,8 +135,12 @@ __global__ void __launch_bounds__(AJ_THREADS) k_adj_begin_step(double *lam, doub
     if (threadIdx.x == 0) *step = *step - 1;
 }
 
-__global__ void k_adj_fetch(const double *__restrict__ rec, const int *step, int st, int N, double *eta) {
-    const double *r = stage_rec(rec, step, st, N);
+// the surface of record 4 step + off (off = -1: the last stage of the step before);
+// past the first record there is nothing to fetch and eta keeps its values
+__global__ void k_adj_fetch(const double *__restrict__ rec, const int *step, int off, int N, double *eta) {
+    const long idx = 4L * *step + off;
+    if (idx < 0) return;
+    const double *r = rec + (size_t)idx * ADJ_REC * N;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) eta[j] = r[j];
 }
 
@@ -405,8 +409,8 @@ int launch_adj_begin_step(Ctx *c, AdjWs *a, const double *cvec) {
     return WW_OK;
 }
 
-int launch_adj_fetch(Ctx *c, AdjWs *a, int st) {
-    k_adj_fetch<<<grid_for(c->N), 256, 0, c->stream>>>(a->rec, a->step, st, c->N, a->eta);
+int launch_adj_fetch(Ctx *c, AdjWs *a, int off) {
+    k_adj_fetch<<<grid_for(c->N), 256, 0, c->stream>>>(a->rec, a->step, off, c->N, a->eta);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }

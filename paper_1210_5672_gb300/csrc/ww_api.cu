@@ -472,7 +472,98 @@ int ensure_adjoint(Owned *o) {
     WW_TRY(dalloc_n(o, &a.psil, N));
     WW_TRY(dalloc_n(o, &a.gT, 1));
     WW_TRY(dalloc_n(o, &a.step, 1));
+    if (c->precision == WW_MIXED) {   // the overlapped sweep's second operand copies
+        WW_TRY(dalloc_n(o, &a.A2, N * N));
+        WW_TRY(dalloc_n(o, &a.G2, N * N));
+        WW_TRY(dalloc_n(o, &a.X2, N * N));
+    }
     return prepare_adjoint(c->N);
+}
+
+// The backward sweep's two chains (MIXED on a stream of its own): the DtN setup
+// of a stage (its surface, geometry, A^T and G^T, the inverse update) needs
+// only the recorded trajectory, not the adjoint vector, so it runs one stage
+// ahead on the side stream while the adjoint of the stage before runs on the
+// caller's.  A^T, G^T and the FP32 inverse alternate between two copies by
+// stage parity; the setup of stage k waits for the adjoint of stage k + 2
+// (the last reader of that copy).
+bool adj_overlapped(const Owned *o) {
+    const Ctx *c = &o->c;
+    return c->precision == WW_MIXED && c->stream != nullptr && o->side_stream != nullptr && o->adj.A2 != nullptr;
+}
+
+struct AdjOperands {
+    double *A[2], *G[2];
+    float *X[2];
+};
+
+void adj_select(Owned *o, const AdjOperands &ops, int p) {
+    Ctx *c = &o->c;
+    c->A = ops.A[p];
+    c->G = ops.G[p];
+    mixed_set_inverse(c, ops.X[p]);
+}
+
+// DtN setup of the stage whose record is 4 step + off, into operand copy p
+int adj_setup(Owned *o, const AdjOperands &ops, int off, int p, bool fresh) {
+    Ctx *c = &o->c;
+    adj_select(o, ops, p);
+    WW_TRY(launch_adj_fetch(c, &o->adj, off));
+    WW_TRY(launch_base_geometry(c, o->adj.eta, o->adj.eta, 0));
+    WW_TRY(launch_assemble(c));                  // A^T, G^T
+    return factor(c, fresh ? 1 : 0, 1);
+}
+
+// the adjoint of stage k of the current step, reading operand copy k & 1
+int adj_stage(Owned *o, const AdjOperands &ops, int k) {
+    Ctx *c = &o->c;
+    AdjWs *a = &o->adj;
+    adj_select(o, ops, k & 1);
+    WW_TRY(launch_adj_local(c, a, k, o->cbuf));
+    WW_TRY(gemv_narrow(c->stream, c->N, 1, c->N, 1.0, c->G, c->N, a->chi, c->N, 0.0, a->y, c->N));   // G^T chi
+    WW_TRY(launch_adj_dtn(c, a));
+    WW_TRY(solve(c, c->M, 1));                   // A^{-T} D (1/2 H chi - G^T chi)
+    return launch_adj_update(c, a, k, o->cbuf);
+}
+
+// turn-around of the overlapped sweep: lambda, and the setup of the last stage
+// (record 4 steps - 1) with a fresh inverse
+int adj_turnaround_overlapped(Owned *o, const AdjOperands &ops) {
+    Ctx *c = &o->c;
+    select_parity(c, 0);
+    WW_TRY(launch_adj_init(c, &o->adj));        // step = steps
+    return adj_setup(o, ops, -1, 1, true);
+}
+
+// one backward step: adjoints of stages 3..0 on the caller's stream, setups of
+// stages 2..0 and of stage 3 of the step before on the side stream
+int adj_backward_step_overlapped(Owned *o, const AdjOperands &ops) {
+    Ctx *c = &o->c;
+    cudaStream_t main_s = c->stream, side = o->side_stream;
+    select_parity(c, 0);
+    int st = launch_adj_begin_step(c, &o->adj, o->cbuf);   // step -= 1
+    if (st != WW_OK) return st;
+    WW_CUDA_TRY(cudaEventRecord(o->ev_fork, main_s));
+    WW_CUDA_TRY(cudaStreamWaitEvent(side, o->ev_fork, 0));
+    for (int k = 3; k >= 0 && st == WW_OK; --k) {
+        // side: the setup of the next stage in backward order (k - 1, or stage 3 of the step
+        // before), after the adjoint of stage k + 1 released that operand copy
+        c->stream = side;
+        if (k <= 2) WW_CUDA_TRY(cudaStreamWaitEvent(side, o->ev_cols[k + 1], 0));
+        st = adj_setup(o, ops, k - 1, (k - 1) & 1, false);
+        if (st != WW_OK) break;
+        WW_CUDA_TRY(cudaEventRecord(k > 0 ? o->ev_base[k - 1] : o->ev_join, side));
+        // main: the adjoint of stage k (its setup ran in the step before when k = 3)
+        c->stream = main_s;
+        if (k <= 2) WW_CUDA_TRY(cudaStreamWaitEvent(main_s, o->ev_base[k], 0));
+        st = adj_stage(o, ops, k);
+        if (st != WW_OK) break;
+        WW_CUDA_TRY(cudaEventRecord(o->ev_cols[k], main_s));
+    }
+    c->stream = main_s;
+    if (st != WW_OK) return st;
+    WW_CUDA_TRY(cudaStreamWaitEvent(main_s, o->ev_join, 0));
+    return WW_OK;
 }
 
 // forward: one RK step of the base state, each stage recorded (its surface
@@ -571,8 +662,21 @@ int run_adjoint(Owned *o, const double *cvec, bool c_on_host, double *f, double 
     for (int s = 0; s < c->steps; ++s) WW_TRY(replay(o, o->adj_fwd, [&] { return adj_forward_step(o); }));
     WW_TRY(launch_outputs(c, o->rbuf, nullptr, f, 0));
     c->trans = 1;
-    WW_TRY(replay(o, o->adj_mid, [&] { return adj_turnaround(o); }));
-    for (int s = 0; s < c->steps; ++s) WW_TRY(replay(o, o->adj_bwd, [&] { return adj_backward_step(o); }));
+    if (adj_overlapped(o)) {
+        // operand copy 0 is the context's own A, G, X; copy 1 the sweep's second set
+        const AdjOperands ops{{c->A, o->adj.A2}, {c->G, o->adj.G2}, {mixed_set_inverse(c, nullptr), o->adj.X2}};
+        struct Back {
+            Owned *o;
+            AdjOperands ops;
+            ~Back() { adj_select(o, ops, 0); }
+        } back{o, ops};
+        WW_TRY(replay(o, o->adj_mid, [&] { return adj_turnaround_overlapped(o, ops); }));
+        for (int s = 0; s < c->steps; ++s)
+            WW_TRY(replay(o, o->adj_bwd, [&] { return adj_backward_step_overlapped(o, ops); }));
+    } else {
+        WW_TRY(replay(o, o->adj_mid, [&] { return adj_turnaround(o); }));
+        for (int s = 0; s < c->steps; ++s) WW_TRY(replay(o, o->adj_bwd, [&] { return adj_backward_step(o); }));
+    }
     c->trans = 0;
     WW_TRY(launch_adj_grad(c, &o->adj, grad));
     c->stats.stages = 8 * c->steps;

@@ -222,13 +222,17 @@ struct AdjWs {
     double *chi, *y, *etal, *psil;   // N each
     double *gT;               // 1: d f / d T
     int *step;                // 1: the RK step the record kernels address
+    // second copies of A^T, G^T and the FP32 inverse: with them the DtN setup of
+    // the next backward stage runs while the adjoint of this one still reads its own
+    double *A2, *G2;
+    float *X2;
 };
 int prepare_adjoint(int Nmax);                            // shared-memory limits of the sweep's FFT kernels
 int launch_adj_record_eta(Ctx *c, AdjWs *a, int st);      // forward: the stage surface (before its RK update)
 int launch_adj_record_fields(Ctx *c, AdjWs *a, int st);   // forward: phi_x, phi_y, w3, F; st == 3 advances the step
 int launch_adj_init(Ctx *c, AdjWs *a);                    // lambda = (0, phi(T/4)/N), dT = 0, step = steps
 int launch_adj_begin_step(Ctx *c, AdjWs *a, const double *cvec);   // step -= 1; filter lambda; kb = b dt/6 lambda
-int launch_adj_fetch(Ctx *c, AdjWs *a, int st);           // the stage surface into a->eta
+int launch_adj_fetch(Ctx *c, AdjWs *a, int off);          // surface of record 4 step + off into a->eta (none if < 0)
 int launch_adj_local(Ctx *c, AdjWs *a, int st, const double *cvec);   // chi, local terms, dT += kb.F/T
 int launch_adj_dtn(Ctx *c, AdjWs *a);                     // M[:,0] = D (1/2 H chi - G^T chi)
 int launch_adj_update(Ctx *c, AdjWs *a, int st, const double *cvec);  // lambda, kb of the previous stage
@@ -258,5 +262,6 @@ int mixed_setup(Ctx *c, int fresh, int update);      // after assembly: operands
 int mixed_read_stats(Ctx *c, double *ratio, double *nsres, int *iters /* [3]: max, sum, solves */, int *err);
 int mixed_solve(Ctx *c, double *B, int ncols);       // B <- A^{-1} B (refined)
 int mixed_apply_G(Ctx *c, int col0, int ncols, int part);   // Gout += G Gam (part 0 split, 1 product; FP64-accurate)
+float *mixed_set_inverse(Ctx *c, float *X);          // the FP32 inverse the updates write (NULL: query)
 
 }  // namespace ww

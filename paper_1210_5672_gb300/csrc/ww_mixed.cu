@@ -425,6 +425,14 @@ int mixed_apply_G(Ctx *c, int col0, int ncols, int part) {
                       m->err, nullptr);
 }
 
+// the FP32 approximate inverse the updates write and the one-column solves read:
+// point it at X (when not NULL) and return the previous pointer
+float *mixed_set_inverse(Ctx *c, float *X) {
+    float *old = c->mx->X;
+    if (X) c->mx->X = X;
+    return old;
+}
+
 // device diagnostics of the mixed path, read (and reset) after a call
 int mixed_read_stats(Ctx *c, double *ratio, double *nsres, int *iters, int *err) {
     Mixed *m = c->mx;
