@@ -204,6 +204,12 @@ int dtn_apply_static(const double *eta, const double *phi, int N, int nrhs, doub
 int ww_selftest_f32gemm(const double *A, const double *B, int M, int Nn, int K, double *max_rel);
 int ww_selftest_ozaki(const double *A, const double *B, int M, int Nn, int K, double *max_rel);
 
+/* Self-test of the assembly's reciprocal (Newton-Raphson from the FP32
+ * hardware reciprocal, two steps): *max_rel = max |r(d_i) - 1/d_i| / (1/d_i)
+ * over the n positive normal doubles d (device array), against the division
+ * operator.  Same conventions as the self-tests above. */
+int ww_selftest_recip(const double *d, int n, double *max_rel);
+
 #ifdef __cplusplus
 }
 #endif

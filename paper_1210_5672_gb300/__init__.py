@@ -36,7 +36,8 @@ ERRORS = {
 WW_FP64, WW_MIXED = 0, 1
 EXPORTS = ("ww_create", "ww_destroy", "ww_set_stream", "ww_get_stats", "ww_last_error", "ww_set_timing",
            "ww_get_timing", "dtn_setup", "dtn_apply", "shoot", "shoot_jacobian", "shoot_jacobian_host",
-           "shoot_jacobian_batch", "objective_and_grad", "dtn_apply_static", "ww_selftest_f32gemm", "ww_selftest_ozaki")
+           "shoot_jacobian_batch", "objective_and_grad", "dtn_apply_static", "ww_selftest_f32gemm", "ww_selftest_ozaki",
+           "ww_selftest_recip")
 STATIC_MAX_N, STATIC_MAX_RHS = 256, 64
 PHASES = ("assembly", "factor", "solve", "gapply", "colrhs", "gamma", "base", "gkernel")
 
@@ -96,6 +97,7 @@ def lib():
             "dtn_apply_static": (I, [V, V, I, I, D, V, V]),
             "ww_selftest_f32gemm": (I, [V, V, I, I, I, C.POINTER(D)]),
             "ww_selftest_ozaki": (I, [V, V, I, I, I, C.POINTER(D)]),
+            "ww_selftest_recip": (I, [V, I, C.POINTER(D)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -278,6 +280,14 @@ def selftest(kind: str, A, B) -> float:
     out = C.c_double(-1.0)
     fn = lib().ww_selftest_f32gemm if kind == "f32gemm" else lib().ww_selftest_ozaki
     _check(fn(_dptr(At, M * K, "A"), _dptr(Bt, K * Nn, "B"), M, Nn, K, C.byref(out)))
+    return out.value
+
+
+def selftest_recip(d) -> float:
+    """max relative difference of the assembly's reciprocal from 1/d over the
+    positive CUDA float64 tensor d."""
+    out = C.c_double(-1.0)
+    _check(lib().ww_selftest_recip(_dptr(d, d.numel(), "d"), int(d.numel()), C.byref(out)))
     return out.value
 
 

@@ -38,6 +38,18 @@ __device__ __forceinline__ double sinh_diff(double y, double ey, double eyi) {
     return 0.5 * (ey - eyi);
 }
 
+// 1/d for a positive normal d: Newton-Raphson, x <- x + x (1 - d x) (each step
+// squares the relative error; the residual 1 - d x is formed with one FMA),
+// started from the FP32 hardware reciprocal of d rounded to FP32 (relative
+// error ~2^-23): two steps reach the FP64 rounding level (within 1 ulp of the
+// division, tested against it by ww_selftest_recip).  Four FP64 operations
+// instead of a full FP64 division.
+__device__ __forceinline__ double recip_nr(double d) {
+    double x = (double)__frcp_rn((float)d);
+    x = fma(x, fma(-d, x, 1.0), x);
+    return fma(x, fma(-d, x, 1.0), x);
+}
+
 // cot((x + i y)/2) with cx = cos x, sx = sin x, ch = cosh y, sh = sinh y
 __device__ __forceinline__ double2 cot_half(double cx, double sx, double ch, double sh) {
     if (cx >= 0.0) {
@@ -117,11 +129,62 @@ __global__ void __launch_bounds__(ASM_TI) k_assemble(const double *__restrict__ 
 // evaluated entry by entry.
 constexpr int ST = 32;
 
+// Off-diagonal pair (i, j): the direct cotangent ct1 = cot((x + i y)/2),
+// y = eta_i - eta_j, and (finite depth) the image one ct2 = cot((x + i y')/2),
+// y' = eta_i + eta_j, share one reciprocal of the product of their denominators;
+// the 1/2 of the kernels and the 1/N of the rule are applied once at the end:
+//   K_ij ~ exj (ct1 + ct2).x + (ct1 - ct2).y,    G_ij ~ (ct1 - ct2).x - exi (ct1 - ct2).y - cot0
+//   K_ji ~ -[exi (ct1 + ct2).x + (ct1 + ct2).y], G_ji ~ (ct2 - ct1).x + exj (ct1 + ct2).y + cot0
+// (cot is odd: the (j, i) pair reuses both cotangents, see below).
+template <bool DEEP>
+__device__ __forceinline__ void pair_entries(double cx, double sx, double c0, double ei, double exi, double Ei,
+                                             double Eii, double ej, double exj, double Ej, double Eij, double &kij,
+                                             double &gij, double &kji, double &gji) {
+    const double y = ei - ej;
+    const double ey = Ei * Eij, eyi = Eii * Ej;
+    const double ch1 = 0.5 * (ey + eyi), sh1 = sinh_diff(y, ey, eyi);
+    double n1, d1, n2 = 0.0, d2 = 1.0, sh2 = 0.0;
+    if (cx >= 0.0) {
+        n1 = cx + ch1;
+        d1 = fma(sx, sx, sh1 * sh1);
+    } else {
+        n1 = 1.0;
+        d1 = ch1 - cx;
+    }
+    if (!DEEP) {
+        const double ep = Ei * Ej, epi = Eii * Eij;
+        const double ch2 = 0.5 * (ep + epi);
+        sh2 = 0.5 * (ep - epi);
+        if (cx >= 0.0) {
+            n2 = cx + ch2;
+            d2 = fma(sx, sx, sh2 * sh2);
+        } else {
+            n2 = 1.0;
+            d2 = ch2 - cx;
+        }
+    }
+    const double r = recip_nr(d1 * d2);
+    const double inv1 = n1 * d2 * r;
+    const double c1x = sx * inv1, c1y = -sh1 * inv1;
+    double c2x = 0.0, c2y = 0.0;
+    if (!DEEP) {
+        const double inv2 = n2 * d1 * r;
+        c2x = sx * inv2;
+        c2y = -sh2 * inv2;
+    }
+    const double a = c1x + c2x, b = c1y - c2y, c = c1x - c2x, d = c1y + c2y;
+    kij = fma(exj, a, b);
+    gij = fma(-exi, b, c) - c0;
+    kji = -fma(exi, a, d);
+    gji = fma(exj, d, -c) + c0;
+}
+
+template <bool DEEP>
 __global__ void __launch_bounds__(256) k_assemble_sym(const double *__restrict__ eta, const double *__restrict__ eta_x,
                                                       const double *__restrict__ eta_xx, const double *__restrict__ E,
                                                       const double *__restrict__ Einv,
                                                       const double *__restrict__ cs, const double *__restrict__ cot0,
-                                                      int N, int deep, int trans, double *A, double *G) {
+                                                      int N, int trans, double *A, double *G) {
     __shared__ double tA[ST][ST + 1], tG[ST][ST + 1];
     // triangular tile index -> (I, J), I <= J
     const int T = N / ST;
@@ -131,7 +194,7 @@ __global__ void __launch_bounds__(256) k_assemble_sym(const double *__restrict__
         ++I;
     }
     const int J = I + b;
-    const double invN = 1.0 / N;
+    const double h = 0.5 / N;   // the kernels' 1/2 and the rule's 1/N
     const int il = threadIdx.x & 31;
     const int i = I * ST + il;
     const double ei = eta[i], exi = eta_x[i], Ei = E[i], Eii = Einv[i];
@@ -139,33 +202,24 @@ __global__ void __launch_bounds__(256) k_assemble_sym(const double *__restrict__
         const int j = J * ST + jl;
         const double ej = eta[j], exj = eta_x[j], Ej = E[j], Eij = Einv[j];
         double kij, gij, kji, gji;
+        int m = i - j;
+        if (m < 0) m += N;
+        const double cx = cs[m], sx = cs[N + m];
         if (i == j) {
-            const double d = 0.5 / fma(exi, exi, 1.0);
-            kij = kji = -eta_xx[i] * d;
-            gij = gji = exi * eta_xx[i] * d;
+            // diagonal limits of the direct kernels, zeta''/(2 zeta') (doubled: h carries 1/2)
+            const double dd = 1.0 / fma(exi, exi, 1.0);
+            kij = -eta_xx[i] * dd;
+            gij = exi * eta_xx[i] * dd;
+            if (!DEEP) {
+                const double ep = Ei * Ej, epi = Eii * Eij;
+                const double2 ct = cot_half(cx, sx, 0.5 * (ep + epi), 0.5 * (ep - epi));
+                kij -= fma(-exj, ct.x, ct.y);
+                gij -= fma(-exi, ct.y, ct.x);
+            }
+            kji = kij;
+            gji = gij;
         } else {
-            int m = i - j;
-            if (m < 0) m += N;
-            const double cx = cs[m], sx = cs[N + m];
-            const double y = ei - ej;
-            const double ey = Ei * Eij, eyi = Eii * Ej;
-            const double2 ct = cot_half(cx, sx, 0.5 * (ey + eyi), sinh_diff(y, ey, eyi));
-            const double c0 = cot0[m];
-            kij = 0.5 * fma(exj, ct.x, ct.y);
-            gij = 0.5 * (fma(-exi, ct.y, ct.x) - c0);
-            kji = -0.5 * fma(exi, ct.x, ct.y);
-            gji = -0.5 * (fma(-exj, ct.y, ct.x) - c0);
-        }
-        if (!deep) {
-            int m = i - j;
-            if (m < 0) m += N;
-            const double cx = cs[m], sx = cs[N + m];
-            const double ep = Ei * Ej, epi = Eii * Eij;
-            const double2 ct = cot_half(cx, sx, 0.5 * (ep + epi), 0.5 * (ep - epi));
-            kij += -0.5 * fma(-exj, ct.x, ct.y);
-            gij += -0.5 * fma(-exi, ct.y, ct.x);
-            kji += -0.5 * fma(exi, ct.x, ct.y);
-            gji += 0.5 * fma(exj, ct.y, ct.x);
+            pair_entries<DEEP>(cx, sx, cot0[m], ei, exi, Ei, Eii, ej, exj, Ej, Eij, kij, gij, kji, gji);
         }
         if (trans) {   // entry (i, j) of A^T is entry (j, i) of A
             const double tk = kij, tg = gij;
@@ -175,10 +229,10 @@ __global__ void __launch_bounds__(256) k_assemble_sym(const double *__restrict__
             gji = tg;
         }
         const size_t idx = (size_t)j * N + i;
-        A[idx] = kij * invN + (i == j ? 0.5 : 0.0);
-        G[idx] = gij * invN;
-        tA[jl][il] = kji * invN + (i == j ? 0.5 : 0.0);
-        tG[jl][il] = gji * invN;
+        A[idx] = fma(h, kij, i == j ? 0.5 : 0.0);
+        G[idx] = h * gij;
+        tA[jl][il] = fma(h, kji, i == j ? 0.5 : 0.0);
+        tG[jl][il] = h * gji;
     }
     if (I == J) return;   // the diagonal tile is complete (uniform branch: no barrier skipped unevenly)
     __syncthreads();
@@ -196,9 +250,9 @@ __global__ void __launch_bounds__(256) k_assemble_sym(const double *__restrict__
 int launch_assemble(Ctx *c) {
     if (c->N % ST == 0) {
         const int T = c->N / ST;
-        k_assemble_sym<<<T * (T + 1) / 2, 256, 0, c->stream>>>(c->eta, c->eta_x, c->eta_xx, c->E, c->Einv, c->cs,
-                                                              c->cs + 2 * c->N, c->N, c->deep ? 1 : 0, c->trans, c->A,
-                                                              c->G);
+        auto kern = c->deep ? k_assemble_sym<true> : k_assemble_sym<false>;
+        kern<<<T * (T + 1) / 2, 256, 0, c->stream>>>(c->eta, c->eta_x, c->eta_xx, c->E, c->Einv, c->cs,
+                                                     c->cs + 2 * c->N, c->N, c->trans, c->A, c->G);
         WW_CUDA_TRY(cudaGetLastError());
         return WW_OK;
     }
@@ -209,4 +263,36 @@ int launch_assemble(Ctx *c) {
     return WW_OK;
 }
 
+namespace {
+__global__ void k_recip_test(const double *d, int n, double *maxrel) {
+    __shared__ double red[8];
+    double m = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const double q = 1.0 / d[k];
+        m = fmax(m, fabs(recip_nr(d[k]) - q) / q);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = fmax(m, red[w]);
+        *maxrel = fmax(m, red[0]);
+    }
+}
+}  // namespace
+
 }  // namespace ww
+
+// self-test (declared in ww.h): max |recip_nr(d) - 1/d| / (1/d) over the n
+// positive device doubles d (the assembly's reciprocal against the division)
+extern "C" int ww_selftest_recip(const double *d, int n, double *max_rel) {
+    using namespace ww;
+    if (!d || n <= 0 || !max_rel) return fail(WW_ERR_ARG, "ww_selftest_recip: bad argument");
+    double *m = nullptr;
+    if (cudaMalloc(&m, sizeof(double)) != cudaSuccess) return fail(WW_ERR_ALLOC, "selftest alloc");
+    k_recip_test<<<1, 256>>>(d, n, m);
+    cudaError_t e = cudaMemcpy(max_rel, m, sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(m);
+    if (e != cudaSuccess) return fail(WW_ERR_CUDA, std::string("ww_selftest_recip: ") + cudaGetErrorString(e));
+    return WW_OK;
+}

@@ -47,3 +47,14 @@ def test_digit_product_is_fp64_accurate(ww, M, Nn, K):
     # kernel matrices it is far smaller relative to the result, whose row
     # maxima are O(1/N) of the operator norm.
     assert err < 1.5e-13, err
+
+
+def test_assembly_reciprocal_within_one_ulp(ww):
+    """The Newton-Raphson reciprocal of the kernel assembly against the division
+    operator, over 16 decades of positive normal doubles (the denominators of
+    the cotangent quotients lie between ~1e-7 and ~1e5)."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(7)
+    d = torch.pow(10.0, torch.empty(1 << 16, dtype=torch.float64, device="cuda").uniform_(-8, 8, generator=g))
+    d = torch.cat([d, torch.tensor([1.0, 2.0, 0.5, 3.0, 1e-7, 1e5], dtype=torch.float64, device="cuda")])
+    assert ww.selftest_recip(d) <= 2.3e-16   # one ulp of the quotient
