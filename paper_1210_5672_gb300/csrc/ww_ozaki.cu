@@ -207,11 +207,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(acc_empty);
         }
+        // column maxima of the residual: reduced over the warp's 32 rows first (one
+        // atomic per warp and column instead of one per element) when all 32 rows exist
+        const bool full_warp = __all_sync(0xffffffffu, row < M);
         if (row < M) {
             const double si = sa[row];
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-                const int col = n0 + chalf * 32 + j;
+                const int col = n0 + chalf * 32 + j;   // the same for every lane of the warp
                 if (col < Nn) {
                     const double val = si * sb[col] * fma((double)hi[j], 0x1p-26, (double)lo[j] * 0x1p-54);
                     const size_t ic = (size_t)col * out.ldc + row;
@@ -228,8 +231,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                             out.rslc[(size_t)col * M + row] = b0;
                             out.rslc[((size_t)Nn + col) * M + row] = __float2bfloat16_rn(v);
                         }
-                        if (out.colmax)
-                            atomicMax(&out.colmax[col], (unsigned long long)__double_as_longlong(fabs(r)));
+                        if (out.colmax) {
+                            if (full_warp) {
+                                double a = fabs(r);
+#pragma unroll
+                                for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+                                if (lane == 0)
+                                    atomicMax(&out.colmax[col], (unsigned long long)__double_as_longlong(a));
+                            } else {
+                                atomicMax(&out.colmax[col], (unsigned long long)__double_as_longlong(fabs(r)));
+                            }
+                        }
                     }
                 }
             }

@@ -52,6 +52,9 @@ class Workload:
 SMALL = Workload("N64_n12_steps64_h1", N=64, n=12, steps=64, amp=0.01)
 MEDIUM = Workload("N512_n128_steps512_h1", N=512, n=128, steps=512, amp=0.2)
 LARGE = Workload("N2048_n512_steps1024_h1", N=2048, n=512, steps=1024, amp=0.4)
+# the gradient workloads.  The shallow one (a wave as tall as the depth) has its
+# trough reach the bottom before T/8: only its first 512 steps (T/16 at the
+# full dt) can be evaluated; the deep-water one with surface tension runs in full.
 SHALLOW = Workload("N1024_n256_steps2048_h0.05", N=1024, n=256, steps=2048, h=0.05,
                    amp=0.05, law="decay")
 DEEP_TENSION = Workload("N1024_n256_steps2048_deep_tau0.1", N=1024, n=256, steps=2048,
