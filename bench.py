@@ -146,7 +146,11 @@ def flush_l2(buf):
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the timed product
 # kernel, from the ncu captures summarised under profiles/ (None: not captured
 # since the kernel last changed).
-TRAFFIC_BYTES = {"mixed": None, "fp64": None}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# roofline kernel, from one ncu capture of the current k_ozaki's column G-apply
+# launch on the N = 2048 workload; other workloads and forms have no capture of
+# their current kernel: null.
+TRAFFIC_BYTES = {("mixed", "N2048_n512_steps1024_h1"): 85.35e6}
 
 # slice pairs (p, q) with p + q <= 6 of the 7 x 7 integer digits: 28 bf16 GEMMs
 OZAKI_PAIRS = 28
@@ -166,14 +170,14 @@ def roofline_for(form, timing, w, pk):
     if form == "fp64":
         achieved = fp64_flops / dur / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES["fp64"], "kernel": "k_dgemm",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES.get(("fp64", w.name)), "kernel": "k_dgemm",
                 "launch_ms": dur * 1e3,
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"}
     peak = pk.get("bf16_tflops_sustained") or 1700.0
     src = "of measured (bf16_tflops_sustained)" if pk.get("bf16_tflops_sustained") else "of fallback (sustained)"
     achieved = OZAKI_PAIRS * fp64_flops / dur / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": TRAFFIC_BYTES["mixed"], "kernel": "k_ozaki",
+            "traffic": TRAFFIC_BYTES.get(("mixed", w.name)), "kernel": "k_ozaki",
             "launch_ms": dur * 1e3, "fp64_equivalent_tflops": fp64_flops / dur / 1e12,
             "work": f"{OZAKI_PAIRS} bf16 digit-pair GEMMs of {N} x {nc} x {N}",
             "peak_source": src}
