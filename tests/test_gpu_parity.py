@@ -261,6 +261,35 @@ def test_adjoint_full_size_two_steps(ww, wl, precision):
 _ADJ_ORACLE = {}
 
 
+def test_adjoint_two_chain_sweep_matches_one_chain_sweep(ww):
+    """The mixed form's reverse sweep on the context's own stream runs as two
+    chains (each stage's DtN setup one stage ahead, operands double-buffered by
+    stage parity); on the legacy default stream it runs as one chain without
+    graphs.  Both refine every solve to 1e-13, so the gradients agree to that
+    level (their approximate inverses start from different surfaces), and both
+    match the oracle.  N = 512 takes the cluster kernels."""
+    import torch
+    w = W.Workload("adj2", N=512, n=24, steps=6, h=math.inf, tau=0.1, amp=0.05, law="decay")
+    c, _ = W.coefficients(w)
+    c[0] = stable_T(w.N, w.steps, w.g, w.tau, w.h)
+    out = []
+    for legacy in (False, True):
+        with ww.Context(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps, precision=ww.WW_MIXED) as ctx:
+            if legacy:
+                ctx.set_stream(None)
+            f = torch.empty(1, dtype=torch.float64, device="cuda")
+            g = torch.empty(w.n + 1, dtype=torch.float64, device="cuda")
+            ww.objective_and_grad(ctx, dev(c), f, g)
+            torch.cuda.synchronize()
+            out.append((f.item(), g.cpu().numpy()))
+    (f1, g1), (f2, g2) = out
+    assert f1 == f2
+    assert rel(g1, g2) < 1e-12
+    prob, _ = O.make_problem(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps)
+    f0, g0 = O.objective_and_grad(prob, c)
+    assert rel(g1, g0) < TOL and rel(g2, g0) < TOL
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_batch_of_uneven_shots_matches_single_shots(ww, precision):
     """shoot_jacobian_batch: independent shots of uneven size (the uneven-batch
