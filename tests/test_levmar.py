@@ -1,0 +1,118 @@
+"""Levenberg-Marquardt with delayed Jacobian updates (App. D), host logic, no GPU.
+
+* the trust-region step from the thin SVD against the KKT conditions of the
+  constrained quadratic model and against a library least-squares solve;
+* convergence on textbook problems (Rosenbrock's residuals: zero residual; an
+  exponential fit: nonzero residual, against scipy's least_squares);
+* the standing-wave problem of Sec. 3 on the CPU oracle (paper basis: even k on
+  eta, odd k on phi; c_1 fixed): the solver reaches the round-off regime, reuses
+  its Jacobian (fewer Jacobians than accepted steps), and the period obeys the
+  weakly nonlinear law T(eps) = T_lin + O(eps^2) with T_lin = 2 pi / sqrt(g tanh h)
+  (Eq. lin:soln): halving eps divides T - T_lin by 4.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1210_5672_gb300.levmar import LMOptions, levmar, trust_region_step
+
+
+def _svd(J):
+    U, s, Vt = np.linalg.svd(J, full_matrices=False)
+    return U, s, Vt.T
+
+
+def test_trust_region_step_kkt():
+    rng = np.random.default_rng(0)
+    J = rng.standard_normal((30, 8))
+    r = rng.standard_normal(30)
+    U, s, V = _svd(J)
+    gn = np.linalg.lstsq(J, -r, rcond=None)[0]
+    # inactive constraint: the Gauss-Newton step, lam = 0
+    p, lam, df = trust_region_step(U, s, V, r, 2 * np.linalg.norm(gn))
+    assert lam == 0.0 and np.allclose(p, gn, rtol=1e-12, atol=1e-14)
+    # active constraint: |p| = Delta and (J^T J + lam I) p = -J^T r with lam > 0
+    delta = 0.3 * np.linalg.norm(gn)
+    p, lam, df = trust_region_step(U, s, V, r, delta)
+    assert lam > 0 and abs(np.linalg.norm(p) - delta) <= 1e-11 * delta
+    ref = np.linalg.solve(J.T @ J + lam * np.eye(8), -J.T @ r)
+    assert np.allclose(p, ref, rtol=1e-10, atol=1e-14)
+    # predicted change of the quadratic model
+    g, B = J.T @ r, J.T @ J
+    assert abs(df - (g @ p + 0.5 * p @ B @ p)) <= 1e-12 * abs(df)
+
+
+def test_rosenbrock_zero_residual():
+    def res(x):
+        return np.array([10.0 * (x[1] - x[0] ** 2), 1.0 - x[0]])
+
+    def resj(x):
+        return res(x), np.array([[-20.0 * x[0], 10.0], [-1.0, 0.0]])
+
+    out = levmar(res, resj, [-1.2, 1.0], 1.0)
+    assert np.allclose(out.c, [1.0, 1.0], atol=1e-12)
+    assert out.f < 1e-26
+
+
+def test_exponential_fit_matches_library():
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    t = np.linspace(0.0, 3.0, 40)
+    rng = np.random.default_rng(2)
+    y = 2.5 * np.exp(-1.3 * t) + 0.4 + 0.01 * rng.standard_normal(t.size)
+
+    def res(x):
+        return x[0] * np.exp(-x[1] * t) + x[2] - y
+
+    def jac(x):
+        e = np.exp(-x[1] * t)
+        return np.stack([e, -x[0] * t * e, np.ones_like(t)], axis=1)
+
+    out = levmar(res, lambda x: (res(x), jac(x)), [1.0, 1.0, 0.0], 1.0)
+    ref = scipy_opt.least_squares(res, [1.0, 1.0, 0.0], jac=jac, xtol=1e-15, ftol=1e-15, gtol=1e-15)
+    assert np.allclose(out.c, ref.x, rtol=1e-8, atol=1e-10)
+    assert out.f > 1e-4                       # a genuine nonzero-residual minimum
+
+
+def _standing_wave(eps, N=32, n=12, steps=96, h=1.0):
+    x = 2 * np.pi * np.arange(N) / N
+    basis = np.zeros((2 * N, n))
+    for k in range(1, n + 1):   # Eq. init:stand: even k on eta, odd k on phi, 2 cos(k x)
+        if k % 2 == 0:
+            basis[:N, k - 1] = 2 * np.cos(k * x)
+        else:
+            basis[N:, k - 1] = 2 * np.cos(k * x)
+    prob, keep = O.make_problem(N, n, h=h, steps=steps, basis=basis)
+    T_lin = 2 * math.pi / math.sqrt(math.tanh(h))
+    c0 = np.zeros(n + 1)
+    c0[0] = T_lin
+    c0[1] = eps
+    free = np.array([0] + list(range(2, n + 1)))
+
+    def full(z):
+        c = c0.copy()
+        c[free] = z
+        return c
+
+    def res(z):
+        return O.shoot(prob, full(z))[0]
+
+    def resj(z):
+        r, J, _ = O.shoot_jacobian(prob, full(z))
+        return r, J[:, free]
+
+    out = levmar(res, resj, c0[free], 0.1 * T_lin, LMOptions())
+    return out, T_lin, keep
+
+
+def test_standing_wave_period_is_second_order_in_amplitude():
+    outs = []
+    for eps in (0.02, 0.01):
+        out, T_lin, _ = _standing_wave(eps)
+        assert out.f < 1e-24, (eps, out.f, out.reason)
+        assert out.jacobians < out.accepted    # the Jacobian was reused across steps
+        outs.append(out.c[0] - T_lin)
+    d1, d2 = outs
+    assert abs(d1) > 1e-6 and np.sign(d1) == np.sign(d2)
+    assert abs(d1 / d2 - 4.0) < 0.1, (d1, d2)
