@@ -27,7 +27,7 @@
  *   Eqs. (l5a), (l6a)   linearised (variational) equations          App. B
  *   Eqs. (f:phi), (Jik), (q:qdot)  objective and Jacobian           Sec. 3.1, 3.3
  *
- * Readings where the paper is garbled or silent (listed again in the design doc):
+ * Readings where the paper is garbled or silent:
  *  R1 image terms K2, G2 carry a MINUS sign (the integrals of App. A subtract
  *     the mirror-image double layer; the printed "+" in Eq. (K1K2) gives the
  *     symbol k coth(kh) on a flat surface instead of k tanh(kh)).
