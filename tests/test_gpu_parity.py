@@ -261,6 +261,23 @@ def test_adjoint_full_size_two_steps(ww, wl, precision):
 _ADJ_ORACLE = {}
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", [0, 1])
+def test_adjoint_jacobian_workload_one_step(ww, precision):
+    """The gradient at the Jacobian benchmark's size (N = 2048, 512 modes + T)
+    for ONE RK4 step of the full run's dt, against the oracle's discrete adjoint."""
+    w = W.shrink(W.LARGE, steps=1)
+    c, _ = W.coefficients(W.LARGE)
+    c[0] /= W.LARGE.steps
+    f, g, _ = gpu_gradient(ww, w, c, precision)
+    if "large1" not in _ADJ_ORACLE:
+        prob, _ = O.make_problem(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=1)
+        _ADJ_ORACLE["large1"] = O.objective_and_grad(prob, c)
+    f0, g0 = _ADJ_ORACLE["large1"]
+    assert abs(f - f0) / f0 < TOL
+    assert rel(g, g0) < TOL
+
+
 def test_adjoint_two_chain_sweep_matches_one_chain_sweep(ww):
     """The mixed form's reverse sweep on the context's own stream runs as two
     chains (each stage's DtN setup one stage ahead, operands double-buffered by
