@@ -24,7 +24,8 @@ the printed form lacks the inverse, which would not be Newton's method for tau.
 The solver is generic: `levmar` takes two callables (residual, and residual
 with Jacobian) on numpy vectors.  `solve_standing_wave` drives it with the GPU
 library's `shoot` and `shoot_jacobian` for the standing-wave problem of Sec. 3
-with some parameters held fixed (the amplitude of a continuation step).
+with some parameters held fixed (the amplitude of a continuation step), and
+`continue_branch` follows a family of solutions in one parameter.
 """
 from __future__ import annotations
 
@@ -162,6 +163,27 @@ def levmar(residual, residual_and_jacobian, c0, delta0, opts: LMOptions | None =
             trigger = None
     return LMResult(c=c, r=r, f=f, jacobians=nJ, residuals=nr, steps=nsteps, accepted=nacc, reason=reason,
                     history=history)
+
+
+def continue_branch(solve, c_a, c_b, index, values):
+    """Numerical continuation of a solution family in the parameter c[index]
+    (the bifurcation parameter, held fixed in each solve; Sec. 4 follows the
+    families of standing waves this way): each next solution is predicted by
+    linear extrapolation in that parameter from the last two solutions and
+    corrected by solve(c_guess) -> LMResult (with the full c in .c).  With small
+    enough steps the prediction is close enough that one Jacobian per solution
+    suffices (the delayed updates of App. D).  Returns the LMResults at `values`."""
+    prev = np.array(c_a, dtype=np.float64)
+    cur = np.array(c_b, dtype=np.float64)
+    out = []
+    for v in values:
+        dp = cur[index] - prev[index]
+        guess = cur + (cur - prev) * ((v - cur[index]) / dp)
+        guess[index] = v
+        res = solve(guess)
+        out.append(res)
+        prev, cur = cur, np.array(res.c, dtype=np.float64)
+    return out
 
 
 def solve_standing_wave(ctx, c0, free, delta0=1e-2, opts: LMOptions | None = None) -> LMResult:

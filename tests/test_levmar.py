@@ -8,7 +8,11 @@
   eta, odd k on phi; c_1 fixed): the solver reaches the round-off regime, reuses
   its Jacobian (fewer Jacobians than accepted steps), and the period obeys the
   weakly nonlinear law T(eps) = T_lin + O(eps^2) with T_lin = 2 pi / sqrt(g tanh h)
-  (Eq. lin:soln): halving eps divides T - T_lin by 4.
+  (Eq. lin:soln): halving eps divides T - T_lin by 4;
+* numerical continuation along the unit-depth family (Sec. 4, Fig. bif10: the
+  family bifurcates from T = 2 pi / sqrt(tanh 1) ~ 7.200 and its period first
+  decreases with amplitude): one Jacobian per solution, a decreasing period, and
+  the same solutions as direct solves.
 """
 import math
 
@@ -16,7 +20,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from paper_1210_5672_gb300.levmar import LMOptions, levmar, trust_region_step
+from paper_1210_5672_gb300.levmar import LMOptions, continue_branch, levmar, trust_region_step
 
 
 def _svd(J):
@@ -75,6 +79,49 @@ def test_exponential_fit_matches_library():
     assert out.f > 1e-4                       # a genuine nonzero-residual minimum
 
 
+def _problem(N=32, n=12, steps=96, h=1.0):
+    x = 2 * np.pi * np.arange(N) / N
+    basis = np.zeros((2 * N, n))
+    for k in range(1, n + 1):   # Eq. init:stand: even k on eta, odd k on phi, 2 cos(k x)
+        if k % 2 == 0:
+            basis[:N, k - 1] = 2 * np.cos(k * x)
+        else:
+            basis[N:, k - 1] = 2 * np.cos(k * x)
+    prob, keep = O.make_problem(N, n, h=h, steps=steps, basis=basis)
+    free = np.array([0] + list(range(2, n + 1)))
+
+    def solve(guess):
+        def full(z):
+            c = guess.copy()
+            c[free] = z
+            return c
+
+        out = levmar(lambda z: O.shoot(prob, full(z))[0],
+                     lambda z: (lambda rJ: (rJ[0], rJ[1][:, free]))(O.shoot_jacobian(prob, full(z))),
+                     guess[free], 0.01 * guess[0], LMOptions())
+        out.c = full(out.c)
+        return out
+
+    return solve, keep
+
+
+def test_continuation_along_the_unit_depth_family():
+    solve, keep = _problem()
+    T_lin = 2 * math.pi / math.sqrt(math.tanh(1.0))
+    assert abs(T_lin - 7.200) < 1e-3             # Fig. bif10's bifurcation point
+    lin = lambda e: np.concatenate([[T_lin, e], np.zeros(11)])
+    a, b = solve(lin(0.01)), solve(lin(0.015))
+    values = [0.02, 0.025, 0.03, 0.035, 0.04]
+    branch = continue_branch(solve, a.c, b.c, 1, values)
+    Ts = [a.c[0], b.c[0]] + [r.c[0] for r in branch]
+    assert all(r.f < 1e-24 for r in branch)
+    assert sum(r.jacobians == 1 for r in branch) >= 4    # one Jacobian per solution, as a rule
+    assert all(t1 > t2 for t1, t2 in zip(Ts, Ts[1:]))    # the period decreases with amplitude
+    assert Ts[-1] < T_lin
+    direct = solve(lin(values[-1]))
+    assert np.max(np.abs(direct.c - branch[-1].c)) < 1e-9 * values[-1]
+
+
 def _standing_wave(eps, N=32, n=12, steps=96, h=1.0):
     x = 2 * np.pi * np.arange(N) / N
     basis = np.zeros((2 * N, n))
@@ -114,5 +161,6 @@ def test_standing_wave_period_is_second_order_in_amplitude():
         assert out.jacobians < out.accepted    # the Jacobian was reused across steps
         outs.append(out.c[0] - T_lin)
     d1, d2 = outs
-    assert abs(d1) > 1e-6 and np.sign(d1) == np.sign(d2)
+    # the unit-depth period first decreases with amplitude (Sec. 4, Fig. bif10)
+    assert d1 < -1e-6 and d2 < 0
     assert abs(d1 / d2 - 4.0) < 0.1, (d1, d2)
