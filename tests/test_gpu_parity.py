@@ -344,6 +344,24 @@ def test_batch_of_uneven_shots_matches_single_shots(ww, precision):
     assert col_rel(J.cpu().numpy().T, J0) < TOL
 
 
+def test_column_split_engine_on_gpu(ww):
+    """The column split's sub-problems on the library (single rank: all mode
+    columns through the combined-shape basis) give the unsharded Jacobian."""
+    from paper_1210_5672_gb300.sharding import gpu_engine, sharded_jacobian
+    N, n, steps = 128, 12, 8
+    w = W.Workload("shard", N=N, n=n, steps=steps, amp=0.05)
+    c, _ = W.coefficients(w)
+    basis = np.zeros((2 * N, n))
+    x = x_grid(N)
+    for k in range(1, n + 1):
+        basis[:N, k - 1] = np.cos(k * x)
+    r, J, f = sharded_jacobian(c, basis, gpu_engine(N, h=w.h, steps=steps), 0, 1)
+    r0, J0, f0, _ = gpu_jacobian(ww, w, c, basis=basis)
+    # the initial states differ by rounding (the shape is summed once on the host)
+    assert rel(r, r0) < 1e-13 and abs(f - f0) <= 1e-13 * f0
+    assert col_rel(J, J0) < TOL
+
+
 def test_host_entry_point_matches_device(ww):
     w = W.shrink(W.MEDIUM, N=128, n=10, steps=4)
     c, _ = W.coefficients(w)
