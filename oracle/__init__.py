@@ -98,6 +98,8 @@ def _set_signatures(L):
         "orc_energy": (C.c_double, [P, _D]),
         "orc_objective_and_grad": (None, [P, _D, _D, _D]),
         "orc_dtn_T": (None, [C.c_int, C.c_double, _D, _D, _D]),
+        "orc_trajectory_columns": (None, [P, C.c_double, _D, _D, C.c_int, C.c_int, _D]),
+        "orc_adjoint_trajectory": (None, [P, _D, _D]),
         "orc_lu_solve_T": (None, [C.c_int, _D, C.POINTER(C.c_int), _D, _D]),
         "orc_threads": (C.c_int, []),
         "orc_set_threads": (None, [C.c_int]),
@@ -228,6 +230,26 @@ def objective_and_grad(prob: Problem, c):
     g = np.empty(prob.n + 1)
     lib().orc_objective_and_grad(C.byref(prob), _p(c), _p(f), _p(g))
     return float(f[0]), g
+
+
+def trajectory_columns(prob: Problem, T: float, q0, cols, t_col: int = 0) -> np.ndarray:
+    """Base state and variational columns at every step boundary: shape
+    (steps + 1, ncol + 1, 2N)."""
+    q0 = _f64(q0)
+    cols = _f64(np.atleast_2d(cols))
+    ncol = cols.shape[0]
+    out = np.empty((prob.steps + 1, ncol + 1, 2 * prob.N))
+    lib().orc_trajectory_columns(C.byref(prob), float(T), _p(q0), _p(cols), ncol, int(t_col), _p(out))
+    return out
+
+
+def adjoint_trajectory(prob: Problem, c) -> np.ndarray:
+    """The discrete adjoint state at every step boundary, shape (steps + 1, 2N):
+    row n is the gradient of f with respect to the state at the start of step n."""
+    c = _f64(c)
+    out = np.empty((prob.steps + 1, 2 * prob.N))
+    lib().orc_adjoint_trajectory(C.byref(prob), _p(c), _p(out))
+    return out
 
 
 def dtn_T(eta, x, h) -> np.ndarray:

@@ -498,8 +498,14 @@ void orc_initial(const orc_problem *p, const double *c, double *q0)
 }
 
 /* Integrate base + ncol variational columns from 0 to T/4 with p->steps RK4
- * steps; y holds the initial data on entry and the final data on exit. */
+ * steps; y holds the initial data on entry and the final data on exit.  rec
+ * (NULL or (steps + 1) x len) receives y at every step boundary. */
+static void integrate_rec(const orc_problem *p, double T, double *y, int ncol, int t_col, double *rec);
 static void integrate(const orc_problem *p, double T, double *y, int ncol, int t_col)
+{
+    integrate_rec(p, T, y, ncol, t_col, NULL);
+}
+static void integrate_rec(const orc_problem *p, double T, double *y, int ncol, int t_col, double *rec)
 {
     int N = p->N;
     size_t len = (size_t)(ncol + 1) * 2 * N;
@@ -508,6 +514,7 @@ static void integrate(const orc_problem *p, double T, double *y, int ncol, int t
     double *ys = malloc(sizeof(double) * len);
     static const double a[4] = {0.0, 0.5, 0.5, 1.0};
     static const double b[4] = {1.0, 2.0, 2.0, 1.0};
+    if (rec) memcpy(rec, y, sizeof(double) * len);
     for (int n = 0; n < p->steps; ++n) {
         for (size_t i = 0; i < len; ++i) acc[i] = 0.0;
         for (int st = 0; st < 4; ++st) {
@@ -521,8 +528,24 @@ static void integrate(const orc_problem *p, double T, double *y, int ncol, int t
             orc_spectral(N, MUL_FILTER, y + (size_t)c * 2 * N, y + (size_t)c * 2 * N);
             orc_spectral(N, MUL_FILTER, y + (size_t)c * 2 * N + N, y + (size_t)c * 2 * N + N);
         }
+        if (rec) memcpy(rec + (size_t)(n + 1) * len, y, sizeof(double) * len);
     }
     free(k); free(acc); free(ys);
+}
+
+/* Base state and ncol variational columns (initial data cols, each 2N; column
+ * t_col forced as in orc_rhs) at every step boundary: rec is
+ * (steps + 1) x (ncol + 1) x 2N. */
+void orc_trajectory_columns(const orc_problem *p, double T, const double *q0, const double *cols, int ncol,
+                            int t_col, double *rec)
+{
+    int N = p->N;
+    size_t len = (size_t)(ncol + 1) * 2 * N;
+    double *y = malloc(sizeof(double) * len);
+    memcpy(y, q0, sizeof(double) * 2 * N);
+    memcpy(y + 2 * N, cols, sizeof(double) * (size_t)ncol * 2 * N);
+    integrate_rec(p, T, y, ncol, t_col, rec);
+    free(y);
 }
 
 /* Evolve the base state only (no columns): q_end = q(T/4). */
@@ -649,7 +672,26 @@ static void rhs_T(const orc_problem *p, const double *q, const double *kb, doubl
  * the stages in reverse order, stage st contributing its transposed RHS to
  * lambda and, scaled by a_st dt, to the adjoint of the previous stage's RHS.
  * grad_k = basis_k . lambda(0); grad_0 = sum over stages of kbar . F / T. */
+static void adjoint_sweep(const orc_problem *p, const double *c, double *f, double *grad, double *lam_rec);
+
 void orc_objective_and_grad(const orc_problem *p, const double *c, double *f, double *grad)
+{
+    adjoint_sweep(p, c, f, grad, NULL);
+}
+
+/* The adjoint state at every step boundary: lam_rec[n] (n = 0..steps, 2N each)
+ * is the gradient of f with respect to the state at the start of step n
+ * (lam_rec[steps] = (0, phi(T/4)/N)).  The discrete counterpart of Sec. 3.2's
+ * identity <q~(T/4 - t), qdot(t)> = const: lam_rec[n] . w_n is the same for
+ * every n when w is an unforced variational column. */
+void orc_adjoint_trajectory(const orc_problem *p, const double *c, double *lam_rec)
+{
+    double f, *grad = malloc(sizeof(double) * (p->n + 1));
+    adjoint_sweep(p, c, &f, grad, lam_rec);
+    free(grad);
+}
+
+static void adjoint_sweep(const orc_problem *p, const double *c, double *f, double *grad, double *lam_rec)
 {
     int N = p->N, S = 4 * p->steps;
     size_t n2 = (size_t)2 * N;
@@ -680,6 +722,7 @@ void orc_objective_and_grad(const orc_problem *p, const double *c, double *f, do
     double *lam = malloc(sizeof(double) * n2), *kb = malloc(sizeof(double) * n2 * 4);
     double *wb = malloc(sizeof(double) * n2);
     for (int i = 0; i < N; ++i) { lam[i] = 0.0; lam[N + i] = y[N + i] / N; }
+    if (lam_rec) memcpy(lam_rec + (size_t)p->steps * n2, lam, sizeof(double) * n2);
     double gT = 0.0;
     for (int n = p->steps - 1; n >= 0; --n) {
         orc_spectral(N, MUL_FILTER, lam, lam);   /* the end-of-step filter, transposed */
@@ -694,6 +737,7 @@ void orc_objective_and_grad(const orc_problem *p, const double *c, double *f, do
             if (st > 0)
                 for (size_t i = 0; i < n2; ++i) kb[(st - 1) * n2 + i] += a[st] * dt * wb[i];
         }
+        if (lam_rec) memcpy(lam_rec + (size_t)n * n2, lam, sizeof(double) * n2);
     }
     grad[0] = gT;
     for (int kk = 1; kk <= p->n; ++kk) {

@@ -402,3 +402,29 @@ def test_lu_transposed_solve():
     O.lib().orc_lu_solve_T(N, O._p(LU), piv.ctypes.data_as(C.POINTER(C.c_int)), O._p(b), O._p(x))
     ref = np.linalg.solve(A.T, b)
     assert np.max(np.abs(x - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_adjoint_identity_at_every_step():
+    """Sec. 3.2: <q~(T/4 - t), qdot(t)> is constant in time.  For the discrete
+    adjoint, the pairing lam_n . w_n of the adjoint state with an unforced
+    variational column is the same at every step boundary (each transposed
+    step is exactly the transpose of its forward step), and equals that
+    column's gradient entry."""
+    prob, keep, c = _adjoint_case(32, 6, 16, 0.5, 0.05, 0.08)
+    N = prob.N
+    lam = O.adjoint_trajectory(prob, c)
+    f, g = O.objective_and_grad(prob, c)
+    q0 = O.initial(prob, c)
+    x = x_grid(N)
+    for k in (1, 4):
+        col = np.concatenate([np.cos(k * x), np.zeros(N)])    # the default basis column of c_k
+        w = O.trajectory_columns(prob, c[0], q0, col)[:, 1, :]
+        pair = np.einsum("ni,ni->n", lam, w)
+        # rounding of each inner product scales with |lam_n| |w_n| (Cauchy-Schwarz)
+        scale = np.linalg.norm(lam, axis=1) * np.linalg.norm(w, axis=1)
+        assert np.all(np.abs(pair - g[k]) <= 1e-13 * scale), (k, pair, g[k])
+        assert abs(g[k]) > 1e-6 * scale.max()   # far above the rounding bound: the identity is not vacuous
+    # the final adjoint state is the gradient of f = r.r/2 with respect to the final state
+    qT = O.evolve(prob, c[0], q0)
+    assert np.array_equal(lam[-1][:N], np.zeros(N))
+    assert np.allclose(lam[-1][N:], qT[N:] / N, rtol=0, atol=1e-18)
