@@ -1,0 +1,48 @@
+"""The seeded input recipe (paper_1210_5672_gb300/workloads.py), no GPU:
+initial periods against the values the paper prints, the geometry redraw rule,
+and the uneven-batch recipe's ranges and step rule."""
+import math
+
+import numpy as np
+
+from paper_1210_5672_gb300 import workloads as W
+
+
+def test_linear_periods_match_the_paper():
+    # Sec. 4: T = 2 pi / sqrt(tanh h) = 7.19976 at h = 1; 28.1110 at h = 0.05;
+    # deep water with sigma/rho = 1: 2 pi / sqrt(2) = 4.443
+    assert abs(W.linear_period(1.0, 0.0, 1.0) - 7.19976) < 1e-5
+    assert abs(W.linear_period(1.0, 0.0, 0.05) - 28.1110) < 1e-4
+    assert abs(W.linear_period(1.0, 1.0, math.inf) - 4.443) < 1e-3
+    for w in (W.LARGE, W.SHALLOW, W.DEEP_TENSION):
+        c, _ = W.coefficients(w)
+        assert c[0] == W.linear_period(w.g, w.tau, w.h)
+
+
+def test_redraw_keeps_the_surface_above_half_depth():
+    for w in (W.SMALL, W.MEDIUM, W.LARGE, W.SHALLOW):
+        c, seed = W.coefficients(w)
+        x = W.grid(w.N)
+        surf = w.h + np.cos(np.outer(x, np.arange(1, w.n + 1))) @ c[1:]
+        assert surf.min() >= 0.5 * w.h
+        assert seed >= w.seed
+    # the draw is reproducible
+    a, sa = W.coefficients(W.LARGE)
+    b, sb = W.coefficients(W.LARGE)
+    assert sa == sb and np.array_equal(a, b)
+
+
+def test_uneven_batch_recipe():
+    shots = W.uneven_shots()
+    assert len(shots) == 32
+    for w, c in shots:
+        assert w.N in (256, 512, 1024, 2048, 4096)
+        assert 8 <= w.n + 1 <= 64
+        assert 0.1 <= w.h <= 2.0 and w.tau in (0.0, 0.05)
+        assert 0.01 <= c[1] <= 0.5 and c[1] < 0.45 * w.h
+        assert w.steps == W.stable_steps(w.N, w.g, w.tau, w.h, c[0]) >= w.N // 2
+    capped = W.uneven_shots(step_cap=64)
+    for (w, c), (wc, cc) in zip(shots, capped):
+        assert wc.steps == min(w.steps, 64)
+        # the cap keeps each shot's dt
+        assert abs(cc[0] / (4 * wc.steps) - c[0] / (4 * w.steps)) <= 1e-15 * c[0]
