@@ -124,6 +124,62 @@ def test_analytic_potential_dtn_converges_spectrally(deep):
     assert errs[0] > 10 * errs[1] > 100 * errs[2] or errs[1] < 1e-12
 
 
+def _mp_tools(mp, N):
+    """40-digit trigonometric-interpolant operators on N points (explicit DFT)."""
+    def coeffs(vals):
+        return {k: sum(mp.mpf(vals[j]) * mp.expjpi(-2 * mp.mpf(k * j) / N) for j in range(N)) / N
+                for k in range(-N // 2 + 1, N // 2 + 1)}
+
+    def apply(vals, mult):
+        ck = coeffs(vals)
+        return [mp.re(sum(ck[k] * mult(k) * mp.expjpi(2 * mp.mpf(k * i) / N) for k in ck)) for i in range(N)]
+
+    nyq = N // 2
+    deriv = lambda v: apply(v, lambda k: 0 if abs(k) == nyq else 1j * k)             # Nyquist dropped
+    hilbert = lambda v: apply(v, lambda k: 0 if (k == 0 or abs(k) == nyq) else -1j * mp.sign(k))
+    filt = lambda v: apply(v, lambda k: mp.exp(-36 * (mp.mpf(abs(k)) / nyq) ** 36))
+    proj = lambda v: apply(v, lambda k: 0 if k == 0 else 1)
+    return deriv, hilbert, filt, proj
+
+
+def _mp_dtn(mp, N, h, e, phi):
+    """The discrete DtN of Eq. (K1K2) (images with the minus sign) in mpmath:
+    its own cot, its own elimination and an explicit DFT."""
+    deriv, hilbert, _, _ = _mp_tools(mp, N)
+    # cos/sin rather than mpmath's complex cot, which loses its relative accuracy
+    # near its zeros (cot(-pi/2 + 1e-41 i) comes out near 1e-8 i): points pi apart
+    # with equal heights put the direct kernel exactly there.
+    cot = lambda w: mp.cos(w) / mp.sin(w)
+    ex = deriv(e)
+    exx = deriv(ex)
+    al = [2 * mp.pi * j / N for j in range(N)]
+    z = [al[j] + 1j * e[j] for j in range(N)]
+    dz = [1 + 1j * ex[j] for j in range(N)]
+    ddz = [1j * exx[j] for j in range(N)]
+    A = mp.matrix(N, N)
+    G = mp.matrix(N, N)
+    for i in range(N):
+        for j in range(N):
+            if i == j:
+                k1 = -mp.im(ddz[i] / (2 * dz[i]))
+                g1 = mp.re(ddz[i] / (2 * dz[i]))
+            else:
+                c = cot((z[i] - z[j]) / 2)
+                k1 = mp.im(dz[j] / 2 * c)
+                g1 = mp.re(dz[i] / 2 * c - cot((al[i] - al[j]) / 2) / 2)
+            k2 = g2 = 0
+            if not math.isinf(h):
+                cb = cot((z[i] - mp.conj(z[j])) / 2)
+                k2 = -mp.im(mp.conj(dz[j]) / 2 * cb)
+                g2 = -mp.re(dz[i] / 2 * cb)
+            A[i, j] = (k1 + k2) / N + (mp.mpf(1) / 2 if i == j else 0)
+            G[i, j] = (g1 + g2) / N
+    mu = mp.lu_solve(A, mp.matrix(list(phi)))
+    gam = deriv([mu[j] for j in range(N)])
+    hg = hilbert(gam)
+    return [hg[i] / 2 + sum(G[i, j] * gam[j] for j in range(N)) for i in range(N)], ex
+
+
 def test_dtn_high_precision_tiny_n():
     """Same discrete operator evaluated in 40-digit arithmetic (mpmath: its own
     cot, its own elimination and an explicit DFT) at N = 8 and 16."""
@@ -134,60 +190,47 @@ def test_dtn_high_precision_tiny_n():
         eta = (0.0 if math.isinf(h) else h) + 0.1 * np.cos(x) - 0.04 * np.cos(2 * x)
         phi = 0.3 * np.cos(x) + 0.1 * np.sin(3 * x)
         got = O.dtn(eta, phi, h)
-
-        def deriv(vals):  # exact trigonometric-interpolant derivative, Nyquist dropped
-            out = []
-            for i in range(N):
-                s = mp.mpf(0)
-                for k in range(-N // 2 + 1, N // 2):
-                    ck = sum(mp.mpf(vals[j]) * mp.expjpi(-2 * mp.mpf(k * j) / N) for j in range(N)) / N
-                    s += ck * 1j * k * mp.expjpi(2 * mp.mpf(k * i) / N)
-                out.append(mp.re(s))
-            return out
-
-        def hilbert(vals):
-            out = []
-            for i in range(N):
-                s = mp.mpf(0)
-                for k in range(-N // 2 + 1, N // 2):
-                    if k == 0:
-                        continue
-                    ck = sum(mp.mpf(vals[j]) * mp.expjpi(-2 * mp.mpf(k * j) / N) for j in range(N)) / N
-                    s += ck * (-1j * mp.sign(k)) * mp.expjpi(2 * mp.mpf(k * i) / N)
-                out.append(mp.re(s))
-            return out
-
-        e = [mp.mpf(v) for v in eta]
-        ex = deriv(e)
-        exx = deriv(ex)
-        al = [2 * mp.pi * j / N for j in range(N)]
-        z = [al[j] + 1j * e[j] for j in range(N)]
-        dz = [1 + 1j * ex[j] for j in range(N)]
-        ddz = [1j * exx[j] for j in range(N)]
-        A = mp.matrix(N, N)
-        G = mp.matrix(N, N)
-        for i in range(N):
-            for j in range(N):
-                if i == j:
-                    k1 = -mp.im(ddz[i] / (2 * dz[i]))
-                    g1 = mp.re(ddz[i] / (2 * dz[i]))
-                else:
-                    c = mp.cot((z[i] - z[j]) / 2)
-                    k1 = mp.im(dz[j] / 2 * c)
-                    g1 = mp.re(dz[i] / 2 * c - mp.cot((al[i] - al[j]) / 2) / 2)
-                k2 = g2 = 0
-                if not math.isinf(h):
-                    cb = mp.cot((z[i] - mp.conj(z[j])) / 2)
-                    k2 = -mp.im(mp.conj(dz[j]) / 2 * cb)
-                    g2 = -mp.re(dz[i] / 2 * cb)
-                A[i, j] = (k1 + k2) / N + (mp.mpf(1) / 2 if i == j else 0)
-                G[i, j] = (g1 + g2) / N
-        mu = mp.lu_solve(A, mp.matrix([mp.mpf(v) for v in phi]))
-        gam = deriv([mu[j] for j in range(N)])
-        hg = hilbert(gam)
-        ref = [hg[i] / 2 + sum(G[i, j] * gam[j] for j in range(N)) for i in range(N)]
+        ref, _ = _mp_dtn(mp, N, h, [mp.mpf(v) for v in eta], [mp.mpf(v) for v in phi])
         ref = np.array([float(v) for v in ref])
         assert np.max(np.abs(got - ref)) < 5e-15 * max(1.0, np.max(np.abs(ref))), (N, h)
+
+
+def test_shot_high_precision_tiny_n():
+    """A whole shot (Eq. ww with Eq. uv:from:G, the filter and P, classic RK4
+    with the step filter; r = phi(T/4)/sqrt(N), f = r.r/2) in 40-digit
+    arithmetic at N = 8, against the FP64 oracle: the time loop, the right-hand
+    side and the objective, not only the DtN."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    N, h, g, steps = 8, 1.0, 1.0, 4
+    deriv, _, filt, proj = _mp_tools(mp, N)
+    x = x_grid(N)
+    c = np.array([7.2, 0.05, 0.01, -0.004])
+    prob, _ = O.make_problem(N, 3, g=g, h=h, steps=steps)
+    r64, f64 = O.shoot(prob, c)
+
+    def rhs(e, p):
+        gp, ex = _mp_dtn(mp, N, h, e, p)
+        pp = deriv(p)
+        u = [(pp[i] - ex[i] * gp[i]) / (1 + ex[i] ** 2) for i in range(N)]
+        v = [(ex[i] * pp[i] + gp[i]) / (1 + ex[i] ** 2) for i in range(N)]
+        pt = [v[i] * gp[i] - u[i] ** 2 / 2 - v[i] ** 2 / 2 - g * e[i] for i in range(N)]
+        return filt(gp), filt(proj(pt))
+
+    e = [mp.mpf(h) + sum(mp.mpf(c[k]) * mp.cos(k * 2 * mp.pi * j / N) for k in range(1, 4)) for j in range(N)]
+    p = [mp.mpf(0)] * N
+    dt = mp.mpf(c[0]) / 4 / steps
+    for _ in range(steps):
+        k1 = rhs(e, p)
+        k2 = rhs([e[i] + dt / 2 * k1[0][i] for i in range(N)], [p[i] + dt / 2 * k1[1][i] for i in range(N)])
+        k3 = rhs([e[i] + dt / 2 * k2[0][i] for i in range(N)], [p[i] + dt / 2 * k2[1][i] for i in range(N)])
+        k4 = rhs([e[i] + dt * k3[0][i] for i in range(N)], [p[i] + dt * k3[1][i] for i in range(N)])
+        e = filt([e[i] + dt / 6 * (k1[0][i] + 2 * k2[0][i] + 2 * k3[0][i] + k4[0][i]) for i in range(N)])
+        p = filt([p[i] + dt / 6 * (k1[1][i] + 2 * k2[1][i] + 2 * k3[1][i] + k4[1][i]) for i in range(N)])
+    rq = np.array([float(v / mp.sqrt(N)) for v in p])
+    fq = float(sum(v * v for v in p) / N / 2)
+    assert np.max(np.abs(r64 - rq)) < 1e-14 * np.max(np.abs(rq))
+    assert abs(f64 - fq) < 1e-14 * fq
 
 
 # ----------------------------------------------------------------- evolution pins
