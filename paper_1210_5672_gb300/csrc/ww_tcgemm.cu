@@ -246,7 +246,7 @@ int get_encoder() {
 
 }  // namespace
 
-// resolve the driver's tensor-map encoder outside any stream capture
+// resolve the CUDA driver's tensor-map encoder outside any stream capture
 int tc_init() { return get_encoder(); }
 
 // 2-D bf16 tensor [rows][K] (K contiguous), tile box {64, box_rows}, 128-byte swizzle
