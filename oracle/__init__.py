@@ -22,6 +22,16 @@ the paper the C function follows:
                         reading R18: exact transpose of the discrete map)
 * ``dtn_T``          -- the transpose of the discrete DtN operator
 * ``energy``         -- the energy monitor of Sec. 4
+* ``mesh``, ``mesh_inverse``, ``interp`` -- the change of variables of Eq. (xi)
+                        (Eq. rho:def), its inverse by Newton's method and the
+                        trigonometric interpolant used to respace (Sec. 2.2)
+* ``tableau``        -- explicit Runge-Kutta tableaux: classic RK4, and DOP853
+                        (Dormand and Prince's 8th-order 12-stage scheme of Sec.
+                        2.2, the published coefficients as scipy ships them)
+* ``shoot_segments``, ``shoot_jacobian_segments``, ``evolve_segments`` -- the
+                        shot over time segments with their own grids, meshes
+                        and step counts (Sec. 2.2), any tableau
+* ``rhs_segment``, ``dtn_segment`` -- the RHS and the DtN on a segment's mesh
 """
 from __future__ import annotations
 
@@ -64,6 +74,18 @@ class Problem(C.Structure):
 _D = C.POINTER(C.c_double)
 
 
+class Segment(C.Structure):
+    """One time segment (Sec. 2.2): M grid points, `steps` uniform steps over
+    the fraction theta of T/4, mesh parameter rho of Eq. (xi) (1 = uniform),
+    refined near x = pi (centre = 1) or x = 0 (centre = 0)."""
+    _fields_ = [("M", C.c_int), ("steps", C.c_int), ("theta", C.c_double), ("rho", C.c_double),
+                ("centre", C.c_int)]
+
+
+class Tableau(C.Structure):
+    _fields_ = [("s", C.c_int), ("a", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double))]
+
+
 def load(path: str):
     """ctypes handle of a compiled oracle with the signatures set."""
     L = C.CDLL(path)
@@ -101,6 +123,16 @@ def _set_signatures(L):
         "orc_trajectory_columns": (None, [P, C.c_double, _D, _D, C.c_int, C.c_int, _D]),
         "orc_adjoint_trajectory": (None, [P, _D, _D]),
         "orc_lu_solve_T": (None, [C.c_int, _D, C.POINTER(C.c_int), _D, _D]),
+        "orc_mesh_eval": (None, [C.c_double, C.c_int, C.c_int, _D, _D, _D]),
+        "orc_mesh_inverse": (None, [C.c_double, C.c_int, C.c_int, _D, _D]),
+        "orc_interp": (None, [C.c_int, _D, C.c_int, _D, _D]),
+        "orc_evolve_segments": (C.c_int, [P, C.c_int, C.POINTER(Segment), C.POINTER(Tableau), C.c_double, _D,
+                                          _D]),
+        "orc_shoot_segments": (C.c_int, [P, C.c_int, C.POINTER(Segment), C.POINTER(Tableau), _D, _D, _D]),
+        "orc_shoot_jacobian_segments": (C.c_int, [P, C.c_int, C.POINTER(Segment), C.POINTER(Tableau), _D, _D,
+                                                  _D, _D]),
+        "orc_rhs_segment": (None, [P, C.POINTER(Segment), C.c_double, _D, C.c_int, C.c_int, _D]),
+        "orc_dtn_segment": (None, [C.POINTER(Segment), C.c_double, _D, _D, _D]),
         "orc_threads": (C.c_int, []),
         "orc_set_threads": (None, [C.c_int]),
     }
@@ -264,3 +296,111 @@ def dtn_T(eta, x, h) -> np.ndarray:
 def energy(prob: Problem, q) -> float:
     q = _f64(q)
     return float(lib().orc_energy(C.byref(prob), _p(q)))
+
+
+# ------------------------------------------------------------ segments (Sec. 2.2)
+def mesh(rho: float, M: int, centre: int = 1):
+    """(x, E, E') of Eq. (xi) at alpha_j = 2 pi j / M: x = xi(alpha_j), E = xi', E' = xi''."""
+    x, e, e1 = np.empty(M), np.empty(M), np.empty(M)
+    lib().orc_mesh_eval(float(rho), int(centre), int(M), _p(x), _p(e), _p(e1))
+    return x, e, e1
+
+
+def mesh_inverse(rho: float, x, centre: int = 1) -> np.ndarray:
+    x = _f64(x)
+    out = np.empty_like(x)
+    lib().orc_mesh_inverse(float(rho), int(centre), x.size, _p(x), _p(out))
+    return out
+
+
+def interp(f, beta) -> np.ndarray:
+    """The trigonometric interpolant of f (values at 2 pi j / M) at the points beta."""
+    f, beta = _f64(f), _f64(beta)
+    out = np.empty(beta.size)
+    lib().orc_interp(f.size, _p(f), beta.size, _p(beta), _p(out))
+    return out
+
+
+def tableau(name: str):
+    """(a, b) of an explicit Runge-Kutta scheme: 'rk4' (classic) or 'dop853'.
+    DOP853's coefficients are Dormand and Prince's published ones (Hairer,
+    Norsett and Wanner, Solving ODEs I), read from scipy's copy of the table:
+    its 12 stages and the 8th-order weights; the 13th evaluation of the
+    original code serves only its error estimate and dense output."""
+    if name == "rk4":
+        a = np.zeros((4, 4))
+        a[1, 0], a[2, 1], a[3, 2] = 0.5, 0.5, 1.0
+        return a, np.array([1.0, 2.0, 2.0, 1.0]) / 6.0
+    if name == "dop853":
+        from scipy.integrate._ivp import dop853_coefficients as d
+        s = d.N_STAGES
+        return np.array(d.A[:s, :s], dtype=np.float64), np.array(d.B, dtype=np.float64)
+    raise ValueError(name)
+
+
+def _segments(segs):
+    arr = (Segment * len(segs))()
+    for i, sg in enumerate(segs):
+        M, steps, theta, rho = sg[:4]
+        centre = sg[4] if len(sg) > 4 else 1
+        arr[i] = Segment(int(M), int(steps), float(theta), float(rho), int(centre))
+    return arr
+
+
+def _tableau(tab):
+    a, b = tab if not isinstance(tab, str) else tableau(tab)
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    b = np.ascontiguousarray(np.asarray(b, dtype=np.float64))
+    return Tableau(b.size, _p(a), _p(b)), (a, b)
+
+
+def evolve_segments(prob: Problem, segs, tab, T: float, q0) -> np.ndarray:
+    """segs: [(M, steps, theta, rho[, centre]), ...]; tab: 'rk4', 'dop853' or (a, b)."""
+    sa = _segments(segs)
+    tb, keep = _tableau(tab)
+    q0 = _f64(q0)
+    out = np.empty(2 * sa[len(segs) - 1].M)
+    if lib().orc_evolve_segments(C.byref(prob), len(segs), sa, C.byref(tb), float(T), _p(q0), _p(out)) != 0:
+        raise ValueError("invalid segments")
+    return out
+
+
+def shoot_segments(prob: Problem, segs, tab, c):
+    sa = _segments(segs)
+    tb, keep = _tableau(tab)
+    c = _f64(c)
+    M = sa[len(segs) - 1].M
+    r, f = np.empty(M), np.empty(1)
+    if lib().orc_shoot_segments(C.byref(prob), len(segs), sa, C.byref(tb), _p(c), _p(r), _p(f)) != 0:
+        raise ValueError("invalid segments")
+    return r, float(f[0])
+
+
+def shoot_jacobian_segments(prob: Problem, segs, tab, c):
+    """(r, J, f) on the last segment's grid; J is M_last x (n + 1), column 0 = d r / d T."""
+    sa = _segments(segs)
+    tb, keep = _tableau(tab)
+    c = _f64(c)
+    M = sa[len(segs) - 1].M
+    r, f = np.empty(M), np.empty(1)
+    Jc = np.empty((prob.n + 1, M))
+    if lib().orc_shoot_jacobian_segments(C.byref(prob), len(segs), sa, C.byref(tb), _p(c), _p(r), _p(Jc),
+                                         _p(f)) != 0:
+        raise ValueError("invalid segments")
+    return r, Jc.T.copy(), float(f[0])
+
+
+def rhs_segment(prob: Problem, seg, T: float, y, ncol: int = 0, t_col: int = 0) -> np.ndarray:
+    sa = _segments([seg])
+    y = _f64(y).reshape(ncol + 1, 2 * sa[0].M)
+    out = np.empty_like(y)
+    lib().orc_rhs_segment(C.byref(prob), sa, float(T), _p(y), int(ncol), int(t_col), _p(out))
+    return out
+
+
+def dtn_segment(seg, h: float, eta, phi) -> np.ndarray:
+    sa = _segments([seg])
+    eta, phi = _f64(eta), _f64(phi)
+    out = np.empty(eta.size)
+    lib().orc_dtn_segment(sa, float(h), _p(eta), _p(phi), _p(out))
+    return out

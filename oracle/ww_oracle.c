@@ -52,7 +52,9 @@
  * printed "+" sign, 2 = zeta'(alpha) in K1 instead of zeta'(beta), 3 = gravity
  * term dropped from phi_t, 4 = u psi' term dropped from the variational RHS,
  * 5 = the adjoint takes the forward DtN for its transpose (the continuous
- * self-adjointness of App. C applied to the discrete operator). */
+ * self-adjointness of App. C applied to the discrete operator), 6 = the DtN on
+ * a mesh without the 1/|xi'| of Eq. (G), 7 = P on a mesh as the mean over
+ * alpha instead of x. */
 #ifndef ORC_PLANT
 #define ORC_PLANT 0
 #endif
@@ -166,15 +168,45 @@ void orc_spectral(int N, int kind, const double *in, double *out)
     free(x);
 }
 
+/* A change of variables x = xi(alpha) of the grid alpha_j = 2 pi j / N
+ * (Eq. (zeta), Eq. (xi)): x[j] = xi(alpha_j), e[j] = xi'(alpha_j) = E(alpha_j)
+ * > 0, e1[j] = xi''(alpha_j).  Every function on the surface is stored as its
+ * values at x = xi(alpha_j); a NULL mesh is the uniform grid xi = alpha. */
+typedef struct {
+    const double *x, *e, *e1;
+} orc_mesh;
+
+/* d/dx of a function stored on the mesh: (d/dalpha f) / xi'. */
+static void mesh_dx(const orc_mesh *m, int N, const double *in, double *out)
+{
+    orc_spectral(N, MUL_DERIV, in, out);
+    if (m)
+        for (int i = 0; i < N; ++i) out[i] /= m->e[i];
+}
+
+/* P = id - P0 with P0 f = (1/2 pi) int f(x) dx (Sec. 2.1).  On the mesh the
+ * integral is int f(xi(alpha)) xi'(alpha) dalpha, by the trapezoid rule in
+ * alpha (reading R22); on the uniform grid it is the k = 0 mode. */
+static void mesh_project(const orc_mesh *m, int N, const double *in, double *out)
+{
+    if (!m || ORC_PLANT == 7) { orc_spectral(N, MUL_PROJECT, in, out); return; }
+    double s = 0.0;
+    for (int i = 0; i < N; ++i) s += in[i] * m->e[i];
+    s /= N;
+    for (int i = 0; i < N; ++i) out[i] = in[i] - s;
+}
+
 /* ------------------------------------------------------------------ */
 /* Kernel assembly, Eq. (K1K2) with reading R1; trapezoid rule (Sec. 2.2) */
 /* ------------------------------------------------------------------ */
 static cplx ccot(cplx z) { return ccos(z) / csin(z); }
 
 /* A = 1/2 I + K and G, both row-major N x N: row i = collocation point
- * alpha_i, column j = quadrature point beta = alpha_j; entries divided by N. */
-void orc_assemble(int N, double h, const double *eta, const double *eta_x,
-                  const double *eta_xx, double *A, double *G)
+ * alpha_i, column j = quadrature point beta = alpha_j; entries divided by N.
+ * zeta = xi + i eta (Eq. (zeta)); eta_a, eta_aa are alpha-derivatives of the
+ * stored eta.  The subtracted cot((alpha - beta)/2) stays in alpha. */
+static void assemble_mesh(int N, double h, const orc_mesh *m, const double *eta, const double *eta_a,
+                          const double *eta_aa, double *A, double *G)
 {
     int deep = isinf(h);
 #ifdef _OPENMP
@@ -182,13 +214,13 @@ void orc_assemble(int N, double h, const double *eta, const double *eta_x,
 #endif
     for (int i = 0; i < N; ++i) {
         double ai = TWO_PI * i / N;
-        cplx zi = ai + I * eta[i];
-        cplx dzi = 1.0 + I * eta_x[i];
-        cplx ddzi = I * eta_xx[i];
+        cplx zi = (m ? m->x[i] : ai) + I * eta[i];
+        cplx dzi = (m ? m->e[i] : 1.0) + I * eta_a[i];
+        cplx ddzi = m ? m->e1[i] + I * eta_aa[i] : I * eta_aa[i];
         for (int j = 0; j < N; ++j) {
             double aj = TWO_PI * j / N;
-            cplx zj = aj + I * eta[j];
-            cplx dzj = 1.0 + I * eta_x[j];
+            cplx zj = (m ? m->x[j] : aj) + I * eta[j];
+            cplx dzj = (m ? m->e[j] : 1.0) + I * eta_a[j];
             double k1, g1, k2 = 0.0, g2 = 0.0;
             if (i == j) {                       /* diagonal limits, Sec. 2.2 */
                 k1 = -cimag(ddzi / (2.0 * dzi));
@@ -209,6 +241,12 @@ void orc_assemble(int N, double h, const double *eta, const double *eta_x,
             G[(size_t)i * N + j] = (g1 + g2) / N;
         }
     }
+}
+
+void orc_assemble(int N, double h, const double *eta, const double *eta_x,
+                  const double *eta_xx, double *A, double *G)
+{
+    assemble_mesh(N, h, NULL, eta, eta_x, eta_xx, A, G);
 }
 
 /* ------------------------------------------------------------------ */
@@ -287,14 +325,16 @@ void orc_lu_solve_T(int N, const double *LU, const int *piv, const double *b, do
 /* ------------------------------------------------------------------ */
 typedef struct {
     int N;
-    double *eta, *eta_x, *eta_xx;
+    const orc_mesh *m;              /* NULL: uniform grid */
+    double *eta, *eta_x, *eta_xx;   /* eta and its alpha-derivatives */
     double *LU, *G;
     int *piv;
 } dtn_state;
 
-static void dtn_prepare(dtn_state *s, int N, double h, const double *eta)
+static void dtn_prepare_mesh(dtn_state *s, const orc_mesh *m, int N, double h, const double *eta)
 {
     s->N = N;
+    s->m = m;
     s->eta = malloc(sizeof(double) * N);
     s->eta_x = malloc(sizeof(double) * N);
     s->eta_xx = malloc(sizeof(double) * N);
@@ -304,8 +344,13 @@ static void dtn_prepare(dtn_state *s, int N, double h, const double *eta)
     memcpy(s->eta, eta, sizeof(double) * N);
     orc_spectral(N, MUL_DERIV, eta, s->eta_x);
     orc_spectral(N, MUL_DERIV, s->eta_x, s->eta_xx);
-    orc_assemble(N, h, s->eta, s->eta_x, s->eta_xx, s->LU, s->G);
+    assemble_mesh(N, h, m, s->eta, s->eta_x, s->eta_xx, s->LU, s->G);
     orc_lu(N, s->LU, s->piv);
+}
+
+static void dtn_prepare(dtn_state *s, int N, double h, const double *eta)
+{
+    dtn_prepare_mesh(s, NULL, N, h, eta);
 }
 
 static void dtn_release(dtn_state *s)
@@ -314,8 +359,8 @@ static void dtn_release(dtn_state *s)
     free(s->LU); free(s->G); free(s->piv);
 }
 
-/* G phi on the surface: mu = A^{-1} phi; gamma = mu'; 1/2 H gamma + G gamma
- * (|xi'| = 1 on the uniform grid). */
+/* G phi on the surface (Eq. (G)): mu = A^{-1} phi; gamma = mu' (in alpha);
+ * (1/2 H gamma + G gamma) / |xi'| (xi' = 1 on the uniform grid). */
 static void dtn_apply_one(const dtn_state *s, const double *phi, double *out)
 {
     int N = s->N;
@@ -329,6 +374,7 @@ static void dtn_apply_one(const dtn_state *s, const double *phi, double *out)
         double acc = 0.0;
         for (int j = 0; j < N; ++j) acc += s->G[(size_t)i * N + j] * gam[j];
         out[i] = 0.5 * hg[i] + acc;
+        if (s->m && ORC_PLANT != 6) out[i] /= s->m->e[i];
     }
     free(mu); free(gam); free(hg);
 }
@@ -398,12 +444,22 @@ void orc_dtn_matrices(int N, double h, const double *eta, double *A, double *G)
 /* Evaluate the filtered RHS of the base state and of ncol variational
  * columns.  t_col: index (1-based among the variational columns) of the
  * column that additionally receives F(q)/T (reading R2), or 0 for none. */
+static void rhs_impl(const orc_problem *p, const orc_mesh *m, int N, double T, const double *y, int ncol,
+                     int t_col, double *out);
 void orc_rhs(const orc_problem *p, double T, const double *y, int ncol, int t_col, double *out)
 {
-    int N = p->N;
+    rhs_impl(p, NULL, p->N, T, y, ncol, t_col, out);
+}
+
+/* The same on N points of a mesh (NULL: uniform): every x-derivative is
+ * d/dalpha over xi', P subtracts the x-mean, the filter acts on the alpha
+ * grid's Fourier modes (Sec. 2.2). */
+static void rhs_impl(const orc_problem *p, const orc_mesh *m, int N, double T, const double *y, int ncol,
+                     int t_col, double *out)
+{
     const double *eta = y, *phi = y + N;
     dtn_state s;
-    dtn_prepare(&s, N, p->h, eta);
+    dtn_prepare_mesh(&s, m, N, p->h, eta);
 
     double *phi_p = malloc(sizeof(double) * N);
     double *Gphi = malloc(sizeof(double) * N);
@@ -411,11 +467,13 @@ void orc_rhs(const orc_problem *p, double T, const double *y, int ncol, int t_co
     double *vy = malloc(sizeof(double) * N);  /* phi_y on the surface */
     double *w3 = malloc(sizeof(double) * N);  /* (1 + eta'^2)^{-3/2} */
     double *tmp = malloc(sizeof(double) * N);
+    double *etx = malloc(sizeof(double) * N); /* eta' = d eta / dx */
 
-    orc_spectral(N, MUL_DERIV, phi, phi_p);
+    mesh_dx(m, N, phi, phi_p);
+    for (int i = 0; i < N; ++i) etx[i] = m ? s.eta_x[i] / m->e[i] : s.eta_x[i];
     dtn_apply_one(&s, phi, Gphi);
     for (int i = 0; i < N; ++i) {              /* Eq. (uv:from:G) */
-        double ex = s.eta_x[i], d = 1.0 + ex * ex;
+        double ex = etx[i], d = 1.0 + ex * ex;
         ux[i] = (phi_p[i] - ex * Gphi[i]) / d;
         vy[i] = (ex * phi_p[i] + Gphi[i]) / d;
         w3[i] = 1.0 / (d * sqrt(d));
@@ -425,14 +483,14 @@ void orc_rhs(const orc_problem *p, double T, const double *y, int ncol, int t_co
     double *F = out;                 /* column 0 of out */
     for (int i = 0; i < N; ++i) F[i] = Gphi[i];
     for (int i = 0; i < N; ++i) {
-        double ex = s.eta_x[i];
+        double ex = etx[i];
         tmp[i] = ex / sqrt(1.0 + ex * ex);
     }
-    orc_spectral(N, MUL_DERIV, tmp, tmp);
+    mesh_dx(m, N, tmp, tmp);
     for (int i = 0; i < N; ++i)
         F[N + i] = vy[i] * Gphi[i] - 0.5 * ux[i] * ux[i] - 0.5 * vy[i] * vy[i]
                    - (ORC_PLANT == 3 ? 0.0 : p->g) * eta[i] + p->tau * tmp[i];
-    orc_spectral(N, MUL_PROJECT, F + N, F + N);
+    mesh_project(m, N, F + N, F + N);
     orc_spectral(N, MUL_FILTER, F, F);
     orc_spectral(N, MUL_FILTER, F + N, F + N);
 
@@ -448,29 +506,29 @@ void orc_rhs(const orc_problem *p, double T, const double *y, int ncol, int t_co
         /* psi = phidot - phi_y etadot : the perturbation potential on the surface */
         for (int i = 0; i < N; ++i) psi[i] = pd[i] - vy[i] * ed[i];
         dtn_apply_one(&s, psi, Gpsi);
-        orc_spectral(N, MUL_DERIV, psi, dpsi);
+        mesh_dx(m, N, psi, dpsi);
         /* Eq. (l5a): etadot_t = G psi - (etadot u)' */
         for (int i = 0; i < N; ++i) a[i] = ed[i] * ux[i];
-        orc_spectral(N, MUL_DERIV, a, a);
+        mesh_dx(m, N, a, a);
         for (int i = 0; i < N; ++i) oe[i] = Gpsi[i] - a[i];
         /* Eq. (l6a): phidot_t = P[ -(etadot u v)' - u psi' + v G psi - g etadot
          *                        + tau d/dx( etadot' (1+eta'^2)^{-3/2} ) ] */
         for (int i = 0; i < N; ++i) b[i] = ed[i] * ux[i] * vy[i];
-        orc_spectral(N, MUL_DERIV, b, b);
-        orc_spectral(N, MUL_DERIV, ed, e1);
+        mesh_dx(m, N, b, b);
+        mesh_dx(m, N, ed, e1);
         for (int i = 0; i < N; ++i) e1[i] *= w3[i];
-        orc_spectral(N, MUL_DERIV, e1, e1);
+        mesh_dx(m, N, e1, e1);
         for (int i = 0; i < N; ++i)
             op[i] = -b[i] - (ORC_PLANT == 4 ? 0.0 : ux[i]) * dpsi[i] + vy[i] * Gpsi[i] - p->g * ed[i]
                     + p->tau * e1[i];
-        orc_spectral(N, MUL_PROJECT, op, op);
+        mesh_project(m, N, op, op);
         orc_spectral(N, MUL_FILTER, oe, oe);
         orc_spectral(N, MUL_FILTER, op, op);
         if (c == t_col)
             for (int i = 0; i < 2 * N; ++i) oe[i] += F[i] / T;
         free(psi); free(Gpsi); free(dpsi); free(a); free(b); free(e1);
     }
-    free(phi_p); free(Gphi); free(ux); free(vy); free(w3); free(tmp);
+    free(phi_p); free(Gphi); free(ux); free(vy); free(w3); free(tmp); free(etx);
     dtn_release(&s);
 }
 
@@ -764,4 +822,288 @@ double orc_energy(const orc_problem *p, const double *q)
     }
     free(Gphi); free(ex);
     return e * TWO_PI / N;
+}
+
+/* ------------------------------------------------------------------ */
+/* Time segments, adaptive meshes and a general explicit Runge-Kutta    */
+/* scheme (Sec. 2.2, Eq. (xi), Eq. (rho:def); DOP853 of Hairer et al.)  */
+/* ------------------------------------------------------------------ */
+
+/* One time segment: M grid points, a fixed number of uniform steps over the
+ * fraction theta of the simulated time T/4, and the mesh of Eq. (xi) with
+ * parameter rho (0 < rho <= 1; 1 = uniform) refined near x = pi (centre = 1,
+ * the sin^4 form) or near x = 0 (centre = 0, the cos^4 form). */
+typedef struct {
+    int M;
+    int steps;
+    double theta;
+    double rho;
+    int centre;
+} orc_segment;
+
+/* An explicit Runge-Kutta tableau: s stages, a (s x s, row-major, strictly
+ * lower triangular) and the weights b (s).  The equations are autonomous,
+ * so the nodes are not needed. */
+typedef struct {
+    int s;
+    const double *a, *b;
+} orc_tableau;
+
+/* Eq. (xi): E = 1 - P[A sin^4(alpha/2)] (or cos^4), A = 8 (1 - rho) / (5 + 3 rho).
+ * With sin^4(a/2) = 3/8 - cos(a)/2 + cos(2a)/8 and cos^4(a/2) = 3/8 + cos(a)/2
+ * + cos(2a)/8, P drops the 3/8 and xi = int_0^alpha E is a trigonometric
+ * polynomial in closed form.  Returns xi, E = xi' and E' = xi'' at alpha. */
+static void mesh_point(double rho, int centre, double alpha, double *xi, double *E, double *E1)
+{
+    double A = 8.0 * (1.0 - rho) / (5.0 + 3.0 * rho);
+    double s1 = sin(alpha), c1 = cos(alpha), s2 = sin(2.0 * alpha), c2 = cos(2.0 * alpha);
+    double sg = centre ? 1.0 : -1.0;       /* sign of the cos(alpha) term */
+    *xi = alpha + A * (sg * 0.5 * s1 - s2 / 16.0);
+    *E = 1.0 + A * (sg * 0.5 * c1 - c2 / 8.0);
+    *E1 = A * (-sg * 0.5 * s1 + s2 / 4.0);
+}
+
+/* Public: the mesh of a segment at alpha_j = 2 pi j / M. */
+void orc_mesh_eval(double rho, int centre, int M, double *x, double *e, double *e1)
+{
+    for (int j = 0; j < M; ++j) mesh_point(rho, centre, TWO_PI * j / M, x + j, e + j, e1 + j);
+}
+
+/* xi^{-1}(x) by Newton's method (Sec. 2.2), kept inside the bracket
+ * |alpha - x| <= A (|xi - alpha| <= 9A/16) by bisection when a step leaves it. */
+static double mesh_inverse_one(double rho, int centre, double x)
+{
+    double A = 8.0 * (1.0 - rho) / (5.0 + 3.0 * rho);
+    double lo = x - A - 1e-12, hi = x + A + 1e-12, a = x;
+    for (int it = 0; it < 200; ++it) {
+        double xi, E, E1;
+        mesh_point(rho, centre, a, &xi, &E, &E1);
+        double r = xi - x;
+        if (r == 0.0) break;
+        if (r > 0.0) hi = a; else lo = a;
+        double an = a - r / E;
+        if (!(an > lo && an < hi)) an = 0.5 * (lo + hi);
+        if (fabs(an - a) <= 4e-16 * (1.0 + fabs(a))) { a = an; break; }
+        a = an;
+    }
+    return a;
+}
+
+void orc_mesh_inverse(double rho, int centre, int n, const double *x, double *alpha)
+{
+    for (int i = 0; i < n; ++i) alpha[i] = mesh_inverse_one(rho, centre, x[i]);
+}
+
+/* The trigonometric interpolant of f (values at alpha_j = 2 pi j / M) at the
+ * points beta[0..n): sum over |k| < M/2 of fhat_k e^{i k beta} plus the
+ * Nyquist mode as fhat_{M/2} cos(M beta / 2) (reading R22); direct sums. */
+void orc_interp(int M, const double *f, int n, const double *beta, double *out)
+{
+    cplx *fh = malloc(sizeof(cplx) * M);
+    for (int j = 0; j < M; ++j) fh[j] = f[j];
+    orc_fft(M, fh, 0);
+    for (int j = 0; j < M; ++j) fh[j] /= M;
+    for (int i = 0; i < n; ++i) {
+        double acc = creal(fh[0]);
+        for (int k = 1; k < M / 2; ++k)
+            acc += 2.0 * creal(fh[k] * cexp(I * (double)k * beta[i]));
+        acc += creal(fh[M / 2]) * cos(0.5 * M * beta[i]);
+        out[i] = acc;
+    }
+    free(fh);
+}
+
+/* The segment's mesh as an orc_mesh (NULL when rho == 1: the uniform grid,
+ * so a uniform segment runs exactly the uniform arithmetic). */
+typedef struct {
+    orc_mesh m;
+    double *x, *e, *e1;
+} mesh_buf;
+
+static const orc_mesh *mesh_make(mesh_buf *b, const orc_segment *sg)
+{
+    b->x = b->e = b->e1 = NULL;
+    if (sg->rho == 1.0) return NULL;
+    b->x = malloc(sizeof(double) * sg->M);
+    b->e = malloc(sizeof(double) * sg->M);
+    b->e1 = malloc(sizeof(double) * sg->M);
+    orc_mesh_eval(sg->rho, sg->centre, sg->M, b->x, b->e, b->e1);
+    b->m.x = b->x; b->m.e = b->e; b->m.e1 = b->e1;
+    return &b->m;
+}
+
+static void mesh_free(mesh_buf *b) { free(b->x); free(b->e); free(b->e1); }
+
+/* Respacing (Sec. 2.2): the new values at alpha'_j (M' points of segment b)
+ * are those of the old interpolant at xi_a^{-1}(xi_b(alpha'_j)).  ncols
+ * vectors of length Ma in; ncols of length Mb out. */
+static void respace(const orc_segment *sa, const orc_segment *sb, int ncols, const double *in, double *out)
+{
+    int Ma = sa->M, Mb = sb->M;
+    double *beta = malloc(sizeof(double) * Mb);
+    for (int j = 0; j < Mb; ++j) {
+        double xi, E, E1;
+        mesh_point(sb->rho, sb->centre, TWO_PI * j / Mb, &xi, &E, &E1);
+        beta[j] = mesh_inverse_one(sa->rho, sa->centre, xi);
+    }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic)
+#endif
+    for (int c = 0; c < ncols; ++c) orc_interp(Ma, in + (size_t)c * Ma, Mb, beta, out + (size_t)c * Mb);
+    free(beta);
+}
+
+/* One segment: `steps` steps of the tableau of size dt on the mesh, the RHS
+ * filtered at every stage (inside rhs_impl) and the solution after every
+ * step (reading R4). */
+static void integrate_tableau(const orc_problem *p, const orc_mesh *m, int N, const orc_tableau *tb, double T,
+                              double dt, int steps, double *y, int ncol, int t_col)
+{
+    size_t len = (size_t)(ncol + 1) * 2 * N;
+    int s = tb->s;
+    double *k = malloc(sizeof(double) * len * s), *ys = malloc(sizeof(double) * len);
+    for (int n = 0; n < steps; ++n) {
+        for (int st = 0; st < s; ++st) {
+            for (size_t i = 0; i < len; ++i) {
+                double acc = 0.0;
+                for (int j = 0; j < st; ++j) acc += tb->a[st * s + j] * k[(size_t)j * len + i];
+                ys[i] = y[i] + dt * acc;
+            }
+            rhs_impl(p, m, N, T, ys, ncol, t_col, k + (size_t)st * len);
+        }
+        for (size_t i = 0; i < len; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < s; ++j) acc += tb->b[j] * k[(size_t)j * len + i];
+            y[i] += dt * acc;
+        }
+        for (int c = 0; c <= ncol; ++c) {
+            orc_spectral(N, MUL_FILTER, y + (size_t)c * 2 * N, y + (size_t)c * 2 * N);
+            orc_spectral(N, MUL_FILTER, y + (size_t)c * 2 * N + N, y + (size_t)c * 2 * N + N);
+        }
+    }
+    free(k); free(ys);
+}
+
+static int segments_valid(const orc_problem *p, int nseg, const orc_segment *sg, const orc_tableau *tb)
+{
+    if (nseg < 1 || !tb || tb->s < 1) return 0;
+    if (sg[0].M != p->N || sg[0].rho != 1.0) return 0;    /* x = alpha on the first segment */
+    double th = 0.0;
+    for (int l = 0; l < nseg; ++l) {
+        int M = sg[l].M;
+        if (M < 4 || (M & (M - 1)) || sg[l].steps < 1 || !(sg[l].theta > 0.0)) return 0;
+        if (!(sg[l].rho > 0.0 && sg[l].rho <= 1.0)) return 0;
+        th += sg[l].theta;
+    }
+    return fabs(th - 1.0) <= 1e-12;
+}
+
+/* Integrate y (ncol + 1 columns on segment 0's grid) through all segments
+ * from 0 to T/4; returns the state on the last segment's grid (malloc'd). */
+static double *integrate_segments(const orc_problem *p, int nseg, const orc_segment *sg, const orc_tableau *tb,
+                                  double T, const double *y0, int ncol, int t_col)
+{
+    size_t cols = (size_t)(ncol + 1) * 2;
+    double *y = malloc(sizeof(double) * cols * sg[0].M);
+    memcpy(y, y0, sizeof(double) * cols * sg[0].M);
+    for (int l = 0; l < nseg; ++l) {
+        if (l > 0) {
+            double *z = malloc(sizeof(double) * cols * sg[l].M);
+            respace(&sg[l - 1], &sg[l], (int)cols, y, z);
+            free(y);
+            y = z;
+        }
+        mesh_buf b;
+        const orc_mesh *m = mesh_make(&b, &sg[l]);
+        double dt = sg[l].theta * (T / 4.0) / sg[l].steps;
+        integrate_tableau(p, m, sg[l].M, tb, T, dt, sg[l].steps, y, ncol, t_col);
+        mesh_free(&b);
+    }
+    return y;
+}
+
+/* Residual weights on the last segment: w_i = sqrt(E(alpha_i) / M)
+ * (Eq. (f:phi) with the mesh density E). */
+static void segment_weights(const orc_segment *sl, double *w)
+{
+    for (int i = 0; i < sl->M; ++i) {
+        double xi, E, E1;
+        mesh_point(sl->rho, sl->centre, TWO_PI * i / sl->M, &xi, &E, &E1);
+        w[i] = sqrt(E / sl->M);
+    }
+}
+
+/* Public: evolve q0 (2N on segment 0) to T/4; q_end holds 2 M_last. */
+int orc_evolve_segments(const orc_problem *p, int nseg, const orc_segment *sg, const orc_tableau *tb, double T,
+                        const double *q0, double *q_end)
+{
+    if (!segments_valid(p, nseg, sg, tb)) return -1;
+    double *y = integrate_segments(p, nseg, sg, tb, T, q0, 0, 0);
+    memcpy(q_end, y, sizeof(double) * 2 * sg[nseg - 1].M);
+    free(y);
+    return 0;
+}
+
+/* Public: r (M_last) and f of the segmented shot. */
+int orc_shoot_segments(const orc_problem *p, int nseg, const orc_segment *sg, const orc_tableau *tb,
+                       const double *c, double *r, double *f)
+{
+    if (!segments_valid(p, nseg, sg, tb)) return -1;
+    int N = p->N, M = sg[nseg - 1].M;
+    double *q0 = malloc(sizeof(double) * 2 * N), *w = malloc(sizeof(double) * M);
+    orc_initial(p, c, q0);
+    double *y = integrate_segments(p, nseg, sg, tb, c[0], q0, 0, 0);
+    segment_weights(&sg[nseg - 1], w);
+    double s = 0.0;
+    for (int i = 0; i < M; ++i) { r[i] = w[i] * y[M + i]; s += r[i] * r[i]; }
+    *f = 0.5 * s;
+    free(q0); free(w); free(y);
+    return 0;
+}
+
+/* Public: r, J (M_last x (n + 1), column-major, column 0 = d r / d T) and f.
+ * The variational columns ride through the respacing with the base state:
+ * respacing is linear, so they stay the exact derivative of the discrete map. */
+int orc_shoot_jacobian_segments(const orc_problem *p, int nseg, const orc_segment *sg, const orc_tableau *tb,
+                                const double *c, double *r, double *J, double *f)
+{
+    if (!segments_valid(p, nseg, sg, tb)) return -1;
+    int N = p->N, n = p->n, ncol = n + 1, M = sg[nseg - 1].M;
+    double *y0 = calloc((size_t)(ncol + 1) * 2 * N, sizeof(double)), *w = malloc(sizeof(double) * M);
+    orc_initial(p, c, y0);
+    for (int k = 1; k <= n; ++k)
+        for (int rr = 0; rr < 2 * N; ++rr)
+            y0[(size_t)(k + 1) * 2 * N + rr] = basis_entry(p, rr, k);
+    double *y = integrate_segments(p, nseg, sg, tb, c[0], y0, ncol, 1);
+    segment_weights(&sg[nseg - 1], w);
+    double s = 0.0;
+    for (int i = 0; i < M; ++i) { r[i] = w[i] * y[M + i]; s += r[i] * r[i]; }
+    *f = 0.5 * s;
+    for (int k = 0; k <= n; ++k)
+        for (int i = 0; i < M; ++i)
+            J[(size_t)k * M + i] = w[i] * y[(size_t)(k + 1) * 2 * M + M + i];
+    free(y0); free(w); free(y);
+    return 0;
+}
+
+/* Public (tests): the RHS of ncol + 1 columns on the mesh of a segment. */
+void orc_rhs_segment(const orc_problem *p, const orc_segment *sg, double T, const double *y, int ncol, int t_col,
+                     double *out)
+{
+    mesh_buf b;
+    const orc_mesh *m = mesh_make(&b, sg);
+    rhs_impl(p, m, sg->M, T, y, ncol, t_col, out);
+    mesh_free(&b);
+}
+
+/* Public (tests): the DtN of phi on the surface eta, both stored on the mesh. */
+void orc_dtn_segment(const orc_segment *sg, double h, const double *eta, const double *phi, double *out)
+{
+    mesh_buf b;
+    const orc_mesh *m = mesh_make(&b, sg);
+    dtn_state s;
+    dtn_prepare_mesh(&s, m, sg->M, h, eta);
+    dtn_apply_one(&s, phi, out);
+    dtn_release(&s);
+    mesh_free(&b);
 }

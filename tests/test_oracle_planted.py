@@ -80,6 +80,41 @@ def adjoint_gap(L, N=32, n=6, steps=12):
     return np.linalg.norm(g - jtr) / np.linalg.norm(jtr)
 
 
+def mesh_dtn_error(L, N=64, rho=0.3, k=2):
+    """The DtN on a mesh against the analytic potential cos(kz) (finite depth)."""
+    x = np.empty(N); e = np.empty(N); e1 = np.empty(N)
+    L.orc_mesh_eval(rho, 1, N, O._p(x), O._p(e), O._p(e1))
+    eta = 1.0 + 0.15 * np.cos(x) + 0.03 * np.cos(2 * x) - 0.02 * np.cos(3 * x)
+    ex = -0.15 * np.sin(x) - 0.06 * np.sin(2 * x) + 0.06 * np.sin(3 * x)
+    z = x + 1j * eta
+    phi = np.ascontiguousarray(np.cos(k * z).real)
+    d = -k * np.sin(k * z)
+    out = np.empty(N)
+    L.orc_dtn_segment(O._segments([(N, 1, 1.0, rho)]), 1.0, O._p(eta), O._p(phi), O._p(out))
+    return np.max(np.abs(out - (d.imag * -1.0 - ex * d.real)))
+
+
+def mesh_rhs_gap(L, N=64, rho=0.4):
+    """The RHS on a mesh against the uniform RHS (N = 128) interpolated to the mesh."""
+    import ctypes as C
+    eta_f = lambda s: 1.0 + 0.08 * np.cos(s) + 0.02 * np.cos(2 * s) - 0.01 * np.sin(3 * s)
+    phi_f = lambda s: 0.05 * np.cos(s) - 0.01 * np.cos(3 * s) + 0.004 * np.sin(2 * s)
+    Nu = 128
+    probu, _ = O.make_problem(Nu, 0, h=1.0, tau=0.05)
+    xu = x_grid(Nu)
+    yu = np.concatenate([eta_f(xu), phi_f(xu)])
+    Fu = np.empty(2 * Nu)
+    L.orc_rhs(C.byref(probu), 7.0, O._p(yu), 0, 0, O._p(Fu))
+    x = np.empty(N); e = np.empty(N); e1 = np.empty(N)
+    L.orc_mesh_eval(rho, 1, N, O._p(x), O._p(e), O._p(e1))
+    prob, _ = O.make_problem(N, 0, h=1.0, tau=0.05)
+    y = np.concatenate([eta_f(x), phi_f(x)])
+    F = np.empty(2 * N)
+    L.orc_rhs_segment(C.byref(prob), O._segments([(N, 1, 1.0, rho)]), 7.0, O._p(y), 0, 0, O._p(F))
+    ref = np.concatenate([O.interp(Fu[:Nu], x), O.interp(Fu[Nu:], x)])
+    return np.max(np.abs(F - ref))
+
+
 @pytest.fixture(scope="module")
 def good():
     return O.load(O.build())
@@ -91,6 +126,8 @@ def good():
     (3, dispersion_rest, 5e-3),         # gravity dropped
     (4, linearisation_gap, 1e-8),       # u psi' dropped from Eq. (l6a)
     (5, adjoint_gap, 1e-13),            # forward DtN used as its own transpose
+    (6, mesh_dtn_error, 5e-12),         # 1/|xi'| of Eq. (G) dropped on a mesh
+    (7, mesh_rhs_gap, 2e-12),           # P as the alpha-mean on a mesh
 ])
 def test_pin_catches_planted_mistake(good, plant, probe, bound):
     assert probe(good) < bound
