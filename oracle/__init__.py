@@ -32,6 +32,9 @@ the paper the C function follows:
                         shot over time segments with their own grids, meshes
                         and step counts (Sec. 2.2), any tableau
 * ``rhs_segment``, ``dtn_segment`` -- the RHS and the DtN on a segment's mesh
+* ``wide_*``         -- the same C compiled with long double (x87 extended on
+                        x86-64, binary128 on aarch64): the double build's own
+                        rounding error on the same discrete map
 """
 from __future__ import annotations
 
@@ -50,15 +53,18 @@ _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False, plant: int = 0) -> str:
+def build(force: bool = False, plant: int = 0, wide: bool = False) -> str:
     """Compile ww_oracle.c into oracle/_build/libww_oracle.so (gcc -O2 -fopenmp).
-    plant > 0 builds a deliberately wrong variant (tests of the pins only)."""
+    plant > 0 builds a deliberately wrong variant (tests of the pins only);
+    wide builds the same arithmetic in long double (ORC_WIDE)."""
     os.makedirs(_BUILD, exist_ok=True)
     lib_path = _LIB if plant == 0 else os.path.join(_BUILD, f"libww_oracle_plant{plant}.so")
+    if wide:
+        lib_path = os.path.join(_BUILD, "libww_oracle_wide.so")
     if force or not os.path.exists(lib_path) or os.path.getmtime(lib_path) < os.path.getmtime(_SRC):
         tmp = lib_path + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", f"-DORC_PLANT={int(plant)}", _SRC,
-               "-o", tmp, "-lm"]
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", f"-DORC_PLANT={int(plant)}"] + \
+              (["-DORC_WIDE"] if wide else []) + [_SRC, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, lib_path)
     return lib_path
@@ -403,4 +409,82 @@ def dtn_segment(seg, h: float, eta, phi) -> np.ndarray:
     eta, phi = _f64(eta), _f64(phi)
     out = np.empty(eta.size)
     lib().orc_dtn_segment(sa, float(h), _p(eta), _p(phi), _p(out))
+    return out
+
+
+# ------------------------------------------------------------ the long double build
+class WideProblem(C.Structure):
+    _fields_ = [
+        ("N", C.c_int), ("n", C.c_int), ("g", C.c_longdouble), ("tau", C.c_longdouble),
+        ("h", C.c_longdouble), ("steps", C.c_int), ("basis", C.POINTER(C.c_longdouble)),
+    ]
+
+
+_L = C.POINTER(C.c_longdouble)
+_wide = None
+
+
+def wide_available() -> bool:
+    """True where long double carries more precision than double."""
+    return np.finfo(np.longdouble).eps < np.finfo(np.float64).eps
+
+
+def wide_lib():
+    global _wide
+    with _lock:
+        if _wide is None:
+            L = C.CDLL(build(wide=True))
+            P = C.POINTER(WideProblem)
+            for name, (res, args) in {
+                "orc_shoot": (None, [P, _L, _L, _L]),
+                "orc_shoot_jacobian": (None, [P, _L, _L, _L, _L]),
+                "orc_evolve": (None, [P, C.c_longdouble, _L, _L]),
+                "orc_initial": (None, [P, _L, _L]),
+                "orc_dtn": (None, [C.c_int, C.c_longdouble, _L, _L, C.c_int, _L]),
+            }.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _wide = L
+    return _wide
+
+
+def _lp(a: np.ndarray):
+    return a.ctypes.data_as(_L)
+
+
+def _ld(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.longdouble))
+
+
+def wide_problem(N, n, g=1.0, tau=0.0, h=1.0, steps=64, basis=None):
+    """As make_problem, for the long double build (values converted exactly from double)."""
+    keep = None
+    bp = C.cast(None, _L)
+    if basis is not None:
+        keep = _ld(np.asarray(basis, dtype=np.float64).T)      # column k contiguous
+        bp = _lp(keep)
+    return WideProblem(int(N), int(n), g, tau, h, int(steps), bp), keep
+
+
+def wide_shoot(prob: WideProblem, c):
+    c = _ld(c)
+    r, f = np.empty(prob.N, dtype=np.longdouble), np.empty(1, dtype=np.longdouble)
+    wide_lib().orc_shoot(C.byref(prob), _lp(c), _lp(r), _lp(f))
+    return r, f[0]
+
+
+def wide_shoot_jacobian(prob: WideProblem, c):
+    c = _ld(c)
+    N, n = prob.N, prob.n
+    r, f = np.empty(N, dtype=np.longdouble), np.empty(1, dtype=np.longdouble)
+    Jc = np.empty((n + 1, N), dtype=np.longdouble)
+    wide_lib().orc_shoot_jacobian(C.byref(prob), _lp(c), _lp(r), _lp(Jc), _lp(f))
+    return r, Jc.T.copy(), f[0]
+
+
+def wide_dtn(eta, phi, h) -> np.ndarray:
+    eta, phi = _ld(eta), _ld(phi)
+    out = np.empty(eta.size, dtype=np.longdouble)
+    wide_lib().orc_dtn(eta.size, h, _lp(eta), _lp(phi), 1, _lp(out))
     return out

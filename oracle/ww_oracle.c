@@ -59,16 +59,39 @@
 #define ORC_PLANT 0
 #endif
 
-#include <complex.h>
-#include <math.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* The real type: IEEE double, or with ORC_WIDE the platform's long double
+ * (x87 80-bit extended on x86-64, IEEE binary128 on aarch64), used only to
+ * measure the double build's own rounding error on the same discrete map.
+ * <tgmath.h> then selects each math function's long double form. */
+#ifdef ORC_WIDE
+#include <float.h>
+#include <tgmath.h>
+typedef long double real;
+typedef long double complex cplx;
+#define RL(x) x##L
+#define CCOS(z) cos(z)
+#define CSIN(z) sin(z)
+#define CEXP(z) exp(z)
+#define NEWTON_TOL (4 * LDBL_EPSILON)
+#else
+#include <complex.h>
+#include <math.h>
+typedef double real;
+typedef double complex cplx;
+#define RL(x) x
+#define CCOS(z) ccos(z)
+#define CSIN(z) csin(z)
+#define CEXP(z) cexp(z)
+#define NEWTON_TOL 4e-16
+#endif
 
 #ifdef _OPENMP
 #include <omp.h>
 #endif
 
-typedef double complex cplx;
 
 /* ------------------------------------------------------------------ */
 /* Problem description (oracle-side copy; the CUDA path has its own). */
@@ -76,15 +99,15 @@ typedef double complex cplx;
 typedef struct {
     int N;          /* grid points alpha_j = 2 pi j / N (uniform, xi = alpha)   */
     int n;          /* number of mode unknowns c_1..c_n                         */
-    double g;       /* gravity                                                  */
-    double tau;     /* surface tension sigma/rho                                */
-    double h;       /* mean depth; isinf(h) => infinite depth, no image kernels */
+    real g;       /* gravity                                                  */
+    real tau;     /* surface tension sigma/rho                                */
+    real h;       /* mean depth; isinf(h) => infinite depth, no image kernels */
     int steps;      /* RK4 steps from 0 to T/4                                  */
-    const double *basis; /* 2N x n column-major (eta rows, then phi rows) or NULL
+    const real *basis; /* 2N x n column-major (eta rows, then phi rows) or NULL
                             for the default column k = (cos kx, 0)             */
 } orc_problem;
 
-static const double TWO_PI = 6.283185307179586476925286766559;
+static const real TWO_PI = RL(6.283185307179586476925286766559);
 
 int orc_threads(void)
 {
@@ -117,12 +140,12 @@ void orc_fft(int N, cplx *x, int inverse)
         j ^= bit;
         if (i < j) { cplx t = x[i]; x[i] = x[j]; x[j] = t; }
     }
-    double sgn = inverse ? 1.0 : -1.0;
+    real sgn = inverse ? 1.0 : -1.0;
     for (int len = 2; len <= N; len <<= 1) {
         int half = len >> 1;
         for (int s = 0; s < N; s += len) {
             for (int k = 0; k < half; ++k) {
-                double ang = sgn * TWO_PI * (double)k / (double)len;
+                real ang = sgn * TWO_PI * (real)k / (real)len;
                 cplx w = cos(ang) + I * sin(ang);
                 cplx u = x[s + k];
                 cplx v = x[s + k + half] * w;
@@ -132,7 +155,7 @@ void orc_fft(int N, cplx *x, int inverse)
         }
     }
     if (inverse)
-        for (int i = 0; i < N; ++i) x[i] /= (double)N;
+        for (int i = 0; i < N; ++i) x[i] /= (real)N;
 }
 
 /* signed wavenumber of FFT slot j */
@@ -145,10 +168,10 @@ static cplx multiplier(int kind, int N, int k)
 {
     int nyq = (k == N / 2 || k == -N / 2);
     switch (kind) {
-    case MUL_DERIV:   return nyq ? 0.0 : I * (double)k;               /* d/dx     */
-    case MUL_HILBERT: return nyq ? 0.0 : -I * (double)((k > 0) - (k < 0)); /* H   */
+    case MUL_DERIV:   return nyq ? 0.0 : I * (real)k;               /* d/dx     */
+    case MUL_HILBERT: return nyq ? 0.0 : -I * (real)((k > 0) - (k < 0)); /* H   */
     case MUL_FILTER: {                                                 /* Eq. (filter) */
-        double r = fabs((double)k) / (double)(N / 2);
+        real r = fabs((real)k) / (real)(N / 2);
         return exp(-36.0 * pow(r, 36.0));
     }
     case MUL_PROJECT: return k == 0 ? 0.0 : 1.0;                       /* P = id - P0 */
@@ -157,7 +180,7 @@ static cplx multiplier(int kind, int N, int k)
 }
 
 /* out = Re IFFT( m(k) * FFT(in) ); in and out may alias */
-void orc_spectral(int N, int kind, const double *in, double *out)
+void orc_spectral(int N, int kind, const real *in, real *out)
 {
     cplx *x = malloc(sizeof(cplx) * N);
     for (int j = 0; j < N; ++j) x[j] = in[j];
@@ -173,11 +196,11 @@ void orc_spectral(int N, int kind, const double *in, double *out)
  * > 0, e1[j] = xi''(alpha_j).  Every function on the surface is stored as its
  * values at x = xi(alpha_j); a NULL mesh is the uniform grid xi = alpha. */
 typedef struct {
-    const double *x, *e, *e1;
+    const real *x, *e, *e1;
 } orc_mesh;
 
 /* d/dx of a function stored on the mesh: (d/dalpha f) / xi'. */
-static void mesh_dx(const orc_mesh *m, int N, const double *in, double *out)
+static void mesh_dx(const orc_mesh *m, int N, const real *in, real *out)
 {
     orc_spectral(N, MUL_DERIV, in, out);
     if (m)
@@ -187,10 +210,10 @@ static void mesh_dx(const orc_mesh *m, int N, const double *in, double *out)
 /* P = id - P0 with P0 f = (1/2 pi) int f(x) dx (Sec. 2.1).  On the mesh the
  * integral is int f(xi(alpha)) xi'(alpha) dalpha, by the trapezoid rule in
  * alpha (reading R22); on the uniform grid it is the k = 0 mode. */
-static void mesh_project(const orc_mesh *m, int N, const double *in, double *out)
+static void mesh_project(const orc_mesh *m, int N, const real *in, real *out)
 {
     if (!m || ORC_PLANT == 7) { orc_spectral(N, MUL_PROJECT, in, out); return; }
-    double s = 0.0;
+    real s = 0.0;
     for (int i = 0; i < N; ++i) s += in[i] * m->e[i];
     s /= N;
     for (int i = 0; i < N; ++i) out[i] = in[i] - s;
@@ -199,29 +222,29 @@ static void mesh_project(const orc_mesh *m, int N, const double *in, double *out
 /* ------------------------------------------------------------------ */
 /* Kernel assembly, Eq. (K1K2) with reading R1; trapezoid rule (Sec. 2.2) */
 /* ------------------------------------------------------------------ */
-static cplx ccot(cplx z) { return ccos(z) / csin(z); }
+static cplx ccot(cplx z) { return CCOS(z) / CSIN(z); }
 
 /* A = 1/2 I + K and G, both row-major N x N: row i = collocation point
  * alpha_i, column j = quadrature point beta = alpha_j; entries divided by N.
  * zeta = xi + i eta (Eq. (zeta)); eta_a, eta_aa are alpha-derivatives of the
  * stored eta.  The subtracted cot((alpha - beta)/2) stays in alpha. */
-static void assemble_mesh(int N, double h, const orc_mesh *m, const double *eta, const double *eta_a,
-                          const double *eta_aa, double *A, double *G)
+static void assemble_mesh(int N, real h, const orc_mesh *m, const real *eta, const real *eta_a,
+                          const real *eta_aa, real *A, real *G)
 {
     int deep = isinf(h);
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static)
 #endif
     for (int i = 0; i < N; ++i) {
-        double ai = TWO_PI * i / N;
+        real ai = TWO_PI * i / N;
         cplx zi = (m ? m->x[i] : ai) + I * eta[i];
         cplx dzi = (m ? m->e[i] : 1.0) + I * eta_a[i];
         cplx ddzi = m ? m->e1[i] + I * eta_aa[i] : I * eta_aa[i];
         for (int j = 0; j < N; ++j) {
-            double aj = TWO_PI * j / N;
+            real aj = TWO_PI * j / N;
             cplx zj = (m ? m->x[j] : aj) + I * eta[j];
             cplx dzj = (m ? m->e[j] : 1.0) + I * eta_a[j];
-            double k1, g1, k2 = 0.0, g2 = 0.0;
+            real k1, g1, k2 = 0.0, g2 = 0.0;
             if (i == j) {                       /* diagonal limits, Sec. 2.2 */
                 k1 = -cimag(ddzi / (2.0 * dzi));
                 g1 = creal(ddzi / (2.0 * dzi));
@@ -233,7 +256,7 @@ static void assemble_mesh(int N, double h, const orc_mesh *m, const double *eta,
             }
             if (!deep) {                        /* mirror image, reading R1 */
                 cplx cb = ccot((zi - conj(zj)) / 2.0);
-                double sgn = ORC_PLANT == 1 ? -1.0 : 1.0;
+                real sgn = ORC_PLANT == 1 ? -1.0 : 1.0;
                 k2 = -sgn * cimag(conj(dzj) / 2.0 * cb);
                 g2 = -sgn * creal(dzi / 2.0 * cb);
             }
@@ -243,8 +266,8 @@ static void assemble_mesh(int N, double h, const orc_mesh *m, const double *eta,
     }
 }
 
-void orc_assemble(int N, double h, const double *eta, const double *eta_x,
-                  const double *eta_xx, double *A, double *G)
+void orc_assemble(int N, real h, const real *eta, const real *eta_x,
+                  const real *eta_xx, real *A, real *G)
 {
     assemble_mesh(N, h, NULL, eta, eta_x, eta_xx, A, G);
 }
@@ -252,30 +275,30 @@ void orc_assemble(int N, double h, const double *eta, const double *eta_x,
 /* ------------------------------------------------------------------ */
 /* LU with partial pivoting (row-major, in place) and solve.            */
 /* ------------------------------------------------------------------ */
-int orc_lu(int N, double *A, int *piv)
+int orc_lu(int N, real *A, int *piv)
 {
     for (int k = 0; k < N; ++k) {
         int p = k;
-        double best = fabs(A[(size_t)k * N + k]);
+        real best = fabs(A[(size_t)k * N + k]);
         for (int i = k + 1; i < N; ++i)
             if (fabs(A[(size_t)i * N + k]) > best) { best = fabs(A[(size_t)i * N + k]); p = i; }
         piv[k] = p;
         if (best == 0.0) return -1;
         if (p != k)
             for (int j = 0; j < N; ++j) {
-                double t = A[(size_t)k * N + j];
+                real t = A[(size_t)k * N + j];
                 A[(size_t)k * N + j] = A[(size_t)p * N + j];
                 A[(size_t)p * N + j] = t;
             }
-        double d = A[(size_t)k * N + k];
+        real d = A[(size_t)k * N + k];
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static) if (N - k > 256)
 #endif
         for (int i = k + 1; i < N; ++i) {
-            double l = A[(size_t)i * N + k] / d;
+            real l = A[(size_t)i * N + k] / d;
             A[(size_t)i * N + k] = l;
-            double *ri = A + (size_t)i * N;
-            const double *rk = A + (size_t)k * N;
+            real *ri = A + (size_t)i * N;
+            const real *rk = A + (size_t)k * N;
             for (int j = k + 1; j < N; ++j) ri[j] -= l * rk[j];
         }
     }
@@ -283,18 +306,18 @@ int orc_lu(int N, double *A, int *piv)
 }
 
 /* x = A^{-1} b using the factors of orc_lu; b and x may alias */
-void orc_lu_solve(int N, const double *LU, const int *piv, const double *b, double *x)
+void orc_lu_solve(int N, const real *LU, const int *piv, const real *b, real *x)
 {
-    if (x != b) memcpy(x, b, sizeof(double) * N);
+    if (x != b) memcpy(x, b, sizeof(real) * N);
     for (int k = 0; k < N; ++k)
-        if (piv[k] != k) { double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
+        if (piv[k] != k) { real t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
     for (int i = 0; i < N; ++i) {            /* unit lower */
-        double s = x[i];
+        real s = x[i];
         for (int j = 0; j < i; ++j) s -= LU[(size_t)i * N + j] * x[j];
         x[i] = s;
     }
     for (int i = N - 1; i >= 0; --i) {       /* upper */
-        double s = x[i];
+        real s = x[i];
         for (int j = i + 1; j < N; ++j) s -= LU[(size_t)i * N + j] * x[j];
         x[i] = s / LU[(size_t)i * N + i];
     }
@@ -303,21 +326,21 @@ void orc_lu_solve(int N, const double *LU, const int *piv, const double *b, doub
 /* x = A^{-T} b using the factors of orc_lu: P A = L U, so A^T = U^T L^T P
  * (solve with U^T, then the unit L^T, then undo the interchanges in reverse
  * order); b and x may alias */
-void orc_lu_solve_T(int N, const double *LU, const int *piv, const double *b, double *x)
+void orc_lu_solve_T(int N, const real *LU, const int *piv, const real *b, real *x)
 {
-    if (x != b) memcpy(x, b, sizeof(double) * N);
+    if (x != b) memcpy(x, b, sizeof(real) * N);
     for (int i = 0; i < N; ++i) {            /* U^T: lower, diagonal U_ii */
-        double s = x[i];
+        real s = x[i];
         for (int j = 0; j < i; ++j) s -= LU[(size_t)j * N + i] * x[j];
         x[i] = s / LU[(size_t)i * N + i];
     }
     for (int i = N - 1; i >= 0; --i) {       /* L^T: unit upper */
-        double s = x[i];
+        real s = x[i];
         for (int j = i + 1; j < N; ++j) s -= LU[(size_t)j * N + i] * x[j];
         x[i] = s;
     }
     for (int k = N - 1; k >= 0; --k)
-        if (piv[k] != k) { double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
+        if (piv[k] != k) { real t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
 }
 
 /* ------------------------------------------------------------------ */
@@ -326,29 +349,29 @@ void orc_lu_solve_T(int N, const double *LU, const int *piv, const double *b, do
 typedef struct {
     int N;
     const orc_mesh *m;              /* NULL: uniform grid */
-    double *eta, *eta_x, *eta_xx;   /* eta and its alpha-derivatives */
-    double *LU, *G;
+    real *eta, *eta_x, *eta_xx;   /* eta and its alpha-derivatives */
+    real *LU, *G;
     int *piv;
 } dtn_state;
 
-static void dtn_prepare_mesh(dtn_state *s, const orc_mesh *m, int N, double h, const double *eta)
+static void dtn_prepare_mesh(dtn_state *s, const orc_mesh *m, int N, real h, const real *eta)
 {
     s->N = N;
     s->m = m;
-    s->eta = malloc(sizeof(double) * N);
-    s->eta_x = malloc(sizeof(double) * N);
-    s->eta_xx = malloc(sizeof(double) * N);
-    s->LU = malloc(sizeof(double) * (size_t)N * N);
-    s->G = malloc(sizeof(double) * (size_t)N * N);
+    s->eta = malloc(sizeof(real) * N);
+    s->eta_x = malloc(sizeof(real) * N);
+    s->eta_xx = malloc(sizeof(real) * N);
+    s->LU = malloc(sizeof(real) * (size_t)N * N);
+    s->G = malloc(sizeof(real) * (size_t)N * N);
     s->piv = malloc(sizeof(int) * N);
-    memcpy(s->eta, eta, sizeof(double) * N);
+    memcpy(s->eta, eta, sizeof(real) * N);
     orc_spectral(N, MUL_DERIV, eta, s->eta_x);
     orc_spectral(N, MUL_DERIV, s->eta_x, s->eta_xx);
     assemble_mesh(N, h, m, s->eta, s->eta_x, s->eta_xx, s->LU, s->G);
     orc_lu(N, s->LU, s->piv);
 }
 
-static void dtn_prepare(dtn_state *s, int N, double h, const double *eta)
+static void dtn_prepare(dtn_state *s, int N, real h, const real *eta)
 {
     dtn_prepare_mesh(s, NULL, N, h, eta);
 }
@@ -361,17 +384,17 @@ static void dtn_release(dtn_state *s)
 
 /* G phi on the surface (Eq. (G)): mu = A^{-1} phi; gamma = mu' (in alpha);
  * (1/2 H gamma + G gamma) / |xi'| (xi' = 1 on the uniform grid). */
-static void dtn_apply_one(const dtn_state *s, const double *phi, double *out)
+static void dtn_apply_one(const dtn_state *s, const real *phi, real *out)
 {
     int N = s->N;
-    double *mu = malloc(sizeof(double) * N);
-    double *gam = malloc(sizeof(double) * N);
-    double *hg = malloc(sizeof(double) * N);
+    real *mu = malloc(sizeof(real) * N);
+    real *gam = malloc(sizeof(real) * N);
+    real *hg = malloc(sizeof(real) * N);
     orc_lu_solve(N, s->LU, s->piv, phi, mu);
     orc_spectral(N, MUL_DERIV, mu, gam);
     orc_spectral(N, MUL_HILBERT, gam, hg);
     for (int i = 0; i < N; ++i) {
-        double acc = 0.0;
+        real acc = 0.0;
         for (int j = 0; j < N; ++j) acc += s->G[(size_t)i * N + j] * gam[j];
         out[i] = 0.5 * hg[i] + acc;
         if (s->m && ORC_PLANT != 6) out[i] /= s->m->e[i];
@@ -383,15 +406,15 @@ static void dtn_apply_one(const dtn_state *s, const double *phi, double *out)
  * G phi = (1/2 H + G) D A^{-1} phi.  The Fourier multipliers ik and -i sgn k
  * (Nyquist zeroed) are antisymmetric, D^T = -D and H^T = -H, so
  * G^T x = A^{-T} D (1/2 H x - G^T x). */
-static void dtn_apply_T(const dtn_state *s, const double *x, double *out)
+static void dtn_apply_T(const dtn_state *s, const real *x, real *out)
 {
     int N = s->N;
     if (ORC_PLANT == 5) { dtn_apply_one(s, x, out); return; }
-    double *hx = malloc(sizeof(double) * N);
-    double *t = malloc(sizeof(double) * N);
+    real *hx = malloc(sizeof(real) * N);
+    real *t = malloc(sizeof(real) * N);
     orc_spectral(N, MUL_HILBERT, x, hx);
     for (int i = 0; i < N; ++i) {
-        double acc = 0.0;
+        real acc = 0.0;
         for (int j = 0; j < N; ++j) acc += s->G[(size_t)j * N + i] * x[j];
         t[i] = 0.5 * hx[i] - acc;
     }
@@ -401,7 +424,7 @@ static void dtn_apply_T(const dtn_state *s, const double *x, double *out)
 }
 
 /* Public: the transposed DtN of x on surface eta (tests). */
-void orc_dtn_T(int N, double h, const double *eta, const double *x, double *out)
+void orc_dtn_T(int N, real h, const real *eta, const real *x, real *out)
 {
     dtn_state s;
     dtn_prepare(&s, N, h, eta);
@@ -410,7 +433,7 @@ void orc_dtn_T(int N, double h, const double *eta, const double *x, double *out)
 }
 
 /* Public: DtN of phi (nrhs columns, each length N, contiguous) on surface eta. */
-void orc_dtn(int N, double h, const double *eta, const double *phi, int nrhs, double *out)
+void orc_dtn(int N, real h, const real *eta, const real *phi, int nrhs, real *out)
 {
     dtn_state s;
     dtn_prepare(&s, N, h, eta);
@@ -423,9 +446,9 @@ void orc_dtn(int N, double h, const double *eta, const double *phi, int nrhs, do
 }
 
 /* Public: the assembled matrices (for tests). */
-void orc_dtn_matrices(int N, double h, const double *eta, double *A, double *G)
+void orc_dtn_matrices(int N, real h, const real *eta, real *A, real *G)
 {
-    double *ex = malloc(sizeof(double) * N), *exx = malloc(sizeof(double) * N);
+    real *ex = malloc(sizeof(real) * N), *exx = malloc(sizeof(real) * N);
     orc_spectral(N, MUL_DERIV, eta, ex);
     orc_spectral(N, MUL_DERIV, ex, exx);
     orc_assemble(N, h, eta, ex, exx, A, G);
@@ -444,9 +467,9 @@ void orc_dtn_matrices(int N, double h, const double *eta, double *A, double *G)
 /* Evaluate the filtered RHS of the base state and of ncol variational
  * columns.  t_col: index (1-based among the variational columns) of the
  * column that additionally receives F(q)/T (reading R2), or 0 for none. */
-static void rhs_impl(const orc_problem *p, const orc_mesh *m, int N, double T, const double *y, int ncol,
-                     int t_col, double *out);
-void orc_rhs(const orc_problem *p, double T, const double *y, int ncol, int t_col, double *out)
+static void rhs_impl(const orc_problem *p, const orc_mesh *m, int N, real T, const real *y, int ncol,
+                     int t_col, real *out);
+void orc_rhs(const orc_problem *p, real T, const real *y, int ncol, int t_col, real *out)
 {
     rhs_impl(p, NULL, p->N, T, y, ncol, t_col, out);
 }
@@ -454,36 +477,36 @@ void orc_rhs(const orc_problem *p, double T, const double *y, int ncol, int t_co
 /* The same on N points of a mesh (NULL: uniform): every x-derivative is
  * d/dalpha over xi', P subtracts the x-mean, the filter acts on the alpha
  * grid's Fourier modes (Sec. 2.2). */
-static void rhs_impl(const orc_problem *p, const orc_mesh *m, int N, double T, const double *y, int ncol,
-                     int t_col, double *out)
+static void rhs_impl(const orc_problem *p, const orc_mesh *m, int N, real T, const real *y, int ncol,
+                     int t_col, real *out)
 {
-    const double *eta = y, *phi = y + N;
+    const real *eta = y, *phi = y + N;
     dtn_state s;
     dtn_prepare_mesh(&s, m, N, p->h, eta);
 
-    double *phi_p = malloc(sizeof(double) * N);
-    double *Gphi = malloc(sizeof(double) * N);
-    double *ux = malloc(sizeof(double) * N);  /* phi_x on the surface */
-    double *vy = malloc(sizeof(double) * N);  /* phi_y on the surface */
-    double *w3 = malloc(sizeof(double) * N);  /* (1 + eta'^2)^{-3/2} */
-    double *tmp = malloc(sizeof(double) * N);
-    double *etx = malloc(sizeof(double) * N); /* eta' = d eta / dx */
+    real *phi_p = malloc(sizeof(real) * N);
+    real *Gphi = malloc(sizeof(real) * N);
+    real *ux = malloc(sizeof(real) * N);  /* phi_x on the surface */
+    real *vy = malloc(sizeof(real) * N);  /* phi_y on the surface */
+    real *w3 = malloc(sizeof(real) * N);  /* (1 + eta'^2)^{-3/2} */
+    real *tmp = malloc(sizeof(real) * N);
+    real *etx = malloc(sizeof(real) * N); /* eta' = d eta / dx */
 
     mesh_dx(m, N, phi, phi_p);
     for (int i = 0; i < N; ++i) etx[i] = m ? s.eta_x[i] / m->e[i] : s.eta_x[i];
     dtn_apply_one(&s, phi, Gphi);
     for (int i = 0; i < N; ++i) {              /* Eq. (uv:from:G) */
-        double ex = etx[i], d = 1.0 + ex * ex;
+        real ex = etx[i], d = 1.0 + ex * ex;
         ux[i] = (phi_p[i] - ex * Gphi[i]) / d;
         vy[i] = (ex * phi_p[i] + Gphi[i]) / d;
         w3[i] = 1.0 / (d * sqrt(d));
     }
 
     /* base: eta_t = G phi ; phi_t = P[ v eta_t - u^2/2 - v^2/2 - g eta + tau d/dx(eta'/sqrt(1+eta'^2)) ] */
-    double *F = out;                 /* column 0 of out */
+    real *F = out;                 /* column 0 of out */
     for (int i = 0; i < N; ++i) F[i] = Gphi[i];
     for (int i = 0; i < N; ++i) {
-        double ex = etx[i];
+        real ex = etx[i];
         tmp[i] = ex / sqrt(1.0 + ex * ex);
     }
     mesh_dx(m, N, tmp, tmp);
@@ -498,11 +521,11 @@ static void rhs_impl(const orc_problem *p, const orc_mesh *m, int N, double T, c
 #pragma omp parallel for schedule(dynamic)
 #endif
     for (int c = 1; c <= ncol; ++c) {
-        const double *ed = y + (size_t)c * 2 * N, *pd = ed + N;
-        double *oe = out + (size_t)c * 2 * N, *op = oe + N;
-        double *psi = malloc(sizeof(double) * N), *Gpsi = malloc(sizeof(double) * N);
-        double *dpsi = malloc(sizeof(double) * N), *a = malloc(sizeof(double) * N);
-        double *b = malloc(sizeof(double) * N), *e1 = malloc(sizeof(double) * N);
+        const real *ed = y + (size_t)c * 2 * N, *pd = ed + N;
+        real *oe = out + (size_t)c * 2 * N, *op = oe + N;
+        real *psi = malloc(sizeof(real) * N), *Gpsi = malloc(sizeof(real) * N);
+        real *dpsi = malloc(sizeof(real) * N), *a = malloc(sizeof(real) * N);
+        real *b = malloc(sizeof(real) * N), *e1 = malloc(sizeof(real) * N);
         /* psi = phidot - phi_y etadot : the perturbation potential on the surface */
         for (int i = 0; i < N; ++i) psi[i] = pd[i] - vy[i] * ed[i];
         dtn_apply_one(&s, psi, Gpsi);
@@ -535,21 +558,21 @@ static void rhs_impl(const orc_problem *p, const orc_mesh *m, int N, double T, c
 /* ------------------------------------------------------------------ */
 /* Initial data (Sec. 3.1, reading of the basis) and RK4 (classic)       */
 /* ------------------------------------------------------------------ */
-static double basis_entry(const orc_problem *p, int row, int k /* 1..n */)
+static real basis_entry(const orc_problem *p, int row, int k /* 1..n */)
 {
     int N = p->N;
     if (p->basis) return p->basis[(size_t)(k - 1) * 2 * N + row];
     if (row >= N) return 0.0;
-    return cos((double)k * TWO_PI * row / N);
+    return cos((real)k * TWO_PI * row / N);
 }
 
 /* q0 = (mean + sum c_k B_eta[:,k], sum c_k B_phi[:,k]) */
-void orc_initial(const orc_problem *p, const double *c, double *q0)
+void orc_initial(const orc_problem *p, const real *c, real *q0)
 {
     int N = p->N;
-    double mean = isinf(p->h) ? 0.0 : p->h;
+    real mean = isinf(p->h) ? 0.0 : p->h;
     for (int r = 0; r < 2 * N; ++r) {
-        double s = r < N ? mean : 0.0;
+        real s = r < N ? mean : 0.0;
         for (int k = 1; k <= p->n; ++k) s += c[k] * basis_entry(p, r, k);
         q0[r] = s;
     }
@@ -558,25 +581,25 @@ void orc_initial(const orc_problem *p, const double *c, double *q0)
 /* Integrate base + ncol variational columns from 0 to T/4 with p->steps RK4
  * steps; y holds the initial data on entry and the final data on exit.  rec
  * (NULL or (steps + 1) x len) receives y at every step boundary. */
-static void integrate_rec(const orc_problem *p, double T, double *y, int ncol, int t_col, double *rec);
-static void integrate(const orc_problem *p, double T, double *y, int ncol, int t_col)
+static void integrate_rec(const orc_problem *p, real T, real *y, int ncol, int t_col, real *rec);
+static void integrate(const orc_problem *p, real T, real *y, int ncol, int t_col)
 {
     integrate_rec(p, T, y, ncol, t_col, NULL);
 }
-static void integrate_rec(const orc_problem *p, double T, double *y, int ncol, int t_col, double *rec)
+static void integrate_rec(const orc_problem *p, real T, real *y, int ncol, int t_col, real *rec)
 {
     int N = p->N;
     size_t len = (size_t)(ncol + 1) * 2 * N;
-    double dt = T / 4.0 / p->steps;
-    double *k = malloc(sizeof(double) * len), *acc = malloc(sizeof(double) * len);
-    double *ys = malloc(sizeof(double) * len);
-    static const double a[4] = {0.0, 0.5, 0.5, 1.0};
-    static const double b[4] = {1.0, 2.0, 2.0, 1.0};
-    if (rec) memcpy(rec, y, sizeof(double) * len);
+    real dt = T / 4.0 / p->steps;
+    real *k = malloc(sizeof(real) * len), *acc = malloc(sizeof(real) * len);
+    real *ys = malloc(sizeof(real) * len);
+    static const real a[4] = {0.0, 0.5, 0.5, 1.0};
+    static const real b[4] = {1.0, 2.0, 2.0, 1.0};
+    if (rec) memcpy(rec, y, sizeof(real) * len);
     for (int n = 0; n < p->steps; ++n) {
         for (size_t i = 0; i < len; ++i) acc[i] = 0.0;
         for (int st = 0; st < 4; ++st) {
-            if (st == 0) memcpy(ys, y, sizeof(double) * len);
+            if (st == 0) memcpy(ys, y, sizeof(real) * len);
             else for (size_t i = 0; i < len; ++i) ys[i] = y[i] + a[st] * dt * k[i];
             orc_rhs(p, T, ys, ncol, t_col, k);
             for (size_t i = 0; i < len; ++i) acc[i] += b[st] * k[i];
@@ -586,7 +609,7 @@ static void integrate_rec(const orc_problem *p, double T, double *y, int ncol, i
             orc_spectral(N, MUL_FILTER, y + (size_t)c * 2 * N, y + (size_t)c * 2 * N);
             orc_spectral(N, MUL_FILTER, y + (size_t)c * 2 * N + N, y + (size_t)c * 2 * N + N);
         }
-        if (rec) memcpy(rec + (size_t)(n + 1) * len, y, sizeof(double) * len);
+        if (rec) memcpy(rec + (size_t)(n + 1) * len, y, sizeof(real) * len);
     }
     free(k); free(acc); free(ys);
 }
@@ -594,44 +617,44 @@ static void integrate_rec(const orc_problem *p, double T, double *y, int ncol, i
 /* Base state and ncol variational columns (initial data cols, each 2N; column
  * t_col forced as in orc_rhs) at every step boundary: rec is
  * (steps + 1) x (ncol + 1) x 2N. */
-void orc_trajectory_columns(const orc_problem *p, double T, const double *q0, const double *cols, int ncol,
-                            int t_col, double *rec)
+void orc_trajectory_columns(const orc_problem *p, real T, const real *q0, const real *cols, int ncol,
+                            int t_col, real *rec)
 {
     int N = p->N;
     size_t len = (size_t)(ncol + 1) * 2 * N;
-    double *y = malloc(sizeof(double) * len);
-    memcpy(y, q0, sizeof(double) * 2 * N);
-    memcpy(y + 2 * N, cols, sizeof(double) * (size_t)ncol * 2 * N);
+    real *y = malloc(sizeof(real) * len);
+    memcpy(y, q0, sizeof(real) * 2 * N);
+    memcpy(y + 2 * N, cols, sizeof(real) * (size_t)ncol * 2 * N);
     integrate_rec(p, T, y, ncol, t_col, rec);
     free(y);
 }
 
 /* Evolve the base state only (no columns): q_end = q(T/4). */
-void orc_evolve(const orc_problem *p, double T, const double *q0, double *q_end)
+void orc_evolve(const orc_problem *p, real T, const real *q0, real *q_end)
 {
-    memcpy(q_end, q0, sizeof(double) * 2 * p->N);
+    memcpy(q_end, q0, sizeof(real) * 2 * p->N);
     integrate(p, T, q_end, 0, 0);
 }
 
 /* Evolve base + ncol given variational columns (each 2N, contiguous) with
  * an optional T-forcing column (t_col as in orc_rhs). */
-void orc_evolve_columns(const orc_problem *p, double T, const double *q0, const double *cols,
-                        int ncol, int t_col, double *y_end /* (ncol+1)*2N */)
+void orc_evolve_columns(const orc_problem *p, real T, const real *q0, const real *cols,
+                        int ncol, int t_col, real *y_end /* (ncol+1)*2N */)
 {
     int N = p->N;
-    memcpy(y_end, q0, sizeof(double) * 2 * N);
-    memcpy(y_end + 2 * N, cols, sizeof(double) * (size_t)ncol * 2 * N);
+    memcpy(y_end, q0, sizeof(real) * 2 * N);
+    memcpy(y_end + 2 * N, cols, sizeof(real) * (size_t)ncol * 2 * N);
     integrate(p, T, y_end, ncol, t_col);
 }
 
 /* Objective, Eq. (f:phi) with reading R5: r_i = phi(x_i, T/4)/sqrt(N). */
-void orc_shoot(const orc_problem *p, const double *c, double *r, double *f)
+void orc_shoot(const orc_problem *p, const real *c, real *r, real *f)
 {
     int N = p->N;
-    double *y = malloc(sizeof(double) * 2 * N);
+    real *y = malloc(sizeof(real) * 2 * N);
     orc_initial(p, c, y);
     integrate(p, c[0], y, 0, 0);
-    double w = 1.0 / sqrt((double)N), s = 0.0;
+    real w = 1.0 / sqrt((real)N), s = 0.0;
     for (int i = 0; i < N; ++i) { r[i] = w * y[N + i]; s += r[i] * r[i]; }
     *f = 0.5 * s;
     free(y);
@@ -639,18 +662,18 @@ void orc_shoot(const orc_problem *p, const double *c, double *r, double *f)
 
 /* Jacobian, Eqs. (Jik), (q:qdot) with reading R2: J is N x (n+1) column-major,
  * column 0 = d r / d T, column k = d r / d c_k. */
-void orc_shoot_jacobian(const orc_problem *p, const double *c, double *r, double *J, double *f)
+void orc_shoot_jacobian(const orc_problem *p, const real *c, real *r, real *J, real *f)
 {
     int N = p->N, n = p->n, ncol = n + 1;
     size_t len = (size_t)(ncol + 1) * 2 * N;
-    double *y = calloc(len, sizeof(double));
+    real *y = calloc(len, sizeof(real));
     orc_initial(p, c, y);
     /* column 1 (J column 0) = T column, zero initial data; columns 2.. = basis */
     for (int k = 1; k <= n; ++k)
         for (int rr = 0; rr < 2 * N; ++rr)
             y[(size_t)(k + 1) * 2 * N + rr] = basis_entry(p, rr, k);
     integrate(p, c[0], y, ncol, 1);
-    double w = 1.0 / sqrt((double)N), s = 0.0;
+    real w = 1.0 / sqrt((real)N), s = 0.0;
     for (int i = 0; i < N; ++i) { r[i] = w * y[N + i]; s += r[i] * r[i]; }
     *f = 0.5 * s;
     for (int k = 0; k <= n; ++k)
@@ -674,33 +697,33 @@ void orc_shoot_jacobian(const orc_problem *p, const double *c, double *r, double
  *   adjoint of etadot = -phi_y (G^T chi + (phi_x pt)') + phi_x et'
  *                       + phi_x phi_y pt' - g pt + tau (pt' (1+eta'^2)^{-3/2})'
  * (the two phi_y terms combine to App. C's -phi_y phi_x' P phit). */
-static void rhs_T(const orc_problem *p, const double *q, const double *kb, double *out, double *Fdot)
+static void rhs_T(const orc_problem *p, const real *q, const real *kb, real *out, real *Fdot)
 {
     int N = p->N;
-    const double *eta = q, *phi = q + N;
-    double *F = malloc(sizeof(double) * 2 * N);
+    const real *eta = q, *phi = q + N;
+    real *F = malloc(sizeof(real) * 2 * N);
     orc_rhs(p, 1.0, q, 0, 0, F);                 /* base RHS (no T forcing in column 0) */
-    double fd = 0.0;
+    real fd = 0.0;
     for (int i = 0; i < 2 * N; ++i) fd += kb[i] * F[i];
     *Fdot = fd;
 
     dtn_state s;
     dtn_prepare(&s, N, p->h, eta);
-    double *phi_p = malloc(sizeof(double) * N), *Gphi = malloc(sizeof(double) * N);
-    double *ux = malloc(sizeof(double) * N), *vy = malloc(sizeof(double) * N);
-    double *w3 = malloc(sizeof(double) * N);
+    real *phi_p = malloc(sizeof(real) * N), *Gphi = malloc(sizeof(real) * N);
+    real *ux = malloc(sizeof(real) * N), *vy = malloc(sizeof(real) * N);
+    real *w3 = malloc(sizeof(real) * N);
     orc_spectral(N, MUL_DERIV, phi, phi_p);
     dtn_apply_one(&s, phi, Gphi);
     for (int i = 0; i < N; ++i) {              /* Eq. (uv:from:G), as in orc_rhs */
-        double ex = s.eta_x[i], d = 1.0 + ex * ex;
+        real ex = s.eta_x[i], d = 1.0 + ex * ex;
         ux[i] = (phi_p[i] - ex * Gphi[i]) / d;
         vy[i] = (ex * phi_p[i] + Gphi[i]) / d;
         w3[i] = 1.0 / (d * sqrt(d));
     }
-    double *et = malloc(sizeof(double) * N), *pt = malloc(sizeof(double) * N);
-    double *chi = malloc(sizeof(double) * N), *Gchi = malloc(sizeof(double) * N);
-    double *d_et = malloc(sizeof(double) * N), *d_pt = malloc(sizeof(double) * N);
-    double *t1 = malloc(sizeof(double) * N), *t2 = malloc(sizeof(double) * N);
+    real *et = malloc(sizeof(real) * N), *pt = malloc(sizeof(real) * N);
+    real *chi = malloc(sizeof(real) * N), *Gchi = malloc(sizeof(real) * N);
+    real *d_et = malloc(sizeof(real) * N), *d_pt = malloc(sizeof(real) * N);
+    real *t1 = malloc(sizeof(real) * N), *t2 = malloc(sizeof(real) * N);
     orc_spectral(N, MUL_FILTER, kb, et);
     orc_spectral(N, MUL_FILTER, kb + N, pt);
     orc_spectral(N, MUL_PROJECT, pt, pt);
@@ -713,7 +736,7 @@ static void rhs_T(const orc_problem *p, const double *q, const double *kb, doubl
     for (int i = 0; i < N; ++i) t2[i] = w3[i] * d_pt[i];
     orc_spectral(N, MUL_DERIV, t2, t2);        /* (pt' (1+eta'^2)^{-3/2})' */
     for (int i = 0; i < N; ++i) {
-        double pb = Gchi[i] + t1[i];
+        real pb = Gchi[i] + t1[i];
         out[N + i] = pb;
         out[i] = -vy[i] * pb + ux[i] * d_et[i] + ux[i] * vy[i] * d_pt[i] - p->g * pt[i] + p->tau * t2[i];
     }
@@ -730,9 +753,9 @@ static void rhs_T(const orc_problem *p, const double *q, const double *kb, doubl
  * the stages in reverse order, stage st contributing its transposed RHS to
  * lambda and, scaled by a_st dt, to the adjoint of the previous stage's RHS.
  * grad_k = basis_k . lambda(0); grad_0 = sum over stages of kbar . F / T. */
-static void adjoint_sweep(const orc_problem *p, const double *c, double *f, double *grad, double *lam_rec);
+static void adjoint_sweep(const orc_problem *p, const real *c, real *f, real *grad, real *lam_rec);
 
-void orc_objective_and_grad(const orc_problem *p, const double *c, double *f, double *grad)
+void orc_objective_and_grad(const orc_problem *p, const real *c, real *f, real *grad)
 {
     adjoint_sweep(p, c, f, grad, NULL);
 }
@@ -742,29 +765,29 @@ void orc_objective_and_grad(const orc_problem *p, const double *c, double *f, do
  * (lam_rec[steps] = (0, phi(T/4)/N)).  The discrete counterpart of Sec. 3.2's
  * identity <q~(T/4 - t), qdot(t)> = const: lam_rec[n] . w_n is the same for
  * every n when w is an unforced variational column. */
-void orc_adjoint_trajectory(const orc_problem *p, const double *c, double *lam_rec)
+void orc_adjoint_trajectory(const orc_problem *p, const real *c, real *lam_rec)
 {
-    double f, *grad = malloc(sizeof(double) * (p->n + 1));
+    real f, *grad = malloc(sizeof(real) * (p->n + 1));
     adjoint_sweep(p, c, &f, grad, lam_rec);
     free(grad);
 }
 
-static void adjoint_sweep(const orc_problem *p, const double *c, double *f, double *grad, double *lam_rec)
+static void adjoint_sweep(const orc_problem *p, const real *c, real *f, real *grad, real *lam_rec)
 {
     int N = p->N, S = 4 * p->steps;
     size_t n2 = (size_t)2 * N;
-    double T = c[0], dt = T / 4.0 / p->steps;
-    static const double a[4] = {0.0, 0.5, 0.5, 1.0};
-    static const double b[4] = {1.0, 2.0, 2.0, 1.0};
-    double *traj = malloc(sizeof(double) * n2 * (size_t)S);
-    double *y = malloc(sizeof(double) * n2), *k = malloc(sizeof(double) * n2);
-    double *acc = malloc(sizeof(double) * n2);
+    real T = c[0], dt = T / 4.0 / p->steps;
+    static const real a[4] = {0.0, 0.5, 0.5, 1.0};
+    static const real b[4] = {1.0, 2.0, 2.0, 1.0};
+    real *traj = malloc(sizeof(real) * n2 * (size_t)S);
+    real *y = malloc(sizeof(real) * n2), *k = malloc(sizeof(real) * n2);
+    real *acc = malloc(sizeof(real) * n2);
     orc_initial(p, c, y);
     for (int n = 0; n < p->steps; ++n) {         /* forward: as integrate() with no columns */
         for (size_t i = 0; i < n2; ++i) acc[i] = 0.0;
         for (int st = 0; st < 4; ++st) {
-            double *ys = traj + (size_t)(4 * n + st) * n2;
-            if (st == 0) memcpy(ys, y, sizeof(double) * n2);
+            real *ys = traj + (size_t)(4 * n + st) * n2;
+            if (st == 0) memcpy(ys, y, sizeof(real) * n2);
             else for (size_t i = 0; i < n2; ++i) ys[i] = y[i] + a[st] * dt * k[i];
             orc_rhs(p, T, ys, 0, 0, k);
             for (size_t i = 0; i < n2; ++i) acc[i] += b[st] * k[i];
@@ -773,33 +796,33 @@ static void adjoint_sweep(const orc_problem *p, const double *c, double *f, doub
         orc_spectral(N, MUL_FILTER, y, y);
         orc_spectral(N, MUL_FILTER, y + N, y + N);
     }
-    double s = 0.0;
+    real s = 0.0;
     for (int i = 0; i < N; ++i) s += y[N + i] * y[N + i] / N;
     *f = 0.5 * s;
 
-    double *lam = malloc(sizeof(double) * n2), *kb = malloc(sizeof(double) * n2 * 4);
-    double *wb = malloc(sizeof(double) * n2);
+    real *lam = malloc(sizeof(real) * n2), *kb = malloc(sizeof(real) * n2 * 4);
+    real *wb = malloc(sizeof(real) * n2);
     for (int i = 0; i < N; ++i) { lam[i] = 0.0; lam[N + i] = y[N + i] / N; }
-    if (lam_rec) memcpy(lam_rec + (size_t)p->steps * n2, lam, sizeof(double) * n2);
-    double gT = 0.0;
+    if (lam_rec) memcpy(lam_rec + (size_t)p->steps * n2, lam, sizeof(real) * n2);
+    real gT = 0.0;
     for (int n = p->steps - 1; n >= 0; --n) {
         orc_spectral(N, MUL_FILTER, lam, lam);   /* the end-of-step filter, transposed */
         orc_spectral(N, MUL_FILTER, lam + N, lam + N);
         for (int st = 0; st < 4; ++st)
             for (size_t i = 0; i < n2; ++i) kb[st * n2 + i] = b[st] * dt / 6.0 * lam[i];
         for (int st = 3; st >= 0; --st) {
-            double Fd;
+            real Fd;
             rhs_T(p, traj + (size_t)(4 * n + st) * n2, kb + st * n2, wb, &Fd);
             gT += Fd / T;
             for (size_t i = 0; i < n2; ++i) lam[i] += wb[i];
             if (st > 0)
                 for (size_t i = 0; i < n2; ++i) kb[(st - 1) * n2 + i] += a[st] * dt * wb[i];
         }
-        if (lam_rec) memcpy(lam_rec + (size_t)n * n2, lam, sizeof(double) * n2);
+        if (lam_rec) memcpy(lam_rec + (size_t)n * n2, lam, sizeof(real) * n2);
     }
     grad[0] = gT;
     for (int kk = 1; kk <= p->n; ++kk) {
-        double g = 0.0;
+        real g = 0.0;
         for (size_t r = 0; r < n2; ++r) g += basis_entry(p, (int)r, kk) * lam[r];
         grad[kk] = g;
     }
@@ -808,16 +831,16 @@ static void adjoint_sweep(const orc_problem *p, const double *c, double *f, doub
 
 /* Energy (Sec. 4, energy monitor): E = 1/2 int (phi G phi + g (eta - hbar)^2) dx
  * + tau int (sqrt(1 + eta'^2) - 1) dx, trapezoid rule. */
-double orc_energy(const orc_problem *p, const double *q)
+real orc_energy(const orc_problem *p, const real *q)
 {
     int N = p->N;
-    const double *eta = q, *phi = q + N;
-    double *Gphi = malloc(sizeof(double) * N), *ex = malloc(sizeof(double) * N);
+    const real *eta = q, *phi = q + N;
+    real *Gphi = malloc(sizeof(real) * N), *ex = malloc(sizeof(real) * N);
     orc_dtn(N, p->h, eta, phi, 1, Gphi);
     orc_spectral(N, MUL_DERIV, eta, ex);
-    double mean = isinf(p->h) ? 0.0 : p->h, e = 0.0;
+    real mean = isinf(p->h) ? 0.0 : p->h, e = 0.0;
     for (int i = 0; i < N; ++i) {
-        double d = eta[i] - mean;
+        real d = eta[i] - mean;
         e += 0.5 * (phi[i] * Gphi[i] + p->g * d * d) + p->tau * (sqrt(1.0 + ex[i] * ex[i]) - 1.0);
     }
     free(Gphi); free(ex);
@@ -836,8 +859,8 @@ double orc_energy(const orc_problem *p, const double *q)
 typedef struct {
     int M;
     int steps;
-    double theta;
-    double rho;
+    real theta;
+    real rho;
     int centre;
 } orc_segment;
 
@@ -846,50 +869,50 @@ typedef struct {
  * so the nodes are not needed. */
 typedef struct {
     int s;
-    const double *a, *b;
+    const real *a, *b;
 } orc_tableau;
 
 /* Eq. (xi): E = 1 - P[A sin^4(alpha/2)] (or cos^4), A = 8 (1 - rho) / (5 + 3 rho).
  * With sin^4(a/2) = 3/8 - cos(a)/2 + cos(2a)/8 and cos^4(a/2) = 3/8 + cos(a)/2
  * + cos(2a)/8, P drops the 3/8 and xi = int_0^alpha E is a trigonometric
  * polynomial in closed form.  Returns xi, E = xi' and E' = xi'' at alpha. */
-static void mesh_point(double rho, int centre, double alpha, double *xi, double *E, double *E1)
+static void mesh_point(real rho, int centre, real alpha, real *xi, real *E, real *E1)
 {
-    double A = 8.0 * (1.0 - rho) / (5.0 + 3.0 * rho);
-    double s1 = sin(alpha), c1 = cos(alpha), s2 = sin(2.0 * alpha), c2 = cos(2.0 * alpha);
-    double sg = centre ? 1.0 : -1.0;       /* sign of the cos(alpha) term */
+    real A = 8.0 * (1.0 - rho) / (5.0 + 3.0 * rho);
+    real s1 = sin(alpha), c1 = cos(alpha), s2 = sin(2.0 * alpha), c2 = cos(2.0 * alpha);
+    real sg = centre ? 1.0 : -1.0;       /* sign of the cos(alpha) term */
     *xi = alpha + A * (sg * 0.5 * s1 - s2 / 16.0);
     *E = 1.0 + A * (sg * 0.5 * c1 - c2 / 8.0);
     *E1 = A * (-sg * 0.5 * s1 + s2 / 4.0);
 }
 
 /* Public: the mesh of a segment at alpha_j = 2 pi j / M. */
-void orc_mesh_eval(double rho, int centre, int M, double *x, double *e, double *e1)
+void orc_mesh_eval(real rho, int centre, int M, real *x, real *e, real *e1)
 {
     for (int j = 0; j < M; ++j) mesh_point(rho, centre, TWO_PI * j / M, x + j, e + j, e1 + j);
 }
 
 /* xi^{-1}(x) by Newton's method (Sec. 2.2), kept inside the bracket
  * |alpha - x| <= A (|xi - alpha| <= 9A/16) by bisection when a step leaves it. */
-static double mesh_inverse_one(double rho, int centre, double x)
+static real mesh_inverse_one(real rho, int centre, real x)
 {
-    double A = 8.0 * (1.0 - rho) / (5.0 + 3.0 * rho);
-    double lo = x - A - 1e-12, hi = x + A + 1e-12, a = x;
+    real A = 8.0 * (1.0 - rho) / (5.0 + 3.0 * rho);
+    real lo = x - A - 1e-12, hi = x + A + 1e-12, a = x;
     for (int it = 0; it < 200; ++it) {
-        double xi, E, E1;
+        real xi, E, E1;
         mesh_point(rho, centre, a, &xi, &E, &E1);
-        double r = xi - x;
+        real r = xi - x;
         if (r == 0.0) break;
         if (r > 0.0) hi = a; else lo = a;
-        double an = a - r / E;
+        real an = a - r / E;
         if (!(an > lo && an < hi)) an = 0.5 * (lo + hi);
-        if (fabs(an - a) <= 4e-16 * (1.0 + fabs(a))) { a = an; break; }
+        if (fabs(an - a) <= NEWTON_TOL * (1.0 + fabs(a))) { a = an; break; }
         a = an;
     }
     return a;
 }
 
-void orc_mesh_inverse(double rho, int centre, int n, const double *x, double *alpha)
+void orc_mesh_inverse(real rho, int centre, int n, const real *x, real *alpha)
 {
     for (int i = 0; i < n; ++i) alpha[i] = mesh_inverse_one(rho, centre, x[i]);
 }
@@ -897,16 +920,16 @@ void orc_mesh_inverse(double rho, int centre, int n, const double *x, double *al
 /* The trigonometric interpolant of f (values at alpha_j = 2 pi j / M) at the
  * points beta[0..n): sum over |k| < M/2 of fhat_k e^{i k beta} plus the
  * Nyquist mode as fhat_{M/2} cos(M beta / 2) (reading R22); direct sums. */
-void orc_interp(int M, const double *f, int n, const double *beta, double *out)
+void orc_interp(int M, const real *f, int n, const real *beta, real *out)
 {
     cplx *fh = malloc(sizeof(cplx) * M);
     for (int j = 0; j < M; ++j) fh[j] = f[j];
     orc_fft(M, fh, 0);
     for (int j = 0; j < M; ++j) fh[j] /= M;
     for (int i = 0; i < n; ++i) {
-        double acc = creal(fh[0]);
+        real acc = creal(fh[0]);
         for (int k = 1; k < M / 2; ++k)
-            acc += 2.0 * creal(fh[k] * cexp(I * (double)k * beta[i]));
+            acc += 2.0 * creal(fh[k] * CEXP(I * (real)k * beta[i]));
         acc += creal(fh[M / 2]) * cos(0.5 * M * beta[i]);
         out[i] = acc;
     }
@@ -917,16 +940,16 @@ void orc_interp(int M, const double *f, int n, const double *beta, double *out)
  * so a uniform segment runs exactly the uniform arithmetic). */
 typedef struct {
     orc_mesh m;
-    double *x, *e, *e1;
+    real *x, *e, *e1;
 } mesh_buf;
 
 static const orc_mesh *mesh_make(mesh_buf *b, const orc_segment *sg)
 {
     b->x = b->e = b->e1 = NULL;
     if (sg->rho == 1.0) return NULL;
-    b->x = malloc(sizeof(double) * sg->M);
-    b->e = malloc(sizeof(double) * sg->M);
-    b->e1 = malloc(sizeof(double) * sg->M);
+    b->x = malloc(sizeof(real) * sg->M);
+    b->e = malloc(sizeof(real) * sg->M);
+    b->e1 = malloc(sizeof(real) * sg->M);
     orc_mesh_eval(sg->rho, sg->centre, sg->M, b->x, b->e, b->e1);
     b->m.x = b->x; b->m.e = b->e; b->m.e1 = b->e1;
     return &b->m;
@@ -937,12 +960,12 @@ static void mesh_free(mesh_buf *b) { free(b->x); free(b->e); free(b->e1); }
 /* Respacing (Sec. 2.2): the new values at alpha'_j (M' points of segment b)
  * are those of the old interpolant at xi_a^{-1}(xi_b(alpha'_j)).  ncols
  * vectors of length Ma in; ncols of length Mb out. */
-static void respace(const orc_segment *sa, const orc_segment *sb, int ncols, const double *in, double *out)
+static void respace(const orc_segment *sa, const orc_segment *sb, int ncols, const real *in, real *out)
 {
     int Ma = sa->M, Mb = sb->M;
-    double *beta = malloc(sizeof(double) * Mb);
+    real *beta = malloc(sizeof(real) * Mb);
     for (int j = 0; j < Mb; ++j) {
-        double xi, E, E1;
+        real xi, E, E1;
         mesh_point(sb->rho, sb->centre, TWO_PI * j / Mb, &xi, &E, &E1);
         beta[j] = mesh_inverse_one(sa->rho, sa->centre, xi);
     }
@@ -956,23 +979,23 @@ static void respace(const orc_segment *sa, const orc_segment *sb, int ncols, con
 /* One segment: `steps` steps of the tableau of size dt on the mesh, the RHS
  * filtered at every stage (inside rhs_impl) and the solution after every
  * step (reading R4). */
-static void integrate_tableau(const orc_problem *p, const orc_mesh *m, int N, const orc_tableau *tb, double T,
-                              double dt, int steps, double *y, int ncol, int t_col)
+static void integrate_tableau(const orc_problem *p, const orc_mesh *m, int N, const orc_tableau *tb, real T,
+                              real dt, int steps, real *y, int ncol, int t_col)
 {
     size_t len = (size_t)(ncol + 1) * 2 * N;
     int s = tb->s;
-    double *k = malloc(sizeof(double) * len * s), *ys = malloc(sizeof(double) * len);
+    real *k = malloc(sizeof(real) * len * s), *ys = malloc(sizeof(real) * len);
     for (int n = 0; n < steps; ++n) {
         for (int st = 0; st < s; ++st) {
             for (size_t i = 0; i < len; ++i) {
-                double acc = 0.0;
+                real acc = 0.0;
                 for (int j = 0; j < st; ++j) acc += tb->a[st * s + j] * k[(size_t)j * len + i];
                 ys[i] = y[i] + dt * acc;
             }
             rhs_impl(p, m, N, T, ys, ncol, t_col, k + (size_t)st * len);
         }
         for (size_t i = 0; i < len; ++i) {
-            double acc = 0.0;
+            real acc = 0.0;
             for (int j = 0; j < s; ++j) acc += tb->b[j] * k[(size_t)j * len + i];
             y[i] += dt * acc;
         }
@@ -988,7 +1011,7 @@ static int segments_valid(const orc_problem *p, int nseg, const orc_segment *sg,
 {
     if (nseg < 1 || !tb || tb->s < 1) return 0;
     if (sg[0].M != p->N || sg[0].rho != 1.0) return 0;    /* x = alpha on the first segment */
-    double th = 0.0;
+    real th = 0.0;
     for (int l = 0; l < nseg; ++l) {
         int M = sg[l].M;
         if (M < 4 || (M & (M - 1)) || sg[l].steps < 1 || !(sg[l].theta > 0.0)) return 0;
@@ -1000,22 +1023,22 @@ static int segments_valid(const orc_problem *p, int nseg, const orc_segment *sg,
 
 /* Integrate y (ncol + 1 columns on segment 0's grid) through all segments
  * from 0 to T/4; returns the state on the last segment's grid (malloc'd). */
-static double *integrate_segments(const orc_problem *p, int nseg, const orc_segment *sg, const orc_tableau *tb,
-                                  double T, const double *y0, int ncol, int t_col)
+static real *integrate_segments(const orc_problem *p, int nseg, const orc_segment *sg, const orc_tableau *tb,
+                                  real T, const real *y0, int ncol, int t_col)
 {
     size_t cols = (size_t)(ncol + 1) * 2;
-    double *y = malloc(sizeof(double) * cols * sg[0].M);
-    memcpy(y, y0, sizeof(double) * cols * sg[0].M);
+    real *y = malloc(sizeof(real) * cols * sg[0].M);
+    memcpy(y, y0, sizeof(real) * cols * sg[0].M);
     for (int l = 0; l < nseg; ++l) {
         if (l > 0) {
-            double *z = malloc(sizeof(double) * cols * sg[l].M);
+            real *z = malloc(sizeof(real) * cols * sg[l].M);
             respace(&sg[l - 1], &sg[l], (int)cols, y, z);
             free(y);
             y = z;
         }
         mesh_buf b;
         const orc_mesh *m = mesh_make(&b, &sg[l]);
-        double dt = sg[l].theta * (T / 4.0) / sg[l].steps;
+        real dt = sg[l].theta * (T / 4.0) / sg[l].steps;
         integrate_tableau(p, m, sg[l].M, tb, T, dt, sg[l].steps, y, ncol, t_col);
         mesh_free(&b);
     }
@@ -1024,37 +1047,37 @@ static double *integrate_segments(const orc_problem *p, int nseg, const orc_segm
 
 /* Residual weights on the last segment: w_i = sqrt(E(alpha_i) / M)
  * (Eq. (f:phi) with the mesh density E). */
-static void segment_weights(const orc_segment *sl, double *w)
+static void segment_weights(const orc_segment *sl, real *w)
 {
     for (int i = 0; i < sl->M; ++i) {
-        double xi, E, E1;
+        real xi, E, E1;
         mesh_point(sl->rho, sl->centre, TWO_PI * i / sl->M, &xi, &E, &E1);
         w[i] = sqrt(E / sl->M);
     }
 }
 
 /* Public: evolve q0 (2N on segment 0) to T/4; q_end holds 2 M_last. */
-int orc_evolve_segments(const orc_problem *p, int nseg, const orc_segment *sg, const orc_tableau *tb, double T,
-                        const double *q0, double *q_end)
+int orc_evolve_segments(const orc_problem *p, int nseg, const orc_segment *sg, const orc_tableau *tb, real T,
+                        const real *q0, real *q_end)
 {
     if (!segments_valid(p, nseg, sg, tb)) return -1;
-    double *y = integrate_segments(p, nseg, sg, tb, T, q0, 0, 0);
-    memcpy(q_end, y, sizeof(double) * 2 * sg[nseg - 1].M);
+    real *y = integrate_segments(p, nseg, sg, tb, T, q0, 0, 0);
+    memcpy(q_end, y, sizeof(real) * 2 * sg[nseg - 1].M);
     free(y);
     return 0;
 }
 
 /* Public: r (M_last) and f of the segmented shot. */
 int orc_shoot_segments(const orc_problem *p, int nseg, const orc_segment *sg, const orc_tableau *tb,
-                       const double *c, double *r, double *f)
+                       const real *c, real *r, real *f)
 {
     if (!segments_valid(p, nseg, sg, tb)) return -1;
     int N = p->N, M = sg[nseg - 1].M;
-    double *q0 = malloc(sizeof(double) * 2 * N), *w = malloc(sizeof(double) * M);
+    real *q0 = malloc(sizeof(real) * 2 * N), *w = malloc(sizeof(real) * M);
     orc_initial(p, c, q0);
-    double *y = integrate_segments(p, nseg, sg, tb, c[0], q0, 0, 0);
+    real *y = integrate_segments(p, nseg, sg, tb, c[0], q0, 0, 0);
     segment_weights(&sg[nseg - 1], w);
-    double s = 0.0;
+    real s = 0.0;
     for (int i = 0; i < M; ++i) { r[i] = w[i] * y[M + i]; s += r[i] * r[i]; }
     *f = 0.5 * s;
     free(q0); free(w); free(y);
@@ -1065,18 +1088,18 @@ int orc_shoot_segments(const orc_problem *p, int nseg, const orc_segment *sg, co
  * The variational columns ride through the respacing with the base state:
  * respacing is linear, so they stay the exact derivative of the discrete map. */
 int orc_shoot_jacobian_segments(const orc_problem *p, int nseg, const orc_segment *sg, const orc_tableau *tb,
-                                const double *c, double *r, double *J, double *f)
+                                const real *c, real *r, real *J, real *f)
 {
     if (!segments_valid(p, nseg, sg, tb)) return -1;
     int N = p->N, n = p->n, ncol = n + 1, M = sg[nseg - 1].M;
-    double *y0 = calloc((size_t)(ncol + 1) * 2 * N, sizeof(double)), *w = malloc(sizeof(double) * M);
+    real *y0 = calloc((size_t)(ncol + 1) * 2 * N, sizeof(real)), *w = malloc(sizeof(real) * M);
     orc_initial(p, c, y0);
     for (int k = 1; k <= n; ++k)
         for (int rr = 0; rr < 2 * N; ++rr)
             y0[(size_t)(k + 1) * 2 * N + rr] = basis_entry(p, rr, k);
-    double *y = integrate_segments(p, nseg, sg, tb, c[0], y0, ncol, 1);
+    real *y = integrate_segments(p, nseg, sg, tb, c[0], y0, ncol, 1);
     segment_weights(&sg[nseg - 1], w);
-    double s = 0.0;
+    real s = 0.0;
     for (int i = 0; i < M; ++i) { r[i] = w[i] * y[M + i]; s += r[i] * r[i]; }
     *f = 0.5 * s;
     for (int k = 0; k <= n; ++k)
@@ -1087,8 +1110,8 @@ int orc_shoot_jacobian_segments(const orc_problem *p, int nseg, const orc_segmen
 }
 
 /* Public (tests): the RHS of ncol + 1 columns on the mesh of a segment. */
-void orc_rhs_segment(const orc_problem *p, const orc_segment *sg, double T, const double *y, int ncol, int t_col,
-                     double *out)
+void orc_rhs_segment(const orc_problem *p, const orc_segment *sg, real T, const real *y, int ncol, int t_col,
+                     real *out)
 {
     mesh_buf b;
     const orc_mesh *m = mesh_make(&b, sg);
@@ -1097,7 +1120,7 @@ void orc_rhs_segment(const orc_problem *p, const orc_segment *sg, double T, cons
 }
 
 /* Public (tests): the DtN of phi on the surface eta, both stored on the mesh. */
-void orc_dtn_segment(const orc_segment *sg, double h, const double *eta, const double *phi, double *out)
+void orc_dtn_segment(const orc_segment *sg, real h, const real *eta, const real *phi, real *out)
 {
     mesh_buf b;
     const orc_mesh *m = mesh_make(&b, sg);

@@ -15,7 +15,12 @@ per output, how far its own result moves (the sensitivity floor of the
 problem at this size: two correct FP64 evaluations that differ only in
 rounding cannot be expected to agree better than a few times this).
 
-    python tests/golden/make_full_size_samples.py [--spread]
+With --wide the oracle's long double build runs the base shot (r and f, no
+columns) on the same workload and records how far the double oracle's r and
+f are from it: the double oracle's own rounding error at this size (about an
+hour on 8 cores in x87 extended precision).
+
+    python tests/golden/make_full_size_samples.py [--spread | --wide]
 """
 import json
 import os
@@ -58,7 +63,23 @@ def main():
     c, seed = W.coefficients(w)
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "full_n2048_samples.json")
     rows = list(range(0, w.N, ROW_STRIDE))
-    if "--spread" in sys.argv:
+    if "--wide" in sys.argv:
+        with open(path) as fh:
+            out = json.load(fh)
+        wp, _ = O.wide_problem(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps)
+        t0 = time.time()
+        rw, fw = O.wide_shoot(wp, c)
+        rs = rw.astype(np.float64)[rows]
+        out["wide"] = {
+            "what": "the oracle's long double build, base shot: f, and the double oracle's distance to it",
+            "long_double_eps": float(np.finfo(np.longdouble).eps),
+            "f": float(fw),
+            "f_rel_double_oracle": float(abs(out["f"] - fw) / abs(fw)),
+            "r_rel_double_oracle": float(np.linalg.norm(np.asarray(out["r"]) - rs) / np.linalg.norm(rs)),
+            "r": [float(v) for v in rs],
+            "oracle_threads": O.threads(), "oracle_seconds": round(time.time() - t0, 1),
+        }
+    elif "--spread" in sys.argv:
         with open(path) as fh:
             out = json.load(fh)
         cp = c.copy()

@@ -84,6 +84,14 @@ def _check(precision):
     ef, er, ej = _errors(g, r, J, f)
     print(f"\nfull N=2048 precision={precision}: |df|/|f| {ef:.2e}  r {er:.2e}  "
           + "  ".join(f"J[{k}] {e:.2e}" for k, e in ej.items()) + f"  stats {st}")
+    wd = g.get("wide")
+    if wd is not None:      # the long double oracle's base shot: where the rounding sits
+        rows = np.asarray(g["rows"])
+        rw = np.asarray(wd["r"])
+        print(f"full N=2048 precision={precision} vs the long double oracle: "
+              f"|df|/|f| {abs(f - wd['f']) / abs(wd['f']):.2e} (double oracle {wd['f_rel_double_oracle']:.2e})  "
+              f"r {np.linalg.norm(r[rows] - rw) / np.linalg.norm(rw):.2e} "
+              f"(double oracle {wd['r_rel_double_oracle']:.2e})")
     assert ef < _tol(g, "f")
     assert er < _tol(g, "r")
     for k, e in ej.items():
