@@ -447,6 +447,35 @@ def test_lu_transposed_solve():
     assert np.max(np.abs(x - ref)) < 1e-12 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("name", ["N64_n12_steps64_h1", "N512_n128_steps512_h1", "N2048_n512_steps1024_h1",
+                                  "N1024_n256_steps2048_h0.05", "N1024_n256_steps2048_deep_tau0.1"])
+def test_partial_pivoting_never_swaps_on_the_workloads(name):
+    """Reading R9: A = 1/2 I + K is a second-kind operator, so the GPU factors it
+    without pivoting.  On every workload's initial surface (and, for the small
+    one, the surface at T/4 and an RK4 stage state) partial pivoting makes no
+    row interchange, so the pivoted factors are the unpivoted ones, and the
+    growth max|U| / max|A| stays at 1."""
+    import ctypes as C
+    w = W.ALL[name]
+    c, _ = W.coefficients(w)
+    N = w.N
+    x = 2 * np.pi * np.arange(N) / N
+    surfaces = [(0.0 if math.isinf(w.h) else w.h) + np.cos(np.outer(x, np.arange(1, w.n + 1))) @ c[1:]]
+    if N <= 64:
+        prob, _ = O.make_problem(N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps)
+        q0 = O.initial(prob, c)
+        q1 = O.evolve(prob, c[0], q0)
+        k1 = O.rhs(prob, c[0], q0, 0)[0]
+        surfaces += [q1[:N], q0[:N] + 0.5 * (c[0] / 4 / w.steps) * k1[:N]]
+    for eta in surfaces:
+        A, _ = O.dtn_matrices(eta, w.h)
+        LU = np.ascontiguousarray(A.copy())
+        piv = np.zeros(N, dtype=np.int32)
+        assert O.lib().orc_lu(N, O._p(LU), piv.ctypes.data_as(C.POINTER(C.c_int))) == 0
+        assert np.array_equal(piv, np.arange(N, dtype=np.int32)), name
+        assert np.max(np.abs(np.triu(LU))) / np.max(np.abs(A)) <= 1.0 + 1e-12
+
+
 def test_adjoint_identity_at_every_step():
     """Sec. 3.2: <q~(T/4 - t), qdot(t)> is constant in time.  For the discrete
     adjoint, the pairing lam_n . w_n of the adjoint state with an unforced
