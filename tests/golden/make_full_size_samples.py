@@ -17,8 +17,10 @@ rounding cannot be expected to agree better than a few times this).
 
 With --wide the oracle's long double build runs the base shot (r and f, no
 columns) on the same workload and records how far the double oracle's r and
-f are from it: the double oracle's own rounding error at this size (about an
-hour on 8 cores in x87 extended precision).
+f are from it: the double oracle's own rounding error at this size.  It is
+slow: about 1.6 s per RK4 stage on 8 x86-64 cores in x87 extended precision
+(LU and long double cotangents), 6 to 7 hours for the 4096 stages, and far
+longer where long double is software binary128.
 
     python tests/golden/make_full_size_samples.py [--spread | --wide]
 """
