@@ -164,3 +164,42 @@ def test_standing_wave_period_is_second_order_in_amplitude():
     # the unit-depth period first decreases with amplitude (Sec. 4, Fig. bif10)
     assert d1 < -1e-6 and d2 < 0
     assert abs(d1 / d2 - 4.0) < 0.1, (d1, d2)
+
+
+def test_solver_on_a_segmented_dop853_shot():
+    """The paper's own setting (Sec. 2.2): the shot over time segments, the second
+    on twice the points with the mesh refined near x = pi, stepped by DOP853
+    (16 steps in all), drives the solver to the same standing wave as uniform
+    RK4, and its period is the RK4 periods' Richardson extrapolation to dt -> 0
+    (RK4 error ~ dt^4, so T_exact = T_128 - (T_64 - T_128) / 15)."""
+    N, n = 64, 12
+    x = 2 * np.pi * np.arange(N) / N
+    basis = np.zeros((2 * N, n))
+    for k in range(1, n + 1):   # Eq. init:stand: even k on eta, odd k on phi, 2 cos(k x)
+        basis[(N if k % 2 else 0):(2 * N if k % 2 else N), k - 1] = 2 * np.cos(k * x)
+    prob, keep = O.make_problem(N, n, h=1.0, basis=basis)
+    T_lin = 2 * math.pi / math.sqrt(math.tanh(1.0))
+    c0 = np.zeros(n + 1)
+    c0[0], c0[1] = T_lin, 0.02
+    free = np.array([0] + list(range(2, n + 1)))
+
+    def solve(segs, tab):
+        def full(z):
+            c = c0.copy()
+            c[free] = z
+            return c
+
+        out = levmar(lambda z: O.shoot_segments(prob, segs, tab, full(z))[0],
+                     lambda z: (lambda rJ: (rJ[0], rJ[1][:, free]))(O.shoot_jacobian_segments(prob, segs, tab,
+                                                                                                full(z))),
+                     c0[free], 0.01 * T_lin, LMOptions())
+        assert out.f < 1e-28
+        return full(out.c)
+
+    seg = solve([(N, 8, 0.5, 1.0), (2 * N, 8, 0.5, 0.5, 1)], "dop853")
+    r64 = solve([(N, 64, 1.0, 1.0)], "rk4")
+    r128 = solve([(N, 128, 1.0, 1.0)], "rk4")
+    T_exact = r128[0] - (r64[0] - r128[0]) / 15
+    assert abs(r128[0] - T_exact) > 1e-9                 # RK4 at 128 steps is still visibly off
+    assert abs(seg[0] - T_exact) < 1e-12
+    assert np.max(np.abs(seg[2:] - r128[2:])) < 1e-11   # the same initial data
