@@ -32,6 +32,9 @@ the paper the C function follows:
                         shot over time segments with their own grids, meshes
                         and step counts (Sec. 2.2), any tableau
 * ``rhs_segment``, ``dtn_segment`` -- the RHS and the DtN on a segment's mesh
+* ``objective_and_grad_segments``, ``rhs_T_segment`` -- the discrete adjoint of
+                        the segmented shot (reading R18 carried to meshes,
+                        respacing and any tableau) and its transposed RHS
 * ``wide_*``         -- the same C compiled with long double (x87 extended on
                         x86-64, binary128 on aarch64): the double build's own
                         rounding error on the same discrete map
@@ -139,6 +142,9 @@ def _set_signatures(L):
                                                   _D, _D]),
         "orc_rhs_segment": (None, [P, C.POINTER(Segment), C.c_double, _D, C.c_int, C.c_int, _D]),
         "orc_dtn_segment": (None, [C.POINTER(Segment), C.c_double, _D, _D, _D]),
+        "orc_objective_and_grad_segments": (C.c_int, [P, C.c_int, C.POINTER(Segment), C.POINTER(Tableau), _D, _D,
+                                                      _D]),
+        "orc_rhs_T_segment": (None, [P, C.POINTER(Segment), _D, _D, _D, _D]),
         "orc_threads": (C.c_int, []),
         "orc_set_threads": (None, [C.c_int]),
     }
@@ -488,3 +494,24 @@ def wide_dtn(eta, phi, h) -> np.ndarray:
     out = np.empty(eta.size, dtype=np.longdouble)
     wide_lib().orc_dtn(eta.size, h, _lp(eta), _lp(phi), 1, _lp(out))
     return out
+
+
+def objective_and_grad_segments(prob: Problem, segs, tab, c):
+    """(f, grad) of the segmented shot by its discrete adjoint; grad[0] = d f / d T."""
+    sa = _segments(segs)
+    tb, keep = _tableau(tab)
+    c = _f64(c)
+    f, g = np.empty(1), np.empty(prob.n + 1)
+    if lib().orc_objective_and_grad_segments(C.byref(prob), len(segs), sa, C.byref(tb), _p(c), _p(f),
+                                             _p(g)) != 0:
+        raise ValueError("invalid segments")
+    return float(f[0]), g
+
+
+def rhs_T_segment(prob: Problem, seg, q, kb):
+    """(DF(q)^T kb, kb . F(q)) on a segment's mesh."""
+    sa = _segments([seg])
+    q, kb = _f64(q), _f64(kb)
+    out, fd = np.empty_like(kb), np.empty(1)
+    lib().orc_rhs_T_segment(C.byref(prob), sa, _p(q), _p(kb), _p(out), _p(fd))
+    return out, float(fd[0])

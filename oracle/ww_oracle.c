@@ -54,7 +54,7 @@
  * 5 = the adjoint takes the forward DtN for its transpose (the continuous
  * self-adjointness of App. C applied to the discrete operator), 6 = the DtN on
  * a mesh without the 1/|xi'| of Eq. (G), 7 = P on a mesh as the mean over
- * alpha instead of x. */
+ * alpha instead of x, 8 = the adjoint on a mesh takes P for its transpose. */
 #ifndef ORC_PLANT
 #define ORC_PLANT 0
 #endif
@@ -403,24 +403,26 @@ static void dtn_apply_one(const dtn_state *s, const real *phi, real *out)
 }
 
 /* The transpose of the operator of dtn_apply_one (reading R18).  Forward:
- * G phi = (1/2 H + G) D A^{-1} phi.  The Fourier multipliers ik and -i sgn k
- * (Nyquist zeroed) are antisymmetric, D^T = -D and H^T = -H, so
- * G^T x = A^{-T} D (1/2 H x - G^T x). */
+ * G phi = diag(1/xi') (1/2 H + G) D A^{-1} phi.  The Fourier multipliers ik
+ * and -i sgn k (Nyquist zeroed) are antisymmetric, D^T = -D and H^T = -H, so
+ * G^T x = A^{-T} D (1/2 H - G^T) diag(1/xi') x. */
 static void dtn_apply_T(const dtn_state *s, const real *x, real *out)
 {
     int N = s->N;
     if (ORC_PLANT == 5) { dtn_apply_one(s, x, out); return; }
     real *hx = malloc(sizeof(real) * N);
     real *t = malloc(sizeof(real) * N);
-    orc_spectral(N, MUL_HILBERT, x, hx);
+    real *xs = malloc(sizeof(real) * N);          /* diag(1/xi') x on a mesh */
+    for (int i = 0; i < N; ++i) xs[i] = s->m ? x[i] / s->m->e[i] : x[i];
+    orc_spectral(N, MUL_HILBERT, xs, hx);
     for (int i = 0; i < N; ++i) {
         real acc = 0.0;
-        for (int j = 0; j < N; ++j) acc += s->G[(size_t)j * N + i] * x[j];
+        for (int j = 0; j < N; ++j) acc += s->G[(size_t)j * N + i] * xs[j];
         t[i] = 0.5 * hx[i] - acc;
     }
     orc_spectral(N, MUL_DERIV, t, t);
     orc_lu_solve_T(N, s->LU, s->piv, t, out);
-    free(hx); free(t);
+    free(hx); free(t); free(xs);
 }
 
 /* Public: the transposed DtN of x on surface eta (tests). */
@@ -697,25 +699,55 @@ void orc_shoot_jacobian(const orc_problem *p, const real *c, real *r, real *J, r
  *   adjoint of etadot = -phi_y (G^T chi + (phi_x pt)') + phi_x et'
  *                       + phi_x phi_y pt' - g pt + tau (pt' (1+eta'^2)^{-3/2})'
  * (the two phi_y terms combine to App. C's -phi_y phi_x' P phit). */
+/* -D_x^T v with D_x = diag(1/xi') D_alpha: D_alpha (v / xi'), i.e. D v on the
+ * uniform grid (D^T = -D). */
+static void mesh_dxT_neg(const orc_mesh *m, int N, const real *in, real *out)
+{
+    if (!m) { orc_spectral(N, MUL_DERIV, in, out); return; }
+    for (int i = 0; i < N; ++i) out[i] = in[i] / m->e[i];
+    orc_spectral(N, MUL_DERIV, out, out);
+}
+
+/* P^T of mesh_project: v - xi' (sum v) / N on a mesh; P itself when uniform. */
+static void mesh_project_T(const orc_mesh *m, int N, const real *in, real *out)
+{
+    if (!m) { orc_spectral(N, MUL_PROJECT, in, out); return; }
+    if (ORC_PLANT == 8) { mesh_project(m, N, in, out); return; }
+    real s = 0.0;
+    for (int i = 0; i < N; ++i) s += in[i];
+    s /= N;
+    for (int i = 0; i < N; ++i) out[i] = in[i] - m->e[i] * s;
+}
+
+static void rhs_T_mesh(const orc_problem *p, const orc_mesh *m, int N, const real *q, const real *kb, real *out,
+                       real *Fdot);
 static void rhs_T(const orc_problem *p, const real *q, const real *kb, real *out, real *Fdot)
 {
-    int N = p->N;
+    rhs_T_mesh(p, NULL, p->N, q, kb, out, Fdot);
+}
+
+/* The same on N points of a mesh (NULL: uniform): every D of the uniform form
+ * becomes -D_x^T = D_alpha diag(1/xi'), P becomes P^T, and the DtN transpose
+ * carries diag(1/xi'). */
+static void rhs_T_mesh(const orc_problem *p, const orc_mesh *m, int N, const real *q, const real *kb, real *out,
+                       real *Fdot)
+{
     const real *eta = q, *phi = q + N;
     real *F = malloc(sizeof(real) * 2 * N);
-    orc_rhs(p, 1.0, q, 0, 0, F);                 /* base RHS (no T forcing in column 0) */
+    rhs_impl(p, m, N, 1.0, q, 0, 0, F);          /* base RHS (no T forcing in column 0) */
     real fd = 0.0;
     for (int i = 0; i < 2 * N; ++i) fd += kb[i] * F[i];
     *Fdot = fd;
 
     dtn_state s;
-    dtn_prepare(&s, N, p->h, eta);
+    dtn_prepare_mesh(&s, m, N, p->h, eta);
     real *phi_p = malloc(sizeof(real) * N), *Gphi = malloc(sizeof(real) * N);
     real *ux = malloc(sizeof(real) * N), *vy = malloc(sizeof(real) * N);
     real *w3 = malloc(sizeof(real) * N);
-    orc_spectral(N, MUL_DERIV, phi, phi_p);
+    mesh_dx(m, N, phi, phi_p);
     dtn_apply_one(&s, phi, Gphi);
     for (int i = 0; i < N; ++i) {              /* Eq. (uv:from:G), as in orc_rhs */
-        real ex = s.eta_x[i], d = 1.0 + ex * ex;
+        real ex = m ? s.eta_x[i] / m->e[i] : s.eta_x[i], d = 1.0 + ex * ex;
         ux[i] = (phi_p[i] - ex * Gphi[i]) / d;
         vy[i] = (ex * phi_p[i] + Gphi[i]) / d;
         w3[i] = 1.0 / (d * sqrt(d));
@@ -726,15 +758,15 @@ static void rhs_T(const orc_problem *p, const real *q, const real *kb, real *out
     real *t1 = malloc(sizeof(real) * N), *t2 = malloc(sizeof(real) * N);
     orc_spectral(N, MUL_FILTER, kb, et);
     orc_spectral(N, MUL_FILTER, kb + N, pt);
-    orc_spectral(N, MUL_PROJECT, pt, pt);
+    mesh_project_T(m, N, pt, pt);
     for (int i = 0; i < N; ++i) chi[i] = et[i] + vy[i] * pt[i];
     dtn_apply_T(&s, chi, Gchi);
-    orc_spectral(N, MUL_DERIV, et, d_et);
-    orc_spectral(N, MUL_DERIV, pt, d_pt);
+    mesh_dxT_neg(m, N, et, d_et);
+    mesh_dxT_neg(m, N, pt, d_pt);
     for (int i = 0; i < N; ++i) t1[i] = ux[i] * pt[i];
-    orc_spectral(N, MUL_DERIV, t1, t1);        /* (phi_x pt)' */
+    mesh_dxT_neg(m, N, t1, t1);                /* (phi_x pt)' */
     for (int i = 0; i < N; ++i) t2[i] = w3[i] * d_pt[i];
-    orc_spectral(N, MUL_DERIV, t2, t2);        /* (pt' (1+eta'^2)^{-3/2})' */
+    mesh_dxT_neg(m, N, t2, t2);                /* (pt' (1+eta'^2)^{-3/2})' */
     for (int i = 0; i < N; ++i) {
         real pb = Gchi[i] + t1[i];
         out[N + i] = pb;
@@ -1128,5 +1160,161 @@ void orc_dtn_segment(const orc_segment *sg, real h, const real *eta, const real 
     dtn_prepare_mesh(&s, m, sg->M, h, eta);
     dtn_apply_one(&s, phi, out);
     dtn_release(&s);
+    mesh_free(&b);
+}
+
+/* ------------------------------------------------------------------ */
+/* The discrete adjoint of the segmented shot (reading R18 carried to   */
+/* segments, meshes and any explicit tableau)                            */
+/* ------------------------------------------------------------------ */
+
+/* out_a = R^T in_b for the respacing R of respace() (sa -> sb): column j of R
+ * is the interpolant of the unit vector e_j at the new points, so R^T is the
+ * transpose of the very map the forward shot applies. */
+static void respace_T(const orc_segment *sa, const orc_segment *sb, const real *in_b, real *out_a)
+{
+    int Ma = sa->M, Mb = sb->M;
+    real *beta = malloc(sizeof(real) * Mb);
+    for (int j = 0; j < Mb; ++j) {
+        real xi, E, E1;
+        mesh_point(sb->rho, sb->centre, TWO_PI * j / Mb, &xi, &E, &E1);
+        beta[j] = mesh_inverse_one(sa->rho, sa->centre, xi);
+    }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic)
+#endif
+    for (int j = 0; j < Ma; ++j) {
+        real *ej = calloc(Ma, sizeof(real)), *col = malloc(sizeof(real) * Mb);
+        ej[j] = 1.0;
+        orc_interp(Ma, ej, Mb, beta, col);
+        real acc = 0.0;
+        for (int i = 0; i < Mb; ++i) acc += col[i] * in_b[i];
+        out_a[j] = acc;
+        free(ej); free(col);
+    }
+    free(beta);
+}
+
+/* f and grad f (n + 1 entries, grad[0] = d f / d T) of the segmented shot by
+ * its discrete adjoint.  Forward: every stage state of every step of every
+ * segment is kept.  Backward, per step: mu = Filt lambda (the step filter is
+ * symmetric); the stages in reverse order, kbar_i = dt (b_i mu + sum_{j>i}
+ * a_ji Ybar_j) and Ybar_i = DF(Y_i)^T kbar_i; lambda = mu + sum_i Ybar_i; and
+ * d f / d T gains kbar_i . F(Y_i) / T (dt is proportional to T).  Between
+ * segments lambda goes back through R^T.  lambda starts from the gradient of
+ * f = sum_i w_i^2 phi_i^2 / 2 on the last mesh. */
+int orc_objective_and_grad_segments(const orc_problem *p, int nseg, const orc_segment *sg, const orc_tableau *tb,
+                                    const real *c, real *f, real *grad)
+{
+    if (!segments_valid(p, nseg, sg, tb)) return -1;
+    int s = tb->s;
+    real T = c[0];
+    real **traj = malloc(sizeof(real *) * nseg);
+    real *y = malloc(sizeof(real) * 2 * p->N);
+    orc_initial(p, c, y);
+    for (int l = 0; l < nseg; ++l) {                 /* forward, stage states kept */
+        int M = sg[l].M;
+        size_t n2 = (size_t)2 * M;
+        if (l > 0) {
+            real *z = malloc(sizeof(real) * n2);
+            respace(&sg[l - 1], &sg[l], 2, y, z);
+            free(y);
+            y = z;
+        }
+        mesh_buf b;
+        const orc_mesh *m = mesh_make(&b, &sg[l]);
+        real dt = sg[l].theta * (T / 4.0) / sg[l].steps;
+        traj[l] = malloc(sizeof(real) * n2 * (size_t)s * sg[l].steps);
+        real *k = malloc(sizeof(real) * n2 * s);
+        for (int n = 0; n < sg[l].steps; ++n) {
+            for (int st = 0; st < s; ++st) {
+                real *ys = traj[l] + ((size_t)n * s + st) * n2;
+                for (size_t i = 0; i < n2; ++i) {
+                    real acc = 0.0;
+                    for (int j = 0; j < st; ++j) acc += tb->a[st * s + j] * k[(size_t)j * n2 + i];
+                    ys[i] = y[i] + dt * acc;
+                }
+                rhs_impl(p, m, M, T, ys, 0, 0, k + (size_t)st * n2);
+            }
+            for (size_t i = 0; i < n2; ++i) {
+                real acc = 0.0;
+                for (int j = 0; j < s; ++j) acc += tb->b[j] * k[(size_t)j * n2 + i];
+                y[i] += dt * acc;
+            }
+            orc_spectral(M, MUL_FILTER, y, y);
+            orc_spectral(M, MUL_FILTER, y + M, y + M);
+        }
+        free(k);
+        mesh_free(&b);
+    }
+    int ML = sg[nseg - 1].M;
+    real *w = malloc(sizeof(real) * ML);
+    segment_weights(&sg[nseg - 1], w);
+    real *lam = malloc(sizeof(real) * 2 * ML);
+    real sum = 0.0;
+    for (int i = 0; i < ML; ++i) {
+        real ri = w[i] * y[ML + i];
+        sum += ri * ri;
+        lam[i] = 0.0;
+        lam[ML + i] = w[i] * ri;
+    }
+    *f = 0.5 * sum;
+    real gT = 0.0;
+    for (int l = nseg - 1; l >= 0; --l) {            /* backward */
+        int M = sg[l].M;
+        size_t n2 = (size_t)2 * M;
+        mesh_buf b;
+        const orc_mesh *m = mesh_make(&b, &sg[l]);
+        real dt = sg[l].theta * (T / 4.0) / sg[l].steps;
+        real *mu = malloc(sizeof(real) * n2), *kb = malloc(sizeof(real) * n2 * s);
+        real *yb = malloc(sizeof(real) * n2);
+        for (int n = sg[l].steps - 1; n >= 0; --n) {
+            orc_spectral(M, MUL_FILTER, lam, mu);
+            orc_spectral(M, MUL_FILTER, lam + M, mu + M);
+            for (int st = 0; st < s; ++st)
+                for (size_t i = 0; i < n2; ++i) kb[(size_t)st * n2 + i] = dt * tb->b[st] * mu[i];
+            memcpy(lam, mu, sizeof(real) * n2);
+            for (int st = s - 1; st >= 0; --st) {
+                real Fd;
+                rhs_T_mesh(p, m, M, traj[l] + ((size_t)n * s + st) * n2, kb + (size_t)st * n2, yb, &Fd);
+                gT += Fd / T;
+                for (size_t i = 0; i < n2; ++i) lam[i] += yb[i];
+                for (int j = 0; j < st; ++j) {
+                    real a = tb->a[st * s + j];
+                    if (a != 0.0)
+                        for (size_t i = 0; i < n2; ++i) kb[(size_t)j * n2 + i] += dt * a * yb[i];
+                }
+            }
+        }
+        free(mu); free(kb); free(yb);
+        mesh_free(&b);
+        free(traj[l]);
+        if (l > 0) {
+            int Mp = sg[l - 1].M;
+            real *z = malloc(sizeof(real) * 2 * Mp);
+            respace_T(&sg[l - 1], &sg[l], lam, z);
+            respace_T(&sg[l - 1], &sg[l], lam + M, z + Mp);
+            free(lam);
+            lam = z;
+        }
+    }
+    grad[0] = gT;
+    for (int kk = 1; kk <= p->n; ++kk) {
+        real g = 0.0;
+        for (int r = 0; r < 2 * p->N; ++r) g += basis_entry(p, r, kk) * lam[r];
+        grad[kk] = g;
+    }
+    free(traj); free(y); free(w); free(lam);
+    return 0;
+}
+
+/* Public (tests): the transposed variational RHS on a segment's mesh at the
+ * base state q, applied to kb (2M); *Fdot = kb . F(q). */
+void orc_rhs_T_segment(const orc_problem *p, const orc_segment *sg, const real *q, const real *kb, real *out,
+                       real *Fdot)
+{
+    mesh_buf b;
+    const orc_mesh *m = mesh_make(&b, sg);
+    rhs_T_mesh(p, m, sg->M, q, kb, out, Fdot);
     mesh_free(&b);
 }

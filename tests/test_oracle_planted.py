@@ -115,6 +115,26 @@ def mesh_rhs_gap(L, N=64, rho=0.4):
     return np.max(np.abs(F - ref))
 
 
+def mesh_adjoint_gap(L, M=32, rho=0.4):
+    """The transposed variational RHS on a mesh against the explicit transpose."""
+    import ctypes as C
+    prob, _ = O.make_problem(M, 0, h=1.0, tau=0.05)
+    x = np.empty(M); e = np.empty(M); e1 = np.empty(M)
+    L.orc_mesh_eval(rho, 1, M, O._p(x), O._p(e), O._p(e1))
+    q = np.concatenate([1.0 + 0.08 * np.cos(x) + 0.02 * np.cos(2 * x), 0.05 * np.cos(x) - 0.01 * np.cos(3 * x)])
+    y = np.zeros((2 * M + 1, 2 * M))
+    y[0] = q
+    y[1:] = np.eye(2 * M)
+    out = np.empty_like(y)
+    seg = O._segments([(M, 1, 1.0, rho)])
+    L.orc_rhs_segment(C.byref(prob), seg, 7.0, O._p(y), 2 * M, 0, O._p(out))
+    kb = np.random.default_rng(1).standard_normal(2 * M)
+    got, fd = np.empty(2 * M), np.empty(1)
+    L.orc_rhs_T_segment(C.byref(prob), seg, O._p(q), O._p(kb), O._p(got), O._p(fd))
+    ref = out[1:] @ kb
+    return np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+
+
 @pytest.fixture(scope="module")
 def good():
     return O.load(O.build())
@@ -128,6 +148,7 @@ def good():
     (5, adjoint_gap, 1e-13),            # forward DtN used as its own transpose
     (6, mesh_dtn_error, 5e-12),         # 1/|xi'| of Eq. (G) dropped on a mesh
     (7, mesh_rhs_gap, 2e-12),           # P as the alpha-mean on a mesh
+    (8, mesh_adjoint_gap, 1e-14),       # P taken for its own transpose on a mesh
 ])
 def test_pin_catches_planted_mistake(good, plant, probe, bound):
     assert probe(good) < bound

@@ -241,3 +241,49 @@ def test_invalid_segments_are_refused():
                  [(32, 4, 0.5, 1.0), (32, 4, 0.5, 0.0)]):    # rho out of (0, 1]
         with pytest.raises(ValueError):
             O.shoot_segments(prob, segs, "rk4", c)
+
+
+# ----------------------------------------------------------------- the adjoint on segments
+@pytest.mark.parametrize("rho,h,tau", [(0.4, 1.0, 0.05), (1.0, 1.0, 0.0), (0.3, math.inf, 0.1)])
+def test_transposed_rhs_on_a_mesh_is_the_transpose(rho, h, tau):
+    """DF(q)^T kb on a mesh against the explicit transpose of the variational RHS
+    (its 2M columns from unit initial data): P^T, -D_x^T and the DtN transpose
+    with diag(1/xi'); and kb . F(q) for the T forcing."""
+    M = 32
+    prob, _ = O.make_problem(M, 0, h=h, tau=tau)
+    x, _, _ = O.mesh(rho, M)
+    base = 0.0 if math.isinf(h) else h
+    q = np.concatenate([base + 0.08 * np.cos(x) + 0.02 * np.cos(2 * x) - 0.01 * np.sin(3 * x),
+                        0.05 * np.cos(x) - 0.01 * np.cos(3 * x)])
+    y = np.zeros((2 * M + 1, 2 * M))
+    y[0] = q
+    y[1:] = np.eye(2 * M)
+    out = O.rhs_segment(prob, (M, 1, 1.0, rho), 7.0, y, ncol=2 * M)
+    kb = np.random.default_rng(1).standard_normal(2 * M)
+    got, fd = O.rhs_T_segment(prob, (M, 1, 1.0, rho), q, kb)
+    ref = out[1:] @ kb
+    assert np.max(np.abs(got - ref)) < 5e-15 * np.max(np.abs(ref))
+    assert abs(fd - kb @ out[0]) < 1e-15 * np.abs(kb) @ np.abs(out[0])
+
+
+def test_segmented_gradient_is_J_transpose_r():
+    """The discrete adjoint of the segmented shot (three segments, meshes refined
+    near pi then near 0, M doubled, DOP853, surface tension) against J^T r of
+    the segmented Jacobian, an independent algorithm; one uniform RK4 segment
+    reproduces the RK4 adjoint."""
+    N, n = 32, 4
+    x = x_grid(N)
+    basis = np.zeros((2 * N, n))
+    for k in range(1, n + 1):
+        basis[(N if k % 2 else 0):(2 * N if k % 2 else N), k - 1] = 2 * np.cos(k * x)
+    prob, keep = O.make_problem(N, n, h=1.0, tau=0.02, basis=basis, steps=12)
+    c = np.array([7.1, 0.03, 0.004, 0.002, -0.001])
+    segs = [(N, 6, 0.4, 1.0), (N, 6, 0.35, 0.5, 1), (2 * N, 6, 0.25, 0.3, 0)]
+    f, g = O.objective_and_grad_segments(prob, segs, "dop853", c)
+    r, J, f2 = O.shoot_jacobian_segments(prob, segs, "dop853", c)
+    jtr = J.T @ r
+    assert f == f2
+    assert np.linalg.norm(g - jtr) < 1e-13 * np.linalg.norm(jtr)
+    f1, g1 = O.objective_and_grad_segments(prob, [(N, 12, 1.0, 1.0)], "rk4", c)
+    f0, g0 = O.objective_and_grad(prob, c)
+    assert abs(f1 - f0) < 1e-13 * f0 and np.max(np.abs(g1 - g0)) < 1e-12 * np.max(np.abs(g0))
