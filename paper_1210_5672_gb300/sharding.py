@@ -18,10 +18,41 @@ The per-rank engine is a callable engine(c_r, basis_r) -> (r, J_r, f) with J_r
 of shape N x (len(c_r)); `gpu_engine` builds it on the library's
 shoot_jacobian.  The gather uses torch.distributed (NCCL on GPUs, gloo in the
 CPU tests).
+
+Failure detection is on the host.  Given the process group's key-value store,
+every rank reports its status ("ok", or its engine's error) before the
+collective and waits, for at most `timeout` seconds, for every other rank's
+report.  A rank that failed or never reported (it died or hangs) turns into a
+ShardFailure on every surviving rank, naming the ranks, and no rank enters a
+collective that could not complete.
 """
 from __future__ import annotations
 
+import time
+
 import numpy as np
+
+
+class ShardFailure(RuntimeError):
+    """A rank of the column split failed or did not report in time."""
+
+
+def _await_ranks(store, tag: str, world: int, timeout: float):
+    keys = [f"{tag}/{q}" for q in range(world)]
+    deadline = time.monotonic() + timeout
+    missing = keys
+    while True:
+        missing = [k for k in keys if not store.check([k])]
+        if not missing or time.monotonic() > deadline:
+            break
+        time.sleep(0.02)
+    if missing:
+        ranks = [int(k.rsplit("/", 1)[1]) for k in missing]
+        raise ShardFailure(f"ranks {ranks} did not report within {timeout} s")
+    bad = {q: store.get(k).decode() for q, k in enumerate(keys)}
+    bad = {q: v for q, v in bad.items() if v != "ok"}
+    if bad:
+        raise ShardFailure("; ".join(f"rank {q}: {v}" for q, v in sorted(bad.items())))
 
 
 def column_ranges(n: int, world: int):
@@ -49,15 +80,28 @@ def shard_problem(c, basis, rank: int, world: int):
     return c_r, basis_r, (s, e)
 
 
-def sharded_jacobian(c, basis, engine, rank: int, world: int, group=None):
+def sharded_jacobian(c, basis, engine, rank: int, world: int, group=None, store=None, tag: str = "jacobian",
+                     timeout: float = 60.0):
     """The full (r, J, f) of the problem (c, basis) on every rank, each rank
-    computing its block of columns with engine(c_r, basis_r) and one all-gather."""
+    computing its block of columns with engine(c_r, basis_r) and one all-gather.
+    With `store` (the process group's store; `tag` unique per call) the ranks
+    report to each other first and a failed or silent rank raises ShardFailure
+    on every surviving rank."""
     import torch
     import torch.distributed as dist
 
     n = np.asarray(basis).shape[1]
     c_r, basis_r, (s, e) = shard_problem(c, basis, rank, world)
-    r, J_r, f = engine(c_r, basis_r)
+    try:
+        r, J_r, f = engine(c_r, basis_r)
+        status = "ok"
+    except Exception as exc:              # reported to the other ranks, then raised here
+        if store is None or world == 1:
+            raise
+        status = f"engine failed: {type(exc).__name__}: {exc}"
+    if store is not None and world > 1:
+        store.set(f"{tag}/{rank}", status)
+        _await_ranks(store, tag, world, timeout)
     N = J_r.shape[0]
     ranges = column_ranges(n, world)
     width = 1 + max(b - a for a, b in ranges)          # T column + the widest block

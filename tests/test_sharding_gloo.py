@@ -102,3 +102,67 @@ def test_column_ranges_and_single_rank():
     r0, J0, f0 = O.shoot_jacobian(prob, c)
     norms = np.linalg.norm(J0, axis=0)
     assert max(np.linalg.norm(J[:, k] - J0[:, k]) / norms[k] for k in range(NMODES + 1)) < 1e-12
+
+
+def _failing_rank_main(rank, ws, port, q, mode):
+    """Rank 1 fails: its engine raises ("raise"), or it leaves between steps
+    without reporting ("exit"); the others must learn of it on the host through
+    the store and raise ShardFailure, never entering the all-gather."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+    sys.path.insert(0, ROOT)
+    from datetime import timedelta
+
+    import torch.distributed as dist
+
+    from paper_1210_5672_gb300.sharding import ShardFailure, sharded_jacobian
+    store = dist.TCPStore("127.0.0.1", port, ws, is_master=(rank == 0), timeout=timedelta(seconds=30))
+    dist.init_process_group("gloo", store=store, rank=rank, world_size=ws, timeout=timedelta(seconds=30))
+    c, basis = _problem()
+    engine = _oracle_engine()
+    if rank == 1 and mode == "raise":
+        def engine(c_r, basis_r):
+            raise RuntimeError("planted engine failure")
+    if rank == 1 and mode == "exit":
+        q.put((rank, "left"))
+        q.close()
+        q.join_thread()                 # the queue's feeder thread writes before the exit
+        os._exit(0)
+    try:
+        sharded_jacobian(c, basis, engine, rank, ws, store=store, tag="t", timeout=3.0)
+        q.put((rank, "no error"))
+    except ShardFailure as e:
+        q.put((rank, f"ShardFailure: {e}"))
+    store.set(f"done/{rank}", "1")
+    if rank == 0:                       # the store lives here: keep it up for the others
+        import time
+        deadline = time.monotonic() + 10.0
+        live = [r for r in range(ws) if not (mode == "exit" and r == 1)]
+        while time.monotonic() < deadline and not all(store.check([f"done/{r}"]) for r in live):
+            time.sleep(0.02)
+    q.close()
+    q.join_thread()
+    os._exit(0)
+
+
+@pytest.mark.parametrize("mode,ws", [("raise", 2), ("exit", 2), ("exit", 3)])
+def test_a_failed_rank_is_detected_on_the_host(mode, ws):
+    import time
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    t0 = time.monotonic()
+    procs = [ctx.Process(target=_failing_rank_main, args=(r, ws, port, q, mode)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    outs = dict(q.get(timeout=120) for _ in range(ws))
+    for p in procs:
+        p.join(timeout=60)
+    assert [p.exitcode for p in procs] == [0] * ws
+    assert time.monotonic() - t0 < 90
+    for rank, msg in outs.items():
+        if mode == "exit" and rank == 1:
+            assert msg == "left"
+        elif mode == "exit":
+            assert msg.startswith("ShardFailure") and "[1]" in msg and "did not report" in msg, msg
+        else:
+            assert msg.startswith("ShardFailure") and "rank 1: engine failed" in msg and "planted" in msg, msg
