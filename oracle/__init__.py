@@ -145,6 +145,7 @@ def _set_signatures(L):
         "orc_objective_and_grad_segments": (C.c_int, [P, C.c_int, C.POINTER(Segment), C.POINTER(Tableau), _D, _D,
                                                       _D]),
         "orc_rhs_T_segment": (None, [P, C.POINTER(Segment), _D, _D, _D, _D]),
+        "orc_energy_segment": (C.c_double, [P, C.POINTER(Segment), _D]),
         "orc_threads": (C.c_int, []),
         "orc_set_threads": (None, [C.c_int]),
     }
@@ -515,3 +516,8 @@ def rhs_T_segment(prob: Problem, seg, q, kb):
     out, fd = np.empty_like(kb), np.empty(1)
     lib().orc_rhs_T_segment(C.byref(prob), sa, _p(q), _p(kb), _p(out), _p(fd))
     return out, float(fd[0])
+
+
+def energy_segment(prob: Problem, seg, q) -> float:
+    """The energy monitor of Sec. 4 for a state stored on a segment's mesh."""
+    return lib().orc_energy_segment(C.byref(prob), _segments([seg]), _p(_f64(q)))

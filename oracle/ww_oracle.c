@@ -1318,3 +1318,30 @@ void orc_rhs_T_segment(const orc_problem *p, const orc_segment *sg, const real *
     rhs_T_mesh(p, m, sg->M, q, kb, out, Fdot);
     mesh_free(&b);
 }
+
+/* Public (tests): the energy of Sec. 4's monitor for a state stored on a
+ * segment's mesh: 1/2 int (phi G phi + g (eta - hbar)^2) dx + tau int
+ * (sqrt(1 + eta'^2) - 1) dx, each integral int f dx = int f(xi(alpha)) xi'
+ * dalpha by the trapezoid rule in alpha. */
+real orc_energy_segment(const orc_problem *p, const orc_segment *sg, const real *q)
+{
+    int M = sg->M;
+    mesh_buf b;
+    const orc_mesh *m = mesh_make(&b, sg);
+    const real *eta = q, *phi = q + M;
+    real *Gphi = malloc(sizeof(real) * M), *ex = malloc(sizeof(real) * M);
+    dtn_state s;
+    dtn_prepare_mesh(&s, m, M, p->h, eta);
+    dtn_apply_one(&s, phi, Gphi);
+    dtn_release(&s);
+    mesh_dx(m, M, eta, ex);
+    real mean = isinf(p->h) ? 0.0 : p->h, e = 0.0;
+    for (int i = 0; i < M; ++i) {
+        real d = eta[i] - mean;
+        real dens = 0.5 * (phi[i] * Gphi[i] + p->g * d * d) + p->tau * (sqrt(1.0 + ex[i] * ex[i]) - 1.0);
+        e += dens * (m ? m->e[i] : 1.0);
+    }
+    free(Gphi); free(ex);
+    mesh_free(&b);
+    return e * TWO_PI / M;
+}

@@ -287,3 +287,19 @@ def test_segmented_gradient_is_J_transpose_r():
     f1, g1 = O.objective_and_grad_segments(prob, [(N, 12, 1.0, 1.0)], "rk4", c)
     f0, g0 = O.objective_and_grad(prob, c)
     assert abs(f1 - f0) < 1e-13 * f0 and np.max(np.abs(g1 - g0)) < 1e-12 * np.max(np.abs(g0))
+
+
+@pytest.mark.parametrize("h,tau,N,steps", [(1.0, 0.0, 64, 8), (math.inf, 0.05, 32, 24), (0.5, 0.02, 32, 24)])
+def test_energy_is_conserved_across_segments_and_meshes(h, tau, N, steps):
+    """The energy monitor of Sec. 4 (integrals in x by the mesh's own quadrature,
+    weights xi') before and after three segments: refined near pi, then near 0,
+    twice the points, DOP853 (steps chosen inside its stability region).  The
+    paper reports energy conserved to about 14 digits in double precision."""
+    prob, _ = O.make_problem(N, 3, h=h, tau=tau)
+    c = np.array([6.5, 0.05, 0.01, -0.004])
+    q0 = O.initial(prob, c)
+    E0 = O.energy(prob, q0)
+    assert O.energy_segment(prob, (N, 1, 1.0, 1.0), q0) == E0
+    segs = [(N, steps, 0.4, 1.0), (2 * N, steps, 0.3, 0.4, 1), (2 * N, steps, 0.3, 0.3, 0)]
+    q = O.evolve_segments(prob, segs, "dop853", c[0], q0)
+    assert abs(O.energy_segment(prob, segs[-1], q) - E0) < 1e-13 * E0
