@@ -303,3 +303,21 @@ def test_energy_is_conserved_across_segments_and_meshes(h, tau, N, steps):
     segs = [(N, steps, 0.4, 1.0), (2 * N, steps, 0.3, 0.4, 1), (2 * N, steps, 0.3, 0.3, 0)]
     q = O.evolve_segments(prob, segs, "dop853", c[0], q0)
     assert abs(O.energy_segment(prob, segs[-1], q) - E0) < 1e-13 * E0
+
+
+def test_evenness_is_preserved_across_segments_and_meshes():
+    """Sec. 2.3: even initial data stay even.  The meshes of Eq. (xi) are odd
+    about x = 0 (x_{M-j} = 2 pi - x_j), so the stored values of an even state
+    satisfy q_j = q_{M-j} on every segment, through respacing, to roundoff."""
+    N = 32
+    prob, _ = O.make_problem(N, 3, h=1.0, tau=0.01)
+    c = np.array([6.8, 0.05, 0.01, -0.004])
+    q0 = O.initial(prob, c)
+    segs = [(N, 12, 0.4, 1.0), (2 * N, 12, 0.3, 0.4, 1), (2 * N, 12, 0.3, 0.3, 0)]
+    q = O.evolve_segments(prob, segs, "dop853", c[0], q0)
+    M = 2 * N
+    x, _, _ = O.mesh(0.3, M, 0)
+    j = np.arange(1, M)
+    assert np.max(np.abs(x[M - j] - (2 * np.pi - x[j]))) < 1e-14
+    for part in (q[:M], q[M:]):           # roundoff of an O(1) state over 36 steps
+        assert np.max(np.abs(part[j] - part[M - j])) < 5e-14
