@@ -62,6 +62,31 @@ DEEP_TENSION = Workload("N1024_n256_steps2048_deep_tau0.1", N=1024, n=256, steps
 
 ALL = {w.name: w for w in (SMALL, MEDIUM, LARGE, SHALLOW, DEEP_TENSION)}
 
+# Time segments with adaptive meshes (Sec. 2.2), shaped like the paper's double
+# precision run of solution O (Table param:OA): four segments with theta = (0.2,
+# 0.3, 0.3, 0.2) of T/4, rho = (1, 0.4, 0.1, 0.1), n about M_1 / 3, steps in the
+# printed proportions 192 : 432 : 576 : 480 scaled by M_1 / 4608, for DOP853.
+# The grids are powers of two that keep the coarsest spacing from growing (the
+# paper's rule M_{l+1} / M_l >= (5 + 3 rho_l) / (5 + 3 rho_{l+1}) when rho
+# decreases); the printed last rho of 0.09 would need M_4 slightly above M_3, so
+# the last segment keeps rho = 0.1.  Meshes are refined near x = 0, where the
+# initial crest of eta_0 = h + sum c_k cos(kx) sits.  Not part of ALL: the RK4
+# benchmark never selects it.
+SEGMENTED = Workload("N512_n170_segments4_h1", N=512, n=170, steps=186, amp=0.2,
+                     meta={"segments": ((512, 21, 0.2, 1.0, 0), (1024, 48, 0.3, 0.4, 0),
+                                        (2048, 64, 0.3, 0.1, 0), (2048, 53, 0.2, 0.1, 0)),
+                           "tableau": "dop853"})
+
+
+def spacing_rule_ok(segments) -> bool:
+    """Sec. 2.2's rule: where rho decreases from one segment to the next, M
+    grows at least by (5 + 3 rho_l) / (5 + 3 rho_{l+1}), so the coarsest spacing
+    8 / ((5 + 3 rho) M) never grows."""
+    for (Ma, _, _, ra, *_), (Mb, _, _, rb, *_) in zip(segments, segments[1:]):
+        if rb < ra and Mb * (5 + 3 * rb) < Ma * (5 + 3 * ra):
+            return False
+    return True
+
 
 def linear_period(g: float, tau: float, h: float) -> float:
     """T = 2 pi / omega with omega^2 = (g + tau) tanh(h) at k = 1 (Eq. lin:soln)."""

@@ -321,3 +321,20 @@ def test_evenness_is_preserved_across_segments_and_meshes():
     assert np.max(np.abs(x[M - j] - (2 * np.pi - x[j]))) < 1e-14
     for part in (q[:M], q[M:]):           # roundoff of an O(1) state over 36 steps
         assert np.max(np.abs(part[j] - part[M - j])) < 5e-14
+
+
+def test_the_segmented_workload_runs_through_the_oracle():
+    """The segmented workload's structure (four segments, rho down to 0.1, M
+    doubling twice, DOP853), shrunk 16x in M and 4x in steps, is a valid input
+    to the oracle, and energy is conserved through it."""
+    from paper_1210_5672_gb300 import workloads as W
+    w = W.SEGMENTED
+    segs = [(M // 16, max(1, s // 4), th, rho, ctr) for (M, s, th, rho, ctr) in w.meta["segments"]]
+    N = segs[0][0]
+    c, _ = W.coefficients(W.Workload("seg_small", N=N, n=N // 3, steps=1, amp=0.05))
+    prob, _ = O.make_problem(N, N // 3, h=w.h)
+    q0 = O.initial(prob, c)
+    q = O.evolve_segments(prob, segs, w.meta["tableau"], c[0], q0)
+    assert q.shape == (2 * segs[-1][0],) and np.all(np.isfinite(q))
+    E0 = O.energy(prob, q0)
+    assert abs(O.energy_segment(prob, segs[-1], q) - E0) < 1e-11 * E0

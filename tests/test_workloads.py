@@ -46,3 +46,23 @@ def test_uneven_batch_recipe():
         assert wc.steps == min(w.steps, 64)
         # the cap keeps each shot's dt
         assert abs(cc[0] / (4 * wc.steps) - c[0] / (4 * w.steps)) <= 1e-15 * c[0]
+
+
+def test_segmented_recipe():
+    """The segmented workload (shaped like the paper's solution O, Table
+    param:OA): theta sums to 1, the first segment is uniform on N points, the
+    grids are powers of two, the spacing rule of Sec. 2.2 holds, and the
+    steps add up.  The printed table itself breaks the rule between its second
+    and third segments (6912 / 6144 = 1.125 < 6.2 / 5.3), which the rule check
+    detects."""
+    w = W.SEGMENTED
+    segs = w.meta["segments"]
+    assert abs(sum(s[2] for s in segs) - 1.0) < 1e-12
+    assert segs[0][0] == w.N and segs[0][3] == 1.0
+    assert all(s[0] & (s[0] - 1) == 0 for s in segs)
+    assert sum(s[1] for s in segs) == w.steps
+    assert W.spacing_rule_ok(segs)
+    printed = ((4608, 192, 0.2, 1.0), (6144, 432, 0.3, 0.4), (6912, 576, 0.3, 0.1), (8192, 480, 0.2, 0.09))
+    assert not W.spacing_rule_ok(printed)
+    assert W.spacing_rule_ok(printed[:2]) and not W.spacing_rule_ok(printed[1:3]) and W.spacing_rule_ok(printed[2:])
+    assert w.name not in W.ALL
