@@ -5,18 +5,23 @@ outputs included) on the seeded N = 2048 workload (512 Fourier unknowns + T,
 1024 RK4 steps, h = 1, c_1 = 0.4, c_k = 0.4^k u_k).  Prints ONE JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--form mixed|fp64]
-                  [--impl ours|reference] [--workload NAME]
+                  [--impl ours|reference] [--workload NAME] [--no-fp64-form]
 
 --form mixed (default) is the tensor-core form (FP32-accurate inverse, FP64-
-accurate Ozaki products, iterative refinement to a 1e-13 residual); --form
-fp64 is the plain FP64 form it is compared with (~2 minutes per Jacobian at
-N = 2048: run it with --warmup 3 --steps 1).
+accurate Ozaki products, iterative refinement to a 1e-13 residual).  Its line
+also carries the metric's comparison: `fp64_form`, one timed Jacobian of the
+plain FP64 form on the same workload (~1.5 minutes), and `error_vs_oracle`,
+both forms' errors against the oracle's stored samples of the workload.
+--form fp64 times the plain FP64 form alone.  `value` is timed with the
+library's phase events off; one more Jacobian with them on gives the
+per-kernel `rooflines` (and, in the mixed form, the measured refinement
+residual in `stats`).
 
 --impl reference times the CPU FP64 oracle (the only baseline: the paper's
-code is not available) on a bounded sample of the same workload.  Under
-torchrun every rank runs an independent replica (its own seed; the path has
-no exchange step), the slowest rank's time is reported and value counts the
-columns of all ranks.
+code is not available) on a bounded sample of the same workload, scaled to
+the full Jacobian (marked "extrapolated").  Under torchrun every rank runs an
+independent replica (its own seed; the path has no exchange step), the
+slowest rank's time is reported and value counts the columns of all ranks.
 """
 from __future__ import annotations
 
@@ -143,44 +148,173 @@ def flush_l2(buf):
     buf.add_(1.0)   # 512 MB read + write: evicts the 129 MB L2
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the timed product
-# kernel, from the ncu captures summarised under profiles/ (None: not captured
-# since the kernel last changed).
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# roofline kernel, from one ncu capture of the current k_ozaki's column G-apply
-# launch on the N = 2048 workload; other workloads and forms have no capture of
-# their current kernel: null.
-TRAFFIC_BYTES = {("mixed", "N2048_n512_steps1024_h1"): 85.35e6}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
+# kernel, from one ncu capture of the current kernel on the N = 2048 workload
+# (summaries under profiles/); a kernel changed since its capture has none (null).
+TRAFFIC_BYTES = {("mixed", "N2048_n512_steps1024_h1", "k_ozaki"): 85.35e6}
 
 # slice pairs (p, q) with p + q <= 6 of the 7 x 7 integer digits: 28 bf16 GEMMs
 OZAKI_PAIRS = 28
+# slice pairs with p + q <= 2 of the 3 x 3 bf16 slices of the inverse update's products
+NS_PAIRS = 6
+# FP32 pipe of GB300: 128 FP32 lanes per SM, 152 SMs, FMA = 2 flop, 2070 MHz
+FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12
+# k_col_rhs, double-float Stockham radix-8 FFTs: about 120 FP32 flop per point and
+# radix-8 pass, log8(N) passes, 5.5 transforms of N points per column
+DF_FLOP_PER_POINT_PASS = 120
+COLRHS_FFTS = 5.5
+# k_assemble_sym: about 80 FP64 flop per unordered pair (i, j) for both A and G
+ASM_FLOP_PER_PAIR = 80
 
 
-def roofline_for(form, timing, w, pk):
-    """Roofline of the dominant kernel, from the GKERNEL phase: the events around
-    the one product kernel of each stage's column G-apply (k_ozaki in the mixed
-    form, k_dgemm in the FP64 form; the same kernels carry the solves and the
-    FP64 factorisation), so duration = GKERNEL ms / launches."""
+def _entry(kernel, bound, flops, dur, peak, unit, src, w, form, **extra):
+    achieved = flops / dur / 1e12
+    e = {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+         "frac": achieved / peak, "traffic": TRAFFIC_BYTES.get((form, w.name, kernel)),
+         "launch_ms": dur * 1e3, "peak_source": src}
+    e.update(extra)
+    return e
+
+
+def rooflines(form, timing, w, pk):
+    """Per-kernel rooflines of the profiled Jacobian, from the phase events that
+    bracket single kernels on the stream each runs on: gkernel (the column
+    G-apply product), inverse (the two products of the inverse update),
+    assembly (k_assemble_sym), colrhs (k_col_rhs).  Returns (dominant, list):
+    the dominant kernel is the one with the largest share of the stage."""
     N, nc = w.N, w.n + 1
-    ms, cnt = timing["gkernel"]
-    if cnt == 0:
-        return None
-    dur = ms / cnt / 1e3
-    fp64_flops = 2.0 * N * N * nc          # the FP64 product G Gamma it delivers
+    out = []
+
+    def dur(phase, per_phase=1):
+        ms, cnt = timing.get(phase, (0.0, 0))
+        return (ms / cnt / per_phase / 1e3, cnt) if cnt else (None, 0)
+
+    g_fp64 = 2.0 * N * N * nc                 # the FP64 product G Gamma the G-apply delivers
+    fp64_src = "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"
     if form == "fp64":
-        achieved = fp64_flops / dur / 1e12
-        return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES.get(("fp64", w.name)), "kernel": "k_dgemm",
-                "launch_ms": dur * 1e3,
-                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"}
-    peak = pk.get("bf16_tflops_sustained") or 1700.0
-    src = "of measured (bf16_tflops_sustained)" if pk.get("bf16_tflops_sustained") else "of fallback (sustained)"
-    achieved = OZAKI_PAIRS * fp64_flops / dur / 1e12
-    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": TRAFFIC_BYTES.get(("mixed", w.name)), "kernel": "k_ozaki",
-            "launch_ms": dur * 1e3, "fp64_equivalent_tflops": fp64_flops / dur / 1e12,
-            "work": f"{OZAKI_PAIRS} bf16 digit-pair GEMMs of {N} x {nc} x {N}",
-            "peak_source": src}
+        d, _ = dur("gkernel")
+        if d:
+            out.append(_entry("k_dgemm", "alu", g_fp64, d, FP64_PEAK_TFLOPS, "TFLOP/s", fp64_src, w, form,
+                              role="column G-apply", work=f"2 N^2 (n+1) FP64 flop, N={N}, n+1={nc}",
+                              share_ms_per_stage=d * 1e3))
+    else:
+        peak = pk.get("bf16_tflops_sustained") or 1700.0
+        src = "of measured (bf16_tflops_sustained)" if pk.get("bf16_tflops_sustained") else "of fallback (sustained)"
+        d, _ = dur("gkernel")
+        if d:
+            out.append(_entry("k_ozaki", "tensor", OZAKI_PAIRS * g_fp64, d, peak, "TFLOP/s", src, w, form,
+                              role="column G-apply (7+7 digits)",
+                              work=f"{OZAKI_PAIRS} bf16 digit-pair GEMMs of {N} x {nc} x {N}",
+                              method_fp64_tflops=g_fp64 / d / 1e12, share_ms_per_stage=d * 1e3))
+        d, _ = dur("inverse", 2)
+        if d:
+            ns = NS_PAIRS * 2.0 * N ** 3
+            out.append(_entry("k_tc_gemm<128,3,3,32>", "tensor", ns, d, peak, "TFLOP/s", src, w, form,
+                              role="inverse update X <- X (2I - A X), one of its two products",
+                              work=f"{NS_PAIRS} bf16 slice-pair GEMMs of {N}^3",
+                              method_fp32_tflops=2.0 * N ** 3 / d / 1e12, share_ms_per_stage=2 * d * 1e3))
+    d, _ = dur("assembly")
+    if d:
+        out.append(_entry("k_assemble_sym", "alu", ASM_FLOP_PER_PAIR * N * N / 2.0, d, FP64_PEAK_TFLOPS, "TFLOP/s",
+                          fp64_src, w, form, role="A = 1/2 I + K and G",
+                          work=f"~{ASM_FLOP_PER_PAIR} FP64 flop per unordered pair, N^2/2 pairs",
+                          share_ms_per_stage=d * 1e3))
+    d, _ = dur("colrhs")
+    if d:
+        if form == "fp64":
+            work = COLRHS_FFTS * 5.0 * N * math.log2(N) * nc
+            out.append(_entry("k_col_rhs", "alu", work, d, FP64_PEAK_TFLOPS, "TFLOP/s", fp64_src, w, form,
+                              role="variational RHS + RK update", work=f"{COLRHS_FFTS} FP64 FFTs (5 N log2 N) per column",
+                              share_ms_per_stage=d * 1e3))
+        else:
+            work = DF_FLOP_PER_POINT_PASS * N * (math.log2(N) / 3.0) * COLRHS_FFTS * nc
+            out.append(_entry("k_col_rhs", "alu", work, d, FP32_PEAK_TFLOPS, "TFLOP/s",
+                              "derived: 128 FP32 lanes x 2 flop/clk/SM x 152 SMs x 2070 MHz", w, form,
+                              role="variational RHS + RK update (double-float FFTs)",
+                              work=f"{COLRHS_FFTS} double-float FFTs per column, ~{DF_FLOP_PER_POINT_PASS} FP32 "
+                                   f"flop per point and radix-8 pass", share_ms_per_stage=d * 1e3))
+    if not out:
+        return None, []
+    dom = max(out, key=lambda e: e["share_ms_per_stage"])
+    return dom, out
+
+
+def error_vs_oracle(w, r, J, f):
+    """Errors of one Jacobian against the oracle's stored samples of the same
+    workload (tests/golden/full_n2048_samples.json, written from the oracle
+    alone): |df|/|f|, ||dr||/||r|| and per sampled column ||dJ_k|| /
+    max(||J_k||, 1e-4 max_j ||J_j||) over every 16th row.  Each is also given
+    as a ratio to the oracle's own one-ulp spread (how far the oracle moves
+    when c_1 moves by one ulp), the parity test's tolerance unit."""
+    path = os.path.join(ROOT, "tests", "golden", "full_n2048_samples.json")
+    if w.name != W.LARGE.name or not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        g = json.load(fh)
+    rows = np.asarray(g["rows"])
+    big = max(v["norm"] for v in g["columns"].values())
+    ej = {}
+    for k, v in g["columns"].items():
+        ref = np.asarray(v["values"])
+        den = max(np.linalg.norm(ref), 1e-4 * big * math.sqrt(len(rows) / g["N"]))
+        ej[k] = float(np.linalg.norm(J[0 if k == "T" else int(k), rows] - ref) / den)
+    worst = max(ej, key=ej.get)
+    out = {"f_rel": abs(f - g["f"]) / abs(g["f"]),
+           "r_rel": float(np.linalg.norm(r[rows] - np.asarray(g["r"])) / np.linalg.norm(g["r"])),
+           "J_max_col_rel": ej[worst], "J_worst_col": worst, "J_median_col_rel": float(np.median(list(ej.values()))),
+           "columns_compared": len(ej), "rows_compared": len(rows),
+           "reference": "oracle samples (tests/golden/full_n2048_samples.json)"}
+    sp = g.get("spread")
+    if sp:
+        out["J_max_ratio_to_oracle_ulp_spread"] = max(ej[k] / sp["columns"][k] for k in ej)
+        out["oracle_ulp_spread_f"] = sp["f"]
+    return out
+
+
+def _jacobian_rate(ww, ctx, ct, outs, stream, flush, k, warm):
+    """Warm-up calls, then k device-timed calls (L2 flushed between them, outside
+    the events): (seconds per call, kernel launches of the timed calls)."""
+    r, J, f = outs
+    import torch
+    for _ in range(warm):
+        ww.shoot_jacobian(ctx, ct, r, J, f)
+    torch.cuda.synchronize()
+    times, launches = [], 0
+    for _ in range(k):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ww.shoot_jacobian(ctx, ct, r, J, f)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        launches += ctx.stats()["launches"]   # the library counts the kernel nodes it replays
+    return times, launches
+
+
+def run_fp64_form(ww, w, c, dev, flush):
+    """The plain FP64 form on the same workload, for the metric's comparison: one
+    timed Jacobian (device-resident inputs, L2 flushed before it).  Its warm-up
+    is one call of a one-step context of the same sizes (loads the kernels and
+    sizes the allocator); the timed call includes the capture of its own step
+    graph, a few milliseconds against minutes."""
+    import torch
+    cw = c.copy()
+    cw[0] = c[0] / w.steps
+    with ww.Context(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=1, precision=ww.WW_FP64) as warm:
+        r, J, f = warm.empty_outputs()
+        ww.shoot_jacobian(warm, torch.tensor(cw, dtype=torch.float64, device=dev), r, J, f)
+    torch.cuda.synchronize()
+    ctx = ww.Context(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps, precision=ww.WW_FP64)
+    stream = torch.cuda.Stream(dev)
+    ctx.set_stream(stream)
+    outs = ctx.empty_outputs()
+    ct = torch.tensor(c, dtype=torch.float64, device=dev)
+    times, launches = _jacobian_rate(ww, ctx, ct, outs, stream, flush, 1, 0)
+    res = tuple(x.cpu().numpy() for x in outs)
+    ctx.close()
+    return times[0], launches, res
 
 
 def run_ours(args):
@@ -200,38 +334,21 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     ctx = ww.Context(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps, precision=prec)
     ct = torch.tensor(c, dtype=torch.float64, device=dev)
-    r, J, f = ctx.empty_outputs()
+    outs = ctx.empty_outputs()
+    r, J, f = outs
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)
     stream = torch.cuda.Stream(dev)
     ctx.set_stream(stream)
-    ctx.set_timing(True)     # the same step program (with its event nodes) in warm-up and timed steps
-    for _ in range(args.warmup):
-        ww.shoot_jacobian(ctx, ct, r, J, f)
-    torch.cuda.synchronize()
-    # ---- timed region: K Jacobians, L2 flushed between them (outside the events)
-    times, phase, gpu_launches = [], {p: [0.0, 0] for p in ww.PHASES}, 0
+    # ---- timed region: K Jacobians, phase events off, L2 flushed between them
     barrier(ws)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush_l2(flush)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ww.shoot_jacobian(ctx, ct, r, J, f)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1) / 1e3)
-            # our kernels in this call: the library counts the kernel nodes it replays
-            gpu_launches += ctx.stats()["launches"]
-            for p, (ms, cnt) in ctx.timing().items():
-                phase[p][0] += ms
-                phase[p][1] += cnt
+        times, gpu_launches = _jacobian_rate(ww, ctx, ct, outs, stream, flush, args.steps, args.warmup)
     torch.cuda.synchronize()
     barrier(ws)
     clocks = clk.summary()
-    ctx.set_timing(False)
     t_step, value = replica_rate(sum(times) / len(times), ws, w.n + 1)
+    res = (r.cpu().numpy(), J.cpu().numpy(), float(f.item()))
     # ---- end to end through the host-buffer entry point (pinned host memory)
     ch = torch.tensor(c, dtype=torch.float64).pin_memory().numpy()
     rh = torch.empty(w.N, dtype=torch.float64).pin_memory().numpy()
@@ -245,10 +362,33 @@ def run_ours(args):
         ww.shoot_jacobian_host(ctx, ch, rh, Jh, fh)
         e2e_t.append(time.perf_counter() - t0)
     _, e2e_value = replica_rate(sum(e2e_t) / len(e2e_t), ws, w.n + 1)
-    timing = {p: tuple(v) for p, v in phase.items()}
-    roof = roofline_for(form, timing, w, peaks())
+    # ---- profiled Jacobian: phase events on (per-kernel durations on the streams
+    # the kernels run on) and, in the mixed form, the refinement residual
+    # measured after the last correction of every 256th solve
+    ctx.set_timing(True)
+    if form == "mixed":
+        ctx.set_verify(256)
+    _jacobian_rate(ww, ctx, ct, outs, stream, flush, 1, 0)
+    timing = ctx.timing()
     stats = ctx.stats()
+    ctx.set_timing(False)
     ctx.close()
+    dom, roofs = rooflines(form, timing, w, peaks())
+    errors = {form: error_vs_oracle(w, *res)} if ws == 1 else {}
+    fp64 = None
+    if form == "mixed" and ws == 1 and not args.no_fp64_form and not args.rk_steps:
+        t64, l64, res64 = run_fp64_form(ww, w, c, dev, flush)
+        fp64 = {"value": (w.n + 1) / t64, "unit": "Jacobian columns/s", "ms_per_step": t64 * 1e3,
+                "steps": 1, "gpu_launches": l64,
+                "timing": "one device-timed Jacobian (CUDA events), L2 flushed before it",
+                "mixed_over_fp64": value / ((w.n + 1) / t64)}
+        errors["fp64"] = error_vs_oracle(w, *res64)
+        norms = np.linalg.norm(res64[1], axis=1)
+        col = np.linalg.norm(res[1] - res64[1], axis=1) / np.maximum(norms, 1e-4 * norms.max())
+        errors["mixed_vs_fp64"] = {"J_max_col_rel": float(col.max()), "J_worst_col": int(col.argmax()),
+                                   "J_median_col_rel": float(np.median(col)),
+                                   "f_rel": abs(res[2] - res64[2]) / abs(res64[2]),
+                                   "columns_compared": int(len(col)), "rows_compared": int(w.N)}
     if rank != 0:
         return None
     out = {
@@ -262,12 +402,19 @@ def run_ours(args):
                    "l2": "flushed between timed steps (512 MB write)"},
         "e2e": {"value": e2e_value, "unit": "Jacobian columns/s",
                 "h2d_bytes_per_step": 8 * (w.n + 1), "d2h_bytes_per_step": 8 * (w.N + w.N * (w.n + 1) + 1)},
-        "roofline": roof,
-        "phases_ms_per_step": {p: v[0] / args.steps for p, v in timing.items()},
+        "roofline": dom,
+        "rooflines": roofs,
+        "roofline_timing": "phase events around each kernel in one more Jacobian of the same workload "
+                           "(value itself is timed with phase events off)",
+        "phases_ms_per_step": {p: v[0] for p, v in timing.items()},
         "stats": stats,
         "gpu_launches": gpu_launches,
         "clocks": clocks,
     }
+    if fp64 is not None:
+        out["fp64_form"] = fp64
+    if errors:
+        out["error_vs_oracle"] = errors
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(w, c)
     return out
@@ -465,7 +612,8 @@ def cpu_baseline_gradient(w, c):
     t1 = time.perf_counter() - t0
     return {"value": 1.0 / (t1 * w.steps), "unit": "gradients/s", "cores": O.threads(), "kind": "oracle",
             "sample": f"1 RK4 step (forward + adjoint) of the {w.name} workload, {t1:.2f} s, "
-                      f"scaled x{w.steps} steps"}
+                      f"scaled x{w.steps} steps",
+            "extrapolated": True, "measured_rk4_steps": 1, "full_rk4_steps": w.steps}
 
 
 def cpu_baseline(w, c, target_s=20.0):
@@ -490,7 +638,8 @@ def cpu_baseline(w, c, target_s=20.0):
     per_jac = t1 * w.steps
     return {"value": (w.n + 1) / per_jac, "unit": "Jacobian columns/s", "cores": threads, "kind": "oracle",
             "sample": f"{k} RK4 step(s) of the {w.name} workload (all {w.n + 1} columns), "
-                      f"{t1:.2f} s per step, scaled x{w.steps} steps"}
+                      f"{t1:.2f} s per step, scaled x{w.steps} steps",
+            "extrapolated": True, "measured_rk4_steps": k, "full_rk4_steps": w.steps}
 
 
 def run_reference(args):
@@ -513,11 +662,17 @@ def run_reference(args):
     per_jac = statistics.mean(times) * w.steps
     value = (w.n + 1) / per_jac
     cpu = {"value": value, "unit": "Jacobian columns/s", "cores": O.threads(), "kind": "oracle",
-           "sample": f"1 RK4 step of {w.name} per timed step (all {w.n + 1} columns), scaled x{w.steps}"}
+           "sample": f"1 RK4 step of {w.name} per timed step (all {w.n + 1} columns), scaled x{w.steps}",
+           "extrapolated": True, "measured_rk4_steps": 1, "full_rk4_steps": w.steps}
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "Jacobian columns/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_jac * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "N": w.N, "n": w.n, "form": "cpu-oracle"},
+            "extrapolated": True,
+            "timing": f"each timed step runs 1 of the {w.steps} RK4 steps (all {w.n + 1} columns); "
+                      f"ms_per_step and value are scaled to the full {w.steps}-step Jacobian",
+            "config": {"workload": w.name, "N": w.N, "n": w.n, "columns": w.n + 1, "rk4_steps": w.steps,
+                       "h": w.h, "g": w.g, "tau": w.tau, "form": "cpu-oracle", "seed": 0,
+                       "parallelism": "host cores (OpenMP)"},
             "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": "Jacobian columns/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -533,6 +688,8 @@ def main():
     ap.add_argument("--workload", default=None, choices=sorted(W.ALL),
                     help=f"default {W.LARGE.name} (jacobian mode), {W.SHALLOW.name} (gradient mode)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true",
+                    help="jacobian mode, mixed form: leave out the timed plain-FP64 Jacobian of the comparison")
     ap.add_argument("--batch-step-cap", type=int, default=64,
                     help="batch mode: RK4 steps per shot at most (T scaled, each shot's dt kept)")
     ap.add_argument("--mode", default="jacobian", choices=["jacobian", "gradient", "batch"],

@@ -75,6 +75,15 @@ typedef struct {
                                   (graph kernel nodes x replays + outputs; -1 when
                                   the legacy stream forced direct launches)        */
     double refine_iters_mean;  /* WW_MIXED: mean refinement corrections per solve   */
+    double refine_resid_measured;  /* WW_MIXED with ww_set_verify: largest MEASURED
+                                  relative residual max_j max_i |R_ij| / (max|Psi_j| +
+                                  max|M_j|) of the sampled solves, R = Psi - A M
+                                  recomputed (7-digit FP64-accurate product) after
+                                  the last correction; -1 when nothing was sampled */
+    int verified_solves;       /* multi-column solves measured by the last call     */
+    long long device_bytes;    /* device memory held by the context (all workspace)  */
+    long long adjoint_bytes;   /* of which the objective_and_grad workspace (trajectory
+                                  records, checkpoints, second operand copies)      */
 } ww_stats;
 
 typedef struct ww_ctx ww_ctx;
@@ -94,6 +103,19 @@ int ww_set_stream(ww_ctx *ctx, void *stream);
 /* Statistics of the last shoot / shoot_jacobian / dtn_apply call. */
 int ww_get_stats(const ww_ctx *ctx, ww_stats *out);
 
+/* Measured refinement residual (WW_MIXED; a diagnostic of the Sec. 3.3
+ * refinement, which the paper runs with quad-precision residuals).  The
+ * refinement stops when the residual left after its last correction,
+ * extrapolated from the observed contraction, is below refine_tol.  With
+ * every > 0 the library also MEASURES it on a sample: after the last
+ * correction of every every-th multi-column solve of a call (stage 0,
+ * every, 2 every, ... of a shoot_jacobian; dtn_apply solves count too) it
+ * recomputes R = Psi - (1/2 I + K) M with the 7-digit product and records
+ * the worst relative residual in ww_stats.refine_resid_measured.  0 (the
+ * default) turns it off.  A change takes effect at the next call, whose
+ * step program is captured again.  WW_ERR_ARG in WW_FP64 (no refinement). */
+int ww_set_verify(ww_ctx *ctx, int every);
+
 /* Thread-local description of the last error (empty string if none). */
 const char *ww_last_error(void);
 
@@ -112,7 +134,9 @@ const char *ww_last_error(void);
 #define WW_PHASE_GKERNEL    7  /* the single product kernel inside GAPPLY (the
                                   FP64 GEMM, or the MIXED Ozaki tensor-core GEMM
                                   without its operand split)                    */
-#define WW_NPHASE           8
+#define WW_PHASE_INVERSE    8  /* MIXED: the two tensor-core products of the
+                                  inverse update inside FACTOR (none in FP64)   */
+#define WW_NPHASE           9
 int ww_set_timing(ww_ctx *ctx, int enable);
 int ww_get_timing(const ww_ctx *ctx, double *ms /* WW_NPHASE */, int *launches /* WW_NPHASE */);
 
@@ -170,39 +194,64 @@ int shoot_jacobian_batch(ww_ctx *const *ctx, int nshots, const double *const *cv
  * steps backward, each stage with its DtN assembled transposed (A^T, G^T) and
  * factored as in the forward form.  grad equals J^T r of shoot_jacobian up to
  * roundoff, at the cost of about two shots instead of n + 1 columns.
- * Errors as shoot; WW_ERR_ALLOC if the trajectory record does not fit. */
+ * Errors as shoot; WW_ERR_ALLOC if the trajectory record does not fit (see
+ * ww_set_checkpoint for the bounded-memory form). */
 int objective_and_grad(ww_ctx *ctx, const double *c, double *f, double *grad);
 
+/* ww_set_checkpoint -- memory of objective_and_grad (Sec. 3.2: the forward
+ * solution is stored at mile-markers and recomputed between them when memory
+ * is short).  every = 0 (the default) keeps the record of every RK stage of
+ * the forward pass resident (6N doubles a stage).  every = K > 0 keeps the
+ * base state (2N doubles) every K steps and the records of only K steps: the
+ * backward sweep goes segment by segment from the last, and before each
+ * segment (except the last) recomputes that segment's records forward from
+ * its checkpoint: 24 N K + 2 N steps/K doubles instead of 24 N steps, so
+ * K = sqrt(steps) makes the memory grow like sqrt(steps), for one more
+ * forward pass of the base state (all segments but the last).  In
+ * WW_FP64 the gradient is bitwise that of every = 0; in WW_MIXED each
+ * recomputed segment restarts its approximate inverse, so the refined solves
+ * round differently (agreement to ~1e-12 relative).  Takes effect at the next
+ * objective_and_grad, which reallocates the workspace. */
+int ww_set_checkpoint(ww_ctx *ctx, int every);
+
 /* dtn_apply_static -- the same operator as dtn_setup followed by dtn_apply,
- * for callers that cannot allocate device memory: code that runs while a
- * stream is being captured or under an allocator that forbids cudaMalloc,
- * and host applications that own every allocation themselves.  (The paper
- * has no counterpart; it is an interface convenience.)  The caller passes
+ * for callers that cannot allocate device memory when they need it: code
+ * under a memory-pool or allocator policy that forbids cudaMalloc, plug-ins
+ * of a host application that owns every allocation itself, and loops that
+ * must not touch the allocator.  (The paper has no counterpart; it is an
+ * interface convenience.)  The caller passes
  * only inputs and outputs -- eta (device, N), phi (device, N x nrhs,
  * column-major), Gphi (device, N x nrhs, must not alias phi), h (mean depth
  * or INFINITY) and a cudaStream_t (NULL = legacy default stream) -- and the
  * call allocates nothing: its workspace is one fixed array inside the
  * library, sized for N <= WW_STATIC_MAX_N and nrhs <= WW_STATIC_MAX_RHS
  * (1.7 MB, held by every GPU that loads the library until the process
- * exits).  Larger sizes return WW_ERR_ARG.  The first call on a device looks
- * up the array's device address, so make that first call before any stream
- * capture.  All calls share the array and the call synchronises its stream
- * before returning; calls that overlap on the GPU (other threads, other
- * streams) race on the array and must be serialised by the caller. */
+ * exits).  Larger sizes return WW_ERR_ARG.  The first call on a device does
+ * a one-time set-up there (it looks up the array's device address and sets a
+ * kernel attribute), so make that first call before any stream capture.  The
+ * call uploads small tables from host memory, then reads the status word
+ * back and synchronises its stream before returning.  All calls share the
+ * array, which keeps the last call's contents; calls that overlap on the GPU
+ * (other threads, other streams) race on it and must be serialised by the
+ * caller. */
 #define WW_STATIC_MAX_N   256
 #define WW_STATIC_MAX_RHS 64
 int dtn_apply_static(const double *eta, const double *phi, int N, int nrhs, double h, double *Gphi, void *stream);
 
-/* Self-tests of the tensor-core products of WW_MIXED (diagnostics; no
- * counterpart in the paper).  C = A B for column-major FP64 device arrays A
- * (M x K, ld M) and B (K x Nn, ld K), K a multiple of 64, through
- *   ww_selftest_f32gemm: the FP32-accurate product of 3 + 3 bf16 slices,
- *   ww_selftest_ozaki:   the FP64-accurate product of 7 + 7 exact bf16 digits;
- * *max_rel = max|C - C_ref| / max|C_ref| with C_ref the library's FP64 DGEMM.
- * They allocate their own scratch, use the legacy default stream and
- * synchronise the device; WW_ERR_TIMEOUT if a bounded device wait expired. */
-int ww_selftest_f32gemm(const double *A, const double *B, int M, int Nn, int K, double *max_rel);
-int ww_selftest_ozaki(const double *A, const double *B, int M, int Nn, int K, double *max_rel);
+/* Self-tests of the dense products (diagnostics; no counterpart in the
+ * paper).  C = A B for column-major FP64 device arrays A (M x K, ld M),
+ * B (K x Nn, ld K) and the output C (M x Nn, ld M, overwritten), through
+ *   ww_selftest_f32gemm: the FP32-accurate product of 3 + 3 bf16 slices
+ *                        (tensor cores; K a multiple of 64),
+ *   ww_selftest_ozaki:   the FP64-accurate product of 7 + 7 exact bf16 digits
+ *                        (tensor cores; K a multiple of 64),
+ *   ww_selftest_dgemm:   the FP64 DGEMM of the plain form (CUDA cores).
+ * The caller compares C with a product of its own.  They allocate their own
+ * scratch, use the legacy default stream and synchronise the device;
+ * WW_ERR_TIMEOUT if a bounded device wait expired. */
+int ww_selftest_f32gemm(const double *A, const double *B, int M, int Nn, int K, double *C);
+int ww_selftest_ozaki(const double *A, const double *B, int M, int Nn, int K, double *C);
+int ww_selftest_dgemm(const double *A, const double *B, int M, int Nn, int K, double *C);
 
 /* Self-test of the assembly's reciprocal (Newton-Raphson from the FP32
  * hardware reciprocal, two steps): *max_rel = max |r(d_i) - 1/d_i| / (1/d_i)

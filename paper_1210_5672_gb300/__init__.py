@@ -36,10 +36,10 @@ ERRORS = {
 WW_FP64, WW_MIXED = 0, 1
 EXPORTS = ("ww_create", "ww_destroy", "ww_set_stream", "ww_get_stats", "ww_last_error", "ww_set_timing",
            "ww_get_timing", "dtn_setup", "dtn_apply", "shoot", "shoot_jacobian", "shoot_jacobian_host",
-           "shoot_jacobian_batch", "objective_and_grad", "dtn_apply_static", "ww_selftest_f32gemm", "ww_selftest_ozaki",
-           "ww_selftest_recip")
+           "shoot_jacobian_batch", "objective_and_grad", "dtn_apply_static", "ww_set_verify", "ww_set_checkpoint", "ww_selftest_f32gemm",
+           "ww_selftest_ozaki", "ww_selftest_dgemm", "ww_selftest_recip")
 STATIC_MAX_N, STATIC_MAX_RHS = 256, 64
-PHASES = ("assembly", "factor", "solve", "gapply", "colrhs", "gamma", "base", "gkernel")
+PHASES = ("assembly", "factor", "solve", "gapply", "colrhs", "gamma", "base", "gkernel", "inverse")
 
 
 class WWError(RuntimeError):
@@ -60,6 +60,8 @@ class Stats(C.Structure):
     _fields_ = [
         ("refine_iters_max", C.c_int), ("refine_resid_max", C.c_double), ("ns_resid_max", C.c_double),
         ("stages", C.c_int), ("launches", C.c_longlong), ("refine_iters_mean", C.c_double),
+        ("refine_resid_measured", C.c_double), ("verified_solves", C.c_int),
+        ("device_bytes", C.c_longlong), ("adjoint_bytes", C.c_longlong),
     ]
 
     def as_dict(self):
@@ -95,8 +97,11 @@ def lib():
                                          C.POINTER(V)]),
             "objective_and_grad": (I, [V, V, V, V]),
             "dtn_apply_static": (I, [V, V, I, I, D, V, V]),
-            "ww_selftest_f32gemm": (I, [V, V, I, I, I, C.POINTER(D)]),
-            "ww_selftest_ozaki": (I, [V, V, I, I, I, C.POINTER(D)]),
+            "ww_set_verify": (I, [V, I]),
+            "ww_set_checkpoint": (I, [V, I]),
+            "ww_selftest_f32gemm": (I, [V, V, I, I, I, V]),
+            "ww_selftest_ozaki": (I, [V, V, I, I, I, V]),
+            "ww_selftest_dgemm": (I, [V, V, I, I, I, V]),
             "ww_selftest_recip": (I, [V, I, C.POINTER(D)]),
         }
         for name, (res, args) in sig.items():
@@ -181,6 +186,17 @@ class Context:
 
     def set_timing(self, enable: bool):
         _check(lib().ww_set_timing(self.handle, 1 if enable else 0))
+
+    def set_checkpoint(self, every: int):
+        """objective_and_grad memory: 0 keeps every stage's record; K > 0 keeps
+        the base state every K steps and recomputes each segment's records
+        (K = round(sqrt(steps)) bounds the memory by ~sqrt(steps))."""
+        _check(lib().ww_set_checkpoint(self.handle, int(every)))
+
+    def set_verify(self, every: int):
+        """WW_MIXED: measure the true refinement residual of every `every`-th
+        multi-column solve (stats()['refine_resid_measured']); 0 turns it off."""
+        _check(lib().ww_set_verify(self.handle, int(every)))
 
     def timing(self) -> dict:
         """{phase: (total_ms, launches)} of the last shoot / shoot_jacobian."""
@@ -269,18 +285,21 @@ def dtn_apply_static(eta, phi, h, Gphi, stream=None):
     return Gphi
 
 
-def selftest(kind: str, A, B) -> float:
-    """max relative error of the tensor-core product A @ B (A: M x K, B: K x Nn CUDA
-    float64 tensors) against the library's FP64 DGEMM; kind 'f32gemm' or 'ozaki'."""
+def selftest(kind: str, A, B):
+    """The library's product A @ B (A: M x K, B: K x Nn CUDA float64 tensors) as
+    an (M, Nn) CUDA tensor; kind 'f32gemm' (3 + 3 bf16 slices, tensor cores),
+    'ozaki' (7 + 7 exact bf16 digits, tensor cores) or 'dgemm' (FP64 DGEMM)."""
+    import torch
     M, K = A.shape
     K2, Nn = B.shape
     assert K == K2
     At = A.t().contiguous()   # column-major storage
     Bt = B.t().contiguous()
-    out = C.c_double(-1.0)
-    fn = lib().ww_selftest_f32gemm if kind == "f32gemm" else lib().ww_selftest_ozaki
-    _check(fn(_dptr(At, M * K, "A"), _dptr(Bt, K * Nn, "B"), M, Nn, K, C.byref(out)))
-    return out.value
+    Ct = torch.empty(Nn, M, dtype=torch.float64, device=A.device)
+    fn = {"f32gemm": lib().ww_selftest_f32gemm, "ozaki": lib().ww_selftest_ozaki,
+          "dgemm": lib().ww_selftest_dgemm}[kind]
+    _check(fn(_dptr(At, M * K, "A"), _dptr(Bt, K * Nn, "B"), M, Nn, K, _dptr(Ct, M * Nn, "C")))
+    return Ct.t()
 
 
 def selftest_recip(d) -> float:

@@ -5,9 +5,12 @@
 //
 // Forward, the base trajectory runs once and each RK stage leaves a record
 // [eta | phi_x | phi_y | w3 = (1+eta'^2)^{-3/2} | F] (F the filtered base
-// right-hand side): 6N doubles a stage, 0.4 GB for 2048 steps at N = 1024, so
-// HBM holds the whole trajectory and nothing is recomputed between
-// checkpoints (the paper's mile-markers exist for smaller memories).
+// right-hand side): 6N doubles a stage.  Either every stage's record stays
+// resident (0.4 GB for 2048 steps at N = 1024), or, as the paper's
+// mile-markers do (Sec. 3.2), the base state is checkpointed every K steps
+// and each segment's records are recomputed from its checkpoint just before
+// its backward sweep, so the records of only K steps are held at a time
+// (K = sqrt(steps) gives memory ~ sqrt(steps) for one extra forward pass).
 //
 // Backward, step by step from lambda = (0, phi(T/4)/N) (the gradient of
 // f = r.r/2, r = phi/sqrt(N), with respect to the final state): the
@@ -96,16 +99,17 @@ __global__ void k_rec_fields(const double *__restrict__ ux, const double *__rest
     if (st == 3 && threadIdx.x == 0) *step = s + 1;
 }
 
-__global__ void k_adj_init(const double *__restrict__ Y, int N, int steps, double *lam, double *gT, int *step) {
+// lambda = (0, phi(T/4)/N), dT = 0.  The record counter is left as the forward
+// pass left it: the number of steps whose records are held.
+__global__ void k_adj_init(const double *__restrict__ Y, int N, double *lam, double *gT) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
         lam[j] = 0.0;
         lam[N + j] = Y[N + j] / N;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *gT = 0.0;
-        *step = steps;
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *gT = 0.0;
 }
+
+__global__ void k_set_int(int *p, int v) { *p = v; }
 
 // start of a backward step: step -= 1; lambda <- Filt lambda; kb_st = b_st dt/6 lambda
 __global__ void __launch_bounds__(AJ_THREADS) k_adj_begin_step(double *lam, double *kb, int N, int logN,
@@ -393,7 +397,13 @@ int launch_adj_record_fields(Ctx *c, AdjWs *a, int st) {
 }
 
 int launch_adj_init(Ctx *c, AdjWs *a) {
-    k_adj_init<<<grid_for(c->N), 256, 0, c->stream>>>(c->Y, c->N, c->steps, a->lam, a->gT, a->step);
+    k_adj_init<<<grid_for(c->N), 256, 0, c->stream>>>(c->Y, c->N, a->lam, a->gT);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+int launch_adj_set_step(Ctx *c, AdjWs *a, int v) {
+    k_set_int<<<1, 1, 0, c->stream>>>(a->step, v);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }

@@ -60,6 +60,7 @@ struct StepGraph {
     cudaGraphExec_t exec = nullptr;
     std::vector<std::pair<cudaGraphNode_t, int>> ev_nodes;   // node -> flat event slot
     int nkern = 0;                            // kernel nodes (launches per replay)
+    unsigned marked = 0;                      // phases with event nodes in this program
 };
 
 int count_kernel_nodes(cudaGraph_t g, int *out) {
@@ -89,6 +90,7 @@ struct Owned {
     // phase timing
     bool timing = false;
     bool capturing = false;
+    bool in_shot = false;                     // the stages of a shot are being issued (marks allowed)
     int replay = 0;                           // RK step being launched
     unsigned marked = 0;                      // phases recorded by the current step program
     cudaEvent_t placeholder[EV_PER_STEP] = {};
@@ -99,12 +101,13 @@ struct Owned {
     // the forward step, the turn-around and the backward step as graphs
     AdjWs adj = {};
     StepGraph adj_fwd, adj_mid, adj_bwd;
+    StepGraph adj_restart, adj_reentry;       // checkpointed sweep: segment restart (forward) and re-entry (backward)
 };
 
 // record the begin (b = 0) or end (b = 1) event of a phase of stage st
 int mark(Ctx *c, int st, int phase, int b) {
     Owned *o = reinterpret_cast<Owned *>(c->owner);
-    if (!o || !o->timing) return WW_OK;
+    if (!o || !o->timing || !o->in_shot) return WW_OK;
     o->marked |= 1u << phase;
     const int slot = (st * NPH + phase) * 2 + b;
     if (o->capturing) {
@@ -120,7 +123,18 @@ int dalloc(Owned *o, void **p, size_t bytes) {
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) return fail(WW_ERR_ALLOC, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
     o->allocs.push_back(*p);
+    o->c.dev_bytes += bytes;
     return WW_OK;
+}
+
+void dfree(Owned *o, void *p) {
+    if (!p) return;
+    for (size_t i = 0; i < o->allocs.size(); ++i)
+        if (o->allocs[i] == p) {
+            o->allocs.erase(o->allocs.begin() + (long)i);
+            break;
+        }
+    cudaFree(p);
 }
 
 template <typename T>
@@ -165,6 +179,7 @@ int apply_G(Ctx *c, int col0, int ncols, int st = -1) {
 // hidden behind the columns: a fresher inverse saves column refinement
 // iterations), else on even stages and on odd ones only when it drifted.
 int run_base(Ctx *c, int st, const double *cvec, bool ns_every = false) {
+    c->cur_stage = st;
     WW_TRY(launch_base_geometry(c, c->Ys, c->Ys + c->N, 1));
     WW_TRY(mark(c, st, WW_PHASE_ASSEMBLY, 0));
     WW_TRY(launch_assemble(c));
@@ -186,6 +201,7 @@ int run_base(Ctx *c, int st, const double *cvec, bool ns_every = false) {
 // of the same stage (its DtN operands, u, v, w3 and F).
 int run_cols(Ctx *c, int st, const double *cvec) {
     if (c->nc <= 0) return WW_OK;
+    c->cur_stage = st;
     WW_TRY(launch_psi(c));
     WW_TRY(mark(c, st, WW_PHASE_SOLVE, 0));
     WW_TRY(solve(c, c->M + c->N, c->nc));
@@ -265,12 +281,14 @@ int build_step_graph(Owned *o, int with_cols) {
     cudaGraph_t g = nullptr;
     WW_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     o->capturing = true;
+    o->marked = 0;
     int st = WW_OK;
     if (overlapped(o, with_cols))
         st = capture_overlapped(o, o->cbuf);
     else
         for (int s = 0; s < 4 && st == WW_OK; ++s) st = run_stage(c, s, o->cbuf, with_cols);
     o->capturing = false;
+    sg.marked = o->marked;
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (st != WW_OK) {
         if (g) cudaGraphDestroy(g);
@@ -393,10 +411,12 @@ int check_status(Ctx *c) {
     WW_CUDA_TRY(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     WW_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (c->precision == WW_MIXED) {
-        double ratio = 0, nsres = 0;
-        int err = 0, iters[3] = {0, 0, 0};
-        WW_TRY(mixed_read_stats(c, &ratio, &nsres, iters, &err));
+        double ratio = 0, nsres = 0, vmax = 0;
+        int err = 0, iters[3] = {0, 0, 0}, vn = 0;
+        WW_TRY(mixed_read_stats(c, &ratio, &nsres, iters, &err, &vmax, &vn));
         c->stats.refine_resid_max = ratio;
+        c->stats.refine_resid_measured = vn > 0 ? vmax : -1.0;
+        c->stats.verified_solves = vn;
         c->stats.ns_resid_max = nsres;
         c->stats.refine_iters_max = iters[0];
         c->stats.refine_iters_mean = iters[2] > 0 ? (double)iters[1] / iters[2] : 0.0;
@@ -421,6 +441,11 @@ int run_shot(Owned *o, const double *cvec, bool c_on_host, double *r, double *J,
     WW_TRY(run_prologue(o, with_cols));
     if (o->timing) WW_TRY(ensure_timing_events(o));
     o->marked = 0;
+    struct InShot {
+        Owned *o;
+        InShot(Owned *o_) : o(o_) { o->in_shot = true; }
+        ~InShot() { o->in_shot = false; }
+    } in_shot(o);
     if (c->stream == nullptr) {
         // the legacy default stream cannot be captured: launch the stages directly
         for (int s = 0; s < c->steps; ++s) {
@@ -430,11 +455,7 @@ int run_shot(Owned *o, const double *cvec, bool c_on_host, double *r, double *J,
     } else {
         WW_TRY(build_step_graph(o, with_cols));
         StepGraph &sg = o->graphs[with_cols][o->timing ? 1 : 0];
-        if (o->timing)
-            for (int p = 0; p < NPH; ++p)
-                if (with_cols || (p != WW_PHASE_SOLVE && p != WW_PHASE_GAMMA && p != WW_PHASE_GAPPLY &&
-                                  p != WW_PHASE_COLRHS && p != WW_PHASE_GKERNEL))
-                    o->marked |= 1u << p;
+        o->marked = sg.marked;
         for (int s = 0; s < c->steps; ++s) {
             if (o->timing)
                 for (auto &ne : sg.ev_nodes)
@@ -445,6 +466,8 @@ int run_shot(Owned *o, const double *cvec, bool c_on_host, double *r, double *J,
     }
     WW_TRY(launch_outputs(c, r, J, f, with_cols));
     c->stats.stages = 4 * c->steps;
+    c->stats.device_bytes = (long long)c->dev_bytes;
+    c->stats.adjoint_bytes = (long long)o->adj.bytes;
     if (c->stream == nullptr)
         c->stats.launches = -1;   // direct launches are not counted
     else
@@ -457,12 +480,34 @@ int run_shot(Owned *o, const double *cvec, bool c_on_host, double *r, double *J,
 }
 
 // ---------------------------------------------------------------- discrete adjoint
+// steps of records held: all of them, or the checkpoint interval
+int held_steps(const Ctx *c) { return c->ckpt_every > 0 && c->ckpt_every < c->steps ? c->ckpt_every : c->steps; }
+
+void free_adjoint(Owned *o) {
+    AdjWs &a = o->adj;
+    for (void *p : {(void *)a.rec, (void *)a.lam, (void *)a.kb, (void *)a.eta, (void *)a.chi, (void *)a.y,
+                    (void *)a.etal, (void *)a.psil, (void *)a.gT, (void *)a.step, (void *)a.A2, (void *)a.G2,
+                    (void *)a.X2, (void *)a.ckpt})
+        dfree(o, p);
+    o->c.dev_bytes -= a.bytes;
+    a = AdjWs{};
+    for (StepGraph *sg : {&o->adj_fwd, &o->adj_mid, &o->adj_bwd, &o->adj_restart, &o->adj_reentry}) {
+        if (sg->exec) cudaGraphExecDestroy(sg->exec);
+        if (sg->graph) cudaGraphDestroy(sg->graph);
+        *sg = StepGraph();
+    }
+}
+
 int ensure_adjoint(Owned *o) {
     AdjWs &a = o->adj;
-    if (a.rec) return WW_OK;
     const Ctx *c = &o->c;
-    const size_t N = (size_t)c->N;
-    WW_TRY(dalloc_n(o, &a.rec, (size_t)4 * c->steps * ADJ_REC * N));
+    const int K = held_steps(c);
+    if (a.rec && a.kheld == K) return WW_OK;
+    if (a.rec) free_adjoint(o);   // the checkpoint interval changed: the record buffer's size with it
+    const size_t N = (size_t)c->N, before = o->c.dev_bytes;
+    WW_TRY(dalloc_n(o, &a.rec, (size_t)4 * K * ADJ_REC * N));
+    a.kheld = K;
+    if (K < c->steps) WW_TRY(dalloc_n(o, &a.ckpt, (size_t)((c->steps + K - 1) / K) * 2 * N));
     WW_TRY(dalloc_n(o, &a.lam, 2 * N));
     WW_TRY(dalloc_n(o, &a.kb, 8 * N));
     WW_TRY(dalloc_n(o, &a.eta, N));
@@ -477,6 +522,7 @@ int ensure_adjoint(Owned *o) {
         WW_TRY(dalloc_n(o, &a.G2, N * N));
         WW_TRY(dalloc_n(o, &a.X2, N * N));
     }
+    a.bytes = o->c.dev_bytes - before;
     return prepare_adjoint(c->N);
 }
 
@@ -639,52 +685,113 @@ int replay(Owned *o, StepGraph &sg, F body) {
     return WW_OK;
 }
 
+// Checkpointed sweep, restart of a segment from its checkpoint: the base state
+// is already in Y and Ys; the mixed form builds a fresh approximate inverse of
+// the (forward) operator at that surface, as the prologue does at t = 0.
+int adj_restart(Owned *o) {
+    Ctx *c = &o->c;
+    select_parity(c, 0);
+    if (c->precision != WW_MIXED) return WW_OK;
+    WW_TRY(launch_base_geometry(c, c->Ys, c->Ys + c->N, 1));
+    WW_TRY(launch_assemble(c));
+    return factor(c, 1);
+}
+
+// Checkpointed sweep, re-entry into the backward steps after a segment was
+// recomputed: the mixed form's fresh inverse of the transposed operator at the
+// segment's end (the turnaround without lambda), into operand copy 1 in the
+// overlapped sweep (where the setup of the segment's last stage goes).
+int adj_reentry(Owned *o, const AdjOperands *ops) {
+    Ctx *c = &o->c;
+    select_parity(c, 0);
+    if (ops) return adj_setup(o, *ops, -1, 1, true);
+    if (c->precision != WW_MIXED) return WW_OK;
+    WW_TRY(launch_base_geometry(c, c->Ys, c->Ys, 0));
+    WW_TRY(launch_assemble(c));
+    return factor(c, 1);
+}
+
 int run_adjoint(Owned *o, const double *cvec, bool c_on_host, double *f, double *grad) {
     Ctx *c = &o->c;
     WW_TRY(ensure_adjoint(o));
     const bool timing = o->timing;
     o->timing = false;   // the phase timers cover the forward Jacobian only
+    const bool ovl = adj_overlapped(o);
+    // operand copy 0 is the context's own A, G, X; copy 1 the sweep's second set
+    const AdjOperands ops{{c->A, o->adj.A2}, {c->G, o->adj.G2}, {c->mx ? mixed_set_inverse(c, nullptr) : nullptr,
+                                                                 o->adj.X2}};
     struct Restore {
         Owned *o;
         bool t;
+        const AdjOperands *ops;
         ~Restore() {
             o->timing = t;
             o->c.trans = 0;
+            if (ops) adj_select(o, *ops, 0);
         }
-    } restore{o, timing};
+    } restore{o, timing, ovl ? &ops : nullptr};
     c->one_col = true;
+    const size_t N = (size_t)c->N;
+    const int K = held_steps(c);                       // steps per segment
+    const int nseg = (c->steps + K - 1) / K;
     WW_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     WW_CUDA_TRY(cudaMemsetAsync(o->adj.step, 0, sizeof(int), c->stream));
     WW_CUDA_TRY(cudaMemcpyAsync(o->cbuf, cvec, sizeof(double) * (c->n + 1),
                                 c_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
     c->trans = 0;
     WW_TRY(run_prologue(o, 0));
-    for (int s = 0; s < c->steps; ++s) WW_TRY(replay(o, o->adj_fwd, [&] { return adj_forward_step(o); }));
+    // forward: the base trajectory, each stage recorded into the segment's
+    // slots; in checkpointed mode the state at each segment start is kept and
+    // the record counter restarts there
+    for (int s = 0; s < c->steps; ++s) {
+        if (K < c->steps && s % K == 0) {
+            WW_CUDA_TRY(cudaMemcpyAsync(o->adj.ckpt + (size_t)(s / K) * 2 * N, c->Y, sizeof(double) * 2 * N,
+                                        cudaMemcpyDeviceToDevice, c->stream));
+            WW_TRY(launch_adj_set_step(c, &o->adj, 0));
+        }
+        WW_TRY(replay(o, o->adj_fwd, [&] { return adj_forward_step(o); }));
+    }
     WW_TRY(launch_outputs(c, o->rbuf, nullptr, f, 0));
+    long long launches = (long long)o->prologue[0].nkern + (long long)c->steps * o->adj_fwd.nkern + 1 +
+                         (K < c->steps ? nseg : 0);
+    // backward, segment by segment from the last; the last segment's records
+    // are those of the forward pass
     c->trans = 1;
-    if (adj_overlapped(o)) {
-        // operand copy 0 is the context's own A, G, X; copy 1 the sweep's second set
-        const AdjOperands ops{{c->A, o->adj.A2}, {c->G, o->adj.G2}, {mixed_set_inverse(c, nullptr), o->adj.X2}};
-        struct Back {
-            Owned *o;
-            AdjOperands ops;
-            ~Back() { adj_select(o, ops, 0); }
-        } back{o, ops};
+    if (ovl)
         WW_TRY(replay(o, o->adj_mid, [&] { return adj_turnaround_overlapped(o, ops); }));
-        for (int s = 0; s < c->steps; ++s)
-            WW_TRY(replay(o, o->adj_bwd, [&] { return adj_backward_step_overlapped(o, ops); }));
-    } else {
+    else
         WW_TRY(replay(o, o->adj_mid, [&] { return adj_turnaround(o); }));
-        for (int s = 0; s < c->steps; ++s) WW_TRY(replay(o, o->adj_bwd, [&] { return adj_backward_step(o); }));
+    launches += o->adj_mid.nkern;
+    for (int j = nseg - 1; j >= 0; --j) {
+        const int L = j == nseg - 1 ? c->steps - j * K : K;
+        if (j < nseg - 1) {
+            // recompute the segment's records from its checkpoint
+            if (ovl) adj_select(o, ops, 0);
+            c->trans = 0;
+            const double *ck = o->adj.ckpt + (size_t)j * 2 * N;
+            WW_CUDA_TRY(cudaMemcpyAsync(c->Y, ck, sizeof(double) * 2 * N, cudaMemcpyDeviceToDevice, c->stream));
+            WW_CUDA_TRY(cudaMemcpyAsync(c->Ys, ck, sizeof(double) * 2 * N, cudaMemcpyDeviceToDevice, c->stream));
+            WW_TRY(launch_adj_set_step(c, &o->adj, 0));
+            WW_TRY(replay(o, o->adj_restart, [&] { return adj_restart(o); }));
+            for (int s = 0; s < L; ++s) WW_TRY(replay(o, o->adj_fwd, [&] { return adj_forward_step(o); }));
+            c->trans = 1;
+            WW_TRY(replay(o, o->adj_reentry, [&] { return adj_reentry(o, ovl ? &ops : nullptr); }));
+            launches += 1 + o->adj_restart.nkern + (long long)L * o->adj_fwd.nkern + o->adj_reentry.nkern;
+        }
+        for (int s = 0; s < L; ++s) {
+            if (ovl)
+                WW_TRY(replay(o, o->adj_bwd, [&] { return adj_backward_step_overlapped(o, ops); }));
+            else
+                WW_TRY(replay(o, o->adj_bwd, [&] { return adj_backward_step(o); }));
+        }
+        launches += (long long)L * o->adj_bwd.nkern;
     }
     c->trans = 0;
     WW_TRY(launch_adj_grad(c, &o->adj, grad));
     c->stats.stages = 8 * c->steps;
-    if (c->stream == nullptr)
-        c->stats.launches = -1;
-    else
-        c->stats.launches = (long long)o->prologue[0].nkern + (long long)c->steps * o->adj_fwd.nkern + 1 +
-                            o->adj_mid.nkern + (long long)c->steps * o->adj_bwd.nkern + 1;
+    c->stats.launches = c->stream == nullptr ? -1 : launches + 1;
+    c->stats.adjoint_bytes = (long long)o->adj.bytes;
+    c->stats.device_bytes = (long long)c->dev_bytes;
     c->dtn_ready = false;
     return check_status(c);
 }
@@ -692,6 +799,9 @@ int run_adjoint(Owned *o, const double *cvec, bool c_on_host, double *f, double 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 }  // namespace
+
+int phase_mark(Ctx *c, int phase, int b) { return mark(c, c->cur_stage, phase, b); }
+
 }  // namespace ww
 
 using namespace ww;
@@ -868,7 +978,7 @@ void ww_destroy(ww_ctx *ctx) {
         if (o->prologue[w].exec) cudaGraphExecDestroy(o->prologue[w].exec);
         if (o->prologue[w].graph) cudaGraphDestroy(o->prologue[w].graph);
     }
-    for (StepGraph *sg : {&o->adj_fwd, &o->adj_mid, &o->adj_bwd}) {
+    for (StepGraph *sg : {&o->adj_fwd, &o->adj_mid, &o->adj_bwd, &o->adj_restart, &o->adj_reentry}) {
         if (sg->exec) cudaGraphExecDestroy(sg->exec);
         if (sg->graph) cudaGraphDestroy(sg->graph);
     }
@@ -910,6 +1020,36 @@ int ww_get_timing(const ww_ctx *ctx, double *ms, int *launches) {
         ms[p] = o->ph_ms[p];
         launches[p] = o->ph_count[p];
     }
+    return WW_OK;
+}
+
+int ww_set_verify(ww_ctx *ctx, int every) {
+    if (!ctx) return fail(WW_ERR_ARG, "ww_set_verify: NULL context");
+    if (every < 0) return fail(WW_ERR_ARG, "ww_set_verify: every must be >= 0");
+    Owned *o = owner(ctx);
+    if (o->c.precision != WW_MIXED && every > 0)
+        return fail(WW_ERR_ARG, "ww_set_verify: only WW_MIXED has a refinement residual to measure");
+    if (o->c.verify_every == every) return WW_OK;
+    WW_CUDA_TRY(cudaStreamSynchronize(o->c.stream));
+    // the step programs captured so far were built without (or with) the measurement
+    for (int w = 0; w < 2; ++w)
+        for (int t = 0; t < 2; ++t) {
+            StepGraph &sg = o->graphs[w][t];
+            if (sg.exec) cudaGraphExecDestroy(sg.exec);
+            if (sg.graph) cudaGraphDestroy(sg.graph);
+            sg = StepGraph();
+        }
+    o->c.verify_every = every;
+    return WW_OK;
+}
+
+int ww_set_checkpoint(ww_ctx *ctx, int every) {
+    if (!ctx) return fail(WW_ERR_ARG, "ww_set_checkpoint: NULL context");
+    if (every < 0) return fail(WW_ERR_ARG, "ww_set_checkpoint: every must be >= 0");
+    Owned *o = owner(ctx);
+    WW_CUDA_TRY(cudaStreamSynchronize(o->c.stream));
+    if (o->side_stream) WW_CUDA_TRY(cudaStreamSynchronize(o->side_stream));
+    o->c.ckpt_every = every;   // the adjoint workspace is resized by the next objective_and_grad
     return WW_OK;
 }
 

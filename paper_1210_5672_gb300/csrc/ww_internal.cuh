@@ -104,6 +104,10 @@ struct Ctx {
     int trans;                // 1 while the adjoint sweep assembles A^T and G^T in place of A and G
     bool one_col;             // only one-column solves and products follow (base-only shots, the adjoint):
                               // the mixed form skips the digit splits of K and G that wide products read
+    int verify_every;         // WW_MIXED: measure the true residual of every verify_every-th wide solve (0: off)
+    int cur_stage;            // RK stage (0..3) whose work is being issued (phase timing)
+    int ckpt_every;           // adjoint: checkpoint the base state every ckpt_every steps (0: keep every record)
+    size_t dev_bytes;         // device memory this context allocated
     ww_stats stats;
     Mixed *mx;
     void *owner;              // the API-side object holding this context (phase timing)
@@ -208,6 +212,10 @@ int launch_cbase_rhs(Ctx *c, int stage, const double *cvec);
 int launch_outputs(Ctx *c, double *r, double *J, double *f, int with_J);
 int launch_copy_cols(Ctx *c, const double *src, int ncols, double *dst);
 
+// phase timing (ww_api.cu): begin (b = 0) or end (b = 1) event of `phase` in
+// the current stage; a no-op unless a timed shot is being issued
+int phase_mark(Ctx *c, int phase, int b);
+
 // assembly (ww_assemble.cu); c->trans selects A^T, G^T
 int launch_assemble(Ctx *c);
 
@@ -215,7 +223,10 @@ int launch_assemble(Ctx *c);
 // [eta | phi_x | phi_y | (1+eta'^2)^{-3/2} | F (2N)], ADJ_REC doubles per point
 constexpr int ADJ_REC = 6;
 struct AdjWs {
-    double *rec;              // 4 steps records of ADJ_REC * N
+    double *rec;              // 4 K records of ADJ_REC * N (K = the steps of records held)
+    int kheld;                // K: steps whose records are held (all steps, or the checkpoint interval)
+    double *ckpt;             // checkpointed mode: the base state (2N) at steps 0, K, 2K, ...
+    size_t bytes;             // device bytes of this workspace
     double *lam;              // 2N: the adjoint state
     double *kb;               // 4 x 2N: adjoints of the stage right-hand sides
     double *eta;              // N: the stage surface fetched for its geometry
@@ -230,7 +241,8 @@ struct AdjWs {
 int prepare_adjoint(int Nmax);                            // shared-memory limits of the sweep's FFT kernels
 int launch_adj_record_eta(Ctx *c, AdjWs *a, int st);      // forward: the stage surface (before its RK update)
 int launch_adj_record_fields(Ctx *c, AdjWs *a, int st);   // forward: phi_x, phi_y, w3, F; st == 3 advances the step
-int launch_adj_init(Ctx *c, AdjWs *a);                    // lambda = (0, phi(T/4)/N), dT = 0, step = steps
+int launch_adj_init(Ctx *c, AdjWs *a);                    // lambda = (0, phi(T/4)/N), dT = 0
+int launch_adj_set_step(Ctx *c, AdjWs *a, int v);         // record counter = v
 int launch_adj_begin_step(Ctx *c, AdjWs *a, const double *cvec);   // step -= 1; filter lambda; kb = b dt/6 lambda
 int launch_adj_fetch(Ctx *c, AdjWs *a, int off);          // surface of record 4 step + off into a->eta (none if < 0)
 int launch_adj_local(Ctx *c, AdjWs *a, int st, const double *cvec);   // chi, local terms, dT += kb.F/T
@@ -259,7 +271,8 @@ int mixed_create(Ctx *c);
 int tc_init();   // resolves the tensor-map encoder (called before any capture)
 void mixed_destroy(Ctx *c);
 int mixed_setup(Ctx *c, int fresh, int update);      // after assembly: operands, inverse update
-int mixed_read_stats(Ctx *c, double *ratio, double *nsres, int *iters /* [3]: max, sum, solves */, int *err);
+int mixed_read_stats(Ctx *c, double *ratio, double *nsres, int *iters /* [3]: max, sum, solves */, int *err,
+                     double *vmax, int *vn);   // vmax, vn: measured residual of the sampled solves
 int mixed_solve(Ctx *c, double *B, int ncols);       // B <- A^{-1} B (refined)
 int mixed_apply_G(Ctx *c, int col0, int ncols, int part);   // Gout += G Gam (part 0 split, 1 product; FP64-accurate)
 float *mixed_set_inverse(Ctx *c, float *X);          // the FP32 inverse the updates write (NULL: query)

@@ -89,6 +89,11 @@ struct Mixed {
     int *ns_skip;                          // device decision: this stage reuses the previous X
     int *iters;                            // [0] most residuals any solve needed, [1] their sum, [2] solves
     int *err;
+    // measured residual of sampled wide solves (ww_set_verify)
+    unsigned long long *vcm;               // NC: max|R_j| of the verification product
+    int *vcount, *vskip;                   // wide solves seen this call; this one is not sampled
+    double *vmax;                          // worst measured relative residual (bits of a double)
+    int *vn;                               // sampled solves this call
 };
 
 namespace {
@@ -174,6 +179,36 @@ __global__ void k_converged(const unsigned long long *cm, const unsigned long lo
     }
 }
 
+// Sampling of the verified solves: solve number *count is measured when it is
+// a multiple of `every`.
+__global__ void k_verify_tick(int *count, int every, int *skip) {
+    *skip = (*count % every) != 0;
+    *count += 1;
+}
+
+// worst measured relative residual of one sampled solve:
+// max_j max|R_j| / (max|Psi_j| + max|M_j|), the normalisation of k_converged
+__global__ void k_verify_fold(const unsigned long long *cm, const double *psis, const double *ms, int ncols,
+                              const int *skip, unsigned long long *vmax, int *vn) {
+    if (*skip) return;
+    __shared__ double red[32];
+    double worst = 0.0;
+    for (int j = threadIdx.x; j < ncols; j += blockDim.x) {
+        const double r = __longlong_as_double((long long)cm[j]);
+        const double den = psis[j] + ms[j];
+        worst = fmax(worst, den > 0 ? r / den : (r > 0 ? INFINITY : 0.0));
+    }
+    for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = worst;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) worst = fmax(worst, red[w]);
+        worst = fmax(worst, red[0]);
+        atomicMax(vmax, (unsigned long long)__double_as_longlong(worst));
+        atomicAdd(vn, 1);
+    }
+}
+
 // Start of a wide solve, one block per column: Psi <- B, max|Psi_j| -> psis,
 // and the 2 bf16 slices of Psi as the right operand of X Psi.
 __global__ void k_prep_psi(const double *__restrict__ B, int N, int ncols, double *Psi, double *psis,
@@ -218,6 +253,7 @@ int ns_step(Ctx *c, bool record, const int *skip) {
     cudaStream_t s = c->stream;
     if (record) WW_CUDA_TRY(cudaMemsetAsync(m->nsres_last, 0, sizeof(unsigned), s));
     // W = 2I - A X, written straight as the slices of the next product's right operand
+    if (record) WW_TRY(phase_mark(c, WW_PHASE_INVERSE, 0));
     TcOut o3{};
     o3.mode = 3;
     o3.shift = 2.f;
@@ -233,6 +269,7 @@ int ns_step(Ctx *c, bool record, const int *skip) {
     o4.s_row = m->XnA;
     o4.s_row2 = m->Xrow[c->par];
     WW_TRY(tc_gemm_f32acc_sliced(s, m->XslcA, m->Wslc, N, N, N, o4, m->err, skip));
+    if (record) WW_TRY(phase_mark(c, WW_PHASE_INVERSE, 1));
     // the product above still reads XslcA while it writes: its slices land in XnA / XnB
     // and move over afterwards (after a skipped update both already hold the same data)
     const size_t bytes = sizeof(__nv_bfloat16) * 3 * (size_t)N * N;
@@ -254,8 +291,11 @@ int mixed_create(Ctx *c) {
     c->mx = m;
     const size_t N = c->N, NC = c->NC, NN = N * N;
     int st = WW_OK;
-#define MA(p, n) \
-    if (st == WW_OK) st = alloc(&(p), (n))
+#define MA(p, n)                                                \
+    if (st == WW_OK) {                                          \
+        st = alloc(&(p), (n));                                  \
+        c->dev_bytes += sizeof(*(p)) * (size_t)((n) ? (n) : 1); \
+    }
     MA(m->X, NN);
     MA(m->XnA, 3 * NN);
     MA(m->XnB, 3 * NN);
@@ -293,6 +333,11 @@ int mixed_create(Ctx *c) {
     MA(m->ns_skip, 1);
     MA(m->iters, 3);
     MA(m->err, 1);
+    MA(m->vcm, NC);
+    MA(m->vcount, 1);
+    MA(m->vskip, 1);
+    MA(m->vmax, 1);
+    MA(m->vn, 1);
 #undef MA
     if (st != WW_OK) return st;
     WW_CUDA_TRY(cudaMemset(m->err, 0, sizeof(int)));
@@ -301,6 +346,9 @@ int mixed_create(Ctx *c) {
     WW_CUDA_TRY(cudaMemset(m->nsres_last, 0xFF, sizeof(unsigned)));   // NaN bits: never skip before an update
     WW_CUDA_TRY(cudaMemset(m->ns_skip, 0, sizeof(int)));
     WW_CUDA_TRY(cudaMemset(m->iters, 0, 3 * sizeof(int)));
+    WW_CUDA_TRY(cudaMemset(m->vcount, 0, sizeof(int)));
+    WW_CUDA_TRY(cudaMemset(m->vmax, 0, sizeof(double)));
+    WW_CUDA_TRY(cudaMemset(m->vn, 0, sizeof(int)));
     return WW_OK;
 }
 
@@ -313,7 +361,8 @@ void mixed_destroy(Ctx *c) {
                     m->Rd,          m->Rs,          m->Re,         m->Bslc,         m->wide.R,      m->wide.Psi,
                     m->wide.psis,   m->wide.mscale, m->wide.colmax, m->wide.colmax0, m->wide.done,  m->nar.R,
                     m->nar.Psi,     m->nar.psis,    m->nar.mscale, m->nar.colmax,   m->nar.colmax0, m->nar.done,
-                    m->ratio,       m->nsres,       m->nsres_last, m->ns_skip,      m->iters,       m->err};
+                    m->ratio,       m->nsres,       m->nsres_last, m->ns_skip,      m->iters,       m->err,
+                    m->vcm,         m->vcount,      m->vskip,      m->vmax,         m->vn};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -409,6 +458,18 @@ int mixed_solve(Ctx *c, double *B, int ncols) {
         cm_prev = cm;
         cm = t;
     }
+    // measured residual of a sampled solve: R = Psi - 1/2 M - K M of the final M,
+    // 7 digits, after the last correction (the estimate above extrapolates it)
+    if (!narrow && c->verify_every > 0) {
+        k_verify_tick<<<1, 1, 0, s>>>(m->vcount, c->verify_every, m->vskip);
+        WW_CUDA_TRY(cudaGetLastError());
+        WW_TRY(ozaki_digits_cols(s, B, N, ncols, N, m->Rs, m->Rd, m->vcm, m->vskip));
+        WW_TRY(ozaki_gemm(s, m->Kd[q], m->Ks[q], m->Rd, m->Rs, N, ncols, N, 1, nullptr, N, w.Psi, N, B, N, m->vcm,
+                          m->err, m->vskip, nullptr, 7));
+        k_verify_fold<<<1, 512, 0, s>>>(m->vcm, w.psis, m->Rs, ncols, m->vskip,
+                                        reinterpret_cast<unsigned long long *>(m->vmax), m->vn);
+        WW_CUDA_TRY(cudaGetLastError());
+    }
     return WW_OK;
 }
 
@@ -434,9 +495,11 @@ float *mixed_set_inverse(Ctx *c, float *X) {
 }
 
 // device diagnostics of the mixed path, read (and reset) after a call
-int mixed_read_stats(Ctx *c, double *ratio, double *nsres, int *iters, int *err) {
+int mixed_read_stats(Ctx *c, double *ratio, double *nsres, int *iters, int *err, double *vmax, int *vn) {
     Mixed *m = c->mx;
     unsigned nb = 0;
+    WW_CUDA_TRY(cudaMemcpyAsync(vmax, m->vmax, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    WW_CUDA_TRY(cudaMemcpyAsync(vn, m->vn, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     WW_CUDA_TRY(cudaMemcpyAsync(ratio, m->ratio, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     WW_CUDA_TRY(cudaMemcpyAsync(&nb, m->nsres, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     WW_CUDA_TRY(cudaMemcpyAsync(iters, m->iters, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -449,6 +512,9 @@ int mixed_read_stats(Ctx *c, double *ratio, double *nsres, int *iters, int *err)
     WW_CUDA_TRY(cudaMemsetAsync(m->nsres, 0, sizeof(unsigned), c->stream));
     WW_CUDA_TRY(cudaMemsetAsync(m->iters, 0, 3 * sizeof(int), c->stream));
     WW_CUDA_TRY(cudaMemsetAsync(m->err, 0, sizeof(int), c->stream));
+    WW_CUDA_TRY(cudaMemsetAsync(m->vcount, 0, sizeof(int), c->stream));
+    WW_CUDA_TRY(cudaMemsetAsync(m->vmax, 0, sizeof(double), c->stream));
+    WW_CUDA_TRY(cudaMemsetAsync(m->vn, 0, sizeof(int), c->stream));
     return WW_OK;
 }
 

@@ -3,18 +3,24 @@
 // kernels as dtn_setup + dtn_apply) in a single call that allocates nothing.
 //
 // Some callers cannot allocate device memory at the time they need the
-// operator: code running inside a stream-capture region or a memory-pool
-// policy that forbids cudaMalloc, plug-ins of a host application that owns
-// every allocation, or real-time loops that must not touch the allocator.
-// They pass only their inputs and outputs; the workspace is the file-scope
-// device array below, sized for N <= WW_STATIC_MAX_N and
-// nrhs <= WW_STATIC_MAX_RHS (1.7 MB, held by every GPU that loads the library
-// until the process exits).
+// operator: code under a memory-pool or allocator policy that forbids
+// cudaMalloc, plug-ins of a host application that owns every allocation, or
+// real-time loops that must not touch the allocator.  They pass only their
+// inputs and outputs; the workspace is the file-scope device array below,
+// sized for N <= WW_STATIC_MAX_N and nrhs <= WW_STATIC_MAX_RHS (1.7 MB, held
+// by every GPU that loads the library until the process exits).
+//
+// Host code cannot use the array's name as a device address: the first call
+// on each device, with that device current, looks the address up with
+// cudaGetSymbolAddress (and raises the LU kernel's shared-memory limit there),
+// and every call passes that address to the kernels.
 //
 // The array is shared by every call on a device and keeps the last call's
 // contents; only the status word has to start at zero and is cleared here.
-// Calls whose work overlaps on the GPU (different streams, or different host
-// threads) race on the array: serialise them.
+// The call uploads its small tables from host memory, reads the status word
+// back and synchronises its stream before it returns.  Calls whose work
+// overlaps on the GPU (different streams, or different host threads) race on
+// the array: serialise them.
 #include <mutex>
 
 #include "ww_internal.cuh"
@@ -53,12 +59,14 @@ int workspace(double **out) {
     if (dev < 0 || dev >= MAX_DEVICES) return fail(WW_ERR_ARG, "dtn_apply_static: device index out of range");
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_ws_ptr[dev]) {
+        // publish the address only once the whole set-up has succeeded, so that a
+        // failed first call is repeated (with its own error) by the next one
+        WW_TRY(prepare_dense());   // shared-memory limit of the LU block kernel on this device
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_static_ws);
         if (e != cudaSuccess)
             return fail(WW_ERR_CUDA, std::string("dtn_apply_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         g_ws_ptr[dev] = static_cast<double *>(p);
-        WW_TRY(prepare_dense());   // shared-memory limit of the LU block kernel on this device
     }
     *out = g_ws_ptr[dev];
     return WW_OK;

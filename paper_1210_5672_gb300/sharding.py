@@ -16,15 +16,16 @@ column is computed on every rank (one column) and taken from rank 0.
 
 The per-rank engine is a callable engine(c_r, basis_r) -> (r, J_r, f) with J_r
 of shape N x (len(c_r)); `gpu_engine` builds it on the library's
-shoot_jacobian.  The gather uses torch.distributed (NCCL on GPUs, gloo in the
-CPU tests).
+shoot_jacobian.  The gather uses torch.distributed: on a NCCL group the
+gathered blocks travel as CUDA tensors of the current device, on a gloo group
+(the CPU tests) as CPU tensors.
 
-Failure detection is on the host.  Given the process group's key-value store,
-every rank reports its status ("ok", or its engine's error) before the
-collective and waits, for at most `timeout` seconds, for every other rank's
-report.  A rank that failed or never reported (it died or hangs) turns into a
-ShardFailure on every surviving rank, naming the ranks, and no rank enters a
-collective that could not complete.
+Failure detection is on the host.  Through a key-value store (by default the
+process group's own), every rank reports its status ("ok", or its engine's
+error) before the collective and waits, for at most `timeout` seconds, for
+every other rank's report.  A rank that failed or never reported (it died or
+hangs) turns into a ShardFailure on every surviving rank, naming the ranks,
+and no rank enters a collective that could not complete.
 """
 from __future__ import annotations
 
@@ -84,22 +85,25 @@ def sharded_jacobian(c, basis, engine, rank: int, world: int, group=None, store=
                      timeout: float = 60.0):
     """The full (r, J, f) of the problem (c, basis) on every rank, each rank
     computing its block of columns with engine(c_r, basis_r) and one all-gather.
-    With `store` (the process group's store; `tag` unique per call) the ranks
-    report to each other first and a failed or silent rank raises ShardFailure
-    on every surviving rank."""
+    With world > 1 the ranks first report to each other through `store` (the
+    default process group's store when None; `tag` unique per call), and a
+    failed or silent rank raises ShardFailure on every surviving rank."""
     import torch
     import torch.distributed as dist
 
+    if world > 1 and store is None:
+        from torch.distributed import distributed_c10d as c10d
+        store = c10d._get_default_store()
     n = np.asarray(basis).shape[1]
     c_r, basis_r, (s, e) = shard_problem(c, basis, rank, world)
     try:
         r, J_r, f = engine(c_r, basis_r)
         status = "ok"
     except Exception as exc:              # reported to the other ranks, then raised here
-        if store is None or world == 1:
+        if world == 1:
             raise
         status = f"engine failed: {type(exc).__name__}: {exc}"
-    if store is not None and world > 1:
+    if world > 1:
         store.set(f"{tag}/{rank}", status)
         _await_ranks(store, tag, world, timeout)
     N = J_r.shape[0]
@@ -110,8 +114,11 @@ def sharded_jacobian(c, basis, engine, rank: int, world: int, group=None, store=
     local[1:1 + (e - s)] = J_r[:, 2:].T
     t = torch.tensor(local, dtype=torch.float64)
     if world > 1:
+        if dist.get_backend(group) == "nccl":      # NCCL gathers device tensors only
+            t = t.to(torch.device("cuda", torch.cuda.current_device()))
         parts = [torch.empty_like(t) for _ in range(world)]
         dist.all_gather(parts, t, group=group)
+        parts = [p.cpu() for p in parts]
     else:
         parts = [t]
     J = np.empty((N, n + 1))

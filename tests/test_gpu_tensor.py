@@ -1,8 +1,10 @@
-"""Tensor-core products of the mixed form, through the C ABI self-tests
-(standard-normal operands; the reference is the library's FP64 DGEMM):
-the 3+3-slice bf16 product must be FP32-accurate, the 7+7-digit product
-(Ozaki scheme) FP64-accurate, on shapes that cover one tile, several tiles,
-ragged edges and the full N = 2048 x 514 x 2048 size of the benchmark."""
+"""Dense products of both forms, through the C ABI self-tests, against an
+independent host product (numpy FP64 matmul of the same operands, copied to
+the CPU): the 3+3-slice bf16 tensor-core product must be FP32-accurate, the
+7+7-digit tensor-core product (Ozaki scheme) and the FP64 DGEMM of the plain
+form FP64-accurate, on shapes that cover one tile, several tiles, ragged
+edges and the full N = 2048 x 514 x 2048 size of the benchmark.  Standard-
+normal operands; the error is max|C - C_host| / max|C_host|."""
 import numpy as np
 import pytest
 
@@ -27,10 +29,16 @@ def operands(M, Nn, K, seed):
     return A, B
 
 
+def rel_err(ww, kind, M, Nn, K, seed):
+    A, B = operands(M, Nn, K, seed)
+    C = ww.selftest(kind, A, B).cpu().numpy()
+    ref = A.cpu().numpy() @ B.cpu().numpy()
+    return float(np.abs(C - ref).max() / np.abs(ref).max())
+
+
 @pytest.mark.parametrize("M,Nn,K", SHAPES)
 def test_sliced_product_is_fp32_accurate(ww, M, Nn, K):
-    A, B = operands(M, Nn, K, 1)
-    err = ww.selftest("f32gemm", A, B)
+    err = rel_err(ww, "f32gemm", M, Nn, K, 1)
     # 24-bit operands; the tensor cores accumulate in fp32 once per K = 16 MMA
     # and pair (6 K/16 roundings), ~1e-5 of max |C| at K = 2048 -- ample for
     # a preconditioner, whose error is squared away by the refinement
@@ -39,14 +47,20 @@ def test_sliced_product_is_fp32_accurate(ww, M, Nn, K):
 
 @pytest.mark.parametrize("M,Nn,K", SHAPES)
 def test_digit_product_is_fp64_accurate(ww, M, Nn, K):
-    A, B = operands(M, Nn, K, 2)
-    err = ww.selftest("ozaki", A, B)
+    err = rel_err(ww, "ozaki", M, Nn, K, 2)
     # the kept pairs end at g = 6; the first dropped group (g = 7, weight
-    # 2^-61 of 2^(ea + fb)) is ~5e-14 of max|C| for Gaussian operands (the
-    # same digits emulated exactly on the CPU give the same figure).  For the
-    # kernel matrices it is far smaller relative to the result, whose row
-    # maxima are O(1/N) of the operator norm.
+    # 2^-61 of 2^(ea + fb)) is ~5e-14 of max|C| for Gaussian operands.  The
+    # host product's own rounding (~1e-15 of max|C|) is far below.  For the
+    # kernel matrices the dropped group is far smaller relative to the result,
+    # whose row maxima are O(1/N) of the operator norm.
     assert err < 1.5e-13, err
+
+
+@pytest.mark.parametrize("M,Nn,K", SHAPES)
+def test_fp64_dgemm_is_fp64_accurate(ww, M, Nn, K):
+    err = rel_err(ww, "dgemm", M, Nn, K, 3)
+    # two FP64 sums of K products in different orders: ~sqrt(K) eps of max|C|
+    assert err < 1e-14, err
 
 
 def test_assembly_reciprocal_within_one_ulp(ww):

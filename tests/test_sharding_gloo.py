@@ -105,9 +105,10 @@ def test_column_ranges_and_single_rank():
 
 
 def _failing_rank_main(rank, ws, port, q, mode):
-    """Rank 1 fails: its engine raises ("raise"), or it leaves between steps
-    without reporting ("exit"); the others must learn of it on the host through
-    the store and raise ShardFailure, never entering the all-gather."""
+    """Rank 1 fails: its engine raises ("raise"; "raise-default" passes no store,
+    so the process group's own store carries the reports), or it leaves between
+    steps without reporting ("exit"); the others must learn of it on the host
+    through the store and raise ShardFailure, never entering the all-gather."""
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
     sys.path.insert(0, ROOT)
     from datetime import timedelta
@@ -119,7 +120,7 @@ def _failing_rank_main(rank, ws, port, q, mode):
     dist.init_process_group("gloo", store=store, rank=rank, world_size=ws, timeout=timedelta(seconds=30))
     c, basis = _problem()
     engine = _oracle_engine()
-    if rank == 1 and mode == "raise":
+    if rank == 1 and mode.startswith("raise"):
         def engine(c_r, basis_r):
             raise RuntimeError("planted engine failure")
     if rank == 1 and mode == "exit":
@@ -128,7 +129,8 @@ def _failing_rank_main(rank, ws, port, q, mode):
         q.join_thread()                 # the queue's feeder thread writes before the exit
         os._exit(0)
     try:
-        sharded_jacobian(c, basis, engine, rank, ws, store=store, tag="t", timeout=3.0)
+        sharded_jacobian(c, basis, engine, rank, ws, store=None if mode == "raise-default" else store, tag="t",
+                         timeout=3.0)
         q.put((rank, "no error"))
     except ShardFailure as e:
         q.put((rank, f"ShardFailure: {e}"))
@@ -144,7 +146,7 @@ def _failing_rank_main(rank, ws, port, q, mode):
     os._exit(0)
 
 
-@pytest.mark.parametrize("mode,ws", [("raise", 2), ("exit", 2), ("exit", 3)])
+@pytest.mark.parametrize("mode,ws", [("raise", 2), ("raise-default", 2), ("exit", 2), ("exit", 3)])
 def test_a_failed_rank_is_detected_on_the_host(mode, ws):
     import time
     ctx = mp.get_context("spawn")
