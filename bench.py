@@ -312,7 +312,7 @@ def run_fp64_form(ww, w, c, dev, flush):
     outs = ctx.empty_outputs()
     ct = torch.tensor(c, dtype=torch.float64, device=dev)
     times, launches = _jacobian_rate(ww, ctx, ct, outs, stream, flush, 1, 0)
-    res = tuple(x.cpu().numpy() for x in outs)
+    res = (outs[0].cpu().numpy(), outs[1].cpu().numpy(), float(outs[2].item()))
     ctx.close()
     return times[0], launches, res
 
@@ -424,11 +424,13 @@ GRAD_METRIC = "gradients/s of f(c) by the discrete adjoint at N=1024 (256 modes 
 
 
 def run_gradient(args):
-    """--mode gradient: one step = one objective_and_grad (forward shot that
-    records every stage, then the transposed RK4 sweep) on a gradient workload
-    (default: N = 1024, 256 modes + T, 2048 steps, h = 0.05).  The forward
-    Jacobian route (shoot_jacobian, then J^T r) on the same problem is timed
-    once beside it."""
+    """--mode gradient: one step = one objective_and_grad (forward shot, then
+    the transposed RK4 sweep) on a gradient workload (default: N = 1024, 256
+    modes + T, 2048 steps, h = 0.05), with the base trajectory checkpointed
+    every --checkpoint steps (default 45 ~ sqrt(2048); 0 keeps every stage's
+    record resident).  The other memory mode and the forward Jacobian route
+    (shoot_jacobian, then J^T r) on the same problem are timed once beside it,
+    with their device memory and agreement."""
     import torch
     import paper_1210_5672_gb300 as ww
 
@@ -449,6 +451,8 @@ def run_gradient(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)
     stream = torch.cuda.Stream(dev)
     ctx.set_stream(stream)
+    ckpt = min(args.checkpoint, w.steps)
+    ctx.set_checkpoint(ckpt)
     for _ in range(args.warmup):
         ww.objective_and_grad(ctx, ct, f, grad)
     torch.cuda.synchronize()
@@ -488,6 +492,23 @@ def run_gradient(args):
         stream.synchronize()
         e2e_t.append(time.perf_counter() - t0)
     _, e2e_value = replica_rate(sum(e2e_t) / len(e2e_t), ws, 1)
+    # the other memory mode, once (after one untimed call that sizes its workspace)
+    g_main = grad.cpu().numpy()
+    other = 0 if ckpt else max(1, round(math.sqrt(w.steps)))
+    ctx.set_checkpoint(other)
+    ww.objective_and_grad(ctx, ct, f, grad)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ww.objective_and_grad(ctx, ct, f, grad)
+    e1.record(stream)
+    e1.synchronize()
+    st_other = ctx.stats()
+    g_other = grad.cpu().numpy()
+    other_mode = {"checkpoint_every": other, "seconds": e0.elapsed_time(e1) / 1e3,
+                  "adjoint_bytes": st_other["adjoint_bytes"], "device_bytes": st_other["device_bytes"],
+                  "rel_diff_grad": float(np.linalg.norm(g_other - g_main) / np.linalg.norm(g_main))}
+    ctx.set_checkpoint(ckpt)
     # the forward route for comparison: n + 1 variational columns, then J^T r
     r, J, fj = ctx.empty_outputs()
     ww.shoot_jacobian(ctx, ct, r, J, fj)
@@ -499,7 +520,7 @@ def run_gradient(args):
     e1.synchronize()
     t_jac = e0.elapsed_time(e1) / 1e3
     jtr = (J @ r).cpu().numpy()
-    g_adj = grad.cpu().numpy()
+    g_adj = g_main
     agree = float(np.linalg.norm(g_adj - jtr) / np.linalg.norm(jtr))
     ctx.close()
     if rank != 0:
@@ -511,6 +532,7 @@ def run_gradient(args):
         "data": "synthetic (seeded PCG64 standing-wave coefficients)",
         "config": {"workload": w.name, "N": w.N, "n": w.n, "rk4_steps": w.steps, "h": w.h, "g": w.g,
                    "tau": w.tau, "form": args.form, "seed": seed_used, "mode": "gradient",
+                   "checkpoint_every": ckpt,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "flushed between timed steps (512 MB write)"},
         "e2e": {"value": e2e_value, "unit": "gradients/s", "h2d_bytes_per_step": 8 * (w.n + 1),
@@ -518,6 +540,9 @@ def run_gradient(args):
         "roofline": None,
         "forward_route": {"shoot_jacobian_s": t_jac, "adjoint_s": t_step,
                           "speedup": t_jac / t_step, "rel_diff_grad_vs_JTr": agree},
+        "memory": {"checkpoint_every": ckpt, "adjoint_bytes": stats["adjoint_bytes"],
+                   "device_bytes": stats["device_bytes"]},
+        "other_memory_mode": other_mode,
         "stats": stats,
         "gpu_launches": gpu_launches,
         "clocks": clocks,
@@ -695,6 +720,8 @@ def main():
     ap.add_argument("--mode", default="jacobian", choices=["jacobian", "gradient", "batch"],
                     help="gradient: objective_and_grad by the discrete adjoint (default workload "
                          "N1024_n256_steps2048_h0.05)")
+    ap.add_argument("--checkpoint", type=int, default=45,
+                    help="gradient mode: checkpoint the base state every K steps (0: every stage's record resident)")
     ap.add_argument("--rk-steps", type=int, default=0,
                     help="profiling only: override the workload's RK4 step count (not a bench number)")
     args = ap.parse_args()
@@ -707,7 +734,8 @@ def main():
         B.build()
         out = {"gradient": run_gradient, "batch": run_batch}.get(args.mode, run_ours)(args)
     if out is not None:
-        print(json.dumps(out), flush=True)
+        # numpy scalars and arrays (should any reach the line) print as plain numbers / lists
+        print(json.dumps(out, default=lambda v: v.tolist() if hasattr(v, "tolist") else str(v)), flush=True)
 
 
 if __name__ == "__main__":

@@ -86,6 +86,19 @@ typedef struct {
                                   records, checkpoints, second operand copies)      */
 } ww_stats;
 
+/* How a context lays out its step program (no counterpart in the paper: the
+ * knobs of the GB300 kernels; ww_autotune picks them by timing).  Every
+ * schedule computes the same discrete map to the same accuracy. */
+typedef struct {
+    int overlap;   /* WW_MIXED: run the base chain one stage ahead of the columns on a
+                      second branch of the step graph (1), or in line (0)              */
+    int ns_every;  /* WW_MIXED with overlap: move the approximate inverse to every
+                      stage's A (1), or on even stages and when it drifted (0)         */
+    int corr_bn;   /* WW_MIXED: column tile of the refinement corrections X R (32, 64, 128) */
+    int inv_bn;    /* WW_MIXED: column tile of the inverse update's products (64, 128)  */
+    int lu_nb;     /* WW_FP64: block size of the LU and triangular solves (32, 64)      */
+} ww_schedule;
+
 typedef struct ww_ctx ww_ctx;
 
 /* Create a context for problem *p on the current CUDA device: validates the
@@ -115,6 +128,25 @@ int ww_get_stats(const ww_ctx *ctx, ww_stats *out);
  * default) turns it off.  A change takes effect at the next call, whose
  * step program is captured again.  WW_ERR_ARG in WW_FP64 (no refinement). */
 int ww_set_verify(ww_ctx *ctx, int every);
+
+/* The context's schedule.  ww_create sets the default {1, 1, 64, 128, 64};
+ * ww_set_schedule validates the fields (WW_ERR_ARG) and drops the captured
+ * step programs, which the next call captures again. */
+int ww_set_schedule(ww_ctx *ctx, const ww_schedule *s);
+int ww_get_schedule(const ww_ctx *ctx, ww_schedule *s);
+
+/* ww_autotune -- choose the context's schedule by timing.  Candidate
+ * schedules (coordinate by coordinate: the stage program, then the tile of
+ * the corrections, then the tile of the inverse update in WW_MIXED; the LU
+ * block in WW_FP64) each run the initial data and probe_steps RK steps of the
+ * Jacobian of the shot c (device, n+1 doubles) on the context's stream, timed
+ * with CUDA events after one untimed step; the fastest is kept.  cache_path
+ * (NULL: none) names a text file of earlier choices, one line per (N, n+1,
+ * precision): a cached choice is taken without timing, and a new one is
+ * appended.  *ms_per_step (may be NULL) receives the chosen schedule's probe
+ * time per RK step (0 when it came from the cache).  The context's outputs
+ * are not touched; its state afterwards is that of a partial shot. */
+int ww_autotune(ww_ctx *ctx, const double *c, int probe_steps, const char *cache_path, double *ms_per_step);
 
 /* Thread-local description of the last error (empty string if none). */
 const char *ww_last_error(void);
@@ -173,16 +205,20 @@ int shoot_jacobian(ww_ctx *ctx, const double *c, double *r, double *J, double *f
 int shoot_jacobian_host(ww_ctx *ctx, const double *c, double *r, double *J, double *f);
 
 /* shoot_jacobian_batch -- nshots independent shots (each its own context,
- * problem size and step count) in one call, run concurrently on one GPU:
- * every shot replays its own captured step graph on its own stream, and the
- * replays of all shots are issued in turn, so small shots fill the SMs that a
- * large one leaves idle (the paper runs 2-3 jobs per GPU for the same reason,
- * Sec. 4.6).  ctx[i], cvec[i], r[i], J[i], f[i] as for shoot_jacobian (device
- * arrays of shot i's sizes).  The contexts must be distinct and each on a
- * stream of its own (ww_create gives one; the legacy default stream is
- * rejected with WW_ERR_ARG).  Returns when every shot is done; the first
- * failing shot's status is returned, its message naming the shot.  Results
- * are bitwise those of shoot_jacobian on each context. */
+ * problem size, step count and schedule) in ONE graph launch on one GPU: the
+ * batch graph holds, per shot, a branch [inputs, initial data, a WHILE node
+ * whose body is the shot's captured RK step and a counter that ends the loop
+ * after its `steps` steps, outputs], and the branches run concurrently, so
+ * small shots fill the SMs that a large one leaves idle (the paper runs 2-3
+ * jobs per GPU for the same reason, Sec. 4.6).  ctx[i], cvec[i], r[i], J[i],
+ * f[i] as for shoot_jacobian (device arrays of shot i's sizes).  The
+ * contexts must be distinct and each on a stream of its own (ww_create gives
+ * one; the legacy default stream is rejected with WW_ERR_ARG).  The graph is
+ * built on the first call with a given set of contexts and arrays and kept
+ * for the next; it is launched on ctx[0]'s stream after the other shots'
+ * streams, which wait for it in turn.  Returns when every shot is done; the
+ * first failing shot's status is returned, its message naming the shot.
+ * Results are bitwise those of shoot_jacobian on each context. */
 int shoot_jacobian_batch(ww_ctx *const *ctx, int nshots, const double *const *cvec, double *const *r,
                          double *const *J, double *const *f);
 

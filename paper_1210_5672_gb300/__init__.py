@@ -36,7 +36,8 @@ ERRORS = {
 WW_FP64, WW_MIXED = 0, 1
 EXPORTS = ("ww_create", "ww_destroy", "ww_set_stream", "ww_get_stats", "ww_last_error", "ww_set_timing",
            "ww_get_timing", "dtn_setup", "dtn_apply", "shoot", "shoot_jacobian", "shoot_jacobian_host",
-           "shoot_jacobian_batch", "objective_and_grad", "dtn_apply_static", "ww_set_verify", "ww_set_checkpoint", "ww_selftest_f32gemm",
+           "shoot_jacobian_batch", "objective_and_grad", "dtn_apply_static", "ww_set_verify", "ww_set_checkpoint", "ww_set_schedule", "ww_get_schedule",
+           "ww_autotune", "ww_selftest_f32gemm",
            "ww_selftest_ozaki", "ww_selftest_dgemm", "ww_selftest_recip")
 STATIC_MAX_N, STATIC_MAX_RHS = 256, 64
 PHASES = ("assembly", "factor", "solve", "gapply", "colrhs", "gamma", "base", "gkernel", "inverse")
@@ -54,6 +55,15 @@ class _Problem(C.Structure):
         ("steps", C.c_int), ("basis", C.POINTER(C.c_double)), ("precision", C.c_int),
         ("refine_tol", C.c_double), ("max_refine", C.c_int),
     ]
+
+
+class Schedule(C.Structure):
+    """ww_schedule: the knobs of the step program (see include/ww.h)."""
+    _fields_ = [("overlap", C.c_int), ("ns_every", C.c_int), ("corr_bn", C.c_int), ("inv_bn", C.c_int),
+                ("lu_nb", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Stats(C.Structure):
@@ -99,6 +109,9 @@ def lib():
             "dtn_apply_static": (I, [V, V, I, I, D, V, V]),
             "ww_set_verify": (I, [V, I]),
             "ww_set_checkpoint": (I, [V, I]),
+            "ww_set_schedule": (I, [V, C.POINTER(Schedule)]),
+            "ww_get_schedule": (I, [V, C.POINTER(Schedule)]),
+            "ww_autotune": (I, [V, V, I, C.c_char_p, C.POINTER(D)]),
             "ww_selftest_f32gemm": (I, [V, V, I, I, I, V]),
             "ww_selftest_ozaki": (I, [V, V, I, I, I, V]),
             "ww_selftest_dgemm": (I, [V, V, I, I, I, V]),
@@ -192,6 +205,29 @@ class Context:
         the base state every K steps and recomputes each segment's records
         (K = round(sqrt(steps)) bounds the memory by ~sqrt(steps))."""
         _check(lib().ww_set_checkpoint(self.handle, int(every)))
+
+    def schedule(self) -> dict:
+        sch = Schedule()
+        _check(lib().ww_get_schedule(self.handle, C.byref(sch)))
+        return sch.as_dict()
+
+    def set_schedule(self, **kw):
+        """Change fields of the schedule (overlap, ns_every, corr_bn, inv_bn, lu_nb)."""
+        cur = self.schedule()
+        unknown = set(kw) - set(cur)
+        if unknown:
+            raise ValueError(f"unknown schedule fields {sorted(unknown)}")
+        cur.update(kw)
+        _check(lib().ww_set_schedule(self.handle, C.byref(Schedule(**cur))))
+
+    def autotune(self, c, probe_steps: int = 4, cache_path=None) -> float:
+        """ww_autotune on the shot c (CUDA float64, n+1): the fastest schedule is
+        kept (and appended to cache_path); returns its probe ms per RK step
+        (0.0 when the choice came from the cache)."""
+        ms = C.c_double(0.0)
+        path = None if cache_path is None else os.fsencode(cache_path)
+        _check(lib().ww_autotune(self.handle, _dptr(c, self.n + 1, "c"), int(probe_steps), path, C.byref(ms)))
+        return ms.value
 
     def set_verify(self, every: int):
         """WW_MIXED: measure the true refinement residual of every `every`-th

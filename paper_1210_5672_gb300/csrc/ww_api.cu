@@ -5,9 +5,15 @@
 // captured once per context into a CUDA graph and replayed `steps` times; in
 // the mixed form the base chain runs one stage ahead of the columns on a
 // second branch of that graph (capture_overlapped).
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -102,7 +108,30 @@ struct Owned {
     AdjWs adj = {};
     StepGraph adj_fwd, adj_mid, adj_bwd;
     StepGraph adj_restart, adj_reentry;       // checkpointed sweep: segment restart (forward) and re-entry (backward)
+    // the batch graph: this shot's step counter, and identifiers that key cached batch graphs
+    int *loop_count = nullptr;
+    unsigned long long id = 0;                // unique per context, never reused
+    unsigned long long version = 0;           // bumped whenever the captured step programs are dropped
 };
+
+void destroy_graph(StepGraph &sg) {
+    if (sg.exec) cudaGraphExecDestroy(sg.exec);
+    if (sg.graph) cudaGraphDestroy(sg.graph);
+    sg = StepGraph();
+}
+
+void drop_batch_graphs(unsigned long long id);   // below
+
+// every captured program of a context (after a change of its schedule or verification)
+void drop_graphs(Owned *o) {
+    for (int w = 0; w < 2; ++w) {
+        for (int t = 0; t < 2; ++t) destroy_graph(o->graphs[w][t]);
+        destroy_graph(o->prologue[w]);
+    }
+    for (StepGraph *sg : {&o->adj_fwd, &o->adj_mid, &o->adj_bwd, &o->adj_restart, &o->adj_reentry}) destroy_graph(*sg);
+    o->version += 1;
+    drop_batch_graphs(o->id);
+}
 
 // record the begin (b = 0) or end (b = 1) event of a phase of stage st
 int mark(Ctx *c, int st, int phase, int b) {
@@ -238,7 +267,8 @@ int run_stage(Ctx *c, int st, const double *cvec, int with_cols) {
 // that is not taken and changes nothing that is read afterwards.
 bool overlapped(const Owned *o, int with_cols) {
     const Ctx *c = &o->c;
-    return c->precision == WW_MIXED && with_cols && c->nc > 0 && c->stream != nullptr && o->side_stream != nullptr;
+    return c->precision == WW_MIXED && with_cols && c->nc > 0 && c->stream != nullptr && o->side_stream != nullptr &&
+           c->sch.overlap != 0;
 }
 
 int capture_overlapped(Owned *o, const double *cvec) {
@@ -260,7 +290,7 @@ int capture_overlapped(Owned *o, const double *cvec) {
             if (e != cudaSuccess) st = fail(WW_ERR_CUDA, std::string("capture join: ") + cudaGetErrorString(e));
         }
         select_parity(c, (s + 1) & 1);
-        if (st == WW_OK) st = run_base(c, (s + 1) & 3, cvec, true);
+        if (st == WW_OK) st = run_base(c, (s + 1) & 3, cvec, c->sch.ns_every != 0);
         if (st == WW_OK && s < 3) {
             cudaError_t e = cudaEventRecord(o->ev_base[s + 1], side);
             if (e != cudaSuccess) st = fail(WW_ERR_CUDA, std::string("capture fork: ") + cudaGetErrorString(e));
@@ -335,21 +365,33 @@ int prologue(Owned *o, const double *cvec, int with_cols) {
         WW_TRY(launch_base_geometry(c, c->Ys, c->Ys + c->N, 1));
         WW_TRY(launch_assemble(c));
         WW_TRY(factor(c, 1));
-        if (overlapped(o, with_cols)) WW_TRY(run_base(c, 0, cvec, true));   // the base chain runs one stage ahead
+        if (overlapped(o, with_cols))   // the base chain runs one stage ahead
+            WW_TRY(run_base(c, 0, cvec, c->sch.ns_every != 0));
     }
     return WW_OK;
 }
 
+int build_prologue_graph(Owned *o, int with_cols);
+
 int run_prologue(Owned *o, int with_cols) {
+    Ctx *c = &o->c;
+    if (c->stream == nullptr) {
+        const bool timing = o->timing;
+        o->timing = false;   // the prologue is not part of the timed phases
+        const int st = prologue(o, o->cbuf, with_cols);
+        o->timing = timing;
+        return st;
+    }
+    WW_TRY(build_prologue_graph(o, with_cols));
+    WW_CUDA_TRY(cudaGraphLaunch(o->prologue[with_cols].exec, c->stream));
+    return WW_OK;
+}
+
+int build_prologue_graph(Owned *o, int with_cols) {
     Ctx *c = &o->c;
     const bool timing = o->timing;
     o->timing = false;   // the prologue is not part of the timed phases
     int st = WW_OK;
-    if (c->stream == nullptr) {
-        st = prologue(o, o->cbuf, with_cols);
-        o->timing = timing;
-        return st;
-    }
     StepGraph &pg = o->prologue[with_cols];
     if (!pg.exec) {
         cudaGraph_t g = nullptr;
@@ -372,7 +414,6 @@ int run_prologue(Owned *o, int with_cols) {
         if (e != cudaSuccess) return fail(WW_ERR_CUDA, std::string("prologue instantiate: ") + cudaGetErrorString(e));
     }
     o->timing = timing;
-    WW_CUDA_TRY(cudaGraphLaunch(pg.exec, c->stream));
     return WW_OK;
 }
 
@@ -796,6 +837,208 @@ int run_adjoint(Owned *o, const double *cvec, bool c_on_host, double *f, double 
     return check_status(c);
 }
 
+// ---------------------------------------------------------------- the batch graph
+// One RK step of a shot inside the batch graph's WHILE node ends with this
+// kernel: it counts the steps and keeps the loop going while steps remain.
+__global__ void k_loop_tick(int *count, int steps, cudaGraphConditionalHandle h) {
+    const int k = *count + 1;
+    *count = k;
+    cudaGraphSetConditional(h, k < steps ? 1u : 0u);
+}
+
+struct BatchGraph {
+    std::vector<unsigned long long> key;      // (id, version) of each context, then the array pointers
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long step_kernels = 0;               // kernels per step of every shot, summed (launch counts)
+};
+
+std::mutex g_batch_mu;
+std::vector<BatchGraph> g_batch;              // a few recently used batch graphs
+
+void destroy_batch(BatchGraph &b) {
+    if (b.exec) cudaGraphExecDestroy(b.exec);
+    if (b.graph) cudaGraphDestroy(b.graph);
+    b = BatchGraph();
+}
+
+void drop_batch_graphs(unsigned long long id) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (size_t i = 0; i < g_batch.size();) {
+        bool has = false;
+        const size_t nctx = g_batch[i].key.empty() ? 0 : (size_t)g_batch[i].key[0];
+        for (size_t k = 0; k < nctx && !has; ++k) has = g_batch[i].key[1 + 2 * k] == id;
+        if (has) {
+            destroy_batch(g_batch[i]);
+            g_batch.erase(g_batch.begin() + (long)i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+// a small graph captured on the context's stream from `body`
+template <class F>
+int capture_small(Ctx *c, cudaGraph_t *out, F body) {
+    *out = nullptr;
+    WW_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    const int st = body();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (st != WW_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(WW_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    *out = g;
+    return WW_OK;
+}
+
+// the branch of shot `o` in the batch graph bg: inputs, initial data, the WHILE
+// node of its steps, outputs
+int add_batch_branch(cudaGraph_t bg, Owned *o, const double *cvec, double *r, double *J, double *f) {
+    Ctx *c = &o->c;
+    c->one_col = false;
+    WW_TRY(build_prologue_graph(o, 1));
+    WW_TRY(build_step_graph(o, 1));
+    cudaGraph_t pre = nullptr, post = nullptr;
+    WW_TRY(capture_small(c, &pre, [&] {
+        WW_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+        WW_CUDA_TRY(cudaMemsetAsync(o->loop_count, 0, sizeof(int), c->stream));
+        WW_CUDA_TRY(cudaMemcpyAsync(o->cbuf, cvec, sizeof(double) * (c->n + 1), cudaMemcpyDeviceToDevice, c->stream));
+        return WW_OK;
+    }));
+    int st = capture_small(c, &post, [&] { return launch_outputs(c, r, J, f, 1); });
+    cudaGraphNode_t n_pre = nullptr, n_pro = nullptr, n_loop = nullptr, n_post = nullptr, n_step = nullptr,
+                    n_tick = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (st == WW_OK) e = cudaGraphAddChildGraphNode(&n_pre, bg, nullptr, 0, pre);
+    if (st == WW_OK && e == cudaSuccess)
+        e = cudaGraphAddChildGraphNode(&n_pro, bg, &n_pre, 1, o->prologue[1].graph);
+    cudaGraphConditionalHandle h{};
+    if (st == WW_OK && e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, bg, 1, cudaGraphCondAssignDefault);
+    cudaGraph_t body = nullptr;
+    if (st == WW_OK && e == cudaSuccess) {
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&n_loop, bg, &n_pro, nullptr, 1, &cp);
+        if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+    }
+    if (st == WW_OK && e == cudaSuccess)
+        e = cudaGraphAddChildGraphNode(&n_step, body, nullptr, 0, o->graphs[1][0].graph);
+    if (st == WW_OK && e == cudaSuccess) {
+        int *cnt = o->loop_count;
+        int steps = c->steps;
+        void *args[] = {&cnt, &steps, &h};
+        cudaKernelNodeParams kp{};
+        kp.func = reinterpret_cast<void *>(k_loop_tick);
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(1);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args;
+        e = cudaGraphAddKernelNode(&n_tick, body, &n_step, 1, &kp);
+    }
+    if (st == WW_OK && e == cudaSuccess) e = cudaGraphAddChildGraphNode(&n_post, bg, &n_loop, 1, post);
+    if (pre) cudaGraphDestroy(pre);     // the child nodes hold copies
+    if (post) cudaGraphDestroy(post);
+    if (st != WW_OK) return st;
+    if (e != cudaSuccess) return fail(WW_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    return WW_OK;
+}
+
+// ---------------------------------------------------------------- schedules and the autotuner
+int check_schedule(const Ctx *c, const ww_schedule &s) {
+    if ((s.overlap != 0 && s.overlap != 1) || (s.ns_every != 0 && s.ns_every != 1))
+        return fail(WW_ERR_ARG, "ww_schedule: overlap and ns_every must be 0 or 1");
+    if (s.corr_bn != 32 && s.corr_bn != 64 && s.corr_bn != 128)
+        return fail(WW_ERR_ARG, "ww_schedule: corr_bn must be 32, 64 or 128");
+    if (s.inv_bn != 64 && s.inv_bn != 128) return fail(WW_ERR_ARG, "ww_schedule: inv_bn must be 64 or 128");
+    if (s.lu_nb != 32 && s.lu_nb != 64) return fail(WW_ERR_ARG, "ww_schedule: lu_nb must be 32 or 64");
+    (void)c;
+    return WW_OK;
+}
+
+int apply_schedule(Owned *o, const ww_schedule &s) {
+    Ctx *c = &o->c;
+    WW_TRY(check_schedule(c, s));
+    if (std::memcmp(&c->sch, &s, sizeof(s)) == 0) return WW_OK;
+    WW_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (o->side_stream) WW_CUDA_TRY(cudaStreamSynchronize(o->side_stream));
+    drop_graphs(o);
+    c->sch = s;
+    // the LU block (the inverted diagonal blocks' buffer is sized for LU_NB, the largest)
+    c->nb = c->N < s.lu_nb ? c->N : s.lu_nb;
+    return WW_OK;
+}
+
+std::string tune_key(const Ctx *c) {
+    std::ostringstream k;
+    k << c->N << " " << c->nc << " " << (c->precision == WW_MIXED ? "mixed" : "fp64");
+    return k.str();
+}
+
+// the cached schedule of this (N, n+1, precision), if the file has one
+bool cache_lookup(const char *path, const std::string &key, ww_schedule *out) {
+    if (!path) return false;
+    std::ifstream in(path);
+    std::string line;
+    bool found = false;
+    while (std::getline(in, line)) {
+        std::istringstream ls(line);
+        int N = 0, nc = 0;
+        std::string form;
+        ww_schedule s{};
+        if (!(ls >> N >> nc >> form >> s.overlap >> s.ns_every >> s.corr_bn >> s.inv_bn >> s.lu_nb)) continue;
+        std::ostringstream k;
+        k << N << " " << nc << " " << form;
+        if (k.str() == key) {
+            *out = s;
+            found = true;   // the last line for a key wins
+        }
+    }
+    return found;
+}
+
+int cache_store(const char *path, const std::string &key, const ww_schedule &s, double ms) {
+    if (!path) return WW_OK;
+    std::ofstream out(path, std::ios::app);
+    if (!out) return fail(WW_ERR_ARG, std::string("ww_autotune: cannot append to ") + path);
+    out << key << " " << s.overlap << " " << s.ns_every << " " << s.corr_bn << " " << s.inv_bn << " " << s.lu_nb << " "
+        << ms << "\n";
+    return WW_OK;
+}
+
+// ms per RK step of the Jacobian program under schedule s: initial data, one
+// untimed step (captures the program), probe steps timed with events
+int probe_schedule(Owned *o, const ww_schedule &s, int probe_steps, double *ms) {
+    Ctx *c = &o->c;
+    WW_TRY(apply_schedule(o, s));
+    c->one_col = false;
+    WW_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    WW_TRY(run_prologue(o, 1));
+    WW_TRY(build_step_graph(o, 1));
+    const cudaGraphExec_t ex = o->graphs[1][0].exec;
+    WW_CUDA_TRY(cudaGraphLaunch(ex, c->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    WW_CUDA_TRY(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+    for (int k = 0; k < probe_steps && e == cudaSuccess; ++k) e = cudaGraphLaunch(ex, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(WW_ERR_CUDA, std::string("ww_autotune probe: ") + cudaGetErrorString(e));
+    const int stt = check_status(c);   // a schedule that fails to converge is not a candidate
+    *ms = stt == WW_OK ? (double)t / probe_steps : INFINITY;
+    return WW_OK;
+}
+
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 }  // namespace
@@ -842,7 +1085,12 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
     c->precision = p->precision;
     c->refine_tol = p->refine_tol > 0.0 ? p->refine_tol : 1e-13;
     c->max_refine = p->max_refine > 0 ? p->max_refine : 4;
+    c->sch = ww_schedule{1, 1, 64, 128, LU_NB};
     c->nb = c->N < LU_NB ? c->N : LU_NB;
+    {
+        static std::atomic<unsigned long long> next_id{1};
+        o->id = next_id++;
+    }
     {
         cudaError_t e0 = cudaStreamCreateWithFlags(&o->own_stream, cudaStreamNonBlocking);
         if (e0 != cudaSuccess) {
@@ -913,6 +1161,7 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
     ALLOC(o->rbuf, N);
     ALLOC(o->Jbuf, N * c->nc);
     ALLOC(o->fbuf, 1);
+    ALLOC(o->loop_count, 1);
 #undef ALLOC
     if (st != WW_OK) {
         ww_destroy(reinterpret_cast<ww_ctx *>(o));
@@ -970,6 +1219,7 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
 void ww_destroy(ww_ctx *ctx) {
     if (!ctx) return;
     Owned *o = owner(ctx);
+    drop_batch_graphs(o->id);
     for (int w = 0; w < 2; ++w) {
         for (int t = 0; t < 2; ++t) {
             if (o->graphs[w][t].exec) cudaGraphExecDestroy(o->graphs[w][t].exec);
@@ -1031,14 +1281,9 @@ int ww_set_verify(ww_ctx *ctx, int every) {
         return fail(WW_ERR_ARG, "ww_set_verify: only WW_MIXED has a refinement residual to measure");
     if (o->c.verify_every == every) return WW_OK;
     WW_CUDA_TRY(cudaStreamSynchronize(o->c.stream));
+    if (o->side_stream) WW_CUDA_TRY(cudaStreamSynchronize(o->side_stream));
     // the step programs captured so far were built without (or with) the measurement
-    for (int w = 0; w < 2; ++w)
-        for (int t = 0; t < 2; ++t) {
-            StepGraph &sg = o->graphs[w][t];
-            if (sg.exec) cudaGraphExecDestroy(sg.exec);
-            if (sg.graph) cudaGraphDestroy(sg.graph);
-            sg = StepGraph();
-        }
+    drop_graphs(o);
     o->c.verify_every = every;
     return WW_OK;
 }
@@ -1114,6 +1359,7 @@ int shoot_jacobian_batch(ww_ctx *const *ctx, int nshots, const double *const *cv
                          double *const *J, double *const *f) {
     if (nshots < 0 || (nshots > 0 && (!ctx || !cvec || !r || !J || !f)))
         return fail(WW_ERR_ARG, "shoot_jacobian_batch: NULL argument");
+    if (nshots == 0) return WW_OK;
     for (int i = 0; i < nshots; ++i) {
         if (!ctx[i] || !cvec[i] || !r[i] || !J[i] || !f[i])
             return fail(WW_ERR_ARG, "shoot_jacobian_batch: NULL entry for shot " + std::to_string(i));
@@ -1132,38 +1378,72 @@ int shoot_jacobian_batch(ww_ctx *const *ctx, int nshots, const double *const *cv
             for (auto &p : saved) p.first->timing = p.second;
         }
     } guard;
+    std::vector<unsigned long long> key{(unsigned long long)nshots};
     for (int i = 0; i < nshots; ++i) {
         Owned *o = owner(ctx[i]);
         guard.saved.emplace_back(o, o->timing);
         o->timing = false;
+        key.push_back(o->id);
+        key.push_back(o->version);
     }
-    // 1. per shot: inputs, initial data, its step graph (captured on first use)
-    int max_steps = 0;
-    for (int i = 0; i < nshots; ++i) {
-        Owned *o = owner(ctx[i]);
-        Ctx *c = &o->c;
-        c->one_col = false;
-        WW_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
-        WW_CUDA_TRY(cudaMemcpyAsync(o->cbuf, cvec[i], sizeof(double) * (c->n + 1), cudaMemcpyDeviceToDevice,
-                                    c->stream));
-        WW_TRY(run_prologue(o, 1));
-        WW_TRY(build_step_graph(o, 1));
-        max_steps = c->steps > max_steps ? c->steps : max_steps;
+    for (int i = 0; i < nshots; ++i)
+        for (const void *p : {(const void *)cvec[i], (const void *)r[i], (const void *)J[i], (const void *)f[i]})
+            key.push_back((unsigned long long)(uintptr_t)p);
+    Owned *o0 = owner(ctx[0]);
+    cudaStream_t s0 = o0->c.stream;
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        for (size_t i = 0; i < g_batch.size(); ++i)
+            if (g_batch[i].key == key) {
+                std::rotate(g_batch.begin(), g_batch.begin() + (long)i, g_batch.begin() + (long)i + 1);
+                exec = g_batch[0].exec;
+                break;
+            }
     }
-    // 2. the RK steps of all shots interleaved, one graph launch per shot in turn:
-    //    every stream always has work queued, so the shots share the GPU
-    for (int s = 0; s < max_steps; ++s)
-        for (int i = 0; i < nshots; ++i) {
+    if (!exec) {
+        BatchGraph b;
+        b.key = key;
+        WW_CUDA_TRY(cudaGraphCreate(&b.graph, 0));
+        int st = WW_OK;
+        for (int i = 0; i < nshots && st == WW_OK; ++i) {
             Owned *o = owner(ctx[i]);
-            if (s < o->c.steps) WW_CUDA_TRY(cudaGraphLaunch(o->graphs[1][0].exec, o->c.stream));
+            st = add_batch_branch(b.graph, o, cvec[i], r[i], J[i], f[i]);
+            if (st != WW_OK) st = fail(st, "shot " + std::to_string(i) + ": " + ww_last_error());
+            else b.step_kernels += o->graphs[1][0].nkern;
         }
-    // 3. outputs and each shot's status
+        if (st == WW_OK) {
+            const cudaError_t e = cudaGraphInstantiate(&b.exec, b.graph, 0);
+            if (e != cudaSuccess) st = fail(WW_ERR_CUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+        }
+        if (st != WW_OK) {
+            destroy_batch(b);
+            return st;
+        }
+        exec = b.exec;
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        g_batch.insert(g_batch.begin(), b);
+        while (g_batch.size() > 4) {
+            destroy_batch(g_batch.back());
+            g_batch.pop_back();
+        }
+    }
+    // one launch on the first shot's stream, ordered after the other shots' streams
+    for (int i = 1; i < nshots; ++i) {
+        Owned *o = owner(ctx[i]);
+        WW_CUDA_TRY(cudaEventRecord(o->ev_join, o->c.stream));
+        WW_CUDA_TRY(cudaStreamWaitEvent(s0, o->ev_join, 0));
+    }
+    WW_CUDA_TRY(cudaGraphLaunch(exec, s0));
+    WW_CUDA_TRY(cudaEventRecord(o0->ev_join, s0));
+    for (int i = 1; i < nshots; ++i) WW_CUDA_TRY(cudaStreamWaitEvent(owner(ctx[i])->c.stream, o0->ev_join, 0));
     for (int i = 0; i < nshots; ++i) {
         Owned *o = owner(ctx[i]);
         Ctx *c = &o->c;
-        WW_TRY(launch_outputs(c, r[i], J[i], f[i], 1));
         c->stats.stages = 4 * c->steps;
-        c->stats.launches = (long long)o->prologue[1].nkern + (long long)c->steps * o->graphs[1][0].nkern + 2;
+        // prologue, steps x (step program + the loop counter), outputs
+        c->stats.launches = (long long)o->prologue[1].nkern + (long long)c->steps * (o->graphs[1][0].nkern + 1) + 2;
+        c->stats.device_bytes = (long long)c->dev_bytes;
         c->dtn_ready = false;
     }
     for (int i = 0; i < nshots; ++i) {
@@ -1171,6 +1451,77 @@ int shoot_jacobian_batch(ww_ctx *const *ctx, int nshots, const double *const *cv
         if (st != WW_OK) return fail(st, "shot " + std::to_string(i) + ": " + ww_last_error());
     }
     return WW_OK;
+}
+
+int ww_set_schedule(ww_ctx *ctx, const ww_schedule *s) {
+    if (!ctx || !s) return fail(WW_ERR_ARG, "ww_set_schedule: NULL argument");
+    return apply_schedule(owner(ctx), *s);
+}
+
+int ww_get_schedule(const ww_ctx *ctx, ww_schedule *s) {
+    if (!ctx || !s) return fail(WW_ERR_ARG, "ww_get_schedule: NULL argument");
+    *s = reinterpret_cast<const Owned *>(ctx)->c.sch;
+    return WW_OK;
+}
+
+int ww_autotune(ww_ctx *ctx, const double *cvec, int probe_steps, const char *cache_path, double *ms_per_step) {
+    if (!ctx || !cvec) return fail(WW_ERR_ARG, "ww_autotune: NULL argument");
+    if (probe_steps < 1) return fail(WW_ERR_ARG, "ww_autotune: probe_steps must be >= 1");
+    Owned *o = owner(ctx);
+    Ctx *c = &o->c;
+    if (c->stream == nullptr) return fail(WW_ERR_ARG, "ww_autotune: the legacy default stream runs no step graphs");
+    if (ms_per_step) *ms_per_step = 0.0;
+    const std::string key = tune_key(c);
+    ww_schedule best = c->sch;
+    if (cache_lookup(cache_path, key, &best)) return apply_schedule(o, best);
+    const bool timing = o->timing;
+    o->timing = false;
+    struct Restore {
+        Owned *o;
+        bool t;
+        ~Restore() { o->timing = t; }
+    } restore{o, timing};
+    WW_CUDA_TRY(cudaMemcpyAsync(o->cbuf, cvec, sizeof(double) * (c->n + 1), cudaMemcpyDeviceToDevice, c->stream));
+    double best_ms = INFINITY;
+    auto consider = [&](ww_schedule s) -> int {
+        double ms = INFINITY;
+        WW_TRY(probe_schedule(o, s, probe_steps, &ms));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = s;
+        }
+        return WW_OK;
+    };
+    // coordinate by coordinate from the default schedule
+    ww_schedule base = ww_schedule{1, 1, 64, 128, LU_NB};
+    if (c->precision == WW_MIXED) {
+        for (int v : {0, 1, 2}) {   // stage program: in line, overlapped with every-stage or alternate updates
+            ww_schedule s = base;
+            s.overlap = v > 0;
+            s.ns_every = v == 1;
+            WW_TRY(consider(s));
+        }
+        base = best;
+        for (int bn : {32, 128}) {
+            ww_schedule s = base;
+            s.corr_bn = bn;
+            WW_TRY(consider(s));
+        }
+        base = best;
+        ww_schedule s = base;
+        s.inv_bn = 64;
+        WW_TRY(consider(s));
+    } else {
+        for (int nb : {64, 32}) {
+            ww_schedule s = base;
+            s.lu_nb = nb;
+            WW_TRY(consider(s));
+        }
+    }
+    if (!std::isfinite(best_ms)) return fail(WW_ERR_NO_CONVERGENCE, "ww_autotune: no candidate schedule converged");
+    WW_TRY(apply_schedule(o, best));
+    if (ms_per_step) *ms_per_step = best_ms;
+    return cache_store(cache_path, key, best, best_ms);
 }
 
 int objective_and_grad(ww_ctx *ctx, const double *cvec, double *f, double *grad) {

@@ -107,6 +107,7 @@ struct Ctx {
     int verify_every;         // WW_MIXED: measure the true residual of every verify_every-th wide solve (0: off)
     int cur_stage;            // RK stage (0..3) whose work is being issued (phase timing)
     int ckpt_every;           // adjoint: checkpoint the base state every ckpt_every steps (0: keep every record)
+    ww_schedule sch;          // tile shapes and stage schedule (ww_set_schedule / ww_autotune)
     size_t dev_bytes;         // device memory this context allocated
     ww_stats stats;
     Mixed *mx;

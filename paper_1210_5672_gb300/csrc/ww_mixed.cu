@@ -42,9 +42,9 @@ int tc_slice_f64(cudaStream_t s, const double *src, int ld, int rows, int K, int
 int tc_gemm_f32acc(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 *B3, int M, int Nn, int K,
                    int out_mode, float *Cf, double *Cd, int ldc, double alpha, int *err, const int *skip = nullptr);
 int tc_gemm_2x2(cudaStream_t s, const __nv_bfloat16 *A2, const __nv_bfloat16 *B2, int M, int Nn, int K, int out_mode,
-                float *Cf, double *Cd, int ldc, double alpha, int *err, const int *skip = nullptr);
+                float *Cf, double *Cd, int ldc, double alpha, int *err, const int *skip, int bn);
 int tc_gemm_f32acc_sliced(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 *B3, int M, int Nn, int K,
-                          const TcOut &o, int *err, const int *skip);
+                          const TcOut &o, int *err, const int *skip, int bn);
 // ww_ozaki.cu
 int ozaki_digits(cudaStream_t s, const double *X, int ld, int rows, int K, int side, float diag_shift, int *emax,
                  double *scale, __nv_bfloat16 *dst, const int *skip);
@@ -259,7 +259,7 @@ int ns_step(Ctx *c, bool record, const int *skip) {
     o3.shift = 2.f;
     o3.s_col = m->Wslc;
     o3.dev_max = record ? m->nsres_last : nullptr;
-    WW_TRY(tc_gemm_f32acc_sliced(s, m->Aslc, m->XslcB, N, N, N, o3, m->err, skip));
+    WW_TRY(tc_gemm_f32acc_sliced(s, m->Aslc, m->XslcB, N, N, N, o3, m->err, skip, c->sch.inv_bn));
     // X <- X W: the FP32 X, its slices for the next update, and this stage's rows of X
     TcOut o4{};
     o4.mode = 4;
@@ -268,7 +268,7 @@ int ns_step(Ctx *c, bool record, const int *skip) {
     o4.s_col = m->XnB;
     o4.s_row = m->XnA;
     o4.s_row2 = m->Xrow[c->par];
-    WW_TRY(tc_gemm_f32acc_sliced(s, m->XslcA, m->Wslc, N, N, N, o4, m->err, skip));
+    WW_TRY(tc_gemm_f32acc_sliced(s, m->XslcA, m->Wslc, N, N, N, o4, m->err, skip, c->sch.inv_bn));
     if (record) WW_TRY(phase_mark(c, WW_PHASE_INVERSE, 1));
     // the product above still reads XslcA while it writes: its slices land in XnA / XnB
     // and move over afterwards (after a skipped update both already hold the same data)
@@ -424,7 +424,8 @@ int mixed_solve(Ctx *c, double *B, int ncols) {
     } else {
         k_prep_psi<<<ncols, 256, 0, s>>>(B, N, ncols, w.Psi, w.psis, m->Bslc);
         WW_CUDA_TRY(cudaGetLastError());
-        WW_TRY(tc_gemm_2x2(s, m->Xrow[q], m->Bslc, N, ncols, N, 1, nullptr, B, N, 1.0, m->err));
+        WW_TRY(tc_gemm_2x2(s, m->Xrow[q], m->Bslc, N, ncols, N, 1, nullptr, B, N, 1.0, m->err, nullptr,
+                           c->sch.corr_bn));
     }
     unsigned long long *cm_prev = w.colmax0, *cm = w.colmax;
     const int *done = w.done;
@@ -447,7 +448,8 @@ int mixed_solve(Ctx *c, double *B, int ncols) {
             // (2^-35 of the operands' maxima) leave the result within the 7-digit floor
             WW_TRY(ozaki_gemm(s, m->Kd[q], m->Ks[q], m->Rd, m->Rs, N, ncols, N, 1, nullptr, N, w.Psi, N, B, N, cm,
                               m->err, done, m->Bslc, it == 0 ? 5 : 7));
-            WW_TRY(tc_gemm_2x2(s, m->Xrow[q], m->Bslc, N, ncols, N, 2, nullptr, B, N, 1.0, m->err, done));
+            WW_TRY(tc_gemm_2x2(s, m->Xrow[q], m->Bslc, N, ncols, N, 2, nullptr, B, N, 1.0, m->err, done,
+                               c->sch.corr_bn));
         }
         // converged after this correction?
         k_converged<<<1, 512, 0, s>>>(cm, it > 0 ? cm_prev : nullptr, w.psis, narrow ? w.mscale : m->Rs, ncols,

@@ -381,7 +381,7 @@ int tc_gemm_f32acc(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 
 // of the iteration (the residuals themselves are FP64-accurate).  Reads slices
 // 0 and 1 of 2- or 3-slice operands.
 int tc_gemm_2x2(cudaStream_t s, const __nv_bfloat16 *A2, const __nv_bfloat16 *B2, int M, int Nn, int K, int out_mode,
-                float *Cf, double *Cd, int ldc, double alpha, int *err, const int *skip) {
+                float *Cf, double *Cd, int ldc, double alpha, int *err, const int *skip, int bn) {
     if (K % TC_BK != 0) return fail(WW_ERR_ARG, "tc_gemm: K must be a multiple of 64");
     Pairs P{};
     const int pp[3] = {1, 0, 0}, qq[3] = {0, 1, 0};   // smallest terms first
@@ -396,13 +396,16 @@ int tc_gemm_2x2(cudaStream_t s, const __nv_bfloat16 *A2, const __nv_bfloat16 *B2
     o.Cd = Cd;
     o.ldc = ldc;
     o.alpha = alpha;
-    // 64-wide column tiles: 2x the CTAs of 128-wide ones for the narrow (513-column) products
+    // column tile from the schedule: 64 (default) gives 2x the CTAs of 128-wide
+    // tiles for the narrow (513-column) products, 32 4x for a handful of columns
+    if (bn == 32) return launch_tc<32, 2, 2>(s, A2, B2, M, Nn, K, P, o, err, skip);
+    if (bn == 128) return launch_tc<128, 2, 2>(s, A2, B2, M, Nn, K, P, o, err, skip);
     return launch_tc<64, 2, 2>(s, A2, B2, M, Nn, K, P, o, err, skip);
 }
 
 // FP32-accurate product with a sliced output (modes 3 and 4 of TcOut), 3 + 3 slices
 int tc_gemm_f32acc_sliced(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 *B3, int M, int Nn, int K,
-                          const TcOut &o, int *err, const int *skip) {
+                          const TcOut &o, int *err, const int *skip, int bn) {
     if (K % TC_BK != 0) return fail(WW_ERR_ARG, "tc_gemm: K must be a multiple of 64");
     Pairs P{};
     const int pp[6] = {2, 1, 0, 1, 0, 0}, qq[6] = {0, 1, 2, 0, 1, 0};   // smallest terms first
@@ -411,7 +414,9 @@ int tc_gemm_f32acc_sliced(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bf
         P.p[i] = (unsigned char)pp[i];
         P.q[i] = (unsigned char)qq[i];
     }
-    // 32-wide K chunks (64-byte swizzle): 4 stages of 48 KB instead of 2 of 96 KB
+    // 32-wide K chunks (64-byte swizzle): 4 stages of 48 KB instead of 2 of 96 KB;
+    // 64-wide column tiles (schedule) double the CTAs of small products
+    if (bn == 64) return launch_tc<64, 3, 3, 32>(s, A3, B3, M, Nn, K, P, o, err, skip);
     return launch_tc<128, 3, 3, 32>(s, A3, B3, M, Nn, K, P, o, err, skip);
 }
 

@@ -325,7 +325,8 @@ def test_adjoint_checkpointed_matches_resident(ww, precision, N, h, tau, legacy)
     shrinks from 4 x 18 stage records to 4 x 4 plus 5 checkpoints."""
     import torch
     steps, K, n = 18, 4, 12
-    w = W.Workload("ckpt", N=N, n=n, steps=steps, h=h, tau=tau, amp=0.05, law="decay")
+    w = W.Workload("ckpt", N=N, n=n, steps=steps, h=h, tau=tau, amp=0.05,
+                   law="power" if N < 512 else "decay")
     c, _ = W.coefficients(w)
     c[0] = stable_T(N, steps, w.g, tau, h)
     out = []
@@ -357,14 +358,25 @@ def test_adjoint_checkpointed_matches_resident(ww, precision, N, h, tau, legacy)
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_batch_of_uneven_shots_matches_single_shots(ww, precision):
-    """shoot_jacobian_batch: independent shots of uneven size (the uneven-batch
-    recipe at N = 128..512, 8 steps of each shot's own dt) run concurrently give
-    bitwise the results of shoot_jacobian on each context; one shot is also
-    checked against the oracle."""
+    """shoot_jacobian_batch: independent shots of uneven size and step count
+    (the uneven-batch recipe at N = 128..512, 5..8 steps of each shot's own dt,
+    every other shot on a non-default schedule) run as ONE graph launch give
+    bitwise the results of shoot_jacobian on each context, also on a second
+    call (the cached batch graph); one shot is also checked against the
+    oracle."""
     shots = W.uneven_shots(n_shots=6, seed=5, step_cap=8, sizes=(128, 256, 512))
+    shots = [(W.shrink(w, steps=w.steps - (i % 4), name=w.name), c * np.r_[(w.steps - (i % 4)) / w.steps,
+                                                                         np.ones(w.n)])
+             for i, (w, c) in enumerate(shots)]
     assert len({w.N for w, _ in shots}) > 1 and len({w.n for w, _ in shots}) > 1
+    assert len({w.steps for w, _ in shots}) > 1
     ctxs = [ww.Context(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps, precision=precision) for w, _ in shots]
     try:
+        for i, ctx in enumerate(ctxs[1::2]):
+            if precision == ww.WW_MIXED:
+                ctx.set_schedule(**[dict(overlap=0), dict(corr_bn=32, inv_bn=64), dict(ns_every=0, corr_bn=128)][i % 3])
+            else:
+                ctx.set_schedule(lu_nb=32)
         cs = [dev(c) for _, c in shots]
         single = []
         for ctx, c in zip(ctxs, cs):
@@ -372,9 +384,16 @@ def test_batch_of_uneven_shots_matches_single_shots(ww, precision):
             ww.shoot_jacobian(ctx, c, r, J, f)
             single.append((r.cpu().numpy(), J.cpu().numpy(), f.item()))
         outs = [ctx.empty_outputs() for ctx in ctxs]
-        ww.shoot_jacobian_batch(ctxs, cs, [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
-        for (r0, J0, f0), (r, J, f) in zip(single, outs):
-            assert np.array_equal(r.cpu().numpy(), r0) and np.array_equal(J.cpu().numpy(), J0) and f.item() == f0
+        for _ in range(2):
+            for o in outs:
+                for t in o:
+                    t.fill_(float("nan"))
+            ww.shoot_jacobian_batch(ctxs, cs, [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
+            for (r0, J0, f0), (r, J, f) in zip(single, outs):
+                assert np.array_equal(r.cpu().numpy(), r0) and np.array_equal(J.cpu().numpy(), J0)
+                assert f.item() == f0
+        st = ctxs[0].stats()
+        assert st["stages"] == 4 * shots[0][0].steps and st["launches"] > 8 * st["stages"]
         with pytest.raises(ww.WWError) as ei:   # a context may appear once
             dup = [outs[0], outs[1], outs[0]]
             ww.shoot_jacobian_batch(ctxs[:2] + ctxs[:1], cs[:2] + cs[:1], [o[0] for o in dup],
@@ -390,6 +409,47 @@ def test_batch_of_uneven_shots_matches_single_shots(ww, precision):
     r, J, f = outs[i]
     assert rel(r.cpu().numpy(), r0) < TOL and abs(f.item() - f0) / f0 < TOL
     assert col_rel(J.cpu().numpy().T, J0) < TOL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_schedules_agree_and_autotune_caches(ww, precision, tmp_path):
+    """Every schedule computes the same Jacobian (to the refinement's level in
+    the mixed form: other tiles round the FP32 corrections differently, and
+    bitwise in the FP64 form across LU block sizes up to the LU's rounding);
+    ww_autotune picks one, appends it to its cache file, and takes it from
+    there without timing on the next call."""
+    w = W.Workload("sched", N=256, n=40, steps=6, h=0.8, amp=0.1)
+    c, _ = W.coefficients(w)
+    c[0] = stable_T(w.N, w.steps, h=w.h)
+    prob, _ = O.make_problem(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps)
+    r0, J0, f0 = O.shoot_jacobian(prob, c)
+    if precision == ww.WW_MIXED:
+        variants = [dict(), dict(overlap=0), dict(ns_every=0), dict(corr_bn=32), dict(corr_bn=128),
+                    dict(inv_bn=64)]
+    else:
+        variants = [dict(), dict(lu_nb=32)]
+    with ww.Context(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps, precision=precision) as ctx:
+        default = ctx.schedule()
+        for v in variants:
+            ctx.set_schedule(**{**default, **v})
+            r, J, f = ctx.empty_outputs()
+            ww.shoot_jacobian(ctx, dev(c), r, J, f)
+            assert rel(r.cpu().numpy(), r0) < TOL and abs(f.item() - f0) / f0 < TOL, v
+            assert col_rel(J.cpu().numpy().T, J0) < TOL, v
+        with pytest.raises(ww.WWError):
+            ctx.set_schedule(corr_bn=48)
+        cache = tmp_path / "tune.txt"
+        ms = ctx.autotune(dev(c), probe_steps=2, cache_path=str(cache))
+        chosen = ctx.schedule()
+        lines = cache.read_text().splitlines()
+        assert ms > 0 and len(lines) == 1
+        assert lines[0].split()[:3] == [str(w.N), str(w.n + 1), "mixed" if precision else "fp64"]
+        ctx.set_schedule(**default)
+        assert ctx.autotune(dev(c), probe_steps=2, cache_path=str(cache)) == 0.0   # from the cache
+        assert ctx.schedule() == chosen and len(cache.read_text().splitlines()) == 1
+        r, J, f = ctx.empty_outputs()
+        ww.shoot_jacobian(ctx, dev(c), r, J, f)
+        assert col_rel(J.cpu().numpy().T, J0) < TOL
 
 
 def test_column_split_engine_on_gpu(ww):
