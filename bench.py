@@ -556,15 +556,17 @@ BATCH_METRIC = "Jacobian columns/s over a batch of 32 uneven shots (N 256..4096,
 
 
 def run_batch(args):
-    """--mode batch: one step = shoot_jacobian_batch over the 32 seeded shots of
-    the uneven batch (each shot's step count capped at --batch-step-cap at its
-    own dt); the per-shot loop (shoot_jacobian on each context in turn) on the
-    same shots is timed beside it, and the two must agree bitwise."""
+    """--mode batch: one step = shoot_jacobian_batch (ONE graph launch) over the
+    32 seeded shots of the uneven batch, each shot's step count capped at
+    --batch-step-cap at its own dt, after the autotuner picked each shot's
+    schedule.  Beside it, timed once each: the per-shot loop of the same tuned
+    contexts (bitwise the batch's results) and the plain FP64 per-shot loop,
+    whose Jacobians the batch is compared with column by column."""
     import torch
     import paper_1210_5672_gb300 as ww
 
     rank, ws, local = dist_init()
-    shots = W.uneven_shots(n_shots=32, seed=rank, step_cap=args.batch_step_cap)
+    shots = W.uneven_shots(n_shots=32, seed=rank, step_cap=args.batch_step_cap or None)
     prec = ww.WW_MIXED if args.form == "mixed" else ww.WW_FP64
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
@@ -573,6 +575,14 @@ def run_batch(args):
     outs = [ctx.empty_outputs() for ctx in ctxs]
     cols = sum(w.n + 1 for w, _ in shots)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)
+    # the autotuner: each shot's schedule from timed probes (or the cache file)
+    cache = args.tune_cache or os.path.join(tempfile.mkdtemp(prefix="ww_tune_"), "schedules.txt")
+    t0 = time.perf_counter()
+    tuned = []
+    for (w, _), ctx, c in zip(shots, ctxs, cs):
+        ms = ctx.autotune(c, probe_steps=3, cache_path=cache)
+        tuned.append({"shot": w.name, "schedule": ctx.schedule(), "probe_ms_per_step": ms})
+    t_tune = time.perf_counter() - t0
 
     def batch():
         ww.shoot_jacobian_batch(ctxs, cs, [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
@@ -592,8 +602,9 @@ def run_batch(args):
     barrier(ws)
     clocks = clk.summary()
     t_step, value = replica_rate(sum(times) / len(times), ws, cols)
+    launches = sum(ctx.stats()["launches"] for ctx in ctxs) * args.steps
     got = [(o[0].cpu(), o[1].cpu(), o[2].cpu()) for o in outs]
-    # the per-shot loop on the same contexts
+    # the per-shot loop on the same (tuned) contexts
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for ctx, c, o in zip(ctxs, cs, outs):
@@ -602,27 +613,52 @@ def run_batch(args):
     t_loop = time.perf_counter() - t0
     same = all(torch.equal(a[0], o[0].cpu()) and torch.equal(a[1], o[1].cpu()) and torch.equal(a[2], o[2].cpu())
                for a, o in zip(got, outs))
-    launches = sum(ctx.stats()["launches"] for ctx in ctxs) * args.steps
     for ctx in ctxs:
         ctx.close()
+    # the plain FP64 per-shot loop (one context per shot, first call captures its graph)
+    fp64 = None
+    if prec == ww.WW_MIXED and not args.no_fp64_form:
+        worst, t64 = 0.0, 0.0
+        for (w, _), c, a in zip(shots, cs, got):
+            with ww.Context(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps, precision=ww.WW_FP64) as ctx:
+                r, J, f = ctx.empty_outputs()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ww.shoot_jacobian(ctx, c, r, J, f)
+                torch.cuda.synchronize()
+                t64 += time.perf_counter() - t0
+                Jd = J.cpu().numpy()
+            norms = np.linalg.norm(Jd, axis=1)
+            col = np.linalg.norm(a[1].numpy() - Jd, axis=1) / np.maximum(norms, 1e-4 * norms.max())
+            worst = max(worst, float(col.max()))
+        fp64 = {"seconds": t64, "columns_per_s": cols / t64, "batch_speedup": t64 / t_step,
+                "J_max_col_rel_batch_vs_fp64": worst,
+                "timing": "host wall clock, one shoot_jacobian per shot in turn (synchronised)"}
     if rank != 0:
         return None
-    return {
+    out = {
         "metric": BATCH_METRIC, "value": value, "unit": "Jacobian columns/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.form == "fp64" else "f64+f32/bf16-tensor",
         "data": "synthetic (seeded uneven-batch recipe)",
-        "config": {"workload": f"uneven batch of 32 shots, steps capped at {args.batch_step_cap} (each shot's own dt)",
+        "config": {"workload": ("uneven batch of 32 shots, steps capped at "
+                                f"{args.batch_step_cap} (each shot's own dt)") if args.batch_step_cap else
+                               "uneven batch of 32 shots at their full step counts",
                    "shots": [w.name + f"_steps{w.steps}" for w, _ in shots], "columns": cols, "form": args.form,
-                   "mode": "batch", "timing": "host wall clock around the batch call (it synchronises)",
+                   "mode": "batch", "timing": "host wall clock around the batch call (one graph launch; it "
+                                              "synchronises)",
                    "l2": "flushed between timed steps (512 MB write)"},
         "e2e": None,
         "roofline": None,
+        "autotune": {"seconds": t_tune, "cache": "per (N, n+1, form) text file", "choices": tuned},
         "per_shot_loop": {"seconds": t_loop, "columns_per_s": cols / t_loop, "batch_speedup": t_loop / t_step,
                           "bitwise_equal_to_batch": same},
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if fp64 is not None:
+        out["fp64_per_shot_loop"] = fp64
+    return out
 
 
 def cpu_baseline_gradient(w, c):
@@ -715,8 +751,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true",
                     help="jacobian mode, mixed form: leave out the timed plain-FP64 Jacobian of the comparison")
-    ap.add_argument("--batch-step-cap", type=int, default=64,
-                    help="batch mode: RK4 steps per shot at most (T scaled, each shot's dt kept)")
+    ap.add_argument("--batch-step-cap", type=int, default=32,
+                    help="batch mode: RK4 steps per shot at most (T scaled, each shot's dt kept); 0: no cap")
+    ap.add_argument("--tune-cache", default=None,
+                    help="batch mode: the autotuner's cache file (default: a fresh temporary file)")
     ap.add_argument("--mode", default="jacobian", choices=["jacobian", "gradient", "batch"],
                     help="gradient: objective_and_grad by the discrete adjoint (default workload "
                          "N1024_n256_steps2048_h0.05)")

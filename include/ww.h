@@ -274,6 +274,46 @@ int ww_set_checkpoint(ww_ctx *ctx, int every);
 #define WW_STATIC_MAX_RHS 64
 int dtn_apply_static(const double *eta, const double *phi, int N, int nrhs, double h, double *Gphi, void *stream);
 
+/* Time segments with adaptive meshes and a general explicit Runge-Kutta
+ * scheme (Sec. 2.2, Eq. (xi); the paper's production runs use DOP853).  The
+ * quarter period is split into segments; segment l covers the fraction
+ * theta_l of T/4 with `steps` uniform steps of the tableau (a, b) on the
+ * grid x_j = xi_l(alpha_j), alpha_j = 2 pi j / M_l, of the mesh of Eq. (xi):
+ * xi' = 1 - P[A sin^4(alpha/2)] (centre = 1, refined near x = pi) or
+ * 1 - P[A cos^4(alpha/2)] (centre = 0, near x = 0), A = 8 (1 - rho)/(5 + 3 rho),
+ * P the mean-free part (rho = min xi' / max xi'; rho = 1 is the uniform grid).
+ * On a mesh every x-derivative is d/dalpha over xi', the DtN carries Eq. (G)'s
+ * 1/|xi'|, P removes the mean over x and the residual weights are
+ * sqrt(xi'/M) (Eq. (f:phi)).  Between segments the state and every
+ * variational column are carried over by trigonometric interpolation of the
+ * old grid at xi_old^{-1}(xi_new(alpha'_j)). */
+typedef struct {
+    int steps;          /* uniform steps of the tableau in this segment (>= 1)             */
+    double theta;       /* fraction of T/4 the segment covers (the fractions sum to 1)      */
+    double rho;         /* mesh parameter, 0 < rho <= 1 (1: uniform)                        */
+    int centre;         /* 1: refined near x = pi, 0: near x = 0                            */
+    int stages;         /* stages s of the explicit tableau (1..16)                         */
+    const double *a;    /* HOST, s x s row-major, strictly lower triangular (copied)        */
+    const double *b;    /* HOST, s weights (copied)                                         */
+} ww_segment;
+
+/* ww_set_segment -- make the context (its N is the segment's M) a segment of
+ * a segmented shot: uploads the mesh tables and the tableau and allocates the
+ * stage right-hand sides (s (n + 2) 2N doubles).  NULL removes it.  N must be
+ * a multiple of 32.  The context's uniform RK4 entry points are unaffected. */
+int ww_set_segment(ww_ctx *ctx, const ww_segment *seg);
+
+/* shoot_jacobian_segments -- Sec. 2.2 and Sec. 3.3 on segments: r, J and f
+ * (device; r: M_last, J: M_last x (n+1) column-major, f: 1) of the segmented
+ * shot from c (device, n+1; c[0] = T) through the contexts ctx[0..nseg), one
+ * per segment in time order, each set up by ww_set_segment.  ctx[0] holds
+ * the initial data (its basis) and must be uniform (rho = 1); all contexts
+ * share n, g, tau, h and the form; the thetas sum to 1.  The variational
+ * columns (the T column forced by F(q)/T in every segment) ride through the
+ * respacing with the base state, so J is the derivative of the discrete map.
+ * All work runs on ctx[0]'s stream.  Errors as shoot_jacobian. */
+int shoot_jacobian_segments(ww_ctx *const *ctx, int nseg, const double *c, double *r, double *J, double *f);
+
 /* Self-tests of the dense products (diagnostics; no counterpart in the
  * paper).  C = A B for column-major FP64 device arrays A (M x K, ld M),
  * B (K x Nn, ld K) and the output C (M x Nn, ld M, overwritten), through

@@ -37,7 +37,7 @@ WW_FP64, WW_MIXED = 0, 1
 EXPORTS = ("ww_create", "ww_destroy", "ww_set_stream", "ww_get_stats", "ww_last_error", "ww_set_timing",
            "ww_get_timing", "dtn_setup", "dtn_apply", "shoot", "shoot_jacobian", "shoot_jacobian_host",
            "shoot_jacobian_batch", "objective_and_grad", "dtn_apply_static", "ww_set_verify", "ww_set_checkpoint", "ww_set_schedule", "ww_get_schedule",
-           "ww_autotune", "ww_selftest_f32gemm",
+           "ww_autotune", "ww_set_segment", "shoot_jacobian_segments", "ww_selftest_f32gemm",
            "ww_selftest_ozaki", "ww_selftest_dgemm", "ww_selftest_recip")
 STATIC_MAX_N, STATIC_MAX_RHS = 256, 64
 PHASES = ("assembly", "factor", "solve", "gapply", "colrhs", "gamma", "base", "gkernel", "inverse")
@@ -64,6 +64,11 @@ class Schedule(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class _Segment(C.Structure):
+    _fields_ = [("steps", C.c_int), ("theta", C.c_double), ("rho", C.c_double), ("centre", C.c_int),
+                ("stages", C.c_int), ("a", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double))]
 
 
 class Stats(C.Structure):
@@ -112,6 +117,8 @@ def lib():
             "ww_set_schedule": (I, [V, C.POINTER(Schedule)]),
             "ww_get_schedule": (I, [V, C.POINTER(Schedule)]),
             "ww_autotune": (I, [V, V, I, C.c_char_p, C.POINTER(D)]),
+            "ww_set_segment": (I, [V, C.POINTER(_Segment)]),
+            "shoot_jacobian_segments": (I, [C.POINTER(V), I, V, V, V, V]),
             "ww_selftest_f32gemm": (I, [V, V, I, I, I, V]),
             "ww_selftest_ozaki": (I, [V, V, I, I, I, V]),
             "ww_selftest_dgemm": (I, [V, V, I, I, I, V]),
@@ -319,6 +326,46 @@ def dtn_apply_static(eta, phi, h, Gphi, stream=None):
     _check(lib().dtn_apply_static(_dptr(eta, N, "eta"), _dptr(phi, N * nrhs, "phi"), int(N), int(nrhs),
                                   float(h), _dptr(Gphi, N * nrhs, "Gphi"), C.c_void_p(int(raw) if raw else None)))
     return Gphi
+
+
+def tableau(name: str):
+    """(a, b) of an explicit Runge-Kutta scheme: 'rk4' (classic) or 'dop853'
+    (Dormand and Prince's 8th-order scheme, the paper's integrator: its 12
+    stages and 8th-order weights, read from scipy's table of the published
+    coefficients)."""
+    if name == "rk4":
+        a = np.zeros((4, 4))
+        a[1, 0], a[2, 1], a[3, 2] = 0.5, 0.5, 1.0
+        return a, np.array([1.0, 2.0, 2.0, 1.0]) / 6.0
+    if name == "dop853":
+        from scipy.integrate._ivp import dop853_coefficients as d
+        s = d.N_STAGES
+        return np.array(d.A[:s, :s], dtype=np.float64), np.array(d.B, dtype=np.float64)
+    raise ValueError(f"unknown tableau {name!r}")
+
+
+def set_segment(ctx: Context, steps: int, theta: float, rho: float = 1.0, centre: int = 1, scheme="dop853"):
+    """Make ctx (N = the segment's M) a segment of a segmented shot (Sec. 2.2):
+    `steps` uniform steps of `scheme` ('rk4', 'dop853' or an (a, b) pair) over
+    the fraction theta of T/4 on the mesh of Eq. (xi) with parameter rho,
+    refined near x = pi (centre 1) or x = 0 (centre 0)."""
+    a, b = tableau(scheme) if isinstance(scheme, str) else scheme
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    b = np.ascontiguousarray(np.asarray(b, dtype=np.float64))
+    if a.shape != (b.size, b.size):
+        raise ValueError("tableau: a must be s x s and b of length s")
+    sg = _Segment(int(steps), float(theta), float(rho), int(centre), int(b.size),
+                  a.ctypes.data_as(C.POINTER(C.c_double)), b.ctypes.data_as(C.POINTER(C.c_double)))
+    _check(lib().ww_set_segment(ctx.handle, C.byref(sg)))
+
+
+def shoot_jacobian_segments(ctxs, c, r, J, f):
+    """The segmented shot through the contexts of its segments (in time order):
+    r (M_last,), J (n+1, M_last) and f (1,) CUDA float64; c (n+1,) on ctxs[0]'s device."""
+    last = ctxs[-1]
+    arr = (C.c_void_p * len(ctxs))(*[x.handle for x in ctxs])
+    _check(lib().shoot_jacobian_segments(arr, len(ctxs), _dptr(c, ctxs[0].n + 1, "c"), _dptr(r, last.N, "r"),
+                                         _dptr(J, last.N * (last.n + 1), "J"), _dptr(f, 1, "f")))
 
 
 def selftest(kind: str, A, B):

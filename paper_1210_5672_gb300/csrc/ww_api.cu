@@ -1045,6 +1045,10 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 int phase_mark(Ctx *c, int phase, int b) { return mark(c, c->cur_stage, phase, b); }
 
+Ctx *ctx_of(ww_ctx *h) { return &owner(h)->c; }
+
+int read_status(Ctx *c) { return check_status(c); }
+
 }  // namespace ww
 
 using namespace ww;
@@ -1236,6 +1240,7 @@ void ww_destroy(ww_ctx *ctx) {
         if (ev) cudaEventDestroy(ev);
     for (cudaEvent_t ev : o->pool) cudaEventDestroy(ev);
     if (o->c.mx) mixed_destroy(&o->c);
+    if (o->c.seg) segment_destroy(&o->c);
     if (o->c.stream) cudaStreamSynchronize(o->c.stream);
     if (o->side_stream) cudaStreamSynchronize(o->side_stream);
     for (void *p : o->allocs) cudaFree(p);

@@ -248,7 +248,7 @@ constexpr int FFT_STOCKHAM_MAXN = 2048;
 
 // not inlined: the kernels call it 5-7 times and one copy of its code keeps the
 // instruction cache warm
-__device__ __noinline__ void block_fft_stockham(cdf *s, int N, int logN, const cdf *__restrict__ twd,
+static __device__ __noinline__ void block_fft_stockham(cdf *s, int N, int logN, const cdf *__restrict__ twd,
                                                 bool inverse) {
     const int n4 = (logN % 3 == 0) ? 0 : (logN % 3 == 2 ? 1 : 2);   // radix-4 passes
     const int n8 = (logN - 2 * n4) / 3;                              // radix-8 passes

@@ -46,6 +46,7 @@ constexpr int LU_NB = 64;   // block size of the blocked LU / triangular solves
 // the per-problem context: all device buffers are allocated in ww_create
 // --------------------------------------------------------------------------
 struct Mixed;   // mixed-precision workspace (ww_mixed.cu)
+struct Seg;     // time-segment workspace: mesh, tableau, stage buffers (ww_segments.cu)
 
 struct Ctx {
     // problem
@@ -111,6 +112,7 @@ struct Ctx {
     size_t dev_bytes;         // device memory this context allocated
     ww_stats stats;
     Mixed *mx;
+    Seg *seg;                 // set by ww_set_segment (NULL: the uniform RK4 shot only)
     void *owner;              // the API-side object holding this context (phase timing)
 };
 
@@ -216,6 +218,12 @@ int launch_copy_cols(Ctx *c, const double *src, int ncols, double *dst);
 // phase timing (ww_api.cu): begin (b = 0) or end (b = 1) event of `phase` in
 // the current stage; a no-op unless a timed shot is being issued
 int phase_mark(Ctx *c, int phase, int b);
+// ww_api.cu: the context behind a handle; the device status word read back
+// (and the mixed form's statistics), as every entry point ends
+Ctx *ctx_of(ww_ctx *h);
+int read_status(Ctx *c);
+// ww_segments.cu: free a context's segment workspace
+void segment_destroy(Ctx *c);
 
 // assembly (ww_assemble.cu); c->trans selects A^T, G^T
 int launch_assemble(Ctx *c);

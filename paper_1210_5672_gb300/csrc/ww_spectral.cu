@@ -9,99 +9,11 @@
 // d/dx, H d/dx = |k| and the filter are real operators, two real signals a, b
 // are transformed together as one complex signal a + i b and come back as
 // (L a) + i (L b) -- no even/odd separation is needed anywhere.
-#include "ww_df.cuh"
-#include "ww_internal.cuh"
+#include "ww_ar.cuh"
 
 namespace ww {
 
 namespace {
-
-constexpr int FFT_THREADS = 256;
-
-__device__ __forceinline__ double2 times_ik(double2 z, int k) {   // (ik) z
-    return make_double2(-(double)k * z.y, (double)k * z.x);
-}
-
-// Arithmetic of the in-shared-memory transforms.  ArF64: IEEE double (the
-// WW_FP64 form).  ArDF: double-float (ww_df.cuh) for the WW_MIXED form, where
-// the FP64 pipe is the bottleneck; inputs, outputs and all pointwise algebra
-// stay FP64 in both.
-struct ArF64 {
-    using C = double2;
-    using R = double;   // real values of the pointwise algebra
-    using T = double;   // entries of the per-slot / per-point tables
-    static __device__ __forceinline__ C mk(double re, double im) { return make_double2(re, im); }
-    static __device__ __forceinline__ double2 get(C z) { return z; }
-    static __device__ __forceinline__ void fft(C *s, int N, int logN, const void *tw, bool inv) {
-        block_fft(s, N, logN, static_cast<const double2 *>(tw), inv);
-    }
-    // points of shared memory one transform needs
-    static __host__ __device__ __forceinline__ int cap(int N) { return N; }
-    static __device__ __forceinline__ C scalef(C z, float f) { return cscale(z, (double)f); }
-    static __device__ __forceinline__ C ikscale(C z, int k, float p2) { return cscale(times_ik(z, k), (double)p2); }
-    static __device__ __forceinline__ C add(C a, C b) { return cadd(a, b); }
-    static __device__ __forceinline__ C zero() { return make_double2(0.0, 0.0); }
-    // tables and real arithmetic
-    static __device__ __forceinline__ R tab(const void *t, int j) { return static_cast<const T *>(t)[j]; }
-    static __device__ __forceinline__ C scale_tab(C z, const void *t, int j) { return cscale(z, tab(t, j)); }
-    static __device__ __forceinline__ C re_only_tab(C z, const void *t, int j) { return make_double2(z.x * tab(t, j), 0.0); }
-    static __device__ __forceinline__ R from(double x) { return x; }
-    static __device__ __forceinline__ R rmul(R a, R b) { return a * b; }
-    static __device__ __forceinline__ R radd(R a, R b) { return a + b; }
-    static __device__ __forceinline__ R rsub(R a, R b) { return a - b; }
-    static __device__ __forceinline__ R rneg(R a) { return -a; }
-    static __device__ __forceinline__ C mkr(R re, R im) { return make_double2(re, im); }
-    static __device__ __forceinline__ R re(C z) { return z.x; }
-    static __device__ __forceinline__ R im(C z) { return z.y; }
-    static __device__ __forceinline__ C addr(C z, R a, R b) { return make_double2(z.x + a, z.y + b); }
-};
-
-struct ArDF {
-    using C = dfl::cdf;
-    using R = dfl::df;
-    using T = float2;   // double-float table entry (hi, lo)
-    static __device__ __forceinline__ C mk(double re, double im) { return dfl::from_d2(make_double2(re, im)); }
-    static __device__ __forceinline__ double2 get(C z) { return dfl::to_d2(z); }
-    static __device__ __forceinline__ void fft(C *s, int N, int logN, const void *tw, bool inv) {
-        if (N >= 16 && N <= dfl::FFT_STOCKHAM_MAXN)
-            dfl::block_fft_stockham(s, N, logN, static_cast<const dfl::cdf *>(tw), inv);
-        else
-            dfl::block_fft(s, N, logN, static_cast<const dfl::cdf *>(tw), inv);
-    }
-    // points of shared memory one transform needs (the Stockham passes pad)
-    static __host__ __device__ __forceinline__ int cap(int N) {
-        return (N >= 16 && N <= dfl::FFT_STOCKHAM_MAXN) ? N + N / 8 : N;
-    }
-    static __device__ __forceinline__ C scalef(C z, float f) { return dfl::cscalef(z, f); }
-    static __device__ __forceinline__ C ikscale(C z, int k, float p2) { return dfl::cscalef(dfl::times_ik(z, k), p2); }
-    static __device__ __forceinline__ C add(C a, C b) { return dfl::cadd(a, b); }
-    static __device__ __forceinline__ C zero() { return C{0.f, 0.f, 0.f, 0.f}; }
-    static __device__ __forceinline__ R tab(const void *t, int j) {
-        const float2 v = static_cast<const T *>(t)[j];
-        return R{v.x, v.y};
-    }
-    static __device__ __forceinline__ C scale_tab(C z, const void *t, int j) { return dfl::cscale(z, tab(t, j)); }
-    static __device__ __forceinline__ C re_only_tab(C z, const void *t, int j) {
-        return dfl::make(dfl::mul(dfl::re(z), tab(t, j)), dfl::df{0.f, 0.f});
-    }
-    static __device__ __forceinline__ R from(double x) { return dfl::from_double(x); }
-    static __device__ __forceinline__ R rmul(R a, R b) { return dfl::mul(a, b); }
-    static __device__ __forceinline__ R radd(R a, R b) { return dfl::add(a, b); }
-    static __device__ __forceinline__ R rsub(R a, R b) { return dfl::sub(a, b); }
-    static __device__ __forceinline__ R rneg(R a) { return R{-a.hi, -a.lo}; }
-    static __device__ __forceinline__ C mkr(R re, R im) { return dfl::make(re, im); }
-    static __device__ __forceinline__ R re(C z) { return dfl::re(z); }
-    static __device__ __forceinline__ R im(C z) { return dfl::im(z); }
-    static __device__ __forceinline__ C addr(C z, R a, R b) { return dfl::make(dfl::add(dfl::re(z), a), dfl::add(dfl::im(z), b)); }
-};
-
-// s <- s * (ik) / N (Nyquist zero)
-template <class AR>
-__device__ __forceinline__ void mul_deriv(typename AR::C *s, int N) {
-    const float invN = 1.0f / (float)N;   // exact: N is a power of two
-    for (int j = threadIdx.x; j < N; j += blockDim.x)
-        s[j] = (j == (N >> 1)) ? AR::zero() : AR::ikscale(s[j], wavenum(j, N), invN);
-}
 
 // ------------------------------------------------------------------------
 // base geometry: eta', phi', eta'' (= d/dx of eta'), curvature term

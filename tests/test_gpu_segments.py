@@ -1,0 +1,145 @@
+"""The segmented shot on the GPU (Sec. 2.2: time segments, the adaptive meshes
+of Eq. (xi), respacing, DOP853) against the oracle's segmented shot
+(orc_shoot_jacobian_segments), both forms, element by element at 1e-11
+relative (per-column measure with the 1e-4 floor of the other parity tests).
+
+Cases: one uniform RK4 segment (the same discrete map as the plain shot);
+three segments with meshes refined near x = 0 and a doubled grid, DOP853,
+finite depth and deep water with surface tension; and the segmented workload
+(four segments, rho down to 0.1, M doubling twice) shrunk 8x in M and 4x in
+steps so that the oracle finishes in seconds."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1210_5672_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def ww():
+    from paper_1210_5672_gb300 import build as B
+    B.build()
+    import paper_1210_5672_gb300 as m
+    return m
+
+
+def dev(a):
+    import torch
+    return torch.tensor(np.asarray(a, dtype=np.float64), device="cuda")
+
+
+def col_err(J, J0):
+    """max over columns of ||dJ_k|| / max(||J_k||, 1e-4 max_j ||J_j||); J, J0 are M x (n+1)."""
+    norms = np.linalg.norm(J0, axis=0)
+    return float(max(np.linalg.norm(J[:, k] - J0[:, k]) / max(norms[k], 1e-4 * norms.max())
+                     for k in range(J0.shape[1])))
+
+
+def gpu_segments(ww, segs, scheme, N0, n, c, precision, g=1.0, tau=0.0, h=1.0, basis=None):
+    """segs: [(M, steps, theta, rho, centre)]; one context per segment."""
+    import torch
+    ctxs = []
+    try:
+        for i, (M, steps, theta, rho, centre) in enumerate(segs):
+            ctx = ww.Context(M, n, g=g, tau=tau, h=h, steps=steps, precision=precision,
+                             basis=basis if i == 0 else None)
+            ctxs.append(ctx)
+            ww.set_segment(ctx, steps, theta, rho, centre, scheme)
+        last = ctxs[-1]
+        r = torch.empty(last.N, dtype=torch.float64, device="cuda")
+        J = torch.empty(n + 1, last.N, dtype=torch.float64, device="cuda")
+        f = torch.empty(1, dtype=torch.float64, device="cuda")
+        ww.shoot_jacobian_segments(ctxs, dev(c), r, J, f)
+        out = (r.cpu().numpy(), J.cpu().numpy().T.copy(), float(f.item()))
+        ww.shoot_jacobian_segments(ctxs, dev(c), r, J, f)     # a second call: captured programs, cached respacing
+        again = (r.cpu().numpy(), J.cpu().numpy().T.copy(), float(f.item()))
+        assert np.array_equal(out[0], again[0]) and np.array_equal(out[1], again[1]) and out[2] == again[2]
+        return out
+    finally:
+        for ctx in ctxs:
+            ctx.close()
+
+
+def check(ww, segs, scheme, n, c, precision, **kw):
+    r, J, f = gpu_segments(ww, segs, scheme, segs[0][0], n, c, precision, **kw)
+    prob, keep = O.make_problem(segs[0][0], n, g=kw.get("g", 1.0), tau=kw.get("tau", 0.0), h=kw.get("h", 1.0),
+                                basis=kw.get("basis"))
+    r0, J0, f0 = O.shoot_jacobian_segments(prob, segs, scheme, c)
+    er = np.linalg.norm(r - r0) / np.linalg.norm(r0)
+    ef = abs(f - f0) / abs(f0)
+    ej = col_err(J, J0)
+    print(f"\nsegments {[s[:4] for s in segs]} {scheme} precision={precision}: r {er:.2e} f {ef:.2e} J {ej:.2e}")
+    assert er < TOL and ef < TOL and ej < TOL
+    return r, J, f
+
+
+def test_one_uniform_rk4_segment_is_the_plain_shot(ww):
+    """The general-tableau path with the RK4 tableau on one uniform segment
+    computes the plain shot's discrete map (its stage sums round differently)."""
+    import torch
+    N, n, steps = 64, 8, 16
+    w = W.Workload("seg1", N=N, n=n, steps=steps, amp=0.05)
+    c, _ = W.coefficients(w)
+    for precision in (ww.WW_FP64, ww.WW_MIXED):
+        with ww.Context(N, n, steps=steps, precision=precision) as ctx:
+            r, J, f = ctx.empty_outputs()
+            ww.shoot_jacobian(ctx, dev(c), r, J, f)
+            plain = (r.cpu().numpy(), J.cpu().numpy().T.copy(), float(f.item()))
+        rs, Js, fs = gpu_segments(ww, [(N, steps, 1.0, 1.0, 1)], "rk4", N, n, c, precision)
+        assert np.linalg.norm(rs - plain[0]) / np.linalg.norm(plain[0]) < 1e-13
+        assert abs(fs - plain[2]) / plain[2] < 1e-13 and col_err(Js, plain[1]) < 1e-12
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("h,tau", [(1.0, 0.0), (math.inf, 0.1)])
+def test_three_segments_with_meshes_match_oracle(ww, precision, h, tau):
+    N, n = 64, 12
+    w = W.Workload("seg3", N=N, n=n, steps=1, h=h, tau=tau, amp=0.05)
+    c, _ = W.coefficients(w)
+    segs = [(N, 5, 0.375, 1.0, 0), (2 * N, 8, 0.375, 0.4, 0), (2 * N, 6, 0.25, 0.2, 0)]
+    check(ww, segs, "dop853", n, c, precision, h=h, tau=tau)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_segmented_workload_shrunk_matches_oracle(ww, precision):
+    """The segmented workload's structure, shrunk: M = 64, 128, 256, 256 (8x
+    fewer points), rho = 1, 0.4, 0.1, 0.1 refined near x = 0, DOP853 steps in
+    the workload's proportions (4x fewer), n = M_1 / 3 modes + T."""
+    wl = W.SEGMENTED
+    segs = [(M // 8, max(2, s // 4), th, rho, ctr) for (M, s, th, rho, ctr) in wl.meta["segments"]]
+    N, n = segs[0][0], segs[0][0] // 3
+    w = W.Workload("seg_wl", N=N, n=n, steps=1, h=wl.h, amp=0.05)
+    c, _ = W.coefficients(w)
+    check(ww, segs, wl.meta["tableau"], n, c, precision, h=wl.h)
+
+
+def test_paper_basis_and_bad_segments(ww):
+    """The paper's initial-data basis (Eq. init:stand: phi components) through
+    segments, and invalid segment lists refused before any work."""
+    import torch
+    N, n = 64, 6
+    x = 2 * np.pi * np.arange(N) / N
+    B = np.zeros((2 * N, n))
+    for k in range(1, n + 1):
+        B[(0 if k % 2 == 0 else N):(N if k % 2 == 0 else 2 * N), k - 1] = 2 * np.cos(k * x)
+    c = np.array([7.1, 0.03, 0.004, 0.002, -0.001, 0.0005, 0.0002])
+    segs = [(N, 6, 0.5, 1.0, 1), (2 * N, 6, 0.5, 0.5, 1)]
+    check(ww, segs, "dop853", n, c, 0, basis=B)
+    with ww.Context(N, n) as a, ww.Context(N, n) as b:
+        ww.set_segment(a, 4, 0.5, 0.5, 1)                 # a refined FIRST segment
+        ww.set_segment(b, 4, 0.5, 1.0, 1)
+        r = torch.empty(N, dtype=torch.float64, device="cuda")
+        J = torch.empty(n + 1, N, dtype=torch.float64, device="cuda")
+        f = torch.empty(1, dtype=torch.float64, device="cuda")
+        with pytest.raises(ww.WWError):
+            ww.shoot_jacobian_segments([a, b], dev(c), r, J, f)
+        ww.set_segment(a, 4, 0.5, 1.0, 1)
+        ww.set_segment(b, 4, 0.4, 1.0, 1)                 # thetas sum to 0.9
+        with pytest.raises(ww.WWError):
+            ww.shoot_jacobian_segments([a, b], dev(c), r, J, f)
