@@ -95,7 +95,8 @@ typedef struct {
     int ns_every;  /* WW_MIXED with overlap: move the approximate inverse to every
                       stage's A (1), or on even stages and when it drifted (0)         */
     int corr_bn;   /* WW_MIXED: column tile of the refinement corrections X R (32, 64, 128) */
-    int inv_bn;    /* WW_MIXED: column tile of the inverse update's products (64, 128)  */
+    int inv_bn;    /* WW_MIXED: column tile of the inverse update's products (64, 128,
+                      256; 256 needs N a multiple of 256)                               */
     int lu_nb;     /* WW_FP64: block size of the LU and triangular solves (32, 64)      */
 } ww_schedule;
 

@@ -955,9 +955,10 @@ int check_schedule(const Ctx *c, const ww_schedule &s) {
         return fail(WW_ERR_ARG, "ww_schedule: overlap and ns_every must be 0 or 1");
     if (s.corr_bn != 32 && s.corr_bn != 64 && s.corr_bn != 128)
         return fail(WW_ERR_ARG, "ww_schedule: corr_bn must be 32, 64 or 128");
-    if (s.inv_bn != 64 && s.inv_bn != 128) return fail(WW_ERR_ARG, "ww_schedule: inv_bn must be 64 or 128");
+    if (s.inv_bn != 64 && s.inv_bn != 128 && s.inv_bn != 256)
+        return fail(WW_ERR_ARG, "ww_schedule: inv_bn must be 64, 128 or 256");
+    if (s.inv_bn == 256 && c->N % 256 != 0) return fail(WW_ERR_ARG, "ww_schedule: inv_bn 256 needs N % 256 == 0");
     if (s.lu_nb != 32 && s.lu_nb != 64) return fail(WW_ERR_ARG, "ww_schedule: lu_nb must be 32 or 64");
-    (void)c;
     return WW_OK;
 }
 
@@ -1513,9 +1514,12 @@ int ww_autotune(ww_ctx *ctx, const double *cvec, int probe_steps, const char *ca
             WW_TRY(consider(s));
         }
         base = best;
-        ww_schedule s = base;
-        s.inv_bn = 64;
-        WW_TRY(consider(s));
+        for (int bn : {64, 256}) {
+            if (bn == 256 && c->N % 256 != 0) continue;
+            ww_schedule s = base;
+            s.inv_bn = bn;
+            WW_TRY(consider(s));
+        }
     } else {
         for (int nb : {64, 32}) {
             ww_schedule s = base;

@@ -77,95 +77,113 @@ __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha
 // Factor the kb x kb diagonal block at A(k0, k0) in place (no pivoting) and
 // write its inverse triangles Linv (unit lower) and Uinv (upper), kb x kb,
 // column-major.  Everything happens in shared memory (3 x 64 x 65 doubles,
-// dynamic): threads 0..127 build Linv row by row from the top while threads
-// 128..255 build Uinv row by row from the bottom.
+// dynamic), 512 threads.  One SM's FP64 pipe (2 FMA per clock: a warp-wide
+// FP64 instruction occupies it for 16 clocks) bounds the block, so the work is
+// laid out to keep warps full and divisions out of the loops:
+//  * the factorisation pivot by pivot: the column below the pivot is scaled by
+//    the pivot's reciprocal, then the trailing block takes its rank-1 update,
+//    its (rem x rem) entries spread contiguously over all threads;
+//  * the inverse triangles column by column, all 2 x 64 columns at once, four
+//    lanes of a warp per column: Linv(r, c) = -sum_{q=c}^{r-1} L(r,q) Linv(q,c)
+//    down the column, Uinv(r, c) = -sum_{q=r+1}^{c} U(r,q) Uinv(q,c) / U(r,r)
+//    up the column (the reciprocals of U's diagonal taken once), each sum split
+//    over the four lanes and combined by shuffles (no block-wide barrier
+//    between the rows of a column).
+// About 85k FMA for the factors and 88k for the inverses at kb = 64.
 constexpr int LD = LU_NB + 1;
 constexpr size_t LU_DIAG_SMEM = 3 * sizeof(double) * LU_NB * LD;
+constexpr int LU_DIAG_THREADS = 512;
 
-__global__ void __launch_bounds__(256) k_lu_diag(double *A, int lda, int k0, int kb, double *Linv, double *Uinv,
-                                                 int *status) {
+__global__ void __launch_bounds__(LU_DIAG_THREADS) k_lu_diag(double *A, int lda, int k0, int kb, double *Linv,
+                                                             double *Uinv, int *status) {
     extern __shared__ double dsm[];
     double(*a)[LD] = reinterpret_cast<double(*)[LD]>(dsm);                    // a[col][row]
     double(*li)[LD] = reinterpret_cast<double(*)[LD]>(dsm + LU_NB * LD);      // li[row][col]
     double(*ui)[LD] = reinterpret_cast<double(*)[LD]>(dsm + 2 * LU_NB * LD);  // ui[row][col]
+    __shared__ double rdiag[LU_NB];                                           // 1 / U(r, r)
     const int tid = threadIdx.x;
     for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
-        int r = idx % kb, c = idx / kb;
+        const int r = idx % kb, c = idx / kb;
         a[c][r] = A[(size_t)(k0 + c) * lda + k0 + r];
     }
     __syncthreads();
     for (int p = 0; p < kb; ++p) {
-        const double d = a[p][p];
         const int rem = kb - p - 1;
-        for (int idx = tid; idx < rem; idx += blockDim.x) a[p][p + 1 + idx] /= d;
+        if (tid < LU_NB) {   // two warps: one reciprocal each lane (divisions are dear on the FP64 pipe)
+            const double inv = 1.0 / a[p][p];
+            if (tid < rem) a[p][p + 1 + tid] *= inv;
+            if (tid == 0) rdiag[p] = inv;
+        }
         __syncthreads();
         for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
-            int r = p + 1 + idx % rem, c = p + 1 + idx / rem;
+            const int r = p + 1 + idx % rem, c = p + 1 + idx / rem;
             a[c][r] = fma(-a[p][r], a[c][p], a[c][r]);   // A(r,c) -= L(r,p) U(p,c)
         }
         __syncthreads();
     }
     int bad = 0;
     for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
-        int r = idx % kb, c = idx / kb;
-        double v = a[c][r];
+        const int r = idx % kb, c = idx / kb;
+        const double v = a[c][r];
         if (!isfinite(v)) bad = 1;
         A[(size_t)(k0 + c) * lda + k0 + r] = v;
     }
     if (__syncthreads_or(bad) && tid == 0) atomicOr(status, ST_NONFINITE);
-    // inverse triangles: step s builds row s of Linv and row kb-1-s of Uinv
-    for (int st = 0; st < kb; ++st) {
-        if (tid < 128) {
-            const int r = st;
-            for (int c = tid; c < kb; c += 128) {
-                double v;
-                if (c > r) {
-                    v = 0.0;
-                } else if (c == r) {
-                    v = 1.0;
-                } else {
-                    v = 0.0;   // Linv(r,c) = -sum_{q=c}^{r-1} L(r,q) Linv(q,c)
-                    for (int q = c; q < r; ++q) v = fma(-a[q][r], li[q][c], v);
-                }
-                li[r][c] = v;
-            }
-        } else {
-            const int r = kb - 1 - st, t = tid - 128;
-            for (int c = t; c < kb; c += 128) {
-                double v;
-                if (c < r) {
-                    v = 0.0;
-                } else if (c == r) {
-                    v = 1.0 / a[r][r];
-                } else {
-                    v = 0.0;   // Uinv(r,c) = -sum_{q=r+1}^{c} U(r,q) Uinv(q,c) / U(r,r)
-                    for (int q = r + 1; q <= c; ++q) v = fma(-a[q][r], ui[q][c], v);
-                    v /= a[r][r];
-                }
-                ui[r][c] = v;
-            }
+    // inverse triangles: warps 0..7 the columns of Linv, warps 8..15 those of Uinv,
+    // four lanes per column (8 columns per warp).  Every lane of a warp walks
+    // the same rows (uniform loop and shuffles), inactive lanes adding zeros.
+    const int lane4 = tid & 3, c = (tid >> 2) & 63;
+    const bool own = c < kb;
+    if (tid < 256) {
+        if (own && lane4 == 0)
+            for (int r = 0; r < kb; ++r) li[r][c] = r == c ? 1.0 : 0.0;
+        __syncwarp();
+        for (int r = 1; r < kb; ++r) {
+            const bool act = own && r > c;
+            double part = 0.0;
+            if (act)
+                for (int q = c + lane4; q < r; q += 4) part = fma(-a[q][r], li[q][c], part);
+            part += __shfl_xor_sync(0xffffffffu, part, 1);
+            part += __shfl_xor_sync(0xffffffffu, part, 2);
+            if (act && lane4 == 0) li[r][c] = part;
+            __syncwarp();
         }
-        __syncthreads();
+    } else {
+        if (own && lane4 == 0)
+            for (int r = 0; r < kb; ++r) ui[r][c] = r == c ? rdiag[c] : 0.0;
+        __syncwarp();
+        for (int r = kb - 2; r >= 0; --r) {
+            const bool act = own && r < c;
+            double part = 0.0;
+            if (act)
+                for (int q = r + 1 + lane4; q <= c; q += 4) part = fma(-a[q][r], ui[q][c], part);
+            part += __shfl_xor_sync(0xffffffffu, part, 1);
+            part += __shfl_xor_sync(0xffffffffu, part, 2);
+            if (act && lane4 == 0) ui[r][c] = part * rdiag[r];
+            __syncwarp();
+        }
     }
+    __syncthreads();
     for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
-        int r = idx % kb, c = idx / kb;
+        const int r = idx % kb, c = idx / kb;
         Linv[(size_t)c * kb + r] = li[r][c];
         Uinv[(size_t)c * kb + r] = ui[r][c];
     }
 }
 
-constexpr int AP_T = 16;   // columns (apply_left) / rows (apply_right) per block
+constexpr int AP_T = 16;   // rows per block (apply_right)
+constexpr int AP_L = 4;    // columns per block (apply_left): 129 blocks for 513 columns
 
 // B(kb x ncols, leading dim ldb) <- T * B, T kb x kb (in place).
-// One block per AP_T columns; each block reads its whole column slab before
-// writing it back.
+// One block per AP_L columns (enough blocks to fill the GPU at a few hundred
+// columns); each block reads its whole column slab before writing it back.
 __global__ void __launch_bounds__(256) k_apply_left(const double *__restrict__ T, int kb, double *B, int ldb,
                                                     int ncols) {
     __shared__ double t[LU_NB][LU_NB + 1];   // t[col][row]
-    __shared__ double b[AP_T][LU_NB + 1];    // b[col][row]
+    __shared__ double b[AP_L][LU_NB + 1];    // b[col][row]
     const int tid = threadIdx.x;
-    const int c0 = blockIdx.x * AP_T;
-    const int nc = min(AP_T, ncols - c0);
+    const int c0 = blockIdx.x * AP_L;
+    const int nc = min(AP_L, ncols - c0);
     for (int idx = tid; idx < kb * kb; idx += blockDim.x) t[idx / kb][idx % kb] = T[idx];
     for (int idx = tid; idx < kb * nc; idx += blockDim.x) {
         int r = idx % kb, c = idx / kb;
@@ -225,7 +243,7 @@ int lu_factor_fp64(Ctx *c) {
     for (int k0 = 0, blk = 0; k0 < N; k0 += nb, ++blk) {
         const int kb = min(nb, N - k0);
         double *Linv = c->Dinv + (size_t)blk * 2 * nb * nb, *Uinv = Linv + (size_t)nb * nb;
-        k_lu_diag<<<1, 256, LU_DIAG_SMEM, c->stream>>>(c->A, N, k0, kb, Linv, Uinv, c->status);
+        k_lu_diag<<<1, LU_DIAG_THREADS, LU_DIAG_SMEM, c->stream>>>(c->A, N, k0, kb, Linv, Uinv, c->status);
         WW_CUDA_TRY(cudaGetLastError());
         const int r = N - k0 - kb;
         if (r <= 0) continue;
@@ -233,7 +251,7 @@ int lu_factor_fp64(Ctx *c) {
         double *A12 = c->A + (size_t)(k0 + kb) * N + k0;    // kb x r
         double *A22 = c->A + (size_t)(k0 + kb) * N + k0 + kb;
         k_apply_right<<<(r + AP_T - 1) / AP_T, 256, 0, c->stream>>>(Uinv, kb, A21, N, r);   // L21 = A21 U11^-1
-        k_apply_left<<<(r + AP_T - 1) / AP_T, 256, 0, c->stream>>>(Linv, kb, A12, N, r);    // U12 = L11^-1 A12
+        k_apply_left<<<(r + AP_L - 1) / AP_L, 256, 0, c->stream>>>(Linv, kb, A12, N, r);    // U12 = L11^-1 A12
         WW_CUDA_TRY(cudaGetLastError());
         WW_TRY(dgemm(c->stream, r, r, kb, -1.0, A21, N, A12, N, 1.0, A22, N));
     }
@@ -243,7 +261,7 @@ int lu_factor_fp64(Ctx *c) {
 int lu_solve_fp64(Ctx *c, double *B, int ncols) {
     const int N = c->N, nb = c->nb;
     const int nblk = (N + nb - 1) / nb;
-    const unsigned gcols = (unsigned)((ncols + AP_T - 1) / AP_T);
+    const unsigned gcols = (unsigned)((ncols + AP_L - 1) / AP_L);
     // forward: L X = B
     for (int blk = 0; blk < nblk; ++blk) {
         const int k0 = blk * nb, kb = min(nb, N - k0);

@@ -200,7 +200,8 @@ __device__ __forceinline__ double filt36(int k, int N) {
 // spectral (ww_spectral.cu)
 int prepare_spectral(Ctx *c);                        // shared-memory limits of the FFT kernels
 int launch_base_geometry(Ctx *c, const double *eta, const double *phi, int with_phi);
-int launch_gamma(Ctx *c, int col0, int ncols);       // Gam = D M, Gout = 1/2 H D M (columns col0..)
+int launch_gamma(Ctx *c, int col0, int ncols, bool fp64 = false);   // Gam = D M, Gout = 1/2 H D M (columns col0..);
+                                                     // fp64: FP64 transforms also in the mixed form
 int launch_psi(Ctx *c);                              // M[:,1..nc] = phidot - phi_y etadot
 int launch_phi0(Ctx *c);                             // M[:,0] = phi of the base stage state
 int launch_base_rhs(Ctx *c, int stage, const double *cvec);

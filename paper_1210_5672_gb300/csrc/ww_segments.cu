@@ -15,9 +15,9 @@
 // segment: geometry and assembly on the mesh, the factorisation and the
 // multi-right-hand-side solves of the context's form (FP64 LU, or the mixed
 // form's inverse and refinement: they see only the assembled matrices), the
-// base and variational right-hand sides on the mesh, and the stage update of
-// the tableau, which keeps every stage's right-hand side ([S][n+2][2][N]
-// doubles).  One stage program is captured per context and replayed `steps`
+// base and variational right-hand sides on the mesh (FP64 transforms in both
+// forms), and the stage update of the tableau, which keeps every stage's
+// right-hand side ([S][n+2][2][N] doubles).  One stage program is captured per context and replayed `steps`
 // times; there is no second graph branch here.
 //
 // Respacing from segment a (M_a points) to b (M_b): the new values at
@@ -48,7 +48,6 @@ struct Seg {
     // xi'/N (weights of the x-mean), sqrt(xi'/N) (residual weights)
     double *xi = nullptr, *e = nullptr, *e1 = nullptr, *cxi = nullptr, *sxi = nullptr, *einv = nullptr,
            *pw = nullptr, *wts = nullptr;
-    float2 *einv_df = nullptr;              // 1/xi' in double-float (WW_MIXED column kernels)
     double *K = nullptr;                    // stage right-hand sides [S][NC][2][N]
     // respacing into this segment: the interpolation matrix (N x M_a) and the
     // previous segment it was built for
@@ -305,17 +304,29 @@ __global__ void __launch_bounds__(256) k_assemble_mesh(const double *__restrict_
 }
 
 // ---------------------------------------------------------------- the tableau's stage update
-// s holds the filtered right-hand side k_st of one column (physical values).
-// Before the last stage: K[st] = k_st and Ys = Y + dt sum_{q <= st} a[st+1][q] K[q];
-// at the last: Y = Ys = filter(Y + dt sum_q b[q] K[q]).
+// s holds the filtered right-hand side k_st of one column (physical values);
+// F (or NULL) an FP64 forcing added as F * fs (the T column's F(q)/T, added
+// in FP64 so that the column's small values keep their precision in the
+// double-float form).  Before the last stage: K[st] = k_st and
+// Ys = Y + dt sum_{q <= st} a[st+1][q] K[q]; at the last:
+// Y = Ys = filter(Y + dt sum_q b[q] K[q]).
 template <class AR>
 __device__ void tab_update(typename AR::C *s, int N, int logN, const void *__restrict__ tw,
                            const void *__restrict__ filt, int st, int S, const double *__restrict__ ta,
-                           const double *__restrict__ tb, double dt, double *Yc, double *Ysc, double *Kc, size_t ks) {
+                           const double *__restrict__ tb, double dt, double *Yc, double *Ysc, double *Kc, size_t ks,
+                           const double *__restrict__ F, double fs) {
+    auto kval = [&](int j) {
+        double2 k = AR::get(s[j]);
+        if (F) {
+            k.x += F[j] * fs;
+            k.y += F[N + j] * fs;
+        }
+        return k;
+    };
     if (st < S - 1) {
         const double *arow = ta + (size_t)(st + 1) * S;
         for (int j = threadIdx.x; j < N; j += blockDim.x) {
-            const double2 k = AR::get(s[j]);
+            const double2 k = kval(j);
             Kc[(size_t)st * ks + j] = k.x;
             Kc[(size_t)st * ks + N + j] = k.y;
             double ae = 0.0, ap = 0.0;
@@ -331,7 +342,7 @@ __device__ void tab_update(typename AR::C *s, int N, int logN, const void *__res
         return;
     }
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        const double2 k = AR::get(s[j]);
+        const double2 k = kval(j);
         double ae = 0.0, ap = 0.0;
         for (int q = 0; q < st; ++q) {
             ae += tb[q] * Kc[(size_t)q * ks + j];
@@ -416,7 +427,7 @@ __global__ void __launch_bounds__(SEG_THREADS) k_base_rhs_mesh(
     }
     const double dt = theta * (cvec[0] / 4.0) / steps;
     __syncthreads();
-    tab_update<ArF64>(s, N, logN, tw, filt, st, S, ta, tb, dt, Y, Ys, K, ks);
+    tab_update<ArF64>(s, N, logN, tw, filt, st, S, ta, tb, dt, Y, Ys, K, ks, nullptr, 0.0);
 }
 
 // ---------------------------------------------------------------- variational right-hand sides on the mesh
@@ -485,14 +496,11 @@ __global__ void __launch_bounds__(SEG_THREADS, 2) k_col_rhs_mesh(
     for (int j = threadIdx.x; j < N; j += blockDim.x) z[j] = AR::scale_tab(z[j], filt, j);
     __syncthreads();
     AR::fft(z, N, logN, tw, true);
-    if (c == 1) {   // d/dT column: + F(q) / T (every step's dt is proportional to T)
-        const double invT = 1.0 / cvec[0];
-        for (int j = threadIdx.x; j < N; j += blockDim.x)
-            z[j] = AR::addr(z[j], AR::from(Fbase[j] * invT), AR::from(Fbase[N + j] * invT));
-    }
+    // d/dT column: + F(q) / T (every step's dt is proportional to T), added in FP64
     const double dt = theta * (cvec[0] / 4.0) / steps;
     __syncthreads();
-    tab_update<AR>(z, N, logN, tw, filt, st, S, ta, tb, dt, Yc, Ysc, Kc, ks);
+    tab_update<AR>(z, N, logN, tw, filt, st, S, ta, tb, dt, Yc, Ysc, Kc, ks, c == 1 ? Fbase : nullptr,
+                   1.0 / cvec[0]);
 }
 
 // ---------------------------------------------------------------- respacing and outputs
@@ -609,32 +617,24 @@ int seg_stage(Ctx *c, Seg *g, int st, const double *cvec) {
     if (c->nc <= 0) return WW_OK;
     WW_TRY(launch_psi(c));
     WW_TRY(seg_solve(c, c->M + N, c->nc));
-    WW_TRY(launch_gamma(c, 1, c->nc));
+    WW_TRY(launch_gamma(c, 1, c->nc, true));
     WW_TRY(seg_apply_G(c, 1, c->nc));
-    const bool df = c->precision == WW_MIXED && c->twd != nullptr && c->uxd != nullptr;
-    if (df) {
-        const size_t sm = 2 * sizeof(dfl::cdf) * (size_t)ArDF::cap(c->N);
-        k_col_rhs_mesh<ArDF><<<c->nc, SEG_THREADS, sm, c->stream>>>(
-            c->Gout, c->uxd, c->vyd, c->w3d, g->einv_df, g->einv, c->vy, g->pw, c->Fbase, c->g, c->tau, c->N,
-            c->logN, c->twd, c->filt_df, c->Y, c->Ys, g->K, ks, st, g->S, g->d_a, g->d_b, cvec, g->theta, g->steps,
-            c->status);
-    } else {
-        const size_t sm = 2 * sizeof(double2) * N;
-        k_col_rhs_mesh<ArF64><<<c->nc, SEG_THREADS, sm, c->stream>>>(
-            c->Gout, c->ux, c->vy, c->w3, g->einv, g->einv, c->vy, g->pw, c->Fbase, c->g, c->tau, c->N, c->logN,
-            c->tw, c->filt_d, c->Y, c->Ys, g->K, ks, st, g->S, g->d_a, g->d_b, cvec, g->theta, g->steps, c->status);
-    }
+    // The variational transforms of a segment run in FP64 in both forms: on the
+    // mesh the double-float transforms' rounding, amplified in the small T
+    // column, reached ten times the oracle's own rounding sensitivity.
+    k_col_rhs_mesh<ArF64><<<c->nc, SEG_THREADS, 2 * sizeof(double2) * N, c->stream>>>(
+        c->Gout, c->ux, c->vy, c->w3, g->einv, g->einv, c->vy, g->pw, c->Fbase, c->g, c->tau, c->N, c->logN, c->tw,
+        c->filt_d, c->Y, c->Ys, g->K, ks, st, g->S, g->d_a, g->d_b, cvec, g->theta, g->steps, c->status);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
 
 int seg_prepare(Ctx *c) {
     const size_t N = (size_t)c->N;
-    const size_t two = 2 * sizeof(double2) * N, two_df = 2 * sizeof(dfl::cdf) * (size_t)ArDF::cap(c->N);
+    const size_t two = 2 * sizeof(double2) * N;
     WW_CUDA_TRY(cudaFuncSetAttribute(k_geom_mesh, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two));
     WW_CUDA_TRY(cudaFuncSetAttribute(k_base_rhs_mesh, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(two / 2)));
     WW_CUDA_TRY(cudaFuncSetAttribute(k_col_rhs_mesh<ArF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two));
-    WW_CUDA_TRY(cudaFuncSetAttribute(k_col_rhs_mesh<ArDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two_df));
     return WW_OK;
 }
 
@@ -756,7 +756,6 @@ extern "C" int ww_set_segment(ww_ctx *ctx, const ww_segment *sg) {
     SA(g->einv, N);
     SA(g->pw, N);
     SA(g->wts, N);
-    SA(g->einv_df, N);
     SA(g->K, (size_t)S * c->NC * 2 * N);
 #undef SA
     if (st != WW_OK) {
@@ -765,7 +764,6 @@ extern "C" int ww_set_segment(ww_ctx *ctx, const ww_segment *sg) {
     }
     // the mesh of Eq. (xi) at alpha_j (xi = alpha when rho = 1)
     std::vector<double> x(N), e(N), e1(N), cx(N), sx(N), ei(N), pw(N), wts(N);
-    std::vector<float2> eidf(N);
     const double two_pi = 6.283185307179586476925286766559;
     for (size_t j = 0; j < N; ++j) {
         const double al = two_pi * (double)j / (double)N;
@@ -781,7 +779,6 @@ extern "C" int ww_set_segment(ww_ctx *ctx, const ww_segment *sg) {
         ei[j] = 1.0 / e[j];
         pw[j] = e[j] / (double)N;
         wts[j] = std::sqrt(e[j] / (double)N);
-        eidf[j] = df_split(ei[j]);
     }
     cudaError_t ce = cudaMemcpy(g->d_a, g->a.data(), sizeof(double) * S * S, cudaMemcpyHostToDevice);
     const std::pair<double *, const std::vector<double> *> tabs[] = {{g->d_b, &g->b}, {g->xi, &x},  {g->e, &e},
@@ -790,7 +787,6 @@ extern "C" int ww_set_segment(ww_ctx *ctx, const ww_segment *sg) {
     for (const auto &t : tabs)
         if (ce == cudaSuccess)
             ce = cudaMemcpy(t.first, t.second->data(), sizeof(double) * t.second->size(), cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess) ce = cudaMemcpy(g->einv_df, eidf.data(), sizeof(float2) * N, cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) {
         free_seg(c, g);
         return fail(WW_ERR_CUDA, std::string("ww_set_segment upload: ") + cudaGetErrorString(ce));

@@ -433,11 +433,11 @@ int launch_base_geometry(Ctx *c, const double *eta, const double *phi, int with_
     return WW_OK;
 }
 
-int launch_gamma(Ctx *c, int col0, int ncols) {
+int launch_gamma(Ctx *c, int col0, int ncols, bool fp64) {
     if (col0 == 0 && ncols == 1 && cbase_ok(c)) return launch_cbase_gamma(c);
     size_t sm = 2 * sizeof(double2) * c->N;
     size_t off = (size_t)col0 * c->N;
-    if (use_df(c) && col0 >= 1)
+    if (use_df(c) && col0 >= 1 && !fp64)
         k_gamma<ArDF><<<(ncols + 1) / 2, FFT_THREADS, 2 * sizeof(double2) * (size_t)ArDF::cap(c->N), c->stream>>>(c->M + off, ncols, c->N, c->logN, c->twd,
                                                                       c->Gam + off, c->Gout + off);
     else

@@ -425,7 +425,7 @@ def test_schedules_agree_and_autotune_caches(ww, precision, tmp_path):
     r0, J0, f0 = O.shoot_jacobian(prob, c)
     if precision == ww.WW_MIXED:
         variants = [dict(), dict(overlap=0), dict(ns_every=0), dict(corr_bn=32), dict(corr_bn=128),
-                    dict(inv_bn=64)]
+                    dict(inv_bn=64), dict(inv_bn=256)]
     else:
         variants = [dict(), dict(lu_nb=32)]
     with ww.Context(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps, precision=precision) as ctx:

@@ -66,3 +66,20 @@ def test_segmented_recipe():
     assert not W.spacing_rule_ok(printed)
     assert W.spacing_rule_ok(printed[:2]) and not W.spacing_rule_ok(printed[1:3]) and W.spacing_rule_ok(printed[2:])
     assert w.name not in W.ALL
+
+
+def test_stored_oracle_samples_match_the_workload_recipe():
+    """The golden files of the full-length parity tests were written by the
+    oracle for exactly the workloads the recipe builds today (sizes, steps,
+    the seed actually used, T): a stale file would hold a test to the wrong
+    problem."""
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    for name, w in (("medium_n512_samples.json", W.MEDIUM), ("full_n2048_samples.json", W.LARGE)):
+        with open(os.path.join(here, name)) as fh:
+            g = json.load(fh)
+        c, seed = W.coefficients(w)
+        assert (g["N"], g["n"], g["steps"], g["seed"], g["workload"]) == (w.N, w.n, w.steps, seed, w.name), name
+        assert g["T"] == c[0], name
+        assert g["rows"] == list(range(0, w.N, 16)), name
