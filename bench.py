@@ -151,7 +151,9 @@ def flush_l2(buf):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
 # kernel, from one ncu capture of the current kernel on the N = 2048 workload
 # (summaries under profiles/); a kernel changed since its capture has none (null).
-TRAFFIC_BYTES = {("mixed", "N2048_n512_steps1024_h1", "k_ozaki"): 85.35e6}
+TRAFFIC_BYTES = {("mixed", "N2048_n512_steps1024_h1", "k_ozaki"): 85.35e6,
+                 # mean of the update's two launches (54.1 and 101.2 MB), profiles/k_tc_gemm_N2048.md
+                 ("mixed", "N2048_n512_steps1024_h1", "k_tc_gemm<128,3,3,32>"): 77.65e6}
 
 # slice pairs (p, q) with p + q <= 6 of the 7 x 7 integer digits: 28 bf16 GEMMs
 OZAKI_PAIRS = 28
@@ -426,7 +428,8 @@ GRAD_METRIC = "gradients/s of f(c) by the discrete adjoint at N=1024 (256 modes 
 def run_gradient(args):
     """--mode gradient: one step = one objective_and_grad (forward shot, then
     the transposed RK4 sweep) on a gradient workload (default: N = 1024, 256
-    modes + T, 2048 steps, h = 0.05), with the base trajectory checkpointed
+    modes + T, 2048 steps, deep water, tau = 0.1; the shallow one reaches the
+    bottom before T/4 and runs with --rk-steps 512), with the base trajectory checkpointed
     every --checkpoint steps (default 45 ~ sqrt(2048); 0 keeps every stage's
     record resident).  The other memory mode and the forward Jacobian route
     (shoot_jacobian, then J^T r) on the same problem are timed once beside it,
@@ -661,6 +664,101 @@ def run_batch(args):
     return out
 
 
+SEG_METRIC = "Jacobian columns/s of the segmented DOP853 shot on adaptive meshes (4 segments, M 512..2048)"
+
+
+def run_segments(args):
+    """--mode segments: one step = shoot_jacobian_segments of the segmented
+    workload (four time segments with rho = 1, 0.4, 0.1, 0.1 refined near
+    x = 0, M = 512, 1024, 2048, 2048, DOP853 steps 21, 48, 64, 53, 170 modes +
+    T), in the chosen form; the same shot in the other form is timed once
+    beside it, and the two compared column by column."""
+    import torch
+    import paper_1210_5672_gb300 as ww
+
+    rank, ws, local = dist_init()
+    wl = W.SEGMENTED
+    segs = wl.meta["segments"]
+    c, seed_used = W.coefficients(W.Workload("seg", N=segs[0][0], n=wl.n, steps=1, h=wl.h, amp=wl.amp,
+                                             seed=wl.seed + rank))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ct = torch.tensor(c, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)
+
+    def build(prec):
+        ctxs = []
+        for (M, steps, theta, rho, centre) in segs:
+            ctx = ww.Context(M, wl.n, g=wl.g, tau=wl.tau, h=wl.h, steps=steps, precision=prec)
+            ww.set_segment(ctx, steps, theta, rho, centre, wl.meta["tableau"])
+            ctxs.append(ctx)
+        stream = torch.cuda.Stream(dev)
+        ctxs[0].set_stream(stream)
+        M = segs[-1][0]
+        out = (torch.empty(M, dtype=torch.float64, device=dev), torch.empty(wl.n + 1, M, dtype=torch.float64, device=dev),
+               torch.empty(1, dtype=torch.float64, device=dev))
+        return ctxs, stream, out
+
+    def timed(ctxs, stream, out, k, warm):
+        for _ in range(warm):
+            ww.shoot_jacobian_segments(ctxs, ct, *out)
+        torch.cuda.synchronize()
+        ts, launches = [], 0
+        for _ in range(k):
+            flush_l2(flush)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ww.shoot_jacobian_segments(ctxs, ct, *out)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+            launches += ctxs[0].stats()["launches"]
+        return ts, launches
+
+    prec = ww.WW_MIXED if args.form == "mixed" else ww.WW_FP64
+    ctxs, stream, out = build(prec)
+    barrier(ws)
+    with ClockSampler(local) as clk:
+        times, gpu_launches = timed(ctxs, stream, out, args.steps, args.warmup)
+    barrier(ws)
+    clocks = clk.summary()
+    t_step, value = replica_rate(sum(times) / len(times), ws, wl.n + 1)
+    J1 = out[1].cpu().numpy()
+    for x in ctxs:
+        x.close()
+    other = None
+    if ws == 1:
+        oprec = ww.WW_FP64 if prec == ww.WW_MIXED else ww.WW_MIXED
+        octx, ostream, oout = build(oprec)
+        ot, _ = timed(octx, ostream, oout, 1, 1)
+        J2 = oout[1].cpu().numpy()
+        for x in octx:
+            x.close()
+        norms = np.linalg.norm(J2, axis=1)
+        col = np.linalg.norm(J1 - J2, axis=1) / np.maximum(norms, 1e-4 * norms.max())
+        other = {"form": "fp64" if oprec == ww.WW_FP64 else "mixed", "seconds": ot[0],
+                 "columns_per_s": (wl.n + 1) / ot[0], "J_max_col_rel_between_forms": float(col.max())}
+    if rank != 0:
+        return None
+    stages = sum(st for (_, st, _, _, _) in segs) * 12
+    return {
+        "metric": SEG_METRIC, "value": value, "unit": "Jacobian columns/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.form == "fp64" else "f64+f32/bf16-tensor",
+        "data": "synthetic (seeded PCG64 standing-wave coefficients, the segmented workload)",
+        "config": {"workload": wl.name, "segments": [list(x) for x in segs], "tableau": wl.meta["tableau"],
+                   "columns": wl.n + 1, "dtn_stages": stages, "h": wl.h, "form": args.form, "seed": seed_used,
+                   "mode": "segments", "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "flushed between timed steps (512 MB write)"},
+        "e2e": None,
+        "roofline": None,
+        "other_form": other,
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+    }
+
+
 def cpu_baseline_gradient(w, c):
     """The oracle's discrete adjoint on one RK4 step of the workload (the full
     run's dt), scaled to the full step count."""
@@ -747,7 +845,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--workload", default=None, choices=sorted(W.ALL),
-                    help=f"default {W.LARGE.name} (jacobian mode), {W.SHALLOW.name} (gradient mode)")
+                    help=f"default {W.LARGE.name} (jacobian mode), {W.DEEP_TENSION.name} (gradient mode)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true",
                     help="jacobian mode, mixed form: leave out the timed plain-FP64 Jacobian of the comparison")
@@ -755,22 +853,23 @@ def main():
                     help="batch mode: RK4 steps per shot at most (T scaled, each shot's dt kept); 0: no cap")
     ap.add_argument("--tune-cache", default=None,
                     help="batch mode: the autotuner's cache file (default: a fresh temporary file)")
-    ap.add_argument("--mode", default="jacobian", choices=["jacobian", "gradient", "batch"],
+    ap.add_argument("--mode", default="jacobian", choices=["jacobian", "gradient", "batch", "segments"],
                     help="gradient: objective_and_grad by the discrete adjoint (default workload "
-                         "N1024_n256_steps2048_h0.05)")
+                         "N1024_n256_steps2048_deep_tau0.1); batch: the uneven batch; segments: the "
+                         "segmented DOP853 workload")
     ap.add_argument("--checkpoint", type=int, default=45,
                     help="gradient mode: checkpoint the base state every K steps (0: every stage's record resident)")
     ap.add_argument("--rk-steps", type=int, default=0,
                     help="profiling only: override the workload's RK4 step count (not a bench number)")
     args = ap.parse_args()
     if args.workload is None:
-        args.workload = W.SHALLOW.name if args.mode == "gradient" else W.LARGE.name
+        args.workload = W.DEEP_TENSION.name if args.mode == "gradient" else W.LARGE.name
     if args.impl == "reference":
         out = run_reference(args)
     else:
         from paper_1210_5672_gb300 import build as B
         B.build()
-        out = {"gradient": run_gradient, "batch": run_batch}.get(args.mode, run_ours)(args)
+        out = {"gradient": run_gradient, "batch": run_batch, "segments": run_segments}.get(args.mode, run_ours)(args)
     if out is not None:
         # numpy scalars and arrays (should any reach the line) print as plain numbers / lists
         print(json.dumps(out, default=lambda v: v.tolist() if hasattr(v, "tolist") else str(v)), flush=True)

@@ -130,7 +130,7 @@ int ww_get_stats(const ww_ctx *ctx, ww_stats *out);
  * step program is captured again.  WW_ERR_ARG in WW_FP64 (no refinement). */
 int ww_set_verify(ww_ctx *ctx, int every);
 
-/* The context's schedule.  ww_create sets the default {1, 1, 64, 128, 64};
+/* The context's schedule.  ww_create sets the default {1, 0, 64, 128, 64};
  * ww_set_schedule validates the fields (WW_ERR_ARG) and drops the captured
  * step programs, which the next call captures again. */
 int ww_set_schedule(ww_ctx *ctx, const ww_schedule *s);

@@ -66,7 +66,7 @@ struct StepGraph {
     cudaGraphExec_t exec = nullptr;
     std::vector<std::pair<cudaGraphNode_t, int>> ev_nodes;   // node -> flat event slot
     int nkern = 0;                            // kernel nodes (launches per replay)
-    unsigned marked = 0;                      // phases with event nodes in this program
+    unsigned marked[4] = {};                  // per stage: phases with event nodes in this program
 };
 
 int count_kernel_nodes(cudaGraph_t g, int *out) {
@@ -98,7 +98,7 @@ struct Owned {
     bool capturing = false;
     bool in_shot = false;                     // the stages of a shot are being issued (marks allowed)
     int replay = 0;                           // RK step being launched
-    unsigned marked = 0;                      // phases recorded by the current step program
+    unsigned marked[4] = {};                  // per stage: phases recorded by the current step program
     cudaEvent_t placeholder[EV_PER_STEP] = {};
     std::vector<cudaEvent_t> pool;            // steps * EV_PER_STEP
     double ph_ms[NPH] = {};
@@ -137,7 +137,7 @@ void drop_graphs(Owned *o) {
 int mark(Ctx *c, int st, int phase, int b) {
     Owned *o = reinterpret_cast<Owned *>(c->owner);
     if (!o || !o->timing || !o->in_shot) return WW_OK;
-    o->marked |= 1u << phase;
+    o->marked[st & 3] |= 1u << phase;
     const int slot = (st * NPH + phase) * 2 + b;
     if (o->capturing) {
         // an "external" record becomes an event-record node of the captured graph
@@ -311,14 +311,14 @@ int build_step_graph(Owned *o, int with_cols) {
     cudaGraph_t g = nullptr;
     WW_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     o->capturing = true;
-    o->marked = 0;
+    for (unsigned &m : o->marked) m = 0;
     int st = WW_OK;
     if (overlapped(o, with_cols))
         st = capture_overlapped(o, o->cbuf);
     else
         for (int s = 0; s < 4 && st == WW_OK; ++s) st = run_stage(c, s, o->cbuf, with_cols);
     o->capturing = false;
-    sg.marked = o->marked;
+    for (int k = 0; k < 4; ++k) sg.marked[k] = o->marked[k];
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (st != WW_OK) {
         if (g) cudaGraphDestroy(g);
@@ -437,7 +437,7 @@ int collect_timing(Owned *o) {
     for (int rep = 0; rep < o->c.steps; ++rep)
         for (int st = 0; st < 4; ++st)
             for (int p = 0; p < NPH; ++p) {
-                if (!(o->marked & (1u << p))) continue;
+                if (!(o->marked[st] & (1u << p))) continue;   // a phase this stage does not run
                 const size_t base = (size_t)rep * EV_PER_STEP + (size_t)(st * NPH + p) * 2;
                 float ms = 0.f;
                 WW_CUDA_TRY(cudaEventElapsedTime(&ms, o->pool[base], o->pool[base + 1]));
@@ -481,7 +481,7 @@ int run_shot(Owned *o, const double *cvec, bool c_on_host, double *r, double *J,
                                 c_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
     WW_TRY(run_prologue(o, with_cols));
     if (o->timing) WW_TRY(ensure_timing_events(o));
-    o->marked = 0;
+    for (unsigned &m : o->marked) m = 0;
     struct InShot {
         Owned *o;
         InShot(Owned *o_) : o(o_) { o->in_shot = true; }
@@ -496,7 +496,7 @@ int run_shot(Owned *o, const double *cvec, bool c_on_host, double *r, double *J,
     } else {
         WW_TRY(build_step_graph(o, with_cols));
         StepGraph &sg = o->graphs[with_cols][o->timing ? 1 : 0];
-        o->marked = sg.marked;
+        for (int k = 0; k < 4; ++k) o->marked[k] = sg.marked[k];
         for (int s = 0; s < c->steps; ++s) {
             if (o->timing)
                 for (auto &ne : sg.ev_nodes)
@@ -1090,7 +1090,7 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
     c->precision = p->precision;
     c->refine_tol = p->refine_tol > 0.0 ? p->refine_tol : 1e-13;
     c->max_refine = p->max_refine > 0 ? p->max_refine : 4;
-    c->sch = ww_schedule{1, 1, 64, 128, LU_NB};
+    c->sch = ww_schedule{1, 0, 64, 128, LU_NB};
     c->nb = c->N < LU_NB ? c->N : LU_NB;
     {
         static std::atomic<unsigned long long> next_id{1};
@@ -1499,7 +1499,7 @@ int ww_autotune(ww_ctx *ctx, const double *cvec, int probe_steps, const char *ca
         return WW_OK;
     };
     // coordinate by coordinate from the default schedule
-    ww_schedule base = ww_schedule{1, 1, 64, 128, LU_NB};
+    ww_schedule base = ww_schedule{1, 0, 64, 128, LU_NB};
     if (c->precision == WW_MIXED) {
         for (int v : {0, 1, 2}) {   // stage program: in line, overlapped with every-stage or alternate updates
             ww_schedule s = base;

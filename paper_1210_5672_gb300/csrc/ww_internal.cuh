@@ -19,12 +19,16 @@ void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
 void fill_tables(int N, double *tw /* N */, double *cs /* 3N */);
 
+// on failure the runtime's last-error state is cleared too, so that a
+// non-sticky error does not resurface in the next call's launch checks
 #define WW_CUDA_TRY(expr)                                                        \
     do {                                                                         \
         cudaError_t e_ = (expr);                                                 \
-        if (e_ != cudaSuccess)                                                   \
+        if (e_ != cudaSuccess) {                                                 \
+            (void)cudaGetLastError();                                            \
             return ::ww::fail(WW_ERR_CUDA, std::string(#expr " : ") +            \
                                                cudaGetErrorString(e_));          \
+        }                                                                        \
     } while (0)
 
 #define WW_TRY(expr)                                                             \

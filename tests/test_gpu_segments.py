@@ -73,6 +73,7 @@ def gpu_segments(ww, segs, scheme, N0, n, c, precision, g=1.0, tau=0.0, h=1.0, b
 
 
 _SPREAD = {}
+_ORACLE = {}
 
 
 def check(ww, segs, scheme, n, c, precision, **kw):
@@ -84,8 +85,10 @@ def check(ww, segs, scheme, n, c, precision, **kw):
     r, J, f = gpu_segments(ww, segs, scheme, segs[0][0], n, c, precision, **kw)
     prob, keep = O.make_problem(segs[0][0], n, g=kw.get("g", 1.0), tau=kw.get("tau", 0.0), h=kw.get("h", 1.0),
                                 basis=kw.get("basis"))
-    r0, J0, f0 = O.shoot_jacobian_segments(prob, segs, scheme, c)
     key = (tuple(segs), scheme, n, tuple(c), tuple(sorted((k, str(v)) for k, v in kw.items())))
+    if key not in _ORACLE:
+        _ORACLE[key] = O.shoot_jacobian_segments(prob, segs, scheme, c)
+    r0, J0, f0 = _ORACLE[key]
     if key not in _SPREAD:
         cp = c.copy()
         cp[1] = np.nextafter(c[1], np.inf)
@@ -147,6 +150,19 @@ def test_segmented_workload_shrunk_matches_oracle(ww, precision):
     segs = [(M // 8, max(2, s // 4), th, rho, ctr) for (M, s, th, rho, ctr) in wl.meta["segments"]]
     N, n = segs[0][0], segs[0][0] // 3
     w = W.Workload("seg_wl", N=N, n=n, steps=1, h=wl.h, amp=0.05)
+    c, _ = W.coefficients(w)
+    check(ww, segs, wl.meta["tableau"], n, c, precision, h=wl.h)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_segmented_workload_quarter_size_at_its_amplitude(ww, precision):
+    """The segmented workload at a quarter of its points (M = 128, 256, 512,
+    512: the base transforms of the last segments take the 8-CTA cluster path)
+    with all of its DOP853 steps and its own amplitude c_1 = 0.2, 42 modes + T."""
+    wl = W.SEGMENTED
+    segs = [(M // 4, s, th, rho, ctr) for (M, s, th, rho, ctr) in wl.meta["segments"]]
+    N, n = segs[0][0], 42
+    w = W.Workload("seg_q", N=N, n=n, steps=1, h=wl.h, amp=wl.amp)
     c, _ = W.coefficients(w)
     check(ww, segs, wl.meta["tableau"], n, c, precision, h=wl.h)
 
