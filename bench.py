@@ -672,7 +672,9 @@ def run_segments(args):
     workload (four time segments with rho = 1, 0.4, 0.1, 0.1 refined near
     x = 0, M = 512, 1024, 2048, 2048, DOP853 steps 21, 48, 64, 53, 170 modes +
     T), in the chosen form; the same shot in the other form is timed once
-    beside it, and the two compared column by column."""
+    beside it, and the two compared column by column.  The line also carries
+    the timed form's own one-ulp sensitivity and the gradient of the same
+    shot by the discrete adjoint (time, agreement with J^T r)."""
     import torch
     import paper_1210_5672_gb300 as ww
 
@@ -725,6 +727,40 @@ def run_segments(args):
     clocks = clk.summary()
     t_step, value = replica_rate(sum(times) / len(times), ws, wl.n + 1)
     J1 = out[1].cpu().numpy()
+    jtr = J1 @ out[0].cpu().numpy()
+
+    # the gradient of the same segmented shot by its discrete adjoint, in the timed form
+    fg = torch.empty(1, dtype=torch.float64, device=dev)
+    gg = torch.empty(wl.n + 1, dtype=torch.float64, device=dev)
+    ww.objective_and_grad_segments(ctxs, ct, fg, gg)
+    torch.cuda.synchronize()
+    gts = []
+    for _ in range(2):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ww.objective_and_grad_segments(ctxs, ct, fg, gg)
+        e1.record(stream)
+        e1.synchronize()
+        gts.append(e0.elapsed_time(e1) / 1e3)
+    gvec = gg.cpu().numpy()
+    gradient = {"seconds": sum(gts) / len(gts), "gradients_per_s": len(gts) / sum(gts),
+                "rel_diff_vs_JT_r": float(np.linalg.norm(gvec - jtr) / np.linalg.norm(jtr)),
+                "adjoint_bytes": int(sum(x.stats()["adjoint_bytes"] for x in ctxs)),
+                "device_bytes": int(sum(x.stats()["device_bytes"] for x in ctxs)),
+                "what": "objective_and_grad_segments (discrete adjoint) in the timed form; J^T r from its Jacobian"}
+
+    def col_rel(A, B):
+        norms = np.linalg.norm(B, axis=1)
+        return np.linalg.norm(A - B, axis=1) / np.maximum(norms, 1e-4 * norms.max())
+
+    # the timed form's own rounding sensitivity: the same shot with c_1 one ulp up
+    cp = c.copy()
+    cp[1] = np.nextafter(c[1], np.inf)
+    ww.shoot_jacobian_segments(ctxs, torch.tensor(cp, dtype=torch.float64, device=dev), *out)
+    torch.cuda.synchronize()
+    spread = col_rel(out[1].cpu().numpy(), J1)
     for x in ctxs:
         x.close()
     other = None
@@ -735,10 +771,13 @@ def run_segments(args):
         J2 = oout[1].cpu().numpy()
         for x in octx:
             x.close()
-        norms = np.linalg.norm(J2, axis=1)
-        col = np.linalg.norm(J1 - J2, axis=1) / np.maximum(norms, 1e-4 * norms.max())
+        col = col_rel(J1, J2)
         other = {"form": "fp64" if oprec == ww.WW_FP64 else "mixed", "seconds": ot[0],
-                 "columns_per_s": (wl.n + 1) / ot[0], "J_max_col_rel_between_forms": float(col.max())}
+                 "columns_per_s": (wl.n + 1) / ot[0], "J_max_col_rel_between_forms": float(col.max()),
+                 "worst_column": int(col.argmax())}
+    sens = {"J_max_col_rel": float(spread.max()), "J_median_col_rel": float(np.median(spread)),
+            "worst_column": int(spread.argmax()),
+            "what": "the timed form's J moved by one ulp of c_1 (its own rounding sensitivity)"}
     if rank != 0:
         return None
     stages = sum(st for (_, st, _, _, _) in segs) * 12
@@ -754,6 +793,8 @@ def run_segments(args):
         "e2e": None,
         "roofline": None,
         "other_form": other,
+        "one_ulp_sensitivity": sens,
+        "gradient": gradient,
         "gpu_launches": gpu_launches,
         "clocks": clocks,
     }

@@ -315,6 +315,22 @@ int ww_set_segment(ww_ctx *ctx, const ww_segment *seg);
  * All work runs on ctx[0]'s stream.  Errors as shoot_jacobian. */
 int shoot_jacobian_segments(ww_ctx *const *ctx, int nseg, const double *c, double *r, double *J, double *f);
 
+/* objective_and_grad_segments -- Sec. 3.2's gradient (Eqs. (adj), (nabla:f))
+ * of the segmented shot of Sec. 2.2: f (device, 1 double) and its gradient
+ * with respect to c (device, n+1 doubles; grad[0] = d f / d T) by the
+ * DISCRETE adjoint of the map shoot_jacobian_segments differentiates.  A
+ * forward pass of the base state alone records every stage of every segment
+ * (6 M_l doubles a stage, allocated by the first call and kept with each
+ * segment's context); then, segment by segment from the last, the transposed
+ * steps of the segment's tableau run backward, each stage with its DtN
+ * assembled transposed on the segment's mesh (A^T, G^T) and factored in the
+ * context's form, and the adjoint state goes back through the transposed
+ * respacing between segments.  grad equals J^T r of shoot_jacobian_segments
+ * up to roundoff, for about two base shots instead of n + 1 columns.
+ * Contexts, stream and errors as shoot_jacobian_segments; WW_ERR_ALLOC if
+ * the records do not fit. */
+int objective_and_grad_segments(ww_ctx *const *ctx, int nseg, const double *c, double *f, double *grad);
+
 /* Self-tests of the dense products (diagnostics; no counterpart in the
  * paper).  C = A B for column-major FP64 device arrays A (M x K, ld M),
  * B (K x Nn, ld K) and the output C (M x Nn, ld M, overwritten), through

@@ -37,7 +37,8 @@ WW_FP64, WW_MIXED = 0, 1
 EXPORTS = ("ww_create", "ww_destroy", "ww_set_stream", "ww_get_stats", "ww_last_error", "ww_set_timing",
            "ww_get_timing", "dtn_setup", "dtn_apply", "shoot", "shoot_jacobian", "shoot_jacobian_host",
            "shoot_jacobian_batch", "objective_and_grad", "dtn_apply_static", "ww_set_verify", "ww_set_checkpoint", "ww_set_schedule", "ww_get_schedule",
-           "ww_autotune", "ww_set_segment", "shoot_jacobian_segments", "ww_selftest_f32gemm",
+           "ww_autotune", "ww_set_segment", "shoot_jacobian_segments", "objective_and_grad_segments",
+           "ww_selftest_f32gemm",
            "ww_selftest_ozaki", "ww_selftest_dgemm", "ww_selftest_recip")
 STATIC_MAX_N, STATIC_MAX_RHS = 256, 64
 PHASES = ("assembly", "factor", "solve", "gapply", "colrhs", "gamma", "base", "gkernel", "inverse")
@@ -119,6 +120,7 @@ def lib():
             "ww_autotune": (I, [V, V, I, C.c_char_p, C.POINTER(D)]),
             "ww_set_segment": (I, [V, C.POINTER(_Segment)]),
             "shoot_jacobian_segments": (I, [C.POINTER(V), I, V, V, V, V]),
+            "objective_and_grad_segments": (I, [C.POINTER(V), I, V, V, V]),
             "ww_selftest_f32gemm": (I, [V, V, I, I, I, V]),
             "ww_selftest_ozaki": (I, [V, V, I, I, I, V]),
             "ww_selftest_dgemm": (I, [V, V, I, I, I, V]),
@@ -366,6 +368,15 @@ def shoot_jacobian_segments(ctxs, c, r, J, f):
     arr = (C.c_void_p * len(ctxs))(*[x.handle for x in ctxs])
     _check(lib().shoot_jacobian_segments(arr, len(ctxs), _dptr(c, ctxs[0].n + 1, "c"), _dptr(r, last.N, "r"),
                                          _dptr(J, last.N * (last.n + 1), "J"), _dptr(f, 1, "f")))
+
+
+def objective_and_grad_segments(ctxs, c, f, grad):
+    """f (1,) and grad (n+1,) CUDA float64 of the segmented shot by its discrete
+    adjoint (grad[0] = d f / d T); contexts as shoot_jacobian_segments."""
+    arr = (C.c_void_p * len(ctxs))(*[x.handle for x in ctxs])
+    n = ctxs[0].n
+    _check(lib().objective_and_grad_segments(arr, len(ctxs), _dptr(c, n + 1, "c"), _dptr(f, 1, "f"),
+                                             _dptr(grad, n + 1, "grad")))
 
 
 def selftest(kind: str, A, B):

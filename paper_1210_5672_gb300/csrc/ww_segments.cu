@@ -27,6 +27,18 @@
 // D the Dirichlet kernel of the modes |k| < M_a/2 (the Nyquist mode enters
 // as f_{M/2} cos(M beta / 2)).  Respacing is linear, so the variational
 // columns stay the exact derivative of the discrete map.
+//
+// The gradient of f on segments (Sec. 3.2 with the meshes of Sec. 2.2) is
+// the discrete adjoint of this map: a forward pass of the base state alone
+// that records every stage, then, segment by segment from the last, the
+// transposed steps of the tableau (the filter, then the stages in reverse
+// order, each with kbar_i = dt (b_i mu + sum_{j>i} a_ji Ybar_j) and Ybar_i =
+// DF(Y_i)^T kbar_i) and, between segments, lambda <- R^T lambda.  On a mesh
+// the transposed stage reads every D_x = diag(1/xi') D_alpha as -D_x^T =
+// D_alpha diag(1/xi'), P (the xi'-weighted mean removed) as P^T v = v - xi'
+// (sum v) / M, and the DtN's diag(1/xi') on the right of its transpose:
+// G^T x = A^{-T} D (1/2 H - G^T) diag(1/xi') x, with A^T and G^T assembled
+// on the mesh and factored in the context's form.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -57,6 +69,19 @@ struct Seg {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int nkern = 0;
+    // objective_and_grad_segments (allocated by its first call): the records of
+    // the forward pass [steps][S][6][N] (eta, u, v, w3, F_eta, F_phi of each
+    // stage), the step counter that addresses them, the adjoint state lambda
+    // (2N), the adjoints of the stage right-hand sides [S][2][N], the stage's
+    // scratch and this segment's share of d f / d T; the base-only step
+    // program (with the records) and the transposed step program
+    double *rec = nullptr, *kb = nullptr, *lam = nullptr, *chi = nullptr, *etal = nullptr, *psil = nullptr,
+           *y = nullptr, *aeta = nullptr, *gT = nullptr;
+    int *rstep = nullptr;
+    cudaGraph_t fgraph = nullptr, bgraph = nullptr;
+    cudaGraphExec_t fexec = nullptr, bexec = nullptr;
+    int fkern = 0, bkern = 0;
+    size_t gbytes = 0;                      // of `bytes`, the gradient's workspace
     std::vector<void *> allocs;
     size_t bytes = 0;
 };
@@ -231,8 +256,9 @@ constexpr int MT = 32;
 //   2 K_ij = ea_j (c1 + c2).x + e_j (c1 - c2).y,   2 G_ij = e_i (c1 - c2).x - ea_i (c1 - c2).y - c0
 //   2 K_ji = -[ea_i (c1 + c2).x + e_i (c1 + c2).y], 2 G_ji = -e_j (c1 - c2).x + ea_j (c1 + c2).y + c0
 // c1 = cot((zeta_i - zeta_j)/2), c2 = cot((zeta_i - conj zeta_j)/2), c0 = cot((alpha_i - alpha_j)/2);
-// diagonal: zeta''/(2 zeta') with zeta'' = e1 + i eta_aa.
-template <bool DEEP>
+// diagonal: zeta''/(2 zeta') with zeta'' = e1 + i eta_aa.  TR: A^T and G^T
+// (the discrete adjoint's transposed DtN).
+template <bool DEEP, bool TR>
 __global__ void __launch_bounds__(256) k_assemble_mesh(const double *__restrict__ eta, const double *__restrict__ ea,
                                                        const double *__restrict__ eaa, const double *__restrict__ E,
                                                        const double *__restrict__ Einv, const double *__restrict__ xi,
@@ -286,6 +312,13 @@ __global__ void __launch_bounds__(256) k_assemble_mesh(const double *__restrict_
             gij = fma(-exi, bb, mi * cc) - c0;
             kji = -fma(exi, a, mi * d);
             gji = fma(exj, d, -(mj * cc)) + c0;
+        }
+        if (TR) {   // A^T and G^T: the (j, i) entries go where the (i, j) ones would
+            const double tk = kij, tg = gij;
+            kij = kji;
+            gij = gji;
+            kji = tk;
+            gji = tg;
         }
         const size_t idx = (size_t)j * N + i;
         A[idx] = fma(h, kij, i == j ? 0.5 : 0.0);
@@ -542,6 +575,235 @@ __global__ void k_outputs_mesh_J(const double *__restrict__ Y, const double *__r
     J[(size_t)c * N + i] = Y[(size_t)(c + 1) * 2 * N + N + i] * wts[i];
 }
 
+// ---------------------------------------------------------------- the discrete adjoint on a segment
+constexpr int SEG_REC = 6;   // doubles per point in a stage record
+
+// the record of stage `off` of the current step (off = -1: the last stage of
+// the step before), or NULL outside the records held
+__device__ __forceinline__ const double *seg_rec_at(const double *rec, const int *rstep, int off, int S, int steps,
+                                                    int N) {
+    const long idx = (long)(*rstep) * S + off;
+    if (idx < 0 || idx >= (long)steps * S) return nullptr;
+    return rec + (size_t)idx * SEG_REC * N;
+}
+
+// forward: the stage's surface (its eta before the stage) and fields into the
+// record of (step, st); the last stage advances the step counter
+__global__ void k_seg_record(const double *__restrict__ eta, const double *__restrict__ ux,
+                             const double *__restrict__ vy, const double *__restrict__ w3,
+                             const double *__restrict__ F, int N, int st, int S, int steps, double *rec, int *rstep) {
+    const int n = *rstep;
+    if (n >= 0 && n < steps) {
+        double *r = rec + ((size_t)n * S + st) * SEG_REC * N;
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            r[j] = eta[j];
+            r[N + j] = ux[j];
+            r[2 * N + j] = vy[j];
+            r[3 * N + j] = w3[j];
+            r[4 * N + j] = F[j];
+            r[5 * N + j] = F[N + j];
+        }
+    }
+    __syncthreads();   // every thread has read the counter
+    if (st == S - 1 && threadIdx.x == 0) *rstep = n + 1;
+}
+
+// lambda = (0, w^2 phi) on the last mesh (the gradient of f = sum (w_i phi_i)^2 / 2
+// with respect to the final state), f itself, in the order of k_outputs_mesh_r
+__global__ void k_seg_adj_init(const double *__restrict__ Y, const double *__restrict__ wts, int N, double *lam,
+                               double *f) {
+    __shared__ double red[33];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double w = wts[i], v = Y[N + i] * w;
+        lam[i] = 0.0;
+        lam[N + i] = w * v;
+        acc = fma(v, v, acc);
+    }
+    const double t = block_wsum(acc, red);
+    if (threadIdx.x == 0) *f = 0.5 * t;
+}
+
+// start of a transposed step: step -= 1; lambda <- Filt lambda (= mu);
+// kbar_st = dt b_st mu for every stage
+__global__ void __launch_bounds__(SEG_THREADS) k_seg_adj_begin(double *lam, double *kb, int N, int logN,
+                                                               const double2 *__restrict__ tw,
+                                                               const double *__restrict__ filt,
+                                                               const double *__restrict__ tb, int S,
+                                                               const double *__restrict__ cvec, double theta,
+                                                               int steps, int *rstep) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double2 *s = reinterpret_cast<double2 *>(smraw);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) s[j] = make_double2(lam[j], lam[N + j]);
+    __syncthreads();
+    block_fft(s, N, logN, tw, false);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) s[j] = cscale(s[j], filt[j]);
+    __syncthreads();
+    block_fft(s, N, logN, tw, true);
+    const double dt = theta * (cvec[0] / 4.0) / steps;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const double2 v = s[j];
+        lam[j] = v.x;
+        lam[N + j] = v.y;
+        for (int st = 0; st < S; ++st) {
+            const double w = dt * tb[st];
+            kb[(size_t)st * 2 * N + j] = w * v.x;
+            kb[(size_t)st * 2 * N + N + j] = w * v.y;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *rstep = *rstep - 1;
+}
+
+// the recorded surface of stage `off` of the current step
+__global__ void k_seg_adj_fetch(const double *__restrict__ rec, const int *rstep, int off, int S, int steps, int N,
+                                double *eta) {
+    const double *r = seg_rec_at(rec, rstep, off, S, steps, N);
+    if (!r) return;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) eta[j] = r[j];
+}
+
+// i k / N on FFT slot j (Nyquist zeroed): the derivative in alpha, normalised
+__device__ __forceinline__ double2 deriv_slot(double2 v, int j, int N) {
+    if (2 * j == N) return make_double2(0.0, 0.0);
+    const double k = (double)wavenum(j, N) / N;
+    return make_double2(-k * v.y, k * v.x);
+}
+
+// the stage's local adjoint terms on the mesh (one block):
+//   et = Filt kbar_eta, pt = P^T Filt kbar_phi, chis = (et + v pt) / xi',
+//   etal = u D_a(et/xi') + u v D_a(pt/xi') - g pt + tau D_a(w3 D_a(pt/xi') / xi'),
+//   psil = D_a(u pt / xi'), and d f / d T += kbar . F / T
+__global__ void __launch_bounds__(SEG_THREADS) k_seg_adj_local(
+    const double *__restrict__ kb, const double *__restrict__ rec, const int *rstep, int st, int S, int steps, int N,
+    int logN, const double2 *__restrict__ tw, const double *__restrict__ filt, const double *__restrict__ e,
+    const double *__restrict__ einv, double g, double tau, const double *__restrict__ cvec, double *chis,
+    double *etal, double *psil, double *gT) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double red[33];
+    double2 *s0 = reinterpret_cast<double2 *>(smraw), *s1 = s0 + N;
+    const double *r = seg_rec_at(rec, rstep, st, S, steps, N);
+    if (!r) return;
+    const double *ux = r + N, *vy = r + 2 * N, *w3 = r + 3 * N, *F = r + 4 * N;
+    double fd = 0.0;
+    for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) fd = fma(kb[j], F[j], fd);
+    fd = block_wsum(fd, red);
+    if (threadIdx.x == 0) *gT += fd / cvec[0];
+    for (int j = threadIdx.x; j < N; j += blockDim.x) s0[j] = make_double2(kb[j], kb[N + j]);
+    __syncthreads();
+    block_fft(s0, N, logN, tw, false);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) s0[j] = cscale(s0[j], filt[j]);
+    __syncthreads();
+    block_fft(s0, N, logN, tw, true);
+    double part = 0.0;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) part += s0[j].y;
+    const double mean = block_wsum(part, red) / N;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const double et = s0[j].x, pt = s0[j].y - e[j] * mean, ei = einv[j];
+        chis[j] = fma(vy[j], pt, et) * ei;
+        s0[j] = make_double2(et * ei, pt * ei);
+        s1[j] = make_double2(pt, 0.0);
+    }
+    __syncthreads();
+    block_fft(s0, N, logN, tw, false);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) s0[j] = deriv_slot(s0[j], j, N);
+    __syncthreads();
+    block_fft(s0, N, logN, tw, true);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const double det = s0[j].x, dpt = s0[j].y, u = ux[j], v = vy[j], pt = s1[j].x, ei = einv[j];
+        etal[j] = u * det + u * v * dpt - g * pt;
+        s0[j] = make_double2(u * pt * ei, w3[j] * dpt * ei);
+    }
+    __syncthreads();
+    block_fft(s0, N, logN, tw, false);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) s0[j] = deriv_slot(s0[j], j, N);
+    __syncthreads();
+    block_fft(s0, N, logN, tw, true);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        psil[j] = s0[j].x;
+        etal[j] += tau * s0[j].y;
+    }
+}
+
+// M[:, 0] = D (1/2 H chis - y), y = G^T chis, from one transform of chis + i y:
+// the real multiplier |k|/2 - k (even part |k|/2, the symbol of D H / 2, on
+// chis; odd part -k, i.e. -ik = -D, on y), Nyquist zeroed
+__global__ void __launch_bounds__(SEG_THREADS) k_seg_adj_dtn(const double *__restrict__ chis,
+                                                             const double *__restrict__ y, int N, int logN,
+                                                             const double2 *__restrict__ tw, double *M) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double2 *s = reinterpret_cast<double2 *>(smraw);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) s[j] = make_double2(chis[j], y[j]);
+    __syncthreads();
+    block_fft(s, N, logN, tw, false);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const double k = (double)wavenum(j, N);
+        s[j] = cscale(s[j], 2 * j == N ? 0.0 : (0.5 * fabs(k) - k) / N);
+    }
+    __syncthreads();
+    block_fft(s, N, logN, tw, true);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) M[j] = s[j].x;
+}
+
+// pb = A^{-T}(...) + psil, eb = etal - v pb; lambda += (eb, pb);
+// kbar_q += dt a[st][q] (eb, pb) for the stages q < st
+__global__ void k_seg_adj_update(const double *__restrict__ M, const double *__restrict__ psil,
+                                 const double *__restrict__ etal, const double *__restrict__ rec, const int *rstep,
+                                 int st, int S, int steps, int N, const double *__restrict__ ta, double theta,
+                                 const double *__restrict__ cvec, double *lam, double *kb) {
+    const double *r = seg_rec_at(rec, rstep, st, S, steps, N);
+    if (!r) return;
+    const double *vy = r + 2 * N;
+    const double dt = theta * (cvec[0] / 4.0) / steps;
+    const double *arow = ta + (size_t)st * S;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+        const double pb = M[j] + psil[j];
+        const double eb = fma(-vy[j], pb, etal[j]);
+        lam[j] += eb;
+        lam[N + j] += pb;
+        for (int q = 0; q < st; ++q) {
+            const double a = arow[q];
+            if (a == 0.0) continue;
+            const double w = dt * a;
+            kb[(size_t)q * 2 * N + j] += w * eb;
+            kb[(size_t)q * 2 * N + N + j] += w * pb;
+        }
+    }
+}
+
+// lambda_a = R^T lambda_b for both halves (R: Mb x Ma column-major), one block per row of R^T
+__global__ void k_seg_respace_T(const double *__restrict__ R, int Mb, int Ma, const double *__restrict__ lb,
+                                double *la) {
+    __shared__ double red[33];
+    const int l = blockIdx.x;
+    const double *col = R + (size_t)l * Mb;
+    double ae = 0.0, ap = 0.0;
+    for (int j = threadIdx.x; j < Mb; j += blockDim.x) {
+        ae = fma(col[j], lb[j], ae);
+        ap = fma(col[j], lb[Mb + j], ap);
+    }
+    ae = block_wsum(ae, red);
+    ap = block_wsum(ap, red);
+    if (threadIdx.x == 0) {
+        la[l] = ae;
+        la[Ma + l] = ap;
+    }
+}
+
+// grad[0] += this segment's d f / d T
+__global__ void k_seg_add(double *dst, const double *__restrict__ src) { *dst += *src; }
+
+// grad[k] = basis_k . lambda(0) for k = 1..n, one block per entry
+__global__ void k_seg_grad(const double *__restrict__ basis, const double *__restrict__ lam, int N, double *grad) {
+    __shared__ double red[33];
+    const int k = blockIdx.x + 1;
+    const double *b = basis + (size_t)(k - 1) * 2 * N;
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) acc = fma(b[j], lam[j], acc);
+    acc = block_wsum(acc, red);
+    if (threadIdx.x == 0) grad[k] = acc;
+}
+
 template <typename T>
 int seg_alloc(Ctx *c, Seg *g, T **p, size_t n) {
     const size_t bytes = sizeof(T) * (n ? n : 1);
@@ -556,6 +818,10 @@ int seg_alloc(Ctx *c, Seg *g, T **p, size_t n) {
 void free_seg(Ctx *c, Seg *g) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->fexec) cudaGraphExecDestroy(g->fexec);
+    if (g->fgraph) cudaGraphDestroy(g->fgraph);
+    if (g->bexec) cudaGraphExecDestroy(g->bexec);
+    if (g->bgraph) cudaGraphDestroy(g->bgraph);
     for (void *p : g->allocs) cudaFree(p);
     c->dev_bytes -= g->bytes;
     delete g;
@@ -581,25 +847,35 @@ int seg_apply_G(Ctx *c, int col0, int ncols) {
                  c->Gout + (size_t)col0 * c->N, c->N);
 }
 
-int seg_geometry(Ctx *c, Seg *g) {
+// the geometry of the surface eta_in (and phi_x of phi_in); the stage state's by default
+int seg_geometry(Ctx *c, Seg *g, const double *eta_in = nullptr, const double *phi_in = nullptr,
+                 bool with_curv = true) {
     const size_t sm = 2 * sizeof(double2) * (size_t)c->N;
-    k_geom_mesh<<<1, SEG_THREADS, sm, c->stream>>>(c->Ys, c->Ys + c->N, c->N, c->logN, c->deep ? 1 : 0,
-                                                  c->tau != 0.0 ? 1 : 0, c->tw, g->einv, c->eta, c->eta_x,
-                                                  c->eta_xx, c->phi_s, c->curv, c->E, c->Einv, c->status);
+    if (!eta_in) {
+        eta_in = c->Ys;
+        phi_in = c->Ys + c->N;
+    }
+    k_geom_mesh<<<1, SEG_THREADS, sm, c->stream>>>(eta_in, phi_in, c->N, c->logN, c->deep ? 1 : 0,
+                                                  with_curv && c->tau != 0.0 ? 1 : 0, c->tw, g->einv, c->eta,
+                                                  c->eta_x, c->eta_xx, c->phi_s, c->curv, c->E, c->Einv, c->status);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
 
+// A = 1/2 I + K and G on the mesh, or A^T and G^T while c->trans is set
 int seg_assemble(Ctx *c, Seg *g) {
     const int T = c->N / MT;
-    auto kern = c->deep ? k_assemble_mesh<true> : k_assemble_mesh<false>;
+    auto kern = c->deep ? (c->trans ? k_assemble_mesh<true, true> : k_assemble_mesh<true, false>)
+                        : (c->trans ? k_assemble_mesh<false, true> : k_assemble_mesh<false, false>);
     kern<<<T * (T + 1) / 2, 256, 0, c->stream>>>(c->eta, c->eta_x, c->eta_xx, c->E, c->Einv, g->xi, g->e, g->e1,
                                                  g->cxi, g->sxi, c->cs + 2 * c->N, c->N, c->A, c->G);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
 }
 
-int seg_stage(Ctx *c, Seg *g, int st, const double *cvec) {
+// the base state's part of stage st: the DtN at the stage's surface and the
+// base right-hand side with the tableau's update of column 0
+int seg_base(Ctx *c, Seg *g, int st, const double *cvec) {
     select_parity(c, 0);
     const size_t N = (size_t)c->N, ks = (size_t)c->NC * 2 * N;
     WW_TRY(seg_geometry(c, g));
@@ -614,6 +890,12 @@ int seg_stage(Ctx *c, Seg *g, int st, const double *cvec) {
         c->filt_d, c->ux, c->vy, c->w3, c->uxd, c->vyd, c->w3d, c->Fbase, c->Y, c->Ys, g->K, ks, st, g->S, g->d_a,
         g->d_b, cvec, g->theta, g->steps, c->status);
     WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+int seg_stage(Ctx *c, Seg *g, int st, const double *cvec) {
+    const size_t N = (size_t)c->N, ks = (size_t)c->NC * 2 * N;
+    WW_TRY(seg_base(c, g, st, cvec));
     if (c->nc <= 0) return WW_OK;
     WW_TRY(launch_psi(c));
     WW_TRY(seg_solve(c, c->M + N, c->nc));
@@ -629,12 +911,59 @@ int seg_stage(Ctx *c, Seg *g, int st, const double *cvec) {
     return WW_OK;
 }
 
+// forward stage of the gradient: the base part, then its record
+int seg_fwd_stage(Ctx *c, Seg *g, int st, const double *cvec) {
+    WW_TRY(seg_base(c, g, st, cvec));
+    k_seg_record<<<1, SEG_THREADS, 0, c->stream>>>(c->eta, c->ux, c->vy, c->w3, c->Fbase, c->N, st, g->S, g->steps,
+                                                   g->rec, g->rstep);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
+// the DtN setup of the transposed operator at the recorded surface of stage
+// `off` of the current step (off = -1: the last stage of the step before)
+int seg_adj_setup(Ctx *c, Seg *g, int off, bool fresh) {
+    select_parity(c, 0);
+    k_seg_adj_fetch<<<(c->N + 255) / 256, 256, 0, c->stream>>>(g->rec, g->rstep, off, g->S, g->steps, c->N, g->aeta);
+    WW_CUDA_TRY(cudaGetLastError());
+    WW_TRY(seg_geometry(c, g, g->aeta, g->aeta, false));
+    WW_TRY(seg_assemble(c, g));   // A^T, G^T (c->trans is set)
+    return seg_factor(c, fresh);
+}
+
+// one transposed step of the tableau: Filt, then stages S-1..0
+int seg_adj_step(Ctx *c, Seg *g, const double *cvec) {
+    const int N = c->N;
+    const size_t one = sizeof(double2) * (size_t)N;
+    k_seg_adj_begin<<<1, SEG_THREADS, one, c->stream>>>(g->lam, g->kb, N, c->logN, c->tw, c->filt_d, g->d_b, g->S,
+                                                        cvec, g->theta, g->steps, g->rstep);
+    WW_CUDA_TRY(cudaGetLastError());
+    for (int st = g->S - 1; st >= 0; --st) {
+        WW_TRY(seg_adj_setup(c, g, st, false));
+        k_seg_adj_local<<<1, SEG_THREADS, 2 * one, c->stream>>>(
+            g->kb + (size_t)st * 2 * N, g->rec, g->rstep, st, g->S, g->steps, N, c->logN, c->tw, c->filt_d, g->e,
+            g->einv, c->g, c->tau, cvec, g->chi, g->etal, g->psil, g->gT);
+        WW_CUDA_TRY(cudaGetLastError());
+        WW_TRY(gemv_narrow(c->stream, N, 1, N, 1.0, c->G, N, g->chi, N, 0.0, g->y, N));   // G^T chis
+        k_seg_adj_dtn<<<1, SEG_THREADS, one, c->stream>>>(g->chi, g->y, N, c->logN, c->tw, c->M);
+        WW_CUDA_TRY(cudaGetLastError());
+        WW_TRY(seg_solve(c, c->M, 1));   // A^{-T} D (1/2 H - G^T) diag(1/xi') chi
+        k_seg_adj_update<<<(N + 255) / 256, 256, 0, c->stream>>>(c->M, g->psil, g->etal, g->rec, g->rstep, st, g->S,
+                                                                 g->steps, N, g->d_a, g->theta, cvec, g->lam, g->kb);
+        WW_CUDA_TRY(cudaGetLastError());
+    }
+    return WW_OK;
+}
+
 int seg_prepare(Ctx *c) {
     const size_t N = (size_t)c->N;
     const size_t two = 2 * sizeof(double2) * N;
     WW_CUDA_TRY(cudaFuncSetAttribute(k_geom_mesh, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two));
     WW_CUDA_TRY(cudaFuncSetAttribute(k_base_rhs_mesh, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(two / 2)));
     WW_CUDA_TRY(cudaFuncSetAttribute(k_col_rhs_mesh<ArF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two));
+    WW_CUDA_TRY(cudaFuncSetAttribute(k_seg_adj_begin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(two / 2)));
+    WW_CUDA_TRY(cudaFuncSetAttribute(k_seg_adj_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two));
+    WW_CUDA_TRY(cudaFuncSetAttribute(k_seg_adj_dtn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(two / 2)));
     return WW_OK;
 }
 
@@ -653,12 +982,12 @@ int count_kernels(cudaGraph_t gr, int *out) {
     return WW_OK;
 }
 
-// the segment's step (all S stages) as a graph, captured on first use
-int seg_step_graph(Ctx *c, Seg *g, const double *cvec) {
-    if (g->exec) return WW_OK;
+// capture body() on the context's stream into a graph, once
+template <class F>
+int seg_capture(Ctx *c, cudaGraph_t *graph, cudaGraphExec_t *exec, int *nkern, F body) {
+    if (*exec) return WW_OK;
     WW_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    int st = WW_OK;
-    for (int k = 0; k < g->S && st == WW_OK; ++k) st = seg_stage(c, g, k, cvec);
+    const int st = body();
     cudaGraph_t gr = nullptr;
     const cudaError_t e = cudaStreamEndCapture(c->stream, &gr);
     if (st != WW_OK) {
@@ -666,11 +995,54 @@ int seg_step_graph(Ctx *c, Seg *g, const double *cvec) {
         return st;
     }
     if (e != cudaSuccess) return fail(WW_ERR_CUDA, std::string("segment capture: ") + cudaGetErrorString(e));
-    WW_TRY(count_kernels(gr, &g->nkern));
-    const cudaError_t ei = cudaGraphInstantiate(&g->exec, gr, 0);
-    g->graph = gr;
+    WW_TRY(count_kernels(gr, nkern));
+    const cudaError_t ei = cudaGraphInstantiate(exec, gr, 0);
+    *graph = gr;
     if (ei != cudaSuccess) return fail(WW_ERR_CUDA, std::string("segment instantiate: ") + cudaGetErrorString(ei));
     return WW_OK;
+}
+
+// the segment's step (all S stages) as a graph, captured on first use
+int seg_step_graph(Ctx *c, Seg *g, const double *cvec) {
+    return seg_capture(c, &g->graph, &g->exec, &g->nkern, [&] {
+        int st = WW_OK;
+        for (int k = 0; k < g->S && st == WW_OK; ++k) st = seg_stage(c, g, k, cvec);
+        return st;
+    });
+}
+
+// the gradient's step programs: forward (base only, recorded) and transposed
+int seg_fwd_graph(Ctx *c, Seg *g, const double *cvec) {
+    return seg_capture(c, &g->fgraph, &g->fexec, &g->fkern, [&] {
+        int st = WW_OK;
+        for (int k = 0; k < g->S && st == WW_OK; ++k) st = seg_fwd_stage(c, g, k, cvec);
+        return st;
+    });
+}
+
+int seg_bwd_graph(Ctx *c, Seg *g, const double *cvec) {
+    return seg_capture(c, &g->bgraph, &g->bexec, &g->bkern, [&] { return seg_adj_step(c, g, cvec); });
+}
+
+// the gradient's workspace of a segment (first call)
+int seg_grad_alloc(Ctx *c, Seg *g) {
+    const size_t N = (size_t)c->N, before = g->bytes;
+    int st = WW_OK;
+#define GA(p, n) \
+    if (st == WW_OK && !(p)) st = seg_alloc(c, g, &(p), (n))
+    GA(g->rec, (size_t)g->steps * g->S * SEG_REC * N);
+    GA(g->kb, (size_t)g->S * 2 * N);
+    GA(g->lam, 2 * N);
+    GA(g->chi, N);
+    GA(g->etal, N);
+    GA(g->psil, N);
+    GA(g->y, N);
+    GA(g->aeta, N);
+    GA(g->gT, 1);
+    GA(g->rstep, 1);
+#undef GA
+    g->gbytes += g->bytes - before;
+    return st;
 }
 
 // the interpolation matrix from the previous segment's grid into this one's
@@ -795,44 +1167,63 @@ extern "C" int ww_set_segment(ww_ctx *ctx, const ww_segment *sg) {
     return WW_OK;
 }
 
-extern "C" int shoot_jacobian_segments(ww_ctx *const *ctx, int nseg, const double *cvec, double *r, double *J,
-                                       double *f) {
-    if (nseg < 1 || !ctx || !cvec || !r || !J || !f) return fail(WW_ERR_ARG, "shoot_jacobian_segments: bad argument");
-    std::vector<Ctx *> cs(nseg);
+namespace {
+
+// the contexts of a segmented call, checked: one per segment, each set up by
+// ww_set_segment, sharing n, g, tau, h and the form; the first uniform; the
+// thetas summing to 1
+int segment_contexts(ww_ctx *const *ctx, int nseg, const char *who, std::vector<Ctx *> &cs) {
+    const std::string w(who);
+    cs.assign(nseg, nullptr);
     double th = 0.0;
     for (int l = 0; l < nseg; ++l) {
-        if (!ctx[l]) return fail(WW_ERR_ARG, "shoot_jacobian_segments: NULL context");
+        if (!ctx[l]) return fail(WW_ERR_ARG, w + ": NULL context");
         cs[l] = ctx_of(ctx[l]);
         Ctx *c = cs[l];
-        if (!c->seg) return fail(WW_ERR_ARG, "shoot_jacobian_segments: segment " + std::to_string(l) +
-                                                 " has no ww_set_segment");
-        if (c->stream == nullptr)
-            return fail(WW_ERR_ARG, "shoot_jacobian_segments: the legacy default stream runs no step graphs");
+        if (!c->seg) return fail(WW_ERR_ARG, w + ": segment " + std::to_string(l) + " has no ww_set_segment");
+        if (c->stream == nullptr) return fail(WW_ERR_ARG, w + ": the legacy default stream runs no step graphs");
         const Ctx *c0 = cs[0];
         if (c->n != c0->n || c->g != c0->g || c->tau != c0->tau || c->deep != c0->deep ||
             (!c->deep && c->h != c0->h) || c->precision != c0->precision)
-            return fail(WW_ERR_ARG, "shoot_jacobian_segments: the segments' contexts differ in n, g, tau, h or form");
+            return fail(WW_ERR_ARG, w + ": the segments' contexts differ in n, g, tau, h or form");
         for (int k = 0; k < l; ++k)
-            if (cs[k] == c) return fail(WW_ERR_ARG, "shoot_jacobian_segments: a context may serve one segment");
+            if (cs[k] == c) return fail(WW_ERR_ARG, w + ": a context may serve one segment");
         th += c->seg->theta;
     }
-    if (cs[0]->seg->rho != 1.0)
-        return fail(WW_ERR_ARG, "shoot_jacobian_segments: the first segment is uniform (rho = 1)");
-    if (std::fabs(th - 1.0) > 1e-12) return fail(WW_ERR_ARG, "shoot_jacobian_segments: the thetas must sum to 1");
-    // everything runs on the first context's stream
-    cudaStream_t s0 = cs[0]->stream;
-    std::vector<cudaStream_t> saved(nseg);
-    for (int l = 0; l < nseg; ++l) {
-        saved[l] = cs[l]->stream;
-        cs[l]->stream = s0;
-    }
-    struct Restore {
-        std::vector<Ctx *> &cs;
-        std::vector<cudaStream_t> &saved;
-        ~Restore() {
-            for (size_t l = 0; l < cs.size(); ++l) cs[l]->stream = saved[l];
+    if (cs[0]->seg->rho != 1.0) return fail(WW_ERR_ARG, w + ": the first segment is uniform (rho = 1)");
+    if (std::fabs(th - 1.0) > 1e-12) return fail(WW_ERR_ARG, w + ": the thetas must sum to 1");
+    return WW_OK;
+}
+
+// every segment's work runs on the first context's stream; the contexts'
+// own streams and flags come back on return
+struct SegCall {
+    std::vector<Ctx *> &cs;
+    std::vector<cudaStream_t> saved;
+    explicit SegCall(std::vector<Ctx *> &v) : cs(v), saved(v.size()) {
+        for (size_t l = 0; l < cs.size(); ++l) {
+            saved[l] = cs[l]->stream;
+            cs[l]->stream = cs[0]->stream;
         }
-    } restore{cs, saved};
+    }
+    ~SegCall() {
+        for (size_t l = 0; l < cs.size(); ++l) {
+            cs[l]->stream = saved[l];
+            cs[l]->trans = 0;
+            cs[l]->one_col = false;
+        }
+    }
+};
+
+}  // namespace
+
+extern "C" int shoot_jacobian_segments(ww_ctx *const *ctx, int nseg, const double *cvec, double *r, double *J,
+                                       double *f) {
+    if (nseg < 1 || !ctx || !cvec || !r || !J || !f) return fail(WW_ERR_ARG, "shoot_jacobian_segments: bad argument");
+    std::vector<Ctx *> cs;
+    WW_TRY(segment_contexts(ctx, nseg, "shoot_jacobian_segments", cs));
+    cudaStream_t s0 = cs[0]->stream;
+    SegCall call(cs);
     long long launches = 0;
     for (int l = 0; l < nseg; ++l) {
         Ctx *c = cs[l];
@@ -872,6 +1263,90 @@ extern "C" int shoot_jacobian_segments(ww_ctx *const *ctx, int nseg, const doubl
         const int st = read_status(cs[l]);
         if (st != WW_OK) return fail(st, "segment " + std::to_string(l) + ": " + ww_last_error());
         cs[l]->stats.stages = cs[l]->seg->S * cs[l]->seg->steps;
+        cs[l]->stats.device_bytes = (long long)cs[l]->dev_bytes;
+    }
+    cs[0]->stats.launches = launches;
+    return WW_OK;
+}
+
+extern "C" int objective_and_grad_segments(ww_ctx *const *ctx, int nseg, const double *cvec, double *f,
+                                           double *grad) {
+    if (nseg < 1 || !ctx || !cvec || !f || !grad)
+        return fail(WW_ERR_ARG, "objective_and_grad_segments: bad argument");
+    std::vector<Ctx *> cs;
+    WW_TRY(segment_contexts(ctx, nseg, "objective_and_grad_segments", cs));
+    for (Ctx *c : cs) WW_TRY(seg_grad_alloc(c, c->seg));
+    cudaStream_t s0 = cs[0]->stream;
+    SegCall call(cs);
+    long long launches = 0;
+    // forward: the base state through the segments, every stage recorded
+    for (int l = 0; l < nseg; ++l) {
+        Ctx *c = cs[l];
+        Seg *g = c->seg;
+        c->one_col = true;
+        c->trans = 0;
+        WW_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), s0));
+        WW_CUDA_TRY(cudaMemcpyAsync(c->small, cvec, sizeof(double), cudaMemcpyDeviceToDevice, s0));
+        if (l == 0) {
+            WW_TRY(launch_initial(c, cvec, 0));
+        } else {
+            Ctx *ca = cs[l - 1];
+            WW_TRY(seg_respace_matrix(c, g, ca->N, ca->seg->rho, ca->seg->centre));
+            WW_TRY(dgemm(s0, c->N, 2, ca->N, 1.0, g->R, c->N, ca->Y, ca->N, 0.0, c->Y, c->N));
+            WW_CUDA_TRY(cudaMemcpyAsync(c->Ys, c->Y, sizeof(double) * 2 * c->N, cudaMemcpyDeviceToDevice, s0));
+        }
+        launches += 1;
+        if (c->precision == WW_MIXED) {
+            select_parity(c, 0);
+            WW_TRY(seg_geometry(c, g));
+            WW_TRY(seg_assemble(c, g));
+            WW_TRY(seg_factor(c, true));
+        }
+        WW_CUDA_TRY(cudaMemsetAsync(g->rstep, 0, sizeof(int), s0));
+        WW_TRY(seg_fwd_graph(c, g, c->small));
+        for (int s = 0; s < g->steps; ++s) WW_CUDA_TRY(cudaGraphLaunch(g->fexec, s0));
+        launches += (long long)g->steps * g->fkern;
+    }
+    Ctx *cl = cs[nseg - 1];
+    k_seg_adj_init<<<1, 1024, 0, s0>>>(cl->Y, cl->seg->wts, cl->N, cl->seg->lam, f);
+    WW_CUDA_TRY(cudaGetLastError());
+    WW_CUDA_TRY(cudaMemsetAsync(grad, 0, sizeof(double), s0));
+    launches += 1;
+    // backward: segment by segment from the last
+    for (int l = nseg - 1; l >= 0; --l) {
+        Ctx *c = cs[l];
+        Seg *g = c->seg;
+        c->trans = 1;
+        WW_CUDA_TRY(cudaMemsetAsync(g->gT, 0, sizeof(double), s0));
+        if (c->precision == WW_MIXED) {   // a fresh inverse of A^T at the segment's last stage
+            WW_TRY(seg_adj_setup(c, g, -1, true));
+        }
+        WW_TRY(seg_bwd_graph(c, g, c->small));
+        for (int s = 0; s < g->steps; ++s) WW_CUDA_TRY(cudaGraphLaunch(g->bexec, s0));
+        launches += (long long)g->steps * g->bkern;
+        c->trans = 0;
+        k_seg_add<<<1, 1, 0, s0>>>(grad, g->gT);
+        if (l > 0) {
+            Ctx *ca = cs[l - 1];
+            k_seg_respace_T<<<ca->N, 256, 0, s0>>>(g->R, c->N, ca->N, g->lam, ca->seg->lam);
+            launches += 1;
+        }
+        WW_CUDA_TRY(cudaGetLastError());
+        launches += 1;
+        c->dtn_ready = false;
+    }
+    Ctx *c0 = cs[0];
+    if (c0->n > 0) {
+        k_seg_grad<<<c0->n, 256, 0, s0>>>(c0->basis, c0->seg->lam, c0->N, grad);
+        WW_CUDA_TRY(cudaGetLastError());
+        launches += 1;
+    }
+    for (int l = 0; l < nseg; ++l) {
+        const int st = read_status(cs[l]);
+        if (st != WW_OK) return fail(st, "segment " + std::to_string(l) + ": " + ww_last_error());
+        cs[l]->stats.stages = 2 * cs[l]->seg->S * cs[l]->seg->steps;
+        cs[l]->stats.device_bytes = (long long)cs[l]->dev_bytes;
+        cs[l]->stats.adjoint_bytes = (long long)cs[l]->seg->gbytes;
     }
     cs[0]->stats.launches = launches;
     return WW_OK;

@@ -9,7 +9,12 @@ Cases: one uniform RK4 segment (the same discrete map as the plain shot);
 three segments with meshes refined near x = 0 and a doubled grid, DOP853, in
 finite depth and deep water; two segments with surface tension; and the
 segmented workload (four segments, rho down to 0.1, M doubling twice) shrunk
-8x in M and 4x in steps so that the oracle finishes in seconds."""
+8x in M and 4x in steps so that the oracle finishes in seconds.
+
+The segmented gradient by the GPU's discrete adjoint
+(objective_and_grad_segments) on the same cases against the oracle's
+(orc_objective_and_grad_segments) and against J^T r of the GPU's segmented
+Jacobian."""
 import math
 
 import numpy as np
@@ -191,3 +196,104 @@ def test_paper_basis_and_bad_segments(ww):
         ww.set_segment(b, 4, 0.4, 1.0, 1)                 # thetas sum to 0.9
         with pytest.raises(ww.WWError):
             ww.shoot_jacobian_segments([a, b], dev(c), r, J, f)
+
+
+def gpu_grad_segments(ww, segs, scheme, n, c, precision, g=1.0, tau=0.0, h=1.0, basis=None):
+    """f and grad of the segmented shot by the GPU's discrete adjoint (called
+    twice: bitwise the same), and J^T r of the GPU's segmented Jacobian through
+    the same contexts afterwards."""
+    import torch
+    ctxs = []
+    try:
+        for i, (M, steps, theta, rho, centre) in enumerate(segs):
+            ctx = ww.Context(M, n, g=g, tau=tau, h=h, steps=steps, precision=precision,
+                             basis=basis if i == 0 else None)
+            ctxs.append(ctx)
+            ww.set_segment(ctx, steps, theta, rho, centre, scheme)
+        f = torch.empty(1, dtype=torch.float64, device="cuda")
+        grad = torch.empty(n + 1, dtype=torch.float64, device="cuda")
+        ww.objective_and_grad_segments(ctxs, dev(c), f, grad)
+        out = (float(f.item()), grad.cpu().numpy())
+        ww.objective_and_grad_segments(ctxs, dev(c), f, grad)
+        assert float(f.item()) == out[0] and np.array_equal(grad.cpu().numpy(), out[1])
+        last = ctxs[-1]
+        r = torch.empty(last.N, dtype=torch.float64, device="cuda")
+        J = torch.empty(n + 1, last.N, dtype=torch.float64, device="cuda")
+        fj = torch.empty(1, dtype=torch.float64, device="cuda")
+        ww.shoot_jacobian_segments(ctxs, dev(c), r, J, fj)
+        jtr = J.cpu().numpy() @ r.cpu().numpy()
+        return out[0], out[1], jtr, float(fj.item())
+    finally:
+        for ctx in ctxs:
+            ctx.close()
+
+
+_GSPREAD = {}
+
+
+def check_grad(ww, segs, scheme, n, c, precision, **kw):
+    """f at 1e-11 and grad (norm-wise) at max(1e-11, 4 x the oracle's one-ulp
+    spread of its own gradient) against the oracle's discrete adjoint, and
+    against J^T r of the GPU's segmented Jacobian in the same form."""
+    f, g, jtr, fj = gpu_grad_segments(ww, segs, scheme, n, c, precision, **kw)
+    prob, keep = O.make_problem(segs[0][0], n, g=kw.get("g", 1.0), tau=kw.get("tau", 0.0), h=kw.get("h", 1.0),
+                             basis=kw.get("basis"))
+    key = (tuple(segs), scheme, n, tuple(c), tuple(sorted((k, str(v)) for k, v in kw.items())))
+    f0, g0 = O.objective_and_grad_segments(prob, segs, scheme, c)
+    if key not in _GSPREAD:
+        cp = c.copy()
+        cp[1] = np.nextafter(c[1], np.inf)
+        _, gp = O.objective_and_grad_segments(prob, segs, scheme, cp)
+        _GSPREAD[key] = np.linalg.norm(gp - g0) / np.linalg.norm(g0)
+    tol = max(TOL, 4.0 * _GSPREAD[key])
+    eg = np.linalg.norm(g - g0) / np.linalg.norm(g0)
+    ej = np.linalg.norm(g - jtr) / np.linalg.norm(jtr)
+    ef = abs(f - f0) / abs(f0)
+    print(f"\ngradient {[s[:4] for s in segs]} {scheme} precision={precision}: f {ef:.2e}, grad vs oracle {eg:.2e}, "
+          f"vs J^T r {ej:.2e} (tolerance {tol:.2e}; oracle one-ulp spread {_GSPREAD[key]:.2e})")
+    assert ef < TOL and abs(f - fj) <= 1e-14 * abs(fj)
+    assert eg < tol and ej < tol
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("h,tau,segs", [
+    (1.0, 0.0, [(64, 5, 0.375, 1.0, 0), (128, 8, 0.375, 0.4, 0), (128, 6, 0.25, 0.2, 0)]),
+    (math.inf, 0.0, [(64, 5, 0.375, 1.0, 0), (128, 8, 0.375, 0.4, 0), (128, 6, 0.25, 0.2, 0)]),
+    (0.5, 0.01, [(64, 8, 0.5, 1.0, 1), (128, 24, 0.5, 0.7, 1)]),
+])
+def test_segmented_gradient_matches_oracle(ww, precision, h, tau, segs):
+    """The discrete adjoint of the segmented shot (meshes, respacing, DOP853)
+    against the oracle's (orc_objective_and_grad_segments)."""
+    N, n = segs[0][0], 12
+    w = W.Workload("seg3", N=N, n=n, steps=1, h=h, tau=tau, amp=0.05)
+    c, _ = W.coefficients(w)
+    check_grad(ww, segs, "dop853", n, c, precision, h=h, tau=tau)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_segmented_workload_gradient_shrunk(ww, precision):
+    """The segmented workload's structure shrunk as in the Jacobian test above."""
+    wl = W.SEGMENTED
+    segs = [(M // 8, max(2, s // 4), th, rho, ctr) for (M, s, th, rho, ctr) in wl.meta["segments"]]
+    N, n = segs[0][0], segs[0][0] // 3
+    w = W.Workload("seg_wl", N=N, n=n, steps=1, h=wl.h, amp=0.05)
+    c, _ = W.coefficients(w)
+    check_grad(ww, segs, wl.meta["tableau"], n, c, precision, h=wl.h)
+
+
+def test_one_uniform_rk4_segment_gradient_is_the_plain_adjoint(ww):
+    """One uniform RK4 segment: the segmented adjoint equals the plain
+    objective_and_grad (the same transposed map; its sums round differently)."""
+    import torch
+    N, n, steps = 64, 8, 16
+    w = W.Workload("seg1", N=N, n=n, steps=steps, amp=0.05)
+    c, _ = W.coefficients(w)
+    for precision in (ww.WW_FP64, ww.WW_MIXED):
+        with ww.Context(N, n, steps=steps, precision=precision) as ctx:
+            f = torch.empty(1, dtype=torch.float64, device="cuda")
+            g = torch.empty(n + 1, dtype=torch.float64, device="cuda")
+            ww.objective_and_grad(ctx, dev(c), f, g)
+            plain = (float(f.item()), g.cpu().numpy())
+        fs, gs, jtr, _ = gpu_grad_segments(ww, [(N, steps, 1.0, 1.0, 1)], "rk4", n, c, precision)
+        assert abs(fs - plain[0]) <= 1e-13 * abs(plain[0])
+        assert np.linalg.norm(gs - plain[1]) / np.linalg.norm(plain[1]) < 1e-12
