@@ -152,7 +152,9 @@ def flush_l2(buf):
 # kernel, from one ncu capture of the current kernel on the N = 2048 workload
 # (summaries under profiles/); a kernel changed since its capture has none (null).
 TRAFFIC_BYTES = {("mixed", "N2048_n512_steps1024_h1", "k_ozaki"): 85.35e6,
-                 # mean of the update's two launches (54.1 and 101.2 MB), profiles/k_tc_gemm_N2048.md
+                 # mean of the update's two launches, profiles/k_tc_gemm_N2048.md: two CTAs
+                 # per SM (54.6 and 89.9 MB) and one (54.1 and 101.2 MB)
+                 ("mixed", "N2048_n512_steps1024_h1", "k_tc_gemm<128,3,3,32,2>"): 72.27e6,
                  ("mixed", "N2048_n512_steps1024_h1", "k_tc_gemm<128,3,3,32>"): 77.65e6}
 
 # slice pairs (p, q) with p + q <= 6 of the 7 x 7 integer digits: 28 bf16 GEMMs
@@ -178,7 +180,13 @@ def _entry(kernel, bound, flops, dur, peak, unit, src, w, form, **extra):
     return e
 
 
-def rooflines(form, timing, w, pk):
+def tc_gemm_name(sched):
+    """The inverse update's kernel under a schedule: its column tile, and a
+    fifth template argument 2 when two CTAs share an SM."""
+    return f"k_tc_gemm<{sched['inv_bn']},3,3,32{',2' if sched.get('inv_ctas', 1) == 2 else ''}>"
+
+
+def rooflines(form, timing, w, pk, sched=None):
     """Per-kernel rooflines of the profiled Jacobian, from the phase events that
     bracket single kernels on the stream each runs on: gkernel (the column
     G-apply product), inverse (the two products of the inverse update),
@@ -211,7 +219,7 @@ def rooflines(form, timing, w, pk):
         d, _ = dur("inverse", 2)
         if d:
             ns = NS_PAIRS * 2.0 * N ** 3
-            out.append(_entry("k_tc_gemm<128,3,3,32>", "tensor", ns, d, peak, "TFLOP/s", src, w, form,
+            out.append(_entry(tc_gemm_name(sched or {"inv_bn": 128}), "tensor", ns, d, peak, "TFLOP/s", src, w, form,
                               role="inverse update X <- X (2I - A X), one of its two products",
                               work=f"{NS_PAIRS} bf16 slice-pair GEMMs of {N}^3",
                               method_fp32_tflops=2.0 * N ** 3 / d / 1e12, share_ms_per_stage=2 * d * 1e3))
@@ -367,6 +375,7 @@ def run_ours(args):
     # ---- profiled Jacobian: phase events on (per-kernel durations on the streams
     # the kernels run on) and, in the mixed form, the refinement residual
     # measured after the last correction of every 256th solve
+    sched = ctx.schedule()
     ctx.set_timing(True)
     if form == "mixed":
         ctx.set_verify(256)
@@ -375,7 +384,7 @@ def run_ours(args):
     stats = ctx.stats()
     ctx.set_timing(False)
     ctx.close()
-    dom, roofs = rooflines(form, timing, w, peaks())
+    dom, roofs = rooflines(form, timing, w, peaks(), sched)
     errors = {form: error_vs_oracle(w, *res)} if ws == 1 else {}
     fp64 = None
     if form == "mixed" and ws == 1 and not args.no_fp64_form and not args.rk_steps:

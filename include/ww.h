@@ -98,6 +98,14 @@ typedef struct {
     int inv_bn;    /* WW_MIXED: column tile of the inverse update's products (64, 128,
                       256; 256 needs N a multiple of 256)                               */
     int lu_nb;     /* WW_FP64: block size of the LU and triangular solves (32, 64)      */
+    int inv_ctas;  /* WW_MIXED: CTAs per SM of the inverse update's products: 1 (one
+                      CTA with a 4-deep operand ring) or 2 (two CTAs with 2-deep rings,
+                      so that one's epilogue overlaps the other's main loop; inv_bn
+                      64 or 128)                                                        */
+    int prio;      /* WW_MIXED with overlap: the step graph runs the base chain's
+                      kernels at a higher priority than the columns' (1: its blocks
+                      go first when SMs free up), or all at the launching stream's
+                      priority (0)                                                      */
 } ww_schedule;
 
 typedef struct ww_ctx ww_ctx;
@@ -130,7 +138,7 @@ int ww_get_stats(const ww_ctx *ctx, ww_stats *out);
  * step program is captured again.  WW_ERR_ARG in WW_FP64 (no refinement). */
 int ww_set_verify(ww_ctx *ctx, int every);
 
-/* The context's schedule.  ww_create sets the default {1, 0, 64, 128, 64};
+/* The context's schedule.  ww_create sets the default {1, 0, 64, 128, 64, 2, 1};
  * ww_set_schedule validates the fields (WW_ERR_ARG) and drops the captured
  * step programs, which the next call captures again. */
 int ww_set_schedule(ww_ctx *ctx, const ww_schedule *s);
@@ -138,7 +146,8 @@ int ww_get_schedule(const ww_ctx *ctx, ww_schedule *s);
 
 /* ww_autotune -- choose the context's schedule by timing.  Candidate
  * schedules (coordinate by coordinate: the stage program, then the tile of
- * the corrections, then the tile of the inverse update in WW_MIXED; the LU
+ * the corrections, then the tile and the CTAs per SM of the inverse update in
+ * WW_MIXED; the LU
  * block in WW_FP64) each run the initial data and probe_steps RK steps of the
  * Jacobian of the shot c (device, n+1 doubles) on the context's stream, timed
  * with CUDA events after one untimed step; the fastest is kept.  cache_path

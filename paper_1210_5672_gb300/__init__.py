@@ -61,7 +61,7 @@ class _Problem(C.Structure):
 class Schedule(C.Structure):
     """ww_schedule: the knobs of the step program (see include/ww.h)."""
     _fields_ = [("overlap", C.c_int), ("ns_every", C.c_int), ("corr_bn", C.c_int), ("inv_bn", C.c_int),
-                ("lu_nb", C.c_int)]
+                ("lu_nb", C.c_int), ("inv_ctas", C.c_int), ("prio", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -221,7 +221,7 @@ class Context:
         return sch.as_dict()
 
     def set_schedule(self, **kw):
-        """Change fields of the schedule (overlap, ns_every, corr_bn, inv_bn, lu_nb)."""
+        """Change fields of the schedule (overlap, ns_every, corr_bn, inv_bn, lu_nb, inv_ctas, prio)."""
         cur = self.schedule()
         unknown = set(kw) - set(cur)
         if unknown:

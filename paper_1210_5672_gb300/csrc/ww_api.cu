@@ -346,7 +346,9 @@ int build_step_graph(Owned *o, int with_cols) {
         }
     }
     WW_TRY(count_kernel_nodes(g, &sg.nkern));
-    e = cudaGraphInstantiate(&sg.exec, g, 0);
+    // prio: the kernel nodes keep the priorities of the streams they were
+    // captured on (the base chain's side stream is the device's highest)
+    e = cudaGraphInstantiate(&sg.exec, g, c->sch.prio ? cudaGraphInstantiateFlagUseNodePriority : 0);
     if (e != cudaSuccess) {
         cudaGraphDestroy(g);
         return fail(WW_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
@@ -959,6 +961,10 @@ int check_schedule(const Ctx *c, const ww_schedule &s) {
         return fail(WW_ERR_ARG, "ww_schedule: inv_bn must be 64, 128 or 256");
     if (s.inv_bn == 256 && c->N % 256 != 0) return fail(WW_ERR_ARG, "ww_schedule: inv_bn 256 needs N % 256 == 0");
     if (s.lu_nb != 32 && s.lu_nb != 64) return fail(WW_ERR_ARG, "ww_schedule: lu_nb must be 32 or 64");
+    if (s.inv_ctas != 1 && s.inv_ctas != 2) return fail(WW_ERR_ARG, "ww_schedule: inv_ctas must be 1 or 2");
+    if (s.inv_ctas == 2 && s.inv_bn == 256)
+        return fail(WW_ERR_ARG, "ww_schedule: inv_ctas 2 needs inv_bn 64 or 128");
+    if (s.prio != 0 && s.prio != 1) return fail(WW_ERR_ARG, "ww_schedule: prio must be 0 or 1");
     return WW_OK;
 }
 
@@ -981,7 +987,9 @@ std::string tune_key(const Ctx *c) {
     return k.str();
 }
 
-// the cached schedule of this (N, n+1, precision), if the file has one
+// the cached schedule of this (N, n+1, precision), if the file has one; lines
+// read "v2 N n+1 form overlap ns_every corr_bn inv_bn lu_nb inv_ctas prio ms"
+// (lines of another layout are passed over)
 bool cache_lookup(const char *path, const std::string &key, ww_schedule *out) {
     if (!path) return false;
     std::ifstream in(path);
@@ -990,9 +998,12 @@ bool cache_lookup(const char *path, const std::string &key, ww_schedule *out) {
     while (std::getline(in, line)) {
         std::istringstream ls(line);
         int N = 0, nc = 0;
-        std::string form;
+        std::string tag, form;
         ww_schedule s{};
-        if (!(ls >> N >> nc >> form >> s.overlap >> s.ns_every >> s.corr_bn >> s.inv_bn >> s.lu_nb)) continue;
+        if (!(ls >> tag) || tag != "v2") continue;
+        if (!(ls >> N >> nc >> form >> s.overlap >> s.ns_every >> s.corr_bn >> s.inv_bn >> s.lu_nb >> s.inv_ctas >>
+              s.prio))
+            continue;
         std::ostringstream k;
         k << N << " " << nc << " " << form;
         if (k.str() == key) {
@@ -1007,8 +1018,8 @@ int cache_store(const char *path, const std::string &key, const ww_schedule &s, 
     if (!path) return WW_OK;
     std::ofstream out(path, std::ios::app);
     if (!out) return fail(WW_ERR_ARG, std::string("ww_autotune: cannot append to ") + path);
-    out << key << " " << s.overlap << " " << s.ns_every << " " << s.corr_bn << " " << s.inv_bn << " " << s.lu_nb << " "
-        << ms << "\n";
+    out << "v2 " << key << " " << s.overlap << " " << s.ns_every << " " << s.corr_bn << " " << s.inv_bn << " "
+        << s.lu_nb << " " << s.inv_ctas << " " << s.prio << " " << ms << "\n";
     return WW_OK;
 }
 
@@ -1090,7 +1101,7 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
     c->precision = p->precision;
     c->refine_tol = p->refine_tol > 0.0 ? p->refine_tol : 1e-13;
     c->max_refine = p->max_refine > 0 ? p->max_refine : 4;
-    c->sch = ww_schedule{1, 0, 64, 128, LU_NB};
+    c->sch = ww_schedule{1, 0, 64, 128, LU_NB, 2, 1};
     c->nb = c->N < LU_NB ? c->N : LU_NB;
     {
         static std::atomic<unsigned long long> next_id{1};
@@ -1499,7 +1510,7 @@ int ww_autotune(ww_ctx *ctx, const double *cvec, int probe_steps, const char *ca
         return WW_OK;
     };
     // coordinate by coordinate from the default schedule
-    ww_schedule base = ww_schedule{1, 0, 64, 128, LU_NB};
+    ww_schedule base = ww_schedule{1, 0, 64, 128, LU_NB, 2, 1};
     if (c->precision == WW_MIXED) {
         for (int v : {0, 1, 2}) {   // stage program: in line, overlapped with every-stage or alternate updates
             ww_schedule s = base;
@@ -1514,10 +1525,21 @@ int ww_autotune(ww_ctx *ctx, const double *cvec, int probe_steps, const char *ca
             WW_TRY(consider(s));
         }
         base = best;
-        for (int bn : {64, 256}) {
+        for (int bn : {64, 256}) {   // (256-wide tiles take one CTA per SM)
             if (bn == 256 && c->N % 256 != 0) continue;
             ww_schedule s = base;
             s.inv_bn = bn;
+            if (bn == 256) s.inv_ctas = 1;
+            WW_TRY(consider(s));
+        }
+        if (best.inv_bn != 256) {
+            ww_schedule s = best;
+            s.inv_ctas = 3 - best.inv_ctas;
+            WW_TRY(consider(s));
+        }
+        if (best.overlap) {
+            ww_schedule s = best;
+            s.prio = 1 - best.prio;
             WW_TRY(consider(s));
         }
     } else {

@@ -44,7 +44,7 @@ int tc_gemm_f32acc(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 
 int tc_gemm_2x2(cudaStream_t s, const __nv_bfloat16 *A2, const __nv_bfloat16 *B2, int M, int Nn, int K, int out_mode,
                 float *Cf, double *Cd, int ldc, double alpha, int *err, const int *skip, int bn);
 int tc_gemm_f32acc_sliced(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 *B3, int M, int Nn, int K,
-                          const TcOut &o, int *err, const int *skip, int bn);
+                          const TcOut &o, int *err, const int *skip, int bn, int ctas);
 // ww_ozaki.cu
 int ozaki_digits(cudaStream_t s, const double *X, int ld, int rows, int K, int side, float diag_shift, int *emax,
                  double *scale, __nv_bfloat16 *dst, const int *skip);
@@ -259,7 +259,7 @@ int ns_step(Ctx *c, bool record, const int *skip) {
     o3.shift = 2.f;
     o3.s_col = m->Wslc;
     o3.dev_max = record ? m->nsres_last : nullptr;
-    WW_TRY(tc_gemm_f32acc_sliced(s, m->Aslc, m->XslcB, N, N, N, o3, m->err, skip, c->sch.inv_bn));
+    WW_TRY(tc_gemm_f32acc_sliced(s, m->Aslc, m->XslcB, N, N, N, o3, m->err, skip, c->sch.inv_bn, c->sch.inv_ctas));
     // X <- X W: the FP32 X, its slices for the next update, and this stage's rows of X
     TcOut o4{};
     o4.mode = 4;
@@ -268,7 +268,7 @@ int ns_step(Ctx *c, bool record, const int *skip) {
     o4.s_col = m->XnB;
     o4.s_row = m->XnA;
     o4.s_row2 = m->Xrow[c->par];
-    WW_TRY(tc_gemm_f32acc_sliced(s, m->XslcA, m->Wslc, N, N, N, o4, m->err, skip, c->sch.inv_bn));
+    WW_TRY(tc_gemm_f32acc_sliced(s, m->XslcA, m->Wslc, N, N, N, o4, m->err, skip, c->sch.inv_bn, c->sch.inv_ctas));
     if (record) WW_TRY(phase_mark(c, WW_PHASE_INVERSE, 1));
     // the product above still reads XslcA while it writes: its slices land in XnA / XnB
     // and move over afterwards (after a skipped update both already hold the same data)

@@ -51,22 +51,25 @@ struct Pairs {
 //      operand (s_row[k][i][j]), and 2 more left-operand slices (s_row2)).
 namespace {
 
-// ring depth: as many K-chunk stages as fit in 216 KB, at most 4
-template <int BN, int SA, int SB, int BK = TC_BK>
+// ring depth: as many K-chunk stages as fit in 216 KB (MINB = 1 CTA per SM)
+// or 104 KB (MINB = 2: two CTAs share an SM, so that one's epilogue overlaps
+// the other's main loop), at most 4
+template <int BN, int SA, int SB, int BK = TC_BK, int MINB = 1>
 struct TcSmem {
     static constexpr int A_TILE = TC_BM * BK * 2;   // bytes
     static constexpr int B_TILE = BN * BK * 2;
     static constexpr int STAGE = SA * A_TILE + SB * B_TILE;
-    static constexpr int STAGES = (216 * 1024 / STAGE) < 4 ? (216 * 1024 / STAGE) : 4;
+    static constexpr int BUDGET = (MINB == 1 ? 216 : 104) * 1024;
+    static constexpr int STAGES = (BUDGET / STAGE) < 4 ? (BUDGET / STAGE) : 4;
     static constexpr int BYTES = STAGES * STAGE + 1024 /* align */ + 256 /* barriers */;
 };
 
-template <int BN, int SA, int SB, int BK>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+template <int BN, int SA, int SB, int BK, int MINB>
+__global__ void __launch_bounds__(TC_THREADS, MINB)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int Nn, int K,
               Pairs pairs, TcOut o, int *err, const int *skip) {
     if (skip && *skip) return;   // a step the caller decided on the device to leave out
-    using L = TcSmem<BN, SA, SB, BK>;
+    using L = TcSmem<BN, SA, SB, BK, MINB>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t base = tc::smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024 - (base & 1023)) & 1023);
@@ -269,18 +272,19 @@ int tc_make_map(CUtensorMap *map, const void *ptr, int K, long rows, int box_row
 
 namespace {
 
-template <int BN, int SA, int SB, int BK = TC_BK>
+template <int BN, int SA, int SB, int BK = TC_BK, int MINB = 1>
 int launch_tc(cudaStream_t s, const void *A, const void *B, int M, int Nn, int K, const Pairs &pairs, const TcOut &o,
               int *err, const int *skip) {
     if (o.mode == 4 && (M != Nn || Nn % 32 != 0))
         return fail(WW_ERR_ARG, "tc_gemm: slice output needs a square product with N a multiple of 32");
-    using L = TcSmem<BN, SA, SB, BK>;
+    using L = TcSmem<BN, SA, SB, BK, MINB>;
+    static_assert(MINB == 1 || L::STAGES >= 2, "two CTAs per SM need two stages each");
     static_assert(L::BYTES <= 227 * 1024, "shared memory");
     if (K % BK != 0) return fail(WW_ERR_ARG, "tc_gemm: K must be a multiple of the K chunk");
     CUtensorMap ta, tb;
     WW_TRY(tc_make_map(&ta, A, K, (long)SA * M, TC_BM, BK));
     WW_TRY(tc_make_map(&tb, B, K, (long)SB * Nn, BN, BK));
-    auto kern = k_tc_gemm<BN, SA, SB, BK>;
+    auto kern = k_tc_gemm<BN, SA, SB, BK, MINB>;
     WW_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES));
     dim3 grid((M + TC_BM - 1) / TC_BM, (Nn + BN - 1) / BN);
     kern<<<grid, TC_THREADS, L::BYTES, s>>>(ta, tb, M, Nn, K, pairs, o, err, skip);
@@ -405,7 +409,7 @@ int tc_gemm_2x2(cudaStream_t s, const __nv_bfloat16 *A2, const __nv_bfloat16 *B2
 
 // FP32-accurate product with a sliced output (modes 3 and 4 of TcOut), 3 + 3 slices
 int tc_gemm_f32acc_sliced(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bfloat16 *B3, int M, int Nn, int K,
-                          const TcOut &o, int *err, const int *skip, int bn) {
+                          const TcOut &o, int *err, const int *skip, int bn, int ctas) {
     if (K % TC_BK != 0) return fail(WW_ERR_ARG, "tc_gemm: K must be a multiple of 64");
     Pairs P{};
     const int pp[6] = {2, 1, 0, 1, 0, 0}, qq[6] = {0, 1, 2, 0, 1, 0};   // smallest terms first
@@ -416,7 +420,10 @@ int tc_gemm_f32acc_sliced(cudaStream_t s, const __nv_bfloat16 *A3, const __nv_bf
     }
     // 32-wide K chunks (64-byte swizzle): 4 stages of 48 KB instead of 2 of 96 KB;
     // 64-wide column tiles (schedule) double the CTAs of small products; 256-wide
-    // ones (3 stages of 72 KB) load a third fewer operand bytes per flop
+    // ones (3 stages of 72 KB) load a third fewer operand bytes per flop; two
+    // CTAs per SM (2 stages each) overlap one tile's epilogue with another's MMAs
+    if (ctas == 2 && bn == 64) return launch_tc<64, 3, 3, 32, 2>(s, A3, B3, M, Nn, K, P, o, err, skip);
+    if (ctas == 2) return launch_tc<128, 3, 3, 32, 2>(s, A3, B3, M, Nn, K, P, o, err, skip);
     if (bn == 64) return launch_tc<64, 3, 3, 32>(s, A3, B3, M, Nn, K, P, o, err, skip);
     if (bn == 256) return launch_tc<256, 3, 3, 32>(s, A3, B3, M, Nn, K, P, o, err, skip);
     return launch_tc<128, 3, 3, 32>(s, A3, B3, M, Nn, K, P, o, err, skip);

@@ -425,7 +425,8 @@ def test_schedules_agree_and_autotune_caches(ww, precision, tmp_path):
     r0, J0, f0 = O.shoot_jacobian(prob, c)
     if precision == ww.WW_MIXED:
         variants = [dict(), dict(overlap=0), dict(ns_every=1), dict(corr_bn=32), dict(corr_bn=128),
-                    dict(inv_bn=64), dict(inv_bn=256)]
+                    dict(inv_bn=64), dict(inv_bn=256, inv_ctas=1), dict(inv_ctas=1), dict(inv_bn=64, inv_ctas=1),
+                    dict(prio=0)]
     else:
         variants = [dict(), dict(lu_nb=32)]
     with ww.Context(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps, precision=precision) as ctx:
@@ -438,12 +439,14 @@ def test_schedules_agree_and_autotune_caches(ww, precision, tmp_path):
             assert col_rel(J.cpu().numpy().T, J0) < TOL, v
         with pytest.raises(ww.WWError):
             ctx.set_schedule(corr_bn=48)
+        with pytest.raises(ww.WWError):
+            ctx.set_schedule(inv_bn=256, inv_ctas=2)
         cache = tmp_path / "tune.txt"
         ms = ctx.autotune(dev(c), probe_steps=2, cache_path=str(cache))
         chosen = ctx.schedule()
         lines = cache.read_text().splitlines()
         assert ms > 0 and len(lines) == 1
-        assert lines[0].split()[:3] == [str(w.N), str(w.n + 1), "mixed" if precision else "fp64"]
+        assert lines[0].split()[:4] == ["v2", str(w.N), str(w.n + 1), "mixed" if precision else "fp64"]
         ctx.set_schedule(**default)
         assert ctx.autotune(dev(c), probe_steps=2, cache_path=str(cache)) == 0.0   # from the cache
         assert ctx.schedule() == chosen and len(cache.read_text().splitlines()) == 1
