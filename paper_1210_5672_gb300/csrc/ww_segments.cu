@@ -828,8 +828,12 @@ void free_seg(Ctx *c, Seg *g) {
 }
 
 // ---------------------------------------------------------------- one stage of a segment
-int seg_factor(Ctx *c, bool fresh) {
-    if (c->precision == WW_MIXED) return mixed_setup(c, fresh ? 1 : 0, 1);
+// the form's factorisation of the assembled operator; the mixed form moves its
+// approximate inverse to it (fresh: from 4/3 I), on odd stages only when the
+// last move left max|I - A X| above its threshold unless the schedule updates
+// on every stage
+int seg_factor(Ctx *c, bool fresh, int st = 0) {
+    if (c->precision == WW_MIXED) return mixed_setup(c, fresh ? 1 : 0, c->sch.ns_every || st % 2 == 0);
     return lu_factor_fp64(c);
 }
 
@@ -880,7 +884,7 @@ int seg_base(Ctx *c, Seg *g, int st, const double *cvec) {
     const size_t N = (size_t)c->N, ks = (size_t)c->NC * 2 * N;
     WW_TRY(seg_geometry(c, g));
     WW_TRY(seg_assemble(c, g));
-    WW_TRY(seg_factor(c, false));
+    WW_TRY(seg_factor(c, false, st));
     WW_TRY(launch_phi0(c));
     WW_TRY(seg_solve(c, c->M, 1));
     WW_TRY(launch_gamma(c, 0, 1));
@@ -928,7 +932,7 @@ int seg_adj_setup(Ctx *c, Seg *g, int off, bool fresh) {
     WW_CUDA_TRY(cudaGetLastError());
     WW_TRY(seg_geometry(c, g, g->aeta, g->aeta, false));
     WW_TRY(seg_assemble(c, g));   // A^T, G^T (c->trans is set)
-    return seg_factor(c, fresh);
+    return seg_factor(c, fresh, off < 0 ? 0 : off);
 }
 
 // one transposed step of the tableau: Filt, then stages S-1..0
