@@ -216,13 +216,16 @@ def rooflines(form, timing, w, pk, sched=None):
                               role="column G-apply (7+7 digits)",
                               work=f"{OZAKI_PAIRS} bf16 digit-pair GEMMs of {N} x {nc} x {N}",
                               method_fp64_tflops=g_fp64 / d / 1e12, share_ms_per_stage=d * 1e3))
-        d, _ = dur("inverse", 2)
+        d, n_upd = dur("inverse", 2)
         if d:
             ns = NS_PAIRS * 2.0 * N ** 3
+            # the update runs on the stages that move the inverse (even ones by default)
+            stages = timing.get("assembly", (0.0, 0))[1] or n_upd
             out.append(_entry(tc_gemm_name(sched or {"inv_bn": 128}), "tensor", ns, d, peak, "TFLOP/s", src, w, form,
                               role="inverse update X <- X (2I - A X), one of its two products",
                               work=f"{NS_PAIRS} bf16 slice-pair GEMMs of {N}^3",
-                              method_fp32_tflops=2.0 * N ** 3 / d / 1e12, share_ms_per_stage=2 * d * 1e3))
+                              method_fp32_tflops=2.0 * N ** 3 / d / 1e12, updates_per_stage=n_upd / stages,
+                              share_ms_per_stage=2 * d * 1e3 * n_upd / stages))
     d, _ = dur("assembly")
     if d:
         out.append(_entry("k_assemble_sym", "alu", ASM_FLOP_PER_PAIR * N * N / 2.0, d, FP64_PEAK_TFLOPS, "TFLOP/s",

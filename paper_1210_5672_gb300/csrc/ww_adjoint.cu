@@ -377,10 +377,10 @@ size_t fft_smem(int N, int arrays) { return (size_t)arrays * sizeof(double2) * N
 }  // namespace
 
 int prepare_adjoint(int Nmax) {
-    const int one = (int)fft_smem(Nmax, 1), two = (int)fft_smem(Nmax, 2);
-    WW_CUDA_TRY(cudaFuncSetAttribute(k_adj_begin_step, cudaFuncAttributeMaxDynamicSharedMemorySize, one));
-    WW_CUDA_TRY(cudaFuncSetAttribute(k_adj_local, cudaFuncAttributeMaxDynamicSharedMemorySize, two));
-    WW_CUDA_TRY(cudaFuncSetAttribute(k_adj_dtn, cudaFuncAttributeMaxDynamicSharedMemorySize, one));
+    const size_t one = fft_smem(Nmax, 1), two = fft_smem(Nmax, 2);
+    WW_TRY(raise_smem(reinterpret_cast<const void *>(k_adj_begin_step), one));
+    WW_TRY(raise_smem(reinterpret_cast<const void *>(k_adj_local), two));
+    WW_TRY(raise_smem(reinterpret_cast<const void *>(k_adj_dtn), one));
     return WW_OK;
 }
 

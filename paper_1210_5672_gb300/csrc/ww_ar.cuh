@@ -91,6 +91,24 @@ struct ArDF {
     static __device__ __forceinline__ C addr(C z, R a, R b) { return dfl::make(dfl::add(dfl::re(z), a), dfl::add(dfl::im(z), b)); }
 };
 
+// The transforms' twiddle table (N/2 complex entries, the same element type as
+// the transform's data) copied into shared memory at dst, right after the
+// kernel's work arrays: the passes then read their twiddles at shared-memory
+// latency instead of through L1.  The caller synchronises before the first
+// transform; the returned pointer replaces the global table.
+template <class AR>
+__device__ __forceinline__ const void *stage_twiddles(const void *tw, typename AR::C *dst, int N) {
+    const typename AR::C *src = static_cast<const typename AR::C *>(tw);
+    for (int j = threadIdx.x; j < (N >> 1); j += blockDim.x) dst[j] = src[j];
+    return dst;
+}
+
+// bytes of shared memory of a kernel with `arrays` transform buffers and the staged twiddles
+template <class AR>
+__host__ __forceinline__ size_t fft_smem_bytes(int N, int arrays) {
+    return sizeof(typename AR::C) * ((size_t)arrays * AR::cap(N) + (size_t)(N >> 1));
+}
+
 // s <- s * (ik) / N (Nyquist zero)
 template <class AR>
 __device__ __forceinline__ void mul_deriv(typename AR::C *s, int N) {

@@ -246,10 +246,11 @@ __device__ __forceinline__ void stockham_pass(cdf *s, int N, int L, bool pad_in,
 // complete); the routine ends with a barrier.
 constexpr int FFT_STOCKHAM_MAXN = 2048;
 
-// not inlined: the kernels call it 5-7 times and one copy of its code keeps the
-// instruction cache warm
-static __device__ __noinline__ void block_fft_stockham(cdf *s, int N, int logN, const cdf *__restrict__ twd,
-                                                bool inverse) {
+// not inlined: the kernels call it 5-7 times and one copy of each direction's
+// code keeps the instruction cache warm; one function per direction keeps the
+// register footprint of each to its own passes
+template <bool INV>
+static __device__ __noinline__ void stockham_fft(cdf *s, int N, int logN, const cdf *__restrict__ twd) {
     const int n4 = (logN % 3 == 0) ? 0 : (logN % 3 == 2 ? 1 : 2);   // radix-4 passes
     const int n8 = (logN - 2 * n4) / 3;                              // radix-8 passes
     const int npass = n4 + n8;
@@ -257,15 +258,20 @@ static __device__ __noinline__ void block_fft_stockham(cdf *s, int N, int logN, 
     for (int pi = 0; pi < npass; ++pi) {
         const bool r8 = pi < n8;
         const bool pin = pi > 0, pout = pi < npass - 1;
-        if (inverse) {
-            if (r8) stockham_pass<true, 8>(s, N, L, pin, pout, twd);
-            else stockham_pass<true, 4>(s, N, L, pin, pout, twd);
-        } else {
-            if (r8) stockham_pass<false, 8>(s, N, L, pin, pout, twd);
-            else stockham_pass<false, 4>(s, N, L, pin, pout, twd);
-        }
+        if (r8)
+            stockham_pass<INV, 8>(s, N, L, pin, pout, twd);
+        else
+            stockham_pass<INV, 4>(s, N, L, pin, pout, twd);
         L *= r8 ? 8 : 4;
     }
+}
+
+static __device__ __forceinline__ void block_fft_stockham(cdf *s, int N, int logN, const cdf *__restrict__ twd,
+                                                          bool inverse) {
+    if (inverse)
+        stockham_fft<true>(s, N, logN, twd);
+    else
+        stockham_fft<false>(s, N, logN, twd);
 }
 
 }  // namespace dfl

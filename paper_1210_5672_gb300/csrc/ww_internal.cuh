@@ -156,7 +156,9 @@ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -
 // In-place complex FFT of length N = 2^logN held in shared memory, computed by
 // the whole thread block (radix-2, decimation in time after a bit-reversal
 // permutation).  Forward sign exp(-2 pi i jk/N); the inverse is unscaled.
-// Callers synchronise before and after.
+// Callers synchronise before and after.  tw may point to global or shared
+// memory (kernels stage the table into shared memory), so it is read with
+// plain loads, never the global-only __ldg.
 // --------------------------------------------------------------------------
 __device__ __forceinline__ void block_fft(double2 *s, int N, int logN, const double2 *__restrict__ tw,
                                           bool inverse) {
@@ -177,7 +179,7 @@ __device__ __forceinline__ void block_fft(double2 *s, int N, int logN, const dou
             int k = b & (half - 1);
             int i0 = ((b >> lh) << (lh + 1)) + k;
             int i1 = i0 + half;
-            double2 w = __ldg(&tw[k << tshift]);
+            double2 w = tw[k << tshift];
             if (inverse) w.y = -w.y;
             double2 v = cmul(s[i1], w);
             double2 u = s[i0];
@@ -203,6 +205,9 @@ __device__ __forceinline__ double filt36(int k, int N) {
 // --------------------------------------------------------------------------
 // spectral (ww_spectral.cu)
 int prepare_spectral(Ctx *c);                        // shared-memory limits of the FFT kernels
+// raise a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes` (never lowers it: contexts of different sizes share kernels)
+int raise_smem(const void *kernel, size_t bytes);
 int launch_base_geometry(Ctx *c, const double *eta, const double *phi, int with_phi);
 int launch_gamma(Ctx *c, int col0, int ncols, bool fp64 = false);   // Gam = D M, Gout = 1/2 H D M (columns col0..);
                                                      // fp64: FP64 transforms also in the mixed form

@@ -473,12 +473,13 @@ __global__ void __launch_bounds__(SEG_THREADS, 2) k_col_rhs_mesh(
     const double *__restrict__ Gout, const void *__restrict__ uT, const void *__restrict__ vT,
     const void *__restrict__ wT, const void *__restrict__ einvT, const double *__restrict__ einv,
     const double *__restrict__ vy, const double *__restrict__ pw, const double *__restrict__ Fbase, double g,
-    double tau, int N, int logN, const void *__restrict__ tw, const void *__restrict__ filt, double *Y, double *Ys,
+    double tau, int N, int logN, const void *__restrict__ tw_table, const void *__restrict__ filt, double *Y, double *Ys,
     double *K, size_t ks, int st, int S, const double *__restrict__ ta, const double *__restrict__ tb,
     const double *__restrict__ cvec, double theta, int steps, int *status) {
     using R = typename AR::R;
     extern __shared__ __align__(16) unsigned char smraw[];
     typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw), *z = s + AR::cap(N);
+    const void *tw = stage_twiddles<AR>(tw_table, z + AR::cap(N), N);   // read after the first barrier
     __shared__ double red[33];
     const int c = blockIdx.x + 1;
     double *Yc = Y + (size_t)c * 2 * N, *Ysc = Ys + (size_t)c * 2 * N, *Kc = K + (size_t)c * 2 * N;
@@ -908,7 +909,7 @@ int seg_stage(Ctx *c, Seg *g, int st, const double *cvec) {
     // The variational transforms of a segment run in FP64 in both forms: on the
     // mesh the double-float transforms' rounding, amplified in the small T
     // column, reached ten times the oracle's own rounding sensitivity.
-    k_col_rhs_mesh<ArF64><<<c->nc, SEG_THREADS, 2 * sizeof(double2) * N, c->stream>>>(
+    k_col_rhs_mesh<ArF64><<<c->nc, SEG_THREADS, fft_smem_bytes<ArF64>(c->N, 2), c->stream>>>(
         c->Gout, c->ux, c->vy, c->w3, g->einv, g->einv, c->vy, g->pw, c->Fbase, c->g, c->tau, c->N, c->logN, c->tw,
         c->filt_d, c->Y, c->Ys, g->K, ks, st, g->S, g->d_a, g->d_b, cvec, g->theta, g->steps, c->status);
     WW_CUDA_TRY(cudaGetLastError());
@@ -962,12 +963,12 @@ int seg_adj_step(Ctx *c, Seg *g, const double *cvec) {
 int seg_prepare(Ctx *c) {
     const size_t N = (size_t)c->N;
     const size_t two = 2 * sizeof(double2) * N;
-    WW_CUDA_TRY(cudaFuncSetAttribute(k_geom_mesh, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two));
-    WW_CUDA_TRY(cudaFuncSetAttribute(k_base_rhs_mesh, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(two / 2)));
-    WW_CUDA_TRY(cudaFuncSetAttribute(k_col_rhs_mesh<ArF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two));
-    WW_CUDA_TRY(cudaFuncSetAttribute(k_seg_adj_begin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(two / 2)));
-    WW_CUDA_TRY(cudaFuncSetAttribute(k_seg_adj_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two));
-    WW_CUDA_TRY(cudaFuncSetAttribute(k_seg_adj_dtn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(two / 2)));
+    WW_TRY(raise_smem(reinterpret_cast<const void *>(k_geom_mesh), two));
+    WW_TRY(raise_smem(reinterpret_cast<const void *>(k_base_rhs_mesh), two / 2));
+    WW_TRY(raise_smem(reinterpret_cast<const void *>(k_col_rhs_mesh<ArF64>), fft_smem_bytes<ArF64>(c->N, 2)));
+    WW_TRY(raise_smem(reinterpret_cast<const void *>(k_seg_adj_begin), two / 2));
+    WW_TRY(raise_smem(reinterpret_cast<const void *>(k_seg_adj_local), two));
+    WW_TRY(raise_smem(reinterpret_cast<const void *>(k_seg_adj_dtn), two / 2));
     return WW_OK;
 }
 

@@ -9,6 +9,10 @@
 // d/dx, H d/dx = |k| and the filter are real operators, two real signals a, b
 // are transformed together as one complex signal a + i b and come back as
 // (L a) + i (L b) -- no even/odd separation is needed anywhere.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "ww_ar.cuh"
 
 namespace ww {
@@ -75,10 +79,11 @@ __global__ void k_base_geometry(const double *__restrict__ eta_in, const double 
 // gamma = mu' and 1/2 H gamma for pairs of columns of M (Eq. G)
 // ------------------------------------------------------------------------
 template <class AR>
-__global__ void __launch_bounds__(FFT_THREADS, 2) k_gamma(const double *__restrict__ M, int ncols, int N, int logN, const void *__restrict__ tw,
+__global__ void __launch_bounds__(FFT_THREADS, 2) k_gamma(const double *__restrict__ M, int ncols, int N, int logN, const void *__restrict__ tw_table,
                         double *Gam, double *Gout) {
     extern __shared__ __align__(16) unsigned char smraw[];
     typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw), *z = s + AR::cap(N);
+    const void *tw = stage_twiddles<AR>(tw_table, z + AR::cap(N), N);   // read after the first barrier
     const int ca = 2 * blockIdx.x, cb = ca + 1;
     const bool hasb = cb < ncols;
     const double *ma = M + (size_t)ca * N, *mb = M + (size_t)cb * N;
@@ -253,11 +258,12 @@ template <class AR>
 __global__ void __launch_bounds__(FFT_THREADS, 2) k_col_rhs(const double *__restrict__ Gout, const void *__restrict__ uT, const void *__restrict__ vT,
                           const void *__restrict__ wT, const double *__restrict__ vy,
                           const double *__restrict__ Fbase, double g, double tau, int N, int logN,
-                          const void *__restrict__ tw, const void *__restrict__ filt, double *Y, double *Ys,
+                          const void *__restrict__ tw_table, const void *__restrict__ filt, double *Y, double *Ys,
                           double *Acc, int st, const double *__restrict__ cvec, int steps, int *status) {
     using R = typename AR::R;
     extern __shared__ __align__(16) unsigned char smraw[];
     typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw), *z = s + AR::cap(N);
+    const void *tw = stage_twiddles<AR>(tw_table, z + AR::cap(N), N);   // read after the first barrier
     const int c = blockIdx.x + 1;
     double *Yc = Y + (size_t)c * 2 * N, *Ysc = Ys + (size_t)c * 2 * N, *Accc = Acc + (size_t)c * 2 * N;
     const double *Gpsi = Gout + (size_t)c * N;
@@ -394,8 +400,7 @@ __global__ void k_copy_phi0(const double *__restrict__ Ys, int N, double *M) {
 
 template <typename K>
 int set_smem(K kernel, size_t bytes) {
-    if (bytes > 48 * 1024) WW_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    return WW_OK;
+    return raise_smem(reinterpret_cast<const void *>(kernel), bytes);
 }
 
 }  // namespace
@@ -403,15 +408,28 @@ int set_smem(K kernel, size_t bytes) {
 // ==========================================================================
 // host launchers
 // ==========================================================================
+int raise_smem(const void *kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return WW_OK;   // within the default limit
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> raised;   // (device, kernel) -> limit set
+    int dev = 0;
+    WW_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &cur = raised[{dev, kernel}];
+    if (bytes <= cur) return WW_OK;
+    WW_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
+    return WW_OK;
+}
+
 int prepare_spectral(Ctx *c) {
     const size_t one = sizeof(double2) * c->N, two = 2 * one;
-    const size_t two_df = 2 * sizeof(double2) * (size_t)ArDF::cap(c->N);
     WW_TRY(set_smem(k_base_geometry<ArF64>, two));
     WW_TRY(set_smem(k_base_rhs<ArF64>, one));
-    WW_TRY(set_smem(k_gamma<ArF64>, two));
-    WW_TRY(set_smem(k_col_rhs<ArF64>, two));
-    WW_TRY(set_smem(k_gamma<ArDF>, two_df));
-    WW_TRY(set_smem(k_col_rhs<ArDF>, two_df));
+    WW_TRY(set_smem(k_gamma<ArF64>, fft_smem_bytes<ArF64>(c->N, 2)));
+    WW_TRY(set_smem(k_col_rhs<ArF64>, fft_smem_bytes<ArF64>(c->N, 2)));
+    WW_TRY(set_smem(k_gamma<ArDF>, fft_smem_bytes<ArDF>(c->N, 2)));
+    WW_TRY(set_smem(k_col_rhs<ArDF>, fft_smem_bytes<ArDF>(c->N, 2)));
     return WW_OK;
 }
 
@@ -435,13 +453,12 @@ int launch_base_geometry(Ctx *c, const double *eta, const double *phi, int with_
 
 int launch_gamma(Ctx *c, int col0, int ncols, bool fp64) {
     if (col0 == 0 && ncols == 1 && cbase_ok(c)) return launch_cbase_gamma(c);
-    size_t sm = 2 * sizeof(double2) * c->N;
     size_t off = (size_t)col0 * c->N;
     if (use_df(c) && col0 >= 1 && !fp64)
-        k_gamma<ArDF><<<(ncols + 1) / 2, FFT_THREADS, 2 * sizeof(double2) * (size_t)ArDF::cap(c->N), c->stream>>>(c->M + off, ncols, c->N, c->logN, c->twd,
+        k_gamma<ArDF><<<(ncols + 1) / 2, FFT_THREADS, fft_smem_bytes<ArDF>(c->N, 2), c->stream>>>(c->M + off, ncols, c->N, c->logN, c->twd,
                                                                       c->Gam + off, c->Gout + off);
     else
-        k_gamma<ArF64><<<(ncols + 1) / 2, FFT_THREADS, sm, c->stream>>>(c->M + off, ncols, c->N, c->logN, c->tw,
+        k_gamma<ArF64><<<(ncols + 1) / 2, FFT_THREADS, fft_smem_bytes<ArF64>(c->N, 2), c->stream>>>(c->M + off, ncols, c->N, c->logN, c->tw,
                                                                        c->Gam + off, c->Gout + off);
     WW_CUDA_TRY(cudaGetLastError());
     return WW_OK;
@@ -475,7 +492,7 @@ int launch_base_rhs(Ctx *c, int stage, const double *cvec) {
 int launch_col_rhs(Ctx *c, int stage, const double *cvec) {
     if (c->nc <= 0) return WW_OK;
     const bool df = use_df(c);
-    const size_t sm = 2 * sizeof(double2) * (size_t)(df ? ArDF::cap(c->N) : c->N);
+    const size_t sm = df ? fft_smem_bytes<ArDF>(c->N, 2) : fft_smem_bytes<ArF64>(c->N, 2);
     auto kern = df ? k_col_rhs<ArDF> : k_col_rhs<ArF64>;
     kern<<<c->nc, FFT_THREADS, sm, c->stream>>>(
         c->Gout, df ? (const void *)c->uxd : (const void *)c->ux, df ? (const void *)c->vyd : (const void *)c->vy,

@@ -297,3 +297,34 @@ def test_one_uniform_rk4_segment_gradient_is_the_plain_adjoint(ww):
         fs, gs, jtr, _ = gpu_grad_segments(ww, [(N, steps, 1.0, 1.0, 1)], "rk4", n, c, precision)
         assert abs(fs - plain[0]) <= 1e-13 * abs(plain[0])
         assert np.linalg.norm(gs - plain[1]) / np.linalg.norm(plain[1]) < 1e-12
+
+
+def test_contexts_created_largest_first(ww):
+    """Kernels shared by contexts of different sizes keep the largest
+    shared-memory limit any context asked for: a 2048-point segment set up
+    before a 512-point one still runs, with the same result as in the other
+    order of creation."""
+    import torch
+    n = 4
+    segs = [(512, 2, 0.5, 1.0, 0), (2048, 2, 0.5, 0.4, 0)]
+    w = W.Workload("seg_order", N=512, n=n, steps=1, amp=0.05)
+    c, _ = W.coefficients(w)
+    c[0] *= 1.0 / 256   # a short shot: two DOP853 steps stay stable on the 2048-point mesh
+    results = []
+    for order in ((0, 1), (1, 0)):
+        made = {}
+        try:
+            for i in order:
+                M, steps, th, rho, ctr = segs[i]
+                made[i] = ww.Context(M, n, steps=steps, precision=ww.WW_FP64)
+                ww.set_segment(made[i], steps, th, rho, ctr, "dop853")
+            ctxs = [made[0], made[1]]
+            r = torch.empty(2048, dtype=torch.float64, device="cuda")
+            J = torch.empty(n + 1, 2048, dtype=torch.float64, device="cuda")
+            f = torch.empty(1, dtype=torch.float64, device="cuda")
+            ww.shoot_jacobian_segments(ctxs, dev(c), r, J, f)
+            results.append((r.cpu().numpy(), J.cpu().numpy()))
+        finally:
+            for x in made.values():
+                x.close()
+    assert np.array_equal(results[0][0], results[1][0]) and np.array_equal(results[0][1], results[1][1])
