@@ -33,6 +33,13 @@ struct ArF64 {
     }
     // points of shared memory one transform needs
     static __host__ __device__ __forceinline__ int cap(int N) { return N; }
+    // the twiddle table the transforms read, staged into shared memory: the
+    // half table exp(-2 pi i m / N), m < N/2, as it is
+    static __host__ __device__ __forceinline__ int table_entries(int N, int) { return N >> 1; }
+    static __device__ __forceinline__ void stage(const void *tw, C *dst, int N, int) {
+        const C *src = static_cast<const C *>(tw);
+        for (int j = threadIdx.x; j < (N >> 1); j += blockDim.x) dst[j] = src[j];
+    }
     static __device__ __forceinline__ C scalef(C z, float f) { return cscale(z, (double)f); }
     static __device__ __forceinline__ C ikscale(C z, int k, float p2) { return cscale(times_ik(z, k), (double)p2); }
     static __device__ __forceinline__ C add(C a, C b) { return cadd(a, b); }
@@ -68,6 +75,19 @@ struct ArDF {
     static __host__ __device__ __forceinline__ int cap(int N) {
         return (N >= 16 && N <= dfl::FFT_STOCKHAM_MAXN) ? N + N / 8 : N;
     }
+    // the twiddles the transforms read, staged into shared memory: the
+    // Stockham passes' per-pass tables (conflict-free reads), else the half
+    // table exp(-2 pi i m / N), m < N/2, as it is
+    static __host__ __device__ __forceinline__ int table_entries(int N, int logN) {
+        return (N >= 16 && N <= dfl::FFT_STOCKHAM_MAXN) ? dfl::stockham_table_size(logN) : (N >> 1);
+    }
+    static __device__ __forceinline__ void stage(const void *tw, C *dst, int N, int logN) {
+        const C *src = static_cast<const C *>(tw);
+        if (N >= 16 && N <= dfl::FFT_STOCKHAM_MAXN)
+            dfl::build_stockham_twiddles(src, dst, N, logN);
+        else
+            for (int j = threadIdx.x; j < (N >> 1); j += blockDim.x) dst[j] = src[j];
+    }
     static __device__ __forceinline__ C scalef(C z, float f) { return dfl::cscalef(z, f); }
     static __device__ __forceinline__ C ikscale(C z, int k, float p2) { return dfl::cscalef(dfl::times_ik(z, k), p2); }
     static __device__ __forceinline__ C add(C a, C b) { return dfl::cadd(a, b); }
@@ -91,22 +111,24 @@ struct ArDF {
     static __device__ __forceinline__ C addr(C z, R a, R b) { return dfl::make(dfl::add(dfl::re(z), a), dfl::add(dfl::im(z), b)); }
 };
 
-// The transforms' twiddle table (N/2 complex entries, the same element type as
-// the transform's data) copied into shared memory at dst, right after the
-// kernel's work arrays: the passes then read their twiddles at shared-memory
-// latency instead of through L1.  The caller synchronises before the first
-// transform; the returned pointer replaces the global table.
+// The transforms' twiddles (built from the global half table tw, the same
+// element type as the transform's data) staged into shared memory at dst,
+// right after the kernel's work arrays: the passes then read them at
+// shared-memory latency instead of through L1.  The caller synchronises
+// before the first transform; the returned pointer replaces tw in every
+// transform of the kernel.
 template <class AR>
-__device__ __forceinline__ const void *stage_twiddles(const void *tw, typename AR::C *dst, int N) {
-    const typename AR::C *src = static_cast<const typename AR::C *>(tw);
-    for (int j = threadIdx.x; j < (N >> 1); j += blockDim.x) dst[j] = src[j];
+__device__ __forceinline__ const void *stage_twiddles(const void *tw, typename AR::C *dst, int N, int logN) {
+    AR::stage(tw, dst, N, logN);
     return dst;
 }
 
 // bytes of shared memory of a kernel with `arrays` transform buffers and the staged twiddles
 template <class AR>
 __host__ __forceinline__ size_t fft_smem_bytes(int N, int arrays) {
-    return sizeof(typename AR::C) * ((size_t)arrays * AR::cap(N) + (size_t)(N >> 1));
+    int logN = 0;
+    while ((1 << logN) < N) ++logN;
+    return sizeof(typename AR::C) * ((size_t)arrays * AR::cap(N) + (size_t)AR::table_entries(N, logN));
 }
 
 // s <- s * (ik) / N (Nyquist zero)

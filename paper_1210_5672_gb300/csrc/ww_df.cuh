@@ -195,13 +195,16 @@ __device__ __forceinline__ cdf twiddle(const cdf *__restrict__ twd, int m, int h
     return w;
 }
 
+// The twiddles of one pass with sub-transform length L, W_{L R}^{k r} for
+// r = 1..R-1 and k < L, stored row by row: tp[(r - 1) L + k] (forward sign).
+// Threads of a warp read consecutive k, i.e. consecutive addresses, so the
+// reads from shared memory are free of bank conflicts.
 template <bool INV, int R>
 __device__ __forceinline__ void stockham_pass(cdf *s, int N, int L, bool pad_in, bool pad_out,
-                                              const cdf *__restrict__ twd) {
+                                              const cdf *tp) {
     // each thread holds up to MAXC groups of R points (N <= 2048 with 256 threads)
     constexpr int MAXC = (R == 8) ? 1 : 2;
-    const int NR = N / R, halfN = N >> 1;
-    const int tstride = N / (L * R);   // W_{L R}^{k r} = W_N^{k r N / (L R)}
+    const int NR = N / R;
     cdf v[MAXC][R];
 #pragma unroll
     for (int c = 0; c < MAXC; ++c) {
@@ -215,7 +218,14 @@ __device__ __forceinline__ void stockham_pass(cdf *s, int N, int L, bool pad_in,
             const int k = j % L;
             if (k != 0) {
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[c][r] = cmul(v[c][r], twiddle<INV>(twd, k * r * tstride, halfN));
+                for (int r = 1; r < R; ++r) {
+                    cdf w = tp[(r - 1) * L + k];
+                    if (INV) {
+                        w.ih = -w.ih;
+                        w.il = -w.il;
+                    }
+                    v[c][r] = cmul(v[c][r], w);
+                }
             }
             if (R == 8)
                 dft8<INV>(v[c]);
@@ -240,8 +250,9 @@ __device__ __forceinline__ void stockham_pass(cdf *s, int N, int L, bool pad_in,
 }
 
 // In-place FFT of s[0..N) (natural order in and out), 16 <= N = 2^logN <= 2048
-// and blockDim.x == 256 (FFT_STOCKHAM_MAXN), s with room for N + N/8 points;
-// unscaled inverse.  Radix-8 passes, and one or two radix-4 passes when
+// and blockDim.x == 256 (FFT_STOCKHAM_MAXN), s with room for N + N/8 points,
+// twiddles from the per-pass tables of build_stockham_twiddles; unscaled
+// inverse.  Radix-8 passes, and one or two radix-4 passes when
 // log2 N is not a multiple of 3.  Callers synchronise before (the data is
 // complete); the routine ends with a barrier.
 constexpr int FFT_STOCKHAM_MAXN = 2048;
@@ -249,29 +260,63 @@ constexpr int FFT_STOCKHAM_MAXN = 2048;
 // not inlined: the kernels call it 5-7 times and one copy of each direction's
 // code keeps the instruction cache warm; one function per direction keeps the
 // register footprint of each to its own passes
+// the passes of a Stockham transform of 2^logN points: radix-8 ones, then n4 radix-4
+__host__ __device__ __forceinline__ int stockham_n4(int logN) { return (logN % 3 == 0) ? 0 : (logN % 3 == 2 ? 1 : 2); }
+__host__ __device__ __forceinline__ int stockham_n8(int logN) { return (logN - 2 * stockham_n4(logN)) / 3; }
+
+// entries of the per-pass twiddle tables of a transform of N = 2^logN points:
+// (R - 1) L per pass with sub-transform length L (fewer than N in all)
+__host__ __device__ __forceinline__ int stockham_table_size(int logN) {
+    const int n4 = stockham_n4(logN), n8 = stockham_n8(logN);
+    int L = 1, total = 0;
+    for (int pi = 0; pi < n4 + n8; ++pi) {
+        const int R = pi < n8 ? 8 : 4;
+        total += (R - 1) * L;
+        L *= R;
+    }
+    return total;
+}
+
+// the per-pass tables (stockham_pass) built by the whole block from the
+// half table twd[m] = exp(-2 pi i m / N), m < N/2 (global memory)
+__device__ __forceinline__ void build_stockham_twiddles(const cdf *__restrict__ twd, cdf *dst, int N, int logN) {
+    const int n4 = stockham_n4(logN), n8 = stockham_n8(logN), halfN = N >> 1;
+    int L = 1;
+    for (int pi = 0; pi < n4 + n8; ++pi) {
+        const int R = pi < n8 ? 8 : 4;
+        const int tstride = N / (L * R);   // W_{L R}^{k r} = W_N^{k r N / (L R)}
+        for (int e = threadIdx.x; e < (R - 1) * L; e += blockDim.x) {
+            const int r = e / L + 1, k = e % L;
+            dst[e] = twiddle<false>(twd, k * r * tstride, halfN);
+        }
+        dst += (R - 1) * L;
+        L *= R;
+    }
+}
+
+// tp: the per-pass tables of build_stockham_twiddles (shared memory)
 template <bool INV>
-static __device__ __noinline__ void stockham_fft(cdf *s, int N, int logN, const cdf *__restrict__ twd) {
-    const int n4 = (logN % 3 == 0) ? 0 : (logN % 3 == 2 ? 1 : 2);   // radix-4 passes
-    const int n8 = (logN - 2 * n4) / 3;                              // radix-8 passes
+static __device__ __noinline__ void stockham_fft(cdf *s, int N, int logN, const cdf *tp) {
+    const int n4 = stockham_n4(logN), n8 = stockham_n8(logN);
     const int npass = n4 + n8;
     int L = 1;
     for (int pi = 0; pi < npass; ++pi) {
         const bool r8 = pi < n8;
         const bool pin = pi > 0, pout = pi < npass - 1;
         if (r8)
-            stockham_pass<INV, 8>(s, N, L, pin, pout, twd);
+            stockham_pass<INV, 8>(s, N, L, pin, pout, tp);
         else
-            stockham_pass<INV, 4>(s, N, L, pin, pout, twd);
+            stockham_pass<INV, 4>(s, N, L, pin, pout, tp);
+        tp += (r8 ? 7 : 3) * L;
         L *= r8 ? 8 : 4;
     }
 }
 
-static __device__ __forceinline__ void block_fft_stockham(cdf *s, int N, int logN, const cdf *__restrict__ twd,
-                                                          bool inverse) {
+static __device__ __forceinline__ void block_fft_stockham(cdf *s, int N, int logN, const cdf *tp, bool inverse) {
     if (inverse)
-        stockham_fft<true>(s, N, logN, twd);
+        stockham_fft<true>(s, N, logN, tp);
     else
-        stockham_fft<false>(s, N, logN, twd);
+        stockham_fft<false>(s, N, logN, tp);
 }
 
 }  // namespace dfl

@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(SEG_THREADS, 2) k_col_rhs_mesh(
     using R = typename AR::R;
     extern __shared__ __align__(16) unsigned char smraw[];
     typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw), *z = s + AR::cap(N);
-    const void *tw = stage_twiddles<AR>(tw_table, z + AR::cap(N), N);   // read after the first barrier
+    const void *tw = stage_twiddles<AR>(tw_table, z + AR::cap(N), N, logN);   // read after the first barrier
     __shared__ double red[33];
     const int c = blockIdx.x + 1;
     double *Yc = Y + (size_t)c * 2 * N, *Ysc = Ys + (size_t)c * 2 * N, *Kc = K + (size_t)c * 2 * N;

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) k_gamma(const double *__restri
                         double *Gam, double *Gout) {
     extern __shared__ __align__(16) unsigned char smraw[];
     typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw), *z = s + AR::cap(N);
-    const void *tw = stage_twiddles<AR>(tw_table, z + AR::cap(N), N);   // read after the first barrier
+    const void *tw = stage_twiddles<AR>(tw_table, z + AR::cap(N), N, logN);   // read after the first barrier
     const int ca = 2 * blockIdx.x, cb = ca + 1;
     const bool hasb = cb < ncols;
     const double *ma = M + (size_t)ca * N, *mb = M + (size_t)cb * N;
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) k_col_rhs(const double *__rest
     using R = typename AR::R;
     extern __shared__ __align__(16) unsigned char smraw[];
     typename AR::C *s = reinterpret_cast<typename AR::C *>(smraw), *z = s + AR::cap(N);
-    const void *tw = stage_twiddles<AR>(tw_table, z + AR::cap(N), N);   // read after the first barrier
+    const void *tw = stage_twiddles<AR>(tw_table, z + AR::cap(N), N, logN);   // read after the first barrier
     const int c = blockIdx.x + 1;
     double *Yc = Y + (size_t)c * 2 * N, *Ysc = Ys + (size_t)c * 2 * N, *Accc = Acc + (size_t)c * 2 * N;
     const double *Gpsi = Gout + (size_t)c * N;
