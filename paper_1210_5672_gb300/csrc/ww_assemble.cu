@@ -50,6 +50,9 @@ __device__ __forceinline__ double recip_nr(double d) {
     return fma(x, fma(-d, x, 1.0), x);
 }
 
+// biased exponent field of x (0 for zero), the scale the digit splits take per row
+__device__ __forceinline__ int bexp_of(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+
 // cot((x + i y)/2) with cx = cos x, sx = sin x, ch = cosh y, sh = sinh y
 __device__ __forceinline__ double2 cot_half(double cx, double sx, double ch, double sh) {
     if (cx >= 0.0) {
@@ -184,8 +187,10 @@ __global__ void __launch_bounds__(256) k_assemble_sym(const double *__restrict__
                                                       const double *__restrict__ eta_xx, const double *__restrict__ E,
                                                       const double *__restrict__ Einv,
                                                       const double *__restrict__ cs, const double *__restrict__ cot0,
-                                                      int N, int trans, double *A, double *G) {
+                                                      int N, int trans, double *A, double *G, int *emaxK,
+                                                      int *emaxG) {
     __shared__ double tA[ST][ST + 1], tG[ST][ST + 1];
+    __shared__ int redK[8][ST], redG[8][ST];   // row exponent maxima per warp (emaxK != NULL)
     // triangular tile index -> (I, J), I <= J
     const int T = N / ST;
     int b = blockIdx.x, I = 0;
@@ -198,6 +203,7 @@ __global__ void __launch_bounds__(256) k_assemble_sym(const double *__restrict__
     const int il = threadIdx.x & 31;
     const int i = I * ST + il;
     const double ei = eta[i], exi = eta_x[i], Ei = E[i], Eii = Einv[i];
+    int mK = 0, mG = 0;   // this thread's row exponent maxima
     for (int jl = threadIdx.x >> 5; jl < ST; jl += 8) {
         const int j = J * ST + jl;
         const double ej = eta[j], exj = eta_x[j], Ej = E[j], Eij = Einv[j];
@@ -229,19 +235,58 @@ __global__ void __launch_bounds__(256) k_assemble_sym(const double *__restrict__
             gji = tg;
         }
         const size_t idx = (size_t)j * N + i;
-        A[idx] = fma(h, kij, i == j ? 0.5 : 0.0);
-        G[idx] = h * gij;
+        const double aij = fma(h, kij, i == j ? 0.5 : 0.0), gv = h * gij;
+        A[idx] = aij;
+        G[idx] = gv;
         tA[jl][il] = fma(h, kji, i == j ? 0.5 : 0.0);
         tG[jl][il] = h * gji;
+        if (emaxK) {
+            mK = max(mK, bexp_of(i == j ? aij - 0.5 : aij));   // K = A - I/2, as the digit split shifts it
+            mG = max(mG, bexp_of(gv));
+        }
+    }
+    const int warp = threadIdx.x >> 5;
+    if (emaxK) {   // rows I*ST + il: this tile's columns
+        redK[warp][il] = mK;
+        redG[warp][il] = mG;
+        __syncthreads();
+        if (threadIdx.x < ST) {
+            int k = redK[0][threadIdx.x], g = redG[0][threadIdx.x];
+            for (int w = 1; w < 8; ++w) {
+                k = max(k, redK[w][threadIdx.x]);
+                g = max(g, redG[w][threadIdx.x]);
+            }
+            atomicMax(&emaxK[I * ST + threadIdx.x], k);
+            atomicMax(&emaxG[I * ST + threadIdx.x], g);
+        }
     }
     if (I == J) return;   // the diagonal tile is complete (uniform branch: no barrier skipped unevenly)
     __syncthreads();
     // transposed tile: entry (j, i) at A[i * N + j]; consecutive threads walk j
+    const int jl2 = threadIdx.x & 31;
+    mK = 0;
+    mG = 0;
     for (int il2 = threadIdx.x >> 5; il2 < ST; il2 += 8) {
-        const int jl2 = threadIdx.x & 31;
         const size_t idx = (size_t)(I * ST + il2) * N + J * ST + jl2;
-        A[idx] = tA[jl2][il2];
-        G[idx] = tG[jl2][il2];
+        const double a = tA[jl2][il2], g = tG[jl2][il2];
+        A[idx] = a;
+        G[idx] = g;
+        mK = max(mK, bexp_of(a));   // off the diagonal (I < J): no shift
+        mG = max(mG, bexp_of(g));
+    }
+    if (emaxK) {   // rows J*ST + jl2: the mirrored tile's columns
+        redK[warp][jl2] = mK;
+        redG[warp][jl2] = mG;
+        __syncthreads();
+        if (threadIdx.x < ST) {
+            int k = redK[0][threadIdx.x], g = redG[0][threadIdx.x];
+            for (int w = 1; w < 8; ++w) {
+                k = max(k, redK[w][threadIdx.x]);
+                g = max(g, redG[w][threadIdx.x]);
+            }
+            atomicMax(&emaxK[J * ST + threadIdx.x], k);
+            atomicMax(&emaxG[J * ST + threadIdx.x], g);
+        }
     }
 }
 
@@ -251,11 +296,21 @@ int launch_assemble(Ctx *c) {
     if (c->N % ST == 0) {
         const int T = c->N / ST;
         auto kern = c->deep ? k_assemble_sym<true> : k_assemble_sym<false>;
+        // the mixed form's digit splits of K and G need each row's largest
+        // exponent: taken here, while the entries are in registers
+        const bool emax = c->emax_K != nullptr && !c->one_col;
+        if (emax) {
+            WW_CUDA_TRY(cudaMemsetAsync(c->emax_K, 0, sizeof(int) * c->N, c->stream));
+            WW_CUDA_TRY(cudaMemsetAsync(c->emax_G, 0, sizeof(int) * c->N, c->stream));
+        }
         kern<<<T * (T + 1) / 2, 256, 0, c->stream>>>(c->eta, c->eta_x, c->eta_xx, c->E, c->Einv, c->cs,
-                                                     c->cs + 2 * c->N, c->N, c->trans, c->A, c->G);
+                                                     c->cs + 2 * c->N, c->N, c->trans, c->A, c->G,
+                                                     emax ? c->emax_K : nullptr, emax ? c->emax_G : nullptr);
+        c->emax_ready = emax;
         WW_CUDA_TRY(cudaGetLastError());
         return WW_OK;
     }
+    c->emax_ready = false;
     dim3 grid((c->N + ASM_TI - 1) / ASM_TI, (c->N + ASM_TJ - 1) / ASM_TJ);
     k_assemble<<<grid, ASM_TI, 0, c->stream>>>(c->eta, c->eta_x, c->eta_xx, c->E, c->Einv, c->cs, c->cs + 2 * c->N,
                                                c->N, c->deep ? 1 : 0, c->trans, c->A, c->G);

@@ -113,6 +113,8 @@ struct Ctx {
     int cur_stage;            // RK stage (0..3) whose work is being issued (phase timing)
     int ckpt_every;           // adjoint: checkpoint the base state every ckpt_every steps (0: keep every record)
     ww_schedule sch;          // tile shapes and stage schedule (ww_set_schedule / ww_autotune)
+    int *emax_K, *emax_G;     // WW_MIXED: row exponent maxima of K = A - I/2 and G (the digit splits' scales)
+    bool emax_ready;          // the last assembly issued also filled emax_K and emax_G
     size_t dev_bytes;         // device memory this context allocated
     ww_stats stats;
     Mixed *mx;

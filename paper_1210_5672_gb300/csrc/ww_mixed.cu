@@ -52,6 +52,8 @@ int ozaki_gemm(cudaStream_t s, const __nv_bfloat16 *Ad, const double *sa, const 
                int M, int Nn, int K, int mode, double *C, int ldc, const double *Psi, int ldpsi, const double *Mh,
                int ldm, unsigned long long *colmax, int *err, const int *skip, __nv_bfloat16 *rslc = nullptr,
                int nd = 7);
+int ozaki_digits_rows_emax(cudaStream_t s, const double *X, int ld, int rows, int K, float diag_shift,
+                           const int *emax, double *scale, __nv_bfloat16 *dst, const int *skip);
 int ozaki_digits_cols(cudaStream_t s, const double *X, int ld, int ncols, int K, double *scale, __nv_bfloat16 *dst,
                       unsigned long long *zero_cm, const int *skip);
 
@@ -312,6 +314,8 @@ int mixed_create(Ctx *c) {
     }
     MA(m->Ke, N);
     MA(m->Ge, N);
+    c->emax_K = m->Ke;
+    c->emax_G = m->Ge;
     MA(m->Rd, (7 * NC + 256) * N);   // + rows so that a TMA box never leaves the buffer
     MA(m->Rs, NC);
     MA(m->Re, NC);
@@ -399,7 +403,14 @@ int mixed_setup(Ctx *c, int fresh, int update) {
     }
     // an update left out on the device leaves this stage's rows of X to a slice of X
     if (skip) WW_TRY(tc_slice_f32(s, m->X, N, N, N, 1, 0.f, 2, m->Xrow[q], nullptr, skip, 1));
+    const bool emax_ready = c->emax_ready;
+    c->emax_ready = false;
     if (c->one_col) return WW_OK;   // the narrow solves and products read A and G directly
+    if (emax_ready) {   // the assembly already took the row exponent maxima
+        WW_TRY(ozaki_digits_rows_emax(s, c->A, N, N, N, 0.5f, m->Ke, m->Ks[q], m->Kd[q], nullptr));   // K = A - I/2
+        WW_TRY(ozaki_digits_rows_emax(s, c->G, N, N, N, 0.f, m->Ge, m->Gs[q], m->Gd[q], nullptr));
+        return WW_OK;
+    }
     WW_TRY(ozaki_digits(s, c->A, N, N, N, 0, 0.5f, m->Ke, m->Ks[q], m->Kd[q], nullptr));   // K = A - I/2
     WW_TRY(ozaki_digits(s, c->G, N, N, N, 0, 0.f, m->Ge, m->Gs[q], m->Gd[q], nullptr));
     return WW_OK;

@@ -397,6 +397,17 @@ int ozaki_digits(cudaStream_t s, const double *X, int ld, int rows, int K, int s
     return WW_OK;
 }
 
+// The same digits of a left operand whose row exponent maxima emax (biased,
+// of the shifted entries) were taken elsewhere (by the assembly).
+int ozaki_digits_rows_emax(cudaStream_t s, const double *X, int ld, int rows, int K, float diag_shift,
+                           const int *emax, double *scale, __nv_bfloat16 *dst, const int *skip) {
+    k_scales<<<(rows + 255) / 256, 256, 0, s>>>(emax, rows, scale, skip);
+    dim3 gd((K + 31) / 32, (rows + 31) / 32);
+    k_digits<<<gd, 256, 0, s>>>(X, ld, rows, K, diag_shift, emax, dst, skip);
+    WW_CUDA_TRY(cudaGetLastError());
+    return WW_OK;
+}
+
 // mode 0: C += A B ; mode 1: C = Psi - 0.5 Mh - A B  (A = left digits, B = right digits)
 int ozaki_gemm(cudaStream_t s, const __nv_bfloat16 *Ad, const double *sa, const __nv_bfloat16 *Bd, const double *sb,
                int M, int Nn, int K, int mode, double *C, int ldc, const double *Psi, int ldpsi, const double *Mh,
