@@ -111,27 +111,51 @@ __global__ void k_scaled_identity(float *X, int N, float v) {
     if (i < (size_t)N * N) X[i] = ((i % N) == (i / N)) ? v : 0.f;
 }
 
-// column max |.| of an N x ncols column-major block (bits of a positive double)
-__global__ void k_colmax(const double *X, int N, unsigned long long *colmax, const int *skip) {
-    if (skip && *skip) return;
-    __shared__ double red[32];
-    const double *col = X + (size_t)blockIdx.x * N;
-    double m = 0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) m = fmax(m, fabs(col[i]));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+// block max of v (256-thread blocks), every thread gets it
+__device__ __forceinline__ double block_max256(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
-        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (threadIdx.x == 0) colmax[blockIdx.x] = (unsigned long long)__double_as_longlong(m);
-    }
+    double m = red[0];
+    for (int w = 1; w < 8; ++w) m = fmax(m, red[w]);
+    __syncthreads();
+    return m;
 }
 
-__global__ void k_colscale_from_max(const unsigned long long *colmax, int n, double *scale, const int *skip) {
+// narrow solves, before the first product: Psi = B (one column per block)
+// and its column maxima as scales
+__global__ void __launch_bounds__(256) k_narrow_prep(const double *__restrict__ B, int N, double *Psi, double *psis) {
+    __shared__ double red[8];
+    const double *b = B + (size_t)blockIdx.x * N;
+    double *p = Psi + (size_t)blockIdx.x * N;
+    double m = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double v = b[i];
+        p[i] = v;
+        m = fmax(m, fabs(v));
+    }
+    m = block_max256(m, red);
+    if (threadIdx.x == 0) psis[blockIdx.x] = m;
+}
+
+// narrow solves, after a residual: max|R_j| (bits, for the convergence test)
+// and max|M_j| (the test's scale) in one pass, one column per block
+__global__ void __launch_bounds__(256) k_narrow_maxima(const double *__restrict__ R, const double *__restrict__ M,
+                                                       int N, unsigned long long *cm, double *ms, const int *skip) {
     if (skip && *skip) return;
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n) scale[j] = __longlong_as_double((long long)colmax[j]);
+    __shared__ double red[8];
+    const double *r = R + (size_t)blockIdx.x * N, *mm = M + (size_t)blockIdx.x * N;
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        a = fmax(a, fabs(r[i]));
+        b = fmax(b, fabs(mm[i]));
+    }
+    a = block_max256(a, red);
+    b = block_max256(b, red);
+    if (threadIdx.x == 0) {
+        cm[blockIdx.x] = (unsigned long long)__double_as_longlong(a);
+        ms[blockIdx.x] = b;
+    }
 }
 
 // Convergence test after residual `it` (0-based) and its correction: per
@@ -423,13 +447,10 @@ int mixed_solve(Ctx *c, double *B, int ncols) {
     cudaStream_t s = c->stream;
     const bool narrow = ncols <= SMALL_COLS;
     SolveWs &w = narrow ? m->nar : m->wide;
-    const unsigned cg = (unsigned)((ncols + 255) / 256);
     WW_CUDA_TRY(cudaMemsetAsync(w.done, 0, sizeof(int), s));
     // Psi = B, the column maxima of Psi (scale of the convergence test), M = X Psi
     if (narrow) {
-        WW_CUDA_TRY(cudaMemcpyAsync(w.Psi, B, sizeof(double) * N * ncols, cudaMemcpyDeviceToDevice, s));
-        k_colmax<<<ncols, 256, 0, s>>>(w.Psi, N, w.colmax, nullptr);
-        k_colscale_from_max<<<cg, 256, 0, s>>>(w.colmax, ncols, w.psis, nullptr);
+        k_narrow_prep<<<ncols, 256, 0, s>>>(B, N, w.Psi, w.psis);
         WW_CUDA_TRY(cudaGetLastError());
         WW_TRY(gemv_narrow_f32(s, N, ncols, N, m->X, N, w.Psi, N, 0.0, B, N));
     } else {
@@ -445,10 +466,7 @@ int mixed_solve(Ctx *c, double *B, int ncols) {
         // R = Psi - A M_it (FP64-accurate) and max|R_j|, then M += X R
         if (narrow) {
             WW_TRY(resid_narrow(s, N, ncols, N, c->A, N, B, N, w.Psi, N, w.R, N, done));
-            k_colmax<<<ncols, 256, 0, s>>>(w.R, N, cm, done);
-            k_colmax<<<ncols, 256, 0, s>>>(B, N, reinterpret_cast<unsigned long long *>(w.mscale), done);
-            k_colscale_from_max<<<cg, 256, 0, s>>>(reinterpret_cast<unsigned long long *>(w.mscale), ncols,
-                                                   w.mscale, done);
+            k_narrow_maxima<<<ncols, 256, 0, s>>>(w.R, B, N, cm, w.mscale, done);
             WW_CUDA_TRY(cudaGetLastError());
             WW_TRY(gemv_narrow_f32(s, N, ncols, N, m->X, N, w.R, N, 1.0, B, N, done));
         } else {
