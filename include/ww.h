@@ -93,7 +93,9 @@ typedef struct {
     int overlap;   /* WW_MIXED: run the base chain one stage ahead of the columns on a
                       second branch of the step graph (1), or in line (0)              */
     int ns_every;  /* WW_MIXED with overlap: move the approximate inverse to every
-                      stage's A (1), or on even stages and when it drifted (0)         */
+                      stage's A (1); on even stages and when it drifted (0); or as 0
+                      until a wide solve of an odd stage has needed three
+                      corrections in this shot, then on every stage (2)                */
     int corr_bn;   /* WW_MIXED: column tile of the refinement corrections X R (32, 64, 128) */
     int inv_bn;    /* WW_MIXED: column tile of the inverse update's products (64, 128,
                       256; 256 needs N a multiple of 256)                               */
@@ -138,7 +140,7 @@ int ww_get_stats(const ww_ctx *ctx, ww_stats *out);
  * step program is captured again.  WW_ERR_ARG in WW_FP64 (no refinement). */
 int ww_set_verify(ww_ctx *ctx, int every);
 
-/* The context's schedule.  ww_create sets the default {1, 0, 64, 128, 64, 2, 1};
+/* The context's schedule.  ww_create sets the default {1, 2, 64, 128, 64, 2, 1};
  * ww_set_schedule validates the fields (WW_ERR_ARG) and drops the captured
  * step programs, which the next call captures again. */
 int ww_set_schedule(ww_ctx *ctx, const ww_schedule *s);

@@ -290,7 +290,7 @@ int capture_overlapped(Owned *o, const double *cvec) {
             if (e != cudaSuccess) st = fail(WW_ERR_CUDA, std::string("capture join: ") + cudaGetErrorString(e));
         }
         select_parity(c, (s + 1) & 1);
-        if (st == WW_OK) st = run_base(c, (s + 1) & 3, cvec, c->sch.ns_every != 0);
+        if (st == WW_OK) st = run_base(c, (s + 1) & 3, cvec, c->sch.ns_every == 1);
         if (st == WW_OK && s < 3) {
             cudaError_t e = cudaEventRecord(o->ev_base[s + 1], side);
             if (e != cudaSuccess) st = fail(WW_ERR_CUDA, std::string("capture fork: ") + cudaGetErrorString(e));
@@ -368,7 +368,7 @@ int prologue(Owned *o, const double *cvec, int with_cols) {
         WW_TRY(launch_assemble(c));
         WW_TRY(factor(c, 1));
         if (overlapped(o, with_cols))   // the base chain runs one stage ahead
-            WW_TRY(run_base(c, 0, cvec, c->sch.ns_every != 0));
+            WW_TRY(run_base(c, 0, cvec, c->sch.ns_every == 1));
     }
     return WW_OK;
 }
@@ -953,8 +953,8 @@ int add_batch_branch(cudaGraph_t bg, Owned *o, const double *cvec, double *r, do
 
 // ---------------------------------------------------------------- schedules and the autotuner
 int check_schedule(const Ctx *c, const ww_schedule &s) {
-    if ((s.overlap != 0 && s.overlap != 1) || (s.ns_every != 0 && s.ns_every != 1))
-        return fail(WW_ERR_ARG, "ww_schedule: overlap and ns_every must be 0 or 1");
+    if ((s.overlap != 0 && s.overlap != 1) || s.ns_every < 0 || s.ns_every > 2)
+        return fail(WW_ERR_ARG, "ww_schedule: overlap must be 0 or 1, ns_every 0, 1 or 2");
     if (s.corr_bn != 32 && s.corr_bn != 64 && s.corr_bn != 128)
         return fail(WW_ERR_ARG, "ww_schedule: corr_bn must be 32, 64 or 128");
     if (s.inv_bn != 64 && s.inv_bn != 128 && s.inv_bn != 256)
@@ -1101,7 +1101,7 @@ int ww_create(ww_ctx **out, const ww_problem *p) {
     c->precision = p->precision;
     c->refine_tol = p->refine_tol > 0.0 ? p->refine_tol : 1e-13;
     c->max_refine = p->max_refine > 0 ? p->max_refine : 4;
-    c->sch = ww_schedule{1, 0, 64, 128, LU_NB, 2, 1};
+    c->sch = ww_schedule{1, 2, 64, 128, LU_NB, 2, 1};
     c->nb = c->N < LU_NB ? c->N : LU_NB;
     {
         static std::atomic<unsigned long long> next_id{1};
@@ -1510,12 +1510,14 @@ int ww_autotune(ww_ctx *ctx, const double *cvec, int probe_steps, const char *ca
         return WW_OK;
     };
     // coordinate by coordinate from the default schedule
-    ww_schedule base = ww_schedule{1, 0, 64, 128, LU_NB, 2, 1};
+    ww_schedule base = ww_schedule{1, 2, 64, 128, LU_NB, 2, 1};
     if (c->precision == WW_MIXED) {
-        for (int v : {0, 1, 2}) {   // stage program: in line, overlapped with every-stage or alternate updates
+        // stage program: in line, overlapped with every-stage, alternate, or alternate
+        // until odd stages need a third correction
+        for (int v : {0, 1, 2, 3}) {
             ww_schedule s = base;
             s.overlap = v > 0;
-            s.ns_every = v == 1;
+            s.ns_every = v == 1 ? 1 : (v == 3 ? 2 : 0);
             WW_TRY(consider(s));
         }
         base = best;

@@ -89,6 +89,7 @@ struct Mixed {
     double *ratio;                         // worst final residual ratio (bits of a double)
     unsigned *nsres, *nsres_last;          // max|I - A X| before an update: worst, and the latest (fp32 bits)
     int *ns_skip;                          // device decision: this stage reuses the previous X
+    int *maxit;                            // [2] most corrections a wide solve of each stage parity took in this shot
     int *iters;                            // [0] most residuals any solve needed, [1] their sum, [2] solves
     int *err;
     // measured residual of sampled wide solves (ww_set_verify)
@@ -100,8 +101,10 @@ struct Mixed {
 
 namespace {
 
-__global__ void k_ns_decide(const unsigned *nsres_last, float thr, int *skip) {
-    *skip = __uint_as_float(*nsres_last) < thr ? 1 : 0;
+// reuse X when the last update left max|I - A X| below thr and (maxit, when
+// given) no wide solve of this stage parity has yet needed three corrections
+__global__ void k_ns_decide(const unsigned *nsres_last, float thr, const int *maxit, int *skip) {
+    *skip = (__uint_as_float(*nsres_last) < thr && (!maxit || *maxit < 3)) ? 1 : 0;
 }
 
 __global__ void k_fold_nsres(const unsigned *last, unsigned *worst) { atomicMax(worst, *last); }
@@ -166,7 +169,7 @@ __global__ void __launch_bounds__(256) k_narrow_maxima(const double *__restrict_
 // block; returns at once when an earlier call already set *done.
 __global__ void k_converged(const unsigned long long *cm, const unsigned long long *cm_prev, const double *psis,
                             const double *ms, int ncols, double tol, int it, int last, int *done, int *iters,
-                            unsigned long long *ratio, int *status) {
+                            unsigned long long *ratio, int *status, int *maxit) {
     if (*done) return;
     __shared__ double red[32];
     double worst = 0.0;
@@ -189,6 +192,7 @@ __global__ void k_converged(const unsigned long long *cm, const unsigned long lo
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) worst = fmax(worst, red[w]);
         worst = fmax(worst, red[0]);
+        if (maxit && (worst <= tol || last)) atomicMax(maxit, it + 1);
         if (worst <= tol) {
             *done = 1;
             atomicMax(iters, it + 1);
@@ -359,6 +363,7 @@ int mixed_create(Ctx *c) {
     MA(m->nsres, 1);
     MA(m->nsres_last, 1);
     MA(m->ns_skip, 1);
+    MA(m->maxit, 2);
     MA(m->iters, 3);
     MA(m->err, 1);
     MA(m->vcm, NC);
@@ -373,6 +378,7 @@ int mixed_create(Ctx *c) {
     WW_CUDA_TRY(cudaMemset(m->nsres, 0, sizeof(unsigned)));
     WW_CUDA_TRY(cudaMemset(m->nsres_last, 0xFF, sizeof(unsigned)));   // NaN bits: never skip before an update
     WW_CUDA_TRY(cudaMemset(m->ns_skip, 0, sizeof(int)));
+    WW_CUDA_TRY(cudaMemset(m->maxit, 0, 2 * sizeof(int)));
     WW_CUDA_TRY(cudaMemset(m->iters, 0, 3 * sizeof(int)));
     WW_CUDA_TRY(cudaMemset(m->vcount, 0, sizeof(int)));
     WW_CUDA_TRY(cudaMemset(m->vmax, 0, sizeof(double)));
@@ -408,7 +414,8 @@ int mixed_setup(Ctx *c, int fresh, int update) {
     cudaStream_t s = c->stream;
     const int *skip = nullptr;
     if (!fresh && !update) {
-        k_ns_decide<<<1, 1, 0, s>>>(m->nsres_last, NS_SKIP, m->ns_skip);
+        k_ns_decide<<<1, 1, 0, s>>>(m->nsres_last, NS_SKIP, c->sch.ns_every == 2 ? m->maxit + c->par : nullptr,
+                                    m->ns_skip);
         WW_CUDA_TRY(cudaGetLastError());
         skip = m->ns_skip;
     }
@@ -422,6 +429,7 @@ int mixed_setup(Ctx *c, int fresh, int update) {
         WW_TRY(tc_slice_f32(s, m->X, N, N, N, 1, 0.f, 3, m->XslcA));   // rows of X
         for (int i = 0; i < NS_INIT; ++i) WW_TRY(ns_step(c, false, nullptr));
         WW_CUDA_TRY(cudaMemsetAsync(m->nsres_last, 0xFF, sizeof(unsigned), s));
+        WW_CUDA_TRY(cudaMemsetAsync(m->maxit, 0, 2 * sizeof(int), s));   // a new shot
     } else {
         WW_TRY(ns_step(c, skip == nullptr, skip));
     }
@@ -483,7 +491,8 @@ int mixed_solve(Ctx *c, double *B, int ncols) {
         // converged after this correction?
         k_converged<<<1, 512, 0, s>>>(cm, it > 0 ? cm_prev : nullptr, w.psis, narrow ? w.mscale : m->Rs, ncols,
                                       c->refine_tol, it, it == nit - 1, w.done, m->iters,
-                                      reinterpret_cast<unsigned long long *>(m->ratio), c->status);
+                                      reinterpret_cast<unsigned long long *>(m->ratio), c->status,
+                                      narrow ? nullptr : m->maxit + q);
         WW_CUDA_TRY(cudaGetLastError());
         unsigned long long *t = cm_prev;
         cm_prev = cm;

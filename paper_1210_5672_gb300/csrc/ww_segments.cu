@@ -834,7 +834,7 @@ void free_seg(Ctx *c, Seg *g) {
 // last move left max|I - A X| above its threshold unless the schedule updates
 // on every stage
 int seg_factor(Ctx *c, bool fresh, int st = 0) {
-    if (c->precision == WW_MIXED) return mixed_setup(c, fresh ? 1 : 0, c->sch.ns_every || st % 2 == 0);
+    if (c->precision == WW_MIXED) return mixed_setup(c, fresh ? 1 : 0, c->sch.ns_every == 1 || st % 2 == 0);
     return lu_factor_fp64(c);
 }
 

@@ -426,7 +426,7 @@ def test_schedules_agree_and_autotune_caches(ww, precision, tmp_path):
     if precision == ww.WW_MIXED:
         variants = [dict(), dict(overlap=0), dict(ns_every=1), dict(corr_bn=32), dict(corr_bn=128),
                     dict(inv_bn=64), dict(inv_bn=256, inv_ctas=1), dict(inv_ctas=1), dict(inv_bn=64, inv_ctas=1),
-                    dict(prio=0)]
+                    dict(prio=0), dict(ns_every=0)]
     else:
         variants = [dict(), dict(lu_nb=32)]
     with ww.Context(w.N, w.n, g=w.g, tau=w.tau, h=w.h, steps=w.steps, precision=precision) as ctx:
