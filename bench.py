@@ -219,7 +219,8 @@ def rooflines(form, timing, w, pk, sched=None):
         d, n_upd = dur("inverse", 2)
         if d:
             ns = NS_PAIRS * 2.0 * N ** 3
-            # the update runs on the stages that move the inverse (even ones by default)
+            # the phase events time the updates of the even stages (which always move the
+            # inverse); odd-stage updates run through the device-side decision untimed
             stages = timing.get("assembly", (0.0, 0))[1] or n_upd
             out.append(_entry(tc_gemm_name(sched or {"inv_bn": 128}), "tensor", ns, d, peak, "TFLOP/s", src, w, form,
                               role="inverse update X <- X (2I - A X), one of its two products",
