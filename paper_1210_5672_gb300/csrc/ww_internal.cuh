@@ -291,7 +291,8 @@ int lu_solve_fp64(Ctx *c, double *B, int ncols);     // B <- A^{-1} B using the 
 int mixed_create(Ctx *c);
 int tc_init();   // resolves the tensor-map encoder (called before any capture)
 void mixed_destroy(Ctx *c);
-int mixed_setup(Ctx *c, int fresh, int update);      // after assembly: operands, inverse update
+int mixed_setup(Ctx *c, int fresh, int update,       // after assembly: operands, inverse update
+                bool adaptive = true);                // (adaptive: honour the schedule's cadence 2)
 int mixed_read_stats(Ctx *c, double *ratio, double *nsres, int *iters /* [3]: max, sum, solves */, int *err,
                      double *vmax, int *vn);   // vmax, vn: measured residual of the sampled solves
 int mixed_solve(Ctx *c, double *B, int ncols);       // B <- A^{-1} B (refined)

@@ -408,14 +408,14 @@ void mixed_destroy(Ctx *c) {
 // when the last update found max|I - A X| < NS_SKIP (A changes by O(dt) per
 // stage, so the refinement contraction only grows from ~1e-7 to a few 1e-6;
 // the adaptive refinement absorbs the rest).
-int mixed_setup(Ctx *c, int fresh, int update) {
+int mixed_setup(Ctx *c, int fresh, int update, bool adaptive) {
     Mixed *m = c->mx;
     const int N = c->N;
     cudaStream_t s = c->stream;
     const int *skip = nullptr;
     if (!fresh && !update) {
-        k_ns_decide<<<1, 1, 0, s>>>(m->nsres_last, NS_SKIP, c->sch.ns_every == 2 ? m->maxit + c->par : nullptr,
-                                    m->ns_skip);
+        k_ns_decide<<<1, 1, 0, s>>>(m->nsres_last, NS_SKIP,
+                                    adaptive && c->sch.ns_every == 2 ? m->maxit + c->par : nullptr, m->ns_skip);
         WW_CUDA_TRY(cudaGetLastError());
         skip = m->ns_skip;
     }

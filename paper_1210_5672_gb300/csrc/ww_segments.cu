@@ -832,9 +832,11 @@ void free_seg(Ctx *c, Seg *g) {
 // the form's factorisation of the assembled operator; the mixed form moves its
 // approximate inverse to it (fresh: from 4/3 I), on odd stages only when the
 // last move left max|I - A X| above its threshold unless the schedule updates
-// on every stage
+// on every stage.  The shot-adaptive cadence is not used here: with a few
+// hundred columns a third correction costs less than moving the inverse.
 int seg_factor(Ctx *c, bool fresh, int st = 0) {
-    if (c->precision == WW_MIXED) return mixed_setup(c, fresh ? 1 : 0, c->sch.ns_every == 1 || st % 2 == 0);
+    if (c->precision == WW_MIXED)
+        return mixed_setup(c, fresh ? 1 : 0, c->sch.ns_every == 1 || st % 2 == 0, false);
     return lu_factor_fp64(c);
 }
 
