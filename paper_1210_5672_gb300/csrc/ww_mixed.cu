@@ -165,8 +165,11 @@ __global__ void __launch_bounds__(256) k_narrow_maxima(const double *__restrict_
 // column the residual left after the correction is estimated as
 // |R_it| (|R_it| / |R_it-1|) (the refinement is a linear iteration with a
 // fixed X), relative to max|Psi| + max|M|.  Sets *done when every column is
-// below tol; on the last allowed iteration a miss raises ST_NO_CONV.  One
-// block; returns at once when an earlier call already set *done.
+// below tol; on the last allowed iteration a miss raises ST_NO_CONV.  maxit
+// (wide solves; NULL for narrow ones) keeps the most corrections a solve of
+// this stage parity has taken in the shot, which the shot-adaptive inverse
+// cadence reads.  One block; returns at once when an earlier call already
+// set *done.
 __global__ void k_converged(const unsigned long long *cm, const unsigned long long *cm_prev, const double *psis,
                             const double *ms, int ncols, double tol, int it, int last, int *done, int *iters,
                             unsigned long long *ratio, int *status, int *maxit) {
