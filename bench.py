@@ -155,7 +155,9 @@ TRAFFIC_BYTES = {("mixed", "N2048_n512_steps1024_h1", "k_ozaki"): 85.35e6,
                  # mean of the update's two launches, profiles/k_tc_gemm_N2048.md: two CTAs
                  # per SM (54.6 and 89.9 MB) and one (54.1 and 101.2 MB)
                  ("mixed", "N2048_n512_steps1024_h1", "k_tc_gemm<128,3,3,32,2>"): 72.27e6,
-                 ("mixed", "N2048_n512_steps1024_h1", "k_tc_gemm<128,3,3,32>"): 77.65e6}
+                 ("mixed", "N2048_n512_steps1024_h1", "k_tc_gemm<128,3,3,32>"): 77.65e6,
+                 # 59.05 + 1.78 MB, profiles/k_col_rhs_N2048.md (per-pass twiddle rows)
+                 ("mixed", "N2048_n512_steps1024_h1", "k_col_rhs"): 60.84e6}
 
 # slice pairs (p, q) with p + q <= 6 of the 7 x 7 integer digits: 28 bf16 GEMMs
 OZAKI_PAIRS = 28
